@@ -1,0 +1,190 @@
+"""FP64 CPU oracle for patch-graph Gauss-Newton bundle adjustment.
+
+TEST INFRASTRUCTURE, NOT PRODUCT CODE.  Only ``tests/``, the smoke check in
+``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py`` may import
+this package.  The CUDA path never calls it and shares no code with it.
+
+The numerical work lives in ``ba_oracle.cpp`` (plain C++, FP64, templated so
+the same code runs on forward-mode dual numbers); this module only marshals
+numpy arrays through ctypes.  What each entry point computes, with the passage
+of arxiv 2408.01654 it follows:
+
+* ``edge_terms``   Eq. 2 reprojection of each patch centre, residual against the
+                   target and the analytic Jacobians in both poses and the
+                   inverse depth (Sec. 3.1).
+* ``schur_system`` the Gauss-Newton normal equations of Eq. 3 with the inverse
+                   depths eliminated (Sec. 3.2 "Efficient Global Optimization",
+                   appendix "Bundle-Adjustment Efficiency").
+* ``gn``           whole Gauss-Newton iterations: linearise, Schur-eliminate,
+                   Cholesky-solve the pose system, back-substitute the depths,
+                   retract the poses on SE(3).
+* ``grad_fwd``     exact derivatives of a linear functional of the final state
+                   with respect to single targets/weights (dual numbers through
+                   the unrolled iterations).
+
+Parity pins: every routine here is checked in ``tests/test_oracle_*.py``
+against closed forms, finite differences, a library dense solve, the gauge
+null space, world-frame equivariance and noise-free convergence; the paper
+prints no worked example, so nothing is pinned to printed values.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "ba_oracle.cpp")
+_LIB = os.path.join(_HERE, "liboracle.so")
+
+# damping and clamps: lambda_p, lambda_d, z_min, d_min
+DEFAULT_OPTS = (1e-4, 1e-4, 0.1, 1e-3)
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle (single-threaded, -O2, no fast-math)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        subprocess.check_call(["g++", "-O2", "-std=c++17", "-shared", "-fPIC", "-o", _LIB, _SRC])
+    return _LIB
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = ctypes.CDLL(build())
+    return _lib
+
+
+def _d(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _i(a):
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+def _p(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _check(st):
+    if st == 1:
+        raise ValueError("oracle: edge index out of range or patch with two source frames")
+    if st == 4:
+        raise np.linalg.LinAlgError("oracle: reduced pose system is not positive definite")
+    if st:
+        raise RuntimeError(f"oracle: status {st}")
+
+
+def se3_retract(xi, pose):
+    """T <- Exp(xi) T for one pose (t, q[x,y,z,w]), xi = (rho, phi)."""
+    xi, pose = _d(xi), _d(pose)
+    out = np.empty(7)
+    lib().oracle_se3_retract(_p(xi), _p(pose), _p(out))
+    return out
+
+
+def quat_to_rot(q):
+    q = _d(q)
+    R = np.empty(9)
+    lib().oracle_quat_to_rot(_p(q), _p(R))
+    return R.reshape(3, 3)
+
+
+def edge_terms(s, poses=None, patches=None, targets=None, z_min=DEFAULT_OPTS[2]):
+    """Per-edge (proj [E,2], r [E,2], Ji [E,2,6], Jj [E,2,6], Jd [E,2], valid [E])."""
+    poses = _d(s.poses if poses is None else poses)
+    patches = _d(s.patches if patches is None else patches)
+    targets = _d(s.targets if targets is None else targets)
+    E = len(s.kk)
+    proj, res = np.empty((E, 2)), np.empty((E, 2))
+    Ji, Jj, Jd = np.empty((E, 2, 6)), np.empty((E, 2, 6)), np.empty((E, 2))
+    valid = np.empty(E, np.int32)
+    ii, jj, kk = _i(s.ii), _i(s.jj), _i(s.kk)
+    _check(lib().oracle_edge_terms(
+        s.N, s.P, E, _p(poses), _p(patches), _p(ii), _p(jj), _p(kk), _p(targets),
+        _p(_d(s.intrinsics)), ctypes.c_double(z_min), _p(proj), _p(res), _p(Ji), _p(Jj), _p(Jd), _p(valid)))
+    return proj, res, Ji, Jj, Jd, valid.astype(bool)
+
+
+def schur_system(s, fixed=None, opts=DEFAULT_OPTS, poses=None, patches=None, targets=None, weights=None):
+    """Reduced pose system at the given state: (S [n,n], y [n], Ct [P], w [P], cost)."""
+    fixed = s.fixed if fixed is None else fixed
+    poses = _d(s.poses if poses is None else poses)
+    patches = _d(s.patches if patches is None else patches)
+    targets = _d(s.targets if targets is None else targets)
+    weights = _d(s.weights if weights is None else weights)
+    n = 6 * (s.N - fixed)
+    S, y = np.empty((n, n)), np.empty(n)
+    Ct, w = np.empty(s.P), np.empty(s.P)
+    cost = ctypes.c_double()
+    ii, jj, kk = _i(s.ii), _i(s.jj), _i(s.kk)
+    _check(lib().oracle_schur_system(
+        s.N, s.P, len(s.kk), _p(poses), _p(patches), _p(ii), _p(jj), _p(kk), _p(targets), _p(weights),
+        _p(_d(s.intrinsics)), fixed, _p(_d(opts)), _p(S), _p(y), _p(Ct), _p(w), ctypes.byref(cost)))
+    return S, y, Ct, w, cost.value
+
+
+def gn(s, iters=None, fixed=None, opts=DEFAULT_OPTS, poses=None, patches=None, targets=None, weights=None):
+    """Run GN iterations from the scene's state.  Returns a dict with the final
+    poses [N,7], patches [P,3,3,3], the per-iteration steps dxi [iters,n] and
+    dd [iters,P], and the cost before each iteration plus after the last."""
+    iters = s.iters if iters is None else iters
+    fixed = s.fixed if fixed is None else fixed
+    poses = _d(s.poses if poses is None else poses).copy()
+    patches = _d(s.patches if patches is None else patches).copy()
+    targets = _d(s.targets if targets is None else targets)
+    weights = _d(s.weights if weights is None else weights)
+    n = 6 * (s.N - fixed)
+    dxi, dd, cost = np.empty((iters, n)), np.empty((iters, s.P)), np.empty(iters + 1)
+    ii, jj, kk = _i(s.ii), _i(s.jj), _i(s.kk)
+    _check(lib().oracle_gn(
+        s.N, s.P, len(s.kk), _p(poses), _p(patches), _p(ii), _p(jj), _p(kk), _p(targets), _p(weights),
+        _p(_d(s.intrinsics)), iters, fixed, _p(_d(opts)), _p(dxi), _p(dd), _p(cost)))
+    return {"poses": poses, "patches": patches, "dxi": dxi, "dd": dd, "cost": cost}
+
+
+def gn_steps(s, iters=None, fixed=None, opts=DEFAULT_OPTS):
+    """States after each GN iteration: list of (poses, depths) of length iters."""
+    iters = s.iters if iters is None else iters
+    out, poses, patches = [], s.poses, s.patches
+    for _ in range(iters):
+        r = gn(s, 1, fixed, opts, poses=poses, patches=patches)
+        poses, patches = r["poses"], r["patches"]
+        out.append((poses.copy(), patches[:, 2, 1, 1].copy()))
+    return out
+
+
+def grad_fwd(s, a, b, kind, index, iters=None, fixed=None, opts=DEFAULT_OPTS):
+    """d/d(input coordinate) of <a, poses_final> + <b, depths_final>, one value
+    per coordinate; kind 0 = target, 1 = weight; index into the flat [E,2]."""
+    iters = s.iters if iters is None else iters
+    fixed = s.fixed if fixed is None else fixed
+    kind = _i(kind)
+    index = np.ascontiguousarray(index, dtype=np.int64)
+    out = np.empty(len(kind))
+    ii, jj, kk = _i(s.ii), _i(s.jj), _i(s.kk)
+    _check(lib().oracle_grad_fwd(
+        s.N, s.P, len(s.kk), _p(_d(s.poses)), _p(_d(s.patches)), _p(ii), _p(jj), _p(kk), _p(_d(s.targets)),
+        _p(_d(s.weights)), _p(_d(s.intrinsics)), iters, fixed, _p(_d(opts)), _p(_d(a)), _p(_d(b)),
+        len(kind), _p(kind), _p(index), _p(out)))
+    return out
+
+
+def block_keys(ii, jj, fixed):
+    """Canonical pose-pose block keys of the reduced system's B part: the sorted
+    unique (a, b), a <= b, over (i,i), (j,j), (min, max) of every non-self edge,
+    both poses free (index >= fixed).  Plain Python, for bit-exact checks."""
+    keys = set()
+    for i, j in zip(np.asarray(ii).tolist(), np.asarray(jj).tolist()):
+        if i == j:
+            continue
+        for a, b in ((i, i), (j, j), (min(i, j), max(i, j))):
+            if a >= fixed and b >= fixed:
+                keys.add((a, b))
+    return np.array(sorted(keys), dtype=np.int32).reshape(-1, 2)

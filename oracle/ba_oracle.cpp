@@ -1,0 +1,538 @@
+// FP64 CPU oracle for Gauss-Newton bundle adjustment over the DPVO patch graph.
+//
+// TEST INFRASTRUCTURE, NOT PRODUCT CODE.  Only the test suite, the smoke check
+// and the benchmark's CPU-baseline leg may load this library.  It shares no
+// code, header, table or constant with the CUDA path.
+//
+// What it computes (arxiv 2408.01654, Sec. 3.1 "DPVO Preliminaries"):
+//   Eq. 2  reprojection  P'_ikj = Pi[ G_j^-1 G_i Pi^-1(P_ik) ]
+//   Eq. 3  argmin_{G,d} sum_(i,k,j) || P'_ikj - I_ikj ||^2_{Sigma},  Sigma = diag(w)
+// solved by plain Gauss-Newton, with the inverse depths Schur-eliminated and
+// the pose system Cholesky-factored (the block-sparse BA of Sec. 3.2
+// "Efficient Global Optimization" and the appendix "Bundle-Adjustment
+// Efficiency", which names the pose-block Cholesky of the Schur complement).
+//
+// Readings of points the paper leaves open (each also listed in the design
+// notes of the repository):
+//   * residual on the patch centre pixel only: r = I - proj (2-vector per edge);
+//   * cost = sum_c w_c r_c^2 (w multiplies, Eq. 3 with Sigma = diag(w));
+//   * poses stored world->camera, T_i = G_i^-1, as (t, q) with q = (x,y,z,w);
+//     perturbation on the left, T <- Exp(xi) T, xi = (rho, phi) translation first;
+//   * an edge is masked when i == j or when the reprojected point's depth in
+//     frame j, Z/d, is below z_min (i.e. Z <= z_min * d);
+//   * damping: lambda_p on every free-pose diagonal, lambda_d added to each
+//     depth diagonal; pure GN, no step rejection;
+//   * inverse depths clamped below at d_min after each step; the new depth is
+//     written to all nine pixels of the patch.
+//
+// Every routine is templated on the scalar so the same plain code runs on
+// forward-mode dual numbers (exact derivatives for the gradient oracle).
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <algorithm>
+#include <vector>
+
+namespace {
+
+// ----------------------------------------------------------------------------
+// forward-mode dual numbers (value, derivative along one seed direction)
+// ----------------------------------------------------------------------------
+struct Dual {
+  double v, d;
+  Dual() : v(0), d(0) {}
+  Dual(double x) : v(x), d(0) {}
+  Dual(double x, double dx) : v(x), d(dx) {}
+};
+inline Dual operator+(Dual a, Dual b) { return {a.v + b.v, a.d + b.d}; }
+inline Dual operator-(Dual a, Dual b) { return {a.v - b.v, a.d - b.d}; }
+inline Dual operator-(Dual a) { return {-a.v, -a.d}; }
+inline Dual operator*(Dual a, Dual b) { return {a.v * b.v, a.d * b.v + a.v * b.d}; }
+inline Dual operator/(Dual a, Dual b) { return {a.v / b.v, (a.d * b.v - a.v * b.d) / (b.v * b.v)}; }
+inline Dual& operator+=(Dual& a, Dual b) { a = a + b; return a; }
+inline Dual& operator-=(Dual& a, Dual b) { a = a - b; return a; }
+inline Dual& operator*=(Dual& a, Dual b) { a = a * b; return a; }
+inline Dual sqrt(Dual a) { double s = std::sqrt(a.v); return {s, a.d / (2.0 * s)}; }
+inline Dual sin(Dual a) { return {std::sin(a.v), a.d * std::cos(a.v)}; }
+inline Dual cos(Dual a) { return {std::cos(a.v), -a.d * std::sin(a.v)}; }
+inline double sqrt(double a) { return std::sqrt(a); }
+inline double sin(double a) { return std::sin(a); }
+inline double cos(double a) { return std::cos(a); }
+inline double val(double x) { return x; }
+inline double val(Dual x) { return x.v; }
+
+// ----------------------------------------------------------------------------
+// rotations and poses
+// ----------------------------------------------------------------------------
+template <class T> struct Pose { T t[3]; T q[4]; };  // world->camera, q=(x,y,z,w)
+
+template <class T> void quat_to_rot(const T q[4], T R[9]) {
+  const T x = q[0], y = q[1], z = q[2], w = q[3];
+  R[0] = 1.0 - 2.0 * (y * y + z * z); R[1] = 2.0 * (x * y - z * w);       R[2] = 2.0 * (x * z + y * w);
+  R[3] = 2.0 * (x * y + z * w);       R[4] = 1.0 - 2.0 * (x * x + z * z); R[5] = 2.0 * (y * z - x * w);
+  R[6] = 2.0 * (x * z - y * w);       R[7] = 2.0 * (y * z + x * w);       R[8] = 1.0 - 2.0 * (x * x + y * y);
+}
+
+template <class T> void quat_mul(const T a[4], const T b[4], T c[4]) {  // c = a (x) b
+  c[0] = a[3] * b[0] + a[0] * b[3] + a[1] * b[2] - a[2] * b[1];
+  c[1] = a[3] * b[1] - a[0] * b[2] + a[1] * b[3] + a[2] * b[0];
+  c[2] = a[3] * b[2] + a[0] * b[1] - a[1] * b[0] + a[2] * b[3];
+  c[3] = a[3] * b[3] - a[0] * b[0] - a[1] * b[1] - a[2] * b[2];
+}
+
+// T <- Exp(xi) T with xi = (rho, phi):  Exp(xi) = [ R(phi)  V(phi) rho ; 0 1 ],
+// R(phi) by the unit quaternion (sin(th/2) phi/th, cos(th/2)),
+// V = I + B [phi]x + C [phi]x^2,  B = (1-cos th)/th^2,  C = (th - sin th)/th^3.
+// Below th = 1e-3 every coefficient is its Taylor series in th^2 (exact to
+// FP64 there); above, B is evaluated as 2 sin^2(th/2)/th^2 to avoid cancellation.
+template <class T> void se3_retract(const T xi[6], Pose<T>& p) {
+  const T* rho = xi;
+  const T* phi = xi + 3;
+  const T th2 = phi[0] * phi[0] + phi[1] * phi[1] + phi[2] * phi[2];
+  T a, c, B, C;  // a = sin(th/2)/th, c = cos(th/2)
+  if (val(th2) < 1e-6) {
+    const T th4 = th2 * th2;
+    a = 0.5 - th2 / 48.0 + th4 / 3840.0;
+    c = 1.0 - th2 / 8.0 + th4 / 384.0;
+    B = 0.5 - th2 / 24.0 + th4 / 720.0;
+    C = 1.0 / 6.0 - th2 / 120.0 + th4 / 5040.0;
+  } else {
+    const T th = sqrt(th2);
+    const T sh = sin(th * 0.5);
+    a = sh / th;
+    c = cos(th * 0.5);
+    B = 2.0 * sh * sh / th2;
+    C = (th - sin(th)) / (th2 * th);
+  }
+  const T qe[4] = {a * phi[0], a * phi[1], a * phi[2], c};
+  // V rho = rho + B (phi x rho) + C (phi x (phi x rho))
+  T pxr[3] = {phi[1] * rho[2] - phi[2] * rho[1], phi[2] * rho[0] - phi[0] * rho[2],
+              phi[0] * rho[1] - phi[1] * rho[0]};
+  T pxpxr[3] = {phi[1] * pxr[2] - phi[2] * pxr[1], phi[2] * pxr[0] - phi[0] * pxr[2],
+                phi[0] * pxr[1] - phi[1] * pxr[0]};
+  T Re[9];
+  quat_to_rot(qe, Re);
+  T tn[3];
+  for (int r = 0; r < 3; ++r)
+    tn[r] = Re[3 * r] * p.t[0] + Re[3 * r + 1] * p.t[1] + Re[3 * r + 2] * p.t[2] + rho[r] +
+            B * pxr[r] + C * pxpxr[r];
+  T qn[4];
+  quat_mul(qe, p.q, qn);
+  const T nrm = sqrt(qn[0] * qn[0] + qn[1] * qn[1] + qn[2] * qn[2] + qn[3] * qn[3]);
+  for (int r = 0; r < 3; ++r) p.t[r] = tn[r];
+  for (int r = 0; r < 4; ++r) p.q[r] = qn[r] / nrm;
+}
+
+// ----------------------------------------------------------------------------
+// per-edge reprojection, residual and Jacobians (Eq. 2 and Eq. 3)
+// ----------------------------------------------------------------------------
+template <class T> struct EdgeTerms {
+  T proj[2], r[2];
+  T Ji[2][6], Jj[2][6], Jd[2];
+  bool valid;
+};
+
+template <class T>
+void edge_terms(const Pose<T>& Pi, const Pose<T>& Pj, T u, T v, T d, const T tgt[2],
+                const double K[4], double z_min, bool self_edge, EdgeTerms<T>& o) {
+  const double fx = K[0], fy = K[1], cx = K[2], cy = K[3];
+  T Ri[9], Rj[9], R[9], t[3];
+  quat_to_rot(Pi.q, Ri);
+  quat_to_rot(Pj.q, Rj);
+  // T_ij = T_j T_i^-1 :  R = Rj Ri^T,  t = tj - R ti
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c)
+      R[3 * r + c] = Rj[3 * r] * Ri[3 * c] + Rj[3 * r + 1] * Ri[3 * c + 1] + Rj[3 * r + 2] * Ri[3 * c + 2];
+  for (int r = 0; r < 3; ++r)
+    t[r] = Pj.t[r] - (R[3 * r] * Pi.t[0] + R[3 * r + 1] * Pi.t[1] + R[3 * r + 2] * Pi.t[2]);
+  // back-projection with inverse depth: homogeneous (x, y, 1, d)
+  const T xb[3] = {(u - cx) / fx, (v - cy) / fy, T(1.0)};
+  T X[3];
+  for (int r = 0; r < 3; ++r) X[r] = R[3 * r] * xb[0] + R[3 * r + 1] * xb[1] + R[3 * r + 2] * xb[2] + t[r] * d;
+  o.valid = !self_edge && val(X[2]) > z_min * val(d);
+  const T iz = 1.0 / X[2];
+  o.proj[0] = fx * X[0] * iz + cx;
+  o.proj[1] = fy * X[1] * iz + cy;
+  o.r[0] = tgt[0] - o.proj[0];
+  o.r[1] = tgt[1] - o.proj[1];
+  // D = d proj / d X
+  const T D[2][3] = {{fx * iz, T(0.0), -fx * X[0] * iz * iz}, {T(0.0), fy * iz, -fy * X[1] * iz * iz}};
+  // dX/dxi_j = [ d I | -[X]x ]
+  const T M[3][6] = {{d, T(0.0), T(0.0), T(0.0), X[2], -X[1]},
+                     {T(0.0), d, T(0.0), -X[2], T(0.0), X[0]},
+                     {T(0.0), T(0.0), d, X[1], -X[0], T(0.0)}};
+  // Ad(T_ij) = [ R  [t]x R ; 0  R ]
+  T tx[9] = {T(0.0), -t[2], t[1], t[2], T(0.0), -t[0], -t[1], t[0], T(0.0)};
+  T txR[9];
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c)
+      txR[3 * r + c] = tx[3 * r] * R[c] + tx[3 * r + 1] * R[3 + c] + tx[3 * r + 2] * R[6 + c];
+  T Ad[6][6];
+  for (int r = 0; r < 6; ++r)
+    for (int c = 0; c < 6; ++c) Ad[r][c] = T(0.0);
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c) {
+      Ad[r][c] = R[3 * r + c];
+      Ad[r][3 + c] = txR[3 * r + c];
+      Ad[3 + r][3 + c] = R[3 * r + c];
+    }
+  for (int a = 0; a < 2; ++a) {
+    for (int c = 0; c < 6; ++c) {
+      T s = T(0.0);
+      for (int m = 0; m < 3; ++m) s += D[a][m] * M[m][c];
+      o.Jj[a][c] = s;
+    }
+    for (int c = 0; c < 6; ++c) {
+      T s = T(0.0);
+      for (int m = 0; m < 6; ++m) s += o.Jj[a][m] * Ad[m][c];
+      o.Ji[a][c] = -s;
+    }
+    o.Jd[a] = D[a][0] * t[0] + D[a][1] * t[1] + D[a][2] * t[2];
+  }
+}
+
+// ----------------------------------------------------------------------------
+// problem description shared by the entry points
+// ----------------------------------------------------------------------------
+struct Opts { double lambda_p, lambda_d, z_min, d_min; };
+
+template <class T> struct Problem {
+  int N, P, E;
+  std::vector<Pose<T>> poses;      // [N]
+  std::vector<T> u, v, d;          // patch centre pixel and inverse depth [P]
+  const int *ii, *jj, *kk;
+  std::vector<T> tgt, wgt;         // [E,2]
+  double K[4];
+};
+
+template <class T>
+void load_problem(Problem<T>& pb, int N, int P, int E, const double* poses, const double* patches,
+                  const int* ii, const int* jj, const int* kk, const double* targets,
+                  const double* weights, const double* intr) {
+  pb.N = N; pb.P = P; pb.E = E;
+  pb.poses.resize(N);
+  for (int a = 0; a < N; ++a) {
+    for (int r = 0; r < 3; ++r) pb.poses[a].t[r] = T(poses[7 * a + r]);
+    for (int r = 0; r < 4; ++r) pb.poses[a].q[r] = T(poses[7 * a + 3 + r]);
+  }
+  pb.u.resize(P); pb.v.resize(P); pb.d.resize(P);
+  for (int k = 0; k < P; ++k) {  // patches [P,3,3,3]: centre pixel is [k][c][1][1]
+    pb.u[k] = T(patches[27 * k + 0 * 9 + 4]);
+    pb.v[k] = T(patches[27 * k + 1 * 9 + 4]);
+    pb.d[k] = T(patches[27 * k + 2 * 9 + 4]);
+  }
+  pb.ii = ii; pb.jj = jj; pb.kk = kk;
+  pb.tgt.resize(2 * (size_t)E); pb.wgt.resize(2 * (size_t)E);
+  for (size_t e = 0; e < 2 * (size_t)E; ++e) { pb.tgt[e] = T(targets[e]); pb.wgt[e] = T(weights[e]); }
+  for (int r = 0; r < 4; ++r) pb.K[r] = intr[r];
+}
+
+int check_indices(int N, int P, int E, const int* ii, const int* jj, const int* kk) {
+  std::vector<int> src(P, -1);
+  for (int e = 0; e < E; ++e) {
+    if (ii[e] < 0 || ii[e] >= N || jj[e] < 0 || jj[e] >= N || kk[e] < 0 || kk[e] >= P) return 1;
+    if (src[kk[e]] < 0) src[kk[e]] = ii[e];
+    else if (src[kk[e]] != ii[e]) return 1;  // one source frame per patch
+  }
+  return 0;
+}
+
+// ----------------------------------------------------------------------------
+// normal equations with the inverse depths eliminated (Schur complement)
+//   H = [ B  E ; E^T  C ],  g = [ v ; w ],  r ~ r - J delta  =>  H delta = g
+//   S = B + lambda_p I - E Ct^-1 E^T,   y = v - E Ct^-1 w,   Ct = C + lambda_d
+// Only free poses (index >= fixed) are variables.
+// ----------------------------------------------------------------------------
+template <class T> struct Linear {
+  int n;                                   // 6 * free poses
+  std::vector<T> B, vv;                    // dense [n*n], [n]
+  std::vector<T> C, w;                     // [P]
+  std::vector<std::vector<std::pair<int, std::vector<T>>>> Ek;  // per patch: (free pose, 6-vector)
+  T cost;
+};
+
+template <class T> std::vector<T>& ek_slot(std::vector<std::pair<int, std::vector<T>>>& lst, int a) {
+  for (auto& pr : lst)
+    if (pr.first == a) return pr.second;
+  lst.emplace_back(a, std::vector<T>(6, T(0.0)));
+  return lst.back().second;
+}
+
+template <class T>
+void linearize(const Problem<T>& pb, int fixed, const Opts& o, Linear<T>& L) {
+  const int nf = pb.N - fixed;
+  L.n = 6 * nf;
+  L.B.assign((size_t)L.n * L.n, T(0.0));
+  L.vv.assign(L.n, T(0.0));
+  L.C.assign(pb.P, T(0.0));
+  L.w.assign(pb.P, T(0.0));
+  L.Ek.assign(pb.P, {});
+  L.cost = T(0.0);
+  EdgeTerms<T> et;
+  for (int e = 0; e < pb.E; ++e) {  // input order
+    const int i = pb.ii[e], j = pb.jj[e], k = pb.kk[e];
+    edge_terms(pb.poses[i], pb.poses[j], pb.u[k], pb.v[k], pb.d[k], &pb.tgt[2 * (size_t)e], pb.K, o.z_min,
+               i == j, et);
+    if (!et.valid) continue;
+    const T* w = &pb.wgt[2 * (size_t)e];
+    for (int c = 0; c < 2; ++c) L.cost += w[c] * et.r[c] * et.r[c];
+    const int fi = i - fixed, fj = j - fixed;  // free index or negative
+    // depth-depth and depth-gradient
+    for (int c = 0; c < 2; ++c) {
+      L.C[k] += w[c] * et.Jd[c] * et.Jd[c];
+      L.w[k] += w[c] * et.Jd[c] * et.r[c];
+    }
+    const T* Jp[2] = {&et.Ji[0][0], &et.Jj[0][0]};
+    const int fp[2] = {fi, fj};
+    for (int s = 0; s < 2; ++s) {
+      if (fp[s] < 0) continue;
+      // pose gradient and pose-depth coupling
+      std::vector<T>& Ev = ek_slot(L.Ek[k], fp[s]);
+      for (int r = 0; r < 6; ++r) {
+        T gv = T(0.0), ev = T(0.0);
+        for (int c = 0; c < 2; ++c) {
+          gv += w[c] * Jp[s][6 * c + r] * et.r[c];
+          ev += w[c] * Jp[s][6 * c + r] * et.Jd[c];
+        }
+        L.vv[6 * fp[s] + r] += gv;
+        Ev[r] += ev;
+      }
+      // pose-pose blocks
+      for (int s2 = 0; s2 < 2; ++s2) {
+        if (fp[s2] < 0) continue;
+        for (int r = 0; r < 6; ++r)
+          for (int cc = 0; cc < 6; ++cc) {
+            T h = T(0.0);
+            for (int c = 0; c < 2; ++c) h += w[c] * Jp[s][6 * c + r] * Jp[s2][6 * c + cc];
+            L.B[(size_t)(6 * fp[s] + r) * L.n + 6 * fp[s2] + cc] += h;
+          }
+      }
+    }
+  }
+}
+
+template <class T>
+void schur(const Problem<T>& pb, const Opts& o, Linear<T>& L, std::vector<T>& S, std::vector<T>& y) {
+  const int n = L.n;
+  S = L.B;
+  y = L.vv;
+  for (int r = 0; r < n; ++r) S[(size_t)r * n + r] += o.lambda_p;
+  for (int k = 0; k < pb.P; ++k) {
+    const T Ct = L.C[k] + o.lambda_d;
+    for (auto& pa : L.Ek[k]) {
+      for (int r = 0; r < 6; ++r) y[6 * pa.first + r] -= pa.second[r] * L.w[k] / Ct;
+      for (auto& pb2 : L.Ek[k])
+        for (int r = 0; r < 6; ++r)
+          for (int c = 0; c < 6; ++c)
+            S[(size_t)(6 * pa.first + r) * n + 6 * pb2.first + c] -= pa.second[r] * pb2.second[c] / Ct;
+    }
+  }
+}
+
+// plain dense Cholesky S = L L^T (lower, in place) and the two triangular solves
+template <class T> int cholesky_solve(std::vector<T>& S, int n, const std::vector<T>& y, std::vector<T>& x) {
+  for (int j = 0; j < n; ++j) {
+    T s = S[(size_t)j * n + j];
+    for (int p = 0; p < j; ++p) s -= S[(size_t)j * n + p] * S[(size_t)j * n + p];
+    if (!(val(s) > 0.0)) return 4;  // not positive definite
+    const T ljj = sqrt(s);
+    S[(size_t)j * n + j] = ljj;
+    for (int i = j + 1; i < n; ++i) {
+      T a = S[(size_t)i * n + j];
+      for (int p = 0; p < j; ++p) a -= S[(size_t)i * n + p] * S[(size_t)j * n + p];
+      S[(size_t)i * n + j] = a / ljj;
+    }
+  }
+  x = y;
+  for (int i = 0; i < n; ++i) {  // L z = y
+    T a = x[i];
+    for (int p = 0; p < i; ++p) a -= S[(size_t)i * n + p] * x[p];
+    x[i] = a / S[(size_t)i * n + i];
+  }
+  for (int i = n - 1; i >= 0; --i) {  // L^T x = z
+    T a = x[i];
+    for (int p = i + 1; p < n; ++p) a -= S[(size_t)p * n + i] * x[p];
+    x[i] = a / S[(size_t)i * n + i];
+  }
+  return 0;
+}
+
+// one GN iteration: linearise, eliminate depths, solve, back-substitute, retract
+template <class T>
+int gn_iteration(Problem<T>& pb, int fixed, const Opts& o, std::vector<T>* dxi_out, std::vector<T>* dd_out,
+                 T* cost_out) {
+  Linear<T> L;
+  linearize(pb, fixed, o, L);
+  std::vector<T> S, y, dxi;
+  schur(pb, o, L, S, y);
+  const int n = L.n;
+  int st = cholesky_solve(S, n, y, dxi);
+  if (st) return st;
+  std::vector<T> dd(pb.P, T(0.0));
+  for (int k = 0; k < pb.P; ++k) {  // dd_k = Ct_k^-1 (w_k - sum_a E_ak^T dxi_a)
+    T a = L.w[k];
+    for (auto& pa : L.Ek[k])
+      for (int r = 0; r < 6; ++r) a -= pa.second[r] * dxi[6 * pa.first + r];
+    dd[k] = a / (L.C[k] + o.lambda_d);
+  }
+  for (int f = 0; f < pb.N - fixed; ++f) se3_retract(&dxi[6 * f], pb.poses[fixed + f]);
+  for (int k = 0; k < pb.P; ++k) {
+    T nd = pb.d[k] + dd[k];
+    pb.d[k] = val(nd) > o.d_min ? nd : T(o.d_min);
+  }
+  if (dxi_out) *dxi_out = dxi;
+  if (dd_out) *dd_out = dd;
+  if (cost_out) *cost_out = L.cost;
+  return 0;
+}
+
+template <class T>
+T problem_cost(const Problem<T>& pb, const Opts& o) {
+  T cost = T(0.0);
+  EdgeTerms<T> et;
+  for (int e = 0; e < pb.E; ++e) {
+    const int i = pb.ii[e], j = pb.jj[e], k = pb.kk[e];
+    edge_terms(pb.poses[i], pb.poses[j], pb.u[k], pb.v[k], pb.d[k], &pb.tgt[2 * (size_t)e], pb.K, o.z_min,
+               i == j, et);
+    if (!et.valid) continue;
+    for (int c = 0; c < 2; ++c) cost += pb.wgt[2 * (size_t)e + c] * et.r[c] * et.r[c];
+  }
+  return cost;
+}
+
+void store_state(const Problem<double>& pb, double* poses, double* patches) {
+  for (int a = 0; a < pb.N; ++a) {
+    for (int r = 0; r < 3; ++r) poses[7 * a + r] = pb.poses[a].t[r];
+    for (int r = 0; r < 4; ++r) poses[7 * a + 3 + r] = pb.poses[a].q[r];
+  }
+  for (int k = 0; k < pb.P; ++k)
+    for (int p = 0; p < 9; ++p) patches[27 * k + 18 + p] = pb.d[k];
+}
+
+}  // namespace
+
+// ============================================================================
+// C entry points (ctypes).  All arrays are host memory, row-major, float64
+// unless stated; indices int32.  Return 0 on success, 1 on bad indices,
+// 4 if the reduced pose system is not positive definite.
+// ============================================================================
+extern "C" {
+
+int oracle_version() { return 1; }
+
+void oracle_se3_retract(const double* xi, const double* pose_in, double* pose_out) {
+  Pose<double> p;
+  for (int r = 0; r < 3; ++r) p.t[r] = pose_in[r];
+  for (int r = 0; r < 4; ++r) p.q[r] = pose_in[3 + r];
+  se3_retract(xi, p);
+  for (int r = 0; r < 3; ++r) pose_out[r] = p.t[r];
+  for (int r = 0; r < 4; ++r) pose_out[3 + r] = p.q[r];
+}
+
+void oracle_quat_to_rot(const double* q, double* R) { quat_to_rot(q, R); }
+
+// per-edge projection, Jacobians (Ji, Jj [E,2,6], Jd [E,2]) and validity
+int oracle_edge_terms(int N, int P, int E, const double* poses, const double* patches, const int* ii,
+                      const int* jj, const int* kk, const double* targets, const double* intr, double z_min,
+                      double* proj, double* res, double* Ji, double* Jj, double* Jd, int* valid) {
+  if (check_indices(N, P, E, ii, jj, kk)) return 1;
+  std::vector<double> ones(2 * (size_t)E, 1.0);
+  Problem<double> pb;
+  load_problem(pb, N, P, E, poses, patches, ii, jj, kk, targets, ones.data(), intr);
+  EdgeTerms<double> et;
+  for (int e = 0; e < E; ++e) {
+    const int i = ii[e], j = jj[e], k = kk[e];
+    edge_terms(pb.poses[i], pb.poses[j], pb.u[k], pb.v[k], pb.d[k], &pb.tgt[2 * (size_t)e], pb.K, z_min, i == j,
+               et);
+    for (int c = 0; c < 2; ++c) {
+      proj[2 * e + c] = et.proj[c];
+      res[2 * e + c] = et.r[c];
+      Jd[2 * e + c] = et.Jd[c];
+      for (int m = 0; m < 6; ++m) {
+        Ji[12 * (size_t)e + 6 * c + m] = et.Ji[c][m];
+        Jj[12 * (size_t)e + 6 * c + m] = et.Jj[c][m];
+      }
+    }
+    valid[e] = et.valid ? 1 : 0;
+  }
+  return 0;
+}
+
+// reduced pose system of the current state: S [n*n] (full, symmetric), y [n],
+// Ct [P] = C + lambda_d, w [P]; n = 6 (N - fixed); cost = sum w r^2
+int oracle_schur_system(int N, int P, int E, const double* poses, const double* patches, const int* ii,
+                        const int* jj, const int* kk, const double* targets, const double* weights,
+                        const double* intr, int fixed, const double* opts4, double* S, double* y, double* Ct,
+                        double* w, double* cost) {
+  if (check_indices(N, P, E, ii, jj, kk)) return 1;
+  const Opts o{opts4[0], opts4[1], opts4[2], opts4[3]};
+  Problem<double> pb;
+  load_problem(pb, N, P, E, poses, patches, ii, jj, kk, targets, weights, intr);
+  Linear<double> L;
+  linearize(pb, fixed, o, L);
+  std::vector<double> Sv, yv;
+  schur(pb, o, L, Sv, yv);
+  std::memcpy(S, Sv.data(), Sv.size() * sizeof(double));
+  std::memcpy(y, yv.data(), yv.size() * sizeof(double));
+  for (int k = 0; k < P; ++k) { Ct[k] = L.C[k] + o.lambda_d; w[k] = L.w[k]; }
+  *cost = L.cost;
+  return 0;
+}
+
+// `iters` GN iterations in place on poses [N,7] and patches [P,3,3,3];
+// dxi [iters, 6(N-fixed)], dd [iters, P], cost [iters+1] (cost before each
+// iteration and after the last).
+int oracle_gn(int N, int P, int E, double* poses, double* patches, const int* ii, const int* jj, const int* kk,
+              const double* targets, const double* weights, const double* intr, int iters, int fixed,
+              const double* opts4, double* dxi, double* dd, double* cost) {
+  if (check_indices(N, P, E, ii, jj, kk)) return 1;
+  const Opts o{opts4[0], opts4[1], opts4[2], opts4[3]};
+  Problem<double> pb;
+  load_problem(pb, N, P, E, poses, patches, ii, jj, kk, targets, weights, intr);
+  const int n = 6 * (N - fixed);
+  for (int it = 0; it < iters; ++it) {
+    std::vector<double> x, dk;
+    double c;
+    int st = gn_iteration(pb, fixed, o, &x, &dk, &c);
+    if (st) return st;
+    if (dxi) std::memcpy(dxi + (size_t)it * n, x.data(), n * sizeof(double));
+    if (dd) std::memcpy(dd + (size_t)it * P, dk.data(), P * sizeof(double));
+    if (cost) cost[it] = c;
+    store_state(pb, poses, patches);
+  }
+  if (cost) cost[iters] = problem_cost(pb, o);
+  return 0;
+}
+
+// forward-mode derivative of  L = <a, poses_final> + <b, depths_final>  with
+// respect to single input coordinates: kind[c] = 0 -> targets[index[c]],
+// kind[c] = 1 -> weights[index[c]] (index into the flattened [E,2] array).
+// One dual-number GN run per coordinate.
+int oracle_grad_fwd(int N, int P, int E, const double* poses, const double* patches, const int* ii,
+                    const int* jj, const int* kk, const double* targets, const double* weights,
+                    const double* intr, int iters, int fixed, const double* opts4, const double* a,
+                    const double* b, int ncoord, const int* kind, const long long* index, double* out) {
+  if (check_indices(N, P, E, ii, jj, kk)) return 1;
+  const Opts o{opts4[0], opts4[1], opts4[2], opts4[3]};
+  for (int c = 0; c < ncoord; ++c) {
+    Problem<Dual> pb;
+    load_problem(pb, N, P, E, poses, patches, ii, jj, kk, targets, weights, intr);
+    if (kind[c] == 0) pb.tgt[index[c]].d = 1.0;
+    else pb.wgt[index[c]].d = 1.0;
+    for (int it = 0; it < iters; ++it) {
+      int st = gn_iteration(pb, fixed, o, (std::vector<Dual>*)nullptr, (std::vector<Dual>*)nullptr,
+                            (Dual*)nullptr);
+      if (st) return st;
+    }
+    double g = 0.0;
+    for (int q = 0; q < N; ++q) {
+      for (int r = 0; r < 3; ++r) g += a[7 * q + r] * pb.poses[q].t[r].d;
+      for (int r = 0; r < 4; ++r) g += a[7 * q + 3 + r] * pb.poses[q].q[r].d;
+    }
+    for (int k = 0; k < P; ++k) g += b[k] * pb.d[k].d;
+    out[c] = g;
+  }
+  return 0;
+}
+
+}  // extern "C"

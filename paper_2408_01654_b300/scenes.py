@@ -1,0 +1,280 @@
+"""Seeded synthetic patch-graph scenes shaped like the paper's workloads.
+
+This module only *synthesises inputs*.  It holds none of the bundle-adjustment
+arithmetic (no residual, Jacobian, normal equation, Schur step or SE(3)
+retraction): ground-truth targets come from a plain 4x4-matrix camera model
+(camera-to-world matrices, world points, pinhole projection) and every rotation
+goes through ``scipy.spatial.transform.Rotation``.  Both the CUDA path and the
+FP64 oracle consume what it returns, so it is the only code they share.
+
+Conventions of the returned arrays (the library's input layout):
+
+* ``poses``   float64 [N,7]  world->camera (tx,ty,tz,qx,qy,qz,qw)
+* ``patches`` float32 [P,3,3,3]  channels (x, y, inverse depth), 3x3 pixels;
+  the centre pixel is ``[:, :, 1, 1]`` and all nine pixels share one inverse
+  depth (the paper's patch, Sec. 3.1 Eq. 1, with p = 3)
+* ``ii, jj, kk`` int32 [E]  edge (i,k,j): patch ``kk`` of frame ``ii`` seen in
+  frame ``jj`` (Sec. 3.1, the patch graph)
+* ``targets`` float32 [E,2] pixels, ``weights`` float32 [E,2] (Eq. 3)
+* ``intrinsics`` float32 [4] (fx, fy, cx, cy)
+
+Workloads (patches per frame, patch size, camera and noise model as the paper's
+DPVO setting: 96 random patches per frame, Sec. 3.1 and Sec. 3.3):
+
+* ``tiny``      8 frames, each patch -> the 6 nearest other frames
+* ``odometry``  22 frames, each patch -> the 13 nearest other frames
+                ("patch lifetime 13"), 8% outliers
+* ``global``    1000 frames, local edges within +-6 frames plus proximity loop
+                edges (old patches -> recent frame, Sec. 3.2)
+* ``batched``   many problems with log-uniform frame counts in [8, 400] and the
+                ``global`` edge rules
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+from scipy.spatial.transform import Rotation
+
+WIDTH, HEIGHT = 640, 480
+FX = FY = 320.0
+CX, CY = 320.0, 240.0
+PATCHES_PER_FRAME = 96
+
+
+@dataclass
+class Scene:
+    name: str
+    seed: int
+    N: int
+    P: int
+    E: int
+    fixed: int
+    iters: int
+    poses: np.ndarray          # float64 [N,7] initial (perturbed) poses
+    patches: np.ndarray        # float32 [P,3,3,3] initial patches
+    ii: np.ndarray             # int32 [E]
+    jj: np.ndarray             # int32 [E]
+    kk: np.ndarray             # int32 [E]
+    targets: np.ndarray        # float32 [E,2]
+    weights: np.ndarray        # float32 [E,2]
+    intrinsics: np.ndarray     # float32 [4]
+    poses_gt: np.ndarray       # float64 [N,7]
+    depth_gt: np.ndarray       # float64 [P]  ground-truth inverse depth
+    proj_gt: np.ndarray        # float64 [E,2] noise-free ground-truth projections
+    info: dict = field(default_factory=dict)
+
+
+# --------------------------------------------------------------------------- #
+# small helpers (input synthesis only)
+# --------------------------------------------------------------------------- #
+def _unit(rng: np.random.Generator, n: int) -> np.ndarray:
+    v = rng.normal(size=(n, 3))
+    return v / np.linalg.norm(v, axis=1, keepdims=True)
+
+
+def _random_walk(rng: np.random.Generator, n: int, step_m=0.1, step_deg=2.0):
+    """Camera-to-world 4x4 matrices: G_0 = I, G_{i+1} = G_i * D_i, where D_i
+    rotates 2 degrees about a uniformly random axis and translates 0.1 m along
+    a uniformly random direction."""
+    G = np.zeros((n, 4, 4))
+    G[0] = np.eye(4)
+    axes = _unit(rng, n)
+    dirs = _unit(rng, n)
+    for i in range(1, n):
+        D = np.eye(4)
+        D[:3, :3] = Rotation.from_rotvec(math.radians(step_deg) * axes[i]).as_matrix()
+        D[:3, 3] = step_m * dirs[i]
+        G[i] = G[i - 1] @ D
+    return G
+
+
+def _world_to_camera(G: np.ndarray):
+    """Invert camera-to-world matrices; return (R [n,3,3], t [n,3])."""
+    R = np.transpose(G[:, :3, :3], (0, 2, 1))
+    t = -np.einsum("nij,nj->ni", R, G[:, :3, 3])
+    return R, t
+
+
+def _pose_vec(R: np.ndarray, t: np.ndarray) -> np.ndarray:
+    q = Rotation.from_matrix(R).as_quat()  # (x, y, z, w)
+    q = np.where(q[:, 3:4] < 0, -q, q)
+    return np.concatenate([t, q], axis=1).astype(np.float64)
+
+
+def _camera_points(u, v, d):
+    """Points in the source camera for pixels (u,v) at inverse depth d."""
+    z = 1.0 / d
+    return np.stack([(u - CX) / FX * z, (v - CY) / FY * z, z], axis=-1)
+
+
+def _project(Rw2c, tw2c, pw):
+    """Pinhole projection of world points pw [E,3] with per-edge world->camera
+    (R [E,3,3], t [E,3]).  Returns (uv [E,2], z [E])."""
+    pc = np.einsum("eij,ej->ei", Rw2c, pw) + tw2c
+    z = pc[:, 2]
+    with np.errstate(divide="ignore", invalid="ignore"):
+        uv = np.stack([FX * pc[:, 0] / z + CX, FY * pc[:, 1] / z + CY], axis=1)
+    return uv, z
+
+
+def _shifted_window(i: int, n: int, size: int) -> list[int]:
+    """The `size`-frame window around i, shifted to stay inside [0, n),
+    without i itself (the `size`-1 nearest other frames)."""
+    size = min(size, n)
+    lo = min(max(i - (size - 1) // 2, 0), n - size)
+    return [j for j in range(lo, lo + size) if j != i]
+
+
+def _clipped_window(i: int, n: int, radius: int) -> list[int]:
+    return [j for j in range(max(0, i - radius), min(n, i + radius + 1)) if j != i]
+
+
+# --------------------------------------------------------------------------- #
+# scene assembly
+# --------------------------------------------------------------------------- #
+def _build(name, seed, N, neighbours, fixed, iters, outlier_frac=0.0,
+           loop=False, rng=None) -> Scene:
+    rng = np.random.default_rng(seed) if rng is None else rng
+    M = PATCHES_PER_FRAME
+    P = N * M
+
+    G = _random_walk(rng, N)
+    Rgt, tgt = _world_to_camera(G)
+    poses_gt = _pose_vec(Rgt, tgt)
+
+    # patch centres are rounded to float32 first so that the stored patches
+    # and the ground-truth geometry agree exactly
+    u = rng.uniform(1.0, WIDTH - 1.0, size=P).astype(np.float32).astype(np.float64)
+    v = rng.uniform(1.0, HEIGHT - 1.0, size=P).astype(np.float32).astype(np.float64)
+    dgt = rng.uniform(0.2, 2.0, size=P)
+    src = np.repeat(np.arange(N), M)
+    pcam = _camera_points(u, v, dgt)
+    pw = np.einsum("pij,pj->pi", G[src, :3, :3], pcam) + G[src, :3, 3]
+
+    # local edges: patch-major, targets ascending within a patch
+    kk_l, jj_l = [], []
+    for i in range(N):
+        js = neighbours(i, N)
+        ks = np.arange(i * M, (i + 1) * M)
+        kk_l.append(np.repeat(ks, len(js)))
+        jj_l.append(np.tile(np.asarray(js, dtype=np.int64), M))
+    kk = np.concatenate(kk_l) if kk_l else np.zeros(0, np.int64)
+    jj = np.concatenate(jj_l) if jj_l else np.zeros(0, np.int64)
+    n_local = len(kk)
+
+    if loop:
+        # proximity loop edges (Sec. 3.2): for each frame b, the nearest
+        # (ground-truth camera centre) frame a with b - a > 30 closer than
+        # 2 m; all patches of a get a uni-directional edge a -> b.
+        centres = G[:, :3, 3]
+        lk, lj = [], []
+        for b in range(N):
+            cand = np.arange(0, max(0, b - 30))
+            if len(cand) == 0:
+                continue
+            dist = np.linalg.norm(centres[cand] - centres[b], axis=1)
+            a = int(cand[np.argmin(dist)])
+            if dist.min() >= 2.0:
+                continue
+            lk.append(np.arange(a * M, (a + 1) * M))
+            lj.append(np.full(M, b))
+        if lk:
+            kk = np.concatenate([kk] + lk)
+            jj = np.concatenate([jj] + lj)
+    ii = src[kk]
+
+    uv, z = _project(Rgt[jj], tgt[jj], pw[kk])
+    keep = z > 0.1
+    if loop:
+        inside = (uv[:, 0] >= 0) & (uv[:, 0] < WIDTH) & (uv[:, 1] >= 0) & (uv[:, 1] < HEIGHT)
+        is_loop = np.arange(len(kk)) >= n_local
+        keep &= ~is_loop | inside
+    ii, jj, kk, uv = ii[keep], jj[keep], kk[keep], uv[keep]
+    n_loop = int(np.count_nonzero(np.arange(len(keep))[keep] >= n_local))
+
+    # sort edges by (kk, jj): the natural patch-major order of a patch graph
+    order = np.lexsort((jj, kk))
+    ii, jj, kk, uv = ii[order], jj[order], kk[order], uv[order]
+    E = len(kk)
+
+    targets = uv + rng.normal(0.0, 0.5, size=(E, 2))
+    weights = rng.uniform(0.5, 1.0, size=(E, 2))
+    n_out = 0
+    if outlier_frac > 0:
+        out = rng.random(E) < outlier_frac
+        n_out = int(out.sum())
+        ang = rng.uniform(0, 2 * np.pi, size=n_out)
+        mag = rng.uniform(5.0, 30.0, size=n_out)
+        targets[out] += np.stack([np.cos(ang), np.sin(ang)], 1) * mag[:, None]
+        weights[out] = 0.05
+
+    # initial state: free poses perturbed 0.05 rad / 0.05 m, depths log-normal
+    Rin, tin = Rgt.copy(), tgt.copy()
+    free = np.arange(fixed, N)
+    if len(free):
+        rot = Rotation.from_rotvec(0.05 * _unit(rng, len(free))).as_matrix()
+        Rin[free] = rot @ Rgt[free]
+        tin[free] = tgt[free] + 0.05 * _unit(rng, len(free))
+    poses = _pose_vec(Rin, tin)
+    poses[:fixed] = poses_gt[:fixed]
+    d0 = dgt * np.exp(rng.normal(0.0, 0.1, size=P))
+
+    patches = np.empty((P, 3, 3, 3), np.float32)
+    off = np.array([-1.0, 0.0, 1.0])
+    patches[:, 0] = (u[:, None, None] + off[None, None, :]).astype(np.float32)
+    patches[:, 1] = (v[:, None, None] + off[None, :, None]).astype(np.float32)
+    patches[:, 2] = d0[:, None, None].astype(np.float32)
+
+    return Scene(
+        name=name, seed=seed, N=N, P=P, E=E, fixed=fixed, iters=iters,
+        poses=poses, patches=patches,
+        ii=ii.astype(np.int32), jj=jj.astype(np.int32), kk=kk.astype(np.int32),
+        targets=targets.astype(np.float32), weights=weights.astype(np.float32),
+        intrinsics=np.array([FX, FY, CX, CY], np.float32),
+        poses_gt=poses_gt, depth_gt=dgt, proj_gt=uv,
+        info={"local_edges": E - n_loop, "loop_edges": n_loop, "outliers": n_out},
+    )
+
+
+def tiny(seed: int = 0) -> Scene:
+    """8 frames, 96 patches/frame, each patch -> 6 nearest other frames
+    (about 4.6k edges), first 2 poses fixed, 2 GN iterations."""
+    return _build("tiny", seed, 8, lambda i, n: _shifted_window(i, n, 7), 2, 2)
+
+
+def odometry(seed: int = 0) -> Scene:
+    """Odometry window: 22 keyframes, patch lifetime 13 (about 27k edges),
+    8% outlier targets offset U[5,30] px with weight 0.05, 2 GN iterations."""
+    return _build("odometry", seed, 22, lambda i, n: _shifted_window(i, n, 14),
+                  2, 2, outlier_frac=0.08)
+
+
+def global_ba(seed: int = 0, N: int = 1000) -> Scene:
+    """Global loop-closure BA: 1000 keyframes, local edges within +-6 frames
+    plus proximity loop edges, 4 GN iterations."""
+    return _build("global", seed, N, lambda i, n: _clipped_window(i, n, 6),
+                  2, 4, loop=True)
+
+
+def batched(seed: int = 0, B: int = 64, lo: int = 8, hi: int = 400) -> list[Scene]:
+    """Independent problems with frame counts round(exp(U[ln lo, ln hi])) and
+    the global edge rules, 4 GN iterations each."""
+    rng = np.random.default_rng(seed)
+    Ns = np.rint(np.exp(rng.uniform(math.log(lo), math.log(hi), size=B))).astype(int)
+    return [_build("batched", seed * 1000 + b, int(n), lambda i, m: _clipped_window(i, m, 6),
+                   2, 4, loop=True) for b, n in enumerate(Ns)]
+
+
+def noise_free(scene: Scene) -> Scene:
+    """Copy of a scene whose targets are the exact ground-truth projections
+    (float64; a float32 cast of them is the GPU input) and whose first `fixed`
+    poses sit at ground truth."""
+    s = Scene(**{k: getattr(scene, k) for k in scene.__dataclass_fields__})
+    s.targets = scene.proj_gt.copy()
+    s.info = dict(scene.info, noise_free=True)
+    return s
+
+
+WORKLOADS = {"tiny": tiny, "odometry": odometry, "global": global_ba}
