@@ -1,0 +1,397 @@
+"""Benchmark of the patch-graph Gauss-Newton bundle adjustment on B300.
+
+One *step* is one pass of the whole hot path over one synthetic problem:
+``ba_set_graph`` (validation, edge sort, group windows) followed by
+``ba_step`` with the workload's GN iterations (linearise + reduce + Schur,
+pose Cholesky + solves, depth back-substitution, SE(3) retraction).
+
+Metric: GN iterations per second (and edges per second) over all ranks, with
+the per-step pose/depth error against the FP64 oracle stated beside it.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload odometry]
+    python bench.py --impl reference      # the FP64 CPU oracle, same workload
+
+Under torchrun each rank solves its own independent problem (seed = rank):
+weak scaling, no collective on the data path.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2408_01654_b300 import scenes  # noqa: E402
+
+METRIC = "GN iterations/sec and edges/sec for patch-graph BA at stated FP64-oracle error"
+UNIT = "GN it/s"
+FALLBACK_HBM = 6400.0
+WORKLOADS = {
+    "odometry": ("odometry-window BA: 22 keyframes, 96 patches/frame, patch lifetime 13, 8% outliers, "
+                 "2 GN iterations, 2 fixed poses", scenes.odometry),
+    "tiny": ("tiny BA: 8 frames, 96 patches/frame, +-3 frame edges, 2 GN iterations, 2 fixed poses", scenes.tiny),
+    "global": ("global loop-closure BA: 1000 keyframes, 96 patches/frame, +-6 local + proximity loop edges, "
+               "4 GN iterations, 2 fixed poses", scenes.global_ba),
+}
+KERNEL_FILES = {"assemble": "assemble.cu", "solve": "solve_small.cu", "backsub": "update.cu",
+                "retract": "update.cu", "init": "assemble.cu", "preprocess": "preprocess.cu"}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="odometry")
+    ap.add_argument("--precision", choices=["fp32", "mixed"], default="fp32")
+    ap.add_argument("--group", type=int, default=0, help="patches per group (0 = automatic)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# --------------------------------------------------------------------------- #
+# helpers
+# --------------------------------------------------------------------------- #
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM, "fallback"
+
+
+def algorithmic_bytes(kind, N, P, E, n):
+    """Bytes a kernel class must move per launch at minimum (inputs read once,
+    outputs written once)."""
+    tri = n * (n + 1) // 2
+    if kind == "assemble":
+        # edges: ii, jj, kk, target, weight (28 B); patches: centre + depth (12 B);
+        # poses (56 B); outputs: lower triangle of S, y, Ct and w
+        return 28 * E + 12 * P + 56 * N + 4 * tri + 4 * n + 8 * P
+    if kind == "backsub":
+        # edges: ii, jj, kk, weight (20 B); patches: centre + depth + Ct + w (20 B);
+        # outputs: nine depths (36 B) and the step (4 B)
+        return 20 * E + 20 * P + 56 * N + 8 * n + 40 * P
+    if kind == "solve":
+        return 4 * tri + 4 * n + 8 * n
+    if kind == "init":
+        return 4 * tri + 4 * n
+    if kind == "retract":
+        return 8 * n + 112 * N
+    if kind == "preprocess":
+        return 12 * E + 4 * E + 12 * E
+    return 0
+
+
+def kernel_hash(kind):
+    f = os.path.join(ROOT, "paper_2408_01654_b300", "csrc", KERNEL_FILES.get(kind, "assemble.cu"))
+    with open(f, "rb") as fh:
+        return hashlib.sha256(fh.read()).hexdigest()[:16]
+
+
+def committed_traffic(kind, workload):
+    """dram bytes per launch from the committed ncu summary, if it was taken
+    on the current source of the kernel."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        r = d[f"{kind}:{workload}"]
+        if r["source_sha"] != kernel_hash(kind):
+            return None
+        return r["dram_bytes_per_launch"]
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle-reason samples during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in self.rows for k in range(4) if len(r) > 4 + k and r[4 + k] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def pose_errors(a, b):
+    from scipy.spatial.transform import Rotation
+    rot = (Rotation.from_quat(a[:, 3:]) * Rotation.from_quat(b[:, 3:]).inv()).magnitude().max()
+    tr = (np.linalg.norm(a[:, :3] - b[:, :3], axis=1) / np.maximum(1.0, np.linalg.norm(b[:, :3], axis=1))).max()
+    return float(rot), float(tr)
+
+
+# --------------------------------------------------------------------------- #
+# CPU oracle timing (reference arm and cpu_baseline leg)
+# --------------------------------------------------------------------------- #
+def time_oracle(scene, budget_s=10.0, max_runs=1000):
+    import oracle
+    oracle.build()
+    runs, t0 = 0, time.perf_counter()
+    while True:
+        oracle.gn(scene)
+        runs += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s or runs >= max_runs:
+            break
+    return runs, el
+
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count()
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    desc, make = WORKLOADS[args.workload]
+    scene = make(seed=0)
+    import oracle
+    oracle.build()
+    for _ in range(min(args.warmup, 1)):
+        oracle.gn(scene)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.gn(scene)
+    el = time.perf_counter() - t0
+    value = args.steps * scene.iters / el
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": desc, "N": scene.N, "P": scene.P, "E": scene.E, "iters": scene.iters},
+        "edges_per_sec": value * scene.E,
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"full workload, {args.steps} steps of {scene.iters} GN iterations, "
+                                   f"single-threaded FP64 oracle (-O2), {cpu_cores()} cores visible"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# --------------------------------------------------------------------------- #
+# GPU arm
+# --------------------------------------------------------------------------- #
+def run_ours(args):
+    import torch
+
+    from paper_2408_01654_b300 import build as pbuild
+    from paper_2408_01654_b300.ba import DPVBA, scene_tensors
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    if rank == 0:
+        pbuild.build()
+    if dist:
+        dist.barrier()
+    desc, make = WORKLOADS[args.workload]
+    scene = make(seed=rank)
+    dev = torch.device("cuda", local)
+    T = scene_tensors(scene, dev)
+    pristine = {k: v.clone() for k, v in T.items()}
+    stream = torch.cuda.current_stream(dev)
+    ba = DPVBA(precision=args.precision, patches_per_group=args.group, stream=stream)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > L2 (126 MB)
+
+    def reset():
+        T["poses"].copy_(pristine["poses"])
+        T["patches"].copy_(pristine["patches"])
+
+    def one_step():
+        ba.set_graph(**T)
+        ba.step(scene.iters, scene.fixed)
+
+    for _ in range(max(args.warmup, 3)):
+        reset()
+        one_step()
+    ba.sync()
+
+    # ---- timed region: per-step events, L2 flushed between steps ----------
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    launches0 = ba.info()["launches"]
+    ba.profile(True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            reset()
+            flush.zero_()
+            ev[k][0].record(stream)
+            one_step()
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ba.sync()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    prof = ba.profile_read()
+    ba.profile(False)
+    launches = ba.info()["launches"] - launches0
+    if dist:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    gn_iters = world * args.steps * scene.iters
+    value = gn_iters / (total_ms / 1e3)
+
+    # ---- end to end through the C ABI with host buffers -------------------
+    host_in = {k: v.cpu().pin_memory() for k, v in pristine.items()}
+    host_out = {"poses": torch.empty_like(host_in["poses"]).pin_memory(),
+                "patches": torch.empty_like(host_in["patches"]).pin_memory()}
+    h2d = sum(v.numel() * v.element_size() for v in host_in.values())
+    d2h = sum(v.numel() * v.element_size() for v in host_out.values())
+    e2e_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+    for k in range(args.steps):
+        flush.zero_()
+        e2e_ev[k][0].record(stream)
+        for name, hv in host_in.items():
+            T[name].copy_(hv, non_blocking=True)
+        one_step()
+        host_out["poses"].copy_(T["poses"], non_blocking=True)
+        host_out["patches"].copy_(T["patches"], non_blocking=True)
+        e2e_ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = sum(a.elapsed_time(b) for a, b in e2e_ev)
+    if dist:
+        t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e_value = gn_iters / (e2e_ms / 1e3)
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return 0
+
+    # ---- roofline of the dominant kernel ----------------------------------
+    inf = ba.info()
+    n = inf["n"]
+    dom = max((k for k in prof if prof[k][1] > 0), key=lambda k: prof[k][0])
+    t_ms, cnt = prof[dom]
+    per_launch_s = t_ms / cnt / 1e3
+    ab = algorithmic_bytes(dom, scene.N, scene.P, scene.E, n)
+    peak, peak_kind = measured_peaks()
+    achieved = ab / per_launch_s / 1e9
+    roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": committed_traffic(dom, args.workload),
+            "algorithmic_bytes_per_launch": ab, "avg_launch_us": per_launch_s * 1e6, "peak_source": peak_kind,
+            "per_class_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()}}
+
+    # ---- error against the oracle and the CPU baseline --------------------
+    err = None
+    cpu = None
+    if not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        reset()
+        ba.set_graph(**T)
+        errs = []
+        want = oracle.gn_steps(scene, iters=scene.iters)
+        for it in range(scene.iters):
+            ba.step(1, scene.fixed)
+            ba.sync()
+            rot, tr = pose_errors(T["poses"].cpu().numpy(), want[it][0])
+            d = T["patches"][:, 2, 1, 1].cpu().numpy().astype(np.float64)
+            dep = float(np.max(np.abs(d - want[it][1]) / np.abs(want[it][1])))
+            errs.append({"iter": it + 1, "rot_rad": rot, "trans_rel": tr, "depth_rel": dep})
+        err = errs
+        runs, el = time_oracle(scene, budget_s=10.0)
+        cv = runs * scene.iters / el
+        cpu = {"value": cv, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{runs} full runs of the workload ({scene.iters} GN iterations each), single-threaded "
+                         f"FP64 oracle (-O2) on 1 of {cpu_cores()} host cores, {el:.1f} s"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": desc, "N": scene.N, "P": scene.P, "E": scene.E, "iters": scene.iters,
+                   "fixed": scene.fixed, "precision": args.precision, "patches_per_group": inf["G"],
+                   "l2": "flushed between steps (256 MiB write)", "step": "ba_set_graph + ba_step"},
+        "edges_per_sec": value * scene.E,
+        "error_vs_oracle": err,
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "clocks": clk.summary(),
+        "step_ms": {"min": min(step_ms), "median": statistics.median(step_ms), "max": max(step_ms)},
+    }
+    print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,188 @@
+/*
+ * dpvba.h -- C ABI of a single-GPU (B300, sm_103a) Gauss-Newton bundle
+ * adjustment over the DPVO patch graph (arxiv 2408.01654).
+ *
+ * The operation (Sec. 3.1, Eq. 2 and Eq. 3): every edge (i,k,j) reprojects
+ * patch k of frame i into frame j,
+ *     P'_ikj = Pi[ G_j^-1 G_i Pi^-1(P_ik) ],
+ * and one Gauss-Newton iteration minimises
+ *     sum_(i,k,j) || P'_ikj - I_ikj ||^2_{diag(w_ikj)}
+ * over the free camera poses and the per-patch inverse depths, with the
+ * inverse depths Schur-eliminated and the dense pose system Cholesky-solved
+ * (Sec. 3.2 "Efficient Global Optimization"; the appendix "Bundle-Adjustment
+ * Efficiency" names that pose-block Cholesky as the bottleneck).
+ *
+ * Conventions used by every call:
+ *   - poses  : float64 [N,7] (tx,ty,tz,qx,qy,qz,qw), world->camera (the
+ *              inverse of the paper's G_i); perturbed on the left,
+ *              T <- Exp(xi) T, xi = (rho, phi), translation first.
+ *   - patches: float32 [P,3,3,3], channels (x, y, inverse depth) over a 3x3
+ *              pixel patch (Eq. 1 with p = 3).  The residual uses the centre
+ *              pixel [k][:][1][1]; the nine pixels share one inverse depth.
+ *   - ii, jj, kk : int32 [E]; edge e is patch kk[e] of frame ii[e] observed in
+ *              frame jj[e].  All edges of one patch must have the same ii.
+ *   - targets: float32 [E,2] pixels (the paper's I_ikj); weights: float32
+ *              [E,2] (w_ikj); residual r = target - proj, cost sum w_c r_c^2.
+ *   - intrinsics: float32 [4] (fx, fy, cx, cy), host or device memory.
+ *   - an edge with i == j, or whose point lies less than z_min (metres) in
+ *     front of frame j, contributes nothing.
+ *
+ * Memory and streams: every pointer argument is DEVICE memory unless stated.
+ * The handle owns its workspace; it BORROWS poses, patches, targets and
+ * weights, which must stay allocated until the next ba_set_graph or
+ * ba_destroy.  All work is ordered on the handle's stream; calls return as
+ * soon as the work is queued.
+ *
+ * Errors: arguments a host can check (null pointers, non-positive sizes,
+ * fixed_poses out of range, a call out of order) return an error at once and
+ * queue nothing.  Errors the GPU detects (an index out of range, a patch with
+ * two source frames, a pose system that is not positive definite, a window
+ * wider than the kernels support) are written to a device status word; the
+ * kernels that follow skip their work, the poses and depths stay at the last
+ * completed iteration, and ba_sync returns the first such error.
+ */
+#ifndef DPVBA_H
+#define DPVBA_H
+
+#if defined(__GNUC__)
+#define DPVBA_API __attribute__((visibility("default")))
+#else
+#define DPVBA_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ba_handle_s* ba_handle_t;
+
+typedef enum {
+  BA_OK = 0,
+  BA_ERR_INVALID_ARG = 1, /* bad argument, or an invalid edge index found on the GPU */
+  BA_ERR_CUDA = 2,        /* a CUDA runtime call failed                             */
+  BA_ERR_OOM = 3,         /* workspace allocation failed                            */
+  BA_ERR_NOT_SPD = 4,     /* reduced pose system not positive definite              */
+  BA_ERR_TIMEOUT = 5,     /* a bounded device-side wait ran out                     */
+  BA_ERR_STATE = 6,       /* call out of order (e.g. ba_step before ba_set_graph)   */
+  BA_ERR_UNSUPPORTED = 7  /* graph shape beyond the kernels' limits                 */
+} ba_status_t;
+
+typedef enum {
+  BA_FP32 = 0, /* FP32 linearisation, reduction and factorisation; FP64 retraction  */
+  BA_MIXED = 1 /* as BA_FP32, plus FP64 iterative refinement of the pose solve      */
+} ba_precision_t;
+
+typedef struct {
+  int precision;           /* ba_precision_t                                     */
+  float lambda_pose;       /* added to every free-pose diagonal (default 1e-4)    */
+  float lambda_depth;      /* added to every inverse-depth diagonal (1e-4)        */
+  float z_min;             /* minimum depth in frame j, metres (0.1)              */
+  float d_min;             /* lower clamp of inverse depth after a step (1e-3)    */
+  int patches_per_group;   /* patches per reduction group; 0 = automatic          */
+  int max_refine;          /* FP64 refinement sweeps in BA_MIXED (default 2)      */
+  long long timeout_cycles;/* bound on any device-side wait (default 2e9 cycles)  */
+  void* stream;            /* cudaStream_t for all work; NULL = legacy stream      */
+} ba_options_t;
+
+/* Fill *opt with the defaults above. */
+DPVBA_API ba_status_t ba_default_options(ba_options_t* opt);
+
+/* Create a handle on the current CUDA device.  opt == NULL means defaults.
+ * *out receives the handle.  Allocates only a small fixed workspace. */
+DPVBA_API ba_status_t ba_create(ba_handle_t* out, const ba_options_t* opt);
+
+/* Release the handle and its workspace (synchronises its stream first). */
+DPVBA_API ba_status_t ba_destroy(ba_handle_t h);
+
+/* Change the stream used by later calls. */
+DPVBA_API ba_status_t ba_set_stream(ba_handle_t h, void* stream);
+
+/* Bind a patch graph (Sec. 3.1 "The patch graph").  Validates the indices on
+ * the GPU, sorts the edges into reduction groups and builds the group windows,
+ * edge->block slot maps and run tables; grows the workspace if needed (the
+ * only call that may allocate).  poses and patches are updated in place by
+ * ba_step; targets and weights are read on every ba_step, so the caller may
+ * refresh their contents between steps without calling ba_set_graph again.
+ * ii, jj, kk are read only during this call's queued work.
+ * N >= 1, P >= 1, E >= 0.  intrinsics may be host or device memory and is
+ * copied. */
+DPVBA_API ba_status_t ba_set_graph(ba_handle_t h, int N, int P, int E, double* poses, float* patches,
+                         const int* ii, const int* jj, const int* kk, const float* targets,
+                         const float* weights, const float* intrinsics);
+
+/* Run `iters` Gauss-Newton iterations of Eq. 3 in place (Sec. 3.1-3.2):
+ * linearise every edge, reduce into the block system, eliminate the inverse
+ * depths, factor and solve the pose system, back-substitute the depths,
+ * retract the poses.  Poses [0, fixed_poses) are held constant (gauge).
+ * 0 <= fixed_poses <= N, iters >= 0. */
+DPVBA_API ba_status_t ba_step(ba_handle_t h, int iters, int fixed_poses);
+
+/* Wait for the handle's stream; return the first device-detected error. */
+DPVBA_API ba_status_t ba_sync(ba_handle_t h);
+
+/* Text of the last error on this handle (never NULL). */
+DPVBA_API const char* ba_last_error(ba_handle_t h);
+
+/* Name of a status code (never NULL). */
+DPVBA_API const char* ba_status_string(ba_status_t s);
+
+/* ---- inspection (tests and profiling; not needed to run a step) --------- */
+
+/* Build the reduced pose system at the current state without solving:
+ * afterwards BA_EXPORT_S / _Y / _CT / _W hold S, y, C+lambda_depth and w. */
+DPVBA_API ba_status_t ba_linearize(ba_handle_t h, int fixed_poses);
+
+enum {
+  BA_EXPORT_S = 0,      /* float32 [n,n] dense, lower triangle (upper zero), n = 6 (N - fixed) */
+  BA_EXPORT_Y = 1,      /* float32 [n]        reduced right-hand side                         */
+  BA_EXPORT_DX = 2,     /* float64 [n]        last pose step                                  */
+  BA_EXPORT_DD = 3,     /* float32 [P]        last inverse-depth step                         */
+  BA_EXPORT_CT = 4,     /* float32 [P]        C + lambda_depth                                */
+  BA_EXPORT_W = 5,      /* float32 [P]        depth gradient w                                */
+  BA_EXPORT_PERM = 6,   /* int32 [E]          sorted position -> input edge                   */
+  BA_EXPORT_SLOTS = 7,  /* uint32 [E]         slot_i | slot_j << 8 | patch-in-group << 16     */
+  BA_EXPORT_GPTR = 8,   /* int32 [groups+1]   edge range of each group                        */
+  BA_EXPORT_WIN = 9,    /* int32 [groups, 32] window frames of each group (-1 padded)          */
+  BA_EXPORT_COST = 10   /* float64 [iters]    cost sum w r^2 at each iteration's linearisation point */
+};
+
+/* Copy an internal array into `dst` (device memory, `bytes` long; fails if
+ * too small).  Synchronises the stream. */
+DPVBA_API ba_status_t ba_debug_export(ba_handle_t h, int what, void* dst, long long bytes);
+
+/* Host integers describing the bound graph:
+ * info[0..8] = N, P, E, patches_per_group, groups, n (last fixed), tile size, runs,
+ * kernels launched by the handle so far. */
+DPVBA_API ba_status_t ba_debug_info(ba_handle_t h, long long* info, int cap);
+
+/* Canonical pose-pose block keys of the B part of the system, computed on the
+ * GPU: sorted unique (a,b), a <= b, over (i,i), (j,j), (min,max) of each
+ * non-self edge with both poses free.  keys_out: device int32 [cap,2];
+ * *n_out (host) receives the count.  Synchronises; allocates temporaries. */
+DPVBA_API ba_status_t ba_debug_keys(ba_handle_t h, int fixed_poses, int* keys_out, int cap, int* n_out);
+
+/* ---- timing (CUDA events recorded on the handle's stream) --------------- */
+
+enum {
+  BA_KERNEL_PREPROCESS = 0, /* every kernel of ba_set_graph                     */
+  BA_KERNEL_INIT = 1,       /* clearing the pose system                          */
+  BA_KERNEL_ASSEMBLE = 2,   /* linearisation + block reduction + Schur complement */
+  BA_KERNEL_SOLVE = 3,      /* Cholesky and triangular solves (+ refinement)     */
+  BA_KERNEL_BACKSUB = 4,    /* inverse-depth back-substitution                   */
+  BA_KERNEL_RETRACT = 5,    /* SE(3) retraction                                  */
+  BA_KERNEL_CLASSES = 6
+};
+
+/* on != 0: from now on record a CUDA event pair around every launch of each
+ * kernel class above (and clear earlier records); on == 0: stop recording. */
+DPVBA_API ba_status_t ba_profile_enable(ba_handle_t h, int on);
+
+/* Synchronise, then report for kernel class `kind` the summed event time of
+ * its recorded launches (*total_ms) and their number (*launches). */
+DPVBA_API ba_status_t ba_profile_read(ba_handle_t h, int kind, double* total_ms, long long* launches);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DPVBA_H */

@@ -1,0 +1,142 @@
+"""Torch-facing wrapper of the C ABI (device memory and streams come from
+PyTorch; every computation runs in the library's CUDA kernels)."""
+from __future__ import annotations
+
+import ctypes
+
+import torch
+
+from . import capi
+
+_EXPORT_DTYPES = {
+    capi.EXPORT_Y: torch.float32, capi.EXPORT_DX: torch.float64, capi.EXPORT_DD: torch.float32,
+    capi.EXPORT_CT: torch.float32, capi.EXPORT_W: torch.float32, capi.EXPORT_PERM: torch.int32,
+    capi.EXPORT_SLOTS: torch.int32, capi.EXPORT_GPTR: torch.int32, capi.EXPORT_WIN: torch.int32,
+    capi.EXPORT_COST: torch.float64,
+}
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+class DPVBA:
+    """A bundle-adjustment handle bound to the current CUDA device and stream.
+
+    ``set_graph`` borrows ``poses`` (float64 [N,7]) and ``patches`` (float32
+    [P,3,3,3]), which ``step`` updates in place, and ``targets``/``weights``
+    (float32 [E,2]), which are read on every ``step``.  The wrapper keeps
+    references to them so they outlive the handle's use.
+    """
+
+    def __init__(self, precision: str = "fp32", lambda_pose=1e-4, lambda_depth=1e-4, z_min=0.1, d_min=1e-3,
+                 patches_per_group: int = 0, max_refine: int = 2, stream: torch.cuda.Stream | None = None):
+        self._lib = capi.lib()
+        self._h = ctypes.c_void_p()
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        opt = capi.default_options(
+            precision=capi.BA_MIXED if precision == "mixed" else capi.BA_FP32, lambda_pose=lambda_pose,
+            lambda_depth=lambda_depth, z_min=z_min, d_min=d_min, patches_per_group=patches_per_group,
+            max_refine=max_refine, stream=self.stream.cuda_stream)
+        capi.check(None, self._lib.ba_create(ctypes.byref(self._h), ctypes.byref(opt)))
+        self._keep = ()
+        self.N = self.P = self.E = 0
+
+    # ------------------------------------------------------------------ core
+    def set_graph(self, poses, patches, ii, jj, kk, targets, weights, intrinsics):
+        for name, t, dt in (("poses", poses, torch.float64), ("patches", patches, torch.float32),
+                            ("ii", ii, torch.int32), ("jj", jj, torch.int32), ("kk", kk, torch.int32),
+                            ("targets", targets, torch.float32), ("weights", weights, torch.float32),
+                            ("intrinsics", intrinsics, torch.float32)):
+            if t.dtype != dt or not t.is_contiguous() or not t.is_cuda:
+                raise TypeError(f"{name}: need a contiguous CUDA {dt} tensor")
+        N, P, E = poses.shape[0], patches.shape[0], ii.shape[0]
+        self._keep = (poses, patches, ii, jj, kk, targets, weights, intrinsics)
+        self.N, self.P, self.E = N, P, E
+        capi.check(self._h, self._lib.ba_set_graph(
+            self._h, N, P, E, _ptr(poses), _ptr(patches), _ptr(ii), _ptr(jj), _ptr(kk), _ptr(targets),
+            _ptr(weights), _ptr(intrinsics)))
+
+    def step(self, iters: int, fixed: int):
+        capi.check(self._h, self._lib.ba_step(self._h, iters, fixed))
+
+    def sync(self):
+        capi.check(self._h, self._lib.ba_sync(self._h))
+
+    def close(self):
+        if self._h:
+            self._lib.ba_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------ inspection
+    def linearize(self, fixed: int):
+        capi.check(self._h, self._lib.ba_linearize(self._h, fixed))
+
+    def info(self) -> dict:
+        arr = (ctypes.c_longlong * 9)()
+        capi.check(self._h, self._lib.ba_debug_info(self._h, arr, 9))
+        keys = ("N", "P", "E", "G", "groups", "n", "tile", "runs", "launches")
+        return dict(zip(keys, list(arr)))
+
+    def export(self, what: int, count: int | None = None) -> torch.Tensor:
+        inf = self.info()
+        dev = self._keep[0].device
+        if what == capi.EXPORT_S:
+            out = torch.empty((inf["n"], inf["n"]), dtype=torch.float32, device=dev)
+        else:
+            if count is None:
+                count = {capi.EXPORT_Y: inf["n"], capi.EXPORT_DX: inf["n"], capi.EXPORT_DD: inf["P"],
+                         capi.EXPORT_CT: inf["P"], capi.EXPORT_W: inf["P"], capi.EXPORT_PERM: inf["E"],
+                         capi.EXPORT_SLOTS: inf["E"], capi.EXPORT_GPTR: inf["groups"] + 1,
+                         capi.EXPORT_WIN: inf["groups"] * capi.WMAX, capi.EXPORT_COST: 1}[what]
+            out = torch.empty(max(count, 1), dtype=_EXPORT_DTYPES[what], device=dev)
+        capi.check(self._h, self._lib.ba_debug_export(self._h, what, _ptr(out),
+                                                       out.numel() * out.element_size()))
+        return out
+
+    def profile(self, on: bool = True):
+        capi.check(self._h, self._lib.ba_profile_enable(self._h, 1 if on else 0))
+
+    def profile_read(self) -> dict:
+        """{kernel class: (total event ms, launches)} since profiling was enabled."""
+        out = {}
+        for k, name in enumerate(capi.KERNEL_CLASSES):
+            t, n = ctypes.c_double(), ctypes.c_longlong()
+            capi.check(self._h, self._lib.ba_profile_read(self._h, k, ctypes.byref(t), ctypes.byref(n)))
+            out[name] = (t.value, n.value)
+        return out
+
+    def block_keys(self, fixed: int, cap: int | None = None) -> torch.Tensor:
+        cap = 3 * self.E + 1 if cap is None else cap
+        out = torch.empty((cap, 2), dtype=torch.int32, device=self._keep[0].device)
+        n = ctypes.c_int()
+        capi.check(self._h, self._lib.ba_debug_keys(self._h, fixed, _ptr(out), cap, ctypes.byref(n)))
+        return out[:n.value]
+
+
+def scene_tensors(scene, device="cuda") -> dict:
+    """Device copies of a synthetic scene's arrays in the library's layout."""
+    def t(a, dt):
+        return torch.as_tensor(a).to(device=device, dtype=dt).contiguous()
+    return {
+        "poses": t(scene.poses, torch.float64), "patches": t(scene.patches, torch.float32),
+        "ii": t(scene.ii, torch.int32), "jj": t(scene.jj, torch.int32), "kk": t(scene.kk, torch.int32),
+        "targets": t(scene.targets, torch.float32), "weights": t(scene.weights, torch.float32),
+        "intrinsics": t(scene.intrinsics, torch.float32),
+    }
+
+
+def solve(scene, iters=None, fixed=None, device="cuda", **opts):
+    """Bind a scene, run `iters` GN iterations, return (poses, patches) tensors."""
+    T = scene_tensors(scene, device)
+    ba = DPVBA(**opts)
+    ba.set_graph(**T)
+    ba.step(scene.iters if iters is None else iters, scene.fixed if fixed is None else fixed)
+    ba.sync()
+    return T["poses"], T["patches"], ba

@@ -1,0 +1,401 @@
+// C ABI of the library (declared in include/dpvba.h).
+#include "internal.cuh"
+
+#include <algorithm>
+#include <cstring>
+#include <new>
+
+size_t dpv_assemble_smem(int G);
+
+ba_status_t dpv_fail(ba_handle_t h, ba_status_t s, const std::string& msg) {
+  if (h) h->last_error = std::string(ba_status_string(s)) + ": " + msg;
+  return s;
+}
+
+static cudaEvent_t pool_event(ba_handle_t h) {
+  if (!h->ev_pool.empty()) {
+    cudaEvent_t e = h->ev_pool.back();
+    h->ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return e;
+}
+
+void dpv_prof_begin(ba_handle_t h, int kind) {
+  if (!h->prof_on) return;
+  cudaEvent_t a = pool_event(h), b = pool_event(h);
+  if (!a || !b) return;
+  cudaEventRecord(a, h->stream);
+  h->prof.push_back({kind, a, b});
+  h->prof_open = (int)h->prof.size() - 1;
+}
+
+void dpv_prof_end(ba_handle_t h) {
+  if (!h->prof_on || h->prof_open < 0) return;
+  cudaEventRecord(h->prof[h->prof_open].b, h->stream);
+  h->prof_open = -1;
+}
+
+static void prof_clear(ba_handle_t h) {
+  for (auto& r : h->prof) {
+    h->ev_pool.push_back(r.a);
+    h->ev_pool.push_back(r.b);
+  }
+  h->prof.clear();
+  h->prof_open = -1;
+}
+
+namespace {
+
+template <class T>
+ba_status_t grow(ba_handle_t h, DBuf<T>& b, long long need, const char* what) {
+  need = std::max<long long>(need, 1);
+  if (need <= b.cap && b.p) return BA_OK;
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.cap = 0;
+  cudaError_t e = cudaMalloc((void**)&b.p, sizeof(T) * (size_t)need);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    b.p = nullptr;
+    return dpv_fail(h, BA_ERR_OOM, std::string("allocating ") + what + ": " + cudaGetErrorString(e));
+  }
+  b.cap = need;
+  return BA_OK;
+}
+
+template <class T>
+void release(DBuf<T>& b) {
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.cap = 0;
+}
+
+int bits_for(unsigned long long x) {
+  int b = 0;
+  while (b < 64 && (x >> b)) ++b;
+  return b;
+}
+
+// pose-system geometry for a given number of free poses
+void system_geometry(int n, int& TS, int& T, int& n_pad) {
+  if (n <= DPV_SMALL_N) {
+    n_pad = std::max(32, (n + 31) / 32 * 32);
+    TS = n_pad;
+    T = 1;
+  } else {
+    TS = DPV_TILE;
+    T = (n + TS - 1) / TS;
+    n_pad = T * TS;
+  }
+}
+
+int auto_group(ba_handle_t h, int P) {
+  // enough groups to fill the GPU at least twice, otherwise 32 patches
+  if ((long long)P >= 32LL * 2 * h->num_sms) return 32;
+  if ((long long)P >= 16LL * h->num_sms) return 16;
+  return 8;
+}
+
+ba_status_t ensure_system(ba_handle_t h, int fixed) {
+  Workspace* ws = h->ws;
+  if (fixed == h->fixed) return BA_OK;
+  h->fixed = fixed;
+  h->n = 6 * (h->N - fixed);
+  system_geometry(h->n, h->TS, h->T, h->n_pad);
+  const long long nS = (long long)h->T * (h->T + 1) / 2 * h->TS * h->TS;
+  ba_status_t s;
+  if ((s = grow(h, ws->S, nS, "pose system")) || (s = grow(h, ws->y, h->n_pad, "rhs")) ||
+      (s = grow(h, ws->dx, h->n_pad, "step")) || (s = grow(h, ws->r64, h->n_pad, "residual")) ||
+      (s = grow(h, ws->tmpv, h->n_pad, "vector")))
+    return s;
+  if (h->n > DPV_SMALL_N && (s = grow(h, ws->L, nS, "factor"))) return s;
+  return BA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* ba_status_string(ba_status_t s) {
+  switch (s) {
+    case BA_OK: return "BA_OK";
+    case BA_ERR_INVALID_ARG: return "BA_ERR_INVALID_ARG";
+    case BA_ERR_CUDA: return "BA_ERR_CUDA";
+    case BA_ERR_OOM: return "BA_ERR_OOM";
+    case BA_ERR_NOT_SPD: return "BA_ERR_NOT_SPD";
+    case BA_ERR_TIMEOUT: return "BA_ERR_TIMEOUT";
+    case BA_ERR_STATE: return "BA_ERR_STATE";
+    case BA_ERR_UNSUPPORTED: return "BA_ERR_UNSUPPORTED";
+  }
+  return "BA_ERR_UNKNOWN";
+}
+
+ba_status_t ba_default_options(ba_options_t* opt) {
+  if (!opt) return BA_ERR_INVALID_ARG;
+  opt->precision = BA_FP32;
+  opt->lambda_pose = 1e-4f;
+  opt->lambda_depth = 1e-4f;
+  opt->z_min = 0.1f;
+  opt->d_min = 1e-3f;
+  opt->patches_per_group = 0;
+  opt->max_refine = 2;
+  opt->timeout_cycles = 2000000000LL;
+  opt->stream = nullptr;
+  return BA_OK;
+}
+
+ba_status_t ba_create(ba_handle_t* out, const ba_options_t* opt) {
+  if (!out) return BA_ERR_INVALID_ARG;
+  *out = nullptr;
+  ba_handle_t h = new (std::nothrow) ba_handle_s();
+  if (!h) return BA_ERR_OOM;
+  if (opt) h->opt = *opt;
+  else ba_default_options(&h->opt);
+  if (h->opt.patches_per_group < 0 || h->opt.patches_per_group > DPV_GMAX ||
+      (h->opt.precision != BA_FP32 && h->opt.precision != BA_MIXED) || h->opt.max_refine < 0 ||
+      h->opt.max_refine > 16) {
+    delete h;
+    return BA_ERR_INVALID_ARG;
+  }
+  h->stream = (cudaStream_t)h->opt.stream;
+  h->ws = new (std::nothrow) Workspace();
+  if (!h->ws || cudaGetDevice(&h->device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess ||
+      cudaMalloc(&h->ws->status, sizeof(int)) != cudaSuccess ||
+      cudaMalloc(&h->ws->intr, 4 * sizeof(float)) != cudaSuccess ||
+      cudaMalloc(&h->ws->cost, 256 * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&h->ws->nruns, sizeof(int)) != cudaSuccess ||
+      cudaMemset(h->ws->status, 0, sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    ba_destroy(h);
+    return BA_ERR_CUDA;
+  }
+  h->ws->cost_cap = 256;
+  *out = h;
+  return BA_OK;
+}
+
+ba_status_t ba_destroy(ba_handle_t h) {
+  if (!h) return BA_ERR_INVALID_ARG;
+  if (h->stream || h->ws) cudaStreamSynchronize(h->stream);
+  if (Workspace* ws = h->ws) {
+    void* raw[] = {ws->status, ws->intr, ws->cost, ws->nruns};
+    for (void* b : raw)
+      if (b) cudaFree(b);
+    release(ws->src); release(ws->keys0); release(ws->keys1); release(ws->vals0); release(ws->vals1);
+    release(ws->hist); release(ws->perm); release(ws->eslot); release(ws->runflag); release(ws->runid);
+    release(ws->runptr); release(ws->gptr); release(ws->gseg); release(ws->win); release(ws->wlen);
+    release(ws->scan); release(ws->S); release(ws->y); release(ws->dx); release(ws->Ct); release(ws->wk);
+    release(ws->dd); release(ws->L); release(ws->r64); release(ws->tmpv);
+    delete ws;
+  }
+  prof_clear(h);
+  for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
+  delete h;
+  return BA_OK;
+}
+
+ba_status_t ba_profile_enable(ba_handle_t h, int on) {
+  if (!h) return BA_ERR_INVALID_ARG;
+  if (on) {
+    DPV_CUDA(h, cudaStreamSynchronize(h->stream));
+    prof_clear(h);
+  }
+  h->prof_on = on ? 1 : 0;
+  return BA_OK;
+}
+
+ba_status_t ba_profile_read(ba_handle_t h, int kind, double* total_ms, long long* launches) {
+  if (!h || !total_ms || !launches || kind < 0 || kind >= BA_KERNEL_CLASSES) return BA_ERR_INVALID_ARG;
+  DPV_CUDA(h, cudaStreamSynchronize(h->stream));
+  double t = 0.0;
+  long long c = 0;
+  for (auto& r : h->prof) {
+    if (r.kind != kind) continue;
+    float ms = 0.f;
+    DPV_CUDA(h, cudaEventElapsedTime(&ms, r.a, r.b));
+    t += ms;
+    ++c;
+  }
+  *total_ms = t;
+  *launches = c;
+  return BA_OK;
+}
+
+ba_status_t ba_set_stream(ba_handle_t h, void* stream) {
+  if (!h) return BA_ERR_INVALID_ARG;
+  h->stream = (cudaStream_t)stream;
+  h->opt.stream = stream;
+  return BA_OK;
+}
+
+ba_status_t ba_set_graph(ba_handle_t h, int N, int P, int E, double* poses, float* patches, const int* ii,
+                         const int* jj, const int* kk, const float* targets, const float* weights,
+                         const float* intrinsics) {
+  if (!h) return BA_ERR_INVALID_ARG;
+  if (N < 1 || P < 1 || E < 0) return dpv_fail(h, BA_ERR_INVALID_ARG, "ba_set_graph: need N >= 1, P >= 1, E >= 0");
+  if (!poses || !patches || !intrinsics || (E > 0 && (!ii || !jj || !kk || !targets || !weights)))
+    return dpv_fail(h, BA_ERR_INVALID_ARG, "ba_set_graph: null pointer");
+  if (N > (1 << 20)) return dpv_fail(h, BA_ERR_UNSUPPORTED, "ba_set_graph: more than 2^20 frames");
+  if ((reinterpret_cast<uintptr_t>(targets) | reinterpret_cast<uintptr_t>(weights)) & 7)
+    return dpv_fail(h, BA_ERR_INVALID_ARG, "ba_set_graph: targets/weights must be 8-byte aligned");
+  Workspace* ws = h->ws;
+  h->have_graph = 0;
+  h->N = N;
+  h->P = P;
+  h->E = E;
+  h->poses = poses;
+  h->patches = patches;
+  h->targets = targets;
+  h->weights = weights;
+  h->G = h->opt.patches_per_group > 0 ? h->opt.patches_per_group : auto_group(h, P);
+  h->ngroups = (P + h->G - 1) / h->G;
+  h->fixed = -1;
+  const unsigned long long maxkey = (unsigned long long)h->ngroups * N * N * h->G;
+  h->sort_bits = bits_for(maxkey);
+  ba_status_t s;
+  const long long En = std::max(E, 1);
+  const long long Gn = h->ngroups + 1;
+  const long long scan_need = std::max(dpv_scan_scratch(En + 1), dpv_scan_scratch(dpv_hist_entries(En)));
+  if ((s = grow(h, ws->src, P, "patch table")) || (s = grow(h, ws->Ct, P, "Ct")) || (s = grow(h, ws->wk, P, "w")) ||
+      (s = grow(h, ws->dd, P, "dd")) || (s = grow(h, ws->keys0, En, "sort keys")) ||
+      (s = grow(h, ws->keys1, En, "sort keys")) || (s = grow(h, ws->vals0, En, "sort values")) ||
+      (s = grow(h, ws->vals1, En, "sort values")) || (s = grow(h, ws->perm, En, "permutation")) ||
+      (s = grow(h, ws->eslot, En, "slots")) || (s = grow(h, ws->runflag, En + 1, "runs")) ||
+      (s = grow(h, ws->runid, En + 1, "runs")) || (s = grow(h, ws->runptr, En + 1, "runs")) ||
+      (s = grow(h, ws->hist, dpv_hist_entries(En), "histograms")) || (s = grow(h, ws->scan, scan_need, "scan")) ||
+      (s = grow(h, ws->gptr, Gn, "groups")) || (s = grow(h, ws->gseg, Gn, "groups")) ||
+      (s = grow(h, ws->win, Gn * DPV_WMAX, "windows")) || (s = grow(h, ws->wlen, Gn, "windows")))
+    return s;
+  DPV_CUDA(h, cudaMemsetAsync(ws->status, 0, sizeof(int), h->stream));
+  DPV_CUDA(h, cudaMemcpyAsync(ws->intr, intrinsics, 4 * sizeof(float), cudaMemcpyDefault, h->stream));
+  dpv_prof_begin(h, BA_KERNEL_PREPROCESS);
+  s = dpv_preprocess(h, ii, jj, kk);
+  dpv_prof_end(h);
+  if (s) return s;
+  if ((s = ensure_system(h, 0))) return s;  // size the system for every pose free
+  h->have_graph = 1;
+  return BA_OK;
+}
+
+static ba_status_t check_step_args(ba_handle_t h, int fixed_poses) {
+  if (!h) return BA_ERR_INVALID_ARG;
+  if (!h->have_graph) return dpv_fail(h, BA_ERR_STATE, "no graph bound (call ba_set_graph first)");
+  if (fixed_poses < 0 || fixed_poses > h->N) return dpv_fail(h, BA_ERR_INVALID_ARG, "fixed_poses out of range");
+  return BA_OK;
+}
+
+ba_status_t ba_step(ba_handle_t h, int iters, int fixed_poses) {
+  ba_status_t s = check_step_args(h, fixed_poses);
+  if (s) return s;
+  if (iters < 0) return dpv_fail(h, BA_ERR_INVALID_ARG, "iters < 0");
+  if ((s = ensure_system(h, fixed_poses))) return s;
+  h->last_iters = iters;
+  if (iters == 0 || h->n == 0) return BA_OK;
+  DPV_CUDA(h, cudaMemsetAsync(h->ws->cost, 0, sizeof(double) * h->ws->cost_cap, h->stream));
+  for (int it = 0; it < iters; ++it) {
+    if ((s = dpv_assemble(h, it))) return s;
+    dpv_prof_begin(h, BA_KERNEL_SOLVE);
+    s = dpv_solve(h);
+    dpv_prof_end(h);
+    if (s) return s;
+    dpv_prof_begin(h, BA_KERNEL_BACKSUB);
+    s = dpv_backsub(h);
+    dpv_prof_end(h);
+    if (s) return s;
+    dpv_prof_begin(h, BA_KERNEL_RETRACT);
+    s = dpv_retract(h);
+    dpv_prof_end(h);
+    if (s) return s;
+  }
+  return BA_OK;
+}
+
+ba_status_t ba_linearize(ba_handle_t h, int fixed_poses) {
+  ba_status_t s = check_step_args(h, fixed_poses);
+  if (s) return s;
+  if ((s = ensure_system(h, fixed_poses))) return s;
+  if (h->n == 0) return BA_OK;
+  DPV_CUDA(h, cudaMemsetAsync(h->ws->cost, 0, sizeof(double), h->stream));
+  return dpv_assemble(h, 0);
+}
+
+ba_status_t ba_sync(ba_handle_t h) {
+  if (!h) return BA_ERR_INVALID_ARG;
+  DPV_CUDA(h, cudaStreamSynchronize(h->stream));
+  int st = 0;
+  DPV_CUDA(h, cudaMemcpy(&st, h->ws->status, sizeof(int), cudaMemcpyDeviceToHost));
+  switch (st) {
+    case DST_OK: return BA_OK;
+    case DST_BAD_INDEX:
+      return dpv_fail(h, BA_ERR_INVALID_ARG, "edge index out of range, or a patch with two source frames");
+    case DST_NOT_SPD: return dpv_fail(h, BA_ERR_NOT_SPD, "reduced pose system is not positive definite");
+    case DST_TIMEOUT: return dpv_fail(h, BA_ERR_TIMEOUT, "a device-side wait ran out");
+    case DST_WIDE:
+      return dpv_fail(h, BA_ERR_UNSUPPORTED,
+                      "a patch group touches more than 32 frames; lower patches_per_group");
+  }
+  return dpv_fail(h, BA_ERR_CUDA, "unknown device status");
+}
+
+const char* ba_last_error(ba_handle_t h) {
+  if (!h) return "invalid handle";
+  return h->last_error.c_str();
+}
+
+ba_status_t ba_debug_info(ba_handle_t h, long long* info, int cap) {
+  if (!h || !info) return BA_ERR_INVALID_ARG;
+  int nr = 0;
+  if (h->have_graph) {
+    DPV_CUDA(h, cudaStreamSynchronize(h->stream));
+    DPV_CUDA(h, cudaMemcpy(&nr, h->ws->nruns, sizeof(int), cudaMemcpyDeviceToHost));
+  }
+  const long long v[9] = {h->N, h->P, h->E, h->G, h->ngroups, h->n, h->TS, nr, h->launches};
+  for (int q = 0; q < cap && q < 9; ++q) info[q] = v[q];
+  return BA_OK;
+}
+
+ba_status_t ba_debug_export(ba_handle_t h, int what, void* dst, long long bytes) {
+  if (!h || !dst) return BA_ERR_INVALID_ARG;
+  if (!h->have_graph) return dpv_fail(h, BA_ERR_STATE, "no graph bound");
+  Workspace* ws = h->ws;
+  const void* src = nullptr;
+  long long need = 0;
+  switch (what) {
+    case BA_EXPORT_S: need = 4LL * h->n * h->n; break;
+    case BA_EXPORT_Y: src = ws->y.p; need = 4LL * h->n; break;
+    case BA_EXPORT_DX: src = ws->dx.p; need = 8LL * h->n; break;
+    case BA_EXPORT_DD: src = ws->dd.p; need = 4LL * h->P; break;
+    case BA_EXPORT_CT: src = ws->Ct.p; need = 4LL * h->P; break;
+    case BA_EXPORT_W: src = ws->wk.p; need = 4LL * h->P; break;
+    case BA_EXPORT_PERM: src = ws->perm.p; need = 4LL * h->E; break;
+    case BA_EXPORT_SLOTS: src = ws->eslot.p; need = 4LL * h->E; break;
+    case BA_EXPORT_GPTR: src = ws->gptr.p; need = 4LL * (h->ngroups + 1); break;
+    case BA_EXPORT_WIN: src = ws->win.p; need = 4LL * h->ngroups * DPV_WMAX; break;
+    case BA_EXPORT_COST: src = ws->cost; need = 8LL * std::max(1, std::min<int>(h->last_iters, (int)ws->cost_cap)); break;
+    default: return dpv_fail(h, BA_ERR_INVALID_ARG, "unknown export");
+  }
+  if (bytes < need) return dpv_fail(h, BA_ERR_INVALID_ARG, "export buffer too small");
+  ba_status_t s;
+  if (what == BA_EXPORT_S) {
+    if ((s = dpv_export_S(h, (float*)dst))) return s;
+  } else if (need > 0) {
+    DPV_CUDA(h, cudaMemcpyAsync(dst, src, need, cudaMemcpyDeviceToDevice, h->stream));
+  }
+  DPV_CUDA(h, cudaStreamSynchronize(h->stream));
+  return BA_OK;
+}
+
+ba_status_t ba_debug_keys(ba_handle_t h, int fixed_poses, int* keys_out, int cap, int* n_out) {
+  if (!h || !n_out || (cap > 0 && !keys_out)) return BA_ERR_INVALID_ARG;
+  if (!h->have_graph) return dpv_fail(h, BA_ERR_STATE, "no graph bound");
+  return dpv_block_keys(h, fixed_poses, keys_out, cap, n_out);
+}
+
+}  // extern "C"

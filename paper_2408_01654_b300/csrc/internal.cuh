@@ -1,0 +1,242 @@
+// Internal declarations of the dpvba library (sm_103a).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string>
+#include <vector>
+
+#include "../../include/dpvba.h"
+
+// ---------------------------------------------------------------------------
+// limits of the kernels
+// ---------------------------------------------------------------------------
+#define DPV_WMAX 32          // frames in one group window (slots fit in 8 bits)
+#define DPV_GMAX 64          // patches per group
+#define DPV_SMALL_N 256      // pose systems up to this size use the one-CTA solver
+#define DPV_TILE 64          // tile edge of the blocked pose system (large n)
+
+// device status codes (mirror ba_status_t)
+#define DST_OK 0
+#define DST_BAD_INDEX 1
+#define DST_NOT_SPD 4
+#define DST_TIMEOUT 5
+#define DST_WIDE 7
+
+struct Workspace;
+
+struct ba_handle_s {
+  ba_options_t opt;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  int num_sms = 148;
+  std::string last_error;
+
+  // bound graph (borrowed user buffers)
+  int have_graph = 0;
+  int N = 0, P = 0, E = 0;
+  double* poses = nullptr;
+  float* patches = nullptr;
+  const float* targets = nullptr;
+  const float* weights = nullptr;
+
+  // grouping
+  int G = 32;            // patches per group
+  int ngroups = 0;
+  int sort_bits = 0;
+
+  // solver geometry for the last fixed value
+  int fixed = -1;
+  int n = 0;             // 6 * (N - fixed)
+  int TS = 0;            // tile edge
+  int T = 0;             // tiles per dimension
+  int n_pad = 0;         // T * TS
+  int last_iters = 0;
+
+  Workspace* ws = nullptr;
+
+  // event timing of kernel classes (ba_profile_enable)
+  int prof_on = 0;
+  struct ProfRec {
+    int kind;
+    cudaEvent_t a, b;
+  };
+  std::vector<ProfRec> prof;
+  std::vector<cudaEvent_t> ev_pool;
+  int prof_open = -1;
+
+  long long launches = 0;  // kernels launched by this handle so far
+};
+
+// A device buffer owned by the handle, grown on demand (never shrunk).
+template <class T>
+struct DBuf {
+  T* p = nullptr;
+  long long cap = 0;
+};
+
+// device buffers, all owned by the handle
+struct Workspace {
+  int* status = nullptr;          // [1] first device-detected error
+  float* intr = nullptr;          // [4]
+  double* cost = nullptr;         // [cost_cap] cost at each iteration's linearisation point
+  int* nruns = nullptr;           // [1]
+  long long cost_cap = 0;
+  // preprocessing
+  DBuf<int> src;                  // [P] source frame of each patch, -1 none
+  DBuf<unsigned long long> keys0, keys1;  // [E] sort keys
+  DBuf<int> vals0, vals1;         // [E] sort values
+  DBuf<int> hist;                 // radix histograms + their scan
+  DBuf<int> perm;                 // [E] sorted position -> input edge
+  DBuf<unsigned> eslot;           // [E] packed slots
+  DBuf<int> runflag, runid, runptr;  // [E+1] run starts, ids, positions
+  DBuf<int> gptr, gseg;           // [groups+1] edge and run ranges of each group
+  DBuf<int> win;                  // [groups * DPV_WMAX] window frames
+  DBuf<int> wlen;                 // [groups]
+  DBuf<int> scan;                 // block sums of the scan
+  // per iteration
+  DBuf<float> S;                  // tiled lower triangle of the pose system
+  DBuf<float> y;                  // [n_pad]
+  DBuf<double> dx;                // [n_pad]
+  DBuf<float> Ct, wk, dd;         // [P]
+  // blocked solver
+  DBuf<float> L;                  // factor (large n)
+  DBuf<double> r64;               // [n_pad]
+  DBuf<float> tmpv;               // [n_pad]
+};
+
+// ---------------------------------------------------------------------------
+// host helpers
+// ---------------------------------------------------------------------------
+ba_status_t dpv_fail(ba_handle_t h, ba_status_t s, const std::string& msg);
+#define DPV_CUDA(h, call)                                                              \
+  do {                                                                                 \
+    cudaError_t _e = (call);                                                           \
+    if (_e != cudaSuccess)                                                             \
+      return dpv_fail((h), _e == cudaErrorMemoryAllocation ? BA_ERR_OOM : BA_ERR_CUDA, \
+                      std::string(#call) + ": " + cudaGetErrorString(_e));             \
+  } while (0)
+
+// event timing around a kernel class (no-ops unless profiling is enabled)
+void dpv_prof_begin(ba_handle_t h, int kind);
+void dpv_prof_end(ba_handle_t h);
+
+// preprocessing (preprocess.cu)
+ba_status_t dpv_preprocess(ba_handle_t h, const int* ii, const int* jj, const int* kk);
+ba_status_t dpv_block_keys(ba_handle_t h, int fixed, int* keys_out, int cap, int* n_out);
+ba_status_t dpv_exclusive_scan(ba_handle_t h, const int* in, int* out, int n);  // out has n+1 entries
+long long dpv_scan_scratch(long long n);
+long long dpv_hist_entries(long long m);
+// one GN iteration (assemble.cu, solve_*.cu, update.cu)
+ba_status_t dpv_assemble(ba_handle_t h, int it);
+ba_status_t dpv_solve(ba_handle_t h);
+ba_status_t dpv_backsub(ba_handle_t h);
+ba_status_t dpv_retract(ba_handle_t h);
+ba_status_t dpv_export_S(ba_handle_t h, float* dst);
+
+// ---------------------------------------------------------------------------
+// device helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void dpv_set_status(int* status, int code) { atomicCAS(status, 0, code); }
+__device__ __forceinline__ int dpv_status(const int* status) { return *(volatile const int*)status; }
+
+// Tiled lower-triangular storage of the pose system: tile (ti, tj), ti >= tj,
+// is a TS x TS row-major block at offset (ti (ti+1)/2 + tj) TS^2.
+__host__ __device__ __forceinline__ size_t dpv_tile_base(int ti, int tj, int TS) {
+  return ((size_t)ti * (ti + 1) / 2 + tj) * (size_t)TS * TS;
+}
+__host__ __device__ __forceinline__ size_t dpv_s_index(int r, int c, int TS) {
+  const int ti = r / TS, tj = c / TS;
+  return dpv_tile_base(ti, tj, TS) + (size_t)(r - ti * TS) * TS + (c - tj * TS);
+}
+
+__device__ __forceinline__ void dpv_red_add(float* p, float v) {
+  asm volatile("red.global.add.f32 [%0], %1;" ::"l"(p), "f"(v) : "memory");
+}
+
+// rotation matrix of a unit quaternion (x, y, z, w), FP64
+__device__ __forceinline__ void dpv_quat_rot64(const double* q, double* R) {
+  const double x = q[0], y = q[1], z = q[2], w = q[3];
+  R[0] = 1.0 - 2.0 * (y * y + z * z); R[1] = 2.0 * (x * y - z * w); R[2] = 2.0 * (x * z + y * w);
+  R[3] = 2.0 * (x * y + z * w); R[4] = 1.0 - 2.0 * (x * x + z * z); R[5] = 2.0 * (y * z - x * w);
+  R[6] = 2.0 * (x * z - y * w); R[7] = 2.0 * (y * z + x * w); R[8] = 1.0 - 2.0 * (x * x + y * y);
+}
+
+struct RelPose {
+  float R[9], t[3], txR[9];  // rotation, translation, [t]x R (translation-rotation block of Ad)
+};
+
+// Relative pose T_ij = T_j T_i^-1 of two world->camera poses (t, q), formed
+// in FP64 and rounded to FP32:  R = R_j R_i^T,  t = t_j - R t_i.
+__device__ __forceinline__ void dpv_relative_pose(const double* pi, const double* pj, RelPose& o) {
+  double Ri[9], Rj[9], R[9];
+  dpv_quat_rot64(pi + 3, Ri);
+  dpv_quat_rot64(pj + 3, Rj);
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+      R[3 * r + c] = Rj[3 * r] * Ri[3 * c] + Rj[3 * r + 1] * Ri[3 * c + 1] + Rj[3 * r + 2] * Ri[3 * c + 2];
+  double t[3];
+#pragma unroll
+  for (int r = 0; r < 3; ++r) t[r] = pj[r] - (R[3 * r] * pi[0] + R[3 * r + 1] * pi[1] + R[3 * r + 2] * pi[2]);
+#pragma unroll
+  for (int m = 0; m < 9; ++m) o.R[m] = (float)R[m];
+#pragma unroll
+  for (int m = 0; m < 3; ++m) o.t[m] = (float)t[m];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    o.txR[0 + c] = (float)(-t[2] * R[3 + c] + t[1] * R[6 + c]);
+    o.txR[3 + c] = (float)(t[2] * R[0 + c] - t[0] * R[6 + c]);
+    o.txR[6 + c] = (float)(-t[1] * R[0 + c] + t[0] * R[3 + c]);
+  }
+}
+
+// Per-edge linearisation of Eq. 3 at the patch centre (FP32).
+//   X = R xb + t d  (xb = ((u-cx)/fx, (v-cy)/fy, 1), homogeneous 4th entry d)
+//   proj = (fx X/Z + cx, fy Y/Z + cy),  r = target - proj
+//   Jj = dproj/dX [ d I | -[X]x ],  Ji = -Jj Ad(T_ij),  Jd = dproj/dX t
+struct EdgeLin {
+  float r[2];
+  float Ji[2][6], Jj[2][6], Jd[2];
+  bool valid;
+};
+
+__device__ __forceinline__ void dpv_edge_linearize(const RelPose& T, float xb0, float xb1, float d, float tu,
+                                                   float tv, const float* K, float z_min, bool self_edge,
+                                                   EdgeLin& o) {
+  const float X = fmaf(T.R[0], xb0, fmaf(T.R[1], xb1, fmaf(T.t[0], d, T.R[2])));
+  const float Y = fmaf(T.R[3], xb0, fmaf(T.R[4], xb1, fmaf(T.t[1], d, T.R[5])));
+  const float Z = fmaf(T.R[6], xb0, fmaf(T.R[7], xb1, fmaf(T.t[2], d, T.R[8])));
+  o.valid = !self_edge && (Z > z_min * d);
+  const float iz = 1.0f / Z;
+  const float fx = K[0], fy = K[1];
+  o.r[0] = tu - fmaf(fx * X, iz, K[2]);
+  o.r[1] = tv - fmaf(fy * Y, iz, K[3]);
+  const float a0 = fx * iz, a2 = -fx * X * iz * iz;
+  const float b1 = fy * iz, b2 = -fy * Y * iz * iz;
+  o.Jj[0][0] = a0 * d; o.Jj[0][1] = 0.f; o.Jj[0][2] = a2 * d;
+  o.Jj[0][3] = a2 * Y; o.Jj[0][4] = a0 * Z - a2 * X; o.Jj[0][5] = -a0 * Y;
+  o.Jj[1][0] = 0.f; o.Jj[1][1] = b1 * d; o.Jj[1][2] = b2 * d;
+  o.Jj[1][3] = -b1 * Z + b2 * Y; o.Jj[1][4] = -b2 * X; o.Jj[1][5] = b1 * X;
+#pragma unroll
+  for (int a = 0; a < 2; ++a) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const float jr = o.Jj[a][0] * T.R[c] + o.Jj[a][1] * T.R[3 + c] + o.Jj[a][2] * T.R[6 + c];
+      const float jt = o.Jj[a][0] * T.txR[c] + o.Jj[a][1] * T.txR[3 + c] + o.Jj[a][2] * T.txR[6 + c] +
+                       o.Jj[a][3] * T.R[c] + o.Jj[a][4] * T.R[3 + c] + o.Jj[a][5] * T.R[6 + c];
+      o.Ji[a][c] = -jr;
+      o.Ji[a][3 + c] = -jt;
+    }
+  }
+  o.Jd[0] = a0 * T.t[0] + a2 * T.t[2];
+  o.Jd[1] = b1 * T.t[1] + b2 * T.t[2];
+}
+
+// packed per-edge slot word
+__host__ __device__ __forceinline__ unsigned dpv_pack_slot(int si, int sj, int kl) {
+  return (unsigned)si | ((unsigned)sj << 8) | ((unsigned)kl << 16);
+}
+__host__ __device__ __forceinline__ int dpv_slot_i(unsigned w) { return (int)(w & 0xff); }
+__host__ __device__ __forceinline__ int dpv_slot_j(unsigned w) { return (int)((w >> 8) & 0xff); }
+__host__ __device__ __forceinline__ int dpv_slot_k(unsigned w) { return (int)(w >> 16); }

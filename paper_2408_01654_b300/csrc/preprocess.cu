@@ -1,0 +1,477 @@
+// Graph preprocessing for ba_set_graph (runs once per bound graph).
+//
+// Builds, on the GPU and without host round trips:
+//   * validation of every index and of "one source frame per patch"
+//     (the patch graph of Sec. 3.1: patch k belongs to frame i; edges (i,k,j));
+//   * the edge order used by all reduction kernels: a stable sort by
+//     (group, ii, jj, patch-in-group) with group = kk / G, so that each group
+//     of G consecutive patches owns a contiguous edge range and, inside it,
+//     every (source frame, target frame) pair is one contiguous "run";
+//   * per group: its window (sorted frames touched by its edges, at most
+//     DPV_WMAX) and, per edge, the window slots of ii and jj.
+#include "internal.cuh"
+
+#include <algorithm>
+
+namespace {
+
+constexpr int RS_THREADS = 256;
+constexpr int RS_ITEMS = 8;
+constexpr int RS_TILE = RS_THREADS * RS_ITEMS;
+constexpr int SCAN_THREADS = 1024;
+constexpr int SCAN_ITEMS = 4;
+constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
+
+// ---------------------------------------------------------------------------
+// exclusive scan of int32 (tile sums, scan of the sums, down-sweep)
+// ---------------------------------------------------------------------------
+__device__ int block_exclusive_scan(int v, int* sh, int& total) {
+  const int t = threadIdx.x;
+  const int lane = t & 31, w = t >> 5;
+  int x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) sh[w] = x;
+  __syncthreads();
+  const int nw = blockDim.x >> 5;
+  if (w == 0) {
+    int s = lane < nw ? sh[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, s, o);
+      if (lane >= o) s += y;
+    }
+    if (lane < nw) sh[lane] = s;
+  }
+  __syncthreads();
+  const int wpre = w ? sh[w - 1] : 0;
+  total = sh[nw - 1];
+  __syncthreads();
+  return wpre + x - v;
+}
+
+__global__ void k_scan_tiles(const int* __restrict__ in, int n, int* __restrict__ sums) {
+  __shared__ int sh[32];
+  const int base = blockIdx.x * SCAN_TILE;
+  int s = 0;
+#pragma unroll
+  for (int r = 0; r < SCAN_ITEMS; ++r) {
+    const int idx = base + r * SCAN_THREADS + threadIdx.x;
+    if (idx < n) s += in[idx];
+  }
+  int total;
+  block_exclusive_scan(s, sh, total);
+  if (threadIdx.x == 0) sums[blockIdx.x] = total;
+}
+
+__global__ void k_scan_sums(int* sums, int nb) {
+  __shared__ int sh[32];
+  const int per = (nb + blockDim.x - 1) / blockDim.x;
+  const int lo = threadIdx.x * per, hi = min(nb, lo + per);
+  int s = 0;
+  for (int i = lo; i < hi; ++i) s += sums[i];
+  int total;
+  int run = block_exclusive_scan(s, sh, total);
+  for (int i = lo; i < hi; ++i) {
+    const int v = sums[i];
+    sums[i] = run;
+    run += v;
+  }
+  if (threadIdx.x == 0) sums[nb] = total;
+}
+
+__global__ void k_scan_down(const int* __restrict__ in, int n, const int* __restrict__ sums,
+                            int* __restrict__ out) {
+  __shared__ int sh[32];
+  const int base = blockIdx.x * SCAN_TILE + threadIdx.x * SCAN_ITEMS;
+  int v[SCAN_ITEMS], s = 0;
+#pragma unroll
+  for (int r = 0; r < SCAN_ITEMS; ++r) {
+    v[r] = (base + r < n) ? in[base + r] : 0;
+    s += v[r];
+  }
+  int total;
+  int run = block_exclusive_scan(s, sh, total) + sums[blockIdx.x];
+#pragma unroll
+  for (int r = 0; r < SCAN_ITEMS; ++r) {
+    if (base + r < n) out[base + r] = run;
+    run += v[r];
+  }
+  if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) out[n] = sums[gridDim.x];
+}
+
+// ---------------------------------------------------------------------------
+// validation and sort keys
+// ---------------------------------------------------------------------------
+__global__ void k_validate(int E, int N, int P, int G, const int* __restrict__ ii, const int* __restrict__ jj,
+                           const int* __restrict__ kk, int* __restrict__ src, unsigned long long* __restrict__ keys,
+                           int* __restrict__ vals, int* status) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= E) return;
+  const int i = ii[e], j = jj[e], k = kk[e];
+  vals[e] = e;
+  if (i < 0 || i >= N || j < 0 || j >= N || k < 0 || k >= P) {
+    dpv_set_status(status, DST_BAD_INDEX);
+    keys[e] = 0ull;
+    return;
+  }
+  const int old = atomicCAS(&src[k], -1, i);
+  if (old != -1 && old != i) dpv_set_status(status, DST_BAD_INDEX);
+  const unsigned long long g = (unsigned)(k / G), kl = (unsigned)(k % G);
+  keys[e] = ((g * (unsigned)N + (unsigned)i) * (unsigned)N + (unsigned)j) * (unsigned)G + kl;
+}
+
+// ---------------------------------------------------------------------------
+// stable LSD radix sort, 8-bit digits.  Inside a tile, items are ranked in
+// rounds of 256 consecutive keys; a warp ranks equal digits with
+// __match_any_sync, warps are ordered through a per-digit prefix, so equal
+// keys keep their input order.
+// ---------------------------------------------------------------------------
+__global__ void k_rs_hist(const unsigned long long* __restrict__ keys, int M, int shift, int* __restrict__ hist,
+                          int nblocks) {
+  __shared__ int cnt[256];
+  const int t = threadIdx.x;
+  cnt[t] = 0;
+  __syncthreads();
+  const int base = blockIdx.x * RS_TILE;
+#pragma unroll
+  for (int r = 0; r < RS_ITEMS; ++r) {
+    const int idx = base + r * RS_THREADS + t;
+    if (idx < M) atomicAdd(&cnt[(unsigned)(keys[idx] >> shift) & 255u], 1);
+  }
+  __syncthreads();
+  hist[(size_t)t * nblocks + blockIdx.x] = cnt[t];
+}
+
+__global__ void k_rs_scatter(const unsigned long long* __restrict__ kin, const int* __restrict__ vin,
+                             unsigned long long* __restrict__ kout, int* __restrict__ vout, int M, int shift,
+                             const int* __restrict__ offs, int nblocks) {
+  __shared__ int base_off[256];
+  __shared__ int wcnt[RS_THREADS / 32][256];
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  base_off[t] = offs[(size_t)t * nblocks + blockIdx.x];
+  const unsigned lt = (1u << lane) - 1u;
+  const int base = blockIdx.x * RS_TILE;
+  for (int r = 0; r < RS_ITEMS; ++r) {
+#pragma unroll
+    for (int q = 0; q < RS_THREADS / 32; ++q) wcnt[q][t] = 0;
+    __syncthreads();
+    const int idx = base + r * RS_THREADS + t;
+    const bool valid = idx < M;
+    unsigned long long key = 0;
+    int val = 0;
+    unsigned digit = 256u;
+    if (valid) {
+      key = kin[idx];
+      val = vin[idx];
+      digit = (unsigned)(key >> shift) & 255u;
+    }
+    const unsigned peers = __match_any_sync(0xffffffffu, digit);
+    const int lrank = __popc(peers & lt);
+    if (valid && lrank == 0) wcnt[w][digit] = __popc(peers);
+    __syncthreads();
+    int run = 0;
+#pragma unroll
+    for (int q = 0; q < RS_THREADS / 32; ++q) {
+      const int c = wcnt[q][t];
+      wcnt[q][t] = run;
+      run += c;
+    }
+    __syncthreads();
+    if (valid) {
+      const int pos = base_off[digit] + wcnt[w][digit] + lrank;
+      kout[pos] = key;
+      vout[pos] = val;
+    }
+    __syncthreads();
+    base_off[t] += run;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// group pointers and run flags on the sorted order
+// ---------------------------------------------------------------------------
+__global__ void k_finalize(int E, int G, int ngroups, const int* __restrict__ perm, const int* __restrict__ ii,
+                           const int* __restrict__ jj, const int* __restrict__ kk, int* __restrict__ gptr,
+                           int* __restrict__ runflag, const int* status) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= E) return;
+  if (dpv_status(status)) {
+    runflag[s] = 0;
+    return;
+  }
+  const int e = perm[s];
+  const int i = ii[e], j = jj[e], g = kk[e] / G;
+  int flag;
+  if (s == 0) {
+    for (int q = 0; q <= g; ++q) gptr[q] = 0;
+    flag = 1;
+  } else {
+    const int ep = perm[s - 1];
+    const int gp = kk[ep] / G;
+    for (int q = gp + 1; q <= g; ++q) gptr[q] = s;
+    flag = (g != gp) || (i != ii[ep]) || (j != jj[ep]);
+  }
+  if (s == E - 1)
+    for (int q = g + 1; q <= ngroups; ++q) gptr[q] = E;
+  runflag[s] = flag;
+}
+
+__global__ void k_runs(int E, int ngroups, const int* __restrict__ runflag, const int* __restrict__ runid,
+                       const int* __restrict__ gptr, int* __restrict__ runptr, int* __restrict__ gseg,
+                       int* __restrict__ nruns) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  const int total = runid[E];
+  if (s < E && runflag[s]) runptr[runid[s]] = s;
+  if (s == 0) {
+    runptr[total] = E;
+    *nruns = total;
+  }
+  if (s <= ngroups) {
+    const int p = gptr[s];
+    gseg[s] = p < E ? runid[p] : total;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// group windows: sorted unique frames of each group's edges, and edge slots
+// ---------------------------------------------------------------------------
+__global__ void k_windows(int N, int G, const int* __restrict__ gptr, const int* __restrict__ perm,
+                          const int* __restrict__ ii, const int* __restrict__ jj, const int* __restrict__ kk,
+                          int* __restrict__ win, int* __restrict__ wlen, unsigned* __restrict__ eslot,
+                          int* status) {
+  extern __shared__ unsigned smw[];
+  __shared__ int sh[32];
+  const int nwords = (N + 31) >> 5;
+  unsigned* bm = smw;
+  int* wpre = (int*)(smw + nwords);
+  const int g = blockIdx.x;
+  if (dpv_status(status)) return;
+  const int s0 = gptr[g], s1 = gptr[g + 1];
+  for (int q = threadIdx.x; q < nwords; q += blockDim.x) bm[q] = 0u;
+  __syncthreads();
+  for (int s = s0 + threadIdx.x; s < s1; s += blockDim.x) {
+    const int e = perm[s];
+    const int i = ii[e], j = jj[e];
+    atomicOr(&bm[i >> 5], 1u << (i & 31));
+    atomicOr(&bm[j >> 5], 1u << (j & 31));
+  }
+  __syncthreads();
+  const int per = (nwords + blockDim.x - 1) / blockDim.x;
+  const int lo = threadIdx.x * per, hi = min(nwords, lo + per);
+  int c = 0;
+  for (int q = lo; q < hi; ++q) c += __popc(bm[q]);
+  int total;
+  int run = block_exclusive_scan(c, sh, total);
+  for (int q = lo; q < hi; ++q) {
+    wpre[q] = run;
+    run += __popc(bm[q]);
+  }
+  __syncthreads();
+  if (total > DPV_WMAX) {
+    if (threadIdx.x == 0) {
+      wlen[g] = total;
+      dpv_set_status(status, DST_WIDE);
+    }
+    return;
+  }
+  for (int q = threadIdx.x; q < nwords; q += blockDim.x) {
+    unsigned word = bm[q];
+    int slot = wpre[q];
+    while (word) {
+      const int b = __ffs(word) - 1;
+      win[g * DPV_WMAX + slot++] = (q << 5) + b;
+      word &= word - 1;
+    }
+  }
+  for (int q = total + threadIdx.x; q < DPV_WMAX; q += blockDim.x) win[g * DPV_WMAX + q] = -1;
+  if (threadIdx.x == 0) wlen[g] = total;
+  for (int s = s0 + threadIdx.x; s < s1; s += blockDim.x) {
+    const int e = perm[s];
+    const int i = ii[e], j = jj[e];
+    const int si = wpre[i >> 5] + __popc(bm[i >> 5] & ((1u << (i & 31)) - 1u));
+    const int sj = wpre[j >> 5] + __popc(bm[j >> 5] & ((1u << (j & 31)) - 1u));
+    eslot[s] = dpv_pack_slot(si, sj, kk[e] % G);
+  }
+}
+
+// block keys (inspection): three candidate keys per sorted edge, invalid ->
+// ~0.  The edge's frames are read back from its group window and slots.
+__global__ void k_key_candidates(int N, int fixed, const int* __restrict__ gptr, const unsigned* __restrict__ eslot,
+                                 const int* __restrict__ win, unsigned long long* __restrict__ keys,
+                                 int* __restrict__ vals) {
+  const int g = blockIdx.x;
+  for (int s = gptr[g] + threadIdx.x; s < gptr[g + 1]; s += blockDim.x) {
+    const unsigned w = eslot[s];
+    const int i = win[g * DPV_WMAX + dpv_slot_i(w)], j = win[g * DPV_WMAX + dpv_slot_j(w)];
+    const int a[3] = {i, j, min(i, j)}, b[3] = {i, j, max(i, j)};
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      const bool ok = (i != j) && a[q] >= fixed && b[q] >= fixed;
+      keys[3 * (size_t)s + q] = ok ? (unsigned long long)a[q] * (unsigned)N + (unsigned)b[q] : ~0ull;
+      vals[3 * (size_t)s + q] = 3 * s + q;
+    }
+  }
+}
+
+__global__ void k_key_unique_flags(int M, const unsigned long long* __restrict__ keys, int* __restrict__ flag) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= M) return;
+  const unsigned long long k = keys[s];
+  flag[s] = (k != ~0ull) && (s == 0 || keys[s - 1] != k);
+}
+
+__global__ void k_key_emit(int M, int N, const unsigned long long* __restrict__ keys, const int* __restrict__ flag,
+                           const int* __restrict__ pos, int* __restrict__ out, int cap) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= M || !flag[s]) return;
+  const int p = pos[s];
+  if (p < cap) {
+    out[2 * p] = (int)(keys[s] / (unsigned)N);
+    out[2 * p + 1] = (int)(keys[s] % (unsigned)N);
+  }
+}
+
+// Sorts (k0, v0) by the low `bits` bits of the keys; `which` tells whether
+// the result ended in (k0, v0) or (k1, v1).  hist needs dpv_hist_entries(M).
+ba_status_t radix_sort(ba_handle_t h, unsigned long long* k0, int* v0, unsigned long long* k1, int* v1, int M,
+                       int bits, int* hist, int& which) {
+  which = 0;
+  if (M <= 1) return BA_OK;
+  const int nb = (M + RS_TILE - 1) / RS_TILE;
+  unsigned long long* kin = k0;
+  unsigned long long* kout = k1;
+  int* vin = v0;
+  int* vout = v1;
+  int* offs = hist + 256 * nb;
+  for (int shift = 0; shift < bits; shift += 8) {
+    k_rs_hist<<<nb, RS_THREADS, 0, h->stream>>>(kin, M, shift, hist, nb);
+    ++h->launches;
+    ba_status_t st = dpv_exclusive_scan(h, hist, offs, 256 * nb);
+    if (st) return st;
+    k_rs_scatter<<<nb, RS_THREADS, 0, h->stream>>>(kin, vin, kout, vout, M, shift, offs, nb);
+    ++h->launches;
+    std::swap(kin, kout);
+    std::swap(vin, vout);
+    which ^= 1;
+  }
+  DPV_CUDA(h, cudaGetLastError());
+  return BA_OK;
+}
+
+}  // namespace
+
+long long dpv_scan_scratch(long long n) { return (n + SCAN_TILE - 1) / SCAN_TILE + 2; }
+long long dpv_hist_entries(long long m) { return 2 * 256 * ((m + RS_TILE - 1) / RS_TILE) + 2; }
+
+ba_status_t dpv_exclusive_scan(ba_handle_t h, const int* in, int* out, int n) {
+  Workspace* ws = h->ws;
+  if (n <= 0) {
+    DPV_CUDA(h, cudaMemsetAsync(out, 0, sizeof(int), h->stream));
+    return BA_OK;
+  }
+  const int nb = (n + SCAN_TILE - 1) / SCAN_TILE;
+  if (nb + 1 > ws->scan.cap) return dpv_fail(h, BA_ERR_UNSUPPORTED, "scan larger than its scratch");
+  k_scan_tiles<<<nb, SCAN_THREADS, 0, h->stream>>>(in, n, ws->scan.p);
+  ++h->launches;
+  k_scan_sums<<<1, SCAN_THREADS, 0, h->stream>>>(ws->scan.p, nb);
+  ++h->launches;
+  k_scan_down<<<nb, SCAN_THREADS, 0, h->stream>>>(in, n, ws->scan.p, out);
+  ++h->launches;
+  DPV_CUDA(h, cudaGetLastError());
+  return BA_OK;
+}
+
+ba_status_t dpv_preprocess(ba_handle_t h, const int* ii, const int* jj, const int* kk) {
+  Workspace* ws = h->ws;
+  const int E = h->E, N = h->N, P = h->P, G = h->G;
+  cudaStream_t st = h->stream;
+  DPV_CUDA(h, cudaMemsetAsync(ws->src.p, 0xff, sizeof(int) * P, st));
+  DPV_CUDA(h, cudaMemsetAsync(ws->gptr.p, 0, sizeof(int) * (h->ngroups + 1), st));
+  if (E > 0) {
+    k_validate<<<(E + 255) / 256, 256, 0, st>>>(E, N, P, G, ii, jj, kk, ws->src.p, ws->keys0.p, ws->vals0.p,
+                                                 ws->status);
+    ++h->launches;
+    int which = 0;
+    ba_status_t s = radix_sort(h, ws->keys0.p, ws->vals0.p, ws->keys1.p, ws->vals1.p, E, h->sort_bits,
+                               ws->hist.p, which);
+    if (s) return s;
+    DPV_CUDA(h, cudaMemcpyAsync(ws->perm.p, (which ? ws->vals1.p : ws->vals0.p), sizeof(int) * E, cudaMemcpyDeviceToDevice, st));
+    k_finalize<<<(E + 255) / 256, 256, 0, st>>>(E, G, h->ngroups, ws->perm.p, ii, jj, kk, ws->gptr.p, ws->runflag.p,
+                                                 ws->status);
+    ++h->launches;
+    s = dpv_exclusive_scan(h, ws->runflag.p, ws->runid.p, E);
+    if (s) return s;
+    const int nthr = std::max(E, h->ngroups + 1);
+    k_runs<<<(nthr + 255) / 256, 256, 0, st>>>(E, h->ngroups, ws->runflag.p, ws->runid.p, ws->gptr.p, ws->runptr.p,
+                                                ws->gseg.p, ws->nruns);
+    ++h->launches;
+  } else {
+    DPV_CUDA(h, cudaMemsetAsync(ws->gseg.p, 0, sizeof(int) * (h->ngroups + 1), st));
+    DPV_CUDA(h, cudaMemsetAsync(ws->runptr.p, 0, sizeof(int), st));
+    DPV_CUDA(h, cudaMemsetAsync(ws->nruns, 0, sizeof(int), st));
+  }
+  const int nwords = (N + 31) / 32;
+  const size_t smem = sizeof(unsigned) * nwords + sizeof(int) * nwords;
+  if (smem > 200 * 1024) return dpv_fail(h, BA_ERR_UNSUPPORTED, "too many frames for the window kernel");
+  DPV_CUDA(h, cudaFuncSetAttribute(k_windows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_windows<<<h->ngroups, 256, smem, st>>>(N, G, ws->gptr.p, ws->perm.p, ii, jj, kk, ws->win.p, ws->wlen.p, ws->eslot.p,
+                                           ws->status);
+  ++h->launches;
+  DPV_CUDA(h, cudaGetLastError());
+  return BA_OK;
+}
+
+ba_status_t dpv_block_keys(ba_handle_t h, int fixed, int* keys_out, int cap, int* n_out) {
+  const int E = h->E, N = h->N;
+  const long long M = 3LL * E;
+  *n_out = 0;
+  if (E == 0) return BA_OK;
+  if (M > (1LL << 30)) return dpv_fail(h, BA_ERR_UNSUPPORTED, "ba_debug_keys: graph too large");
+  unsigned long long* kb[2] = {nullptr, nullptr};
+  int* vb[2] = {nullptr, nullptr};
+  int *flag = nullptr, *pos = nullptr, *scan = nullptr, *hist = nullptr;
+  int* saved_scan = h->ws->scan.p;
+  const long long saved_cap = h->ws->scan.cap;
+  auto cleanup = [&]() {
+    cudaFree(kb[0]); cudaFree(kb[1]); cudaFree(vb[0]); cudaFree(vb[1]);
+    cudaFree(flag); cudaFree(pos); cudaFree(scan); cudaFree(hist);
+    h->ws->scan.p = saved_scan;
+    h->ws->scan.cap = saved_cap;
+  };
+  const long long hist_n = dpv_hist_entries(M);
+  const long long scan_n = std::max(dpv_scan_scratch(M), dpv_scan_scratch(hist_n));
+  if (cudaMalloc(&kb[0], 8 * M) || cudaMalloc(&kb[1], 8 * M) || cudaMalloc(&vb[0], 4 * M) ||
+      cudaMalloc(&vb[1], 4 * M) || cudaMalloc(&flag, 4 * M) || cudaMalloc(&pos, 4 * (M + 1)) ||
+      cudaMalloc(&scan, 4 * scan_n) || cudaMalloc(&hist, 4 * hist_n)) {
+    cleanup();
+    return dpv_fail(h, BA_ERR_OOM, "ba_debug_keys: allocation failed");
+  }
+  h->ws->scan.p = scan;
+  h->ws->scan.cap = scan_n;
+  k_key_candidates<<<h->ngroups, 256, 0, h->stream>>>(N, fixed, h->ws->gptr.p, h->ws->eslot.p, h->ws->win.p, kb[0],
+                                                      vb[0]);
+  ++h->launches;
+  int which = 0;
+  ba_status_t rc = radix_sort(h, kb[0], vb[0], kb[1], vb[1], (int)M, 64, hist, which);
+  if (!rc) {
+    k_key_unique_flags<<<(unsigned)((M + 255) / 256), 256, 0, h->stream>>>((int)M, kb[which], flag);
+    ++h->launches;
+    rc = dpv_exclusive_scan(h, flag, pos, (int)M);
+  }
+  if (!rc) {
+    k_key_emit<<<(unsigned)((M + 255) / 256), 256, 0, h->stream>>>((int)M, N, kb[which], flag, pos, keys_out, cap);
+    ++h->launches;
+    int cnt = 0;
+    if (cudaMemcpyAsync(&cnt, pos + M, sizeof(int), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
+        cudaStreamSynchronize(h->stream) != cudaSuccess)
+      rc = dpv_fail(h, BA_ERR_CUDA, "ba_debug_keys: copy failed");
+    *n_out = cnt;
+    if (!rc && cnt > cap) rc = dpv_fail(h, BA_ERR_INVALID_ARG, "ba_debug_keys: cap too small");
+  }
+  cleanup();
+  return rc;
+}
