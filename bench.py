@@ -82,11 +82,12 @@ def algorithmic_bytes(kind, N, P, E, n):
         # poses (56 B); outputs: lower triangle of S, y, Ct and w
         return 28 * E + 12 * P + 56 * N + 4 * tri + 4 * n + 8 * P
     if kind == "backsub":
-        # edges: ii, jj, kk, weight (20 B); patches: centre + depth + Ct + w (20 B);
-        # outputs: nine depths (36 B) and the step (4 B)
-        return 20 * E + 20 * P + 56 * N + 8 * n + 40 * P
+        # per edge the two 6-vectors J^T W Jd (48 B); per patch Ct, w, the depth
+        # (12 B) and the nine updated depths (36 B); the pose step
+        return 48 * E + 48 * P + 4 * n
     if kind == "solve":
-        return 4 * tri + 4 * n + 8 * n
+        # lower triangle of S, y, the step (FP64 + FP32 copy), poses read and written
+        return 4 * tri + 4 * n + 12 * n + 112 * N
     if kind == "init":
         return 4 * tri + 4 * n
     if kind == "retract":

@@ -134,7 +134,7 @@ DPVBA_API ba_status_t ba_linearize(ba_handle_t h, int fixed_poses);
 
 enum {
   BA_EXPORT_S = 0,      /* float32 [n,n] dense, lower triangle (upper zero), n = 6 (N - fixed) */
-  BA_EXPORT_Y = 1,      /* float32 [n]        reduced right-hand side                         */
+  BA_EXPORT_Y = 1,      /* float64 [n]        reduced right-hand side                         */
   BA_EXPORT_DX = 2,     /* float64 [n]        last pose step                                  */
   BA_EXPORT_DD = 3,     /* float32 [P]        last inverse-depth step                         */
   BA_EXPORT_CT = 4,     /* float32 [P]        C + lambda_depth                                */
@@ -143,7 +143,9 @@ enum {
   BA_EXPORT_SLOTS = 7,  /* uint32 [E]         slot_i | slot_j << 8 | patch-in-group << 16     */
   BA_EXPORT_GPTR = 8,   /* int32 [groups+1]   edge range of each group                        */
   BA_EXPORT_WIN = 9,    /* int32 [groups, 32] window frames of each group (-1 padded)          */
-  BA_EXPORT_COST = 10   /* float64 [iters]    cost sum w r^2 at each iteration's linearisation point */
+  BA_EXPORT_COST = 10,  /* float64 [iters]    cost sum w r^2 at each iteration's linearisation point */
+  BA_EXPORT_PMPOS = 11, /* int32 [E]          sorted position -> patch-major position          */
+  BA_EXPORT_PPTR = 12   /* int32 [P+1]        patch-major edge range of each patch             */
 };
 
 /* Copy an internal array into `dst` (device memory, `bytes` long; fails if

@@ -9,10 +9,10 @@ import torch
 from . import capi
 
 _EXPORT_DTYPES = {
-    capi.EXPORT_Y: torch.float32, capi.EXPORT_DX: torch.float64, capi.EXPORT_DD: torch.float32,
+    capi.EXPORT_Y: torch.float64, capi.EXPORT_DX: torch.float64, capi.EXPORT_DD: torch.float32,
     capi.EXPORT_CT: torch.float32, capi.EXPORT_W: torch.float32, capi.EXPORT_PERM: torch.int32,
     capi.EXPORT_SLOTS: torch.int32, capi.EXPORT_GPTR: torch.int32, capi.EXPORT_WIN: torch.int32,
-    capi.EXPORT_COST: torch.float64,
+    capi.EXPORT_COST: torch.float64, capi.EXPORT_PMPOS: torch.int32, capi.EXPORT_PPTR: torch.int32,
 }
 
 
@@ -94,7 +94,8 @@ class DPVBA:
                 count = {capi.EXPORT_Y: inf["n"], capi.EXPORT_DX: inf["n"], capi.EXPORT_DD: inf["P"],
                          capi.EXPORT_CT: inf["P"], capi.EXPORT_W: inf["P"], capi.EXPORT_PERM: inf["E"],
                          capi.EXPORT_SLOTS: inf["E"], capi.EXPORT_GPTR: inf["groups"] + 1,
-                         capi.EXPORT_WIN: inf["groups"] * capi.WMAX, capi.EXPORT_COST: 1}[what]
+                         capi.EXPORT_WIN: inf["groups"] * capi.WMAX, capi.EXPORT_COST: 1,
+                         capi.EXPORT_PMPOS: inf["E"], capi.EXPORT_PPTR: inf["P"] + 1}[what]
             out = torch.empty(max(count, 1), dtype=_EXPORT_DTYPES[what], device=dev)
         capi.check(self._h, self._lib.ba_debug_export(self._h, what, _ptr(out),
                                                        out.numel() * out.element_size()))

@@ -192,7 +192,8 @@ ba_status_t ba_destroy(ba_handle_t h) {
     release(ws->hist); release(ws->perm); release(ws->eslot); release(ws->runflag); release(ws->runid);
     release(ws->runptr); release(ws->gptr); release(ws->gseg); release(ws->win); release(ws->wlen);
     release(ws->scan); release(ws->S); release(ws->y); release(ws->dx); release(ws->Ct); release(ws->wk);
-    release(ws->dd); release(ws->L); release(ws->r64); release(ws->tmpv);
+    release(ws->dd); release(ws->L); release(ws->r64); release(ws->tmpv); release(ws->pmpos); release(ws->pptr);
+    release(ws->pterm); release(ws->posef);
     delete ws;
   }
   prof_clear(h);
@@ -271,7 +272,9 @@ ba_status_t ba_set_graph(ba_handle_t h, int N, int P, int E, double* poses, floa
       (s = grow(h, ws->runid, En + 1, "runs")) || (s = grow(h, ws->runptr, En + 1, "runs")) ||
       (s = grow(h, ws->hist, dpv_hist_entries(En), "histograms")) || (s = grow(h, ws->scan, scan_need, "scan")) ||
       (s = grow(h, ws->gptr, Gn, "groups")) || (s = grow(h, ws->gseg, Gn, "groups")) ||
-      (s = grow(h, ws->win, Gn * DPV_WMAX, "windows")) || (s = grow(h, ws->wlen, Gn, "windows")))
+      (s = grow(h, ws->win, Gn * DPV_WMAX, "windows")) || (s = grow(h, ws->wlen, Gn, "windows")) ||
+      (s = grow(h, ws->pmpos, En, "patch-major positions")) || (s = grow(h, ws->pptr, (long long)P + 1, "patch CSR")) ||
+      (s = grow(h, ws->pterm, 4 * En, "edge depth terms")) || (s = grow(h, ws->posef, 16LL * N, "pose table")))
     return s;
   DPV_CUDA(h, cudaMemsetAsync(ws->status, 0, sizeof(int), h->stream));
   DPV_CUDA(h, cudaMemcpyAsync(ws->intr, intrinsics, 4 * sizeof(float), cudaMemcpyDefault, h->stream));
@@ -301,16 +304,19 @@ ba_status_t ba_step(ba_handle_t h, int iters, int fixed_poses) {
   DPV_CUDA(h, cudaMemsetAsync(h->ws->cost, 0, sizeof(double) * h->ws->cost_cap, h->stream));
   for (int it = 0; it < iters; ++it) {
     if ((s = dpv_assemble(h, it))) return s;
+    int retracted = 0;
     dpv_prof_begin(h, BA_KERNEL_SOLVE);
-    s = dpv_solve(h);
+    s = dpv_solve(h, &retracted);
     dpv_prof_end(h);
     if (s) return s;
+    if (!retracted) {
+      dpv_prof_begin(h, BA_KERNEL_RETRACT);
+      s = dpv_retract(h);
+      dpv_prof_end(h);
+      if (s) return s;
+    }
     dpv_prof_begin(h, BA_KERNEL_BACKSUB);
     s = dpv_backsub(h);
-    dpv_prof_end(h);
-    if (s) return s;
-    dpv_prof_begin(h, BA_KERNEL_RETRACT);
-    s = dpv_retract(h);
     dpv_prof_end(h);
     if (s) return s;
   }
@@ -369,7 +375,7 @@ ba_status_t ba_debug_export(ba_handle_t h, int what, void* dst, long long bytes)
   long long need = 0;
   switch (what) {
     case BA_EXPORT_S: need = 4LL * h->n * h->n; break;
-    case BA_EXPORT_Y: src = ws->y.p; need = 4LL * h->n; break;
+    case BA_EXPORT_Y: src = ws->y.p; need = 8LL * h->n; break;
     case BA_EXPORT_DX: src = ws->dx.p; need = 8LL * h->n; break;
     case BA_EXPORT_DD: src = ws->dd.p; need = 4LL * h->P; break;
     case BA_EXPORT_CT: src = ws->Ct.p; need = 4LL * h->P; break;
@@ -378,6 +384,8 @@ ba_status_t ba_debug_export(ba_handle_t h, int what, void* dst, long long bytes)
     case BA_EXPORT_SLOTS: src = ws->eslot.p; need = 4LL * h->E; break;
     case BA_EXPORT_GPTR: src = ws->gptr.p; need = 4LL * (h->ngroups + 1); break;
     case BA_EXPORT_WIN: src = ws->win.p; need = 4LL * h->ngroups * DPV_WMAX; break;
+    case BA_EXPORT_PMPOS: src = ws->pmpos.p; need = 4LL * h->E; break;
+    case BA_EXPORT_PPTR: src = ws->pptr.p; need = 4LL * (h->P + 1); break;
     case BA_EXPORT_COST: src = ws->cost; need = 8LL * std::max(1, std::min<int>(h->last_iters, (int)ws->cost_cap)); break;
     default: return dpv_fail(h, BA_ERR_INVALID_ARG, "unknown export");
   }

@@ -7,54 +7,65 @@
 //   H = [ B  E ; E^T  C ],  g = [ v ; w ],   S = B + lambda_p I - E Ct^-1 E^T,
 //   y = v - E Ct^-1 w,  Ct = C + lambda_d  (C diagonal: one depth per patch).
 //
-// Because every patch has a single inverse depth, E Ct^-1 E^T is a sum of
-// rank-1 terms e_k e_k^T / Ct_k over patches.  A CTA owns one *group* of G
-// consecutive patches and the window W of frames its edges touch (at most
-// DPV_WMAX).  It
-//   1. linearises every edge of the group (one warp per (source, target) run,
-//      per-lane register accumulation of the 6x6 B blocks and 6x1 v blocks,
-//      one warp reduction per run) and accumulates, in shared memory, the
-//      window-local B, v and the per-patch columns e_k and scalars C_k, w_k;
-//   2. scales e_k by Ct_k^-1/2 and forms the window-local Schur complement
-//      B - E_hat E_hat^T and y - E_hat w_hat (a small dense SYRK over the G
-//      patches of the group);
-//   3. adds the window-local result into the global tiled lower-triangular S
-//      and y with fire-and-forget red.global.add; each entry of S receives at
-//      most one add per group whose window covers it.
+// Every patch has a single inverse depth, so E Ct^-1 E^T is a sum of rank-1
+// terms e_k e_k^T / Ct_k.  A CTA owns one *group* of G consecutive patches and
+// the window W (at most DPV_WMAX frames) its edges touch:
+//
+//   phase 0  relative pose of each (source, target) run of the group, from the
+//            per-pose table (R, camera centre in double-float);
+//   phase 1  one warp per run: each lane linearises an edge, stages its
+//            sqrt(w)-scaled Jacobian rows in shared memory and writes the
+//            edge's depth terms (J^T W Jd, Jd^T W Jd, Jd^T W r) to the
+//            patch-major table; the lanes then reduce the run's 6x6 blocks
+//            Hii, Hij, Hjj and vectors vi, vj with compensated sums;
+//   phase 2  one thread per patch sums its edges' depth terms (compensated)
+//            into e_k, C_k, w_k and forms the column e_k / sqrt(Ct_k);
+//   phase 3  one thread per entry of the window's lower triangle forms
+//            B_ab - sum_k e_a e_b / Ct_k with compensated sums and adds it to
+//            the global tiled S with red.global.add.f64 (likewise y).
+//
+// Why compensated sums: S is the small difference of two large, nearly equal
+// sums (B and E Ct^-1 E^T).  Rounding each FP32 product is harmless, but FP32
+// rounding of the sums costs ~1e-5 of the step on odometry windows; TwoSum /
+// TwoProd ("double-float") sums inside the group remove it.  The sum across
+// groups (up to ~150 groups per entry with small groups) is carried in FP64
+// by the L2 atomics: in FP32 it alone costs ~6e-6 of the step.
 #include "internal.cuh"
 
 namespace {
 
 constexpr int AS_THREADS = 256;
 constexpr int AS_WARPS = AS_THREADS / 32;
-constexpr int EH_STRIDE = 6 * DPV_WMAX + 1;   // floats per patch column of E_hat
-constexpr int NV = 90;                        // run accumulator length
+constexpr int EH_STRIDE = 6 * DPV_WMAX + 1;  // floats per patch column of E_hat
+constexpr int NV = 90;                       // run block entries: Hii 21, Hij 36, Hjj 21, vi 6, vj 6
+constexpr int ROWF = 27;                     // staged floats per edge: 13 per residual component + pad
+
+// (row a, row b) of the staged per-edge vector [sqrt(w) Ji (6), sqrt(w) Jj (6), sqrt(w) r]
+// whose product gives run entry q
+__constant__ unsigned char c_pa[NV], c_pb[NV];
 
 __host__ __device__ constexpr int tri(int r, int c) { return r * (r + 1) / 2 + c; }
 
-struct AsmSmem {
-  static constexpr int SB = tri(6 * DPV_WMAX, 0);  // packed lower (6W)(6W+1)/2
-};
-
 size_t assemble_smem_bytes(int G) {
-  return sizeof(float) * ((size_t)AsmSmem::SB + (size_t)G * EH_STRIDE + 6 * DPV_WMAX + 2 * G + 3 * G + 2 * G +
-                          AS_WARPS * 24) +
-         sizeof(int) * DPV_WMAX;
+  return sizeof(float) * ((size_t)DPV_RMAX * NV * 2 + (size_t)DPV_RMAX * 21 + (size_t)G * EH_STRIDE + 2 * G +
+                          3 * G + (size_t)AS_WARPS * 32 * ROWF) +
+         sizeof(int) * (DPV_RMAX + DPV_WMAX);
 }
 
-__device__ __forceinline__ int pair_a(int p) {
-  int a = (int)((sqrtf(8.0f * p + 1.0f) - 1.0f) * 0.5f);
-  while (tri(a + 1, 0) <= p) ++a;
-  while (tri(a, 0) > p) --a;
+__device__ __forceinline__ int tri_row(int t) {
+  int a = (int)((sqrtf(8.0f * t + 1.0f) - 1.0f) * 0.5f);
+  while (tri(a + 1, 0) <= t) ++a;
+  while (tri(a, 0) > t) --a;
   return a;
 }
 
 __global__ void __launch_bounds__(AS_THREADS) k_assemble(
     int G, int P, int fixed, int TS, float lambda_d, float z_min, const int* __restrict__ gseg,
     const int* __restrict__ runptr, const unsigned* __restrict__ eslot, const int* __restrict__ perm,
-    const int* __restrict__ win, const int* __restrict__ wlen, const double* __restrict__ poses,
-    const float* __restrict__ patches, const float* __restrict__ targets, const float* __restrict__ weights,
-    const float* __restrict__ intr, float* __restrict__ S, float* __restrict__ y, float* __restrict__ Ct_out,
+    const int* __restrict__ pmpos, const int* __restrict__ pptr, const int* __restrict__ win,
+    const int* __restrict__ wlen, const float* __restrict__ posef, const float* __restrict__ patches,
+    const float* __restrict__ targets, const float* __restrict__ weights, const float* __restrict__ intr,
+    float4* __restrict__ pterm, double* __restrict__ S, double* __restrict__ y, float* __restrict__ Ct_out,
     float* __restrict__ wk_out, double* __restrict__ cost, int* status) {
   extern __shared__ float sm[];
   if (dpv_status(status)) return;
@@ -62,26 +73,23 @@ __global__ void __launch_bounds__(AS_THREADS) k_assemble(
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int w = wlen[g];
   const int nr = 6 * w;
-  const int nsb = tri(nr, 0);
+  const int rb = gseg[g], nruns = gseg[g + 1] - rb;
 
-  float* SB = sm;                              // packed lower of the window's B
-  float* Eh = SB + AsmSmem::SB;                // [G][EH_STRIDE]
-  float* yl = Eh + (size_t)G * EH_STRIDE;      // [6W]
-  float* Cw = yl + 6 * DPV_WMAX;               // [G][2] C_k, w_k
-  float* pd = Cw + 2 * G;                      // [G][3] xb0, xb1, d
-  float* sc = pd + 3 * G;                      // [G][2] Ct^-1/2, w Ct^-1/2
-  float* rp = sc + 2 * G;                      // [warps][24] relative pose of the warp's run
-  int* wf = (int*)(rp + AS_WARPS * 24);        // [W] window frames
+  float2* runv = reinterpret_cast<float2*>(sm);            // [RMAX][NV] (hi, lo)
+  float* rpose = sm + DPV_RMAX * NV * 2;                    // [RMAX][21]
+  float* Eh = rpose + DPV_RMAX * 21;                        // [G][EH_STRIDE]
+  float* sc = Eh + (size_t)G * EH_STRIDE;                   // [G][2]  Ct^-1/2, w Ct^-1/2
+  float* pd = sc + 2 * G;                                   // [G][3]  xb0, xb1, d
+  float* rows = pd + 3 * G;                                 // [warps][32][ROWF]
+  int* rsl = reinterpret_cast<int*>(rows + AS_WARPS * 32 * ROWF);  // [RMAX] si | sj << 8
+  int* wf = rsl + DPV_RMAX;                                 // [W] window frames
 
   float K[4];
 #pragma unroll
   for (int q = 0; q < 4; ++q) K[q] = intr[q];
 
-  // ---- phase 0: clear accumulators, stage window and patch centres -------
-  for (int q = tid; q < nsb; q += AS_THREADS) SB[q] = 0.f;
+  // ---- phase 0 ------------------------------------------------------------
   for (int q = tid; q < G * EH_STRIDE; q += AS_THREADS) Eh[q] = 0.f;
-  for (int q = tid; q < 6 * DPV_WMAX; q += AS_THREADS) yl[q] = 0.f;
-  for (int q = tid; q < 2 * G; q += AS_THREADS) Cw[q] = 0.f;
   for (int q = tid; q < w; q += AS_THREADS) wf[q] = win[g * DPV_WMAX + q];
   for (int q = tid; q < G; q += AS_THREADS) {
     const int k = g * G + q;
@@ -97,240 +105,279 @@ __global__ void __launch_bounds__(AS_THREADS) k_assemble(
     pd[3 * q + 2] = d;
   }
   __syncthreads();
-
-  // ---- phase 1: one warp per (source, target) run -------------------------
-  float cst = 0.f;
-  const int r0 = gseg[g], r1 = gseg[g + 1];
-  for (int r = r0 + wid; r < r1; r += AS_WARPS) {
-    const int s0 = runptr[r], s1 = runptr[r + 1];
-    const unsigned sw0 = eslot[s0];
-    const int si = dpv_slot_i(sw0), sj = dpv_slot_j(sw0);
-    if (si == sj) continue;  // self edges are masked (warp-uniform)
-    float* rpw = rp + wid * 24;
-    if (lane == 0) {
-      RelPose T;
-      dpv_relative_pose(poses + 7 * (size_t)wf[si], poses + 7 * (size_t)wf[sj], T);
-#pragma unroll
-      for (int m = 0; m < 9; ++m) rpw[m] = T.R[m];
-#pragma unroll
-      for (int m = 0; m < 3; ++m) rpw[9 + m] = T.t[m];
-#pragma unroll
-      for (int m = 0; m < 9; ++m) rpw[12 + m] = T.txR[m];
-    }
-    __syncwarp();
+  for (int r = tid; r < nruns; r += AS_THREADS) {
+    const unsigned sw = eslot[runptr[rb + r]];
+    const int si = dpv_slot_i(sw), sj = dpv_slot_j(sw);
+    rsl[r] = si | (sj << 8);
     RelPose T;
+    dpv_relative_pose_f(posef + 16 * (size_t)wf[si], posef + 16 * (size_t)wf[sj], T);
+    float* o = rpose + 21 * r;
 #pragma unroll
-    for (int m = 0; m < 9; ++m) T.R[m] = rpw[m];
+    for (int m = 0; m < 9; ++m) o[m] = T.R[m];
 #pragma unroll
-    for (int m = 0; m < 3; ++m) T.t[m] = rpw[9 + m];
+    for (int m = 0; m < 3; ++m) o[9 + m] = T.t[m];
 #pragma unroll
-    for (int m = 0; m < 9; ++m) T.txR[m] = rpw[12 + m];
-    __syncwarp();
+    for (int m = 0; m < 9; ++m) o[12 + m] = T.txR[m];
+  }
+  __syncthreads();
 
-    float acc[NV];
+  // ---- phase 1: one warp per run ------------------------------------------
+  float cst = 0.f;
+  float* rw = rows + wid * 32 * ROWF;
+  for (int r = wid; r < nruns; r += AS_WARPS) {
+    const int s0 = runptr[rb + r], s1 = runptr[rb + r + 1];
+    const int si = rsl[r] & 0xff, sj = rsl[r] >> 8;
+    const bool self_run = si == sj;  // masked edges: they contribute nothing
+    RelPose T;
+    {
+      const float* o = rpose + 21 * r;
 #pragma unroll
-    for (int q = 0; q < NV; ++q) acc[q] = 0.f;
-    for (int s = s0 + lane; s < s1; s += 32) {
-      const int kl = dpv_slot_k(eslot[s]);
-      const int e = perm[s];
-      const float2 tg = *reinterpret_cast<const float2*>(targets + 2 * (size_t)e);
-      const float2 wt = *reinterpret_cast<const float2*>(weights + 2 * (size_t)e);
-      EdgeLin L;
-      dpv_edge_linearize(T, pd[3 * kl], pd[3 * kl + 1], pd[3 * kl + 2], tg.x, tg.y, K, z_min, false, L);
-      if (!L.valid) continue;
-      const float wc[2] = {wt.x, wt.y};
-      cst += wc[0] * L.r[0] * L.r[0] + wc[1] * L.r[1] * L.r[1];
-      // per-patch depth terms
-      const float wJd0 = wc[0] * L.Jd[0], wJd1 = wc[1] * L.Jd[1];
-      atomicAdd(&Cw[2 * kl], wJd0 * L.Jd[0] + wJd1 * L.Jd[1]);
-      atomicAdd(&Cw[2 * kl + 1], wJd0 * L.r[0] + wJd1 * L.r[1]);
-      float* ek = Eh + (size_t)kl * EH_STRIDE;
+      for (int m = 0; m < 9; ++m) T.R[m] = o[m];
 #pragma unroll
-      for (int m = 0; m < 6; ++m) {
-        atomicAdd(&ek[6 * si + m], L.Ji[0][m] * wJd0 + L.Ji[1][m] * wJd1);
-        atomicAdd(&ek[6 * sj + m], L.Jj[0][m] * wJd0 + L.Jj[1][m] * wJd1);
-      }
-      // run blocks: Hii (lower), Hij, Hjj (lower), vi, vj
+      for (int m = 0; m < 3; ++m) T.t[m] = o[9 + m];
 #pragma unroll
-      for (int c = 0; c < 2; ++c) {
-        float wi[6], wj[6];
-#pragma unroll
-        for (int m = 0; m < 6; ++m) {
-          wi[m] = wc[c] * L.Ji[c][m];
-          wj[m] = wc[c] * L.Jj[c][m];
-        }
-        int q = 0;
-#pragma unroll
-        for (int a = 0; a < 6; ++a)
-#pragma unroll
-          for (int b = 0; b <= a; ++b) acc[q++] += wi[a] * L.Ji[c][b];
-#pragma unroll
-        for (int a = 0; a < 6; ++a)
-#pragma unroll
-          for (int b = 0; b < 6; ++b) acc[q++] += wi[a] * L.Jj[c][b];
-#pragma unroll
-        for (int a = 0; a < 6; ++a)
-#pragma unroll
-          for (int b = 0; b <= a; ++b) acc[q++] += wj[a] * L.Jj[c][b];
-#pragma unroll
-        for (int a = 0; a < 6; ++a) acc[q++] += wi[a] * L.r[c];
-#pragma unroll
-        for (int a = 0; a < 6; ++a) acc[q++] += wj[a] * L.r[c];
-      }
+      for (int m = 0; m < 9; ++m) T.txR[m] = o[12 + m];
     }
-    // warp reduction of the run accumulators, then scatter into the window
+    DF acc[3];
 #pragma unroll
-    for (int q = 0; q < NV; ++q) {
-      float v = acc[q];
+    for (int t = 0; t < 3; ++t) acc[t] = DF{0.f, 0.f};
+    for (int b = s0; b < s1; b += 32) {
+      const int s = b + lane;
+      const int nb = min(32, s1 - b);
+      float* row = rw + lane * ROWF;
+      if (s < s1) {
+        const int kl = dpv_slot_k(eslot[s]);
+        const int e = perm[s];
+        const float2 tg = *reinterpret_cast<const float2*>(targets + 2 * (size_t)e);
+        const float2 wt = *reinterpret_cast<const float2*>(weights + 2 * (size_t)e);
+        EdgeLin L;
+        dpv_edge_linearize(T, pd[3 * kl], pd[3 * kl + 1], pd[3 * kl + 2], tg.x, tg.y, K, z_min, self_run, L);
+        float Ei[6], Ej[6], Ce = 0.f, we = 0.f;
+        if (L.valid) {
+          const float wc[2] = {wt.x, wt.y};
+          cst += wc[0] * L.r[0] * L.r[0] + wc[1] * L.r[1] * L.r[1];
+          const float wJd0 = wc[0] * L.Jd[0], wJd1 = wc[1] * L.Jd[1];
+          Ce = wJd0 * L.Jd[0] + wJd1 * L.Jd[1];
+          we = wJd0 * L.r[0] + wJd1 * L.r[1];
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-      acc[q] = v;
-    }
-    const int bi = 6 * si, bj = 6 * sj;
-    int q = 0;
+          for (int m = 0; m < 6; ++m) {
+            Ei[m] = L.Ji[0][m] * wJd0 + L.Ji[1][m] * wJd1;
+            Ej[m] = L.Jj[0][m] * wJd0 + L.Jj[1][m] * wJd1;
+          }
 #pragma unroll
-    for (int a = 0; a < 6; ++a)
+          for (int c = 0; c < 2; ++c) {
+            const float sw = sqrtf(wc[c]);
 #pragma unroll
-      for (int b = 0; b <= a; ++b, ++q)
-        if ((q & 31) == lane) atomicAdd(&SB[tri(bi + a, bi + b)], acc[q]);
+            for (int m = 0; m < 6; ++m) {
+              row[13 * c + m] = sw * L.Ji[c][m];
+              row[13 * c + 6 + m] = sw * L.Jj[c][m];
+            }
+            row[13 * c + 12] = sw * L.r[c];
+          }
+        } else {
 #pragma unroll
-    for (int a = 0; a < 6; ++a)
+          for (int m = 0; m < 6; ++m) Ei[m] = Ej[m] = 0.f;
 #pragma unroll
-      for (int b = 0; b < 6; ++b, ++q)
-        if ((q & 31) == lane) {
-          const int R = bi + a, C = bj + b;
-          atomicAdd(&SB[R >= C ? tri(R, C) : tri(C, R)], acc[q]);
+          for (int m = 0; m < 26; ++m) row[m] = 0.f;
         }
+        float4* pt = pterm + 4 * (size_t)pmpos[s];
+        pt[0] = make_float4(Ei[0], Ei[1], Ei[2], Ei[3]);
+        pt[1] = make_float4(Ei[4], Ei[5], Ej[0], Ej[1]);
+        pt[2] = make_float4(Ej[2], Ej[3], Ej[4], Ej[5]);
+        pt[3] = make_float4(Ce, we, __int_as_float(si | (sj << 8)), 0.f);
+      }
+      __syncwarp();
+      for (int e = 0; e < nb; ++e) {
+        const float* re = rw + e * ROWF;
 #pragma unroll
-    for (int a = 0; a < 6; ++a)
+        for (int t = 0; t < 3; ++t) {
+          const int q = lane + 32 * t;
+          if (q < NV) {
+            const int pa = c_pa[q], pb = c_pb[q];
+            df_fma(acc[t], re[pa], re[pb]);
+            df_fma(acc[t], re[13 + pa], re[13 + pb]);
+          }
+        }
+      }
+      __syncwarp();
+    }
 #pragma unroll
-      for (int b = 0; b <= a; ++b, ++q)
-        if ((q & 31) == lane) atomicAdd(&SB[tri(bj + a, bj + b)], acc[q]);
-#pragma unroll
-    for (int a = 0; a < 6; ++a, ++q)
-      if ((q & 31) == lane) atomicAdd(&yl[bi + a], acc[q]);
-#pragma unroll
-    for (int a = 0; a < 6; ++a, ++q)
-      if ((q & 31) == lane) atomicAdd(&yl[bj + a], acc[q]);
+    for (int t = 0; t < 3; ++t) {
+      const int q = lane + 32 * t;
+      if (q < NV) runv[r * NV + q] = make_float2(acc[t].hi, acc[t].lo);
+    }
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) cst += __shfl_xor_sync(0xffffffffu, cst, o);
   if (lane == 0 && cst != 0.f) atomicAdd(cost, (double)cst);
   __syncthreads();
 
-  // ---- phase 2: per patch Ct = C + lambda_d, scale E_hat columns ----------
+  // ---- phase 2: per patch e_k, C_k, w_k (compensated) ---------------------
   for (int q = tid; q < G; q += AS_THREADS) {
     const int k = g * G + q;
-    const float ct = Cw[2 * q] + lambda_d;
+    float* col = Eh + (size_t)q * EH_STRIDE;
+    DF ei[6], C = {lambda_d, 0.f}, wv = {0.f, 0.f};
+#pragma unroll
+    for (int m = 0; m < 6; ++m) ei[m] = DF{0.f, 0.f};
+    int si = 0;
+    if (k < P) {
+      for (int p = pptr[k]; p < pptr[k + 1]; ++p) {
+        const float4 a = pterm[4 * (size_t)p], b = pterm[4 * (size_t)p + 1], c = pterm[4 * (size_t)p + 2],
+                     d = pterm[4 * (size_t)p + 3];
+        const int sl = __float_as_int(d.z);
+        si = sl & 0xff;
+        const int sj = sl >> 8;
+        df_add(ei[0], a.x); df_add(ei[1], a.y); df_add(ei[2], a.z);
+        df_add(ei[3], a.w); df_add(ei[4], b.x); df_add(ei[5], b.y);
+        col[6 * sj + 0] += b.z; col[6 * sj + 1] += b.w; col[6 * sj + 2] += c.x;
+        col[6 * sj + 3] += c.y; col[6 * sj + 4] += c.z; col[6 * sj + 5] += c.w;
+        df_add(C, d.x);
+        df_add(wv, d.y);
+      }
+    }
+    const float ct = df_val(C), wf_ = df_val(wv);
+#pragma unroll
+    for (int m = 0; m < 6; ++m) col[6 * si + m] += df_val(ei[m]);
     const float s = 1.0f / sqrtf(ct);
     sc[2 * q] = s;
-    sc[2 * q + 1] = Cw[2 * q + 1] * s;
+    sc[2 * q + 1] = wf_ * s;
+    for (int m = 0; m < nr; ++m) col[m] *= s;
     if (k < P) {
       Ct_out[k] = ct;
-      wk_out[k] = Cw[2 * q + 1];
+      wk_out[k] = wf_;
     }
   }
   __syncthreads();
-  for (int q = tid; q < G * nr; q += AS_THREADS) {
-    const int kl = q / nr, row = q - kl * nr;
-    Eh[(size_t)kl * EH_STRIDE + row] *= sc[2 * kl];
-  }
-  __syncthreads();
 
-  // ---- phase 3: window Schur complement, scattered into the global S ------
-  const int npair_all = w * (w + 1) / 2;
-  for (int p = tid; p < npair_all; p += AS_THREADS) {
-    const int a = pair_a(p), b = p - tri(a, 0);
+  // ---- phase 3: window Schur complement into the global S and y -----------
+  const int nent = tri(nr, 0);
+  for (int t = tid; t < nent; t += AS_THREADS) {
+    const int R = tri_row(t), C = t - tri(R, 0);
+    const int a = R / 6, b = C / 6, ra = R - 6 * a, cb = C - 6 * b;
     const int fa = wf[a], fb = wf[b];
     if (fa < fixed || fb < fixed) continue;
-    float acc[36];
-#pragma unroll
-    for (int q = 0; q < 36; ++q) acc[q] = 0.f;
-    for (int kl = 0; kl < G; ++kl) {
-      const float* ek = Eh + (size_t)kl * EH_STRIDE;
-      float ea[6], eb[6];
-#pragma unroll
-      for (int m = 0; m < 6; ++m) {
-        ea[m] = ek[6 * a + m];
-        eb[m] = ek[6 * b + m];
+    DF acc = {0.f, 0.f};
+    for (int r = 0; r < nruns; ++r) {
+      const int si = rsl[r] & 0xff, sj = rsl[r] >> 8;
+      if (si == sj) continue;
+      const float2* rv = runv + r * NV;
+      if (a == b) {
+        if (si == a) df_add_df(acc, DF{rv[tri(ra, cb)].x, rv[tri(ra, cb)].y});
+        if (sj == a) df_add_df(acc, DF{rv[57 + tri(ra, cb)].x, rv[57 + tri(ra, cb)].y});
+      } else {
+        if (si == a && sj == b) df_add_df(acc, DF{rv[21 + 6 * ra + cb].x, rv[21 + 6 * ra + cb].y});
+        if (si == b && sj == a) df_add_df(acc, DF{rv[21 + 6 * cb + ra].x, rv[21 + 6 * cb + ra].y});
       }
-#pragma unroll
-      for (int r = 0; r < 6; ++r)
-#pragma unroll
-        for (int c = 0; c < 6; ++c) acc[6 * r + c] = fmaf(ea[r], eb[c], acc[6 * r + c]);
     }
-    const int gr = 6 * (fa - fixed), gc = 6 * (fb - fixed);
-#pragma unroll
-    for (int r = 0; r < 6; ++r)
-#pragma unroll
-      for (int c = 0; c < 6; ++c) {
-        if (a == b && c > r) continue;
-        const float v = SB[tri(6 * a + r, 6 * b + c)] - acc[6 * r + c];
-        dpv_red_add(S + dpv_s_index(gr + r, gc + c, TS), v);
-      }
+    for (int kl = 0; kl < G; ++kl) {
+      const float* col = Eh + (size_t)kl * EH_STRIDE;
+      df_fma(acc, -col[R], col[C]);
+    }
+    dpv_red_add(S + dpv_s_index(6 * (fa - fixed) + ra, 6 * (fb - fixed) + cb, TS), (double)acc.hi + (double)acc.lo);
   }
   for (int R = tid; R < nr; R += AS_THREADS) {
-    const int fa = wf[R / 6];
+    const int a = R / 6, ra = R - 6 * a;
+    const int fa = wf[a];
     if (fa < fixed) continue;
-    float v = yl[R];
-    for (int kl = 0; kl < G; ++kl) v = fmaf(-Eh[(size_t)kl * EH_STRIDE + R], sc[2 * kl + 1], v);
-    dpv_red_add(y + 6 * (fa - fixed) + (R % 6), v);
+    DF acc = {0.f, 0.f};
+    for (int r = 0; r < nruns; ++r) {
+      const int si = rsl[r] & 0xff, sj = rsl[r] >> 8;
+      if (si == sj) continue;
+      const float2* rv = runv + r * NV;
+      if (si == a) df_add_df(acc, DF{rv[78 + ra].x, rv[78 + ra].y});
+      if (sj == a) df_add_df(acc, DF{rv[84 + ra].x, rv[84 + ra].y});
+    }
+    for (int kl = 0; kl < G; ++kl) df_fma(acc, -Eh[(size_t)kl * EH_STRIDE + R], sc[2 * kl + 1]);
+    dpv_red_add(y + 6 * (fa - fixed) + ra, (double)acc.hi + (double)acc.lo);
   }
 }
 
-// S <- 0 with lambda_p on the free diagonal and 1 on the padding diagonal; y <- 0
-__global__ void k_init_system(float* __restrict__ S, size_t nS, float* __restrict__ y, int n, int n_pad, int TS,
-                              float lambda_p, const int* status) {
+// S <- 0 (lambda_p on the free diagonal, 1 on the padding diagonal), y <- 0,
+// and the per-pose table for this iteration: R (FP32) and the camera centre
+// c = -R^T t as a double-float pair, formed in FP64 from the FP64 pose.
+__global__ void k_init_system(double* __restrict__ S, size_t nS, double* __restrict__ y, int n_pad,
+                              const double* __restrict__ poses, int N, float* __restrict__ posef,
+                              const int* status) {
   if (dpv_status(status)) return;
   const size_t stride = (size_t)gridDim.x * blockDim.x;
-  const size_t n4 = nS / 4;
-  float4* S4 = reinterpret_cast<float4*>(S);
-  for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < n4; q += stride)
-    S4[q] = make_float4(0.f, 0.f, 0.f, 0.f);
-  for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < (size_t)n_pad; q += stride) y[q] = 0.f;
+  const size_t gid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid < (size_t)N) {
+    const double* p = poses + 7 * gid;
+    double R[9];
+    dpv_quat_rot64(p + 3, R);
+    float* o = posef + 16 * gid;
+#pragma unroll
+    for (int m = 0; m < 9; ++m) o[m] = (float)R[m];
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+      const double c = -(R[m] * p[0] + R[3 + m] * p[1] + R[6 + m] * p[2]);
+      const float hi = (float)c;
+      o[9 + m] = hi;
+      o[12 + m] = (float)(c - (double)hi);
+    }
+    o[15] = 0.f;
+  }
+  double2* S2 = reinterpret_cast<double2*>(S);
+  for (size_t q = gid; q < nS / 2; q += stride) S2[q] = make_double2(0.0, 0.0);
+  for (size_t q = gid; q < (size_t)n_pad; q += stride) y[q] = 0.0;
 }
 
-__global__ void k_init_diag(float* __restrict__ S, int n, int n_pad, int TS, float lambda_p, const int* status) {
+__global__ void k_init_diag(double* __restrict__ S, int n, int n_pad, int TS, float lambda_p, const int* status) {
   if (dpv_status(status)) return;
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r < n_pad) S[dpv_s_index(r, r, TS)] = r < n ? lambda_p : 1.0f;
+  if (r < n_pad) S[dpv_s_index(r, r, TS)] = r < n ? (double)lambda_p : 1.0;
 }
 
-__global__ void k_export_S(const float* __restrict__ S, int n, int TS, float* __restrict__ out) {
+__global__ void k_export_S(const double* __restrict__ S, int n, int TS, float* __restrict__ out) {
   const size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= (size_t)n * n) return;
   const int r = (int)(q / n), c = (int)(q % n);
-  out[q] = c <= r ? S[dpv_s_index(r, c, TS)] : 0.f;
+  out[q] = c <= r ? (float)S[dpv_s_index(r, c, TS)] : 0.f;
+}
+
+bool g_tables_ready = false;
+
+ba_status_t upload_tables(ba_handle_t h) {
+  if (g_tables_ready) return BA_OK;
+  unsigned char pa[NV], pb[NV];
+  int q = 0;
+  for (int a = 0; a < 6; ++a)
+    for (int b = 0; b <= a; ++b, ++q) { pa[q] = a; pb[q] = b; }          // Hii (lower)
+  for (int a = 0; a < 6; ++a)
+    for (int b = 0; b < 6; ++b, ++q) { pa[q] = a; pb[q] = 6 + b; }       // Hij
+  for (int a = 0; a < 6; ++a)
+    for (int b = 0; b <= a; ++b, ++q) { pa[q] = 6 + a; pb[q] = 6 + b; }  // Hjj (lower)
+  for (int a = 0; a < 6; ++a, ++q) { pa[q] = a; pb[q] = 12; }            // vi
+  for (int a = 0; a < 6; ++a, ++q) { pa[q] = 6 + a; pb[q] = 12; }        // vj
+  DPV_CUDA(h, cudaMemcpyToSymbol(c_pa, pa, NV));
+  DPV_CUDA(h, cudaMemcpyToSymbol(c_pb, pb, NV));
+  DPV_CUDA(h, cudaFuncSetAttribute(k_assemble, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)assemble_smem_bytes(DPV_GMAX)));
+  g_tables_ready = true;
+  return BA_OK;
 }
 
 }  // namespace
 
-size_t dpv_assemble_smem(int G) { return assemble_smem_bytes(G); }
-
 ba_status_t dpv_assemble(ba_handle_t h, int it) {
   Workspace* ws = h->ws;
+  ba_status_t s = upload_tables(h);
+  if (s) return s;
   const size_t nS = (size_t)h->T * (h->T + 1) / 2 * h->TS * h->TS;
   dpv_prof_begin(h, BA_KERNEL_INIT);
-  k_init_system<<<2 * h->num_sms, 256, 0, h->stream>>>(ws->S.p, nS, ws->y.p, h->n, h->n_pad, h->TS,
-                                                        h->opt.lambda_pose, ws->status);
+  k_init_system<<<2 * h->num_sms, 256, 0, h->stream>>>(ws->S.p, nS, ws->y.p, h->n_pad, h->poses, h->N,
+                                                        ws->posef.p, ws->status);
   ++h->launches;
   k_init_diag<<<(h->n_pad + 255) / 256, 256, 0, h->stream>>>(ws->S.p, h->n, h->n_pad, h->TS, h->opt.lambda_pose,
                                                               ws->status);
   ++h->launches;
   dpv_prof_end(h);
-  const size_t smem = assemble_smem_bytes(h->G);
-  static bool attr_set = false;
-  if (!attr_set) {
-    DPV_CUDA(h, cudaFuncSetAttribute(k_assemble, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)assemble_smem_bytes(DPV_GMAX)));
-    attr_set = true;
-  }
   double* cost = ws->cost + (it < ws->cost_cap ? it : ws->cost_cap - 1);
   dpv_prof_begin(h, BA_KERNEL_ASSEMBLE);
-  k_assemble<<<h->ngroups, AS_THREADS, smem, h->stream>>>(
-      h->G, h->P, h->fixed, h->TS, h->opt.lambda_depth, h->opt.z_min, ws->gseg.p, ws->runptr.p, ws->eslot.p, ws->perm.p,
-      ws->win.p, ws->wlen.p, h->poses, h->patches, h->targets, h->weights, ws->intr, ws->S.p, ws->y.p, ws->Ct.p, ws->wk.p,
-      cost, ws->status);
+  k_assemble<<<h->ngroups, AS_THREADS, assemble_smem_bytes(h->G), h->stream>>>(
+      h->G, h->P, h->fixed, h->TS, h->opt.lambda_depth, h->opt.z_min, ws->gseg.p, ws->runptr.p, ws->eslot.p,
+      ws->perm.p, ws->pmpos.p, ws->pptr.p, ws->win.p, ws->wlen.p, ws->posef.p, h->patches, h->targets, h->weights,
+      ws->intr, ws->pterm.p, ws->S.p, ws->y.p, ws->Ct.p, ws->wk.p, cost, ws->status);
   ++h->launches;
   dpv_prof_end(h);
   DPV_CUDA(h, cudaGetLastError());

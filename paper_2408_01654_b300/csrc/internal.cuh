@@ -14,6 +14,7 @@
 #define DPV_GMAX 64          // patches per group
 #define DPV_SMALL_N 256      // pose systems up to this size use the one-CTA solver
 #define DPV_TILE 64          // tile edge of the blocked pose system (large n)
+#define DPV_RMAX 64          // (source, target) runs in one group
 
 // device status codes (mirror ba_status_t)
 #define DST_OK 0
@@ -93,11 +94,15 @@ struct Workspace {
   DBuf<int> win;                  // [groups * DPV_WMAX] window frames
   DBuf<int> wlen;                 // [groups]
   DBuf<int> scan;                 // block sums of the scan
+  DBuf<int> pmpos;                // [E] sorted position -> patch-major position
+  DBuf<int> pptr;                 // [P+1] patch-major edge range of each patch
   // per iteration
-  DBuf<float> S;                  // tiled lower triangle of the pose system
-  DBuf<float> y;                  // [n_pad]
+  DBuf<double> S;                 // tiled lower triangle of the pose system (FP64 accumulation)
+  DBuf<double> y;                 // [n_pad]
   DBuf<double> dx;                // [n_pad]
   DBuf<float> Ct, wk, dd;         // [P]
+  DBuf<float> posef;              // [N][16] R (9), camera centre hi (3), lo (3)
+  DBuf<float4> pterm;             // [E][4] per-edge depth terms, patch-major (see assemble.cu)
   // blocked solver
   DBuf<float> L;                  // factor (large n)
   DBuf<double> r64;               // [n_pad]
@@ -128,7 +133,7 @@ long long dpv_scan_scratch(long long n);
 long long dpv_hist_entries(long long m);
 // one GN iteration (assemble.cu, solve_*.cu, update.cu)
 ba_status_t dpv_assemble(ba_handle_t h, int it);
-ba_status_t dpv_solve(ba_handle_t h);
+ba_status_t dpv_solve(ba_handle_t h, int* retracted);  // retracted: poses already updated
 ba_status_t dpv_backsub(ba_handle_t h);
 ba_status_t dpv_retract(ba_handle_t h);
 ba_status_t dpv_export_S(ba_handle_t h, float* dst);
@@ -151,6 +156,9 @@ __host__ __device__ __forceinline__ size_t dpv_s_index(int r, int c, int TS) {
 
 __device__ __forceinline__ void dpv_red_add(float* p, float v) {
   asm volatile("red.global.add.f32 [%0], %1;" ::"l"(p), "f"(v) : "memory");
+}
+__device__ __forceinline__ void dpv_red_add(double* p, double v) {
+  asm volatile("red.global.add.f64 [%0], %1;" ::"l"(p), "d"(v) : "memory");
 }
 
 // rotation matrix of a unit quaternion (x, y, z, w), FP64
@@ -231,6 +239,59 @@ __device__ __forceinline__ void dpv_edge_linearize(const RelPose& T, float xb0, 
   }
   o.Jd[0] = a0 * T.t[0] + a2 * T.t[2];
   o.Jd[1] = b1 * T.t[1] + b2 * T.t[2];
+}
+
+// ---------------------------------------------------------------------------
+// compensated FP32 accumulation ("double-float"): value = hi + lo.
+// TwoSum gives the exact rounding error of a sum; fma(a, b, -p) gives the
+// exact rounding error of a product, so acc += a*b keeps ~44 bits.
+// ---------------------------------------------------------------------------
+struct DF {
+  float hi, lo;
+};
+// The explicit _rn intrinsics keep the compiler from contracting a product
+// into the following sum, which would break the error terms.
+__device__ __forceinline__ void df_add(DF& a, float b) {
+  const float s = __fadd_rn(a.hi, b);
+  const float bb = __fsub_rn(s, a.hi);
+  const float err = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  a.hi = s;
+  a.lo = __fadd_rn(a.lo, err);
+}
+__device__ __forceinline__ void df_fma(DF& a, float x, float y) {
+  const float p = __fmul_rn(x, y);
+  const float pe = __fmaf_rn(x, y, -p);
+  df_add(a, p);
+  a.lo = __fadd_rn(a.lo, pe);
+}
+__device__ __forceinline__ void df_add_df(DF& a, const DF& b) {
+  df_add(a, b.hi);
+  a.lo = __fadd_rn(a.lo, b.lo);
+}
+__device__ __forceinline__ float df_val(const DF& a) { return a.hi + a.lo; }
+
+// per-pose FP32 data for the relative poses: rotation R (world->camera) and
+// camera centre c = -R^T t in double-float (hi, lo) so that c_i - c_j keeps
+// full FP32 relative accuracy even far from the origin.
+__device__ __forceinline__ void dpv_relative_pose_f(const float* Pi, const float* Pj, RelPose& o) {
+  // R = Rj Ri^T
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+      o.R[3 * r + c] = Pj[3 * r] * Pi[3 * c] + Pj[3 * r + 1] * Pi[3 * c + 1] + Pj[3 * r + 2] * Pi[3 * c + 2];
+  // t = t_j - R t_i = R_j (c_i - c_j)
+  float dc[3];
+#pragma unroll
+  for (int m = 0; m < 3; ++m) dc[m] = (Pi[9 + m] - Pj[9 + m]) + (Pi[12 + m] - Pj[12 + m]);
+#pragma unroll
+  for (int r = 0; r < 3; ++r) o.t[r] = Pj[3 * r] * dc[0] + Pj[3 * r + 1] * dc[1] + Pj[3 * r + 2] * dc[2];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    o.txR[0 + c] = -o.t[2] * o.R[3 + c] + o.t[1] * o.R[6 + c];
+    o.txR[3 + c] = o.t[2] * o.R[0 + c] - o.t[0] * o.R[6 + c];
+    o.txR[6 + c] = -o.t[1] * o.R[0 + c] + o.t[0] * o.R[3 + c];
+  }
 }
 
 // packed per-edge slot word

@@ -239,12 +239,14 @@ __global__ void k_runs(int E, int ngroups, const int* __restrict__ runflag, cons
 // ---------------------------------------------------------------------------
 // group windows: sorted unique frames of each group's edges, and edge slots
 // ---------------------------------------------------------------------------
-__global__ void k_windows(int N, int G, const int* __restrict__ gptr, const int* __restrict__ perm,
-                          const int* __restrict__ ii, const int* __restrict__ jj, const int* __restrict__ kk,
-                          int* __restrict__ win, int* __restrict__ wlen, unsigned* __restrict__ eslot,
+__global__ void k_windows(int N, int P, int E, int G, const int* __restrict__ gptr, const int* __restrict__ gseg,
+                          const int* __restrict__ perm, const int* __restrict__ ii, const int* __restrict__ jj,
+                          const int* __restrict__ kk, int* __restrict__ win, int* __restrict__ wlen,
+                          unsigned* __restrict__ eslot, int* __restrict__ pmpos, int* __restrict__ pptr,
                           int* status) {
   extern __shared__ unsigned smw[];
   __shared__ int sh[32];
+  __shared__ int poff[DPV_GMAX + 1];
   const int nwords = (N + 31) >> 5;
   unsigned* bm = smw;
   int* wpre = (int*)(smw + nwords);
@@ -271,7 +273,7 @@ __global__ void k_windows(int N, int G, const int* __restrict__ gptr, const int*
     run += __popc(bm[q]);
   }
   __syncthreads();
-  if (total > DPV_WMAX) {
+  if (total > DPV_WMAX || gseg[g + 1] - gseg[g] > DPV_RMAX) {
     if (threadIdx.x == 0) {
       wlen[g] = total;
       dpv_set_status(status, DST_WIDE);
@@ -295,6 +297,41 @@ __global__ void k_windows(int N, int G, const int* __restrict__ gptr, const int*
     const int si = wpre[i >> 5] + __popc(bm[i >> 5] & ((1u << (i & 31)) - 1u));
     const int sj = wpre[j >> 5] + __popc(bm[j >> 5] & ((1u << (j & 31)) - 1u));
     eslot[s] = dpv_pack_slot(si, sj, kk[e] % G);
+  }
+  // patch-major order inside the group: a stable counting sort by patch, so
+  // each patch's edges keep their (ii, jj) order; pptr is the global CSR
+  for (int q = threadIdx.x; q <= G; q += blockDim.x) poff[q] = 0;
+  __syncthreads();
+  for (int s = s0 + threadIdx.x; s < s1; s += blockDim.x) atomicAdd(&poff[kk[perm[s]] % G], 1);
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    if (lane == 0) {
+      int run = 0;
+      for (int q = 0; q < G; ++q) {
+        const int c = poff[q];
+        poff[q] = run;
+        run += c;
+      }
+    }
+    __syncwarp();
+    for (int q = lane; q < G; q += 32)
+      if (g * G + q < P) pptr[g * G + q] = s0 + poff[q];
+    if (lane == 0 && (g + 1) * G >= P) pptr[P] = E;
+    __syncwarp();
+    const unsigned lt = (1u << lane) - 1u;
+    for (int b = s0; b < s1; b += 32) {
+      const int s = b + lane;
+      const bool valid = s < s1;
+      const int kl = valid ? kk[perm[s]] % G : DPV_GMAX;
+      const unsigned peers = __match_any_sync(0xffffffffu, kl);
+      const int base = valid ? poff[kl] : 0;
+      const int rank = __popc(peers & lt);
+      if (valid) pmpos[s] = s0 + base + rank;
+      __syncwarp();
+      if (valid && rank == 0) poff[kl] = base + __popc(peers);
+      __syncwarp();
+    }
   }
 }
 
@@ -418,8 +455,8 @@ ba_status_t dpv_preprocess(ba_handle_t h, const int* ii, const int* jj, const in
   const size_t smem = sizeof(unsigned) * nwords + sizeof(int) * nwords;
   if (smem > 200 * 1024) return dpv_fail(h, BA_ERR_UNSUPPORTED, "too many frames for the window kernel");
   DPV_CUDA(h, cudaFuncSetAttribute(k_windows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  k_windows<<<h->ngroups, 256, smem, st>>>(N, G, ws->gptr.p, ws->perm.p, ii, jj, kk, ws->win.p, ws->wlen.p, ws->eslot.p,
-                                           ws->status);
+  k_windows<<<h->ngroups, 256, smem, st>>>(N, P, E, G, ws->gptr.p, ws->gseg.p, ws->perm.p, ii, jj, kk, ws->win.p,
+                                           ws->wlen.p, ws->eslot.p, ws->pmpos.p, ws->pptr.p, ws->status);
   ++h->launches;
   DPV_CUDA(h, cudaGetLastError());
   return BA_OK;

@@ -1,150 +1,206 @@
 // Dense solve of the reduced pose system S dxi = y for n <= DPV_SMALL_N in
 // one CTA (the Cholesky of the pose block of the Schur complement, appendix
-// "Bundle-Adjustment Efficiency").
+// "Bundle-Adjustment Efficiency"), followed by the SE(3) retraction of the
+// free poses.
 //
-// S (n_pad x n_pad, one tile, lower triangle) is factored as S = L D L^T by
-// right-looking elimination without square roots: after step k, column k+1
-// of the trailing matrix is final.  A 32x32 thread grid owns the entries
-// (ty + 32a, tx + 32b) in registers; each step reads column k from a
-// double-buffered shared vector, updates the owned trailing entries and
-// publishes column k+1, so there is one __syncthreads per column.  D > 0 at
-// every pivot is exactly S being positive definite (the Cholesky factor is
-// L D^1/2).  The two triangular solves run in one warp.  In BA_MIXED mode the
-// solution is refined: rho = y - S x in FP64 from the unfactored S, solved
-// with the same factor, x += delta.
+// S and y arrive in FP64 (the assembly accumulates them so).  S is rounded to
+// FP32 into shared memory as a packed lower triangle and factored as
+// S = L D L^T (the Cholesky factor is L D^1/2; a pivot D_c <= 0 means S is
+// not positive definite) by blocked right-looking elimination with 8-column
+// panels:
+//   * warp 0 holds the panel in registers (rows lane + 32q) and eliminates its
+//     8 columns with shuffles only, then stores it with the scaled copy
+//     W = panel D^-1;
+//   * all 16 warps apply the rank-8 update A -= panel W^T to the trailing
+//     triangle -- two block barriers per panel.
+// The triangular solves run in 32-row blocks: warp 0 keeps the block's 32x32
+// triangle in registers and solves it with shuffles, all warps update the
+// rest of the right-hand side.  In BA_MIXED mode the solution is refined:
+// rho = y - S x in FP64 from the FP64 S in global memory, solved with the same
+// factor, x += delta.
 #include "internal.cuh"
+
+#include "retract.cuh"
 
 namespace {
 
+constexpr int SS_THREADS = 512;
+constexpr int SS_WARPS = SS_THREADS / 32;
+constexpr int PW = 8;  // panel width
+
 __host__ __device__ constexpr int tri(int r, int c) { return r * (r + 1) / 2 + c; }
 
-template <int NB>
-__global__ void __launch_bounds__(1024) k_solve_small(int n, const float* __restrict__ S, const float* __restrict__ y,
-                                                      double* __restrict__ dx, int refine, int* status) {
-  constexpr int NP = NB * 32;
-  __shared__ float col[2][NP];
-  __shared__ float Dsh[NP];
-  __shared__ double xs[NP];
+template <int NQ>  // NP = 32 NQ
+__global__ void __launch_bounds__(SS_THREADS) k_solve_small(int n, const double* __restrict__ S,
+                                                            const double* __restrict__ y, double* __restrict__ dx,
+                                                            float* __restrict__ dxf, int refine, int N, int fixed,
+                                                            double* __restrict__ poses, int* status) {
+  constexpr int NP = 32 * NQ;
+  extern __shared__ float A[];              // packed lower, tri(NP, 0) floats
+  __shared__ float W[PW][NP];               // scaled panel
+  __shared__ float invD[NP];
   __shared__ float rhs[NP];
-  extern __shared__ float Lsh[];  // packed strictly-lower L (unit), tri(i, j) for i > j
+  __shared__ double xs[NP];
+  __shared__ int bad;
   if (dpv_status(status)) return;
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-  float A[NB][NB];
-#pragma unroll
-  for (int a = 0; a < NB; ++a)
-#pragma unroll
-    for (int b = 0; b < NB; ++b) {
-      const int i = ty + 32 * a, j = tx + 32 * b;
-      A[a][b] = (i >= j) ? S[(size_t)i * NP + j] : 0.f;
-    }
-  if (tx == 0) {
-#pragma unroll
-    for (int a = 0; a < NB; ++a) col[0][ty + 32 * a] = A[a][0];
-  }
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  for (int i = wid; i < NP; i += SS_WARPS)
+    for (int j = lane; j <= i; j += 32) A[tri(i, j)] = (float)S[(size_t)i * NP + j];
+  if (tid == 0) bad = 0;
   __syncthreads();
-  bool bad = false;
-  for (int k = 0; k < NP; ++k) {
-    const float* ck = col[k & 1];
-    const float akk = ck[k];
-    if (!(akk > 0.f)) {  // same value in every thread: uniform exit
-      bad = true;
-      break;
-    }
-    const float inv = 1.0f / akk;
-    float ci[NB], cj[NB];
+
+  for (int p0 = 0; p0 < NP; p0 += PW) {
+    if (wid == 0) {
+      // panel rows i = p0 + lane + 32 q, columns p0 .. p0+7, in registers
+      float pr[NQ][PW];
 #pragma unroll
-    for (int a = 0; a < NB; ++a) ci[a] = ck[ty + 32 * a];
+      for (int q = 0; q < NQ; ++q) {
+        const int i = p0 + lane + 32 * q;
 #pragma unroll
-    for (int b = 0; b < NB; ++b) cj[b] = ck[tx + 32 * b] * inv;
-#pragma unroll
-    for (int a = 0; a < NB; ++a)
-#pragma unroll
-      for (int b = 0; b < NB; ++b) {
-        const int i = ty + 32 * a, j = tx + 32 * b;
-        if (j > k && i >= j) A[a][b] = fmaf(-ci[a], cj[b], A[a][b]);
+        for (int c = 0; c < PW; ++c) pr[q][c] = (i < NP && i >= p0 + c) ? A[tri(i, p0 + c)] : 0.f;
       }
-    const int kn = k + 1;
-    if (kn < NP && tx == (kn & 31)) {
+      bool ok = true;
 #pragma unroll
-      for (int b = 0; b < NB; ++b)
-        if (b == (kn >> 5)) {
+      for (int c = 0; c < PW; ++c) {
+        const float dc = __shfl_sync(0xffffffffu, pr[0][c], c);
+        ok = ok && (dc > 0.f);
+        const float inv = 1.0f / dc;
+        if (lane == 0) invD[p0 + c] = inv;
+        float ajc[PW];
 #pragma unroll
-          for (int a = 0; a < NB; ++a) col[kn & 1][ty + 32 * a] = A[a][b];
+        for (int j = c + 1; j < PW; ++j) ajc[j] = __shfl_sync(0xffffffffu, pr[0][c], j);
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+          const int i = p0 + lane + 32 * q;
+          const float aic = pr[q][c] * inv;
+#pragma unroll
+          for (int j = c + 1; j < PW; ++j)
+            if (i >= p0 + j) pr[q][j] = fmaf(-aic, ajc[j], pr[q][j]);
         }
+      }
+      if (!ok && lane == 0) bad = 1;
+      __syncwarp();
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) {
+        const int i = p0 + lane + 32 * q;
+        if (i < NP) {
+#pragma unroll
+          for (int c = 0; c < PW; ++c) {
+            if (i >= p0 + c) A[tri(i, p0 + c)] = pr[q][c];
+            W[c][i] = pr[q][c] * invD[p0 + c];
+          }
+        }
+      }
+    }
+    __syncthreads();
+    if (bad) break;
+    // rank-PW update of the trailing triangle: A[i][j] -= sum_c A[i][p0+c] W[c][j]
+    const int p1 = p0 + PW;
+    for (int i = p1 + wid; i < NP; i += SS_WARPS) {
+      float ai[PW];
+#pragma unroll
+      for (int c = 0; c < PW; ++c) ai[c] = A[tri(i, p0 + c)];
+      for (int j = p1 + lane; j <= i; j += 32) {
+        float s = A[tri(i, j)];
+#pragma unroll
+        for (int c = 0; c < PW; ++c) s = fmaf(-ai[c], W[c][j], s);
+        A[tri(i, j)] = s;
+      }
     }
     __syncthreads();
   }
   if (bad) {
-    if (threadIdx.x == 0) dpv_set_status(status, DST_NOT_SPD);
+    if (tid == 0) dpv_set_status(status, DST_NOT_SPD);
     return;
   }
-  // pivots, then unit-lower L = A / D
-#pragma unroll
-  for (int a = 0; a < NB; ++a)
-#pragma unroll
-    for (int b = 0; b < NB; ++b)
-      if (ty + 32 * a == tx + 32 * b) Dsh[ty + 32 * a] = A[a][b];
-  for (int q = threadIdx.x; q < NP; q += blockDim.x) xs[q] = 0.0;
-  __syncthreads();
-#pragma unroll
-  for (int a = 0; a < NB; ++a)
-#pragma unroll
-    for (int b = 0; b < NB; ++b) {
-      const int i = ty + 32 * a, j = tx + 32 * b;
-      if (i > j) Lsh[tri(i, j)] = A[a][b] / Dsh[j];
-    }
-  for (int q = threadIdx.x; q < NP; q += blockDim.x) rhs[q] = q < n ? y[q] : 0.f;
+  // unit lower factor L = A D^-1 (strict lower part, in place)
+  for (int i = wid; i < NP; i += SS_WARPS)
+    for (int j = lane; j < i; j += 32) A[tri(i, j)] *= invD[j];
+  for (int q = tid; q < NP; q += SS_THREADS) {
+    rhs[q] = q < n ? (float)y[q] : 0.f;
+    xs[q] = 0.0;
+  }
   __syncthreads();
 
   for (int sweep = 0; sweep <= refine; ++sweep) {
-    if (ty == 0) {
-      // forward: L u = rhs (unit lower), column oriented
-      for (int j = 0; j < NP; ++j) {
-        const float uj = rhs[j];
-        __syncwarp();
-        for (int i = j + 1 + tx; i < NP; i += 32) rhs[i] = fmaf(-Lsh[tri(i, j)], uj, rhs[i]);
-        __syncwarp();
+    // forward: L u = rhs
+    for (int r0 = 0; r0 < NP; r0 += 32) {
+      if (wid == 0) {
+        float Lrow[32];  // row r0+lane of the diagonal block
+#pragma unroll
+        for (int c = 0; c < 32; ++c) Lrow[c] = c < lane ? A[tri(r0 + lane, r0 + c)] : 0.f;
+        float v = rhs[r0 + lane];
+#pragma unroll
+        for (int c = 0; c < 32; ++c) v = fmaf(-Lrow[c], __shfl_sync(0xffffffffu, v, c), v);
+        rhs[r0 + lane] = v;
       }
-      for (int j = tx; j < NP; j += 32) rhs[j] /= Dsh[j];
-      __syncwarp();
-      // backward: L^T x = v, row oriented (row i of L is contiguous)
-      for (int i = NP - 1; i >= 0; --i) {
-        const float xi = rhs[i];
-        __syncwarp();
-        for (int j = tx; j < i; j += 32) rhs[j] = fmaf(-Lsh[tri(i, j)], xi, rhs[j]);
-        __syncwarp();
+      __syncthreads();
+      for (int i = r0 + 32 + tid; i < NP; i += SS_THREADS) {
+        float v = rhs[i];
+        const float* li = A + tri(i, r0);
+#pragma unroll 8
+        for (int c = 0; c < 32; ++c) v = fmaf(-li[c], rhs[r0 + c], v);
+        rhs[i] = v;
       }
-      for (int j = tx; j < NP; j += 32) xs[j] += (double)rhs[j];
+      __syncthreads();
     }
+    for (int q = tid; q < NP; q += SS_THREADS) rhs[q] *= invD[q];
+    __syncthreads();
+    // backward: L^T x = v
+    for (int r0 = NP - 32; r0 >= 0; r0 -= 32) {
+      if (wid == 0) {
+        float Lcol[32];  // column r0+lane of the diagonal block
+#pragma unroll
+        for (int r = 0; r < 32; ++r) Lcol[r] = r > lane ? A[tri(r0 + r, r0 + lane)] : 0.f;
+        float v = rhs[r0 + lane];
+#pragma unroll
+        for (int r = 31; r >= 0; --r) v = fmaf(-Lcol[r], __shfl_sync(0xffffffffu, v, r), v);
+        rhs[r0 + lane] = v;
+      }
+      __syncthreads();
+      for (int j = tid; j < r0; j += SS_THREADS) {
+        float v = rhs[j];
+#pragma unroll 8
+        for (int r = 0; r < 32; ++r) v = fmaf(-A[tri(r0 + r, j)], rhs[r0 + r], v);
+        rhs[j] = v;
+      }
+      __syncthreads();
+    }
+    for (int q = tid; q < NP; q += SS_THREADS) xs[q] += (double)rhs[q];
     __syncthreads();
     if (sweep == refine) break;
-    // rho = y - S x in FP64, S symmetric from its lower triangle
-    for (int r = ty; r < n; r += 32) {
+    // rho = y - S x in FP64 from the FP64 S (lower triangle, symmetric)
+    for (int r = wid; r < NP; r += SS_WARPS) {
       double acc = 0.0;
-      for (int c = tx; c < n; c += 32) {
-        const float s = c <= r ? S[(size_t)r * NP + c] : S[(size_t)c * NP + r];
-        acc += (double)s * xs[c];
-      }
+      if (r < n)
+        for (int c = lane; c < n; c += 32) {
+          const double sv = c <= r ? S[(size_t)r * NP + c] : S[(size_t)c * NP + r];
+          acc += sv * xs[c];
+        }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-      if (tx == 0) rhs[r] = (float)((double)y[r] - acc);
+      if (lane == 0) rhs[r] = r < n ? (float)(y[r] - acc) : 0.f;
     }
-    for (int q = n + threadIdx.x; q < NP; q += blockDim.x) rhs[q] = 0.f;
     __syncthreads();
   }
-  for (int q = threadIdx.x; q < n; q += blockDim.x) dx[q] = xs[q];
+  for (int q = tid; q < n; q += SS_THREADS) {
+    dx[q] = xs[q];
+    dxf[q] = (float)xs[q];
+  }
+  // SE(3) retraction of the free poses (FP64)
+  for (int f = tid; f < N - fixed; f += SS_THREADS) dpv_se3_retract(xs + 6 * f, poses + 7 * (size_t)(fixed + f));
 }
 
-template <int NB>
+template <int NQ>
 ba_status_t launch_small(ba_handle_t h, int refine) {
-  constexpr int NP = NB * 32;
-  const size_t smem = sizeof(float) * (size_t)tri(NP, 0);
-  static bool set = false;
-  if (!set) {
-    DPV_CUDA(h, cudaFuncSetAttribute(k_solve_small<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    set = true;
+  static bool attr = false;
+  const size_t smem = sizeof(float) * (size_t)tri(32 * NQ, 0);
+  if (!attr) {
+    DPV_CUDA(h, cudaFuncSetAttribute(k_solve_small<NQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    attr = true;
   }
-  k_solve_small<NB><<<1, 1024, smem, h->stream>>>(h->n, h->ws->S.p, h->ws->y.p, h->ws->dx.p, refine, h->ws->status);
+  k_solve_small<NQ><<<1, SS_THREADS, smem, h->stream>>>(h->n, h->ws->S.p, h->ws->y.p, h->ws->dx.p, h->ws->tmpv.p,
+                                                        refine, h->N, h->fixed, h->poses, h->ws->status);
   ++h->launches;
   DPV_CUDA(h, cudaGetLastError());
   return BA_OK;
@@ -154,19 +210,25 @@ ba_status_t launch_small(ba_handle_t h, int refine) {
 
 ba_status_t dpv_solve_blocked(ba_handle_t h, int refine);
 
-ba_status_t dpv_solve(ba_handle_t h) {
+// Solve S dxi = y.  For n <= DPV_SMALL_N this also retracts the poses
+// (*retracted = 1); otherwise the caller launches the retraction.
+ba_status_t dpv_solve(ba_handle_t h, int* retracted) {
   const int refine = h->opt.precision == BA_MIXED ? h->opt.max_refine : 0;
+  *retracted = 0;
   if (h->n == 0) return BA_OK;
   if (h->n > DPV_SMALL_N) return dpv_solve_blocked(h, refine);
+  ba_status_t s;
   switch (h->n_pad / 32) {
-    case 1: return launch_small<1>(h, refine);
-    case 2: return launch_small<2>(h, refine);
-    case 3: return launch_small<3>(h, refine);
-    case 4: return launch_small<4>(h, refine);
-    case 5: return launch_small<5>(h, refine);
-    case 6: return launch_small<6>(h, refine);
-    case 7: return launch_small<7>(h, refine);
-    case 8: return launch_small<8>(h, refine);
+    case 1: s = launch_small<1>(h, refine); break;
+    case 2: s = launch_small<2>(h, refine); break;
+    case 3: s = launch_small<3>(h, refine); break;
+    case 4: s = launch_small<4>(h, refine); break;
+    case 5: s = launch_small<5>(h, refine); break;
+    case 6: s = launch_small<6>(h, refine); break;
+    case 7: s = launch_small<7>(h, refine); break;
+    case 8: s = launch_small<8>(h, refine); break;
+    default: return dpv_fail(h, BA_ERR_UNSUPPORTED, "pose system size");
   }
-  return dpv_fail(h, BA_ERR_UNSUPPORTED, "pose system size");
+  if (s == BA_OK) *retracted = 1;
+  return s;
 }
