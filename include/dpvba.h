@@ -133,7 +133,7 @@ DPVBA_API const char* ba_status_string(ba_status_t s);
 DPVBA_API ba_status_t ba_linearize(ba_handle_t h, int fixed_poses);
 
 enum {
-  BA_EXPORT_S = 0,      /* float32 [n,n] dense, lower triangle (upper zero), n = 6 (N - fixed) */
+  BA_EXPORT_S = 0,      /* float64 [n,n] dense, lower triangle (upper zero), n = 6 (N - fixed) */
   BA_EXPORT_Y = 1,      /* float64 [n]        reduced right-hand side                         */
   BA_EXPORT_DX = 2,     /* float64 [n]        last pose step                                  */
   BA_EXPORT_DD = 3,     /* float32 [P]        last inverse-depth step                         */

@@ -88,7 +88,7 @@ class DPVBA:
         inf = self.info()
         dev = self._keep[0].device
         if what == capi.EXPORT_S:
-            out = torch.empty((inf["n"], inf["n"]), dtype=torch.float32, device=dev)
+            out = torch.empty((inf["n"], inf["n"]), dtype=torch.float64, device=dev)
         else:
             if count is None:
                 count = {capi.EXPORT_Y: inf["n"], capi.EXPORT_DX: inf["n"], capi.EXPORT_DD: inf["P"],

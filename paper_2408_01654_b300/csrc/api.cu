@@ -374,7 +374,7 @@ ba_status_t ba_debug_export(ba_handle_t h, int what, void* dst, long long bytes)
   const void* src = nullptr;
   long long need = 0;
   switch (what) {
-    case BA_EXPORT_S: need = 4LL * h->n * h->n; break;
+    case BA_EXPORT_S: need = 8LL * h->n * h->n; break;
     case BA_EXPORT_Y: src = ws->y.p; need = 8LL * h->n; break;
     case BA_EXPORT_DX: src = ws->dx.p; need = 8LL * h->n; break;
     case BA_EXPORT_DD: src = ws->dd.p; need = 4LL * h->P; break;
@@ -392,7 +392,7 @@ ba_status_t ba_debug_export(ba_handle_t h, int what, void* dst, long long bytes)
   if (bytes < need) return dpv_fail(h, BA_ERR_INVALID_ARG, "export buffer too small");
   ba_status_t s;
   if (what == BA_EXPORT_S) {
-    if ((s = dpv_export_S(h, (float*)dst))) return s;
+    if ((s = dpv_export_S(h, (double*)dst))) return s;
   } else if (need > 0) {
     DPV_CUDA(h, cudaMemcpyAsync(dst, src, need, cudaMemcpyDeviceToDevice, h->stream));
   }

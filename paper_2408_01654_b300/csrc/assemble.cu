@@ -328,11 +328,11 @@ __global__ void k_init_diag(double* __restrict__ S, int n, int n_pad, int TS, fl
   if (r < n_pad) S[dpv_s_index(r, r, TS)] = r < n ? (double)lambda_p : 1.0;
 }
 
-__global__ void k_export_S(const double* __restrict__ S, int n, int TS, float* __restrict__ out) {
+__global__ void k_export_S(const double* __restrict__ S, int n, int TS, double* __restrict__ out) {
   const size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= (size_t)n * n) return;
   const int r = (int)(q / n), c = (int)(q % n);
-  out[q] = c <= r ? (float)S[dpv_s_index(r, c, TS)] : 0.f;
+  out[q] = c <= r ? S[dpv_s_index(r, c, TS)] : 0.0;
 }
 
 bool g_tables_ready = false;
@@ -384,7 +384,7 @@ ba_status_t dpv_assemble(ba_handle_t h, int it) {
   return BA_OK;
 }
 
-ba_status_t dpv_export_S(ba_handle_t h, float* dst) {
+ba_status_t dpv_export_S(ba_handle_t h, double* dst) {
   const size_t nn = (size_t)h->n * h->n;
   if (nn == 0) return BA_OK;
   k_export_S<<<(unsigned)((nn + 255) / 256), 256, 0, h->stream>>>(h->ws->S.p, h->n, h->TS, dst);

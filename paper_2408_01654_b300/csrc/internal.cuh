@@ -136,7 +136,7 @@ ba_status_t dpv_assemble(ba_handle_t h, int it);
 ba_status_t dpv_solve(ba_handle_t h, int* retracted);  // retracted: poses already updated
 ba_status_t dpv_backsub(ba_handle_t h);
 ba_status_t dpv_retract(ba_handle_t h);
-ba_status_t dpv_export_S(ba_handle_t h, float* dst);
+ba_status_t dpv_export_S(ba_handle_t h, double* dst);
 
 // ---------------------------------------------------------------------------
 // device helpers
