@@ -183,6 +183,28 @@ DPVBA_API ba_status_t ba_profile_enable(ba_handle_t h, int on);
  * its recorded launches (*total_ms) and their number (*launches). */
 DPVBA_API ba_status_t ba_profile_read(ba_handle_t h, int kind, double* total_ms, long long* launches);
 
+/* ---- allocation-free pose-system solve ---------------------------------- */
+
+/* The paper has no counterpart to this call; it exists for callers that cannot
+ * allocate device memory when they need a solve -- a tracking loop with a
+ * fixed per-frame time budget (cudaMalloc may synchronise the device), or a
+ * host framework that owns all device allocations.  It solves S x = y for a
+ * reduced pose system with the same one-CTA LDL^T solver as ba_step, without
+ * a handle and without allocating.
+ *   n      : 1 <= n <= 256; larger n returns BA_ERR_UNSUPPORTED at once.
+ *   S      : device float64 [n,n] row-major; only the lower triangle is read.
+ *   y      : device float64 [n].   x : device float64 [n] (output).
+ *   refine : FP64 refinement sweeps, 0..16 (2 matches BA_MIXED).
+ *   stream : cudaStream_t (NULL = legacy stream).
+ * The call waits for its work and returns BA_ERR_NOT_SPD if S is not positive
+ * definite.  Its working copy lives in a fixed ~0.5 MB device array inside the
+ * library, held by every GPU that loads the library until the process exits.
+ * The first call on each device looks up that array's device address (a
+ * runtime lookup, no allocation); make it before any stream capture.  All
+ * calls share the array, so calls whose GPU work overlaps race. */
+DPVBA_API ba_status_t ba_solve_pose_system_noalloc(int n, const double* S, const double* y, double* x, int refine,
+                                                   void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -232,3 +232,34 @@ ba_status_t dpv_solve(ba_handle_t h, int* retracted) {
   if (s == BA_OK) *retracted = 1;
   return s;
 }
+
+// Launch the one-CTA solver on a system the caller has already laid out as one
+// n_pad x n_pad tile (lower triangle, identity on the padding), without the
+// retraction.  Used by the allocation-free entry point in noalloc.cu.
+namespace {
+template <int NQ>
+ba_status_t launch_small_raw(cudaStream_t st, int n, const double* S, const double* y, double* dx, float* dxf,
+                             int refine, int* status) {
+  const size_t smem = sizeof(float) * (size_t)tri(32 * NQ, 0);
+  if (cudaFuncSetAttribute(k_solve_small<NQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+      cudaSuccess)
+    return BA_ERR_CUDA;
+  k_solve_small<NQ><<<1, SS_THREADS, smem, st>>>(n, S, y, dx, dxf, refine, 0, 0, nullptr, status);
+  return cudaGetLastError() == cudaSuccess ? BA_OK : BA_ERR_CUDA;
+}
+}  // namespace
+
+ba_status_t dpv_launch_small_solver(cudaStream_t st, int n, int n_pad, const double* S, const double* y, double* dx,
+                                    float* dxf, int refine, int* status) {
+  switch (n_pad / 32) {
+    case 1: return launch_small_raw<1>(st, n, S, y, dx, dxf, refine, status);
+    case 2: return launch_small_raw<2>(st, n, S, y, dx, dxf, refine, status);
+    case 3: return launch_small_raw<3>(st, n, S, y, dx, dxf, refine, status);
+    case 4: return launch_small_raw<4>(st, n, S, y, dx, dxf, refine, status);
+    case 5: return launch_small_raw<5>(st, n, S, y, dx, dxf, refine, status);
+    case 6: return launch_small_raw<6>(st, n, S, y, dx, dxf, refine, status);
+    case 7: return launch_small_raw<7>(st, n, S, y, dx, dxf, refine, status);
+    case 8: return launch_small_raw<8>(st, n, S, y, dx, dxf, refine, status);
+  }
+  return BA_ERR_UNSUPPORTED;
+}
