@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <cstring>
 #include <new>
+#include <vector>
 
 size_t dpv_assemble_smem(int G);
 
@@ -96,9 +97,10 @@ void system_geometry(int n, int& TS, int& T, int& n_pad) {
 }
 
 int auto_group(ba_handle_t h, int P) {
-  // enough groups to fill the GPU at least twice, otherwise 32 patches
+  // large graphs: 32 patches per group; small ones: keep about one group
+  // per SM or more (measured on the 22-frame odometry window: 16 best)
   if ((long long)P >= 32LL * 2 * h->num_sms) return 32;
-  if ((long long)P >= 16LL * h->num_sms) return 16;
+  if ((long long)P >= 8LL * h->num_sms) return 16;
   return 8;
 }
 
@@ -170,7 +172,7 @@ ba_status_t ba_create(ba_handle_t* out, const ba_options_t* opt) {
       cudaMalloc(&h->ws->status, sizeof(int)) != cudaSuccess ||
       cudaMalloc(&h->ws->intr, 4 * sizeof(float)) != cudaSuccess ||
       cudaMalloc(&h->ws->cost, 256 * sizeof(double)) != cudaSuccess ||
-      cudaMalloc(&h->ws->nruns, sizeof(int)) != cudaSuccess ||
+      cudaMalloc(&h->ws->unsorted, sizeof(int)) != cudaSuccess ||
       cudaMemset(h->ws->status, 0, sizeof(int)) != cudaSuccess) {
     cudaGetLastError();
     ba_destroy(h);
@@ -185,12 +187,12 @@ ba_status_t ba_destroy(ba_handle_t h) {
   if (!h) return BA_ERR_INVALID_ARG;
   if (h->stream || h->ws) cudaStreamSynchronize(h->stream);
   if (Workspace* ws = h->ws) {
-    void* raw[] = {ws->status, ws->intr, ws->cost, ws->nruns};
+    void* raw[] = {ws->status, ws->intr, ws->cost, ws->unsorted};
     for (void* b : raw)
       if (b) cudaFree(b);
     release(ws->src); release(ws->keys0); release(ws->keys1); release(ws->vals0); release(ws->vals1);
-    release(ws->hist); release(ws->perm); release(ws->eslot); release(ws->runflag); release(ws->runid);
-    release(ws->runptr); release(ws->gptr); release(ws->gseg); release(ws->win); release(ws->wlen);
+    release(ws->hist); release(ws->perm); release(ws->eslot); release(ws->grun); release(ws->gnr);
+    release(ws->gptr); release(ws->win); release(ws->wlen);
     release(ws->scan); release(ws->S); release(ws->y); release(ws->dx); release(ws->Ct); release(ws->wk);
     release(ws->dd); release(ws->L); release(ws->r64); release(ws->tmpv); release(ws->pmpos); release(ws->pptr);
     release(ws->pterm); release(ws->posef);
@@ -258,8 +260,7 @@ ba_status_t ba_set_graph(ba_handle_t h, int N, int P, int E, double* poses, floa
   h->G = h->opt.patches_per_group > 0 ? h->opt.patches_per_group : auto_group(h, P);
   h->ngroups = (P + h->G - 1) / h->G;
   h->fixed = -1;
-  const unsigned long long maxkey = (unsigned long long)h->ngroups * N * N * h->G;
-  h->sort_bits = bits_for(maxkey);
+  h->kk_bits = bits_for((unsigned long long)P);
   ba_status_t s;
   const long long En = std::max(E, 1);
   const long long Gn = h->ngroups + 1;
@@ -268,10 +269,10 @@ ba_status_t ba_set_graph(ba_handle_t h, int N, int P, int E, double* poses, floa
       (s = grow(h, ws->dd, P, "dd")) || (s = grow(h, ws->keys0, En, "sort keys")) ||
       (s = grow(h, ws->keys1, En, "sort keys")) || (s = grow(h, ws->vals0, En, "sort values")) ||
       (s = grow(h, ws->vals1, En, "sort values")) || (s = grow(h, ws->perm, En, "permutation")) ||
-      (s = grow(h, ws->eslot, En, "slots")) || (s = grow(h, ws->runflag, En + 1, "runs")) ||
-      (s = grow(h, ws->runid, En + 1, "runs")) || (s = grow(h, ws->runptr, En + 1, "runs")) ||
+      (s = grow(h, ws->eslot, En, "slots")) || (s = grow(h, ws->grun, Gn * (DPV_RMAX + 1), "run tables")) ||
+      (s = grow(h, ws->gnr, Gn, "run counts")) ||
       (s = grow(h, ws->hist, dpv_hist_entries(En), "histograms")) || (s = grow(h, ws->scan, scan_need, "scan")) ||
-      (s = grow(h, ws->gptr, Gn, "groups")) || (s = grow(h, ws->gseg, Gn, "groups")) ||
+      (s = grow(h, ws->gptr, Gn, "groups")) ||
       (s = grow(h, ws->win, Gn * DPV_WMAX, "windows")) || (s = grow(h, ws->wlen, Gn, "windows")) ||
       (s = grow(h, ws->pmpos, En, "patch-major positions")) || (s = grow(h, ws->pptr, (long long)P + 1, "patch CSR")) ||
       (s = grow(h, ws->pterm, 4 * En, "edge depth terms")) || (s = grow(h, ws->posef, 16LL * N, "pose table")))
@@ -309,14 +310,9 @@ ba_status_t ba_step(ba_handle_t h, int iters, int fixed_poses) {
     s = dpv_solve(h, &retracted);
     dpv_prof_end(h);
     if (s) return s;
-    if (!retracted) {
-      dpv_prof_begin(h, BA_KERNEL_RETRACT);
-      s = dpv_retract(h);
-      dpv_prof_end(h);
-      if (s) return s;
-    }
+    // back-substitution of the depths, with the pose retraction in the same launch
     dpv_prof_begin(h, BA_KERNEL_BACKSUB);
-    s = dpv_backsub(h);
+    s = dpv_backsub(h, !retracted);
     dpv_prof_end(h);
     if (s) return s;
   }
@@ -357,10 +353,12 @@ const char* ba_last_error(ba_handle_t h) {
 
 ba_status_t ba_debug_info(ba_handle_t h, long long* info, int cap) {
   if (!h || !info) return BA_ERR_INVALID_ARG;
-  int nr = 0;
-  if (h->have_graph) {
+  long long nr = 0;
+  if (h->have_graph && h->ngroups > 0) {
     DPV_CUDA(h, cudaStreamSynchronize(h->stream));
-    DPV_CUDA(h, cudaMemcpy(&nr, h->ws->nruns, sizeof(int), cudaMemcpyDeviceToHost));
+    std::vector<int> gnr(h->ngroups);
+    DPV_CUDA(h, cudaMemcpy(gnr.data(), h->ws->gnr.p, sizeof(int) * h->ngroups, cudaMemcpyDeviceToHost));
+    for (int v : gnr) nr += v;
   }
   const long long v[9] = {h->N, h->P, h->E, h->G, h->ngroups, h->n, h->TS, nr, h->launches};
   for (int q = 0; q < cap && q < 9; ++q) info[q] = v[q];

@@ -60,8 +60,9 @@ __device__ __forceinline__ int tri_row(int t) {
 }
 
 __global__ void __launch_bounds__(AS_THREADS) k_assemble(
-    int G, int P, int fixed, int TS, float lambda_d, float z_min, const int* __restrict__ gseg,
-    const int* __restrict__ runptr, const unsigned* __restrict__ eslot, const int* __restrict__ perm,
+    int G, int P, int fixed, int TS, float lambda_d, float z_min, const int* __restrict__ gptr,
+    const int* __restrict__ grun, const int* __restrict__ gnr, const unsigned* __restrict__ eslot,
+    const int* __restrict__ perm,
     const int* __restrict__ pmpos, const int* __restrict__ pptr, const int* __restrict__ win,
     const int* __restrict__ wlen, const float* __restrict__ posef, const float* __restrict__ patches,
     const float* __restrict__ targets, const float* __restrict__ weights, const float* __restrict__ intr,
@@ -73,7 +74,8 @@ __global__ void __launch_bounds__(AS_THREADS) k_assemble(
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int w = wlen[g];
   const int nr = 6 * w;
-  const int rb = gseg[g], nruns = gseg[g + 1] - rb;
+  const int gs = gptr[g], nruns = gnr[g];
+  const int* runptr = grun + (size_t)g * (DPV_RMAX + 1);  // run starts relative to gs
 
   float2* runv = reinterpret_cast<float2*>(sm);            // [RMAX][NV] (hi, lo)
   float* rpose = sm + DPV_RMAX * NV * 2;                    // [RMAX][21]
@@ -106,7 +108,7 @@ __global__ void __launch_bounds__(AS_THREADS) k_assemble(
   }
   __syncthreads();
   for (int r = tid; r < nruns; r += AS_THREADS) {
-    const unsigned sw = eslot[runptr[rb + r]];
+    const unsigned sw = eslot[gs + runptr[r]];
     const int si = dpv_slot_i(sw), sj = dpv_slot_j(sw);
     rsl[r] = si | (sj << 8);
     RelPose T;
@@ -125,7 +127,7 @@ __global__ void __launch_bounds__(AS_THREADS) k_assemble(
   float cst = 0.f;
   float* rw = rows + wid * 32 * ROWF;
   for (int r = wid; r < nruns; r += AS_WARPS) {
-    const int s0 = runptr[rb + r], s1 = runptr[rb + r + 1];
+    const int s0 = gs + runptr[r], s1 = gs + runptr[r + 1];
     const int si = rsl[r] & 0xff, sj = rsl[r] >> 8;
     const bool self_run = si == sj;  // masked edges: they contribute nothing
     RelPose T;
@@ -375,7 +377,7 @@ ba_status_t dpv_assemble(ba_handle_t h, int it) {
   double* cost = ws->cost + (it < ws->cost_cap ? it : ws->cost_cap - 1);
   dpv_prof_begin(h, BA_KERNEL_ASSEMBLE);
   k_assemble<<<h->ngroups, AS_THREADS, assemble_smem_bytes(h->G), h->stream>>>(
-      h->G, h->P, h->fixed, h->TS, h->opt.lambda_depth, h->opt.z_min, ws->gseg.p, ws->runptr.p, ws->eslot.p,
+      h->G, h->P, h->fixed, h->TS, h->opt.lambda_depth, h->opt.z_min, ws->gptr.p, ws->grun.p, ws->gnr.p, ws->eslot.p,
       ws->perm.p, ws->pmpos.p, ws->pptr.p, ws->win.p, ws->wlen.p, ws->posef.p, h->patches, h->targets, h->weights,
       ws->intr, ws->pterm.p, ws->S.p, ws->y.p, ws->Ct.p, ws->wk.p, cost, ws->status);
   ++h->launches;

@@ -43,7 +43,7 @@ struct ba_handle_s {
   // grouping
   int G = 32;            // patches per group
   int ngroups = 0;
-  int sort_bits = 0;
+  int kk_bits = 0;      // bits of the patch index (width of the kk sort)
 
   // solver geometry for the last fixed value
   int fixed = -1;
@@ -80,7 +80,7 @@ struct Workspace {
   int* status = nullptr;          // [1] first device-detected error
   float* intr = nullptr;          // [4]
   double* cost = nullptr;         // [cost_cap] cost at each iteration's linearisation point
-  int* nruns = nullptr;           // [1]
+  int* unsorted = nullptr;        // [1] input kk not non-decreasing
   long long cost_cap = 0;
   // preprocessing
   DBuf<int> src;                  // [P] source frame of each patch, -1 none
@@ -89,8 +89,9 @@ struct Workspace {
   DBuf<int> hist;                 // radix histograms + their scan
   DBuf<int> perm;                 // [E] sorted position -> input edge
   DBuf<unsigned> eslot;           // [E] packed slots
-  DBuf<int> runflag, runid, runptr;  // [E+1] run starts, ids, positions
-  DBuf<int> gptr, gseg;           // [groups+1] edge and run ranges of each group
+  DBuf<int> gptr;                 // [groups+1] edge range of each group
+  DBuf<int> grun;                 // [groups][RMAX+1] run starts relative to the group, then the group size
+  DBuf<int> gnr;                  // [groups] runs per group
   DBuf<int> win;                  // [groups * DPV_WMAX] window frames
   DBuf<int> wlen;                 // [groups]
   DBuf<int> scan;                 // block sums of the scan
@@ -128,13 +129,14 @@ void dpv_prof_end(ba_handle_t h);
 // preprocessing (preprocess.cu)
 ba_status_t dpv_preprocess(ba_handle_t h, const int* ii, const int* jj, const int* kk);
 ba_status_t dpv_block_keys(ba_handle_t h, int fixed, int* keys_out, int cap, int* n_out);
-ba_status_t dpv_exclusive_scan(ba_handle_t h, const int* in, int* out, int n);  // out has n+1 entries
+// out has n+1 entries; when run_if is given the kernels do nothing unless *run_if != 0
+ba_status_t dpv_exclusive_scan(ba_handle_t h, const int* in, int* out, int n, const int* run_if = nullptr);
 long long dpv_scan_scratch(long long n);
 long long dpv_hist_entries(long long m);
 // one GN iteration (assemble.cu, solve_*.cu, update.cu)
 ba_status_t dpv_assemble(ba_handle_t h, int it);
 ba_status_t dpv_solve(ba_handle_t h, int* retracted);  // retracted: poses already updated
-ba_status_t dpv_backsub(ba_handle_t h);
+ba_status_t dpv_backsub(ba_handle_t h, int retract);  // retract: also update the poses
 ba_status_t dpv_retract(ba_handle_t h);
 ba_status_t dpv_export_S(ba_handle_t h, double* dst);
 

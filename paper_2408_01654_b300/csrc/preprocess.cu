@@ -2,13 +2,17 @@
 //
 // Builds, on the GPU and without host round trips:
 //   * validation of every index and of "one source frame per patch"
-//     (the patch graph of Sec. 3.1: patch k belongs to frame i; edges (i,k,j));
-//   * the edge order used by all reduction kernels: a stable sort by
-//     (group, ii, jj, patch-in-group) with group = kk / G, so that each group
-//     of G consecutive patches owns a contiguous edge range and, inside it,
-//     every (source frame, target frame) pair is one contiguous "run";
-//   * per group: its window (sorted frames touched by its edges, at most
-//     DPV_WMAX) and, per edge, the window slots of ii and jj.
+//     (the patch graph of Sec. 3.1: patch k belongs to frame i; edges (i,k,j)),
+//     and whether kk is already non-decreasing;
+//   * the patch-major order: a stable sort of the edges by kk (skipped on the
+//     device when the input is already kk-sorted, the usual case);
+//   * the group and patch CSR (gptr, pptr) from the patch-major order;
+//   * per group of G consecutive patches: its window (sorted frames touched by
+//     its edges, at most DPV_WMAX), and a counting sort of its edges by
+//     (source slot, target slot) in shared memory, so that every
+//     (source frame, target frame) pair is one contiguous "run"; the run
+//     table is per group (at most DPV_RMAX runs), so no global scan is needed.
+// The resulting edge order is the stable sort by (group, ii, jj, kk).
 #include "internal.cuh"
 
 #include <algorithm>
@@ -53,8 +57,9 @@ __device__ int block_exclusive_scan(int v, int* sh, int& total) {
   return wpre + x - v;
 }
 
-__global__ void k_scan_tiles(const int* __restrict__ in, int n, int* __restrict__ sums) {
+__global__ void k_scan_tiles(const int* __restrict__ in, int n, int* __restrict__ sums, const int* run_if) {
   __shared__ int sh[32];
+  if (run_if && !*run_if) return;
   const int base = blockIdx.x * SCAN_TILE;
   int s = 0;
 #pragma unroll
@@ -67,8 +72,9 @@ __global__ void k_scan_tiles(const int* __restrict__ in, int n, int* __restrict_
   if (threadIdx.x == 0) sums[blockIdx.x] = total;
 }
 
-__global__ void k_scan_sums(int* sums, int nb) {
+__global__ void k_scan_sums(int* sums, int nb, const int* run_if) {
   __shared__ int sh[32];
+  if (run_if && !*run_if) return;
   const int per = (nb + blockDim.x - 1) / blockDim.x;
   const int lo = threadIdx.x * per, hi = min(nb, lo + per);
   int s = 0;
@@ -84,8 +90,9 @@ __global__ void k_scan_sums(int* sums, int nb) {
 }
 
 __global__ void k_scan_down(const int* __restrict__ in, int n, const int* __restrict__ sums,
-                            int* __restrict__ out) {
+                            int* __restrict__ out, const int* run_if) {
   __shared__ int sh[32];
+  if (run_if && !*run_if) return;
   const int base = blockIdx.x * SCAN_TILE + threadIdx.x * SCAN_ITEMS;
   int v[SCAN_ITEMS], s = 0;
 #pragma unroll
@@ -106,13 +113,15 @@ __global__ void k_scan_down(const int* __restrict__ in, int n, const int* __rest
 // ---------------------------------------------------------------------------
 // validation and sort keys
 // ---------------------------------------------------------------------------
-__global__ void k_validate(int E, int N, int P, int G, const int* __restrict__ ii, const int* __restrict__ jj,
+__global__ void k_validate(int E, int N, int P, const int* __restrict__ ii, const int* __restrict__ jj,
                            const int* __restrict__ kk, int* __restrict__ src, unsigned long long* __restrict__ keys,
-                           int* __restrict__ vals, int* status) {
+                           int* __restrict__ vals, int* __restrict__ unsorted, int* status) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= E) return;
   const int i = ii[e], j = jj[e], k = kk[e];
   vals[e] = e;
+  keys[e] = (unsigned)k;
+  if (e + 1 < E && k > kk[e + 1]) atomicOr(unsorted, 1);
   if (i < 0 || i >= N || j < 0 || j >= N || k < 0 || k >= P) {
     dpv_set_status(status, DST_BAD_INDEX);
     keys[e] = 0ull;
@@ -120,8 +129,6 @@ __global__ void k_validate(int E, int N, int P, int G, const int* __restrict__ i
   }
   const int old = atomicCAS(&src[k], -1, i);
   if (old != -1 && old != i) dpv_set_status(status, DST_BAD_INDEX);
-  const unsigned long long g = (unsigned)(k / G), kl = (unsigned)(k % G);
-  keys[e] = ((g * (unsigned)N + (unsigned)i) * (unsigned)N + (unsigned)j) * (unsigned)G + kl;
 }
 
 // ---------------------------------------------------------------------------
@@ -131,8 +138,9 @@ __global__ void k_validate(int E, int N, int P, int G, const int* __restrict__ i
 // keys keep their input order.
 // ---------------------------------------------------------------------------
 __global__ void k_rs_hist(const unsigned long long* __restrict__ keys, int M, int shift, int* __restrict__ hist,
-                          int nblocks) {
+                          int nblocks, const int* run_if) {
   __shared__ int cnt[256];
+  if (run_if && !*run_if) return;
   const int t = threadIdx.x;
   cnt[t] = 0;
   __syncthreads();
@@ -148,8 +156,9 @@ __global__ void k_rs_hist(const unsigned long long* __restrict__ keys, int M, in
 
 __global__ void k_rs_scatter(const unsigned long long* __restrict__ kin, const int* __restrict__ vin,
                              unsigned long long* __restrict__ kout, int* __restrict__ vout, int M, int shift,
-                             const int* __restrict__ offs, int nblocks) {
+                             const int* __restrict__ offs, int nblocks, const int* run_if) {
   __shared__ int base_off[256];
+  if (run_if && !*run_if) return;
   __shared__ int wcnt[RS_THREADS / 32][256];
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
   base_off[t] = offs[(size_t)t * nblocks + blockIdx.x];
@@ -192,71 +201,54 @@ __global__ void k_rs_scatter(const unsigned long long* __restrict__ kin, const i
 }
 
 // ---------------------------------------------------------------------------
-// group pointers and run flags on the sorted order
+// group and patch CSR over the patch-major (kk-sorted) order
 // ---------------------------------------------------------------------------
-__global__ void k_finalize(int E, int G, int ngroups, const int* __restrict__ perm, const int* __restrict__ ii,
-                           const int* __restrict__ jj, const int* __restrict__ kk, int* __restrict__ gptr,
-                           int* __restrict__ runflag, const int* status) {
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= E) return;
-  if (dpv_status(status)) {
-    runflag[s] = 0;
-    return;
-  }
-  const int e = perm[s];
-  const int i = ii[e], j = jj[e], g = kk[e] / G;
-  int flag;
-  if (s == 0) {
-    for (int q = 0; q <= g; ++q) gptr[q] = 0;
-    flag = 1;
-  } else {
-    const int ep = perm[s - 1];
-    const int gp = kk[ep] / G;
-    for (int q = gp + 1; q <= g; ++q) gptr[q] = s;
-    flag = (g != gp) || (i != ii[ep]) || (j != jj[ep]);
-  }
-  if (s == E - 1)
-    for (int q = g + 1; q <= ngroups; ++q) gptr[q] = E;
-  runflag[s] = flag;
-}
+__device__ __forceinline__ int pm_edge(int s, const int* perm0, int unsorted) { return unsorted ? perm0[s] : s; }
 
-__global__ void k_runs(int E, int ngroups, const int* __restrict__ runflag, const int* __restrict__ runid,
-                       const int* __restrict__ gptr, int* __restrict__ runptr, int* __restrict__ gseg,
-                       int* __restrict__ nruns) {
+__global__ void k_bounds(int E, int P, int G, int ngroups, const int* __restrict__ kk, const int* __restrict__ perm0,
+                         const int* __restrict__ unsorted_p, int* __restrict__ gptr, int* __restrict__ pptr,
+                         const int* status) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  const int total = runid[E];
-  if (s < E && runflag[s]) runptr[runid[s]] = s;
-  if (s == 0) {
-    runptr[total] = E;
-    *nruns = total;
-  }
-  if (s <= ngroups) {
-    const int p = gptr[s];
-    gseg[s] = p < E ? runid[p] : total;
+  if (s >= E || dpv_status(status)) return;
+  const int uns = *unsorted_p;
+  const int k = kk[pm_edge(s, perm0, uns)];
+  const int kp = s ? kk[pm_edge(s - 1, perm0, uns)] : -1;
+  // patches (kp, k] start at s; groups likewise
+  for (int q = kp + 1; q <= k; ++q) pptr[q] = s;
+  for (int q = (kp < 0 ? 0 : kp / G + 1); q <= k / G; ++q)
+    if (kp < 0 || q * G > kp) gptr[q] = s;
+  if (s == E - 1) {
+    for (int q = k + 1; q <= P; ++q) pptr[q] = E;
+    for (int q = k / G + 1; q <= ngroups; ++q) gptr[q] = E;
   }
 }
 
 // ---------------------------------------------------------------------------
-// group windows: sorted unique frames of each group's edges, and edge slots
+// per group: window, slots, counting sort into (source, target) runs
 // ---------------------------------------------------------------------------
-__global__ void k_windows(int N, int P, int E, int G, const int* __restrict__ gptr, const int* __restrict__ gseg,
-                          const int* __restrict__ perm, const int* __restrict__ ii, const int* __restrict__ jj,
-                          const int* __restrict__ kk, int* __restrict__ win, int* __restrict__ wlen,
-                          unsigned* __restrict__ eslot, int* __restrict__ pmpos, int* __restrict__ pptr,
-                          int* status) {
+constexpr int NBUCKET = DPV_WMAX * DPV_WMAX;
+
+__global__ void __launch_bounds__(256) k_group_build(
+    int N, int G, const int* __restrict__ gptr, const int* __restrict__ perm0, const int* __restrict__ unsorted_p,
+    const int* __restrict__ ii, const int* __restrict__ jj, const int* __restrict__ kk, int* __restrict__ win,
+    int* __restrict__ wlen, int* __restrict__ perm, unsigned* __restrict__ eslot, int* __restrict__ pmpos,
+    int* __restrict__ grun, int* __restrict__ gnr, int* status) {
   extern __shared__ unsigned smw[];
   __shared__ int sh[32];
-  __shared__ int poff[DPV_GMAX + 1];
+  __shared__ int boff[NBUCKET];
+  __shared__ int bcnt[NBUCKET];
   const int nwords = (N + 31) >> 5;
   unsigned* bm = smw;
   int* wpre = (int*)(smw + nwords);
   const int g = blockIdx.x;
   if (dpv_status(status)) return;
+  const int uns = *unsorted_p;
   const int s0 = gptr[g], s1 = gptr[g + 1];
   for (int q = threadIdx.x; q < nwords; q += blockDim.x) bm[q] = 0u;
+  for (int q = threadIdx.x; q < NBUCKET; q += blockDim.x) bcnt[q] = 0;
   __syncthreads();
   for (int s = s0 + threadIdx.x; s < s1; s += blockDim.x) {
-    const int e = perm[s];
+    const int e = pm_edge(s, perm0, uns);
     const int i = ii[e], j = jj[e];
     atomicOr(&bm[i >> 5], 1u << (i & 31));
     atomicOr(&bm[j >> 5], 1u << (j & 31));
@@ -273,7 +265,7 @@ __global__ void k_windows(int N, int P, int E, int G, const int* __restrict__ gp
     run += __popc(bm[q]);
   }
   __syncthreads();
-  if (total > DPV_WMAX || gseg[g + 1] - gseg[g] > DPV_RMAX) {
+  if (total > DPV_WMAX) {
     if (threadIdx.x == 0) {
       wlen[g] = total;
       dpv_set_status(status, DST_WIDE);
@@ -291,45 +283,71 @@ __global__ void k_windows(int N, int P, int E, int G, const int* __restrict__ gp
   }
   for (int q = total + threadIdx.x; q < DPV_WMAX; q += blockDim.x) win[g * DPV_WMAX + q] = -1;
   if (threadIdx.x == 0) wlen[g] = total;
+  // bucket counts by (source slot, target slot)
   for (int s = s0 + threadIdx.x; s < s1; s += blockDim.x) {
-    const int e = perm[s];
+    const int e = pm_edge(s, perm0, uns);
     const int i = ii[e], j = jj[e];
     const int si = wpre[i >> 5] + __popc(bm[i >> 5] & ((1u << (i & 31)) - 1u));
     const int sj = wpre[j >> 5] + __popc(bm[j >> 5] & ((1u << (j & 31)) - 1u));
-    eslot[s] = dpv_pack_slot(si, sj, kk[e] % G);
+    atomicAdd(&bcnt[si * DPV_WMAX + sj], 1);
   }
-  // patch-major order inside the group: a stable counting sort by patch, so
-  // each patch's edges keep their (ii, jj) order; pptr is the global CSR
-  for (int q = threadIdx.x; q <= G; q += blockDim.x) poff[q] = 0;
   __syncthreads();
-  for (int s = s0 + threadIdx.x; s < s1; s += blockDim.x) atomicAdd(&poff[kk[perm[s]] % G], 1);
+  // offsets of the buckets and the run table (non-empty buckets, in order)
+  {
+    int v[4], cnt = 0, nz = 0;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      v[r] = bcnt[4 * threadIdx.x + r];
+      cnt += v[r];
+      nz += v[r] > 0;
+    }
+    int tot;
+    int off = block_exclusive_scan(cnt, sh, tot);
+    int rtot;
+    int rid = block_exclusive_scan(nz, sh, rtot);
+    if (rtot > DPV_RMAX) {
+      if (threadIdx.x == 0) dpv_set_status(status, DST_WIDE);
+      return;
+    }
+    int* gr = grun + (size_t)g * (DPV_RMAX + 1);
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      boff[4 * threadIdx.x + r] = off;
+      if (v[r] > 0) gr[rid++] = off;
+      off += v[r];
+    }
+    if (threadIdx.x == 0) {
+      gr[rtot] = tot;
+      gnr[g] = rtot;
+    }
+  }
   __syncthreads();
+  // stable placement (one warp walks the group in patch-major order)
   if (threadIdx.x < 32) {
     const int lane = threadIdx.x;
-    if (lane == 0) {
-      int run = 0;
-      for (int q = 0; q < G; ++q) {
-        const int c = poff[q];
-        poff[q] = run;
-        run += c;
-      }
-    }
-    __syncwarp();
-    for (int q = lane; q < G; q += 32)
-      if (g * G + q < P) pptr[g * G + q] = s0 + poff[q];
-    if (lane == 0 && (g + 1) * G >= P) pptr[P] = E;
-    __syncwarp();
     const unsigned lt = (1u << lane) - 1u;
     for (int b = s0; b < s1; b += 32) {
       const int s = b + lane;
       const bool valid = s < s1;
-      const int kl = valid ? kk[perm[s]] % G : DPV_GMAX;
-      const unsigned peers = __match_any_sync(0xffffffffu, kl);
-      const int base = valid ? poff[kl] : 0;
+      int bucket = NBUCKET, e = 0, si = 0, sj = 0;
+      if (valid) {
+        e = pm_edge(s, perm0, uns);
+        const int i = ii[e], j = jj[e];
+        si = wpre[i >> 5] + __popc(bm[i >> 5] & ((1u << (i & 31)) - 1u));
+        sj = wpre[j >> 5] + __popc(bm[j >> 5] & ((1u << (j & 31)) - 1u));
+        bucket = si * DPV_WMAX + sj;
+      }
+      const unsigned peers = __match_any_sync(0xffffffffu, bucket);
       const int rank = __popc(peers & lt);
-      if (valid) pmpos[s] = s0 + base + rank;
+      const int base = valid ? boff[bucket] : 0;
+      if (valid) {
+        const int pos = s0 + base + rank;
+        perm[pos] = e;
+        eslot[pos] = dpv_pack_slot(si, sj, kk[e] % G);
+        pmpos[pos] = s;
+      }
       __syncwarp();
-      if (valid && rank == 0) poff[kl] = base + __popc(peers);
+      if (valid && rank == 0) boff[bucket] = base + __popc(peers);
       __syncwarp();
     }
   }
@@ -375,7 +393,7 @@ __global__ void k_key_emit(int M, int N, const unsigned long long* __restrict__ 
 // Sorts (k0, v0) by the low `bits` bits of the keys; `which` tells whether
 // the result ended in (k0, v0) or (k1, v1).  hist needs dpv_hist_entries(M).
 ba_status_t radix_sort(ba_handle_t h, unsigned long long* k0, int* v0, unsigned long long* k1, int* v1, int M,
-                       int bits, int* hist, int& which) {
+                       int bits, int* hist, int& which, const int* run_if = nullptr) {
   which = 0;
   if (M <= 1) return BA_OK;
   const int nb = (M + RS_TILE - 1) / RS_TILE;
@@ -385,11 +403,11 @@ ba_status_t radix_sort(ba_handle_t h, unsigned long long* k0, int* v0, unsigned 
   int* vout = v1;
   int* offs = hist + 256 * nb;
   for (int shift = 0; shift < bits; shift += 8) {
-    k_rs_hist<<<nb, RS_THREADS, 0, h->stream>>>(kin, M, shift, hist, nb);
+    k_rs_hist<<<nb, RS_THREADS, 0, h->stream>>>(kin, M, shift, hist, nb, run_if);
     ++h->launches;
-    ba_status_t st = dpv_exclusive_scan(h, hist, offs, 256 * nb);
+    ba_status_t st = dpv_exclusive_scan(h, hist, offs, 256 * nb, run_if);
     if (st) return st;
-    k_rs_scatter<<<nb, RS_THREADS, 0, h->stream>>>(kin, vin, kout, vout, M, shift, offs, nb);
+    k_rs_scatter<<<nb, RS_THREADS, 0, h->stream>>>(kin, vin, kout, vout, M, shift, offs, nb, run_if);
     ++h->launches;
     std::swap(kin, kout);
     std::swap(vin, vout);
@@ -404,7 +422,7 @@ ba_status_t radix_sort(ba_handle_t h, unsigned long long* k0, int* v0, unsigned 
 long long dpv_scan_scratch(long long n) { return (n + SCAN_TILE - 1) / SCAN_TILE + 2; }
 long long dpv_hist_entries(long long m) { return 2 * 256 * ((m + RS_TILE - 1) / RS_TILE) + 2; }
 
-ba_status_t dpv_exclusive_scan(ba_handle_t h, const int* in, int* out, int n) {
+ba_status_t dpv_exclusive_scan(ba_handle_t h, const int* in, int* out, int n, const int* run_if) {
   Workspace* ws = h->ws;
   if (n <= 0) {
     DPV_CUDA(h, cudaMemsetAsync(out, 0, sizeof(int), h->stream));
@@ -412,11 +430,11 @@ ba_status_t dpv_exclusive_scan(ba_handle_t h, const int* in, int* out, int n) {
   }
   const int nb = (n + SCAN_TILE - 1) / SCAN_TILE;
   if (nb + 1 > ws->scan.cap) return dpv_fail(h, BA_ERR_UNSUPPORTED, "scan larger than its scratch");
-  k_scan_tiles<<<nb, SCAN_THREADS, 0, h->stream>>>(in, n, ws->scan.p);
+  k_scan_tiles<<<nb, SCAN_THREADS, 0, h->stream>>>(in, n, ws->scan.p, run_if);
   ++h->launches;
-  k_scan_sums<<<1, SCAN_THREADS, 0, h->stream>>>(ws->scan.p, nb);
+  k_scan_sums<<<1, SCAN_THREADS, 0, h->stream>>>(ws->scan.p, nb, run_if);
   ++h->launches;
-  k_scan_down<<<nb, SCAN_THREADS, 0, h->stream>>>(in, n, ws->scan.p, out);
+  k_scan_down<<<nb, SCAN_THREADS, 0, h->stream>>>(in, n, ws->scan.p, out, run_if);
   ++h->launches;
   DPV_CUDA(h, cudaGetLastError());
   return BA_OK;
@@ -427,37 +445,36 @@ ba_status_t dpv_preprocess(ba_handle_t h, const int* ii, const int* jj, const in
   const int E = h->E, N = h->N, P = h->P, G = h->G;
   cudaStream_t st = h->stream;
   DPV_CUDA(h, cudaMemsetAsync(ws->src.p, 0xff, sizeof(int) * P, st));
-  DPV_CUDA(h, cudaMemsetAsync(ws->gptr.p, 0, sizeof(int) * (h->ngroups + 1), st));
-  if (E > 0) {
-    k_validate<<<(E + 255) / 256, 256, 0, st>>>(E, N, P, G, ii, jj, kk, ws->src.p, ws->keys0.p, ws->vals0.p,
-                                                 ws->status);
-    ++h->launches;
-    int which = 0;
-    ba_status_t s = radix_sort(h, ws->keys0.p, ws->vals0.p, ws->keys1.p, ws->vals1.p, E, h->sort_bits,
-                               ws->hist.p, which);
-    if (s) return s;
-    DPV_CUDA(h, cudaMemcpyAsync(ws->perm.p, (which ? ws->vals1.p : ws->vals0.p), sizeof(int) * E, cudaMemcpyDeviceToDevice, st));
-    k_finalize<<<(E + 255) / 256, 256, 0, st>>>(E, G, h->ngroups, ws->perm.p, ii, jj, kk, ws->gptr.p, ws->runflag.p,
-                                                 ws->status);
-    ++h->launches;
-    s = dpv_exclusive_scan(h, ws->runflag.p, ws->runid.p, E);
-    if (s) return s;
-    const int nthr = std::max(E, h->ngroups + 1);
-    k_runs<<<(nthr + 255) / 256, 256, 0, st>>>(E, h->ngroups, ws->runflag.p, ws->runid.p, ws->gptr.p, ws->runptr.p,
-                                                ws->gseg.p, ws->nruns);
-    ++h->launches;
+  DPV_CUDA(h, cudaMemsetAsync(ws->unsorted, 0, sizeof(int), st));
+  if (E == 0) {
+    DPV_CUDA(h, cudaMemsetAsync(ws->gptr.p, 0, sizeof(int) * (h->ngroups + 1), st));
+    DPV_CUDA(h, cudaMemsetAsync(ws->pptr.p, 0, sizeof(int) * (P + 1), st));
   } else {
-    DPV_CUDA(h, cudaMemsetAsync(ws->gseg.p, 0, sizeof(int) * (h->ngroups + 1), st));
-    DPV_CUDA(h, cudaMemsetAsync(ws->runptr.p, 0, sizeof(int), st));
-    DPV_CUDA(h, cudaMemsetAsync(ws->nruns, 0, sizeof(int), st));
+    k_validate<<<(E + 255) / 256, 256, 0, st>>>(E, N, P, ii, jj, kk, ws->src.p, ws->keys0.p, ws->vals0.p,
+                                                 ws->unsorted, ws->status);
+    ++h->launches;
+    // stable sort by kk, only when the input is not kk-sorted
+    int which = 0;
+    ba_status_t s = radix_sort(h, ws->keys0.p, ws->vals0.p, ws->keys1.p, ws->vals1.p, E, h->kk_bits, ws->hist.p,
+                               which, ws->unsorted);
+    if (s) return s;
+    const int* perm0 = which ? ws->vals1.p : ws->vals0.p;
+    k_bounds<<<(E + 255) / 256, 256, 0, st>>>(E, P, G, h->ngroups, kk, perm0, ws->unsorted, ws->gptr.p, ws->pptr.p,
+                                               ws->status);
+    ++h->launches;
+    const int nwords = (N + 31) / 32;
+    const size_t smem = sizeof(unsigned) * nwords + sizeof(int) * nwords;
+    if (smem > 160 * 1024) return dpv_fail(h, BA_ERR_UNSUPPORTED, "too many frames for the window kernel");
+    DPV_CUDA(h, cudaFuncSetAttribute(k_group_build, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_group_build<<<h->ngroups, 256, smem, st>>>(N, G, ws->gptr.p, perm0, ws->unsorted, ii, jj, kk, ws->win.p,
+                                                 ws->wlen.p, ws->perm.p, ws->eslot.p, ws->pmpos.p, ws->grun.p,
+                                                 ws->gnr.p, ws->status);
+    ++h->launches;
   }
-  const int nwords = (N + 31) / 32;
-  const size_t smem = sizeof(unsigned) * nwords + sizeof(int) * nwords;
-  if (smem > 200 * 1024) return dpv_fail(h, BA_ERR_UNSUPPORTED, "too many frames for the window kernel");
-  DPV_CUDA(h, cudaFuncSetAttribute(k_windows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  k_windows<<<h->ngroups, 256, smem, st>>>(N, P, E, G, ws->gptr.p, ws->gseg.p, ws->perm.p, ii, jj, kk, ws->win.p,
-                                           ws->wlen.p, ws->eslot.p, ws->pmpos.p, ws->pptr.p, ws->status);
-  ++h->launches;
+  if (E == 0) {
+    DPV_CUDA(h, cudaMemsetAsync(ws->gnr.p, 0, sizeof(int) * h->ngroups, st));
+    DPV_CUDA(h, cudaMemsetAsync(ws->wlen.p, 0, sizeof(int) * h->ngroups, st));
+  }
   DPV_CUDA(h, cudaGetLastError());
   return BA_OK;
 }

@@ -3,109 +3,157 @@
 // "Bundle-Adjustment Efficiency"), followed by the SE(3) retraction of the
 // free poses.
 //
-// S and y arrive in FP64 (the assembly accumulates them so).  S is rounded to
+// S and y arrive in FP64 (the assembly accumulates them so); S is rounded to
 // FP32 into shared memory as a packed lower triangle and factored as
-// S = L D L^T (the Cholesky factor is L D^1/2; a pivot D_c <= 0 means S is
-// not positive definite) by blocked right-looking elimination with 8-column
-// panels:
-//   * warp 0 holds the panel in registers (rows lane + 32q) and eliminates its
-//     8 columns with shuffles only, then stores it with the scaled copy
-//     W = panel D^-1;
-//   * all 16 warps apply the rank-8 update A -= panel W^T to the trailing
-//     triangle -- two block barriers per panel.
-// The triangular solves run in 32-row blocks: warp 0 keeps the block's 32x32
-// triangle in registers and solves it with shuffles, all warps update the
-// rest of the right-hand side.  In BA_MIXED mode the solution is refined:
-// rho = y - S x in FP64 from the FP64 S in global memory, solved with the same
-// factor, x += delta.
+// S = L D L^T (the Cholesky factor is L D^1/2; a pivot D_k <= 0 means S is
+// not positive definite) by blocked right-looking elimination, 32 columns at
+// a time:
+//   1. warp 0 eliminates the 32x32 diagonal block in registers (lane = row);
+//      each column reaches the other rows through a shared-memory vector read
+//      with 128-bit broadcast loads;
+//   2. warp 0 forms the inverse of the block's unit lower factor (lane =
+//      column of the inverse);
+//   3. the panel below is A_panel L_kk^-T, one warp per row with a lane per
+//      output (no dependency chain);
+//   4. all threads apply the rank-32 update to the trailing triangle in 4x4
+//      register tiles.
+// The block inverses also turn the triangular solves into 32-row block
+// matrix-vector products instead of 32-step dependency chains.  The
+// retraction of the poses runs in the back-substitution kernel, off this
+// single-CTA critical path.
+//
+// Refinement: sweeps of x += S^-1 (y - S x) with the same factor.  In
+// BA_FP32 one sweep computes the residual in compensated FP32 (TwoProd /
+// TwoSum) from the FP32 copy of S, which removes the factorisation error;
+// in BA_MIXED the sweeps compute it in FP64 from the FP64 S.
 #include "internal.cuh"
 
 #include "retract.cuh"
 
 namespace {
 
-constexpr int SS_THREADS = 512;
-constexpr int SS_WARPS = SS_THREADS / 32;
-constexpr int PW = 8;  // panel width
-
 __host__ __device__ constexpr int tri(int r, int c) { return r * (r + 1) / 2 + c; }
 
+__host__ __device__ constexpr int small_threads(int NQ) { return NQ <= 2 ? 128 : 512; }
+// the FP32 copy of S for the compensated residual fits in shared memory up to NQ = 6
+__host__ __device__ constexpr bool keep_sf(int NQ) { return NQ <= 6; }
+__host__ __device__ constexpr size_t small_smem(int NQ) {
+  return sizeof(float) * ((size_t)tri(32 * NQ, 0) * (keep_sf(NQ) ? 2 : 1));
+}
+
 template <int NQ>  // NP = 32 NQ
-__global__ void __launch_bounds__(SS_THREADS) k_solve_small(int n, const double* __restrict__ S,
-                                                            const double* __restrict__ y, double* __restrict__ dx,
-                                                            float* __restrict__ dxf, int refine, int N, int fixed,
-                                                            double* __restrict__ poses, int* status) {
+__global__ void __launch_bounds__(small_threads(NQ)) k_solve_small(
+    int n, const double* __restrict__ S, const double* __restrict__ y, double* __restrict__ dx,
+    float* __restrict__ dxf, int refine32, int refine64, int N, int fixed, double* __restrict__ poses, int* status) {
   constexpr int NP = 32 * NQ;
-  extern __shared__ float A[];              // packed lower, tri(NP, 0) floats
-  __shared__ float W[PW][NP];               // scaled panel
+  constexpr int NT = small_threads(NQ);
+  constexpr int NWARP = NT / 32;
+  extern __shared__ float Lsh[];            // packed lower: trailing A, then the unit factor
+  float* Sf = Lsh + tri(NP, 0);             // FP32 copy of S (keep_sf)
+  __shared__ float Pb[NP][33];              // unscaled panel of the current block
+  __shared__ float Linv[NQ][32][33];        // inverses of the unit diagonal blocks
+  __shared__ __align__(16) float ucol[32];  // column broadcast in the diagonal block
   __shared__ float invD[NP];
   __shared__ float rhs[NP];
-  __shared__ double xs[NP];
+  __shared__ float xhi[NP], xlo[NP];
+  __shared__ float yhi[NP], ylo[NP];
   __shared__ int bad;
   if (dpv_status(status)) return;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  for (int i = wid; i < NP; i += SS_WARPS)
-    for (int j = lane; j <= i; j += 32) A[tri(i, j)] = (float)S[(size_t)i * NP + j];
+  for (int i = wid; i < NP; i += NWARP)
+    for (int j = lane; j <= i; j += 32) {
+      const float v = (float)S[(size_t)i * NP + j];
+      Lsh[tri(i, j)] = v;
+      if (keep_sf(NQ)) Sf[tri(i, j)] = v;
+    }
   if (tid == 0) bad = 0;
   __syncthreads();
 
-  for (int p0 = 0; p0 < NP; p0 += PW) {
+  for (int r0 = 0; r0 < NP; r0 += 32) {
+    const int kb = r0 / 32;
+    // 1. diagonal block, lane = row r0 + lane
     if (wid == 0) {
-      // panel rows i = p0 + lane + 32 q, columns p0 .. p0+7, in registers
-      float pr[NQ][PW];
+      float a[32];
 #pragma unroll
-      for (int q = 0; q < NQ; ++q) {
-        const int i = p0 + lane + 32 * q;
-#pragma unroll
-        for (int c = 0; c < PW; ++c) pr[q][c] = (i < NP && i >= p0 + c) ? A[tri(i, p0 + c)] : 0.f;
-      }
+      for (int c = 0; c < 32; ++c) a[c] = c <= lane ? Lsh[tri(r0 + lane, r0 + c)] : 0.f;
       bool ok = true;
 #pragma unroll
-      for (int c = 0; c < PW; ++c) {
-        const float dc = __shfl_sync(0xffffffffu, pr[0][c], c);
-        ok = ok && (dc > 0.f);
-        const float inv = 1.0f / dc;
-        if (lane == 0) invD[p0 + c] = inv;
-        float ajc[PW];
+      for (int c = 0; c < 32; ++c) {
+        ucol[lane] = a[c];
+        __syncwarp();
+        const float d = ucol[c];
+        ok = ok && (d > 0.f);
+        const float inv = __frcp_rn(d);
+        const float l = a[c] * inv;
+        float u[32];
 #pragma unroll
-        for (int j = c + 1; j < PW; ++j) ajc[j] = __shfl_sync(0xffffffffu, pr[0][c], j);
-#pragma unroll
-        for (int q = 0; q < NQ; ++q) {
-          const int i = p0 + lane + 32 * q;
-          const float aic = pr[q][c] * inv;
-#pragma unroll
-          for (int j = c + 1; j < PW; ++j)
-            if (i >= p0 + j) pr[q][j] = fmaf(-aic, ajc[j], pr[q][j]);
+        for (int q = 0; q < 8; ++q) {
+          const float4 v = reinterpret_cast<const float4*>(ucol)[q];
+          u[4 * q] = v.x; u[4 * q + 1] = v.y; u[4 * q + 2] = v.z; u[4 * q + 3] = v.w;
         }
+#pragma unroll
+        for (int j = c + 1; j < 32; ++j) a[j] = fmaf(-l, u[j], a[j]);
+        if (lane == c) invD[r0 + c] = inv;
+        if (lane > c) a[c] = l;
+        __syncwarp();
       }
       if (!ok && lane == 0) bad = 1;
+#pragma unroll
+      for (int c = 0; c < 32; ++c)
+        if (c < lane) Lsh[tri(r0 + lane, r0 + c)] = a[c];
       __syncwarp();
+      // 2. inverse of the unit lower block: lane c solves L_kk x = e_c
+      float x[32];
 #pragma unroll
-      for (int q = 0; q < NQ; ++q) {
-        const int i = p0 + lane + 32 * q;
-        if (i < NP) {
+      for (int i = 0; i < 32; ++i) x[i] = (i == lane) ? 1.f : 0.f;
 #pragma unroll
-          for (int c = 0; c < PW; ++c) {
-            if (i >= p0 + c) A[tri(i, p0 + c)] = pr[q][c];
-            W[c][i] = pr[q][c] * invD[p0 + c];
-          }
-        }
-      }
+      for (int k = 0; k < 31; ++k)
+#pragma unroll
+        for (int i = k + 1; i < 32; ++i) x[i] = fmaf(-Lsh[tri(r0 + i, r0 + k)], x[k], x[i]);
+#pragma unroll
+      for (int i = 0; i < 32; ++i) Linv[kb][i][lane] = x[i];
     }
     __syncthreads();
     if (bad) break;
-    // rank-PW update of the trailing triangle: A[i][j] -= sum_c A[i][p0+c] W[c][j]
-    const int p1 = p0 + PW;
-    for (int i = p1 + wid; i < NP; i += SS_WARPS) {
-      float ai[PW];
+    // 3. panel rows below the block: P = A_panel L_kk^-T (lane = output column)
+    for (int i = r0 + 32 + wid; i < NP; i += NWARP) {
+      const float* ai = Lsh + tri(i, r0);
+      float p = 0.f;
+#pragma unroll 8
+      for (int cp = 0; cp < 32; ++cp) p = fmaf(ai[cp], Linv[kb][lane][cp], p);
+      __syncwarp();
+      Pb[i][lane] = p;
+      Lsh[tri(i, r0 + lane)] = p * invD[r0 + lane];
+    }
+    __syncthreads();
+    // 4. trailing update A[i][j] -= sum_c Pb[i][c] L[j][r0 + c], i >= j >= r0 + 32, 4x4 tiles
+    const int p1 = r0 + 32, m = NP - p1, mt = m / 4;
+    for (int t = tid; t < mt * mt; t += NT) {
+      const int bi = t / mt, bj = t % mt;
+      if (bj > bi) continue;
+      const int i0 = p1 + 4 * bi, j0 = p1 + 4 * bj;
+      float acc[4][4];
 #pragma unroll
-      for (int c = 0; c < PW; ++c) ai[c] = A[tri(i, p0 + c)];
-      for (int j = p1 + lane; j <= i; j += 32) {
-        float s = A[tri(i, j)];
+      for (int a = 0; a < 4; ++a)
 #pragma unroll
-        for (int c = 0; c < PW; ++c) s = fmaf(-ai[c], W[c][j], s);
-        A[tri(i, j)] = s;
+        for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
+#pragma unroll 4
+      for (int c = 0; c < 32; ++c) {
+        float pa[4], lb[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) pa[a] = Pb[i0 + a][c];
+#pragma unroll
+        for (int b = 0; b < 4; ++b) lb[b] = Lsh[tri(j0 + b, r0) + c];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(pa[a], lb[b], acc[a][b]);
       }
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+          if (i0 + a >= j0 + b) Lsh[tri(i0 + a, j0 + b)] -= acc[a][b];
     }
     __syncthreads();
   }
@@ -113,94 +161,126 @@ __global__ void __launch_bounds__(SS_THREADS) k_solve_small(int n, const double*
     if (tid == 0) dpv_set_status(status, DST_NOT_SPD);
     return;
   }
-  // unit lower factor L = A D^-1 (strict lower part, in place)
-  for (int i = wid; i < NP; i += SS_WARPS)
-    for (int j = lane; j < i; j += 32) A[tri(i, j)] *= invD[j];
-  for (int q = tid; q < NP; q += SS_THREADS) {
-    rhs[q] = q < n ? (float)y[q] : 0.f;
-    xs[q] = 0.0;
+  for (int q = tid; q < NP; q += NT) {
+    const double yq = q < n ? y[q] : 0.0;
+    const float yh = (float)yq;
+    yhi[q] = yh;
+    ylo[q] = (float)(yq - (double)yh);
+    rhs[q] = yh;
+    xhi[q] = 0.f;
+    xlo[q] = 0.f;
   }
   __syncthreads();
 
-  for (int sweep = 0; sweep <= refine; ++sweep) {
+  const int sweeps = 1 + refine32 + refine64;
+  for (int sweep = 0; sweep < sweeps; ++sweep) {
     // forward: L u = rhs
-    for (int r0 = 0; r0 < NP; r0 += 32) {
+    for (int kb = 0; kb < NQ; ++kb) {
+      const int r0 = 32 * kb;
       if (wid == 0) {
-        float Lrow[32];  // row r0+lane of the diagonal block
-#pragma unroll
-        for (int c = 0; c < 32; ++c) Lrow[c] = c < lane ? A[tri(r0 + lane, r0 + c)] : 0.f;
-        float v = rhs[r0 + lane];
-#pragma unroll
-        for (int c = 0; c < 32; ++c) v = fmaf(-Lrow[c], __shfl_sync(0xffffffffu, v, c), v);
+        float v = 0.f;
+#pragma unroll 8
+        for (int c = 0; c < 32; ++c) v = fmaf(Linv[kb][lane][c], rhs[r0 + c], v);
+        __syncwarp();
         rhs[r0 + lane] = v;
       }
       __syncthreads();
-      for (int i = r0 + 32 + tid; i < NP; i += SS_THREADS) {
+      for (int i = r0 + 32 + tid; i < NP; i += NT) {
         float v = rhs[i];
-        const float* li = A + tri(i, r0);
+        const float* li = Lsh + tri(i, r0);
 #pragma unroll 8
         for (int c = 0; c < 32; ++c) v = fmaf(-li[c], rhs[r0 + c], v);
         rhs[i] = v;
       }
       __syncthreads();
     }
-    for (int q = tid; q < NP; q += SS_THREADS) rhs[q] *= invD[q];
+    for (int q = tid; q < NP; q += NT) rhs[q] *= invD[q];
     __syncthreads();
     // backward: L^T x = v
-    for (int r0 = NP - 32; r0 >= 0; r0 -= 32) {
+    for (int kb = NQ - 1; kb >= 0; --kb) {
+      const int r0 = 32 * kb;
       if (wid == 0) {
-        float Lcol[32];  // column r0+lane of the diagonal block
-#pragma unroll
-        for (int r = 0; r < 32; ++r) Lcol[r] = r > lane ? A[tri(r0 + r, r0 + lane)] : 0.f;
-        float v = rhs[r0 + lane];
-#pragma unroll
-        for (int r = 31; r >= 0; --r) v = fmaf(-Lcol[r], __shfl_sync(0xffffffffu, v, r), v);
+        float v = 0.f;
+#pragma unroll 8
+        for (int r = 0; r < 32; ++r) v = fmaf(Linv[kb][r][lane], rhs[r0 + r], v);
+        __syncwarp();
         rhs[r0 + lane] = v;
       }
       __syncthreads();
-      for (int j = tid; j < r0; j += SS_THREADS) {
+      for (int j = tid; j < r0; j += NT) {
         float v = rhs[j];
 #pragma unroll 8
-        for (int r = 0; r < 32; ++r) v = fmaf(-A[tri(r0 + r, j)], rhs[r0 + r], v);
+        for (int r = 0; r < 32; ++r) v = fmaf(-Lsh[tri(r0 + r, j)], rhs[r0 + r], v);
         rhs[j] = v;
       }
       __syncthreads();
     }
-    for (int q = tid; q < NP; q += SS_THREADS) xs[q] += (double)rhs[q];
+    // x += correction (double-float)
+    for (int q = tid; q < NP; q += NT) {
+      DF a = {xhi[q], xlo[q]};
+      df_add(a, rhs[q]);
+      xhi[q] = a.hi;
+      xlo[q] = a.lo;
+    }
     __syncthreads();
-    if (sweep == refine) break;
-    // rho = y - S x in FP64 from the FP64 S (lower triangle, symmetric)
-    for (int r = wid; r < NP; r += SS_WARPS) {
-      double acc = 0.0;
-      if (r < n)
-        for (int c = lane; c < n; c += 32) {
-          const double sv = c <= r ? S[(size_t)r * NP + c] : S[(size_t)c * NP + r];
-          acc += sv * xs[c];
-        }
+    if (sweep + 1 == sweeps) break;
+    // residual rho = y - S x
+    if (sweep < refine32 && keep_sf(NQ)) {
+      // compensated FP32 against the FP32 copy of S
+      for (int r = wid; r < NP; r += NWARP) {
+        DF acc = {0.f, 0.f};
+        if (r < n)
+          for (int c = lane; c < n; c += 32) {
+            const float sv = c <= r ? Sf[tri(r, c)] : Sf[tri(c, r)];
+            df_fma(acc, sv, xhi[c]);
+            acc.lo = fmaf(sv, xlo[c], acc.lo);
+          }
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-      if (lane == 0) rhs[r] = r < n ? (float)(y[r] - acc) : 0.f;
+        for (int o = 16; o > 0; o >>= 1) {
+          const float oh = __shfl_xor_sync(0xffffffffu, acc.hi, o), ol = __shfl_xor_sync(0xffffffffu, acc.lo, o);
+          df_add(acc, oh);
+          acc.lo += ol;
+        }
+        if (lane == 0) {
+          DF rr = {yhi[r], ylo[r]};
+          df_add(rr, -acc.hi);
+          rr.lo -= acc.lo;
+          rhs[r] = r < n ? df_val(rr) : 0.f;
+        }
+      }
+    } else {
+      // FP64 from the FP64 S (lower triangle, symmetric)
+      for (int r = wid; r < NP; r += NWARP) {
+        double acc = 0.0;
+        if (r < n)
+          for (int c = lane; c < n; c += 32) {
+            const double sv = c <= r ? S[(size_t)r * NP + c] : S[(size_t)c * NP + r];
+            acc += sv * ((double)xhi[c] + (double)xlo[c]);
+          }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) rhs[r] = r < n ? (float)(y[r] - acc) : 0.f;
+      }
     }
     __syncthreads();
   }
-  for (int q = tid; q < n; q += SS_THREADS) {
-    dx[q] = xs[q];
-    dxf[q] = (float)xs[q];
+  for (int q = tid; q < n; q += NT) {
+    dx[q] = (double)xhi[q] + (double)xlo[q];
+    dxf[q] = xhi[q] + xlo[q];
   }
-  // SE(3) retraction of the free poses (FP64)
-  for (int f = tid; f < N - fixed; f += SS_THREADS) dpv_se3_retract(xs + 6 * f, poses + 7 * (size_t)(fixed + f));
 }
 
 template <int NQ>
-ba_status_t launch_small(ba_handle_t h, int refine) {
+ba_status_t launch_small(ba_handle_t h, int refine32, int refine64) {
   static bool attr = false;
-  const size_t smem = sizeof(float) * (size_t)tri(32 * NQ, 0);
+  const size_t smem = small_smem(NQ);
   if (!attr) {
     DPV_CUDA(h, cudaFuncSetAttribute(k_solve_small<NQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     attr = true;
   }
-  k_solve_small<NQ><<<1, SS_THREADS, smem, h->stream>>>(h->n, h->ws->S.p, h->ws->y.p, h->ws->dx.p, h->ws->tmpv.p,
-                                                        refine, h->N, h->fixed, h->poses, h->ws->status);
+  k_solve_small<NQ><<<1, small_threads(NQ), smem, h->stream>>>(h->n, h->ws->S.p, h->ws->y.p, h->ws->dx.p,
+                                                                h->ws->tmpv.p, refine32, refine64, h->N, h->fixed,
+                                                                h->poses, h->ws->status);
   ++h->launches;
   DPV_CUDA(h, cudaGetLastError());
   return BA_OK;
@@ -210,26 +290,26 @@ ba_status_t launch_small(ba_handle_t h, int refine) {
 
 ba_status_t dpv_solve_blocked(ba_handle_t h, int refine);
 
-// Solve S dxi = y.  For n <= DPV_SMALL_N this also retracts the poses
-// (*retracted = 1); otherwise the caller launches the retraction.
+// Solve S dxi = y (the retraction is launched by the caller).
 ba_status_t dpv_solve(ba_handle_t h, int* retracted) {
-  const int refine = h->opt.precision == BA_MIXED ? h->opt.max_refine : 0;
+  // BA_FP32: one compensated-FP32 refinement sweep; BA_MIXED: FP64 sweeps
+  const int refine32 = h->opt.precision == BA_MIXED ? 0 : 1;
+  const int refine64 = h->opt.precision == BA_MIXED ? h->opt.max_refine : 0;
   *retracted = 0;
   if (h->n == 0) return BA_OK;
-  if (h->n > DPV_SMALL_N) return dpv_solve_blocked(h, refine);
+  if (h->n > DPV_SMALL_N) return dpv_solve_blocked(h, refine64);
   ba_status_t s;
   switch (h->n_pad / 32) {
-    case 1: s = launch_small<1>(h, refine); break;
-    case 2: s = launch_small<2>(h, refine); break;
-    case 3: s = launch_small<3>(h, refine); break;
-    case 4: s = launch_small<4>(h, refine); break;
-    case 5: s = launch_small<5>(h, refine); break;
-    case 6: s = launch_small<6>(h, refine); break;
-    case 7: s = launch_small<7>(h, refine); break;
-    case 8: s = launch_small<8>(h, refine); break;
+    case 1: s = launch_small<1>(h, refine32, refine64); break;
+    case 2: s = launch_small<2>(h, refine32, refine64); break;
+    case 3: s = launch_small<3>(h, refine32, refine64); break;
+    case 4: s = launch_small<4>(h, refine32, refine64); break;
+    case 5: s = launch_small<5>(h, refine32, refine64); break;
+    case 6: s = launch_small<6>(h, refine32, refine64); break;
+    case 7: s = launch_small<7>(h, refine32, refine64); break;
+    case 8: s = launch_small<8>(h, refine32, refine64); break;
     default: return dpv_fail(h, BA_ERR_UNSUPPORTED, "pose system size");
   }
-  if (s == BA_OK) *retracted = 1;
   return s;
 }
 
@@ -240,11 +320,11 @@ namespace {
 template <int NQ>
 ba_status_t launch_small_raw(cudaStream_t st, int n, const double* S, const double* y, double* dx, float* dxf,
                              int refine, int* status) {
-  const size_t smem = sizeof(float) * (size_t)tri(32 * NQ, 0);
+  const size_t smem = small_smem(NQ);
   if (cudaFuncSetAttribute(k_solve_small<NQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
       cudaSuccess)
     return BA_ERR_CUDA;
-  k_solve_small<NQ><<<1, SS_THREADS, smem, st>>>(n, S, y, dx, dxf, refine, 0, 0, nullptr, status);
+  k_solve_small<NQ><<<1, small_threads(NQ), smem, st>>>(n, S, y, dx, dxf, 0, refine, 0, 0, nullptr, status);
   return cudaGetLastError() == cudaSuccess ? BA_OK : BA_ERR_CUDA;
 }
 }  // namespace

@@ -18,8 +18,15 @@ namespace {
 __global__ void k_backsub(int P, int G, int fixed, float d_min, const int* __restrict__ pptr,
                           const float4* __restrict__ pterm, const int* __restrict__ win,
                           const float* __restrict__ dxf, const float* __restrict__ Ct, const float* __restrict__ wk,
-                          float* __restrict__ patches, float* __restrict__ dd_out, const int* status) {
+                          float* __restrict__ patches, float* __restrict__ dd_out, int N, const double* __restrict__ dx,
+                          double* __restrict__ poses, const int* status) {
   if (dpv_status(status)) return;
+  if (N > fixed && blockIdx.x == gridDim.x - 1) {
+    // the extra last CTA retracts the free poses (FP64) while the others back-substitute
+    for (int f = fixed + threadIdx.x; f < N; f += blockDim.x)
+      dpv_se3_retract(dx + 6 * (f - fixed), poses + 7 * (size_t)f);
+    return;
+  }
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= P) return;
   const int* wf = win + (k / G) * DPV_WMAX;
@@ -58,12 +65,14 @@ __global__ void k_retract(int N, int fixed, const double* __restrict__ dx, doubl
 
 }  // namespace
 
-ba_status_t dpv_backsub(ba_handle_t h) {
+// Back-substitution of the depths; with `retract` the kernel also updates the
+// poses (one extra CTA).
+ba_status_t dpv_backsub(ba_handle_t h, int retract) {
   Workspace* ws = h->ws;
-  if (h->P == 0) return BA_OK;
-  k_backsub<<<(h->P + 127) / 128, 128, 0, h->stream>>>(h->P, h->G, h->fixed, h->opt.d_min, ws->pptr.p, ws->pterm.p,
-                                                         ws->win.p, ws->tmpv.p, ws->Ct.p, ws->wk.p, h->patches,
-                                                         ws->dd.p, ws->status);
+  const int nb = (h->P + 127) / 128 + (retract ? 1 : 0);
+  k_backsub<<<nb, 128, 0, h->stream>>>(h->P, h->G, h->fixed, h->opt.d_min, ws->pptr.p, ws->pterm.p, ws->win.p,
+                                       ws->tmpv.p, ws->Ct.p, ws->wk.p, h->patches, ws->dd.p,
+                                       retract ? h->N : h->fixed, ws->dx.p, h->poses, ws->status);
   ++h->launches;
   DPV_CUDA(h, cudaGetLastError());
   return BA_OK;

@@ -30,7 +30,7 @@ def _ptr(t):
 def _system_and_step(scene):
     """The reduced system at the scene's initial state, and ba_step's pose step."""
     T = scene_tensors(scene)
-    ba = DPVBA()
+    ba = DPVBA(precision="mixed", max_refine=2)  # FP64 refinement, as the call below
     ba.set_graph(**T)
     ba.linearize(scene.fixed)
     S = ba.export(capi.EXPORT_S).contiguous()
@@ -51,7 +51,7 @@ def test_noalloc_solve_matches_ba_step_on_two_calls_in_a_row():
     for S, y, want in cases:
         n = y.numel()
         x = torch.full_like(y, float("nan"))
-        st = L.ba_solve_pose_system_noalloc(n, _ptr(S), _ptr(y), _ptr(x), 0, stream)
+        st = L.ba_solve_pose_system_noalloc(n, _ptr(S), _ptr(y), _ptr(x), 2, stream)
         assert st == capi.BA_OK, L.ba_status_string(st)
         err = ((x - want).abs().max() / want.abs().max()).item()
         assert err < TOL, err
