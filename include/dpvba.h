@@ -142,7 +142,7 @@ enum {
   BA_EXPORT_PERM = 6,   /* int32 [E]          sorted position -> input edge                   */
   BA_EXPORT_SLOTS = 7,  /* uint32 [E]         slot_i | slot_j << 8 | patch-in-group << 16     */
   BA_EXPORT_GPTR = 8,   /* int32 [groups+1]   edge range of each group                        */
-  BA_EXPORT_WIN = 9,    /* int32 [groups, 32] window frames of each group (-1 padded)          */
+  BA_EXPORT_WIN = 9,    /* int32 [groups, 64] window frames of each group (-1 padded)          */
   BA_EXPORT_COST = 10,  /* float64 [iters]    cost sum w r^2 at each iteration's linearisation point */
   BA_EXPORT_PMPOS = 11, /* int32 [E]          sorted position -> patch-major position          */
   BA_EXPORT_PPTR = 12   /* int32 [P+1]        patch-major edge range of each patch             */

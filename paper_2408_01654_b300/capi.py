@@ -17,7 +17,7 @@ BA_OK, BA_ERR_INVALID_ARG, BA_ERR_CUDA, BA_ERR_OOM, BA_ERR_NOT_SPD, BA_ERR_TIMEO
 BA_FP32, BA_MIXED = 0, 1
 (EXPORT_S, EXPORT_Y, EXPORT_DX, EXPORT_DD, EXPORT_CT, EXPORT_W, EXPORT_PERM, EXPORT_SLOTS, EXPORT_GPTR,
  EXPORT_WIN, EXPORT_COST, EXPORT_PMPOS, EXPORT_PPTR) = range(13)
-WMAX = 32
+WMAX = 64
 
 
 class BAOptions(ctypes.Structure):

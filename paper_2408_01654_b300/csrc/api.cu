@@ -51,6 +51,8 @@ static void prof_clear(ba_handle_t h) {
   h->prof_open = -1;
 }
 
+long long dpv_large_scratch_floats(int n_pad);
+
 namespace {
 
 template <class T>
@@ -116,7 +118,7 @@ ba_status_t ensure_system(ba_handle_t h, int fixed) {
       (s = grow(h, ws->dx, h->n_pad, "step")) || (s = grow(h, ws->r64, h->n_pad, "residual")) ||
       (s = grow(h, ws->tmpv, h->n_pad, "vector")))
     return s;
-  if (h->n > DPV_SMALL_N && (s = grow(h, ws->L, nS, "factor"))) return s;
+  if (h->n > DPV_SMALL_N && (s = grow(h, ws->L, dpv_large_scratch_floats(h->n_pad), "factor"))) return s;
   return BA_OK;
 }
 
@@ -341,7 +343,7 @@ ba_status_t ba_sync(ba_handle_t h) {
     case DST_TIMEOUT: return dpv_fail(h, BA_ERR_TIMEOUT, "a device-side wait ran out");
     case DST_WIDE:
       return dpv_fail(h, BA_ERR_UNSUPPORTED,
-                      "a patch group touches more than 32 frames; lower patches_per_group");
+                      "a patch group touches more than 64 frames or has more than 64 (source, target) runs");
   }
   return dpv_fail(h, BA_ERR_CUDA, "unknown device status");
 }

@@ -10,7 +10,7 @@
 // ---------------------------------------------------------------------------
 // limits of the kernels
 // ---------------------------------------------------------------------------
-#define DPV_WMAX 32          // frames in one group window (slots fit in 8 bits)
+#define DPV_WMAX 64          // frames in one group window (slots fit in 8 bits)
 #define DPV_GMAX 64          // patches per group
 #define DPV_SMALL_N 256      // pose systems up to this size use the one-CTA solver
 #define DPV_TILE 64          // tile edge of the blocked pose system (large n)

@@ -294,10 +294,11 @@ __global__ void __launch_bounds__(256) k_group_build(
   __syncthreads();
   // offsets of the buckets and the run table (non-empty buckets, in order)
   {
-    int v[4], cnt = 0, nz = 0;
+    constexpr int PER = NBUCKET / 256;
+    int v[PER], cnt = 0, nz = 0;
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
-      v[r] = bcnt[4 * threadIdx.x + r];
+    for (int r = 0; r < PER; ++r) {
+      v[r] = bcnt[PER * threadIdx.x + r];
       cnt += v[r];
       nz += v[r] > 0;
     }
@@ -311,8 +312,8 @@ __global__ void __launch_bounds__(256) k_group_build(
     }
     int* gr = grun + (size_t)g * (DPV_RMAX + 1);
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
-      boff[4 * threadIdx.x + r] = off;
+    for (int r = 0; r < PER; ++r) {
+      boff[PER * threadIdx.x + r] = off;
       if (v[r] > 0) gr[rid++] = off;
       off += v[r];
     }

@@ -297,7 +297,8 @@ ba_status_t dpv_solve(ba_handle_t h, int* retracted) {
   const int refine64 = h->opt.precision == BA_MIXED ? h->opt.max_refine : 0;
   *retracted = 0;
   if (h->n == 0) return BA_OK;
-  if (h->n > DPV_SMALL_N) return dpv_solve_blocked(h, refine64);
+  // large systems: FP64 refinement sweeps (at least one), the residual spread over the GPU
+  if (h->n > DPV_SMALL_N) return dpv_solve_blocked(h, refine32 + refine64);
   ba_status_t s;
   switch (h->n_pad / 32) {
     case 1: s = launch_small<1>(h, refine32, refine64); break;

@@ -167,6 +167,20 @@ def test_gn_step_across_pose_system_sizes(frames):
         assert rot < TOL and tr < TOL and dep < TOL, (frames, precision, rot, tr, dep)
 
 
+@pytest.mark.parametrize("frames", [60, 120])
+def test_gn_step_blocked_solver(frames):
+    # 6 (frames - 2) = 348 / 708 unknowns: the blocked large-system solver
+    s = scenes._build("sized", 13, frames, lambda i, n: scenes._clipped_window(i, n, 6), 2, 1)
+    for precision in ("fp32", "mixed"):
+        ba, T = bind(s, precision=precision)
+        ba.step(1, s.fixed)
+        ba.sync()
+        want = oracle.gn_steps(s, iters=1)[0]
+        rot, tr = pose_error(T["poses"].cpu().numpy(), want[0])
+        dep = depth_error(T["patches"][:, 2, 1, 1].cpu().numpy().astype(np.float64), want[1])
+        assert rot < TOL and tr < TOL and dep < TOL, (frames, precision, rot, tr, dep)
+
+
 def test_gn_step_independent_of_input_edge_order():
     s = scenes.odometry(seed=2)
     order = np.random.default_rng(5).permutation(s.E)
