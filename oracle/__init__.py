@@ -162,7 +162,10 @@ def gn_steps(s, iters=None, fixed=None, opts=DEFAULT_OPTS):
 
 def grad_fwd(s, a, b, kind, index, iters=None, fixed=None, opts=DEFAULT_OPTS):
     """d/d(input coordinate) of <a, poses_final> + <b, depths_final>, one value
-    per coordinate; kind 0 = target, 1 = weight; index into the flat [E,2]."""
+    per coordinate; kind 0 = target, 1 = weight (index into the flat [E,2]),
+    2 = initial inverse depth (index = patch), 3 = left perturbation
+    T <- Exp(xi) T of an initial pose (index = 6 * pose + component of
+    xi = (rho, phi))."""
     iters = s.iters if iters is None else iters
     fixed = s.fixed if fixed is None else fixed
     kind = _i(kind)

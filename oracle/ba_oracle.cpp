@@ -506,7 +506,11 @@ int oracle_gn(int N, int P, int E, double* poses, double* patches, const int* ii
 
 // forward-mode derivative of  L = <a, poses_final> + <b, depths_final>  with
 // respect to single input coordinates: kind[c] = 0 -> targets[index[c]],
-// kind[c] = 1 -> weights[index[c]] (index into the flattened [E,2] array).
+// kind[c] = 1 -> weights[index[c]] (index into the flattened [E,2] array),
+// kind[c] = 2 -> the initial inverse depth of patch index[c],
+// kind[c] = 3 -> component m = index[c] % 6 of a left perturbation
+// T <- Exp(xi) T, xi = (rho, phi), of initial pose a = index[c] / 6, whose
+// first-order change is dt = rho + phi x t, dq = (phi/2, 0) (x) q.
 // One dual-number GN run per coordinate.
 int oracle_grad_fwd(int N, int P, int E, const double* poses, const double* patches, const int* ii,
                     const int* jj, const int* kk, const double* targets, const double* weights,
@@ -515,10 +519,33 @@ int oracle_grad_fwd(int N, int P, int E, const double* poses, const double* patc
   if (check_indices(N, P, E, ii, jj, kk)) return 1;
   const Opts o{opts4[0], opts4[1], opts4[2], opts4[3]};
   for (int c = 0; c < ncoord; ++c) {
+    const long long lim = kind[c] <= 1 ? 2LL * E : (kind[c] == 2 ? (long long)P : 6LL * N);
+    if (kind[c] < 0 || kind[c] > 3 || index[c] < 0 || index[c] >= lim) return 1;
+  }
+  for (int c = 0; c < ncoord; ++c) {
     Problem<Dual> pb;
     load_problem(pb, N, P, E, poses, patches, ii, jj, kk, targets, weights, intr);
-    if (kind[c] == 0) pb.tgt[index[c]].d = 1.0;
-    else pb.wgt[index[c]].d = 1.0;
+    if (kind[c] == 0) {
+      pb.tgt[index[c]].d = 1.0;
+    } else if (kind[c] == 1) {
+      pb.wgt[index[c]].d = 1.0;
+    } else if (kind[c] == 2) {
+      pb.d[index[c]].d = 1.0;
+    } else {
+      const int a = (int)(index[c] / 6), m = (int)(index[c] % 6);
+      double xi[6] = {0, 0, 0, 0, 0, 0};
+      xi[m] = 1.0;
+      double t[3], q[4];
+      for (int r = 0; r < 3; ++r) t[r] = pb.poses[a].t[r].v;
+      for (int r = 0; r < 4; ++r) q[r] = pb.poses[a].q[r].v;
+      const double half_phi[4] = {0.5 * xi[3], 0.5 * xi[4], 0.5 * xi[5], 0.0};
+      double dq[4];
+      quat_mul(half_phi, q, dq);
+      const double dt[3] = {xi[0] + xi[4] * t[2] - xi[5] * t[1], xi[1] + xi[5] * t[0] - xi[3] * t[2],
+                            xi[2] + xi[3] * t[1] - xi[4] * t[0]};
+      for (int r = 0; r < 3; ++r) pb.poses[a].t[r].d = dt[r];
+      for (int r = 0; r < 4; ++r) pb.poses[a].q[r].d = dq[r];
+    }
     for (int it = 0; it < iters; ++it) {
       int st = gn_iteration(pb, fixed, o, (std::vector<Dual>*)nullptr, (std::vector<Dual>*)nullptr,
                             (Dual*)nullptr);

@@ -347,6 +347,69 @@ def test_dual_gradient_matches_central_fd(oracle_lib):
         assert abs(g[c] - fd) <= 1e-5 * max(1.0, abs(fd)), (c, g[c], fd)
 
 
+def _pose_matrix(p):
+    T = np.eye(4)
+    T[:3, :3] = Rotation.from_quat(p[3:]).as_matrix()
+    T[:3, 3] = p[:3]
+    return T
+
+
+def _pose_vector(T):
+    q = Rotation.from_matrix(T[:3, :3]).as_quat()
+    return np.r_[T[:3, 3], q]
+
+
+def _se3_hat(xi):
+    rho, phi = xi[:3], xi[3:]
+    H = np.zeros((4, 4))
+    H[:3, :3] = [[0, -phi[2], phi[1]], [phi[2], 0, -phi[0]], [-phi[1], phi[0], 0]]
+    H[:3, 3] = rho
+    return H
+
+
+def test_dual_gradient_of_initial_state_matches_central_fd(oracle_lib):
+    """Derivatives with respect to the initial inverse depths and to left
+    perturbations of the initial poses (kinds 2 and 3) against central
+    differences; the perturbed pose is formed with the library matrix
+    exponential, independent of the oracle's own perturbation formula."""
+    s = small_graph(seed=5, N=6, M=8)
+    s.iters = 2
+    rng = np.random.default_rng(1)
+    a = rng.normal(size=(s.N, 7))
+    b = rng.normal(size=s.P)
+
+    def L(poses, patches):
+        r = oracle.gn(s, poses=poses, patches=patches)
+        return (a * r["poses"]).sum() + (b * r["patches"][:, 2, 1, 1]).sum()
+
+    kpatch = rng.choice(s.P, 8, replace=False)
+    kpose = rng.choice(np.arange(6 * s.fixed, 6 * s.N), 12, replace=False)
+    kind = np.r_[np.full(8, 2), np.full(12, 3)]
+    index = np.r_[kpatch, kpose]
+    g = oracle.grad_fwd(s, a, b, kind, index)
+    eps = 1e-4
+    for c in range(len(kind)):
+        if kind[c] == 2:
+            pp, pm = s.patches.copy(), s.patches.copy()
+            pp[index[c], 2] += eps
+            pm[index[c], 2] -= eps
+            fd = (L(s.poses, pp) - L(s.poses, pm)) / (2 * eps)
+        else:
+            q, m = divmod(int(index[c]), 6)
+            xi = np.zeros(6)
+            xi[m] = eps
+            Pp, Pm = s.poses.copy(), s.poses.copy()
+            T = _pose_matrix(s.poses[q])
+            Pp[q] = _pose_vector(scipy.linalg.expm(_se3_hat(xi)) @ T)
+            Pm[q] = _pose_vector(scipy.linalg.expm(_se3_hat(-xi)) @ T)
+            # keep the quaternion hemisphere of the input
+            for Pq in (Pp, Pm):
+                if np.dot(Pq[q, 3:], s.poses[q, 3:]) < 0:
+                    Pq[q, 3:] *= -1
+            fd = (L(Pp, s.patches) - L(Pm, s.patches)) / (2 * eps)
+        assert abs(g[c] - fd) <= 1e-5 * max(1.0, abs(fd)), (c, kind[c], g[c], fd)
+
+
 # --------------------------------------------------------------------------- #
 # graph indexing: canonical block keys on a hand-made graph
 # --------------------------------------------------------------------------- #
