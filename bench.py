@@ -322,6 +322,27 @@ def run_ours(args):
         e2e_ms = float(t.item())
     e2e_value = gn_iters / (e2e_ms / 1e3)
 
+    # ---- adjoint of the same step (ba_backward), timed on its own ----------
+    g = torch.Generator(device=dev).manual_seed(rank)
+    gp = torch.randn((scene.N, 7), dtype=torch.float64, device=dev, generator=g)
+    gd = torch.randn(scene.P, dtype=torch.float32, device=dev, generator=g)
+    nb = min(args.steps, 20)
+    bev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(nb)]
+    ba.set_record(True)
+    for k in range(nb + 2):
+        reset()
+        flush.zero_()
+        one_step()
+        if k >= 2:
+            bev[k - 2][0].record(stream)
+        ba.backward(gp, gd)
+        if k >= 2:
+            bev[k - 2][1].record(stream)
+    torch.cuda.synchronize()
+    ba.set_record(False)
+    ba.sync()
+    bwd_ms = statistics.median(a.elapsed_time(b) for a, b in bev)
+
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -380,6 +401,9 @@ def run_ours(args):
         "gpu_launches": launches,
         "clocks": clk.summary(),
         "step_ms": {"min": min(step_ms), "median": statistics.median(step_ms), "max": max(step_ms)},
+        "adjoint": {"backward_ms_per_step": bwd_ms, "forward_ms_per_step": statistics.median(step_ms),
+                    "what": "ba_backward over the recorded ba_step (grad of targets and weights), median of "
+                            f"{nb}, L2 flushed before each forward"},
     }
     print(json.dumps(line))
     if dist:

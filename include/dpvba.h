@@ -172,7 +172,8 @@ enum {
   BA_KERNEL_SOLVE = 3,      /* Cholesky and triangular solves (+ refinement)     */
   BA_KERNEL_BACKSUB = 4,    /* inverse-depth back-substitution                   */
   BA_KERNEL_RETRACT = 5,    /* SE(3) retraction                                  */
-  BA_KERNEL_CLASSES = 6
+  BA_KERNEL_ADJOINT = 6,    /* adjoint-only kernels of ba_backward               */
+  BA_KERNEL_CLASSES = 7
 };
 
 /* on != 0: from now on record a CUDA event pair around every launch of each
@@ -182,6 +183,47 @@ DPVBA_API ba_status_t ba_profile_enable(ba_handle_t h, int on);
 /* Synchronise, then report for kernel class `kind` the summed event time of
  * its recorded launches (*total_ms) and their number (*launches). */
 DPVBA_API ba_status_t ba_profile_read(ba_handle_t h, int kind, double* total_ms, long long* launches);
+
+/* ---- adjoint (reverse mode through the iterations) ----------------------
+ *
+ * The bundle adjustment is a differentiable layer (Sec. 3.1: the update
+ * operator's targets and confidence weights are trained through the unrolled
+ * Gauss-Newton iterations of Eq. 3).  ba_backward gives the derivative of a
+ * scalar loss L(poses_final, depths_final) with respect to the targets and
+ * weights of the last recorded ba_step call, by reverse mode through each
+ * iteration: the retraction, the damped normal equations H Delta = g (solved
+ * with the same Schur/Cholesky path as the forward step, H being symmetric)
+ * and the per-edge linearisation (Eq. 2).  The depth clamp at d_min passes
+ * the cotangent only where it did not clamp; masked edges (i = j, or the point
+ * less than z_min in front of frame j) contribute nothing; fixed poses have no
+ * cotangent. */
+
+/* on != 0: every following ba_step call records its iterations (copies of
+ * the state before each iteration and of each step, ~(56 N + 120 P + 8 n)
+ * bytes per iteration, owned by the handle) and becomes the tape of
+ * ba_backward, replacing the previous tape.  on == 0: stop recording (the
+ * last tape stays usable).  ba_set_graph discards the tape. */
+DPVBA_API ba_status_t ba_set_record(ba_handle_t h, int on);
+
+/* Reverse-mode pass over the tape, stream-ordered on the handle's stream.
+ * Inputs (device, may be null = zero):
+ *   grad_poses  : float64 [N,7], dL/d(t, q) of the final poses (the layout of
+ *                 `poses`; only the component tangent to the unit quaternion
+ *                 matters, and rows of fixed poses are ignored);
+ *   grad_depths : float32 [P], dL/d(inverse depth) of the final patches.
+ * Outputs (device, may be null = not wanted):
+ *   grad_targets, grad_weights : float32 [E,2] in input edge order,
+ *                 8-byte aligned, overwritten;
+ *   grad_tangent0 : float64 [N,6], dL/dxi of the initial poses under the left
+ *                 perturbation T <- Exp(xi) T, xi = (rho, phi) (0 for fixed);
+ *   grad_depths0  : float32 [P], dL/d(initial inverse depth).
+ * The bound targets/weights buffers must hold the values the tape was
+ * recorded with; the poses/patches buffers are not read.  Errors:
+ * BA_ERR_STATE without a tape, BA_ERR_INVALID_ARG for misaligned outputs,
+ * BA_ERR_OOM; device-detected errors (BA_ERR_NOT_SPD) come from ba_sync. */
+DPVBA_API ba_status_t ba_backward(ba_handle_t h, const double* grad_poses, const float* grad_depths,
+                                  float* grad_targets, float* grad_weights, double* grad_tangent0,
+                                  float* grad_depths0);
 
 /* ---- allocation-free pose-system solve ---------------------------------- */
 

@@ -74,6 +74,30 @@ class DPVBA:
         except Exception:
             pass
 
+    # --------------------------------------------------------------- adjoint
+    def set_record(self, on: bool = True):
+        """Record the following ``step`` calls as the tape of ``backward``."""
+        capi.check(self._h, self._lib.ba_set_record(self._h, 1 if on else 0))
+
+    def backward(self, grad_poses=None, grad_depths=None, initial: bool = False):
+        """Reverse-mode pass over the recorded step: returns (grad_targets,
+        grad_weights) as float32 [E,2]; with ``initial`` also the cotangents of
+        the initial state, (grad_tangent0 float64 [N,6], grad_depths0 float32 [P]).
+        ``grad_poses`` is float64 [N,7] (d loss / d(t, q) of the final poses),
+        ``grad_depths`` float32 [P] (d loss / d final inverse depth)."""
+        dev = self._keep[0].device
+        if grad_poses is not None:
+            grad_poses = grad_poses.to(device=dev, dtype=torch.float64).contiguous()
+        if grad_depths is not None:
+            grad_depths = grad_depths.to(device=dev, dtype=torch.float32).contiguous()
+        gT = torch.empty((self.E, 2), dtype=torch.float32, device=dev)
+        gW = torch.empty((self.E, 2), dtype=torch.float32, device=dev)
+        x0 = torch.empty((self.N, 6), dtype=torch.float64, device=dev) if initial else None
+        d0 = torch.empty(self.P, dtype=torch.float32, device=dev) if initial else None
+        capi.check(self._h, self._lib.ba_backward(self._h, _ptr(grad_poses), _ptr(grad_depths), _ptr(gT), _ptr(gW),
+                                                  _ptr(x0), _ptr(d0)))
+        return (gT, gW, x0, d0) if initial else (gT, gW)
+
     # ------------------------------------------------------------ inspection
     def linearize(self, fixed: int):
         capi.check(self._h, self._lib.ba_linearize(self._h, fixed))
@@ -119,6 +143,41 @@ class DPVBA:
         n = ctypes.c_int()
         capi.check(self._h, self._lib.ba_debug_keys(self._h, fixed, _ptr(out), cap, ctypes.byref(n)))
         return out[:n.value]
+
+
+class BAFunction(torch.autograd.Function):
+    """The bundle adjustment as a differentiable layer: ``iters`` Gauss-Newton
+    iterations from (poses, patches) with the given targets and weights,
+    returning the final poses (float64 [N,7]) and inverse depths (float32 [P]).
+    Gradients flow to ``targets`` and ``weights`` (the update operator's
+    outputs); the initial poses and patches are treated as constants."""
+
+    @staticmethod
+    def forward(ctx, targets, weights, poses, patches, ii, jj, kk, intrinsics, iters, fixed, opts):
+        targets = targets.detach().contiguous()
+        weights = weights.detach().contiguous()
+        T = poses.detach().clone().contiguous()
+        Pt = patches.detach().clone().contiguous()
+        ba = DPVBA(**(opts or {}))
+        ba.set_graph(T, Pt, ii.contiguous(), jj.contiguous(), kk.contiguous(), targets, weights,
+                     intrinsics.contiguous())
+        ba.set_record(True)
+        ba.step(iters, fixed)
+        ba.sync()
+        ctx.ba = ba
+        return T, Pt[:, 2, 1, 1].clone()
+
+    @staticmethod
+    def backward(ctx, grad_poses, grad_depths):
+        ba = ctx.ba
+        gT, gW = ba.backward(grad_poses, grad_depths)
+        ba.sync()
+        return gT, gW, None, None, None, None, None, None, None, None, None
+
+
+def bundle_adjust(targets, weights, poses, patches, ii, jj, kk, intrinsics, iters, fixed, **opts):
+    """Functional form of ``BAFunction`` (keyword options as for ``DPVBA``)."""
+    return BAFunction.apply(targets, weights, poses, patches, ii, jj, kk, intrinsics, iters, fixed, opts)
 
 
 def scene_tensors(scene, device="cuda") -> dict:

@@ -37,9 +37,9 @@ class BAOptions(ctypes.Structure):
 EXPORTED = [
     "ba_default_options", "ba_create", "ba_destroy", "ba_set_stream", "ba_set_graph", "ba_step", "ba_sync",
     "ba_last_error", "ba_status_string", "ba_linearize", "ba_debug_export", "ba_debug_info", "ba_debug_keys",
-    "ba_profile_enable", "ba_profile_read", "ba_solve_pose_system_noalloc",
+    "ba_profile_enable", "ba_profile_read", "ba_set_record", "ba_backward", "ba_solve_pose_system_noalloc",
 ]
-KERNEL_CLASSES = ("preprocess", "init", "assemble", "solve", "backsub", "retract")
+KERNEL_CLASSES = ("preprocess", "init", "assemble", "solve", "backsub", "retract", "adjoint")
 
 
 class BAError(RuntimeError):
@@ -78,6 +78,8 @@ def lib():
         L.ba_debug_keys.argtypes = [H, i, P, i, ctypes.POINTER(ctypes.c_int)]
         L.ba_profile_enable.argtypes = [H, i]
         L.ba_profile_read.argtypes = [H, i, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]
+        L.ba_set_record.argtypes = [H, i]
+        L.ba_backward.argtypes = [H, P, P, P, P, P, P]
         L.ba_solve_pose_system_noalloc.argtypes = [i, P, P, P, i, P]
         for name in EXPORTED:
             if name not in ("ba_last_error", "ba_status_string"):

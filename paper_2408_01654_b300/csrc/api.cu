@@ -56,23 +56,6 @@ long long dpv_large_scratch_floats(int n_pad);
 namespace {
 
 template <class T>
-ba_status_t grow(ba_handle_t h, DBuf<T>& b, long long need, const char* what) {
-  need = std::max<long long>(need, 1);
-  if (need <= b.cap && b.p) return BA_OK;
-  if (b.p) cudaFree(b.p);
-  b.p = nullptr;
-  b.cap = 0;
-  cudaError_t e = cudaMalloc((void**)&b.p, sizeof(T) * (size_t)need);
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    b.p = nullptr;
-    return dpv_fail(h, BA_ERR_OOM, std::string("allocating ") + what + ": " + cudaGetErrorString(e));
-  }
-  b.cap = need;
-  return BA_OK;
-}
-
-template <class T>
 void release(DBuf<T>& b) {
   if (b.p) cudaFree(b.p);
   b.p = nullptr;
@@ -114,15 +97,17 @@ ba_status_t ensure_system(ba_handle_t h, int fixed) {
   system_geometry(h->n, h->TS, h->T, h->n_pad);
   const long long nS = (long long)h->T * (h->T + 1) / 2 * h->TS * h->TS;
   ba_status_t s;
-  if ((s = grow(h, ws->S, nS, "pose system")) || (s = grow(h, ws->y, h->n_pad, "rhs")) ||
-      (s = grow(h, ws->dx, h->n_pad, "step")) || (s = grow(h, ws->r64, h->n_pad, "residual")) ||
-      (s = grow(h, ws->tmpv, h->n_pad, "vector")))
+  if ((s = dpv_grow(h, ws->S, nS, "pose system")) || (s = dpv_grow(h, ws->y, h->n_pad, "rhs")) ||
+      (s = dpv_grow(h, ws->dx, h->n_pad, "step")) || (s = dpv_grow(h, ws->r64, h->n_pad, "residual")) ||
+      (s = dpv_grow(h, ws->tmpv, h->n_pad, "vector")))
     return s;
-  if (h->n > DPV_SMALL_N && (s = grow(h, ws->L, dpv_large_scratch_floats(h->n_pad), "factor"))) return s;
+  if (h->n > DPV_SMALL_N && (s = dpv_grow(h, ws->L, dpv_large_scratch_floats(h->n_pad), "factor"))) return s;
   return BA_OK;
 }
 
 }  // namespace
+
+ba_status_t dpv_ensure_system(ba_handle_t h, int fixed) { return ensure_system(h, fixed); }
 
 extern "C" {
 
@@ -198,6 +183,9 @@ ba_status_t ba_destroy(ba_handle_t h) {
     release(ws->scan); release(ws->S); release(ws->y); release(ws->dx); release(ws->Ct); release(ws->wk);
     release(ws->dd); release(ws->L); release(ws->r64); release(ws->tmpv); release(ws->pmpos); release(ws->pptr);
     release(ws->pterm); release(ws->posef);
+    release(ws->tp_poses); release(ws->tp_patches); release(ws->tp_dx); release(ws->tp_dd);
+    release(ws->ad_xb); release(ws->ad_w); release(ws->ad_gd); release(ws->ad_lamd); release(ws->ad_v);
+    release(ws->ad_gt); release(ws->ad_gw);
     delete ws;
   }
   prof_clear(h);
@@ -262,22 +250,23 @@ ba_status_t ba_set_graph(ba_handle_t h, int N, int P, int E, double* poses, floa
   h->G = h->opt.patches_per_group > 0 ? h->opt.patches_per_group : auto_group(h, P);
   h->ngroups = (P + h->G - 1) / h->G;
   h->fixed = -1;
+  h->tape_valid = 0;
   h->kk_bits = bits_for((unsigned long long)P);
   ba_status_t s;
   const long long En = std::max(E, 1);
   const long long Gn = h->ngroups + 1;
   const long long scan_need = std::max(dpv_scan_scratch(En + 1), dpv_scan_scratch(dpv_hist_entries(En)));
-  if ((s = grow(h, ws->src, P, "patch table")) || (s = grow(h, ws->Ct, P, "Ct")) || (s = grow(h, ws->wk, P, "w")) ||
-      (s = grow(h, ws->dd, P, "dd")) || (s = grow(h, ws->keys0, En, "sort keys")) ||
-      (s = grow(h, ws->keys1, En, "sort keys")) || (s = grow(h, ws->vals0, En, "sort values")) ||
-      (s = grow(h, ws->vals1, En, "sort values")) || (s = grow(h, ws->perm, En, "permutation")) ||
-      (s = grow(h, ws->eslot, En, "slots")) || (s = grow(h, ws->grun, Gn * (DPV_RMAX + 1), "run tables")) ||
-      (s = grow(h, ws->gnr, Gn, "run counts")) ||
-      (s = grow(h, ws->hist, dpv_hist_entries(En), "histograms")) || (s = grow(h, ws->scan, scan_need, "scan")) ||
-      (s = grow(h, ws->gptr, Gn, "groups")) ||
-      (s = grow(h, ws->win, Gn * DPV_WMAX, "windows")) || (s = grow(h, ws->wlen, Gn, "windows")) ||
-      (s = grow(h, ws->pmpos, En, "patch-major positions")) || (s = grow(h, ws->pptr, (long long)P + 1, "patch CSR")) ||
-      (s = grow(h, ws->pterm, 4 * En, "edge depth terms")) || (s = grow(h, ws->posef, 16LL * N, "pose table")))
+  if ((s = dpv_grow(h, ws->src, P, "patch table")) || (s = dpv_grow(h, ws->Ct, P, "Ct")) || (s = dpv_grow(h, ws->wk, P, "w")) ||
+      (s = dpv_grow(h, ws->dd, P, "dd")) || (s = dpv_grow(h, ws->keys0, En, "sort keys")) ||
+      (s = dpv_grow(h, ws->keys1, En, "sort keys")) || (s = dpv_grow(h, ws->vals0, En, "sort values")) ||
+      (s = dpv_grow(h, ws->vals1, En, "sort values")) || (s = dpv_grow(h, ws->perm, En, "permutation")) ||
+      (s = dpv_grow(h, ws->eslot, En, "slots")) || (s = dpv_grow(h, ws->grun, Gn * (DPV_RMAX + 1), "run tables")) ||
+      (s = dpv_grow(h, ws->gnr, Gn, "run counts")) ||
+      (s = dpv_grow(h, ws->hist, dpv_hist_entries(En), "histograms")) || (s = dpv_grow(h, ws->scan, scan_need, "scan")) ||
+      (s = dpv_grow(h, ws->gptr, Gn, "groups")) ||
+      (s = dpv_grow(h, ws->win, Gn * DPV_WMAX, "windows")) || (s = dpv_grow(h, ws->wlen, Gn, "windows")) ||
+      (s = dpv_grow(h, ws->pmpos, En, "patch-major positions")) || (s = dpv_grow(h, ws->pptr, (long long)P + 1, "patch CSR")) ||
+      (s = dpv_grow(h, ws->pterm, 4 * En, "edge depth terms")) || (s = dpv_grow(h, ws->posef, 16LL * N, "pose table")))
     return s;
   DPV_CUDA(h, cudaMemsetAsync(ws->status, 0, sizeof(int), h->stream));
   DPV_CUDA(h, cudaMemcpyAsync(ws->intr, intrinsics, 4 * sizeof(float), cudaMemcpyDefault, h->stream));
@@ -303,9 +292,16 @@ ba_status_t ba_step(ba_handle_t h, int iters, int fixed_poses) {
   if (iters < 0) return dpv_fail(h, BA_ERR_INVALID_ARG, "iters < 0");
   if ((s = ensure_system(h, fixed_poses))) return s;
   h->last_iters = iters;
-  if (iters == 0 || h->n == 0) return BA_OK;
-  DPV_CUDA(h, cudaMemsetAsync(h->ws->cost, 0, sizeof(double) * h->ws->cost_cap, h->stream));
-  for (int it = 0; it < iters; ++it) {
+  const int run = (iters > 0 && h->n > 0) ? iters : 0;
+  if (h->record) {
+    // this call becomes the tape of ba_backward
+    h->tape_valid = 0;
+    h->tape_iters_pending = run;
+    if ((s = dpv_tape_reserve(h, run))) return s;
+  }
+  if (run > 0) DPV_CUDA(h, cudaMemsetAsync(h->ws->cost, 0, sizeof(double) * h->ws->cost_cap, h->stream));
+  for (int it = 0; it < run; ++it) {
+    if (h->record && (s = dpv_tape_state(h, it))) return s;
     if ((s = dpv_assemble(h, it))) return s;
     int retracted = 0;
     dpv_prof_begin(h, BA_KERNEL_SOLVE);
@@ -317,6 +313,13 @@ ba_status_t ba_step(ba_handle_t h, int iters, int fixed_poses) {
     s = dpv_backsub(h, !retracted);
     dpv_prof_end(h);
     if (s) return s;
+    if (h->record && (s = dpv_tape_step(h, it))) return s;
+  }
+  if (h->record) {
+    if ((s = dpv_tape_state(h, run))) return s;
+    h->tape_iters = run;
+    h->tape_fixed = fixed_poses;
+    h->tape_valid = 1;
   }
   return BA_OK;
 }

@@ -67,7 +67,7 @@ __global__ void __launch_bounds__(AS_THREADS) k_assemble(
     const int* __restrict__ wlen, const float* __restrict__ posef, const float* __restrict__ patches,
     const float* __restrict__ targets, const float* __restrict__ weights, const float* __restrict__ intr,
     float4* __restrict__ pterm, double* __restrict__ S, double* __restrict__ y, float* __restrict__ Ct_out,
-    float* __restrict__ wk_out, double* __restrict__ cost, int* status) {
+    float* __restrict__ wk_out, double* __restrict__ cost, const float* __restrict__ w_ext, int* status) {
   extern __shared__ float sm[];
   if (dpv_status(status)) return;
   const int g = blockIdx.x;
@@ -211,7 +211,7 @@ __global__ void __launch_bounds__(AS_THREADS) k_assemble(
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) cst += __shfl_xor_sync(0xffffffffu, cst, o);
-  if (lane == 0 && cst != 0.f) atomicAdd(cost, (double)cst);
+  if (cost && lane == 0 && cst != 0.f) atomicAdd(cost, (double)cst);
   __syncthreads();
 
   // ---- phase 2: per patch e_k, C_k, w_k (compensated) ---------------------
@@ -237,7 +237,8 @@ __global__ void __launch_bounds__(AS_THREADS) k_assemble(
         df_add(wv, d.y);
       }
     }
-    const float ct = df_val(C), wf_ = df_val(wv);
+    const float ct = df_val(C);
+    const float wf_ = w_ext ? (k < P ? w_ext[k] : 0.f) : df_val(wv);
 #pragma unroll
     for (int m = 0; m < 6; ++m) col[6 * si + m] += df_val(ei[m]);
     const float s = 1.0f / sqrtf(ct);
@@ -282,7 +283,7 @@ __global__ void __launch_bounds__(AS_THREADS) k_assemble(
     const int fa = wf[a];
     if (fa < fixed) continue;
     DF acc = {0.f, 0.f};
-    for (int r = 0; r < nruns; ++r) {
+    for (int r = 0; r < nruns && !w_ext; ++r) {  // with an external right-hand side v comes from y's init
       const int si = rsl[r] & 0xff, sj = rsl[r] >> 8;
       if (si == sj) continue;
       const float2* rv = runv + r * NV;
@@ -297,9 +298,9 @@ __global__ void __launch_bounds__(AS_THREADS) k_assemble(
 // S <- 0 (lambda_p on the free diagonal, 1 on the padding diagonal), y <- 0,
 // and the per-pose table for this iteration: R (FP32) and the camera centre
 // c = -R^T t as a double-float pair, formed in FP64 from the FP64 pose.
-__global__ void k_init_system(double* __restrict__ S, size_t nS, double* __restrict__ y, int n_pad,
-                              const double* __restrict__ poses, int N, float* __restrict__ posef,
-                              const int* status) {
+__global__ void k_init_system(double* __restrict__ S, size_t nS, double* __restrict__ y, int n_pad, int n,
+                              const double* __restrict__ y_init, const double* __restrict__ poses, int N,
+                              float* __restrict__ posef, const int* status) {
   if (dpv_status(status)) return;
   const size_t stride = (size_t)gridDim.x * blockDim.x;
   const size_t gid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -321,7 +322,7 @@ __global__ void k_init_system(double* __restrict__ S, size_t nS, double* __restr
   }
   double2* S2 = reinterpret_cast<double2*>(S);
   for (size_t q = gid; q < nS / 2; q += stride) S2[q] = make_double2(0.0, 0.0);
-  for (size_t q = gid; q < (size_t)n_pad; q += stride) y[q] = 0.0;
+  for (size_t q = gid; q < (size_t)n_pad; q += stride) y[q] = (y_init && q < (size_t)n) ? y_init[q] : 0.0;
 }
 
 __global__ void k_init_diag(double* __restrict__ S, int n, int n_pad, int TS, float lambda_p, const int* status) {
@@ -361,25 +362,29 @@ ba_status_t upload_tables(ba_handle_t h) {
 
 }  // namespace
 
-ba_status_t dpv_assemble(ba_handle_t h, int it) {
+ba_status_t dpv_assemble(ba_handle_t h, int it) { return dpv_assemble_ext(h, it, nullptr, nullptr); }
+
+// Assembly with an external right-hand side (the adjoint): y = v_ext - E Ct^-1 w_ext
+// instead of the residual-based v and w.  Both null: the normal assembly.
+ba_status_t dpv_assemble_ext(ba_handle_t h, int it, const double* v_ext, const float* w_ext) {  // it < 0: no cost
   Workspace* ws = h->ws;
   ba_status_t s = upload_tables(h);
   if (s) return s;
   const size_t nS = (size_t)h->T * (h->T + 1) / 2 * h->TS * h->TS;
   dpv_prof_begin(h, BA_KERNEL_INIT);
-  k_init_system<<<2 * h->num_sms, 256, 0, h->stream>>>(ws->S.p, nS, ws->y.p, h->n_pad, h->poses, h->N,
+  k_init_system<<<2 * h->num_sms, 256, 0, h->stream>>>(ws->S.p, nS, ws->y.p, h->n_pad, h->n, v_ext, h->poses, h->N,
                                                         ws->posef.p, ws->status);
   ++h->launches;
   k_init_diag<<<(h->n_pad + 255) / 256, 256, 0, h->stream>>>(ws->S.p, h->n, h->n_pad, h->TS, h->opt.lambda_pose,
                                                               ws->status);
   ++h->launches;
   dpv_prof_end(h);
-  double* cost = ws->cost + (it < ws->cost_cap ? it : ws->cost_cap - 1);
+  double* cost = it < 0 ? nullptr : ws->cost + (it < ws->cost_cap ? it : ws->cost_cap - 1);
   dpv_prof_begin(h, BA_KERNEL_ASSEMBLE);
   k_assemble<<<h->ngroups, AS_THREADS, assemble_smem_bytes(h->G), h->stream>>>(
       h->G, h->P, h->fixed, h->TS, h->opt.lambda_depth, h->opt.z_min, ws->gptr.p, ws->grun.p, ws->gnr.p, ws->eslot.p,
       ws->perm.p, ws->pmpos.p, ws->pptr.p, ws->win.p, ws->wlen.p, ws->posef.p, h->patches, h->targets, h->weights,
-      ws->intr, ws->pterm.p, ws->S.p, ws->y.p, ws->Ct.p, ws->wk.p, cost, ws->status);
+      ws->intr, ws->pterm.p, ws->S.p, ws->y.p, ws->Ct.p, ws->wk.p, cost, w_ext, ws->status);
   ++h->launches;
   dpv_prof_end(h);
   DPV_CUDA(h, cudaGetLastError());

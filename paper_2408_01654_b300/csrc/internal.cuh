@@ -66,6 +66,13 @@ struct ba_handle_s {
   int prof_open = -1;
 
   long long launches = 0;  // kernels launched by this handle so far
+
+  // tape of the last recorded ba_step (ba_set_record / ba_backward)
+  int record = 0;
+  int tape_valid = 0;
+  int tape_iters = 0;
+  int tape_fixed = 0;
+  int tape_iters_pending = 0;
 };
 
 // A device buffer owned by the handle, grown on demand (never shrunk).
@@ -108,12 +115,42 @@ struct Workspace {
   DBuf<float> L;                  // factor (large n)
   DBuf<double> r64;               // [n_pad]
   DBuf<float> tmpv;               // [n_pad]
+  // tape of a recorded ba_step: states before each iteration (+ the final poses) and the steps
+  DBuf<double> tp_poses;          // [iters+1][N][7]
+  DBuf<float> tp_patches;         // [iters][P][27]
+  DBuf<double> tp_dx;             // [iters][n]
+  DBuf<float> tp_dd;              // [iters][P]
+  // adjoint pass
+  DBuf<double> ad_xb;             // [2][N][6] pose cotangents (tangent space), double-buffered
+  DBuf<float> ad_w;               // [2][P] depth cotangents that pass the clamp, double-buffered
+  DBuf<float> ad_gd;              // [E] per-edge depth cotangents, patch-major
+  DBuf<float> ad_lamd;            // [P] depth part of the adjoint solve
+  DBuf<double> ad_v;              // [n_pad] pose part of the adjoint right-hand side
+  DBuf<float> ad_gt, ad_gw;       // [E][2] scratch when the caller passes no output
 };
 
 // ---------------------------------------------------------------------------
 // host helpers
 // ---------------------------------------------------------------------------
 ba_status_t dpv_fail(ba_handle_t h, ba_status_t s, const std::string& msg);
+
+// grow a handle-owned device buffer to at least `need` elements (contents not kept)
+template <class T>
+ba_status_t dpv_grow(ba_handle_t h, DBuf<T>& b, long long need, const char* what) {
+  need = need < 1 ? 1 : need;
+  if (need <= b.cap && b.p) return BA_OK;
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.cap = 0;
+  cudaError_t e = cudaMalloc((void**)&b.p, sizeof(T) * (size_t)need);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    b.p = nullptr;
+    return dpv_fail(h, BA_ERR_OOM, std::string("allocating ") + what + ": " + cudaGetErrorString(e));
+  }
+  b.cap = need;
+  return BA_OK;
+}
 #define DPV_CUDA(h, call)                                                              \
   do {                                                                                 \
     cudaError_t _e = (call);                                                           \
@@ -135,6 +172,12 @@ long long dpv_scan_scratch(long long n);
 long long dpv_hist_entries(long long m);
 // one GN iteration (assemble.cu, solve_*.cu, update.cu)
 ba_status_t dpv_assemble(ba_handle_t h, int it);
+ba_status_t dpv_assemble_ext(ba_handle_t h, int it, const double* v_ext, const float* w_ext);
+ba_status_t dpv_ensure_system(ba_handle_t h, int fixed);
+ba_status_t dpv_tape_reserve(ba_handle_t h, int iters);
+ba_status_t dpv_tape_state(ba_handle_t h, int it);
+ba_status_t dpv_tape_step(ba_handle_t h, int it);
+ba_status_t dpv_backsub_ext(ba_handle_t h, const float* w_ext, float* out);
 ba_status_t dpv_solve(ba_handle_t h, int* retracted);  // retracted: poses already updated
 ba_status_t dpv_backsub(ba_handle_t h, int retract);  // retract: also update the poses
 ba_status_t dpv_retract(ba_handle_t h);

@@ -19,7 +19,7 @@ __global__ void k_backsub(int P, int G, int fixed, float d_min, const int* __res
                           const float4* __restrict__ pterm, const int* __restrict__ win,
                           const float* __restrict__ dxf, const float* __restrict__ Ct, const float* __restrict__ wk,
                           float* __restrict__ patches, float* __restrict__ dd_out, int N, const double* __restrict__ dx,
-                          double* __restrict__ poses, const int* status) {
+                          double* __restrict__ poses, int write_depth, const int* status) {
   if (dpv_status(status)) return;
   if (N > fixed && blockIdx.x == gridDim.x - 1) {
     // the extra last CTA retracts the free poses (FP64) while the others back-substitute
@@ -48,9 +48,10 @@ __global__ void k_backsub(int P, int G, int fixed, float d_min, const int* __res
     }
   }
   const float dd = df_val(acc) / Ct[k];
+  dd_out[k] = dd;
+  if (!write_depth) return;
   float* pk = patches + 27 * (size_t)k;
   const float dn = fmaxf(pk[22] + dd, d_min);
-  dd_out[k] = dd;
 #pragma unroll
   for (int m = 18; m < 27; ++m) pk[m] = dn;
 }
@@ -72,7 +73,20 @@ ba_status_t dpv_backsub(ba_handle_t h, int retract) {
   const int nb = (h->P + 127) / 128 + (retract ? 1 : 0);
   k_backsub<<<nb, 128, 0, h->stream>>>(h->P, h->G, h->fixed, h->opt.d_min, ws->pptr.p, ws->pterm.p, ws->win.p,
                                        ws->tmpv.p, ws->Ct.p, ws->wk.p, h->patches, ws->dd.p,
-                                       retract ? h->N : h->fixed, ws->dx.p, h->poses, ws->status);
+                                       retract ? h->N : h->fixed, ws->dx.p, h->poses, 1, ws->status);
+  ++h->launches;
+  DPV_CUDA(h, cudaGetLastError());
+  return BA_OK;
+}
+
+// The adjoint's depth part of lambda: out_k = Ct_k^-1 (w_ext_k - sum_a e_ak^T lambda_a),
+// with lambda_a in the solver's output; no state is changed.
+ba_status_t dpv_backsub_ext(ba_handle_t h, const float* w_ext, float* out) {
+  Workspace* ws = h->ws;
+  const int nb = (h->P + 127) / 128;
+  k_backsub<<<nb, 128, 0, h->stream>>>(h->P, h->G, h->fixed, h->opt.d_min, ws->pptr.p, ws->pterm.p, ws->win.p,
+                                       ws->tmpv.p, ws->Ct.p, w_ext, h->patches, out, h->fixed, ws->dx.p, h->poses, 0,
+                                       ws->status);
   ++h->launches;
   DPV_CUDA(h, cudaGetLastError());
   return BA_OK;
