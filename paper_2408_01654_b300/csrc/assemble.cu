@@ -25,16 +25,21 @@
 //            the global tiled S with red.global.add.f64 (likewise y).
 //
 // Why compensated sums: S is the small difference of two large, nearly equal
-// sums (B and E Ct^-1 E^T).  Rounding each FP32 product is harmless, but FP32
-// rounding of the sums costs ~1e-5 of the step on odometry windows; TwoSum /
-// TwoProd ("double-float") sums inside the group remove it.  The sum across
-// groups (up to ~150 groups per entry with small groups) is carried in FP64
-// by the L2 atomics: in FP32 it alone costs ~6e-6 of the step.
+// sums (B and E Ct^-1 E^T).  Rounding each FP32 product is harmless; each
+// group's compensated contribution goes to FP64 whole (rounding it to FP32
+// costs 1.3e-5 of the step at 708 unknowns) and the sum across groups (up to
+// ~150 groups per entry with small groups) is carried in FP64 by the L2
+// atomics (in FP32 it alone costs ~6e-6 of the step).  Inside
+// a group the long sums (run blocks over a run's edges, the window product
+// over the group's patches) are Kahan-compensated with the product fused into
+// the compensation step; the short per-patch sums use TwoSum pairs.  The FP64
+// operand of each atomic is built from the pair with integer conversions and
+// one FP64 add (FP64 arithmetic runs at ~1/64 of the FP32 rate on this part).
 #include "internal.cuh"
 
 namespace {
 
-constexpr int AS_THREADS = 256;
+constexpr int AS_THREADS = 512;
 constexpr int AS_WARPS = AS_THREADS / 32;
 constexpr int EH_STRIDE = 6 * DPV_WMAX + 1;  // floats per patch column of E_hat
 constexpr int NV = 90;                       // run block entries: Hii 21, Hij 36, Hjj 21, vi 6, vj 6
@@ -45,6 +50,10 @@ constexpr int ROWF = 27;                     // staged floats per edge: 13 per r
 __constant__ unsigned char c_pa[NV], c_pb[NV];
 
 __host__ __device__ constexpr int tri(int r, int c) { return r * (r + 1) / 2 + c; }
+
+// the phase-2b tables live in the phase-1 staging rows
+static_assert(DPV_WMAX * DPV_WMAX + 8 * (DPV_WMAX * 21 + DPV_WMAX * 6) <= 4 * AS_WARPS * 32 * ROWF,
+              "phase-2b tables exceed the staging space");
 
 size_t assemble_smem_bytes(int G) {
   return sizeof(float) * ((size_t)DPV_RMAX * NV * 2 + (size_t)DPV_RMAX * 21 + (size_t)G * EH_STRIDE + 2 * G +
@@ -126,6 +135,15 @@ __global__ void __launch_bounds__(AS_THREADS) k_assemble(
   // ---- phase 1: one warp per run ------------------------------------------
   float cst = 0.f;
   float* rw = rows + wid * 32 * ROWF;
+  // this lane's run entries q = lane + 32 t: staged-row operands, read once
+  // (lanes read different table entries, which the constant cache serialises)
+  int pa[3], pb[3];
+#pragma unroll
+  for (int t = 0; t < 3; ++t) {
+    const int q = lane + 32 * t;
+    pa[t] = q < NV ? c_pa[q] : 0;
+    pb[t] = q < NV ? c_pb[q] : 0;
+  }
   for (int r = wid; r < nruns; r += AS_WARPS) {
     const int s0 = gs + runptr[r], s1 = gs + runptr[r + 1];
     const int si = rsl[r] & 0xff, sj = rsl[r] >> 8;
@@ -140,9 +158,9 @@ __global__ void __launch_bounds__(AS_THREADS) k_assemble(
 #pragma unroll
       for (int m = 0; m < 9; ++m) T.txR[m] = o[12 + m];
     }
-    DF acc[3];
+    KS acc[3];
 #pragma unroll
-    for (int t = 0; t < 3; ++t) acc[t] = DF{0.f, 0.f};
+    for (int t = 0; t < 3; ++t) acc[t] = KS{0.f, 0.f};
     for (int b = s0; b < s1; b += 32) {
       const int s = b + lane;
       const int nb = min(32, s1 - b);
@@ -193,11 +211,9 @@ __global__ void __launch_bounds__(AS_THREADS) k_assemble(
         const float* re = rw + e * ROWF;
 #pragma unroll
         for (int t = 0; t < 3; ++t) {
-          const int q = lane + 32 * t;
-          if (q < NV) {
-            const int pa = c_pa[q], pb = c_pb[q];
-            df_fma(acc[t], re[pa], re[pb]);
-            df_fma(acc[t], re[13 + pa], re[13 + pb]);
+          if (lane + 32 * t < NV) {
+            ks_fma(acc[t], re[pa[t]], re[pb[t]]);
+            ks_fma(acc[t], re[13 + pa[t]], re[13 + pb[t]]);
           }
         }
       }
@@ -206,7 +222,7 @@ __global__ void __launch_bounds__(AS_THREADS) k_assemble(
 #pragma unroll
     for (int t = 0; t < 3; ++t) {
       const int q = lane + 32 * t;
-      if (q < NV) runv[r * NV + q] = make_float2(acc[t].hi, acc[t].lo);
+      if (q < NV) runv[r * NV + q] = make_float2(acc[t].s, -acc[t].c);
     }
   }
 #pragma unroll
@@ -215,15 +231,18 @@ __global__ void __launch_bounds__(AS_THREADS) k_assemble(
   __syncthreads();
 
   // ---- phase 2: per patch e_k, C_k, w_k (compensated) ---------------------
-  for (int q = tid; q < G; q += AS_THREADS) {
+  // one warp per patch, one lane per edge; the target-frame columns of E_hat
+  // are added with shared-memory atomics (two edges of a patch may share a
+  // target), the source-frame column and C, w by a compensated warp sum
+  for (int q = wid; q < G; q += AS_WARPS) {
     const int k = g * G + q;
     float* col = Eh + (size_t)q * EH_STRIDE;
-    DF ei[6], C = {lambda_d, 0.f}, wv = {0.f, 0.f};
+    DF ei[6], C = {0.f, 0.f}, wv = {0.f, 0.f};
 #pragma unroll
     for (int m = 0; m < 6; ++m) ei[m] = DF{0.f, 0.f};
-    int si = 0;
+    int si = -1;
     if (k < P) {
-      for (int p = pptr[k]; p < pptr[k + 1]; ++p) {
+      for (int p = pptr[k] + lane; p < pptr[k + 1]; p += 32) {
         const float4 a = pterm[4 * (size_t)p], b = pterm[4 * (size_t)p + 1], c = pterm[4 * (size_t)p + 2],
                      d = pterm[4 * (size_t)p + 3];
         const int sl = __float_as_int(d.z);
@@ -231,67 +250,158 @@ __global__ void __launch_bounds__(AS_THREADS) k_assemble(
         const int sj = sl >> 8;
         df_add(ei[0], a.x); df_add(ei[1], a.y); df_add(ei[2], a.z);
         df_add(ei[3], a.w); df_add(ei[4], b.x); df_add(ei[5], b.y);
-        col[6 * sj + 0] += b.z; col[6 * sj + 1] += b.w; col[6 * sj + 2] += c.x;
-        col[6 * sj + 3] += c.y; col[6 * sj + 4] += c.z; col[6 * sj + 5] += c.w;
+        float* cj = col + 6 * sj;
+        atomicAdd(cj + 0, b.z); atomicAdd(cj + 1, b.w); atomicAdd(cj + 2, c.x);
+        atomicAdd(cj + 3, c.y); atomicAdd(cj + 4, c.z); atomicAdd(cj + 5, c.w);
         df_add(C, d.x);
         df_add(wv, d.y);
       }
     }
-    const float ct = df_val(C);
-    const float wf_ = w_ext ? (k < P ? w_ext[k] : 0.f) : df_val(wv);
 #pragma unroll
-    for (int m = 0; m < 6; ++m) col[6 * si + m] += df_val(ei[m]);
-    const float s = 1.0f / sqrtf(ct);
-    sc[2 * q] = s;
-    sc[2 * q + 1] = wf_ * s;
-    for (int m = 0; m < nr; ++m) col[m] *= s;
-    if (k < P) {
-      Ct_out[k] = ct;
-      wk_out[k] = wf_;
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+      for (int m = 0; m < 6; ++m) {
+        const DF t = {__shfl_xor_sync(0xffffffffu, ei[m].hi, o), __shfl_xor_sync(0xffffffffu, ei[m].lo, o)};
+        df_add_df(ei[m], t);
+      }
+      const DF tc = {__shfl_xor_sync(0xffffffffu, C.hi, o), __shfl_xor_sync(0xffffffffu, C.lo, o)};
+      const DF tw = {__shfl_xor_sync(0xffffffffu, wv.hi, o), __shfl_xor_sync(0xffffffffu, wv.lo, o)};
+      df_add_df(C, tc);
+      df_add_df(wv, tw);
+      si = max(si, __shfl_xor_sync(0xffffffffu, si, o));
+    }
+    df_add(C, lambda_d);
+    __syncwarp();
+    // lane 0's sums for every lane (the butterfly may differ in the last bit across lanes)
+    const float ct = __shfl_sync(0xffffffffu, df_val(C), 0);
+    const float wf_ = w_ext ? (k < P ? w_ext[k] : 0.f) : __shfl_sync(0xffffffffu, df_val(wv), 0);
+    if (lane == 0 && si >= 0) {
+#pragma unroll
+      for (int m = 0; m < 6; ++m) col[6 * si + m] += df_val(ei[m]);
+    }
+    __syncwarp();
+    const float sq = 1.0f / sqrtf(ct);
+    for (int m = lane; m < nr; m += 32) col[m] *= sq;
+    if (lane == 0) {
+      sc[2 * q] = sq;
+      sc[2 * q + 1] = wf_ * sq;
+      if (k < P) {
+        Ct_out[k] = ct;
+        wk_out[k] = wf_;
+      }
     }
   }
   __syncthreads();
 
-  // ---- phase 3: window Schur complement into the global S and y -----------
-  const int nent = tri(nr, 0);
-  for (int t = tid; t < nent; t += AS_THREADS) {
-    const int R = tri_row(t), C = t - tri(R, 0);
-    const int a = R / 6, b = C / 6, ra = R - 6 * a, cb = C - 6 * b;
-    const int fa = wf[a], fb = wf[b];
-    if (fa < fixed || fb < fixed) continue;
+  // ---- phase 2b: run sums per window block (in the phase-1 staging space) ---
+  // prt[a * w + b] = the run with (source, target) slots (a, b), or -1;
+  // dgb[a][e] = sum of the runs' Hii (a = source) and Hjj (a = target) lower
+  // entries; yrn[a][m] likewise for vi / vj.
+  signed char* prt = reinterpret_cast<signed char*>(rows);
+  float2* dgb = reinterpret_cast<float2*>(rows + DPV_WMAX * DPV_WMAX / 4);
+  float2* yrn = dgb + DPV_WMAX * 21;
+  for (int q = tid; q < w * w; q += AS_THREADS) prt[q] = -1;
+  __syncthreads();
+  for (int r = tid; r < nruns; r += AS_THREADS) {
+    const int si = rsl[r] & 0xff, sj = rsl[r] >> 8;
+    if (si != sj) prt[si * w + sj] = (signed char)r;
+  }
+  for (int q = tid; q < 27 * w; q += AS_THREADS) {
+    const int a = q / 27, e = q - 27 * a;
+    const int oi = e < 21 ? e : 78 + (e - 21), oj = e < 21 ? 57 + e : 84 + (e - 21);
     DF acc = {0.f, 0.f};
     for (int r = 0; r < nruns; ++r) {
       const int si = rsl[r] & 0xff, sj = rsl[r] >> 8;
       if (si == sj) continue;
       const float2* rv = runv + r * NV;
-      if (a == b) {
-        if (si == a) df_add_df(acc, DF{rv[tri(ra, cb)].x, rv[tri(ra, cb)].y});
-        if (sj == a) df_add_df(acc, DF{rv[57 + tri(ra, cb)].x, rv[57 + tri(ra, cb)].y});
-      } else {
-        if (si == a && sj == b) df_add_df(acc, DF{rv[21 + 6 * ra + cb].x, rv[21 + 6 * ra + cb].y});
-        if (si == b && sj == a) df_add_df(acc, DF{rv[21 + 6 * cb + ra].x, rv[21 + 6 * cb + ra].y});
+      if (si == a) df_add_df(acc, DF{rv[oi].x, rv[oi].y});
+      if (sj == a) df_add_df(acc, DF{rv[oj].x, rv[oj].y});
+    }
+    if (e < 21) dgb[a * 21 + e] = make_float2(acc.hi, acc.lo);
+    else yrn[a * 6 + (e - 21)] = make_float2(acc.hi, acc.lo);
+  }
+  __syncthreads();
+
+  // ---- phase 3: window Schur complement into the global S and y -----------
+  // one thread per 3x3 sub-block (rows 3ha.. of frame a, columns 3hb.. of
+  // frame b, a >= b): nine independent compensated sums over the patches.
+  const int nblk = tri(w, 0);
+  for (int t = tid; t < 4 * nblk; t += AS_THREADS) {
+    const int blk = t >> 2, ha = (t >> 1) & 1, hb = t & 1;
+    const int a = tri_row(blk), b = blk - tri(a, 0);
+    if (a == b && hb > ha) continue;
+    const int fa = wf[a], fb = wf[b];
+    if (fa < fixed || fb < fixed) continue;
+    const int R0 = 6 * a + 3 * ha, C0 = 6 * b + 3 * hb;
+    DF acc[3][3];
+    {
+      KS ks[3][3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) ks[i][j] = KS{0.f, 0.f};
+      for (int kl = 0; kl < G; ++kl) {
+        const float* col = Eh + (size_t)kl * EH_STRIDE;
+        const float er[3] = {-col[R0], -col[R0 + 1], -col[R0 + 2]};
+        const float ec[3] = {col[C0], col[C0 + 1], col[C0 + 2]};
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+          for (int j = 0; j < 3; ++j) ks_fma(ks[i][j], er[i], ec[j]);
+      }
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) acc[i][j] = ks_df(ks[i][j]);
+    }
+    if (a == b) {
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+          if (3 * hb + j <= 3 * ha + i) {
+            const float2 v = dgb[a * 21 + tri(3 * ha + i, 3 * hb + j)];
+            df_add_df(acc[i][j], DF{v.x, v.y});
+          }
+    } else {
+      const int r1 = prt[a * w + b], r2 = prt[b * w + a];
+      if (r1 >= 0) {  // run a -> b: Hij rows belong to a
+        const float2* rv = runv + r1 * NV + 21;
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+          for (int j = 0; j < 3; ++j) {
+            const float2 v = rv[6 * (3 * ha + i) + 3 * hb + j];
+            df_add_df(acc[i][j], DF{v.x, v.y});
+          }
+      }
+      if (r2 >= 0) {  // run b -> a: Hij rows belong to b (transposed)
+        const float2* rv = runv + r2 * NV + 21;
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+          for (int j = 0; j < 3; ++j) {
+            const float2 v = rv[6 * (3 * hb + j) + 3 * ha + i];
+            df_add_df(acc[i][j], DF{v.x, v.y});
+          }
       }
     }
-    for (int kl = 0; kl < G; ++kl) {
-      const float* col = Eh + (size_t)kl * EH_STRIDE;
-      df_fma(acc, -col[R], col[C]);
-    }
-    dpv_red_add(S + dpv_s_index(6 * (fa - fixed) + ra, 6 * (fb - fixed) + cb, TS), (double)acc.hi + (double)acc.lo);
+    const int gr = 6 * (fa - fixed) + 3 * ha, gc = 6 * (fb - fixed) + 3 * hb;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j)
+        if (a != b || 3 * hb + j <= 3 * ha + i)
+          dpv_red_add(S + dpv_s_index(gr + i, gc + j, TS), dpv_f2d_bits(acc[i][j].hi) + dpv_f2d_bits(acc[i][j].lo));
   }
   for (int R = tid; R < nr; R += AS_THREADS) {
     const int a = R / 6, ra = R - 6 * a;
     const int fa = wf[a];
     if (fa < fixed) continue;
     DF acc = {0.f, 0.f};
-    for (int r = 0; r < nruns && !w_ext; ++r) {  // with an external right-hand side v comes from y's init
-      const int si = rsl[r] & 0xff, sj = rsl[r] >> 8;
-      if (si == sj) continue;
-      const float2* rv = runv + r * NV;
-      if (si == a) df_add_df(acc, DF{rv[78 + ra].x, rv[78 + ra].y});
-      if (sj == a) df_add_df(acc, DF{rv[84 + ra].x, rv[84 + ra].y});
-    }
+    if (!w_ext) acc = DF{yrn[R].x, yrn[R].y};  // with an external right-hand side v comes from y's init
     for (int kl = 0; kl < G; ++kl) df_fma(acc, -Eh[(size_t)kl * EH_STRIDE + R], sc[2 * kl + 1]);
-    dpv_red_add(y + 6 * (fa - fixed) + ra, (double)acc.hi + (double)acc.lo);
+    dpv_red_add(y + 6 * (fa - fixed) + ra, dpv_f2d_bits(acc.hi) + dpv_f2d_bits(acc.lo));
   }
 }
 

@@ -206,6 +206,21 @@ __device__ __forceinline__ void dpv_red_add(double* p, double v) {
   asm volatile("red.global.add.f64 [%0], %1;" ::"l"(p), "d"(v) : "memory");
 }
 
+// The float as an FP64 value, built with integer operations: B300 runs FP64
+// arithmetic (conversions included) at ~1/64 of the FP32 rate, and the
+// assembly converts several values per thread for its FP64 reductions.  Exact for normal
+// floats; subnormals (|v| < 1.2e-38) become signed zero; inf/NaN stay inf/NaN.
+__device__ __forceinline__ double dpv_f2d_bits(float v) {
+  const unsigned u = __float_as_uint(v);
+  const unsigned e = (u >> 23) & 0xffu;
+  unsigned long long d = (unsigned long long)(u >> 31) << 63;
+  if (e != 0) {
+    const unsigned long long E = e == 255u ? 2047ull : (unsigned long long)(e + 896u);
+    d |= (E << 52) | ((unsigned long long)(u & 0x7fffffu) << 29);
+  }
+  return __longlong_as_double((long long)d);
+}
+
 // rotation matrix of a unit quaternion (x, y, z, w), FP64
 __device__ __forceinline__ void dpv_quat_rot64(const double* q, double* R) {
   const double x = q[0], y = q[1], z = q[2], w = q[3];
@@ -314,6 +329,21 @@ __device__ __forceinline__ void df_add_df(DF& a, const DF& b) {
   a.lo = __fadd_rn(a.lo, b.lo);
 }
 __device__ __forceinline__ float df_val(const DF& a) { return a.hi + a.lo; }
+
+// Kahan-compensated FP32 accumulation of products: value = s - c.  The
+// product is fused into the compensation step (one rounding), so one term
+// costs 4 operations instead of the 10 of df_fma; the error stays
+// 2u sum|x| + O(n u^2) sum|x| (Kahan's bound), independent of the term count.
+struct KS {
+  float s, c;
+};
+__device__ __forceinline__ void ks_fma(KS& a, float x, float y) {
+  const float yv = __fmaf_rn(x, y, -a.c);
+  const float t = __fadd_rn(a.s, yv);
+  a.c = __fsub_rn(__fsub_rn(t, a.s), yv);
+  a.s = t;
+}
+__device__ __forceinline__ DF ks_df(const KS& a) { return DF{a.s, -a.c}; }
 
 // per-pose FP32 data for the relative poses: rotation R (world->camera) and
 // camera centre c = -R^T t in double-float (hi, lo) so that c_i - c_j keeps
