@@ -300,12 +300,15 @@ ba_status_t ba_step(ba_handle_t h, int iters, int fixed_poses) {
     if ((s = dpv_tape_reserve(h, run))) return s;
   }
   if (run > 0) DPV_CUDA(h, cudaMemsetAsync(h->ws->cost, 0, sizeof(double) * h->ws->cost_cap, h->stream));
+  int prepared = 0;  // S, y and the pose table already set up by the previous iteration
   for (int it = 0; it < run; ++it) {
     if (h->record && (s = dpv_tape_state(h, it))) return s;
-    if ((s = dpv_assemble(h, it))) return s;
+    if ((s = dpv_assemble(h, it, prepared))) return s;
     int retracted = 0;
+    // the one-CTA solver re-zeroes S and y for the next iteration's assembly
+    const int reset = it + 1 < run && h->n <= DPV_SMALL_N;
     dpv_prof_begin(h, BA_KERNEL_SOLVE);
-    s = dpv_solve(h, &retracted);
+    s = dpv_solve(h, &retracted, reset);
     dpv_prof_end(h);
     if (s) return s;
     // back-substitution of the depths, with the pose retraction in the same launch
@@ -314,6 +317,7 @@ ba_status_t ba_step(ba_handle_t h, int iters, int fixed_poses) {
     dpv_prof_end(h);
     if (s) return s;
     if (h->record && (s = dpv_tape_step(h, it))) return s;
+    prepared = reset;
   }
   if (h->record) {
     if ((s = dpv_tape_state(h, run))) return s;
@@ -330,7 +334,7 @@ ba_status_t ba_linearize(ba_handle_t h, int fixed_poses) {
   if ((s = ensure_system(h, fixed_poses))) return s;
   if (h->n == 0) return BA_OK;
   DPV_CUDA(h, cudaMemsetAsync(h->ws->cost, 0, sizeof(double), h->stream));
-  return dpv_assemble(h, 0);
+  return dpv_assemble(h, 0, 0);
 }
 
 ba_status_t ba_sync(ba_handle_t h) {

@@ -414,22 +414,7 @@ __global__ void k_init_system(double* __restrict__ S, size_t nS, double* __restr
   if (dpv_status(status)) return;
   const size_t stride = (size_t)gridDim.x * blockDim.x;
   const size_t gid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (gid < (size_t)N) {
-    const double* p = poses + 7 * gid;
-    double R[9];
-    dpv_quat_rot64(p + 3, R);
-    float* o = posef + 16 * gid;
-#pragma unroll
-    for (int m = 0; m < 9; ++m) o[m] = (float)R[m];
-#pragma unroll
-    for (int m = 0; m < 3; ++m) {
-      const double c = -(R[m] * p[0] + R[3 + m] * p[1] + R[6 + m] * p[2]);
-      const float hi = (float)c;
-      o[9 + m] = hi;
-      o[12 + m] = (float)(c - (double)hi);
-    }
-    o[15] = 0.f;
-  }
+  if (gid < (size_t)N) dpv_pose_table_row(poses + 7 * gid, posef + 16 * gid);
   double2* S2 = reinterpret_cast<double2*>(S);
   for (size_t q = gid; q < nS / 2; q += stride) S2[q] = make_double2(0.0, 0.0);
   for (size_t q = gid; q < (size_t)n_pad; q += stride) y[q] = (y_init && q < (size_t)n) ? y_init[q] : 0.0;
@@ -472,23 +457,36 @@ ba_status_t upload_tables(ba_handle_t h) {
 
 }  // namespace
 
-ba_status_t dpv_assemble(ba_handle_t h, int it) { return dpv_assemble_ext(h, it, nullptr, nullptr); }
+namespace {
+ba_status_t assemble_impl(ba_handle_t h, int it, const double* v_ext, const float* w_ext, int skip_init);
+}
+
+ba_status_t dpv_assemble(ba_handle_t h, int it, int skip_init) {
+  return assemble_impl(h, it, nullptr, nullptr, skip_init);
+}
 
 // Assembly with an external right-hand side (the adjoint): y = v_ext - E Ct^-1 w_ext
 // instead of the residual-based v and w.  Both null: the normal assembly.
 ba_status_t dpv_assemble_ext(ba_handle_t h, int it, const double* v_ext, const float* w_ext) {  // it < 0: no cost
+  return assemble_impl(h, it, v_ext, w_ext, 0);
+}
+
+namespace {
+ba_status_t assemble_impl(ba_handle_t h, int it, const double* v_ext, const float* w_ext, int skip_init) {
   Workspace* ws = h->ws;
   ba_status_t s = upload_tables(h);
   if (s) return s;
   const size_t nS = (size_t)h->T * (h->T + 1) / 2 * h->TS * h->TS;
-  dpv_prof_begin(h, BA_KERNEL_INIT);
-  k_init_system<<<2 * h->num_sms, 256, 0, h->stream>>>(ws->S.p, nS, ws->y.p, h->n_pad, h->n, v_ext, h->poses, h->N,
-                                                        ws->posef.p, ws->status);
-  ++h->launches;
-  k_init_diag<<<(h->n_pad + 255) / 256, 256, 0, h->stream>>>(ws->S.p, h->n, h->n_pad, h->TS, h->opt.lambda_pose,
-                                                              ws->status);
-  ++h->launches;
-  dpv_prof_end(h);
+  if (!skip_init) {
+    dpv_prof_begin(h, BA_KERNEL_INIT);
+    k_init_system<<<2 * h->num_sms, 256, 0, h->stream>>>(ws->S.p, nS, ws->y.p, h->n_pad, h->n, v_ext, h->poses,
+                                                          h->N, ws->posef.p, ws->status);
+    ++h->launches;
+    k_init_diag<<<(h->n_pad + 255) / 256, 256, 0, h->stream>>>(ws->S.p, h->n, h->n_pad, h->TS, h->opt.lambda_pose,
+                                                                ws->status);
+    ++h->launches;
+    dpv_prof_end(h);
+  }
   double* cost = it < 0 ? nullptr : ws->cost + (it < ws->cost_cap ? it : ws->cost_cap - 1);
   dpv_prof_begin(h, BA_KERNEL_ASSEMBLE);
   k_assemble<<<h->ngroups, AS_THREADS, assemble_smem_bytes(h->G), h->stream>>>(
@@ -500,6 +498,7 @@ ba_status_t dpv_assemble_ext(ba_handle_t h, int it, const double* v_ext, const f
   DPV_CUDA(h, cudaGetLastError());
   return BA_OK;
 }
+}  // namespace
 
 ba_status_t dpv_export_S(ba_handle_t h, double* dst) {
   const size_t nn = (size_t)h->n * h->n;

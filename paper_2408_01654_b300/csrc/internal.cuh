@@ -171,16 +171,17 @@ ba_status_t dpv_exclusive_scan(ba_handle_t h, const int* in, int* out, int n, co
 long long dpv_scan_scratch(long long n);
 long long dpv_hist_entries(long long m);
 // one GN iteration (assemble.cu, solve_*.cu, update.cu)
-ba_status_t dpv_assemble(ba_handle_t h, int it);
+// skip_init: S, y and the pose table are already prepared (the one-CTA solver
+// of the previous iteration re-zeroed S and y, the retraction refreshed the table)
+ba_status_t dpv_assemble(ba_handle_t h, int it, int skip_init);
 ba_status_t dpv_assemble_ext(ba_handle_t h, int it, const double* v_ext, const float* w_ext);
 ba_status_t dpv_ensure_system(ba_handle_t h, int fixed);
 ba_status_t dpv_tape_reserve(ba_handle_t h, int iters);
 ba_status_t dpv_tape_state(ba_handle_t h, int it);
 ba_status_t dpv_tape_step(ba_handle_t h, int it);
 ba_status_t dpv_backsub_ext(ba_handle_t h, const float* w_ext, float* out);
-ba_status_t dpv_solve(ba_handle_t h, int* retracted);  // retracted: poses already updated
+ba_status_t dpv_solve(ba_handle_t h, int* retracted, int reset_system = 0);
 ba_status_t dpv_backsub(ba_handle_t h, int retract);  // retract: also update the poses
-ba_status_t dpv_retract(ba_handle_t h);
 ba_status_t dpv_export_S(ba_handle_t h, double* dst);
 
 // ---------------------------------------------------------------------------
@@ -221,12 +222,49 @@ __device__ __forceinline__ double dpv_f2d_bits(float v) {
   return __longlong_as_double((long long)d);
 }
 
+// The double rounded to the nearest float (ties to even) with integer
+// operations, for the same reason.  |v| below 2^-126 gives signed zero,
+// above the float range infinity; NaN stays NaN.
+__device__ __forceinline__ float dpv_d2f_bits(double v) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+  const int ed = (int)((b >> 52) & 0x7ff);
+  const unsigned long long m = b & 0xfffffffffffffull;
+  const int e = ed - 1023 + 127;
+  if (ed == 0x7ff) return __uint_as_float(sign | 0x7f800000u | (m ? 0x400000u : 0u));
+  if (e <= 0) return __uint_as_float(sign);
+  if (e >= 255) return __uint_as_float(sign | 0x7f800000u);
+  const unsigned mant = (unsigned)(m >> 29);
+  const unsigned long long rest = m & 0x1fffffffull;
+  unsigned r = ((unsigned)e << 23) | mant;
+  if (rest > 0x10000000ull || (rest == 0x10000000ull && (mant & 1u))) r += 1u;  // may carry to infinity
+  return __uint_as_float(sign | r);
+}
+
 // rotation matrix of a unit quaternion (x, y, z, w), FP64
 __device__ __forceinline__ void dpv_quat_rot64(const double* q, double* R) {
   const double x = q[0], y = q[1], z = q[2], w = q[3];
   R[0] = 1.0 - 2.0 * (y * y + z * z); R[1] = 2.0 * (x * y - z * w); R[2] = 2.0 * (x * z + y * w);
   R[3] = 2.0 * (x * y + z * w); R[4] = 1.0 - 2.0 * (x * x + z * z); R[5] = 2.0 * (y * z - x * w);
   R[6] = 2.0 * (x * z - y * w); R[7] = 2.0 * (y * z + x * w); R[8] = 1.0 - 2.0 * (x * x + y * y);
+}
+
+// One row of the per-pose FP32 table used by the linearisation: R (9 floats)
+// and the camera centre c = -R^T t as a double-float pair (hi 3, lo 3), formed
+// in FP64 from the FP64 pose (t, q).
+__device__ __forceinline__ void dpv_pose_table_row(const double* __restrict__ p, float* __restrict__ o) {
+  double R[9];
+  dpv_quat_rot64(p + 3, R);
+#pragma unroll
+  for (int m = 0; m < 9; ++m) o[m] = dpv_d2f_bits(R[m]);
+#pragma unroll
+  for (int m = 0; m < 3; ++m) {
+    const double c = -(R[m] * p[0] + R[3 + m] * p[1] + R[6 + m] * p[2]);
+    const float hi = dpv_d2f_bits(c);
+    o[9 + m] = hi;
+    o[12 + m] = dpv_d2f_bits(c - dpv_f2d_bits(hi));
+  }
+  o[15] = 0.f;
 }
 
 struct RelPose {

@@ -1,7 +1,6 @@
 // Dense solve of the reduced pose system S dxi = y for n <= DPV_SMALL_N in
 // one CTA (the Cholesky of the pose block of the Schur complement, appendix
-// "Bundle-Adjustment Efficiency"), followed by the SE(3) retraction of the
-// free poses.
+// "Bundle-Adjustment Efficiency").
 //
 // S and y arrive in FP64 (the assembly accumulates them so); S is rounded to
 // FP32 into shared memory as a packed lower triangle and factored as
@@ -28,28 +27,30 @@
 // in BA_MIXED the sweeps compute it in FP64 from the FP64 S.
 #include "internal.cuh"
 
-#include "retract.cuh"
-
 namespace {
 
 __host__ __device__ constexpr int tri(int r, int c) { return r * (r + 1) / 2 + c; }
 
 __host__ __device__ constexpr int small_threads(int NQ) { return NQ <= 2 ? 128 : 512; }
-// the FP32 copy of S for the compensated residual fits in shared memory up to NQ = 6
-__host__ __device__ constexpr bool keep_sf(int NQ) { return NQ <= 6; }
+// the FP32 copy of S for the compensated residual fits in shared memory up to
+// NQ = 5, as a full square with row stride NP + 4 (conflict-free row reads by
+// eight rows x four interleaved column parts per warp)
+__host__ __device__ constexpr bool keep_sf(int NQ) { return NQ <= 5; }
+__host__ __device__ constexpr int sf_stride(int NQ) { return 32 * NQ + 4; }
 __host__ __device__ constexpr size_t small_smem(int NQ) {
-  return sizeof(float) * ((size_t)tri(32 * NQ, 0) * (keep_sf(NQ) ? 2 : 1));
+  return sizeof(float) * ((size_t)tri(32 * NQ, 0) + (keep_sf(NQ) ? (size_t)32 * NQ * sf_stride(NQ) : 0));
 }
 
 template <int NQ>  // NP = 32 NQ
 __global__ void __launch_bounds__(small_threads(NQ)) k_solve_small(
-    int n, const double* __restrict__ S, const double* __restrict__ y, double* __restrict__ dx,
-    float* __restrict__ dxf, int refine32, int refine64, int N, int fixed, double* __restrict__ poses, int* status) {
+    int n, double* __restrict__ S, double* __restrict__ y, double* __restrict__ dx,
+    float* __restrict__ dxf, int refine32, int refine64, float lambda_p, int reset, int* status) {
   constexpr int NP = 32 * NQ;
   constexpr int NT = small_threads(NQ);
   constexpr int NWARP = NT / 32;
+  constexpr int SFS = sf_stride(NQ);
   extern __shared__ float Lsh[];            // packed lower: trailing A, then the unit factor
-  float* Sf = Lsh + tri(NP, 0);             // FP32 copy of S (keep_sf)
+  float* Sf = Lsh + tri(NP, 0);             // FP32 copy of S, full square, row stride SFS (keep_sf)
   __shared__ float Pb[NP][33];              // unscaled panel of the current block
   __shared__ float Linv[NQ][32][33];        // inverses of the unit diagonal blocks
   __shared__ __align__(16) float ucol[32];  // column broadcast in the diagonal block
@@ -60,14 +61,59 @@ __global__ void __launch_bounds__(small_threads(NQ)) k_solve_small(
   __shared__ int bad;
   if (dpv_status(status)) return;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  for (int i = wid; i < NP; i += NWARP)
-    for (int j = lane; j <= i; j += 32) {
-      const float v = (float)S[(size_t)i * NP + j];
-      Lsh[tri(i, j)] = v;
-      if (keep_sf(NQ)) Sf[tri(i, j)] = v;
+  {
+    // S: FP64 row-major NP x NP (lower triangle valid), read as pairs with
+    // four loads in flight per thread, rounded to FP32 with integer operations
+    constexpr int NPH = NP / 2;
+    const double2* S2 = reinterpret_cast<const double2*>(S);
+    for (int q0 = tid; q0 < NP * NPH; q0 += 4 * NT) {
+      double2 v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int q = q0 + u * NT;
+        const int i = q / NPH, p = q - (q / NPH) * NPH;
+        v[u] = (q < NP * NPH && 2 * p <= i) ? S2[q] : make_double2(0.0, 0.0);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int q = q0 + u * NT;
+        const int i = q / NPH, p = q - (q / NPH) * NPH;
+        if (q < NP * NPH && 2 * p <= i) {
+          const float a0 = dpv_d2f_bits(v[u].x), a1 = dpv_d2f_bits(v[u].y);
+          Lsh[tri(i, 2 * p)] = a0;
+          if (keep_sf(NQ)) {
+            Sf[i * SFS + 2 * p] = a0;
+            Sf[2 * p * SFS + i] = a0;
+          }
+          if (2 * p + 1 <= i) {
+            Lsh[tri(i, 2 * p + 1)] = a1;
+            if (keep_sf(NQ)) {
+              Sf[i * SFS + 2 * p + 1] = a1;
+              Sf[(2 * p + 1) * SFS + i] = a1;
+            }
+          }
+        }
+      }
     }
+  }
   if (tid == 0) bad = 0;
+  // reset: leave S (lower triangle) as the next assembly expects it: zero,
+  // lambda_p on the free diagonal, 1 on the padding diagonal.  Done here when
+  // no refinement sweep reads S from global memory again, else at the end.
+  const bool s_read_later = refine64 > 0 || (refine32 > 0 && !keep_sf(NQ));
+  auto reset_S = [&]() {
+    double2* S2w = reinterpret_cast<double2*>(S);
+    for (int q = tid; q < NP * (NP / 2); q += NT) {
+      const int i = q / (NP / 2), p = q - (q / (NP / 2)) * (NP / 2);
+      if (2 * p > i) continue;
+      double2 v = make_double2(0.0, 0.0);
+      if (2 * p == i) v.x = i < n ? (double)lambda_p : 1.0;
+      if (2 * p + 1 == i) v.y = i < n ? (double)lambda_p : 1.0;
+      S2w[q] = v;
+    }
+  };
   __syncthreads();
+  if (reset && !s_read_later) reset_S();
 
   for (int r0 = 0; r0 < NP; r0 += 32) {
     const int kb = r0 / 32;
@@ -83,7 +129,8 @@ __global__ void __launch_bounds__(small_threads(NQ)) k_solve_small(
         __syncwarp();
         const float d = ucol[c];
         ok = ok && (d > 0.f);
-        const float inv = __frcp_rn(d);
+        float inv;  // approximate reciprocal: the refinement absorbs its last-bit error
+        asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(inv) : "f"(d));
         const float l = a[c] * inv;
         float u[32];
 #pragma unroll
@@ -116,21 +163,36 @@ __global__ void __launch_bounds__(small_threads(NQ)) k_solve_small(
     __syncthreads();
     if (bad) break;
     // 3. panel rows below the block: P = A_panel L_kk^-T (lane = output column)
-    for (int i = r0 + 32 + wid; i < NP; i += NWARP) {
-      const float* ai = Lsh + tri(i, r0);
-      float p = 0.f;
+    // (three rows per warp at a time: independent dependency chains)
+    for (int i0 = r0 + 32 + wid; i0 < NP; i0 += 3 * NWARP) {
+      float p[3] = {0.f, 0.f, 0.f};
+      const float* ai[3];
+#pragma unroll
+      for (int u = 0; u < 3; ++u) ai[u] = Lsh + tri(min(i0 + u * NWARP, NP - 1), r0);
 #pragma unroll 8
-      for (int cp = 0; cp < 32; ++cp) p = fmaf(ai[cp], Linv[kb][lane][cp], p);
+      for (int cp = 0; cp < 32; ++cp) {
+        const float li = Linv[kb][lane][cp];
+#pragma unroll
+        for (int u = 0; u < 3; ++u) p[u] = fmaf(ai[u][cp], li, p[u]);
+      }
       __syncwarp();
-      Pb[i][lane] = p;
-      Lsh[tri(i, r0 + lane)] = p * invD[r0 + lane];
+#pragma unroll
+      for (int u = 0; u < 3; ++u) {
+        const int i = i0 + u * NWARP;
+        if (i < NP) {
+          Pb[i][lane] = p[u];
+          Lsh[tri(i, r0 + lane)] = p[u] * invD[r0 + lane];
+        }
+      }
     }
     __syncthreads();
     // 4. trailing update A[i][j] -= sum_c Pb[i][c] L[j][r0 + c], i >= j >= r0 + 32, 4x4 tiles
     const int p1 = r0 + 32, m = NP - p1, mt = m / 4;
-    for (int t = tid; t < mt * mt; t += NT) {
-      const int bi = t / mt, bj = t % mt;
-      if (bj > bi) continue;
+    for (int t = tid; t < tri(mt, 0); t += NT) {  // lower tiles only (bi >= bj)
+      int bi = (int)((sqrtf(8.0f * t + 1.0f) - 1.0f) * 0.5f);
+      while (tri(bi + 1, 0) <= t) ++bi;
+      while (tri(bi, 0) > t) --bi;
+      const int bj = t - tri(bi, 0);
       const int i0 = p1 + 4 * bi, j0 = p1 + 4 * bj;
       float acc[4][4];
 #pragma unroll
@@ -226,22 +288,26 @@ __global__ void __launch_bounds__(small_threads(NQ)) k_solve_small(
     if (sweep + 1 == sweeps) break;
     // residual rho = y - S x
     if (sweep < refine32 && keep_sf(NQ)) {
-      // compensated FP32 against the FP32 copy of S
-      for (int r = wid; r < NP; r += NWARP) {
+      // compensated FP32 against the FP32 copy of S: four threads per row,
+      // each over the columns c = part (mod 4)
+      for (int r0 = 0; r0 < NP; r0 += NT / 4) {
+        const int r = r0 + (tid >> 2), part = tid & 3;
         DF acc = {0.f, 0.f};
-        if (r < n)
-          for (int c = lane; c < n; c += 32) {
-            const float sv = c <= r ? Sf[tri(r, c)] : Sf[tri(c, r)];
+        if (r < n) {
+          const float* srow = Sf + r * SFS;
+          for (int c = part; c < n; c += 4) {
+            const float sv = srow[c];
             df_fma(acc, sv, xhi[c]);
             acc.lo = fmaf(sv, xlo[c], acc.lo);
           }
+        }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
+        for (int o = 1; o < 4; o <<= 1) {
           const float oh = __shfl_xor_sync(0xffffffffu, acc.hi, o), ol = __shfl_xor_sync(0xffffffffu, acc.lo, o);
           df_add(acc, oh);
           acc.lo += ol;
         }
-        if (lane == 0) {
+        if (part == 0 && r < NP) {
           DF rr = {yhi[r], ylo[r]};
           df_add(rr, -acc.hi);
           rr.lo -= acc.lo;
@@ -265,13 +331,20 @@ __global__ void __launch_bounds__(small_threads(NQ)) k_solve_small(
     __syncthreads();
   }
   for (int q = tid; q < n; q += NT) {
-    dx[q] = (double)xhi[q] + (double)xlo[q];
+    dx[q] = dpv_f2d_bits(xhi[q]) + dpv_f2d_bits(xlo[q]);
     dxf[q] = xhi[q] + xlo[q];
+  }
+  if (reset) {
+    if (s_read_later) {
+      __syncthreads();
+      reset_S();
+    }
+    for (int q = tid; q < NP; q += NT) y[q] = 0.0;
   }
 }
 
 template <int NQ>
-ba_status_t launch_small(ba_handle_t h, int refine32, int refine64) {
+ba_status_t launch_small(ba_handle_t h, int refine32, int refine64, int reset) {
   static bool attr = false;
   const size_t smem = small_smem(NQ);
   if (!attr) {
@@ -279,8 +352,8 @@ ba_status_t launch_small(ba_handle_t h, int refine32, int refine64) {
     attr = true;
   }
   k_solve_small<NQ><<<1, small_threads(NQ), smem, h->stream>>>(h->n, h->ws->S.p, h->ws->y.p, h->ws->dx.p,
-                                                                h->ws->tmpv.p, refine32, refine64, h->N, h->fixed,
-                                                                h->poses, h->ws->status);
+                                                                h->ws->tmpv.p, refine32, refine64, h->opt.lambda_pose,
+                                                                reset, h->ws->status);
   ++h->launches;
   DPV_CUDA(h, cudaGetLastError());
   return BA_OK;
@@ -291,7 +364,7 @@ ba_status_t launch_small(ba_handle_t h, int refine32, int refine64) {
 ba_status_t dpv_solve_blocked(ba_handle_t h, int refine);
 
 // Solve S dxi = y (the retraction is launched by the caller).
-ba_status_t dpv_solve(ba_handle_t h, int* retracted) {
+ba_status_t dpv_solve(ba_handle_t h, int* retracted, int reset_system) {
   // BA_FP32: one compensated-FP32 refinement sweep; BA_MIXED: FP64 sweeps
   const int refine32 = h->opt.precision == BA_MIXED ? 0 : 1;
   const int refine64 = h->opt.precision == BA_MIXED ? h->opt.max_refine : 0;
@@ -301,14 +374,14 @@ ba_status_t dpv_solve(ba_handle_t h, int* retracted) {
   if (h->n > DPV_SMALL_N) return dpv_solve_blocked(h, refine32 + refine64);
   ba_status_t s;
   switch (h->n_pad / 32) {
-    case 1: s = launch_small<1>(h, refine32, refine64); break;
-    case 2: s = launch_small<2>(h, refine32, refine64); break;
-    case 3: s = launch_small<3>(h, refine32, refine64); break;
-    case 4: s = launch_small<4>(h, refine32, refine64); break;
-    case 5: s = launch_small<5>(h, refine32, refine64); break;
-    case 6: s = launch_small<6>(h, refine32, refine64); break;
-    case 7: s = launch_small<7>(h, refine32, refine64); break;
-    case 8: s = launch_small<8>(h, refine32, refine64); break;
+    case 1: s = launch_small<1>(h, refine32, refine64, reset_system); break;
+    case 2: s = launch_small<2>(h, refine32, refine64, reset_system); break;
+    case 3: s = launch_small<3>(h, refine32, refine64, reset_system); break;
+    case 4: s = launch_small<4>(h, refine32, refine64, reset_system); break;
+    case 5: s = launch_small<5>(h, refine32, refine64, reset_system); break;
+    case 6: s = launch_small<6>(h, refine32, refine64, reset_system); break;
+    case 7: s = launch_small<7>(h, refine32, refine64, reset_system); break;
+    case 8: s = launch_small<8>(h, refine32, refine64, reset_system); break;
     default: return dpv_fail(h, BA_ERR_UNSUPPORTED, "pose system size");
   }
   return s;
@@ -325,7 +398,9 @@ ba_status_t launch_small_raw(cudaStream_t st, int n, const double* S, const doub
   if (cudaFuncSetAttribute(k_solve_small<NQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
       cudaSuccess)
     return BA_ERR_CUDA;
-  k_solve_small<NQ><<<1, small_threads(NQ), smem, st>>>(n, S, y, dx, dxf, 0, refine, 0, 0, nullptr, status);
+  // reset = 0: the kernel only reads S and y
+  k_solve_small<NQ><<<1, small_threads(NQ), smem, st>>>(n, const_cast<double*>(S), const_cast<double*>(y), dx, dxf, 0,
+                                                        refine, 0.f, 0, status);
   return cudaGetLastError() == cudaSuccess ? BA_OK : BA_ERR_CUDA;
 }
 }  // namespace

@@ -15,23 +15,31 @@
 
 namespace {
 
-__global__ void k_backsub(int P, int G, int fixed, float d_min, const int* __restrict__ pptr,
-                          const float4* __restrict__ pterm, const int* __restrict__ win,
-                          const float* __restrict__ dxf, const float* __restrict__ Ct, const float* __restrict__ wk,
-                          float* __restrict__ patches, float* __restrict__ dd_out, int N, const double* __restrict__ dx,
-                          double* __restrict__ poses, int write_depth, const int* status) {
+constexpr int BS_THREADS = 256;
+constexpr int BS_WARPS = BS_THREADS / 32;
+
+// One warp per patch (lanes over its edges, compensated warp sum).  Thread 0
+// of CTA b < N - fixed also retracts pose fixed + b (FP64) and, when `posef`
+// is given, refreshes that pose's row of the linearisation table; one pose per
+// CTA spreads the FP64 work (1/64 of the FP32 rate) over the SMs.
+__global__ void __launch_bounds__(BS_THREADS) k_backsub(
+    int P, int G, int fixed, float d_min, const int* __restrict__ pptr, const float4* __restrict__ pterm,
+    const int* __restrict__ win, const float* __restrict__ dxf, const float* __restrict__ Ct,
+    const float* __restrict__ wk, float* __restrict__ patches, float* __restrict__ dd_out, int N,
+    const double* __restrict__ dx, double* __restrict__ poses, float* __restrict__ posef, int write_depth,
+    const int* status) {
   if (dpv_status(status)) return;
-  if (N > fixed && blockIdx.x == gridDim.x - 1) {
-    // the extra last CTA retracts the free poses (FP64) while the others back-substitute
-    for (int f = fixed + threadIdx.x; f < N; f += blockDim.x)
-      dpv_se3_retract(dx + 6 * (f - fixed), poses + 7 * (size_t)f);
-    return;
+  const int lane = threadIdx.x & 31;
+  if (threadIdx.x == 0 && (int)blockIdx.x < N - fixed) {
+    const int f = fixed + blockIdx.x;
+    dpv_se3_retract(dx + 6 * (size_t)blockIdx.x, poses + 7 * (size_t)f);
+    if (posef) dpv_pose_table_row(poses + 7 * (size_t)f, posef + 16 * (size_t)f);
   }
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  const int k = blockIdx.x * BS_WARPS + (threadIdx.x >> 5);
   if (k >= P) return;
   const int* wf = win + (k / G) * DPV_WMAX;
-  DF acc = {wk[k], 0.f};
-  for (int p = pptr[k]; p < pptr[k + 1]; ++p) {
+  DF acc = {0.f, 0.f};
+  for (int p = pptr[k] + lane; p < pptr[k + 1]; p += 32) {
     const float4 a = pterm[4 * (size_t)p], b = pterm[4 * (size_t)p + 1], c = pterm[4 * (size_t)p + 2],
                  d = pterm[4 * (size_t)p + 3];
     const int sl = __float_as_int(d.z);
@@ -47,33 +55,39 @@ __global__ void k_backsub(int P, int G, int fixed, float d_min, const int* __res
       df_fma(acc, -c.y, x[3]); df_fma(acc, -c.z, x[4]); df_fma(acc, -c.w, x[5]);
     }
   }
-  const float dd = df_val(acc) / Ct[k];
-  dd_out[k] = dd;
-  if (!write_depth) return;
-  float* pk = patches + 27 * (size_t)k;
-  const float dn = fmaxf(pk[22] + dd, d_min);
 #pragma unroll
-  for (int m = 18; m < 27; ++m) pk[m] = dn;
+  for (int o = 16; o > 0; o >>= 1) {
+    const DF t = {__shfl_xor_sync(0xffffffffu, acc.hi, o), __shfl_xor_sync(0xffffffffu, acc.lo, o)};
+    df_add_df(acc, t);
+  }
+  if (lane == 0) {
+    df_add(acc, wk[k]);
+    const float dd = df_val(acc) / Ct[k];
+    dd_out[k] = dd;
+    if (write_depth) {
+      float* pk = patches + 27 * (size_t)k;
+      const float dn = fmaxf(pk[22] + dd, d_min);
+#pragma unroll
+      for (int m = 18; m < 27; ++m) pk[m] = dn;
+    }
+  }
 }
 
-__global__ void k_retract(int N, int fixed, const double* __restrict__ dx, double* __restrict__ poses,
-                          const int* status) {
-  if (dpv_status(status)) return;
-  const int f = fixed + blockIdx.x * blockDim.x + threadIdx.x;
-  if (f >= N) return;
-  dpv_se3_retract(dx + 6 * (f - fixed), poses + 7 * (size_t)f);
+unsigned backsub_grid(ba_handle_t h, int retract) {
+  const long long wb = ((long long)h->P + BS_WARPS - 1) / BS_WARPS;
+  const long long rb = retract ? (long long)(h->N - h->fixed) : 0;
+  return (unsigned)(wb > rb ? wb : rb);
 }
 
 }  // namespace
 
 // Back-substitution of the depths; with `retract` the kernel also updates the
-// poses (one extra CTA).
+// poses and their rows of the linearisation table.
 ba_status_t dpv_backsub(ba_handle_t h, int retract) {
   Workspace* ws = h->ws;
-  const int nb = (h->P + 127) / 128 + (retract ? 1 : 0);
-  k_backsub<<<nb, 128, 0, h->stream>>>(h->P, h->G, h->fixed, h->opt.d_min, ws->pptr.p, ws->pterm.p, ws->win.p,
-                                       ws->tmpv.p, ws->Ct.p, ws->wk.p, h->patches, ws->dd.p,
-                                       retract ? h->N : h->fixed, ws->dx.p, h->poses, 1, ws->status);
+  k_backsub<<<backsub_grid(h, retract), BS_THREADS, 0, h->stream>>>(
+      h->P, h->G, h->fixed, h->opt.d_min, ws->pptr.p, ws->pterm.p, ws->win.p, ws->tmpv.p, ws->Ct.p, ws->wk.p,
+      h->patches, ws->dd.p, retract ? h->N : h->fixed, ws->dx.p, h->poses, ws->posef.p, 1, ws->status);
   ++h->launches;
   DPV_CUDA(h, cudaGetLastError());
   return BA_OK;
@@ -83,19 +97,9 @@ ba_status_t dpv_backsub(ba_handle_t h, int retract) {
 // with lambda_a in the solver's output; no state is changed.
 ba_status_t dpv_backsub_ext(ba_handle_t h, const float* w_ext, float* out) {
   Workspace* ws = h->ws;
-  const int nb = (h->P + 127) / 128;
-  k_backsub<<<nb, 128, 0, h->stream>>>(h->P, h->G, h->fixed, h->opt.d_min, ws->pptr.p, ws->pterm.p, ws->win.p,
-                                       ws->tmpv.p, ws->Ct.p, w_ext, h->patches, out, h->fixed, ws->dx.p, h->poses, 0,
-                                       ws->status);
-  ++h->launches;
-  DPV_CUDA(h, cudaGetLastError());
-  return BA_OK;
-}
-
-ba_status_t dpv_retract(ba_handle_t h) {
-  const int nf = h->N - h->fixed;
-  if (nf <= 0) return BA_OK;
-  k_retract<<<(nf + 127) / 128, 128, 0, h->stream>>>(h->N, h->fixed, h->ws->dx.p, h->poses, h->ws->status);
+  k_backsub<<<backsub_grid(h, 0), BS_THREADS, 0, h->stream>>>(
+      h->P, h->G, h->fixed, h->opt.d_min, ws->pptr.p, ws->pterm.p, ws->win.p, ws->tmpv.p, ws->Ct.p, w_ext,
+      h->patches, out, h->fixed, ws->dx.p, h->poses, nullptr, 0, ws->status);
   ++h->launches;
   DPV_CUDA(h, cudaGetLastError());
   return BA_OK;
