@@ -185,7 +185,7 @@ ba_status_t ba_destroy(ba_handle_t h) {
     release(ws->pterm); release(ws->posef);
     release(ws->tp_poses); release(ws->tp_patches); release(ws->tp_dx); release(ws->tp_dd);
     release(ws->ad_xb); release(ws->ad_w); release(ws->ad_gd); release(ws->ad_lamd); release(ws->ad_v);
-    release(ws->ad_gt); release(ws->ad_gw);
+    release(ws->ad_gt); release(ws->ad_gw); release(ws->lg_sync);
     delete ws;
   }
   prof_clear(h);

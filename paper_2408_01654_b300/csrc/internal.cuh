@@ -113,6 +113,7 @@ struct Workspace {
   DBuf<float4> pterm;             // [E][4] per-edge depth terms, patch-major (see assemble.cu)
   // blocked solver
   DBuf<float> L;                  // factor (large n)
+  DBuf<int> lg_sync;              // large solver: tile versions, row flags, task counter, grid barrier
   DBuf<double> r64;               // [n_pad]
   DBuf<float> tmpv;               // [n_pad]
   // tape of a recorded ba_step: states before each iteration (+ the final poses) and the steps

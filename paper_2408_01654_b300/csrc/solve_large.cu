@@ -1,0 +1,767 @@
+// Solve of the reduced pose system for n > DPV_SMALL_N (the global
+// loop-closure BA: the dense Cholesky of the pose block of the Schur
+// complement, which the appendix "Bundle-Adjustment Efficiency" names as the
+// memory and runtime bottleneck of global optimisation).
+//
+// S (FP64, tiled lower triangle, 64 x 64 tiles) is rounded to an FP32 copy in
+// the same tiled layout and factored as S = L D L^T by ONE persistent kernel
+// that runs a task graph over the tiles:
+//   DIAG(k)        factor tile (k,k): unit L_kk, D_k, and the inverse L_kk^-1
+//   PANEL(i,k)     L_ik = A_ik L_kk^-T D_k^-1                      (i > k)
+//   UPDATE(i,j,k)  A_ij -= (L_ik D_k) L_jk^T                       (k < j <= i)
+// Each tile carries a version (the number of updates applied, +1 once it is
+// final).  The chain DIAG(k) -> PANEL(k+1,k) -> UPDATE(k+1,k+1,k) -> DIAG(k+1)
+// is the critical path, so one CTA, alone on its SM, runs it step after step
+// without handing tiles over; the other CTAs take the remaining panels and
+// updates from a list in dependency order (lookahead one column) and wait,
+// with a bounded spin, only for the versions their task reads.  Every CTA is
+// resident (cooperative launch) and each wait is on work that is earlier in
+// the critical chain or in the list, so the schedule cannot deadlock.
+//
+// A second persistent kernel runs the triangular solves and the refinement:
+// block row i of the forward solve waits for the rows above it, the backward
+// solve for the rows below; a grid barrier separates the sweeps, whose
+// residual rho = y - S x is formed in FP64 from the FP64 S.
+#include "internal.cuh"
+
+#include <map>
+#include <mutex>
+#include <vector>
+
+namespace {
+
+constexpr int NB = 64;  // tile edge, equal to the assembly's tile for n > DPV_SMALL_N
+constexpr int TILE = NB * NB;
+constexpr int LDS = NB + 1;  // padded shared-memory row
+constexpr int LG_THREADS = 256;
+constexpr int TASK_PANEL = 1, TASK_UPDATE = 2;  // worker task types (the diagonal steps are not listed)
+constexpr int LG_MAX_T = 1023;  // tiles per dimension (10-bit task fields)
+
+static_assert(NB == DPV_TILE, "the large solver works on the assembly's tiles");
+
+__host__ __device__ inline int tri2(int r) { return r * (r + 1) / 2; }
+__host__ __device__ inline unsigned pack_task(int type, int k, int i, int j) {
+  return ((unsigned)type << 30) | ((unsigned)k << 20) | ((unsigned)i << 10) | (unsigned)j;
+}
+
+// ---------------------------------------------------------------------------
+// synchronisation primitives (thread 0 of a CTA; bounded)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int ld_acquire(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release(int* p, int v) {
+  asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Wait until *p >= want.  Gives up when another CTA reported an error or when
+// `timeout` cycles have passed (then reports DST_TIMEOUT).  Returns success.
+__device__ bool wait_geq(const int* p, int want, int* status, long long timeout) {
+  const long long t0 = clock64();
+  for (unsigned it = 0;; ++it) {
+    if (ld_acquire(p) >= want) return true;
+    if ((it & 63u) == 63u) {
+      if (dpv_status(status)) return false;
+      if (clock64() - t0 > timeout) {
+        dpv_set_status(status, DST_TIMEOUT);
+        return false;
+      }
+    }
+    __nanosleep(64);
+  }
+}
+
+// Grid-wide barrier of a cooperative launch: count / generation in bar[0..1].
+__device__ bool grid_barrier(int* bar, int nblocks, int* status, long long timeout) {
+  __syncthreads();
+  __shared__ int ok;
+  if (threadIdx.x == 0) {
+    ok = 1;
+    const int gen = ld_acquire(bar + 1);
+    __threadfence();
+    if (atomicAdd(bar, 1) == nblocks - 1) {
+      bar[0] = 0;
+      __threadfence();
+      st_release(bar + 1, gen + 1);
+    } else {
+      ok = wait_geq(bar + 1, gen + 1, status, timeout) ? 1 : 0;
+    }
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+__device__ __forceinline__ float* tile_ptr(float* A, int i, int j) { return A + (size_t)(tri2(i) + j) * TILE; }
+
+// tile (64 x 64, row-major in global memory, read through L2) -> padded
+// shared; all four loads of a thread are issued before the stores
+__device__ __forceinline__ void load_tile(float* dst, const float* src, bool lower_only) {
+  constexpr int PER = TILE / 4 / LG_THREADS;
+  float4 v[PER];
+#pragma unroll
+  for (int u = 0; u < PER; ++u) v[u] = __ldcg(reinterpret_cast<const float4*>(src) + threadIdx.x + u * LG_THREADS);
+#pragma unroll
+  for (int u = 0; u < PER; ++u) {
+    const int q = threadIdx.x + u * LG_THREADS;
+    const int r = (4 * q) / NB, c = (4 * q) % NB;
+    float* d = dst + r * LDS + c;
+    d[0] = (!lower_only || c <= r) ? v[u].x : 0.f;
+    d[1] = (!lower_only || c + 1 <= r) ? v[u].y : 0.f;
+    d[2] = (!lower_only || c + 2 <= r) ? v[u].z : 0.f;
+    d[3] = (!lower_only || c + 3 <= r) ? v[u].w : 0.f;
+  }
+}
+
+// two tiles, eight loads in flight per thread
+__device__ __forceinline__ void load_tiles2(float* d0, const float* s0, float* d1, const float* s1) {
+  constexpr int PER = TILE / 4 / LG_THREADS;
+  float4 v[2 * PER];
+#pragma unroll
+  for (int u = 0; u < PER; ++u) {
+    v[u] = __ldcg(reinterpret_cast<const float4*>(s0) + threadIdx.x + u * LG_THREADS);
+    v[PER + u] = __ldcg(reinterpret_cast<const float4*>(s1) + threadIdx.x + u * LG_THREADS);
+  }
+#pragma unroll
+  for (int u = 0; u < 2 * PER; ++u) {
+    const int q = threadIdx.x + (u % PER) * LG_THREADS;
+    const int r = (4 * q) / NB, c = (4 * q) % NB;
+    float* d = (u < PER ? d0 : d1) + r * LDS + c;
+    d[0] = v[u].x;
+    d[1] = v[u].y;
+    d[2] = v[u].z;
+    d[3] = v[u].w;
+  }
+}
+
+// acc[a][b] += sum_c X[r][c] w[c] Y[s][c] for r = ty + 16a, s = tx + 16b (w may be null)
+__device__ __forceinline__ void gemm_nt(const float* X, const float* Y, const float* w, float acc[4][4]) {
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+#pragma unroll 4
+  for (int c = 0; c < NB; ++c) {
+    const float wc = w ? w[c] : 1.f;
+    float xa[4], yb[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) xa[a] = X[(ty + 16 * a) * LDS + c] * wc;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) yb[b] = Y[(tx + 16 * b) * LDS + c];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(xa[a], yb[b], acc[a][b]);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// the tasks
+// ---------------------------------------------------------------------------
+struct LgShared {
+  float X[NB * LDS];
+  float Y[NB * LDS];
+  float Z[NB * LDS];
+  float Li[2][32][33];
+  float W[32][33];
+  __align__(16) float ucol[LG_THREADS / 32][32];  // one column broadcast row per warp
+  float invd[NB];
+  float dd[NB];
+  float dprev[NB];  // the previous diagonal step's D and D^-1 (critical-path CTA)
+  float iprev[NB];
+  int task;
+  int bad;
+};
+
+// LDL^T of the 32 x 32 block at (base, base) of Xs (lane = row); writes the
+// unit factor (strict lower), D, D^-1 and the inverse of the unit factor Li
+// (lane = column).  Every warp runs the same elimination on its own broadcast
+// row and only warp 0 stores the results: a CTA barrier after a phase in
+// which one warp worked and seven waited measured ~5x slower single-warp
+// phases afterwards on this part.  Returns false on a non-positive pivot.
+__device__ __noinline__ bool factor32(LgShared& sm, int base, float (*Li)[33]) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const bool w0 = wid == 0;
+  float* Xs = sm.X;
+  float* ucol = sm.ucol[wid];
+  float a[32];
+#pragma unroll
+  for (int c = 0; c < 32; ++c) a[c] = c <= lane ? Xs[(base + lane) * LDS + base + c] : 0.f;
+  bool ok = true;
+#pragma unroll
+  for (int c = 0; c < 32; ++c) {
+    ucol[lane] = a[c];
+    __syncwarp();
+    const float d = ucol[c];
+    ok = ok && (d > 0.f);
+    float inv;  // approximate reciprocal: the refinement absorbs its last-bit error
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(inv) : "f"(d));
+    const float l = a[c] * inv;
+    float u[32];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const float4 v = reinterpret_cast<const float4*>(ucol)[q];
+      u[4 * q] = v.x; u[4 * q + 1] = v.y; u[4 * q + 2] = v.z; u[4 * q + 3] = v.w;
+    }
+#pragma unroll
+    for (int j = c + 1; j < 32; ++j) a[j] = fmaf(-l, u[j], a[j]);
+    if (w0 && lane == c) {
+      sm.invd[base + c] = inv;
+      sm.dd[base + c] = d;
+    }
+    if (lane > c) a[c] = l;
+    __syncwarp();
+  }
+  // every warp has read the block before warp 0 overwrites it
+  __syncthreads();
+  if (w0) {
+#pragma unroll
+    for (int c = 0; c < 32; ++c)
+      if (c < lane) Xs[(base + lane) * LDS + base + c] = a[c];
+  }
+  __syncthreads();
+  float x[32];
+#pragma unroll
+  for (int i = 0; i < 32; ++i) x[i] = (i == lane) ? 1.f : 0.f;
+#pragma unroll
+  for (int k = 0; k < 31; ++k)
+#pragma unroll
+    for (int i = k + 1; i < 32; ++i) x[i] = fmaf(-Xs[(base + i) * LDS + base + k], x[k], x[i]);
+  if (w0) {
+#pragma unroll
+    for (int i = 0; i < 32; ++i) Li[i][lane] = x[i];
+  }
+  return ok;
+}
+
+// DIAG(k): the 64 x 64 diagonal tile as two 32-column steps, then the inverse
+// of the unit factor [[Li0, 0], [-Li1 L10 Li0, Li1]].
+// The tile is in sm.X (lower part); the inverse also stays in sm.Y and D, D^-1
+// in sm.dprev / sm.iprev for the next step.
+__device__ bool factor_diag(LgShared& sm, float* A, float* Linv, float* D, float* invD, int k) {
+  const int tid = threadIdx.x;
+  float* tk = tile_ptr(A, k, k);
+  if (tid == 0) sm.bad = 0;
+  __syncthreads();
+  if (!factor32(sm, 0, sm.Li[0]) && tid == 0) sm.bad = 1;
+  __syncthreads();
+  // panel rows 32..63: W = A10 Li0^T (unscaled), L10 = W D0^-1
+  for (int t = tid; t < 32 * 32; t += LG_THREADS) {
+    const int r = t >> 5, c = t & 31;
+    float w = 0.f;
+    for (int q = 0; q <= c; ++q) w = fmaf(sm.X[(32 + r) * LDS + q], sm.Li[0][c][q], w);
+    sm.W[r][c] = w;
+  }
+  __syncthreads();
+  for (int t = tid; t < 32 * 32; t += LG_THREADS) {
+    const int r = t >> 5, c = t & 31;
+    sm.X[(32 + r) * LDS + c] = sm.W[r][c] * sm.invd[c];
+  }
+  // trailing 32 x 32: A11 -= W D0^-1 W^T (lower)
+  for (int t = tid; t < 32 * 32; t += LG_THREADS) {
+    const int r = t >> 5, s = t & 31;
+    if (s > r) continue;
+    float acc = 0.f;
+#pragma unroll 8
+    for (int c = 0; c < 32; ++c) acc = fmaf(sm.W[r][c] * sm.invd[c], sm.W[s][c], acc);
+    sm.X[(32 + r) * LDS + 32 + s] -= acc;
+  }
+  __syncthreads();
+  if (!factor32(sm, 32, sm.Li[1]) && tid == 0) sm.bad = 1;
+  __syncthreads();
+  if (sm.bad) return false;
+  // off-diagonal block of the inverse: -Li1 (L10 Li0); W <- L10 Li0 first
+  for (int t = tid; t < 32 * 32; t += LG_THREADS) {
+    const int r = t >> 5, c = t & 31;
+    float v = 0.f;
+    for (int q = c; q < 32; ++q) v = fmaf(sm.X[(32 + r) * LDS + q], sm.Li[0][q][c], v);
+    sm.W[r][c] = v;
+  }
+  __syncthreads();
+  float* li = Linv + (size_t)k * TILE;
+  for (int t = tid; t < TILE; t += LG_THREADS) {
+    const int r = t >> 6, c = t & 63;
+    float v = 0.f;
+    if (r < 32) {
+      v = c < 32 && c <= r ? sm.Li[0][r][c] : 0.f;
+    } else if (c >= 32) {
+      v = c <= r ? sm.Li[1][r - 32][c - 32] : 0.f;
+    } else {
+      for (int q = 0; q <= r - 32; ++q) v = fmaf(-sm.Li[1][r - 32][q], sm.W[q][c], v);
+    }
+    li[t] = v;
+    sm.Y[r * LDS + c] = v;
+    tk[t] = c < r ? sm.X[r * LDS + c] : (c == r ? 1.f : 0.f);
+  }
+  if (tid < NB) {
+    D[k * NB + tid] = sm.dd[tid];
+    invD[k * NB + tid] = sm.invd[tid];
+    sm.dprev[tid] = sm.dd[tid];
+    sm.iprev[tid] = sm.invd[tid];
+  }
+  return true;
+}
+
+// Critical-path step k (one dedicated CTA, in order): for k > 0 first the
+// panel of tile (k, k-1) and its update of tile (k, k), from the inverse and D
+// of step k-1 kept in shared memory; then the factorisation of tile (k, k).
+__device__ bool task_diag_step(LgShared& sm, float* A, float* Linv, float* D, float* invD, int k, int* ver,
+                               int* status, long long timeout) {
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  if (k > 0) {
+    if (tid == 0) sm.bad = wait_geq(ver + tri2(k) + k - 1, k - 1, status, timeout) ? 0 : 1;
+    __syncthreads();
+    if (sm.bad) return false;
+    float* tp = tile_ptr(A, k, k - 1);
+    load_tile(sm.Z, tp, false);
+    __syncthreads();
+    float acc[4][4] = {};
+    gemm_nt(sm.Z, sm.Y, nullptr, acc);  // A_{k,k-1} Linv_{k-1}^T
+    __syncthreads();
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        const int r = ty + 16 * a, c = tx + 16 * b;
+        const float l = acc[a][b] * sm.iprev[c];
+        sm.Z[r * LDS + c] = l;
+        tp[r * NB + c] = l;
+      }
+    if (tid < NB) sm.dprev[tid] = -sm.dprev[tid];
+    __syncthreads();
+    if (tid == 0) {
+      __threadfence();
+      st_release(ver + tri2(k) + k - 1, k);  // tile (k, k-1) final
+      sm.bad = wait_geq(ver + tri2(k) + k, k - 1, status, timeout) ? 0 : 1;
+    }
+    __syncthreads();
+    if (sm.bad) return false;
+    load_tile(sm.X, tile_ptr(A, k, k), true);
+    __syncthreads();
+    // X -= (L D_{k-1}) L^T, lower part
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) acc[a][b] = sm.X[(ty + 16 * a) * LDS + tx + 16 * b];
+    gemm_nt(sm.Z, sm.Z, sm.dprev, acc);
+    __syncthreads();
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        const int r = ty + 16 * a, c = tx + 16 * b;
+        if (c <= r) sm.X[r * LDS + c] = acc[a][b];
+      }
+  } else {
+    load_tile(sm.X, tile_ptr(A, 0, 0), true);
+  }
+  __syncthreads();
+  return factor_diag(sm, A, Linv, D, invD, k);
+}
+
+// PANEL(i,k): L_ik = A_ik L_kk^-T D_k^-1
+__device__ void task_panel(LgShared& sm, float* A, const float* Linv, const float* invD, int i, int k) {
+  float* t = tile_ptr(A, i, k);
+  if (threadIdx.x < NB) sm.invd[threadIdx.x] = __ldcg(invD + k * NB + threadIdx.x);
+  load_tiles2(sm.X, t, sm.Y, Linv + (size_t)k * TILE);
+  __syncthreads();
+  float acc[4][4] = {};
+  gemm_nt(sm.X, sm.Y, nullptr, acc);
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int r = ty + 16 * a, c = tx + 16 * b;
+      t[r * NB + c] = acc[a][b] * sm.invd[c];
+    }
+}
+
+// UPDATE(i,j,k): A_ij -= (L_ik D_k) L_jk^T
+__device__ void task_update(LgShared& sm, float* A, const float* D, int i, int j, int k) {
+  float* t = tile_ptr(A, i, j);
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  // this thread's outputs of the target tile, read before the operands land
+  float acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = __ldcg(t + (ty + 16 * a) * NB + tx + 16 * b);
+  if (threadIdx.x < NB) sm.dd[threadIdx.x] = -__ldcg(D + k * NB + threadIdx.x);
+  load_tiles2(sm.X, tile_ptr(A, i, k), sm.Y, tile_ptr(A, j, k));
+  __syncthreads();
+  gemm_nt(sm.X, sm.Y, sm.dd, acc);  // acc = C - (L_ik D_k) L_jk^T
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int r = ty + 16 * a, c = tx + 16 * b;
+      if (i != j || c <= r) t[r * NB + c] = acc[a][b];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// kernels
+// ---------------------------------------------------------------------------
+
+// S (FP64 tiles) -> A (FP32 tiles); identical tile layout
+__global__ void k_lg_convert(const double* __restrict__ S, float* __restrict__ A, size_t count, const int* status) {
+  if (dpv_status(status)) return;
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < count / 2; q += stride) {
+    const double2 v = reinterpret_cast<const double2*>(S)[q];
+    reinterpret_cast<float2*>(A)[q] = make_float2(dpv_d2f_bits(v.x), dpv_d2f_bits(v.y));
+  }
+}
+
+// The factorisation task graph.  ver[tri(T)]: tile versions; ctr: task
+// counter; dsm: the SM of the critical-path CTA (+1).  CTA 0 runs the
+// diagonal steps in order and has its SM to itself (other CTAs there leave);
+// the other CTAs take panels and updates from the list.
+__global__ void __launch_bounds__(LG_THREADS) k_lg_factor(int T, const unsigned* __restrict__ tasks, int ntasks,
+                                                          float* A, float* Linv, float* D, float* invD, int* ver,
+                                                          int* ctr, int* dsm, int* status, long long timeout) {
+  extern __shared__ __align__(16) float lg_smem[];
+  LgShared& sm = *reinterpret_cast<LgShared*>(lg_smem);
+  if (threadIdx.x == 0) {
+    unsigned smid;
+    asm("mov.u32 %0, %%smid;" : "=r"(smid));
+    if (blockIdx.x == 0) {
+      st_release(dsm, (int)smid + 1);
+      sm.task = 0;
+    } else {
+      sm.task = wait_geq(dsm, 1, status, timeout) && ld_acquire(dsm) != (int)smid + 1 ? 1 : -1;
+    }
+  }
+  __syncthreads();
+  if (sm.task < 0) return;
+  if (blockIdx.x == 0) {
+    for (int k = 0; k < T; ++k) {
+      if (dpv_status(status)) return;
+      if (!task_diag_step(sm, A, Linv, D, invD, k, ver, status, timeout)) {
+        if (threadIdx.x == 0 && !dpv_status(status)) dpv_set_status(status, DST_NOT_SPD);
+        return;
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        __threadfence();
+        st_release(ver + tri2(k) + k, k + 1);
+      }
+    }
+    return;
+  }
+  for (;;) {
+    if (threadIdx.x == 0) sm.task = dpv_status(status) ? ntasks : atomicAdd(ctr, 1);
+    __syncthreads();
+    const int t = sm.task;
+    __syncthreads();
+    if (t >= ntasks) return;
+    const unsigned w = tasks[t];
+    const int type = (int)(w >> 30), k = (int)((w >> 20) & 1023u), i = (int)((w >> 10) & 1023u),
+              j = (int)(w & 1023u);
+    if (threadIdx.x == 0) {
+      bool ok;
+      if (type == TASK_PANEL) {
+        ok = wait_geq(ver + tri2(k) + k, k + 1, status, timeout) && wait_geq(ver + tri2(i) + k, k, status, timeout);
+      } else {
+        ok = wait_geq(ver + tri2(i) + k, k + 1, status, timeout) &&
+             wait_geq(ver + tri2(j) + k, k + 1, status, timeout) && wait_geq(ver + tri2(i) + j, k, status, timeout);
+      }
+      sm.bad = ok ? 0 : 1;
+    }
+    __syncthreads();
+    if (sm.bad) return;
+    int tv;  // the tile written
+    if (type == TASK_PANEL) {
+      task_panel(sm, A, Linv, invD, i, k);
+      tv = tri2(i) + k;
+    } else {
+      task_update(sm, A, D, i, j, k);
+      tv = tri2(i) + j;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      st_release(ver + tv, k + 1);
+    }
+  }
+}
+
+// this thread's 4 x 4 block (rows 4 rg.., columns 4 cg..) of a 64 x 64 tile
+struct TileRegs {
+  float4 m[4];
+};
+__device__ __forceinline__ TileRegs load_block(const float* M) {
+  const int cg = threadIdx.x & 15, rg = threadIdx.x >> 4;
+  TileRegs t;
+#pragma unroll
+  for (int rr = 0; rr < 4; ++rr) t.m[rr] = __ldcg(reinterpret_cast<const float4*>(M + (4 * rg + rr) * NB + 4 * cg));
+  return t;
+}
+
+// out[r] = sum_c M[r][c] v[c] (trans = false) or out[c] = sum_r M[r][c] v[r]
+// (trans = true) for a tile held as per-thread blocks; v, out in shared memory
+__device__ void tile_gemv(const TileRegs& t, const float* v, float* out, bool trans, float (*part)[NB + 1]) {
+  const int tid = threadIdx.x, cg = tid & 15, rg = tid >> 4;
+  if (!trans) {
+#pragma unroll
+    for (int rr = 0; rr < 4; ++rr)
+      part[cg][4 * rg + rr] =
+          t.m[rr].x * v[4 * cg] + t.m[rr].y * v[4 * cg + 1] + t.m[rr].z * v[4 * cg + 2] + t.m[rr].w * v[4 * cg + 3];
+  } else {
+    float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+#pragma unroll
+    for (int rr = 0; rr < 4; ++rr) {
+      const float vr = v[4 * rg + rr];
+      s0 = fmaf(t.m[rr].x, vr, s0);
+      s1 = fmaf(t.m[rr].y, vr, s1);
+      s2 = fmaf(t.m[rr].z, vr, s2);
+      s3 = fmaf(t.m[rr].w, vr, s3);
+    }
+    part[rg][4 * cg] = s0;
+    part[rg][4 * cg + 1] = s1;
+    part[rg][4 * cg + 2] = s2;
+    part[rg][4 * cg + 3] = s3;
+  }
+  __syncthreads();
+  if (tid < NB) {
+    float acc = 0.f;
+#pragma unroll
+    for (int g = 0; g < 16; ++g) acc += part[g][tid];
+    out[tid] = acc;
+  }
+  __syncthreads();
+}
+
+// Triangular solves + refinement.  flags[0..T): forward rows done (value =
+// sweep + 1), flags[T..2T): backward rows done; bar[2]: grid barrier.
+// xf: forward results (unit-lower solve), xb: backward results; xacc (FP64)
+// accumulates the sweeps; rhs: right-hand side of the current sweep.  CTA b
+// owns block rows i = b (mod grid), in both directions.
+__global__ void __launch_bounds__(LG_THREADS, 1) k_lg_solve(
+    int T, int n, const float* __restrict__ A, const float* __restrict__ Linv, const float* __restrict__ invD,
+    const double* __restrict__ S, const double* __restrict__ y, float* rhs, float* xf, float* xb, double* xacc,
+    double* __restrict__ dx, float* __restrict__ dxf, int sweeps, int* flags, int* bar, int* status,
+    long long timeout) {
+  __shared__ float acc[NB], vj[NB], prod[NB];
+  __shared__ float part[16][NB + 1];
+  __shared__ int ok;
+  const int tid = threadIdx.x;
+  const int n_pad = T * NB;
+  for (int sweep = 0; sweep < sweeps; ++sweep) {
+    if (dpv_status(status)) return;
+    // ---- forward: L u = rhs
+    for (int i = blockIdx.x; i < T; i += gridDim.x) {
+      if (tid < NB) acc[tid] = __ldcg(rhs + i * NB + tid);
+      // the tiles do not depend on the flags: each is loaded while waiting for the previous row
+      TileRegs m = load_block(i > 0 ? A + (size_t)tri2(i) * TILE : Linv + (size_t)i * TILE);
+      for (int j = 0; j < i; ++j) {
+        const TileRegs mn = load_block(j + 1 < i ? A + (size_t)(tri2(i) + j + 1) * TILE : Linv + (size_t)i * TILE);
+        if (tid == 0) ok = wait_geq(flags + j, sweep + 1, status, timeout) ? 1 : 0;
+        __syncthreads();
+        if (!ok) return;
+        if (tid < NB) vj[tid] = __ldcg(xf + j * NB + tid);
+        __syncthreads();
+        tile_gemv(m, vj, prod, false, part);
+        if (tid < NB) acc[tid] -= prod[tid];
+        m = mn;
+      }
+      __syncthreads();
+      tile_gemv(m, acc, prod, false, part);
+      if (tid < NB) xf[i * NB + tid] = prod[tid];
+      __syncthreads();
+      if (tid == 0) {
+        __threadfence();
+        st_release(flags + i, sweep + 1);
+      }
+    }
+    // ---- backward: L^T x = D^-1 u, rows descending
+    int last = blockIdx.x;
+    while (last + (int)gridDim.x < T) last += gridDim.x;
+    for (int i = last; i >= 0; i -= gridDim.x) {
+      if (tid < NB) acc[tid] = __ldcg(xf + i * NB + tid) * __ldcg(invD + i * NB + tid);
+      TileRegs m = load_block(i + 1 < T ? A + (size_t)(tri2(T - 1) + i) * TILE : Linv + (size_t)i * TILE);
+      for (int j = T - 1; j > i; --j) {
+        const TileRegs mn = load_block(j - 1 > i ? A + (size_t)(tri2(j - 1) + i) * TILE : Linv + (size_t)i * TILE);
+        if (tid == 0) ok = wait_geq(flags + T + j, sweep + 1, status, timeout) ? 1 : 0;
+        __syncthreads();
+        if (!ok) return;
+        if (tid < NB) vj[tid] = __ldcg(xb + j * NB + tid);
+        __syncthreads();
+        tile_gemv(m, vj, prod, true, part);
+        if (tid < NB) acc[tid] -= prod[tid];
+        m = mn;
+      }
+      __syncthreads();
+      tile_gemv(m, acc, prod, true, part);
+      if (tid < NB) xb[i * NB + tid] = prod[tid];
+      __syncthreads();
+      if (tid == 0) {
+        __threadfence();
+        st_release(flags + T + i, sweep + 1);
+      }
+    }
+    if (!grid_barrier(bar, gridDim.x, status, timeout)) return;
+    // ---- accumulate the correction, then the next residual
+    const int gt = blockIdx.x * LG_THREADS + tid, gs = gridDim.x * LG_THREADS;
+    for (int q = gt; q < n_pad; q += gs) xacc[q] = (sweep == 0 ? 0.0 : xacc[q]) + dpv_f2d_bits(__ldcg(xb + q));
+    if (sweep + 1 == sweeps) break;
+    if (!grid_barrier(bar, gridDim.x, status, timeout)) return;
+    // rho = y - S xacc in FP64, one warp per row
+    const int lane = tid & 31, gw = gt >> 5, nw = gs >> 5;
+    for (int row = gw; row < n_pad; row += nw) {
+      double sacc = 0.0;
+      if (row < n)
+        for (int c = lane; c < n; c += 32)
+          sacc += S[c <= row ? dpv_s_index(row, c, NB) : dpv_s_index(c, row, NB)] * __ldcg(xacc + c);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, o);
+      if (lane == 0) rhs[row] = row < n ? dpv_d2f_bits(y[row] - sacc) : 0.f;
+    }
+    if (!grid_barrier(bar, gridDim.x, status, timeout)) return;
+  }
+  const int gt = blockIdx.x * LG_THREADS + tid, gs = gridDim.x * LG_THREADS;
+  for (int q = gt; q < n; q += gs) {
+    const double v = __ldcg(xacc + q);
+    dx[q] = v;
+    dxf[q] = dpv_d2f_bits(v);
+  }
+}
+
+__global__ void k_lg_init_rhs(int n, int n_pad, const double* __restrict__ y, float* __restrict__ rhs,
+                              const int* status) {
+  if (dpv_status(status)) return;
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q < n_pad) rhs[q] = q < n ? dpv_d2f_bits(y[q]) : 0.f;
+}
+
+// Worker task list in dependency order.  The critical-path CTA does DIAG(k),
+// PANEL(k, k-1) and UPDATE(k, k, k-1); the list holds every other panel and
+// update: step k+1's column update and panels come before the bulk of step
+// k's trailing update, whose columns run left to right.
+std::vector<unsigned> build_tasks(int T) {
+  std::vector<unsigned> v;
+  v.reserve((size_t)T * T * T / 6 + (size_t)T * T + 16);
+  for (int i = 2; i < T; ++i) v.push_back(pack_task(TASK_PANEL, 0, i, 0));
+  for (int k = 0; k + 1 < T; ++k) {
+    for (int i = k + 2; i < T; ++i) v.push_back(pack_task(TASK_UPDATE, k, i, k + 1));
+    for (int i = k + 3; i < T; ++i) v.push_back(pack_task(TASK_PANEL, k + 1, i, k + 1));
+    for (int j = k + 2; j < T; ++j)
+      for (int i = j; i < T; ++i) v.push_back(pack_task(TASK_UPDATE, k, i, j));
+  }
+  return v;
+}
+
+struct TaskCache {
+  std::mutex mu;
+  std::map<std::pair<int, int>, unsigned*> lists;  // (device, T) -> device task list
+  std::map<std::pair<int, int>, int> counts;
+};
+TaskCache& task_cache() {
+  static TaskCache c;
+  return c;
+}
+
+int co_resident(ba_handle_t h, const void* fn, size_t smem = 0) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, LG_THREADS, smem) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return per_sm * h->num_sms;
+}
+
+}  // namespace
+
+long long dpv_large_scratch_floats(int n_pad) {
+  const long long T = n_pad / NB;
+  // tiles of A, inverses of the diagonal factors, D, D^-1, rhs, xf, xb
+  return (long long)tri2((int)T) * TILE + T * TILE + 5LL * n_pad;
+}
+
+ba_status_t dpv_solve_blocked(ba_handle_t h, int refine) {
+  Workspace* ws = h->ws;
+  const int n = h->n, n_pad = h->n_pad;
+  if (h->TS != NB || n_pad % NB) return dpv_fail(h, BA_ERR_UNSUPPORTED, "large solver needs 64-row tiles");
+  const int T = n_pad / NB;
+  if (T > LG_MAX_T) return dpv_fail(h, BA_ERR_UNSUPPORTED, "pose system above 65472 unknowns");
+  // the task list of this size, built once per device
+  unsigned* tasks = nullptr;
+  int ntasks = 0;
+  {
+    TaskCache& tc = task_cache();
+    std::lock_guard<std::mutex> lk(tc.mu);
+    auto key = std::make_pair(h->device, T);
+    auto it = tc.lists.find(key);
+    if (it == tc.lists.end()) {
+      std::vector<unsigned> v = build_tasks(T);
+      unsigned* d = nullptr;
+      if (cudaMalloc(&d, sizeof(unsigned) * v.size()) != cudaSuccess) {
+        cudaGetLastError();
+        return dpv_fail(h, BA_ERR_OOM, "large solver task list");
+      }
+      DPV_CUDA(h, cudaMemcpy(d, v.data(), sizeof(unsigned) * v.size(), cudaMemcpyHostToDevice));
+      tc.lists[key] = d;
+      tc.counts[key] = (int)v.size();
+    }
+    tasks = tc.lists[key];
+    ntasks = tc.counts[key];
+  }
+  ba_status_t s;
+  const long long nsync = tri2(T) + 2LL * T + 8;  // versions, row flags, counter, barrier, critical SM
+  if ((s = dpv_grow(h, ws->lg_sync, nsync, "large solver sync"))) return s;
+  float* A = ws->L.p;
+  float* Linv = A + (size_t)tri2(T) * TILE;
+  float* D = Linv + (size_t)T * TILE;
+  float* invD = D + n_pad;
+  float* rhs = invD + n_pad;
+  float* xf = rhs + n_pad;
+  float* xb = xf + n_pad;
+  int* ver = ws->lg_sync.p;
+  int* flags = ver + tri2(T);
+  int* ctr = flags + 2 * T;
+  int* bar = ctr + 1;   // two ints
+  int* dsm = bar + 2;
+  int* status = ws->status;
+  cudaStream_t st = h->stream;
+  DPV_CUDA(h, cudaMemsetAsync(ver, 0, sizeof(int) * nsync, st));
+  const size_t count = (size_t)tri2(T) * TILE;
+  k_lg_convert<<<4 * h->num_sms, 256, 0, st>>>(ws->S.p, A, count, status);
+  ++h->launches;
+  k_lg_init_rhs<<<(n_pad + 255) / 256, 256, 0, st>>>(n, n_pad, ws->y.p, rhs, status);
+  ++h->launches;
+  long long timeout = h->opt.timeout_cycles;
+  {
+    // at most two CTAs per SM: the single-warp pivot chain of DIAG shares its
+    // SM with fewer update CTAs
+    const size_t smem = sizeof(LgShared);
+    static bool attr = false;
+    if (!attr) {
+      DPV_CUDA(h, cudaFuncSetAttribute(k_lg_factor, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      attr = true;
+    }
+    const int grid = std::min(co_resident(h, (const void*)k_lg_factor, smem), 2 * h->num_sms);
+    if (grid <= 1) return dpv_fail(h, BA_ERR_CUDA, "large solver occupancy");
+    void* args[] = {(void*)&T,   (void*)&tasks, (void*)&ntasks, (void*)&A,      (void*)&Linv,    (void*)&D,
+                    (void*)&invD, (void*)&ver,  (void*)&ctr,    (void*)&dsm,    (void*)&status, (void*)&timeout};
+    DPV_CUDA(h, cudaLaunchCooperativeKernel((const void*)k_lg_factor, dim3(grid), dim3(LG_THREADS), args, smem, st));
+    ++h->launches;
+  }
+  {
+    const int maxg = co_resident(h, (const void*)k_lg_solve);
+    const int grid = std::min(T, maxg);
+    if (grid <= 0) return dpv_fail(h, BA_ERR_CUDA, "large solver occupancy");
+    const double* S = ws->S.p;
+    const double* y = ws->y.p;
+    double* xacc = ws->r64.p;
+    double* dx = ws->dx.p;
+    float* dxf = ws->tmpv.p;
+    int sweeps = refine + 1;
+    int n_ = n;
+    void* args[] = {(void*)&T,   (void*)&n_,    (void*)&A,   (void*)&Linv,  (void*)&invD,   (void*)&S,
+                    (void*)&y,   (void*)&rhs,   (void*)&xf,  (void*)&xb,    (void*)&xacc,   (void*)&dx,
+                    (void*)&dxf, (void*)&sweeps, (void*)&flags, (void*)&bar, (void*)&status, (void*)&timeout};
+    DPV_CUDA(h, cudaLaunchCooperativeKernel((const void*)k_lg_solve, dim3(grid), dim3(LG_THREADS), args, 0, st));
+    ++h->launches;
+  }
+  DPV_CUDA(h, cudaGetLastError());
+  return BA_OK;
+}
