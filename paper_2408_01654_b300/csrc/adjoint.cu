@@ -73,13 +73,13 @@ __device__ void tangent_of(const double* p, const double* dt, const double* dq, 
 
 // Cotangent of the final poses, given per coordinate of (t, q), mapped to the
 // tangent space: xb[a][k] = <grad_a, d(t, q)/d xi_k>.  Fixed poses get 0.
-__global__ void k_adj_init(int N, int fixed, const double* __restrict__ poses, const double* __restrict__ grad,
-                           double* __restrict__ xb, const int* status) {
+__global__ void k_adj_init(int N, const int* __restrict__ fdx, const double* __restrict__ poses,
+                           const double* __restrict__ grad, double* __restrict__ xb, const int* status) {
   if (dpv_status(status)) return;
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= 6 * N) return;
   const int a = q / 6, k = q - 6 * a;
-  if (a < fixed) {
+  if (fdx[a] < 0) {
     xb[q] = 0.0;
     return;
   }
@@ -98,7 +98,8 @@ __global__ void k_adj_init(int N, int fixed, const double* __restrict__ poses, c
 // Depth part, thread k: the full cotangent of d_{s+1,k} (the part that passed
 // the clamp + the per-edge terms of iteration s+1, patch-major) times the
 // clamp's derivative [d_s + dd_s > d_min].
-__global__ void k_adj_retract(int N, int fixed, int P, float d_min, const double* __restrict__ xb_next,
+__global__ void k_adj_retract(int N, const int* __restrict__ fdx, int P, float d_min,
+                              const double* __restrict__ xb_next,
                               const double* __restrict__ dx_s, const double* __restrict__ poses_s,
                               double* __restrict__ vext, double* __restrict__ xb_cur,
                               const float* __restrict__ db_next, const float* __restrict__ gd,
@@ -108,15 +109,15 @@ __global__ void k_adj_retract(int N, int fixed, int P, float d_min, const double
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q < 6 * N) {
     const int a = q / 6, k = q - 6 * a;
-    if (a < fixed) {
+    const int o = fdx[a];
+    if (o < 0) {
       xb_cur[q] = 0.0;
       return;
     }
-    const int af = a - fixed;
     D2 x[6], T[7];
 #pragma unroll
     for (int m = 0; m < 6; ++m) {
-      x[m] = dual_const<double, 2>(dx_s[6 * af + m]);
+      x[m] = dual_const<double, 2>(dx_s[o + m]);
       if (m == k) x[m].g[0] = 1.0;
     }
     const double* p = poses_s + 7 * (size_t)a;
@@ -145,7 +146,7 @@ __global__ void k_adj_retract(int N, int fixed, int P, float d_min, const double
 #pragma unroll
       for (int m = 0; m < 6; ++m) out[c] += eta[m] * xn[m];
     }
-    vext[6 * af + k] = out[0];
+    vext[o + k] = out[0];
     xb_cur[q] = out[1];
     return;
   }
@@ -219,7 +220,8 @@ __device__ __forceinline__ void adjoint_apply(const RelPose& T, const float* v, 
 // Step 3 for iteration s: one CTA per patch group, one warp per (source,
 // target) run, one lane per edge.
 __global__ void __launch_bounds__(ADJ_THREADS) k_adj_edges(
-    int G, int P, int fixed, float z_min, const int* __restrict__ gptr, const int* __restrict__ grun,
+    int G, int P, const int* __restrict__ fdx, float z_min, const int* __restrict__ gptr,
+    const int* __restrict__ grun,
     const int* __restrict__ gnr, const unsigned* __restrict__ eslot, const int* __restrict__ perm,
     const int* __restrict__ pmpos, const int* __restrict__ win, const float* __restrict__ posef,
     const float* __restrict__ patches, const float* __restrict__ targets, const float* __restrict__ weights,
@@ -244,13 +246,14 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_edges(
     const int fi = wf[si], fj = wf[sj];
     RelPose T;
     dpv_relative_pose_f(posef + 16 * (size_t)fi, posef + 16 * (size_t)fj, T);
+    const int oi = fdx[fi], oj = fdx[fj];
     float li[6], lj[6], di[6], dj[6];
 #pragma unroll
     for (int m = 0; m < 6; ++m) {
-      li[m] = fi >= fixed ? lam_p[6 * (fi - fixed) + m] : 0.f;
-      lj[m] = fj >= fixed ? lam_p[6 * (fj - fixed) + m] : 0.f;
-      di[m] = fi >= fixed ? (float)dx_s[6 * (fi - fixed) + m] : 0.f;
-      dj[m] = fj >= fixed ? (float)dx_s[6 * (fj - fixed) + m] : 0.f;
+      li[m] = oi >= 0 ? lam_p[oi + m] : 0.f;
+      lj[m] = oj >= 0 ? lam_p[oj + m] : 0.f;
+      di[m] = oi >= 0 ? dpv_d2f_bits(dx_s[oi + m]) : 0.f;
+      dj[m] = oj >= 0 ? dpv_d2f_bits(dx_s[oj + m]) : 0.f;
     }
     float ml[6], md[6];
     adjoint_apply(T, li, ml);
@@ -337,16 +340,16 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_edges(
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) gdel[m] += __shfl_xor_sync(0xffffffffu, gdel[m], o);
     if (lane == 0) {
-      if (fj >= fixed)
-        for (int m = 0; m < 6; ++m) atomicAdd(xb + 6 * (size_t)fj + m, (double)gdel[m]);
-      if (fi >= fixed) {
+      if (oj >= 0)
+        for (int m = 0; m < 6; ++m) atomicAdd(xb + 6 * (size_t)fj + m, dpv_f2d_bits(gdel[m]));
+      if (oi >= 0) {
         // d delta / d xi_i = -Ad(T_ij):  xb_i -= Ad^T gdel = (R^T g_rho, txR^T g_rho + R^T g_phi)
         for (int c = 0; c < 3; ++c) {
           const float pr = T.R[c] * gdel[0] + T.R[3 + c] * gdel[1] + T.R[6 + c] * gdel[2];
           const float pp = T.txR[c] * gdel[0] + T.txR[3 + c] * gdel[1] + T.txR[6 + c] * gdel[2] +
                            T.R[c] * gdel[3] + T.R[3 + c] * gdel[4] + T.R[6 + c] * gdel[5];
-          atomicAdd(xb + 6 * (size_t)fi + c, -(double)pr);
-          atomicAdd(xb + 6 * (size_t)fi + 3 + c, -(double)pp);
+          atomicAdd(xb + 6 * (size_t)fi + c, dpv_f2d_bits(-pr));
+          atomicAdd(xb + 6 * (size_t)fi + 3 + c, dpv_f2d_bits(-pp));
         }
       }
     }
@@ -373,7 +376,7 @@ ba_status_t dpv_tape_reserve(ba_handle_t h, int iters) {
   ba_status_t s;
   if ((s = dpv_grow(h, ws->tp_poses, 7LL * h->N * (iters + 1), "tape poses")) ||
       (s = dpv_grow(h, ws->tp_patches, 27LL * h->P * iters, "tape patches")) ||
-      (s = dpv_grow(h, ws->tp_dx, (long long)h->n * iters, "tape steps")) ||
+      (s = dpv_grow(h, ws->tp_dx, (long long)h->n_pad * iters, "tape steps")) ||
       (s = dpv_grow(h, ws->tp_dd, (long long)h->P * iters, "tape depth steps")))
     return s;
   return BA_OK;
@@ -391,7 +394,7 @@ ba_status_t dpv_tape_state(ba_handle_t h, int it) {
 
 ba_status_t dpv_tape_step(ba_handle_t h, int it) {
   Workspace* ws = h->ws;
-  DPV_CUDA(h, cudaMemcpyAsync(ws->tp_dx.p + (long long)h->n * it, ws->dx.p, sizeof(double) * h->n,
+  DPV_CUDA(h, cudaMemcpyAsync(ws->tp_dx.p + (long long)h->n_pad * it, ws->dx.p, sizeof(double) * h->n_pad,
                               cudaMemcpyDeviceToDevice, h->stream));
   DPV_CUDA(h, cudaMemcpyAsync(ws->tp_dd.p + (long long)h->P * it, ws->dd.p, sizeof(float) * h->P,
                               cudaMemcpyDeviceToDevice, h->stream));
@@ -417,7 +420,7 @@ extern "C" ba_status_t ba_backward(ba_handle_t h, const double* grad_poses, cons
   ba_status_t s;
   // the system geometry of the recorded call (a later ba_step may have used another fixed count)
   if ((s = dpv_ensure_system(h, h->tape_fixed))) return s;
-  const int fixed = h->fixed;
+  const int* fdx = ws->fdx.p;
   const long long E2 = 2LL * (E > 0 ? E : 1);
   if ((s = dpv_grow(h, ws->ad_xb, 12LL * N, "pose cotangents")) ||
       (s = dpv_grow(h, ws->ad_w, 2LL * P, "depth cotangents")) ||
@@ -427,6 +430,7 @@ extern "C" ba_status_t ba_backward(ba_handle_t h, const double* grad_poses, cons
       (!grad_targets && (s = dpv_grow(h, ws->ad_gt, E2, "target cotangents"))) ||
       (!grad_weights && (s = dpv_grow(h, ws->ad_gw, E2, "weight cotangents"))))
     return s;
+  DPV_CUDA(h, cudaMemsetAsync(ws->ad_v.p, 0, sizeof(double) * h->n_pad, h->stream));
   float* gT = grad_targets ? grad_targets : ws->ad_gt.p;
   float* gW = grad_weights ? grad_weights : ws->ad_gw.p;
   if (E > 0) {
@@ -439,7 +443,7 @@ extern "C" ba_status_t ba_backward(ba_handle_t h, const double* grad_poses, cons
   float* wc = ws->ad_w.p + P;
   dpv_prof_begin(h, BA_KERNEL_ADJOINT);
   if (grad_poses) {
-    k_adj_init<<<(6 * N + 127) / 128, 128, 0, h->stream>>>(N, fixed, ws->tp_poses.p + 7LL * N * K, grad_poses, xbn,
+    k_adj_init<<<(6 * N + 127) / 128, 128, 0, h->stream>>>(N, fdx, ws->tp_poses.p + 7LL * N * K, grad_poses, xbn,
                                                              ws->status);
     ++h->launches;
   } else {
@@ -454,11 +458,11 @@ extern "C" ba_status_t ba_backward(ba_handle_t h, const double* grad_poses, cons
   for (int it = K - 1; it >= 0; --it) {
     const double* poses_s = ws->tp_poses.p + 7LL * N * it;
     float* patches_s = ws->tp_patches.p + 27LL * P * it;
-    const double* dx_s = ws->tp_dx.p + (long long)h->n * it;
+    const double* dx_s = ws->tp_dx.p + (long long)h->n_pad * it;
     const float* dd_s = ws->tp_dd.p + (long long)P * it;
     dpv_prof_begin(h, BA_KERNEL_ADJOINT);
     const int nthr = 6 * N + P;
-    k_adj_retract<<<(nthr + 127) / 128, 128, 0, h->stream>>>(N, fixed, P, h->opt.d_min, xbn, dx_s, poses_s,
+    k_adj_retract<<<(nthr + 127) / 128, 128, 0, h->stream>>>(N, fdx, P, h->opt.d_min, xbn, dx_s, poses_s,
                                                                ws->ad_v.p, xbc, wn, gdp, ws->pptr.p, patches_s, dd_s,
                                                                wc, ws->status);
     ++h->launches;
@@ -479,7 +483,7 @@ extern "C" ba_status_t ba_backward(ba_handle_t h, const double* grad_poses, cons
     if (s) return s;
     dpv_prof_begin(h, BA_KERNEL_ADJOINT);
     k_adj_edges<<<h->ngroups, ADJ_THREADS, 0, h->stream>>>(
-        h->G, P, fixed, h->opt.z_min, ws->gptr.p, ws->grun.p, ws->gnr.p, ws->eslot.p, ws->perm.p, ws->pmpos.p,
+        h->G, P, fdx, h->opt.z_min, ws->gptr.p, ws->grun.p, ws->gnr.p, ws->eslot.p, ws->perm.p, ws->pmpos.p,
         ws->win.p, ws->posef.p, patches_s, h->targets, h->weights, ws->intr, ws->tmpv.p, ws->ad_lamd.p, dx_s, dd_s,
         gT, gW, ws->ad_gd.p, xbc, ws->status);
     ++h->launches;

@@ -89,20 +89,73 @@ int auto_group(ba_handle_t h, int P) {
   return 8;
 }
 
+// fdx[f]: offset of frame f's six unknowns in the concatenated system vectors,
+// -1 for the first `fixed` frames of each problem
+__global__ void k_build_fdx(int N, int fixed, const int* __restrict__ fprob, const int* __restrict__ frame_off,
+                            const SysDesc* __restrict__ sysd, int* __restrict__ fdx) {
+  const int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= N) return;
+  const int b = fprob[f];
+  const int lf = f - frame_off[b];
+  fdx[f] = lf < fixed ? -1 : sysd[b].voff + 6 * (lf - fixed);
+}
+
+// Per-problem pose systems for a fixed-pose count: geometry, storage and the
+// frame -> unknown map.
 ba_status_t ensure_system(ba_handle_t h, int fixed) {
   Workspace* ws = h->ws;
   if (fixed == h->fixed) return BA_OK;
   h->fixed = fixed;
-  h->n = 6 * (h->N - fixed);
-  system_geometry(h->n, h->TS, h->T, h->n_pad);
-  const long long nS = (long long)h->T * (h->T + 1) / 2 * h->TS * h->TS;
+  const int B = h->nprob;
+  h->sys.assign(B, SysDesc{});
+  for (auto& v : h->small_nq) v.clear();
+  h->large_sys.clear();
+  long long soff = 0, voff = 0, nsum = 0, large_scratch = 0;
+  for (int b = 0; b < B; ++b) {
+    SysDesc& d = h->sys[b];
+    d.problem = b;
+    d.n = 6 * (h->frame_off[b + 1] - h->frame_off[b] - fixed);
+    system_geometry(d.n, d.TS, d.T, d.n_pad);
+    d.soff = soff;
+    d.voff = (int)voff;
+    soff += (long long)d.T * (d.T + 1) / 2 * d.TS * d.TS;
+    voff += d.n_pad;
+    nsum += d.n;
+    if (d.n == 0) continue;
+    if (d.n <= DPV_SMALL_N) {
+      h->small_nq[d.n_pad / 32].push_back(b);
+    } else {
+      h->large_sys.push_back(b);
+      large_scratch = std::max(large_scratch, dpv_large_scratch_floats(d.n_pad));
+    }
+  }
+  if (voff > (1LL << 30) || soff > (1LL << 40)) return dpv_fail(h, BA_ERR_UNSUPPORTED, "pose systems too large");
+  h->n = (int)nsum;
+  h->n_pad = (int)voff;
+  h->nS = soff;
+  h->TS = h->sys[0].TS;
+  h->T = h->sys[0].T;
   ba_status_t s;
-  if ((s = dpv_grow(h, ws->S, nS, "pose system")) || (s = dpv_grow(h, ws->y, h->n_pad, "rhs")) ||
-      (s = dpv_grow(h, ws->dx, h->n_pad, "step")) || (s = dpv_grow(h, ws->r64, h->n_pad, "residual")) ||
-      (s = dpv_grow(h, ws->tmpv, h->n_pad, "vector")))
+  if ((s = dpv_grow(h, ws->S, soff, "pose system")) || (s = dpv_grow(h, ws->y, voff, "rhs")) ||
+      (s = dpv_grow(h, ws->dx, voff, "step")) || (s = dpv_grow(h, ws->r64, voff, "residual")) ||
+      (s = dpv_grow(h, ws->tmpv, voff, "vector")) || (s = dpv_grow(h, ws->sysd, B, "system table")) ||
+      (s = dpv_grow(h, ws->syslist, B, "system lists")) || (s = dpv_grow(h, ws->fdx, h->N, "frame map")))
     return s;
-  if (h->n > DPV_SMALL_N && (s = dpv_grow(h, ws->L, dpv_large_scratch_floats(h->n_pad), "factor"))) return s;
-  return BA_OK;
+  if (large_scratch > 0 && (s = dpv_grow(h, ws->L, large_scratch, "factor"))) return s;
+  DPV_CUDA(h, cudaMemcpyAsync(ws->sysd.p, h->sys.data(), sizeof(SysDesc) * B, cudaMemcpyHostToDevice, h->stream));
+  // the solver launches read their system indices from syslist: small systems
+  // grouped by block count, then the large ones
+  std::vector<int> lists;
+  for (auto& v : h->small_nq) lists.insert(lists.end(), v.begin(), v.end());
+  lists.insert(lists.end(), h->large_sys.begin(), h->large_sys.end());
+  if (!lists.empty())
+    DPV_CUDA(h, cudaMemcpyAsync(ws->syslist.p, lists.data(), sizeof(int) * lists.size(), cudaMemcpyHostToDevice,
+                                h->stream));
+  k_build_fdx<<<(h->N + 255) / 256, 256, 0, h->stream>>>(h->N, fixed, ws->fprob.p, ws->fprob.p + h->N,
+                                                          ws->sysd.p, ws->fdx.p);
+  ++h->launches;
+  DPV_CUDA(h, cudaGetLastError());
+  return BA_OK;  // (pageable-source async copies are staged before they return)
 }
 
 }  // namespace
@@ -185,7 +238,8 @@ ba_status_t ba_destroy(ba_handle_t h) {
     release(ws->pterm); release(ws->posef);
     release(ws->tp_poses); release(ws->tp_patches); release(ws->tp_dx); release(ws->tp_dd);
     release(ws->ad_xb); release(ws->ad_w); release(ws->ad_gd); release(ws->ad_lamd); release(ws->ad_v);
-    release(ws->ad_gt); release(ws->ad_gw); release(ws->lg_sync);
+    release(ws->ad_gt); release(ws->ad_gw); release(ws->lg_sync); release(ws->fprob); release(ws->gprob);
+    release(ws->fdx); release(ws->sysd); release(ws->syslist);
     delete ws;
   }
   prof_clear(h);
@@ -240,6 +294,11 @@ ba_status_t ba_set_graph(ba_handle_t h, int N, int P, int E, double* poses, floa
     return dpv_fail(h, BA_ERR_INVALID_ARG, "ba_set_graph: targets/weights must be 8-byte aligned");
   Workspace* ws = h->ws;
   h->have_graph = 0;
+  // the frame -> unknown map survives a rebinding with the same frame count
+  const bool same_frames = h->nprob == 1 && h->N == N && h->fixed >= 0;
+  h->nprob = 1;
+  h->frame_off.assign({0, N});
+  h->min_frames = N;
   h->N = N;
   h->P = P;
   h->E = E;
@@ -249,7 +308,7 @@ ba_status_t ba_set_graph(ba_handle_t h, int N, int P, int E, double* poses, floa
   h->weights = weights;
   h->G = h->opt.patches_per_group > 0 ? h->opt.patches_per_group : auto_group(h, P);
   h->ngroups = (P + h->G - 1) / h->G;
-  h->fixed = -1;
+  if (!same_frames) h->fixed = -1;
   h->tape_valid = 0;
   h->kk_bits = bits_for((unsigned long long)P);
   ba_status_t s;
@@ -266,15 +325,19 @@ ba_status_t ba_set_graph(ba_handle_t h, int N, int P, int E, double* poses, floa
       (s = dpv_grow(h, ws->gptr, Gn, "groups")) ||
       (s = dpv_grow(h, ws->win, Gn * DPV_WMAX, "windows")) || (s = dpv_grow(h, ws->wlen, Gn, "windows")) ||
       (s = dpv_grow(h, ws->pmpos, En, "patch-major positions")) || (s = dpv_grow(h, ws->pptr, (long long)P + 1, "patch CSR")) ||
-      (s = dpv_grow(h, ws->pterm, 4 * En, "edge depth terms")) || (s = dpv_grow(h, ws->posef, 16LL * N, "pose table")))
+      (s = dpv_grow(h, ws->pterm, 4 * En, "edge depth terms")) || (s = dpv_grow(h, ws->posef, 16LL * N, "pose table")) ||
+      (s = dpv_grow(h, ws->fprob, (long long)N + 2, "frame problems")) || (s = dpv_grow(h, ws->gprob, Gn, "group problems")))
     return s;
+  // one problem: every frame and group belongs to problem 0; frame_off = {0, N} follows fprob
+  DPV_CUDA(h, cudaMemsetAsync(ws->fprob.p, 0, sizeof(int) * N, h->stream));
+  DPV_CUDA(h, cudaMemcpyAsync(ws->fprob.p + N, h->frame_off.data(), sizeof(int) * 2, cudaMemcpyHostToDevice, h->stream));
+  DPV_CUDA(h, cudaMemsetAsync(ws->gprob.p, 0, sizeof(int) * Gn, h->stream));
   DPV_CUDA(h, cudaMemsetAsync(ws->status, 0, sizeof(int), h->stream));
   DPV_CUDA(h, cudaMemcpyAsync(ws->intr, intrinsics, 4 * sizeof(float), cudaMemcpyDefault, h->stream));
   dpv_prof_begin(h, BA_KERNEL_PREPROCESS);
   s = dpv_preprocess(h, ii, jj, kk);
   dpv_prof_end(h);
   if (s) return s;
-  if ((s = ensure_system(h, 0))) return s;  // size the system for every pose free
   h->have_graph = 1;
   return BA_OK;
 }
@@ -282,7 +345,8 @@ ba_status_t ba_set_graph(ba_handle_t h, int N, int P, int E, double* poses, floa
 static ba_status_t check_step_args(ba_handle_t h, int fixed_poses) {
   if (!h) return BA_ERR_INVALID_ARG;
   if (!h->have_graph) return dpv_fail(h, BA_ERR_STATE, "no graph bound (call ba_set_graph first)");
-  if (fixed_poses < 0 || fixed_poses > h->N) return dpv_fail(h, BA_ERR_INVALID_ARG, "fixed_poses out of range");
+  if (fixed_poses < 0 || fixed_poses > h->min_frames)
+    return dpv_fail(h, BA_ERR_INVALID_ARG, "fixed_poses out of range");
   return BA_OK;
 }
 
@@ -306,7 +370,7 @@ ba_status_t ba_step(ba_handle_t h, int iters, int fixed_poses) {
     if ((s = dpv_assemble(h, it, prepared))) return s;
     int retracted = 0;
     // the one-CTA solver re-zeroes S and y for the next iteration's assembly
-    const int reset = it + 1 < run && h->n <= DPV_SMALL_N;
+    const int reset = it + 1 < run && h->large_sys.empty();
     dpv_prof_begin(h, BA_KERNEL_SOLVE);
     s = dpv_solve(h, &retracted, reset);
     dpv_prof_end(h);

@@ -37,6 +37,8 @@
 // one FP64 add (FP64 arithmetic runs at ~1/64 of the FP32 rate on this part).
 #include "internal.cuh"
 
+#include <algorithm>
+
 namespace {
 
 constexpr int AS_THREADS = 512;
@@ -58,7 +60,7 @@ static_assert(DPV_WMAX * DPV_WMAX + 8 * (DPV_WMAX * 21 + DPV_WMAX * 6) <= 4 * AS
 size_t assemble_smem_bytes(int G) {
   return sizeof(float) * ((size_t)DPV_RMAX * NV * 2 + (size_t)DPV_RMAX * 21 + (size_t)G * EH_STRIDE + 2 * G +
                           3 * G + (size_t)AS_WARPS * 32 * ROWF) +
-         sizeof(int) * (DPV_RMAX + DPV_WMAX);
+         sizeof(int) * (DPV_RMAX + 2 * DPV_WMAX);
 }
 
 __device__ __forceinline__ int tri_row(int t) {
@@ -69,7 +71,8 @@ __device__ __forceinline__ int tri_row(int t) {
 }
 
 __global__ void __launch_bounds__(AS_THREADS) k_assemble(
-    int G, int P, int fixed, int TS, float lambda_d, float z_min, const int* __restrict__ gptr,
+    int G, int P, const int* __restrict__ fdx, const int* __restrict__ gprob, const SysDesc* __restrict__ sysd,
+    float lambda_d, float z_min, const int* __restrict__ gptr,
     const int* __restrict__ grun, const int* __restrict__ gnr, const unsigned* __restrict__ eslot,
     const int* __restrict__ perm,
     const int* __restrict__ pmpos, const int* __restrict__ pptr, const int* __restrict__ win,
@@ -94,6 +97,9 @@ __global__ void __launch_bounds__(AS_THREADS) k_assemble(
   float* rows = pd + 3 * G;                                 // [warps][32][ROWF]
   int* rsl = reinterpret_cast<int*>(rows + AS_WARPS * 32 * ROWF);  // [RMAX] si | sj << 8
   int* wf = rsl + DPV_RMAX;                                 // [W] window frames
+  int* fr = wf + DPV_WMAX;                                  // [W] unknown row in the group's system, -1 fixed
+  // the group's pose system (every frame of a group belongs to one problem)
+  const SysDesc sd = sysd[gprob[g]];
 
   float K[4];
 #pragma unroll
@@ -101,7 +107,12 @@ __global__ void __launch_bounds__(AS_THREADS) k_assemble(
 
   // ---- phase 0 ------------------------------------------------------------
   for (int q = tid; q < G * EH_STRIDE; q += AS_THREADS) Eh[q] = 0.f;
-  for (int q = tid; q < w; q += AS_THREADS) wf[q] = win[g * DPV_WMAX + q];
+  for (int q = tid; q < w; q += AS_THREADS) {
+    const int f = win[g * DPV_WMAX + q];
+    const int o = fdx[f];
+    wf[q] = f;
+    fr[q] = o < 0 ? -1 : o - sd.voff;
+  }
   for (int q = tid; q < G; q += AS_THREADS) {
     const int k = g * G + q;
     float x0 = 0.f, x1 = 0.f, d = 1.f;
@@ -330,8 +341,8 @@ __global__ void __launch_bounds__(AS_THREADS) k_assemble(
     const int blk = t >> 2, ha = (t >> 1) & 1, hb = t & 1;
     const int a = tri_row(blk), b = blk - tri(a, 0);
     if (a == b && hb > ha) continue;
-    const int fa = wf[a], fb = wf[b];
-    if (fa < fixed || fb < fixed) continue;
+    const int ra0 = fr[a], rb0 = fr[b];
+    if (ra0 < 0 || rb0 < 0) continue;
     const int R0 = 6 * a + 3 * ha, C0 = 6 * b + 3 * hb;
     DF acc[3][3];
     {
@@ -386,29 +397,29 @@ __global__ void __launch_bounds__(AS_THREADS) k_assemble(
           }
       }
     }
-    const int gr = 6 * (fa - fixed) + 3 * ha, gc = 6 * (fb - fixed) + 3 * hb;
+    const int gr = ra0 + 3 * ha, gc = rb0 + 3 * hb;
+    double* Sg = S + sd.soff;
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
       for (int j = 0; j < 3; ++j)
         if (a != b || 3 * hb + j <= 3 * ha + i)
-          dpv_red_add(S + dpv_s_index(gr + i, gc + j, TS), dpv_f2d_bits(acc[i][j].hi) + dpv_f2d_bits(acc[i][j].lo));
+          dpv_red_add(Sg + dpv_s_index(gr + i, gc + j, sd.TS), dpv_f2d_bits(acc[i][j].hi) + dpv_f2d_bits(acc[i][j].lo));
   }
   for (int R = tid; R < nr; R += AS_THREADS) {
     const int a = R / 6, ra = R - 6 * a;
-    const int fa = wf[a];
-    if (fa < fixed) continue;
+    if (fr[a] < 0) continue;
     DF acc = {0.f, 0.f};
     if (!w_ext) acc = DF{yrn[R].x, yrn[R].y};  // with an external right-hand side v comes from y's init
     for (int kl = 0; kl < G; ++kl) df_fma(acc, -Eh[(size_t)kl * EH_STRIDE + R], sc[2 * kl + 1]);
-    dpv_red_add(y + 6 * (fa - fixed) + ra, dpv_f2d_bits(acc.hi) + dpv_f2d_bits(acc.lo));
+    dpv_red_add(y + sd.voff + fr[a] + ra, dpv_f2d_bits(acc.hi) + dpv_f2d_bits(acc.lo));
   }
 }
 
 // S <- 0 (lambda_p on the free diagonal, 1 on the padding diagonal), y <- 0,
 // and the per-pose table for this iteration: R (FP32) and the camera centre
 // c = -R^T t as a double-float pair, formed in FP64 from the FP64 pose.
-__global__ void k_init_system(double* __restrict__ S, size_t nS, double* __restrict__ y, int n_pad, int n,
+__global__ void k_init_system(double* __restrict__ S, size_t nS, double* __restrict__ y, int nv,
                               const double* __restrict__ y_init, const double* __restrict__ poses, int N,
                               float* __restrict__ posef, const int* status) {
   if (dpv_status(status)) return;
@@ -417,13 +428,16 @@ __global__ void k_init_system(double* __restrict__ S, size_t nS, double* __restr
   if (gid < (size_t)N) dpv_pose_table_row(poses + 7 * gid, posef + 16 * gid);
   double2* S2 = reinterpret_cast<double2*>(S);
   for (size_t q = gid; q < nS / 2; q += stride) S2[q] = make_double2(0.0, 0.0);
-  for (size_t q = gid; q < (size_t)n_pad; q += stride) y[q] = (y_init && q < (size_t)n) ? y_init[q] : 0.0;
+  for (size_t q = gid; q < (size_t)nv; q += stride) y[q] = y_init ? y_init[q] : 0.0;
 }
 
-__global__ void k_init_diag(double* __restrict__ S, int n, int n_pad, int TS, float lambda_p, const int* status) {
+// lambda_p on the free diagonal of every system, 1 on its padding diagonal (blockIdx.y = system)
+__global__ void k_init_diag(double* __restrict__ S, const SysDesc* __restrict__ sysd, float lambda_p,
+                            const int* status) {
   if (dpv_status(status)) return;
+  const SysDesc sd = sysd[blockIdx.y];
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r < n_pad) S[dpv_s_index(r, r, TS)] = r < n ? (double)lambda_p : 1.0;
+  if (r < sd.n_pad) S[sd.soff + dpv_s_index(r, r, sd.TS)] = r < sd.n ? (double)lambda_p : 1.0;
 }
 
 __global__ void k_export_S(const double* __restrict__ S, int n, int TS, double* __restrict__ out) {
@@ -476,21 +490,24 @@ ba_status_t assemble_impl(ba_handle_t h, int it, const double* v_ext, const floa
   Workspace* ws = h->ws;
   ba_status_t s = upload_tables(h);
   if (s) return s;
-  const size_t nS = (size_t)h->T * (h->T + 1) / 2 * h->TS * h->TS;
+  const size_t nS = (size_t)h->nS;
   if (!skip_init) {
     dpv_prof_begin(h, BA_KERNEL_INIT);
-    k_init_system<<<2 * h->num_sms, 256, 0, h->stream>>>(ws->S.p, nS, ws->y.p, h->n_pad, h->n, v_ext, h->poses,
-                                                          h->N, ws->posef.p, ws->status);
+    k_init_system<<<2 * h->num_sms, 256, 0, h->stream>>>(ws->S.p, nS, ws->y.p, h->n_pad, v_ext, h->poses, h->N,
+                                                          ws->posef.p, ws->status);
     ++h->launches;
-    k_init_diag<<<(h->n_pad + 255) / 256, 256, 0, h->stream>>>(ws->S.p, h->n, h->n_pad, h->TS, h->opt.lambda_pose,
-                                                                ws->status);
+    int maxpad = 0;
+    for (const SysDesc& d : h->sys) maxpad = std::max(maxpad, d.n_pad);
+    k_init_diag<<<dim3((maxpad + 255) / 256, h->nprob), 256, 0, h->stream>>>(ws->S.p, ws->sysd.p,
+                                                                              h->opt.lambda_pose, ws->status);
     ++h->launches;
     dpv_prof_end(h);
   }
   double* cost = it < 0 ? nullptr : ws->cost + (it < ws->cost_cap ? it : ws->cost_cap - 1);
   dpv_prof_begin(h, BA_KERNEL_ASSEMBLE);
   k_assemble<<<h->ngroups, AS_THREADS, assemble_smem_bytes(h->G), h->stream>>>(
-      h->G, h->P, h->fixed, h->TS, h->opt.lambda_depth, h->opt.z_min, ws->gptr.p, ws->grun.p, ws->gnr.p, ws->eslot.p,
+      h->G, h->P, ws->fdx.p, ws->gprob.p, ws->sysd.p, h->opt.lambda_depth, h->opt.z_min, ws->gptr.p, ws->grun.p,
+      ws->gnr.p, ws->eslot.p,
       ws->perm.p, ws->pmpos.p, ws->pptr.p, ws->win.p, ws->wlen.p, ws->posef.p, h->patches, h->targets, h->weights,
       ws->intr, ws->pterm.p, ws->S.p, ws->y.p, ws->Ct.p, ws->wk.p, cost, w_ext, ws->status);
   ++h->launches;

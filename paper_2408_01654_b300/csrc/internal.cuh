@@ -25,6 +25,19 @@
 
 struct Workspace;
 
+// One independent pose system: its dense FP64 lower triangle at S + soff
+// (tiles of TS x TS, T per dimension), its vectors (y, dx, ...) at voff with
+// n_pad entries of which the first n are unknowns.
+struct SysDesc {
+  long long soff;
+  int voff;
+  int n;
+  int n_pad;
+  int TS;
+  int T;
+  int problem;
+};
+
 struct ba_handle_s {
   ba_options_t opt;
   cudaStream_t stream = nullptr;
@@ -45,12 +58,21 @@ struct ba_handle_s {
   int ngroups = 0;
   int kk_bits = 0;      // bits of the patch index (width of the kk sort)
 
+  // independent problems bound together (1 for ba_set_graph)
+  int nprob = 1;
+  std::vector<int> frame_off;   // [nprob + 1] first frame of each problem
+  int min_frames = 0;           // smallest problem (bound on fixed_poses)
+
   // solver geometry for the last fixed value
   int fixed = -1;
-  int n = 0;             // 6 * (N - fixed)
-  int TS = 0;            // tile edge
-  int T = 0;             // tiles per dimension
-  int n_pad = 0;         // T * TS
+  int n = 0;             // unknowns over all systems: sum of 6 (N_b - fixed)
+  int TS = 0;            // tile edge (of system 0)
+  int T = 0;             // tiles per dimension (of system 0)
+  int n_pad = 0;         // length of the concatenated system vectors (sum of the padded sizes)
+  long long nS = 0;      // FP64 entries of all system matrices
+  std::vector<SysDesc> sys;       // per system
+  std::vector<int> small_nq[9];   // systems solved by the one-CTA solver, by 32-row blocks
+  std::vector<int> large_sys;     // systems solved by the persistent tiled solver
   int last_iters = 0;
 
   Workspace* ws = nullptr;
@@ -104,6 +126,11 @@ struct Workspace {
   DBuf<int> scan;                 // block sums of the scan
   DBuf<int> pmpos;                // [E] sorted position -> patch-major position
   DBuf<int> pptr;                 // [P+1] patch-major edge range of each patch
+  DBuf<int> fprob;                // [N] problem of each frame
+  DBuf<int> gprob;                // [groups] problem of each patch group
+  DBuf<int> fdx;                  // [N] offset of the frame's 6 unknowns in the system vectors, -1 fixed
+  DBuf<SysDesc> sysd;             // [systems]
+  DBuf<int> syslist;              // system indices of the solver launches
   // per iteration
   DBuf<double> S;                 // tiled lower triangle of the pose system (FP64 accumulation)
   DBuf<double> y;                 // [n_pad]

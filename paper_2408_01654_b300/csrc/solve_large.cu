@@ -677,10 +677,10 @@ long long dpv_large_scratch_floats(int n_pad) {
   return (long long)tri2((int)T) * TILE + T * TILE + 5LL * n_pad;
 }
 
-ba_status_t dpv_solve_blocked(ba_handle_t h, int refine) {
+ba_status_t dpv_solve_blocked(ba_handle_t h, const SysDesc& sd, int refine) {
   Workspace* ws = h->ws;
-  const int n = h->n, n_pad = h->n_pad;
-  if (h->TS != NB || n_pad % NB) return dpv_fail(h, BA_ERR_UNSUPPORTED, "large solver needs 64-row tiles");
+  const int n = sd.n, n_pad = sd.n_pad;
+  if (sd.TS != NB || n_pad % NB) return dpv_fail(h, BA_ERR_UNSUPPORTED, "large solver needs 64-row tiles");
   const int T = n_pad / NB;
   if (T > LG_MAX_T) return dpv_fail(h, BA_ERR_UNSUPPORTED, "pose system above 65472 unknowns");
   // the task list of this size, built once per device
@@ -724,9 +724,10 @@ ba_status_t dpv_solve_blocked(ba_handle_t h, int refine) {
   cudaStream_t st = h->stream;
   DPV_CUDA(h, cudaMemsetAsync(ver, 0, sizeof(int) * nsync, st));
   const size_t count = (size_t)tri2(T) * TILE;
-  k_lg_convert<<<4 * h->num_sms, 256, 0, st>>>(ws->S.p, A, count, status);
+  const double* Sb = ws->S.p + sd.soff;
+  k_lg_convert<<<4 * h->num_sms, 256, 0, st>>>(Sb, A, count, status);
   ++h->launches;
-  k_lg_init_rhs<<<(n_pad + 255) / 256, 256, 0, st>>>(n, n_pad, ws->y.p, rhs, status);
+  k_lg_init_rhs<<<(n_pad + 255) / 256, 256, 0, st>>>(n, n_pad, ws->y.p + sd.voff, rhs, status);
   ++h->launches;
   long long timeout = h->opt.timeout_cycles;
   {
@@ -749,11 +750,11 @@ ba_status_t dpv_solve_blocked(ba_handle_t h, int refine) {
     const int maxg = co_resident(h, (const void*)k_lg_solve);
     const int grid = std::min(T, maxg);
     if (grid <= 0) return dpv_fail(h, BA_ERR_CUDA, "large solver occupancy");
-    const double* S = ws->S.p;
-    const double* y = ws->y.p;
-    double* xacc = ws->r64.p;
-    double* dx = ws->dx.p;
-    float* dxf = ws->tmpv.p;
+    const double* S = Sb;
+    const double* y = ws->y.p + sd.voff;
+    double* xacc = ws->r64.p + sd.voff;
+    double* dx = ws->dx.p + sd.voff;
+    float* dxf = ws->tmpv.p + sd.voff;
     int sweeps = refine + 1;
     int n_ = n;
     void* args[] = {(void*)&T,   (void*)&n_,    (void*)&A,   (void*)&Linv,  (void*)&invD,   (void*)&S,

@@ -41,10 +41,14 @@ __host__ __device__ constexpr size_t small_smem(int NQ) {
   return sizeof(float) * ((size_t)tri(32 * NQ, 0) + (keep_sf(NQ) ? (size_t)32 * NQ * sf_stride(NQ) : 0));
 }
 
+// CTA b solves system list[b] of the table sysd (its matrix at S + soff, its
+// vectors at voff); without a table (sysd == null) one system of n_direct
+// unknowns at the given pointers.
 template <int NQ>  // NP = 32 NQ
 __global__ void __launch_bounds__(small_threads(NQ)) k_solve_small(
-    int n, double* __restrict__ S, double* __restrict__ y, double* __restrict__ dx,
-    float* __restrict__ dxf, int refine32, int refine64, float lambda_p, int reset, int* status) {
+    const SysDesc* __restrict__ sysd, const int* __restrict__ list, int n_direct, double* __restrict__ S_,
+    double* __restrict__ y_, double* __restrict__ dx_, float* __restrict__ dxf_, int refine32, int refine64,
+    float lambda_p, int reset, int* status) {
   constexpr int NP = 32 * NQ;
   constexpr int NT = small_threads(NQ);
   constexpr int NWARP = NT / 32;
@@ -60,6 +64,19 @@ __global__ void __launch_bounds__(small_threads(NQ)) k_solve_small(
   __shared__ float yhi[NP], ylo[NP];
   __shared__ int bad;
   if (dpv_status(status)) return;
+  int n = n_direct;
+  double* S = S_;
+  double* y = y_;
+  double* dx = dx_;
+  float* dxf = dxf_;
+  if (sysd) {
+    const SysDesc sd = sysd[list[blockIdx.x]];
+    n = sd.n;
+    S += sd.soff;
+    y += sd.voff;
+    dx += sd.voff;
+    dxf += sd.voff;
+  }
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   {
     // S: FP64 row-major NP x NP (lower triangle valid), read as pairs with
@@ -344,16 +361,16 @@ __global__ void __launch_bounds__(small_threads(NQ)) k_solve_small(
 }
 
 template <int NQ>
-ba_status_t launch_small(ba_handle_t h, int refine32, int refine64, int reset) {
+ba_status_t launch_small(ba_handle_t h, int count, const int* list, int refine32, int refine64, int reset) {
   static bool attr = false;
   const size_t smem = small_smem(NQ);
   if (!attr) {
     DPV_CUDA(h, cudaFuncSetAttribute(k_solve_small<NQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     attr = true;
   }
-  k_solve_small<NQ><<<1, small_threads(NQ), smem, h->stream>>>(h->n, h->ws->S.p, h->ws->y.p, h->ws->dx.p,
-                                                                h->ws->tmpv.p, refine32, refine64, h->opt.lambda_pose,
-                                                                reset, h->ws->status);
+  k_solve_small<NQ><<<count, small_threads(NQ), smem, h->stream>>>(
+      h->ws->sysd.p, list, 0, h->ws->S.p, h->ws->y.p, h->ws->dx.p, h->ws->tmpv.p, refine32, refine64,
+      h->opt.lambda_pose, reset, h->ws->status);
   ++h->launches;
   DPV_CUDA(h, cudaGetLastError());
   return BA_OK;
@@ -361,30 +378,39 @@ ba_status_t launch_small(ba_handle_t h, int refine32, int refine64, int reset) {
 
 }  // namespace
 
-ba_status_t dpv_solve_blocked(ba_handle_t h, int refine);
+ba_status_t dpv_solve_blocked(ba_handle_t h, const SysDesc& sd, int refine);
 
-// Solve S dxi = y (the retraction is launched by the caller).
+// Solve every pose system S_b dxi_b = y_b: one launch of the one-CTA solver per
+// block count (one CTA per system), then the large systems.
 ba_status_t dpv_solve(ba_handle_t h, int* retracted, int reset_system) {
   // BA_FP32: one compensated-FP32 refinement sweep; BA_MIXED: FP64 sweeps
   const int refine32 = h->opt.precision == BA_MIXED ? 0 : 1;
   const int refine64 = h->opt.precision == BA_MIXED ? h->opt.max_refine : 0;
   *retracted = 0;
   if (h->n == 0) return BA_OK;
-  // large systems: FP64 refinement sweeps (at least one), the residual spread over the GPU
-  if (h->n > DPV_SMALL_N) return dpv_solve_blocked(h, refine32 + refine64);
-  ba_status_t s;
-  switch (h->n_pad / 32) {
-    case 1: s = launch_small<1>(h, refine32, refine64, reset_system); break;
-    case 2: s = launch_small<2>(h, refine32, refine64, reset_system); break;
-    case 3: s = launch_small<3>(h, refine32, refine64, reset_system); break;
-    case 4: s = launch_small<4>(h, refine32, refine64, reset_system); break;
-    case 5: s = launch_small<5>(h, refine32, refine64, reset_system); break;
-    case 6: s = launch_small<6>(h, refine32, refine64, reset_system); break;
-    case 7: s = launch_small<7>(h, refine32, refine64, reset_system); break;
-    case 8: s = launch_small<8>(h, refine32, refine64, reset_system); break;
-    default: return dpv_fail(h, BA_ERR_UNSUPPORTED, "pose system size");
+  ba_status_t s = BA_OK;
+  int off = 0;
+  for (int nq = 1; nq <= 8; ++nq) {
+    const int cnt = (int)h->small_nq[nq].size();
+    if (!cnt) continue;
+    const int* list = h->ws->syslist.p + off;
+    switch (nq) {
+      case 1: s = launch_small<1>(h, cnt, list, refine32, refine64, reset_system); break;
+      case 2: s = launch_small<2>(h, cnt, list, refine32, refine64, reset_system); break;
+      case 3: s = launch_small<3>(h, cnt, list, refine32, refine64, reset_system); break;
+      case 4: s = launch_small<4>(h, cnt, list, refine32, refine64, reset_system); break;
+      case 5: s = launch_small<5>(h, cnt, list, refine32, refine64, reset_system); break;
+      case 6: s = launch_small<6>(h, cnt, list, refine32, refine64, reset_system); break;
+      case 7: s = launch_small<7>(h, cnt, list, refine32, refine64, reset_system); break;
+      case 8: s = launch_small<8>(h, cnt, list, refine32, refine64, reset_system); break;
+    }
+    if (s) return s;
+    off += cnt;
   }
-  return s;
+  // large systems: FP64 refinement sweeps (at least one)
+  for (int b : h->large_sys)
+    if ((s = dpv_solve_blocked(h, h->sys[b], refine32 + refine64))) return s;
+  return BA_OK;
 }
 
 // Launch the one-CTA solver on a system the caller has already laid out as one
@@ -399,8 +425,8 @@ ba_status_t launch_small_raw(cudaStream_t st, int n, const double* S, const doub
       cudaSuccess)
     return BA_ERR_CUDA;
   // reset = 0: the kernel only reads S and y
-  k_solve_small<NQ><<<1, small_threads(NQ), smem, st>>>(n, const_cast<double*>(S), const_cast<double*>(y), dx, dxf, 0,
-                                                        refine, 0.f, 0, status);
+  k_solve_small<NQ><<<1, small_threads(NQ), smem, st>>>(nullptr, nullptr, n, const_cast<double*>(S),
+                                                        const_cast<double*>(y), dx, dxf, 0, refine, 0.f, 0, status);
   return cudaGetLastError() == cudaSuccess ? BA_OK : BA_ERR_CUDA;
 }
 }  // namespace

@@ -18,22 +18,26 @@ namespace {
 constexpr int BS_THREADS = 256;
 constexpr int BS_WARPS = BS_THREADS / 32;
 
-// One warp per patch (lanes over its edges, compensated warp sum).  Thread 0
-// of CTA b < N - fixed also retracts pose fixed + b (FP64) and, when `posef`
-// is given, refreshes that pose's row of the linearisation table; one pose per
-// CTA spreads the FP64 work (1/64 of the FP32 rate) over the SMs.
+// One warp per patch (lanes over its edges, compensated warp sum).  With
+// `retract`, thread 0 of CTA f < N also retracts pose f when it is free
+// (FP64) and, when `posef` is given, refreshes its row of the linearisation
+// table; one pose per CTA spreads the FP64 work (1/64 of the FP32 rate) over
+// the SMs.  fdx maps a frame to its unknowns in dx / dxf (-1: fixed).
 __global__ void __launch_bounds__(BS_THREADS) k_backsub(
-    int P, int G, int fixed, float d_min, const int* __restrict__ pptr, const float4* __restrict__ pterm,
-    const int* __restrict__ win, const float* __restrict__ dxf, const float* __restrict__ Ct,
-    const float* __restrict__ wk, float* __restrict__ patches, float* __restrict__ dd_out, int N,
-    const double* __restrict__ dx, double* __restrict__ poses, float* __restrict__ posef, int write_depth,
-    const int* status) {
+    int P, int G, const int* __restrict__ fdx, float d_min, const int* __restrict__ pptr,
+    const float4* __restrict__ pterm, const int* __restrict__ win, const float* __restrict__ dxf,
+    const float* __restrict__ Ct, const float* __restrict__ wk, float* __restrict__ patches,
+    float* __restrict__ dd_out, int N, int retract, const double* __restrict__ dx, double* __restrict__ poses,
+    float* __restrict__ posef, int write_depth, const int* status) {
   if (dpv_status(status)) return;
   const int lane = threadIdx.x & 31;
-  if (threadIdx.x == 0 && (int)blockIdx.x < N - fixed) {
-    const int f = fixed + blockIdx.x;
-    dpv_se3_retract(dx + 6 * (size_t)blockIdx.x, poses + 7 * (size_t)f);
-    if (posef) dpv_pose_table_row(poses + 7 * (size_t)f, posef + 16 * (size_t)f);
+  if (retract && threadIdx.x == 0 && (int)blockIdx.x < N) {
+    const int f = blockIdx.x;
+    const int o = fdx[f];
+    if (o >= 0) {
+      dpv_se3_retract(dx + o, poses + 7 * (size_t)f);
+      if (posef) dpv_pose_table_row(poses + 7 * (size_t)f, posef + 16 * (size_t)f);
+    }
   }
   const int k = blockIdx.x * BS_WARPS + (threadIdx.x >> 5);
   if (k >= P) return;
@@ -43,14 +47,14 @@ __global__ void __launch_bounds__(BS_THREADS) k_backsub(
     const float4 a = pterm[4 * (size_t)p], b = pterm[4 * (size_t)p + 1], c = pterm[4 * (size_t)p + 2],
                  d = pterm[4 * (size_t)p + 3];
     const int sl = __float_as_int(d.z);
-    const int fi = wf[sl & 0xff] - fixed, fj = wf[sl >> 8] - fixed;
+    const int fi = fdx[wf[sl & 0xff]], fj = fdx[wf[sl >> 8]];
     if (fi >= 0) {
-      const float* x = dxf + 6 * fi;
+      const float* x = dxf + fi;
       df_fma(acc, -a.x, x[0]); df_fma(acc, -a.y, x[1]); df_fma(acc, -a.z, x[2]);
       df_fma(acc, -a.w, x[3]); df_fma(acc, -b.x, x[4]); df_fma(acc, -b.y, x[5]);
     }
     if (fj >= 0) {
-      const float* x = dxf + 6 * fj;
+      const float* x = dxf + fj;
       df_fma(acc, -b.z, x[0]); df_fma(acc, -b.w, x[1]); df_fma(acc, -c.x, x[2]);
       df_fma(acc, -c.y, x[3]); df_fma(acc, -c.z, x[4]); df_fma(acc, -c.w, x[5]);
     }
@@ -75,7 +79,7 @@ __global__ void __launch_bounds__(BS_THREADS) k_backsub(
 
 unsigned backsub_grid(ba_handle_t h, int retract) {
   const long long wb = ((long long)h->P + BS_WARPS - 1) / BS_WARPS;
-  const long long rb = retract ? (long long)(h->N - h->fixed) : 0;
+  const long long rb = retract ? (long long)h->N : 0;
   return (unsigned)(wb > rb ? wb : rb);
 }
 
@@ -86,8 +90,8 @@ unsigned backsub_grid(ba_handle_t h, int retract) {
 ba_status_t dpv_backsub(ba_handle_t h, int retract) {
   Workspace* ws = h->ws;
   k_backsub<<<backsub_grid(h, retract), BS_THREADS, 0, h->stream>>>(
-      h->P, h->G, h->fixed, h->opt.d_min, ws->pptr.p, ws->pterm.p, ws->win.p, ws->tmpv.p, ws->Ct.p, ws->wk.p,
-      h->patches, ws->dd.p, retract ? h->N : h->fixed, ws->dx.p, h->poses, ws->posef.p, 1, ws->status);
+      h->P, h->G, ws->fdx.p, h->opt.d_min, ws->pptr.p, ws->pterm.p, ws->win.p, ws->tmpv.p, ws->Ct.p, ws->wk.p,
+      h->patches, ws->dd.p, h->N, retract, ws->dx.p, h->poses, ws->posef.p, 1, ws->status);
   ++h->launches;
   DPV_CUDA(h, cudaGetLastError());
   return BA_OK;
@@ -98,8 +102,8 @@ ba_status_t dpv_backsub(ba_handle_t h, int retract) {
 ba_status_t dpv_backsub_ext(ba_handle_t h, const float* w_ext, float* out) {
   Workspace* ws = h->ws;
   k_backsub<<<backsub_grid(h, 0), BS_THREADS, 0, h->stream>>>(
-      h->P, h->G, h->fixed, h->opt.d_min, ws->pptr.p, ws->pterm.p, ws->win.p, ws->tmpv.p, ws->Ct.p, w_ext,
-      h->patches, out, h->fixed, ws->dx.p, h->poses, nullptr, 0, ws->status);
+      h->P, h->G, ws->fdx.p, h->opt.d_min, ws->pptr.p, ws->pterm.p, ws->win.p, ws->tmpv.p, ws->Ct.p, w_ext,
+      h->patches, out, h->N, 0, ws->dx.p, h->poses, nullptr, 0, ws->status);
   ++h->launches;
   DPV_CUDA(h, cudaGetLastError());
   return BA_OK;
