@@ -110,6 +110,34 @@ DPVBA_API ba_status_t ba_set_graph(ba_handle_t h, int N, int P, int E, double* p
                          const int* ii, const int* jj, const int* kk, const float* targets,
                          const float* weights, const float* intrinsics);
 
+/* Bind B independent problems to one handle, solved together (batched
+ * execution of many uneven bundle adjustments, e.g. one per map segment or
+ * per sequence).  The paper solves one problem at a time; this binding runs
+ * every kernel once over all problems: one preprocessing pass, one assembly
+ * launch, the pose systems in batched solver launches, one back-substitution.
+ *   frame_off, patch_off, edge_off : HOST int64 [B+1], non-decreasing from 0;
+ *       problem b owns frames [frame_off[b], frame_off[b+1]) of `poses`,
+ *       patches [patch_off[b], patch_off[b+1]) of `patches`, and edges
+ *       [edge_off[b], edge_off[b+1]) of ii, jj, kk, targets, weights;
+ *       every problem has at least one frame and one patch.
+ *   poses [N,7] f64, patches [P,3,3,3] f32 : device, concatenated, updated by
+ *       ba_step as for ba_set_graph;
+ *   ii, jj, kk : device int32 [E], indices LOCAL to the edge's problem;
+ *   targets, weights : device f32 [E,2], 8-byte aligned;
+ *   intrinsics : host or device f32 [B,4] (fx, fy, cx, cy per problem).
+ * ba_step's fixed_poses applies to each problem (its first fixed_poses
+ * frames) and must not exceed the smallest frame count.  When a problem's
+ * patch count is not a multiple of the reduction group size the library
+ * works on a padded copy of `patches`, read at each ba_step and written back
+ * at its end.  Errors: BA_ERR_INVALID_ARG for bad offsets or pointers (host
+ * checked) and, through ba_sync, for local indices out of range; the
+ * debug exports of S and of the block keys are single-problem only
+ * (BA_ERR_UNSUPPORTED). */
+DPVBA_API ba_status_t ba_set_graph_batched(ba_handle_t h, int B, const long long* frame_off,
+                                           const long long* patch_off, const long long* edge_off, double* poses,
+                                           float* patches, const int* ii, const int* jj, const int* kk,
+                                           const float* targets, const float* weights, const float* intrinsics);
+
 /* Run `iters` Gauss-Newton iterations of Eq. 3 in place (Sec. 3.1-3.2):
  * linearise every edge, reduce into the block system, eliminate the inverse
  * depths, factor and solve the pose system, back-substitute the depths,

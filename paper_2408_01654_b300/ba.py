@@ -4,6 +4,7 @@ from __future__ import annotations
 
 import ctypes
 
+import numpy as np
 import torch
 
 from . import capi
@@ -56,6 +57,28 @@ class DPVBA:
         capi.check(self._h, self._lib.ba_set_graph(
             self._h, N, P, E, _ptr(poses), _ptr(patches), _ptr(ii), _ptr(jj), _ptr(kk), _ptr(targets),
             _ptr(weights), _ptr(intrinsics)))
+
+    def set_graph_batched(self, poses, patches, ii, jj, kk, targets, weights, intrinsics, frame_off, patch_off,
+                          edge_off):
+        """Bind independent problems together: the tensors are the problems'
+        arrays concatenated (ii, jj, kk local to each problem), intrinsics is
+        float32 [B,4], and the offsets are int sequences of length B+1."""
+        for name, t, dt in (("poses", poses, torch.float64), ("patches", patches, torch.float32),
+                            ("ii", ii, torch.int32), ("jj", jj, torch.int32), ("kk", kk, torch.int32),
+                            ("targets", targets, torch.float32), ("weights", weights, torch.float32),
+                            ("intrinsics", intrinsics, torch.float32)):
+            if t.dtype != dt or not t.is_contiguous() or not t.is_cuda:
+                raise TypeError(f"{name}: need a contiguous CUDA {dt} tensor")
+        offs = [np.ascontiguousarray(np.asarray(o, dtype=np.int64)) for o in (frame_off, patch_off, edge_off)]
+        B = len(offs[0]) - 1
+        self._keep = (poses, patches, ii, jj, kk, targets, weights, intrinsics, offs)
+        self.N, self.P, self.E = poses.shape[0], patches.shape[0], ii.shape[0]
+        self.B = B
+        lp = ctypes.POINTER(ctypes.c_longlong)
+        capi.check(self._h, self._lib.ba_set_graph_batched(
+            self._h, B, offs[0].ctypes.data_as(lp), offs[1].ctypes.data_as(lp), offs[2].ctypes.data_as(lp),
+            _ptr(poses), _ptr(patches), _ptr(ii), _ptr(jj), _ptr(kk), _ptr(targets), _ptr(weights),
+            _ptr(intrinsics)))
 
     def step(self, iters: int, fixed: int):
         capi.check(self._h, self._lib.ba_step(self._h, iters, fixed))
@@ -178,6 +201,18 @@ class BAFunction(torch.autograd.Function):
 def bundle_adjust(targets, weights, poses, patches, ii, jj, kk, intrinsics, iters, fixed, **opts):
     """Functional form of ``BAFunction`` (keyword options as for ``DPVBA``)."""
     return BAFunction.apply(targets, weights, poses, patches, ii, jj, kk, intrinsics, iters, fixed, opts)
+
+
+def batch_tensors(scene_list, device="cuda") -> tuple[dict, dict]:
+    """Device copies of independent scenes concatenated for set_graph_batched:
+    (tensors, offsets) with offsets frame_off / patch_off / edge_off (int64 [B+1])."""
+    T = [scene_tensors(sc, device) for sc in scene_list]
+    cat = {k: torch.cat([t[k] for t in T]).contiguous() for k in ("poses", "patches", "ii", "jj", "kk", "targets",
+                                                                  "weights")}
+    cat["intrinsics"] = torch.stack([t["intrinsics"] for t in T]).contiguous()
+    offs = {name: np.r_[0, np.cumsum([getattr(sc, attr) for sc in scene_list])].astype(np.int64)
+            for name, attr in (("frame_off", "N"), ("patch_off", "P"), ("edge_off", "E"))}
+    return cat, offs
 
 
 def scene_tensors(scene, device="cuda") -> dict:

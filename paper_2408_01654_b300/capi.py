@@ -35,7 +35,8 @@ class BAOptions(ctypes.Structure):
 
 
 EXPORTED = [
-    "ba_default_options", "ba_create", "ba_destroy", "ba_set_stream", "ba_set_graph", "ba_step", "ba_sync",
+    "ba_default_options", "ba_create", "ba_destroy", "ba_set_stream", "ba_set_graph", "ba_set_graph_batched",
+    "ba_step", "ba_sync",
     "ba_last_error", "ba_status_string", "ba_linearize", "ba_debug_export", "ba_debug_info", "ba_debug_keys",
     "ba_profile_enable", "ba_profile_read", "ba_set_record", "ba_backward", "ba_solve_pose_system_noalloc",
 ]
@@ -66,6 +67,7 @@ def lib():
         L.ba_destroy.argtypes = [H]
         L.ba_set_stream.argtypes = [H, P]
         L.ba_set_graph.argtypes = [H, i, i, i, P, P, P, P, P, P, P, P]
+        L.ba_set_graph_batched.argtypes = [H, i, P, P, P, P, P, P, P, P, P, P, P]
         L.ba_step.argtypes = [H, i, i]
         L.ba_sync.argtypes = [H]
         L.ba_last_error.argtypes = [H]

@@ -220,7 +220,8 @@ __device__ __forceinline__ void adjoint_apply(const RelPose& T, const float* v, 
 // Step 3 for iteration s: one CTA per patch group, one warp per (source,
 // target) run, one lane per edge.
 __global__ void __launch_bounds__(ADJ_THREADS) k_adj_edges(
-    int G, int P, const int* __restrict__ fdx, float z_min, const int* __restrict__ gptr,
+    int G, int P, const int* __restrict__ fdx, const int* __restrict__ gprob, float z_min,
+    const int* __restrict__ gptr,
     const int* __restrict__ grun,
     const int* __restrict__ gnr, const unsigned* __restrict__ eslot, const int* __restrict__ perm,
     const int* __restrict__ pmpos, const int* __restrict__ win, const float* __restrict__ posef,
@@ -234,7 +235,8 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_edges(
   const int gs = gptr[g], nruns = gnr[g];
   const int* runptr = grun + (size_t)g * (DPV_RMAX + 1);
   const int* wf = win + (size_t)g * DPV_WMAX;
-  const float fx = intr[0], fy = intr[1], cx = intr[2], cy = intr[3];
+  const float* Kg = intr + 4 * gprob[g];  // the group's problem's intrinsics
+  const float fx = Kg[0], fy = Kg[1], cx = Kg[2], cy = Kg[3];
   for (int r = wid; r < nruns; r += ADJ_WARPS) {
     const int s0 = gs + runptr[r], s1 = gs + runptr[r + 1];
     const unsigned sw0 = eslot[s0];
@@ -483,7 +485,7 @@ extern "C" ba_status_t ba_backward(ba_handle_t h, const double* grad_poses, cons
     if (s) return s;
     dpv_prof_begin(h, BA_KERNEL_ADJOINT);
     k_adj_edges<<<h->ngroups, ADJ_THREADS, 0, h->stream>>>(
-        h->G, P, fdx, h->opt.z_min, ws->gptr.p, ws->grun.p, ws->gnr.p, ws->eslot.p, ws->perm.p, ws->pmpos.p,
+        h->G, P, fdx, ws->gprob.p, h->opt.z_min, ws->gptr.p, ws->grun.p, ws->gnr.p, ws->eslot.p, ws->perm.p, ws->pmpos.p,
         ws->win.p, ws->posef.p, patches_s, h->targets, h->weights, ws->intr, ws->tmpv.p, ws->ad_lamd.p, dx_s, dd_s,
         gT, gW, ws->ad_gd.p, xbc, ws->status);
     ++h->launches;

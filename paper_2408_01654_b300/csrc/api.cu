@@ -2,6 +2,7 @@
 #include "internal.cuh"
 
 #include <algorithm>
+#include <cstdint>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -87,6 +88,57 @@ int auto_group(ba_handle_t h, int P) {
   if ((long long)P >= 32LL * 2 * h->num_sms) return 32;
   if ((long long)P >= 8LL * h->num_sms) return 16;
   return 8;
+}
+
+// problem of index x for non-decreasing offsets off[0..B] (largest b with off[b] <= x)
+__device__ __forceinline__ int find_problem(const long long* off, int B, long long x) {
+  int lo = 0, hi = B - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (off[mid] <= x) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Edge indices of bound problems -> the library's numbering: frames offset by
+// the problem's first frame, patches by its (group-aligned) first patch.  Local
+// indices out of range become -1, which validation reports.
+__global__ void k_remap_edges(int E, int B, const long long* __restrict__ offs, const int* __restrict__ ii,
+                              const int* __restrict__ jj, const int* __restrict__ kk, int* __restrict__ mii,
+                              int* __restrict__ mjj, int* __restrict__ mkk) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= E) return;
+  const long long* foff = offs;
+  const long long* moff = offs + (B + 1);
+  const long long* eoff = offs + 2 * (B + 1);
+  const long long* poff = offs + 3 * (B + 1);
+  const int b = find_problem(eoff, B, e);
+  const int nf = (int)(foff[b + 1] - foff[b]), np = (int)(poff[b + 1] - poff[b]);
+  const int i = ii[e], j = jj[e], k = kk[e];
+  mii[e] = (i >= 0 && i < nf) ? (int)foff[b] + i : -1;
+  mjj[e] = (j >= 0 && j < nf) ? (int)foff[b] + j : -1;
+  mkk[e] = (k >= 0 && k < np) ? (int)moff[b] + k : -1;
+}
+
+__global__ void k_frame_problems(int N, int B, const long long* __restrict__ offs, int* __restrict__ fprob) {
+  const int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f < N) fprob[f] = find_problem(offs, B, f);
+}
+
+// padded copy <-> caller's patches (to_copy: caller -> copy, zero padding)
+__global__ void k_patch_copy(int Ppad, int B, const long long* __restrict__ offs, float* __restrict__ user,
+                             float* __restrict__ copy, int to_copy) {
+  const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= 27LL * Ppad) return;
+  const int km = (int)(q / 27), c = (int)(q % 27);
+  const long long* moff = offs + (B + 1);
+  const long long* poff = offs + 3 * (B + 1);
+  const int b = find_problem(moff, B, km);
+  const long long k = km - moff[b];
+  const bool real = k < poff[b + 1] - poff[b];
+  if (to_copy) copy[q] = real ? user[27 * (poff[b] + k) + c] : 0.f;
+  else if (real) user[27 * (poff[b] + k) + c] = copy[q];
 }
 
 // fdx[f]: offset of frame f's six unknowns in the concatenated system vectors,
@@ -239,7 +291,8 @@ ba_status_t ba_destroy(ba_handle_t h) {
     release(ws->tp_poses); release(ws->tp_patches); release(ws->tp_dx); release(ws->tp_dd);
     release(ws->ad_xb); release(ws->ad_w); release(ws->ad_gd); release(ws->ad_lamd); release(ws->ad_v);
     release(ws->ad_gt); release(ws->ad_gw); release(ws->lg_sync); release(ws->fprob); release(ws->gprob);
-    release(ws->fdx); release(ws->sysd); release(ws->syslist);
+    release(ws->fdx); release(ws->sysd); release(ws->syslist); release(ws->mii); release(ws->mjj); release(ws->mkk);
+    release(ws->offs); release(ws->pcopy);
     delete ws;
   }
   prof_clear(h);
@@ -297,6 +350,8 @@ ba_status_t ba_set_graph(ba_handle_t h, int N, int P, int E, double* poses, floa
   // the frame -> unknown map survives a rebinding with the same frame count
   const bool same_frames = h->nprob == 1 && h->N == N && h->fixed >= 0;
   h->nprob = 1;
+  h->user_patches = nullptr;
+  h->patches_padded = 0;
   h->frame_off.assign({0, N});
   h->min_frames = N;
   h->N = N;
@@ -342,6 +397,140 @@ ba_status_t ba_set_graph(ba_handle_t h, int N, int P, int E, double* poses, floa
   return BA_OK;
 }
 
+ba_status_t ba_set_graph_batched(ba_handle_t h, int B, const long long* frame_off, const long long* patch_off,
+                                 const long long* edge_off, double* poses, float* patches, const int* ii,
+                                 const int* jj, const int* kk, const float* targets, const float* weights,
+                                 const float* intrinsics) {
+  if (!h) return BA_ERR_INVALID_ARG;
+  if (B < 1 || !frame_off || !patch_off || !edge_off)
+    return dpv_fail(h, BA_ERR_INVALID_ARG, "ba_set_graph_batched: need B >= 1 and host offset arrays");
+  if (frame_off[0] || patch_off[0] || edge_off[0])
+    return dpv_fail(h, BA_ERR_INVALID_ARG, "ba_set_graph_batched: offsets must start at 0");
+  int min_frames = INT32_MAX;
+  for (int b = 0; b < B; ++b) {
+    if (frame_off[b + 1] - frame_off[b] < 1 || patch_off[b + 1] - patch_off[b] < 1 ||
+        edge_off[b + 1] < edge_off[b])
+      return dpv_fail(h, BA_ERR_INVALID_ARG, "ba_set_graph_batched: each problem needs a frame and a patch");
+    min_frames = std::min<long long>(min_frames, frame_off[b + 1] - frame_off[b]);
+  }
+  const long long Nl = frame_off[B], Pl = patch_off[B], El = edge_off[B];
+  if (Nl > (1 << 20) || Pl > (1LL << 30) || El > (1LL << 30))
+    return dpv_fail(h, BA_ERR_UNSUPPORTED, "ba_set_graph_batched: problem sizes");
+  if (!poses || !patches || !intrinsics || (El > 0 && (!ii || !jj || !kk || !targets || !weights)))
+    return dpv_fail(h, BA_ERR_INVALID_ARG, "ba_set_graph_batched: null pointer");
+  if ((reinterpret_cast<uintptr_t>(targets) | reinterpret_cast<uintptr_t>(weights)) & 7)
+    return dpv_fail(h, BA_ERR_INVALID_ARG, "ba_set_graph_batched: targets/weights must be 8-byte aligned");
+  Workspace* ws = h->ws;
+  const int N = (int)Nl, E = (int)El;
+  const int G = h->opt.patches_per_group > 0 ? h->opt.patches_per_group : auto_group(h, (int)Pl);
+  // group-aligned patch numbering: every reduction group lies inside one problem
+  std::vector<long long> offs(4 * (B + 1));
+  long long* foff = offs.data();
+  long long* moff = foff + (B + 1);
+  long long* eoff = moff + (B + 1);
+  long long* poff = eoff + (B + 1);
+  bool padded = false;
+  moff[0] = 0;
+  for (int b = 0; b <= B; ++b) {
+    foff[b] = frame_off[b];
+    eoff[b] = edge_off[b];
+    poff[b] = patch_off[b];
+    if (b < B) {
+      const long long np = patch_off[b + 1] - patch_off[b];
+      moff[b + 1] = moff[b] + (np + G - 1) / G * G;
+      padded = padded || (np % G != 0);
+    }
+  }
+  const long long Ppad = padded ? moff[B] : Pl;
+  if (!padded)
+    for (int b = 0; b <= B; ++b) moff[b] = poff[b];
+  if (Ppad > (1LL << 30)) return dpv_fail(h, BA_ERR_UNSUPPORTED, "ba_set_graph_batched: problem sizes");
+  const int P = (int)Ppad;
+  h->have_graph = 0;
+  h->tape_valid = 0;
+  h->fixed = -1;
+  h->nprob = B;
+  h->frame_off.assign(frame_off, frame_off + B + 1);
+  h->patch_moff.assign(moff, moff + B + 1);
+  h->user_patch_off.assign(patch_off, patch_off + B + 1);
+  h->min_frames = min_frames;
+  h->N = N;
+  h->P = P;
+  h->E = E;
+  h->poses = poses;
+  h->user_patches = padded ? patches : nullptr;
+  h->patches_padded = padded ? 1 : 0;
+  h->targets = targets;
+  h->weights = weights;
+  h->G = G;
+  h->ngroups = (P + G - 1) / G;
+  h->kk_bits = bits_for((unsigned long long)P);
+  ba_status_t s;
+  const long long En = std::max(E, 1);
+  const long long Gn = h->ngroups + 1;
+  const long long scan_need = std::max(dpv_scan_scratch(En + 1), dpv_scan_scratch(dpv_hist_entries(En)));
+  if ((s = dpv_grow(h, ws->src, P, "patch table")) || (s = dpv_grow(h, ws->Ct, P, "Ct")) ||
+      (s = dpv_grow(h, ws->wk, P, "w")) || (s = dpv_grow(h, ws->dd, P, "dd")) ||
+      (s = dpv_grow(h, ws->keys0, En, "sort keys")) || (s = dpv_grow(h, ws->keys1, En, "sort keys")) ||
+      (s = dpv_grow(h, ws->vals0, En, "sort values")) || (s = dpv_grow(h, ws->vals1, En, "sort values")) ||
+      (s = dpv_grow(h, ws->perm, En, "permutation")) || (s = dpv_grow(h, ws->eslot, En, "slots")) ||
+      (s = dpv_grow(h, ws->grun, Gn * (DPV_RMAX + 1), "run tables")) || (s = dpv_grow(h, ws->gnr, Gn, "run counts")) ||
+      (s = dpv_grow(h, ws->hist, dpv_hist_entries(En), "histograms")) || (s = dpv_grow(h, ws->scan, scan_need, "scan")) ||
+      (s = dpv_grow(h, ws->gptr, Gn, "groups")) || (s = dpv_grow(h, ws->win, Gn * DPV_WMAX, "windows")) ||
+      (s = dpv_grow(h, ws->wlen, Gn, "windows")) || (s = dpv_grow(h, ws->pmpos, En, "patch-major positions")) ||
+      (s = dpv_grow(h, ws->pptr, (long long)P + 1, "patch CSR")) || (s = dpv_grow(h, ws->pterm, 4 * En, "edge depth terms")) ||
+      (s = dpv_grow(h, ws->posef, 16LL * N, "pose table")) ||
+      (s = dpv_grow(h, ws->fprob, (long long)N + B + 1, "frame problems")) ||
+      (s = dpv_grow(h, ws->gprob, Gn, "group problems")) || (s = dpv_grow(h, ws->mii, En, "edge frames")) ||
+      (s = dpv_grow(h, ws->mjj, En, "edge frames")) || (s = dpv_grow(h, ws->mkk, En, "edge patches")) ||
+      (s = dpv_grow(h, ws->offs, 4LL * (B + 1), "problem offsets")) ||
+      (padded && (s = dpv_grow(h, ws->pcopy, 27LL * P, "padded patches"))))
+    return s;
+  if (B > ws->intr_cap) {
+    float* p = nullptr;
+    if (cudaMalloc(&p, sizeof(float) * 4 * B) != cudaSuccess) {
+      cudaGetLastError();
+      return dpv_fail(h, BA_ERR_OOM, "allocating intrinsics");
+    }
+    DPV_CUDA(h, cudaStreamSynchronize(h->stream));
+    cudaFree(ws->intr);
+    ws->intr = p;
+    ws->intr_cap = B;
+  }
+  cudaStream_t st = h->stream;
+  DPV_CUDA(h, cudaMemsetAsync(ws->status, 0, sizeof(int), st));
+  DPV_CUDA(h, cudaMemcpyAsync(ws->intr, intrinsics, sizeof(float) * 4 * B, cudaMemcpyDefault, st));
+  DPV_CUDA(h, cudaMemcpyAsync(ws->offs.p, offs.data(), sizeof(long long) * offs.size(), cudaMemcpyHostToDevice, st));
+  // per-frame problem, then the frame offsets (int) after it; per-group problem
+  k_frame_problems<<<(N + 255) / 256, 256, 0, st>>>(N, B, ws->offs.p, ws->fprob.p);
+  ++h->launches;
+  DPV_CUDA(h, cudaMemcpyAsync(ws->fprob.p + N, h->frame_off.data(), sizeof(int) * (B + 1), cudaMemcpyHostToDevice, st));
+  std::vector<int> gp(h->ngroups);
+  for (int g = 0, b = 0; g < h->ngroups; ++g) {
+    while (b + 1 < B && (long long)g * G >= h->patch_moff[b + 1]) ++b;
+    gp[g] = b;
+  }
+  if (h->ngroups > 0)
+    DPV_CUDA(h, cudaMemcpyAsync(ws->gprob.p, gp.data(), sizeof(int) * h->ngroups, cudaMemcpyHostToDevice, st));
+  if (padded) {
+    k_patch_copy<<<(unsigned)((27LL * P + 255) / 256), 256, 0, st>>>(P, B, ws->offs.p, patches, ws->pcopy.p, 1);
+    ++h->launches;
+    h->patches = ws->pcopy.p;
+  } else {
+    h->patches = patches;
+  }
+  if (E > 0) {
+    k_remap_edges<<<(E + 255) / 256, 256, 0, st>>>(E, B, ws->offs.p, ii, jj, kk, ws->mii.p, ws->mjj.p, ws->mkk.p);
+    ++h->launches;
+  }
+  dpv_prof_begin(h, BA_KERNEL_PREPROCESS);
+  s = dpv_preprocess(h, ws->mii.p, ws->mjj.p, ws->mkk.p);
+  dpv_prof_end(h);
+  if (s) return s;
+  h->have_graph = 1;
+  return BA_OK;
+}
+
 static ba_status_t check_step_args(ba_handle_t h, int fixed_poses) {
   if (!h) return BA_ERR_INVALID_ARG;
   if (!h->have_graph) return dpv_fail(h, BA_ERR_STATE, "no graph bound (call ba_set_graph first)");
@@ -362,6 +551,11 @@ ba_status_t ba_step(ba_handle_t h, int iters, int fixed_poses) {
     h->tape_valid = 0;
     h->tape_iters_pending = run;
     if ((s = dpv_tape_reserve(h, run))) return s;
+  }
+  if (h->patches_padded) {  // the padded working copy follows the caller's patches
+    k_patch_copy<<<(unsigned)((27LL * h->P + 255) / 256), 256, 0, h->stream>>>(h->P, h->nprob, h->ws->offs.p,
+                                                                               h->user_patches, h->ws->pcopy.p, 1);
+    ++h->launches;
   }
   if (run > 0) DPV_CUDA(h, cudaMemsetAsync(h->ws->cost, 0, sizeof(double) * h->ws->cost_cap, h->stream));
   int prepared = 0;  // S, y and the pose table already set up by the previous iteration
@@ -388,6 +582,12 @@ ba_status_t ba_step(ba_handle_t h, int iters, int fixed_poses) {
     h->tape_iters = run;
     h->tape_fixed = fixed_poses;
     h->tape_valid = 1;
+  }
+  if (h->patches_padded && run > 0) {
+    k_patch_copy<<<(unsigned)((27LL * h->P + 255) / 256), 256, 0, h->stream>>>(h->P, h->nprob, h->ws->offs.p,
+                                                                               h->user_patches, h->ws->pcopy.p, 0);
+    ++h->launches;
+    DPV_CUDA(h, cudaGetLastError());
   }
   return BA_OK;
 }
@@ -445,7 +645,10 @@ ba_status_t ba_debug_export(ba_handle_t h, int what, void* dst, long long bytes)
   const void* src = nullptr;
   long long need = 0;
   switch (what) {
-    case BA_EXPORT_S: need = 8LL * h->n * h->n; break;
+    case BA_EXPORT_S:
+      if (h->nprob != 1) return dpv_fail(h, BA_ERR_UNSUPPORTED, "the S export is single-problem only");
+      need = 8LL * h->n * h->n;
+      break;
     case BA_EXPORT_Y: src = ws->y.p; need = 8LL * h->n; break;
     case BA_EXPORT_DX: src = ws->dx.p; need = 8LL * h->n; break;
     case BA_EXPORT_DD: src = ws->dd.p; need = 4LL * h->P; break;
@@ -474,6 +677,7 @@ ba_status_t ba_debug_export(ba_handle_t h, int what, void* dst, long long bytes)
 ba_status_t ba_debug_keys(ba_handle_t h, int fixed_poses, int* keys_out, int cap, int* n_out) {
   if (!h || !n_out || (cap > 0 && !keys_out)) return BA_ERR_INVALID_ARG;
   if (!h->have_graph) return dpv_fail(h, BA_ERR_STATE, "no graph bound");
+  if (h->nprob != 1) return dpv_fail(h, BA_ERR_UNSUPPORTED, "block keys are single-problem only");
   return dpv_block_keys(h, fixed_poses, keys_out, cap, n_out);
 }
 

@@ -101,9 +101,9 @@ __global__ void __launch_bounds__(AS_THREADS) k_assemble(
   // the group's pose system (every frame of a group belongs to one problem)
   const SysDesc sd = sysd[gprob[g]];
 
-  float K[4];
+  float K[4];  // the group's problem's intrinsics
 #pragma unroll
-  for (int q = 0; q < 4; ++q) K[q] = intr[q];
+  for (int q = 0; q < 4; ++q) K[q] = intr[4 * gprob[g] + q];
 
   // ---- phase 0 ------------------------------------------------------------
   for (int q = tid; q < G * EH_STRIDE; q += AS_THREADS) Eh[q] = 0.f;

@@ -61,7 +61,11 @@ struct ba_handle_s {
   // independent problems bound together (1 for ba_set_graph)
   int nprob = 1;
   std::vector<int> frame_off;   // [nprob + 1] first frame of each problem
+  std::vector<int> patch_moff;  // [nprob + 1] first patch of each problem in the library's numbering
+  std::vector<long long> user_patch_off;  // [nprob + 1] the caller's patch offsets
   int min_frames = 0;           // smallest problem (bound on fixed_poses)
+  float* user_patches = nullptr;  // caller's patches when the library works on a padded copy
+  int patches_padded = 0;
 
   // solver geometry for the last fixed value
   int fixed = -1;
@@ -107,7 +111,8 @@ struct DBuf {
 // device buffers, all owned by the handle
 struct Workspace {
   int* status = nullptr;          // [1] first device-detected error
-  float* intr = nullptr;          // [4]
+  float* intr = nullptr;          // [4 * intr_cap] intrinsics per problem
+  int intr_cap = 1;
   double* cost = nullptr;         // [cost_cap] cost at each iteration's linearisation point
   int* unsorted = nullptr;        // [1] input kk not non-decreasing
   long long cost_cap = 0;
@@ -131,6 +136,9 @@ struct Workspace {
   DBuf<int> fdx;                  // [N] offset of the frame's 6 unknowns in the system vectors, -1 fixed
   DBuf<SysDesc> sysd;             // [systems]
   DBuf<int> syslist;              // system indices of the solver launches
+  DBuf<int> mii, mjj, mkk;        // [E] edge indices in the library's numbering (bound problems)
+  DBuf<long long> offs;           // [3 (nprob + 1)] frame, patch and edge offsets of the bound problems
+  DBuf<float> pcopy;              // [P][27] padded patch copy (bound problems whose patch counts need padding)
   // per iteration
   DBuf<double> S;                 // tiled lower triangle of the pose system (FP64 accumulation)
   DBuf<double> y;                 // [n_pad]
