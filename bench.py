@@ -42,6 +42,8 @@ WORKLOADS = {
     "tiny": ("tiny BA: 8 frames, 96 patches/frame, +-3 frame edges, 2 GN iterations, 2 fixed poses", scenes.tiny),
     "global": ("global loop-closure BA: 1000 keyframes, 96 patches/frame, +-6 local + proximity loop edges, "
                "4 GN iterations, 2 fixed poses", scenes.global_ba),
+    "batched": ("batched uneven BA: 64 independent problems, frames round(exp(U[ln 8, ln 400])), 96 patches/frame, "
+                "+-6 local + proximity loop edges, 4 GN iterations each, 2 fixed poses each", scenes.batched),
 }
 KERNEL_FILES = {"assemble": "assemble.cu", "solve": "solve_small.cu", "backsub": "update.cu",
                 "retract": "update.cu", "init": "assemble.cu", "preprocess": "preprocess.cu"}
@@ -54,10 +56,15 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="odometry")
-    ap.add_argument("--precision", choices=["fp32", "mixed"], default="fp32")
+    ap.add_argument("--precision", choices=["fp32", "mixed"], default=None,
+                    help="fp32 (default) or mixed; the batched workload defaults to mixed")
     ap.add_argument("--group", type=int, default=0, help="patches per group (0 = automatic)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    return ap.parse_args()
+    a = ap.parse_args()
+    a.precision_set = a.precision is not None
+    if a.precision is None:
+        a.precision = "fp32"
+    return a
 
 
 # --------------------------------------------------------------------------- #
@@ -199,26 +206,39 @@ def run_reference(args):
     if rank != 0:
         return 0
     desc, make = WORKLOADS[args.workload]
-    scene = make(seed=0)
     import oracle
     oracle.build()
+    if args.workload == "batched":
+        # a bounded sample of the batch: six problems spread over the size range
+        probs = make(seed=0)
+        order = np.argsort([sc.N for sc in probs])
+        sample = [probs[int(b)] for b in order[:: max(1, len(probs) // 6)]][:6]
+        work = lambda: [oracle.gn(sc) for sc in sample]  # noqa: E731
+        iters_per_step = sum(sc.iters for sc in sample)
+        scene = sample[0]
+        desc += f"; oracle sample: problems of {[sc.N for sc in sample]} frames per step"
+    else:
+        scene = make(seed=0)
+        work = lambda: oracle.gn(scene)  # noqa: E731
+        iters_per_step = scene.iters
     for _ in range(min(args.warmup, 1)):
-        oracle.gn(scene)
+        work()
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        oracle.gn(scene)
+        work()
     el = time.perf_counter() - t0
-    value = args.steps * scene.iters / el
+    value = args.steps * iters_per_step / el
+    unit = "problem GN it/s" if args.workload == "batched" else UNIT
     line = {
-        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "impl": "reference", "metric": METRIC, "value": value, "unit": unit, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": desc, "N": scene.N, "P": scene.P, "E": scene.E, "iters": scene.iters},
         "edges_per_sec": value * scene.E,
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"full workload, {args.steps} steps of {scene.iters} GN iterations, "
+        "cpu_baseline": {"value": value, "unit": unit, "cores": 1, "kind": "oracle",
+                         "sample": f"{args.steps} steps of {iters_per_step} GN iterations ({desc.split(';')[-1].strip()}), "
                                    f"single-threaded FP64 oracle (-O2), {cpu_cores()} cores visible"},
-        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
     return 0
@@ -411,10 +431,199 @@ def run_ours(args):
     return 0
 
 
+def run_batched(args):
+    """The batched workload: all problems bound to one handle (one pass of
+    each kernel over every problem) against the plain per-problem form (one
+    handle per problem, FP32, problem after problem) at the same iterations."""
+    import torch
+
+    from paper_2408_01654_b300 import build as pbuild
+    from paper_2408_01654_b300.ba import DPVBA, batch_tensors, scene_tensors
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    if rank == 0:
+        pbuild.build()
+    if dist:
+        dist.barrier()
+    desc, make = WORKLOADS["batched"]
+    probs = make(seed=rank)
+    iters, fixed = probs[0].iters, probs[0].fixed
+    dev = torch.device("cuda", local)
+    T, offs = batch_tensors(probs, dev)
+    pristine = {k: v.clone() for k, v in T.items()}
+    stream = torch.cuda.current_stream(dev)
+    precision = "mixed" if args.precision == "fp32" and not args.precision_set else args.precision
+    ba = DPVBA(precision=precision, patches_per_group=args.group, stream=stream)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    B = len(probs)
+    E_tot = int(offs["edge_off"][-1])
+
+    def reset():
+        T["poses"].copy_(pristine["poses"])
+        T["patches"].copy_(pristine["patches"])
+
+    def one_step():
+        ba.set_graph_batched(**T, **offs)
+        ba.step(iters, fixed)
+
+    for _ in range(max(args.warmup, 3)):
+        reset()
+        one_step()
+    ba.sync()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    launches0 = ba.info()["launches"]
+    ba.profile(True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            reset()
+            flush.zero_()
+            ev[k][0].record(stream)
+            one_step()
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ba.sync()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    prof = ba.profile_read()
+    ba.profile(False)
+    launches = ba.info()["launches"] - launches0
+    if dist:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * args.steps * B * iters / (total_ms / 1e3)
+
+    # the plain form: one FP32 handle per problem, problem after problem
+    plain_T = [scene_tensors(sc, dev) for sc in probs]
+    plain_pristine = [{k: v.clone() for k, v in t.items()} for t in plain_T]
+    plain = [DPVBA(precision="fp32", stream=stream) for _ in probs]
+
+    def plain_step():
+        for h, t, p0 in zip(plain, plain_T, plain_pristine):
+            t["poses"].copy_(p0["poses"])
+            t["patches"].copy_(p0["patches"])
+            h.set_graph(**t)
+            h.step(iters, fixed)
+
+    for _ in range(2):
+        plain_step()
+    torch.cuda.synchronize()
+    pev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for k in range(args.steps):
+        flush.zero_()
+        pev[k][0].record(stream)
+        plain_step()
+        pev[k][1].record(stream)
+    torch.cuda.synchronize()
+    for h in plain:
+        h.sync()
+    plain_ms = sum(a.elapsed_time(b) for a, b in pev)
+    plain_value = args.steps * B * iters / (plain_ms / 1e3)
+
+    # end to end through the C ABI with host buffers
+    host_in = {k: v.cpu().pin_memory() for k, v in pristine.items()}
+    host_out = {"poses": torch.empty_like(host_in["poses"]).pin_memory(),
+                "patches": torch.empty_like(host_in["patches"]).pin_memory()}
+    h2d = sum(v.numel() * v.element_size() for v in host_in.values())
+    d2h = sum(v.numel() * v.element_size() for v in host_out.values())
+    e2e_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for k in range(args.steps):
+        flush.zero_()
+        e2e_ev[k][0].record(stream)
+        for name, hv in host_in.items():
+            T[name].copy_(hv, non_blocking=True)
+        one_step()
+        host_out["poses"].copy_(T["poses"], non_blocking=True)
+        host_out["patches"].copy_(T["patches"], non_blocking=True)
+        e2e_ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    e2e_value = world * args.steps * B * iters / (sum(a.elapsed_time(b) for a, b in e2e_ev) / 1e3)
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return 0
+
+    # error against the oracle on the first iteration of a bounded sample
+    err = None
+    cpu = None
+    if not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        reset()
+        ba.set_graph_batched(**T, **offs)
+        ba.step(1, fixed)
+        ba.sync()
+        order = np.argsort([sc.N for sc in probs])
+        sample = [int(b) for b in order[:: max(1, B // 6)]][:6]
+        errs = []
+        t0 = time.perf_counter()
+        for b in sample:
+            want = oracle.gn_steps(probs[b], iters=1)[0]
+            f0, f1 = offs["frame_off"][b], offs["frame_off"][b + 1]
+            p0, p1 = offs["patch_off"][b], offs["patch_off"][b + 1]
+            rot, tr = pose_errors(T["poses"][f0:f1].cpu().numpy(), want[0])
+            d = T["patches"][p0:p1, 2, 1, 1].cpu().numpy().astype(np.float64)
+            errs.append({"problem": b, "frames": probs[b].N, "rot_rad": rot, "trans_rel": tr,
+                         "depth_rel": float(np.max(np.abs(d - want[1]) / np.abs(want[1])))})
+        err = errs
+        # oracle throughput on the same sample (problem GN iterations per second)
+        runs, el = 0, 0.0
+        t1 = time.perf_counter()
+        for b in sample:
+            oracle.gn(probs[b])
+            runs += probs[b].iters
+            if time.perf_counter() - t1 > 20.0:
+                break
+        el = time.perf_counter() - t1
+        cpu = {"value": runs / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"problems {sample[:len(sample)]} of the batch ({runs} problem GN iterations), "
+                         f"single-threaded FP64 oracle (-O2) on 1 of {cpu_cores()} host cores, {el:.1f} s"}
+
+    dom = max((k for k in prof if prof[k][1] > 0), key=lambda k: prof[k][0])
+    t_ms, cnt = prof[dom]
+    line = {
+        "metric": METRIC, "value": value, "unit": "problem GN it/s", "n_gpus": world, "steps": args.steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": desc, "problems": B, "frames": [sc.N for sc in probs], "E_total": E_tot,
+                   "iters": iters, "fixed": fixed, "precision": precision, "patches_per_group": ba.info()["G"],
+                   "l2": "flushed between steps (256 MiB write)", "step": "ba_set_graph_batched + ba_step"},
+        "edges_per_sec": world * args.steps * E_tot * iters / (total_ms / 1e3),
+        "plain_per_problem_fp32": {"value": plain_value, "unit": "problem GN it/s", "ms_per_step": plain_ms / args.steps,
+                                   "what": "one FP32 handle per problem, set_graph + step, problem after problem"},
+        "batched_vs_plain": value / plain_value,
+        "error_vs_oracle": err,
+        "per_class_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
+        "dominant_class": {"kind": dom, "avg_launch_us": t_ms / cnt * 1e3},
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": "problem GN it/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batched":
+        return run_batched(args)
     return run_ours(args)
 
 

@@ -246,8 +246,8 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_edges(
       continue;
     }
     const int fi = wf[si], fj = wf[sj];
-    RelPose T;
-    dpv_relative_pose_f(posef + 16 * (size_t)fi, posef + 16 * (size_t)fj, T);
+    RelPose T;  // as in the forward assembly (the pose table is the one of x_s)
+    dpv_relative_pose_df(posef + DPV_POSE_ROW * (size_t)fi, posef + DPV_POSE_ROW * (size_t)fj, T);
     const int oi = fdx[fi], oj = fdx[fj];
     float li[6], lj[6], di[6], dj[6];
 #pragma unroll

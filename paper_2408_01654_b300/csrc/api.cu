@@ -380,7 +380,7 @@ ba_status_t ba_set_graph(ba_handle_t h, int N, int P, int E, double* poses, floa
       (s = dpv_grow(h, ws->gptr, Gn, "groups")) ||
       (s = dpv_grow(h, ws->win, Gn * DPV_WMAX, "windows")) || (s = dpv_grow(h, ws->wlen, Gn, "windows")) ||
       (s = dpv_grow(h, ws->pmpos, En, "patch-major positions")) || (s = dpv_grow(h, ws->pptr, (long long)P + 1, "patch CSR")) ||
-      (s = dpv_grow(h, ws->pterm, 4 * En, "edge depth terms")) || (s = dpv_grow(h, ws->posef, 16LL * N, "pose table")) ||
+      (s = dpv_grow(h, ws->pterm, 4 * En, "edge depth terms")) || (s = dpv_grow(h, ws->posef, (long long)DPV_POSE_ROW * N, "pose table")) ||
       (s = dpv_grow(h, ws->fprob, (long long)N + 2, "frame problems")) || (s = dpv_grow(h, ws->gprob, Gn, "group problems")))
     return s;
   // one problem: every frame and group belongs to problem 0; frame_off = {0, N} follows fprob
@@ -479,7 +479,7 @@ ba_status_t ba_set_graph_batched(ba_handle_t h, int B, const long long* frame_of
       (s = dpv_grow(h, ws->gptr, Gn, "groups")) || (s = dpv_grow(h, ws->win, Gn * DPV_WMAX, "windows")) ||
       (s = dpv_grow(h, ws->wlen, Gn, "windows")) || (s = dpv_grow(h, ws->pmpos, En, "patch-major positions")) ||
       (s = dpv_grow(h, ws->pptr, (long long)P + 1, "patch CSR")) || (s = dpv_grow(h, ws->pterm, 4 * En, "edge depth terms")) ||
-      (s = dpv_grow(h, ws->posef, 16LL * N, "pose table")) ||
+      (s = dpv_grow(h, ws->posef, (long long)DPV_POSE_ROW * N, "pose table")) ||
       (s = dpv_grow(h, ws->fprob, (long long)N + B + 1, "frame problems")) ||
       (s = dpv_grow(h, ws->gprob, Gn, "group problems")) || (s = dpv_grow(h, ws->mii, En, "edge frames")) ||
       (s = dpv_grow(h, ws->mjj, En, "edge frames")) || (s = dpv_grow(h, ws->mkk, En, "edge patches")) ||

@@ -131,8 +131,8 @@ __global__ void __launch_bounds__(AS_THREADS) k_assemble(
     const unsigned sw = eslot[gs + runptr[r]];
     const int si = dpv_slot_i(sw), sj = dpv_slot_j(sw);
     rsl[r] = si | (sj << 8);
-    RelPose T;
-    dpv_relative_pose_f(posef + 16 * (size_t)wf[si], posef + 16 * (size_t)wf[sj], T);
+    RelPose T;  // accurate to rounding: its error is shared by the whole run
+    dpv_relative_pose_df(posef + DPV_POSE_ROW * (size_t)wf[si], posef + DPV_POSE_ROW * (size_t)wf[sj], T);
     float* o = rpose + 21 * r;
 #pragma unroll
     for (int m = 0; m < 9; ++m) o[m] = T.R[m];
@@ -416,16 +416,15 @@ __global__ void __launch_bounds__(AS_THREADS) k_assemble(
   }
 }
 
-// S <- 0 (lambda_p on the free diagonal, 1 on the padding diagonal), y <- 0,
-// and the per-pose table for this iteration: R (FP32) and the camera centre
-// c = -R^T t as a double-float pair, formed in FP64 from the FP64 pose.
+// S <- 0, y <- 0 (or the given right-hand side), and the per-pose table for
+// this iteration (R and the camera centre as double-float pairs).
 __global__ void k_init_system(double* __restrict__ S, size_t nS, double* __restrict__ y, int nv,
                               const double* __restrict__ y_init, const double* __restrict__ poses, int N,
                               float* __restrict__ posef, const int* status) {
   if (dpv_status(status)) return;
   const size_t stride = (size_t)gridDim.x * blockDim.x;
   const size_t gid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (gid < (size_t)N) dpv_pose_table_row(poses + 7 * gid, posef + 16 * gid);
+  if (gid < (size_t)N) dpv_pose_table_row(poses + 7 * gid, posef + DPV_POSE_ROW * gid);
   double2* S2 = reinterpret_cast<double2*>(S);
   for (size_t q = gid; q < nS / 2; q += stride) S2[q] = make_double2(0.0, 0.0);
   for (size_t q = gid; q < (size_t)nv; q += stride) y[q] = y_init ? y_init[q] : 0.0;

@@ -285,53 +285,32 @@ __device__ __forceinline__ void dpv_quat_rot64(const double* q, double* R) {
   R[6] = 2.0 * (x * z - y * w); R[7] = 2.0 * (y * z + x * w); R[8] = 1.0 - 2.0 * (x * x + y * y);
 }
 
-// One row of the per-pose FP32 table used by the linearisation: R (9 floats)
-// and the camera centre c = -R^T t as a double-float pair (hi 3, lo 3), formed
-// in FP64 from the FP64 pose (t, q).
+// One row of the per-pose table used by the linearisation (DPV_POSE_ROW
+// floats): R as double-float pairs (hi 9, lo 9) and the camera centre
+// c = -R^T t as pairs (hi 3, lo 3), formed in FP64 from the FP64 pose (t, q).
+#define DPV_POSE_ROW 32
 __device__ __forceinline__ void dpv_pose_table_row(const double* __restrict__ p, float* __restrict__ o) {
   double R[9];
   dpv_quat_rot64(p + 3, R);
 #pragma unroll
-  for (int m = 0; m < 9; ++m) o[m] = dpv_d2f_bits(R[m]);
+  for (int m = 0; m < 9; ++m) {
+    const float hi = dpv_d2f_bits(R[m]);
+    o[m] = hi;
+    o[9 + m] = dpv_d2f_bits(R[m] - dpv_f2d_bits(hi));
+  }
 #pragma unroll
   for (int m = 0; m < 3; ++m) {
     const double c = -(R[m] * p[0] + R[3 + m] * p[1] + R[6 + m] * p[2]);
     const float hi = dpv_d2f_bits(c);
-    o[9 + m] = hi;
-    o[12 + m] = dpv_d2f_bits(c - dpv_f2d_bits(hi));
+    o[18 + m] = hi;
+    o[21 + m] = dpv_d2f_bits(c - dpv_f2d_bits(hi));
   }
-  o[15] = 0.f;
 }
 
 struct RelPose {
   float R[9], t[3], txR[9];  // rotation, translation, [t]x R (translation-rotation block of Ad)
 };
 
-// Relative pose T_ij = T_j T_i^-1 of two world->camera poses (t, q), formed
-// in FP64 and rounded to FP32:  R = R_j R_i^T,  t = t_j - R t_i.
-__device__ __forceinline__ void dpv_relative_pose(const double* pi, const double* pj, RelPose& o) {
-  double Ri[9], Rj[9], R[9];
-  dpv_quat_rot64(pi + 3, Ri);
-  dpv_quat_rot64(pj + 3, Rj);
-#pragma unroll
-  for (int r = 0; r < 3; ++r)
-#pragma unroll
-    for (int c = 0; c < 3; ++c)
-      R[3 * r + c] = Rj[3 * r] * Ri[3 * c] + Rj[3 * r + 1] * Ri[3 * c + 1] + Rj[3 * r + 2] * Ri[3 * c + 2];
-  double t[3];
-#pragma unroll
-  for (int r = 0; r < 3; ++r) t[r] = pj[r] - (R[3 * r] * pi[0] + R[3 * r + 1] * pi[1] + R[3 * r + 2] * pi[2]);
-#pragma unroll
-  for (int m = 0; m < 9; ++m) o.R[m] = (float)R[m];
-#pragma unroll
-  for (int m = 0; m < 3; ++m) o.t[m] = (float)t[m];
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    o.txR[0 + c] = (float)(-t[2] * R[3 + c] + t[1] * R[6 + c]);
-    o.txR[3 + c] = (float)(t[2] * R[0 + c] - t[0] * R[6 + c]);
-    o.txR[6 + c] = (float)(-t[1] * R[0 + c] + t[0] * R[3 + c]);
-  }
-}
 
 // Per-edge linearisation of Eq. 3 at the patch centre (FP32).
 //   X = R xb + t d  (xb = ((u-cx)/fx, (v-cy)/fy, 1), homogeneous 4th entry d)
@@ -419,22 +398,39 @@ __device__ __forceinline__ void ks_fma(KS& a, float x, float y) {
 }
 __device__ __forceinline__ DF ks_df(const KS& a) { return DF{a.s, -a.c}; }
 
-// per-pose FP32 data for the relative poses: rotation R (world->camera) and
-// camera centre c = -R^T t in double-float (hi, lo) so that c_i - c_j keeps
-// full FP32 relative accuracy even far from the origin.
-__device__ __forceinline__ void dpv_relative_pose_f(const float* Pi, const float* Pj, RelPose& o) {
-  // R = Rj Ri^T
+// Relative pose T_ij = T_j T_i^-1 from two rows of the pose table, in
+// double-float arithmetic on the FP32 pipe and rounded once to FP32 (as
+// accurate as forming it in FP64 from the FP64 poses, at a fraction of the
+// cost; FP32 products of FP32-rounded rotations cost ~1e-5 of the step on
+// ill-conditioned systems):  R = R_j R_i^T,  t = R_j (c_i - c_j).
+__device__ __forceinline__ float dpv_dot3_df(const float* ah, const float* al, int as, const float* bh,
+                                             const float* bl, int bs) {
+  DF acc = {0.f, 0.f};
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const float a = ah[k * as], b = bh[k * bs];
+    df_fma(acc, a, b);
+    acc.lo = __fmaf_rn(a, bl[k * bs], __fmaf_rn(al[k * as], b, acc.lo));
+  }
+  return acc.hi + acc.lo;
+}
+__device__ __forceinline__ void dpv_relative_pose_df(const float* Pi, const float* Pj, RelPose& o) {
 #pragma unroll
   for (int r = 0; r < 3; ++r)
 #pragma unroll
     for (int c = 0; c < 3; ++c)
-      o.R[3 * r + c] = Pj[3 * r] * Pi[3 * c] + Pj[3 * r + 1] * Pi[3 * c + 1] + Pj[3 * r + 2] * Pi[3 * c + 2];
-  // t = t_j - R t_i = R_j (c_i - c_j)
-  float dc[3];
+      o.R[3 * r + c] = dpv_dot3_df(Pj + 3 * r, Pj + 9 + 3 * r, 1, Pi + 3 * c, Pi + 9 + 3 * c, 1);
+  float dh[3], dl[3];
 #pragma unroll
-  for (int m = 0; m < 3; ++m) dc[m] = (Pi[9 + m] - Pj[9 + m]) + (Pi[12 + m] - Pj[12 + m]);
+  for (int m = 0; m < 3; ++m) {  // c_i - c_j as a pair
+    DF d = {Pi[18 + m], 0.f};
+    df_add(d, -Pj[18 + m]);
+    d.lo = __fadd_rn(d.lo, __fsub_rn(Pi[21 + m], Pj[21 + m]));
+    dh[m] = d.hi;
+    dl[m] = d.lo;
+  }
 #pragma unroll
-  for (int r = 0; r < 3; ++r) o.t[r] = Pj[3 * r] * dc[0] + Pj[3 * r + 1] * dc[1] + Pj[3 * r + 2] * dc[2];
+  for (int r = 0; r < 3; ++r) o.t[r] = dpv_dot3_df(Pj + 3 * r, Pj + 9 + 3 * r, 1, dh, dl, 1);
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     o.txR[0 + c] = -o.t[2] * o.R[3 + c] + o.t[1] * o.R[6 + c];

@@ -3,8 +3,10 @@
 // complement, which the appendix "Bundle-Adjustment Efficiency" names as the
 // memory and runtime bottleneck of global optimisation).
 //
-// S (FP64, tiled lower triangle, 64 x 64 tiles) is rounded to an FP32 copy in
-// the same tiled layout and factored as S = L D L^T by ONE persistent kernel
+// S (FP64, tiled lower triangle, 64 x 64 tiles) is equilibrated (s_i S_ij s_j,
+// s = diag(S)^-1/2: the factorisation error then scales with the condition
+// number of the equilibrated matrix), rounded to an FP32 copy in the same
+// tiled layout and factored as S' = L D L^T by ONE persistent kernel
 // that runs a task graph over the tiles:
 //   DIAG(k)        factor tile (k,k): unit L_kk, D_k, and the inverse L_kk^-1
 //   PANEL(i,k)     L_ik = A_ik L_kk^-T D_k^-1                      (i > k)
@@ -21,7 +23,8 @@
 // A second persistent kernel runs the triangular solves and the refinement:
 // block row i of the forward solve waits for the rows above it, the backward
 // solve for the rows below; a grid barrier separates the sweeps, whose
-// residual rho = y - S x is formed in FP64 from the FP64 S.
+// residual rho = y - S x is formed in FP64 from the FP64 S, until the
+// correction is below 1e-7 of the solution.
 #include "internal.cuh"
 
 #include <map>
@@ -402,13 +405,34 @@ __device__ void task_update(LgShared& sm, float* A, const float* D, int i, int j
 // kernels
 // ---------------------------------------------------------------------------
 
-// S (FP64 tiles) -> A (FP32 tiles); identical tile layout
-__global__ void k_lg_convert(const double* __restrict__ S, float* __restrict__ A, size_t count, const int* status) {
+// equilibration scale s = diag(S)^-1/2 (1 on the padding)
+__global__ void k_lg_scale(const double* __restrict__ S, int n, int n_pad, float* __restrict__ sc,
+                           const int* status) {
   if (dpv_status(status)) return;
-  const size_t stride = (size_t)gridDim.x * blockDim.x;
-  for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < count / 2; q += stride) {
-    const double2 v = reinterpret_cast<const double2*>(S)[q];
-    reinterpret_cast<float2*>(A)[q] = make_float2(dpv_d2f_bits(v.x), dpv_d2f_bits(v.y));
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n_pad) return;
+  const float d = dpv_d2f_bits(S[dpv_s_index(r, r, NB)]);
+  sc[r] = (r < n && d > 0.f) ? rsqrtf(d) : 1.f;
+}
+
+// S (FP64 tiles) -> A (FP32 tiles, identical layout), equilibrated:
+// A_ij = s_i S_ij s_j.  One CTA per tile.
+__global__ void k_lg_convert(const double* __restrict__ S, const float* __restrict__ sc, float* __restrict__ A,
+                             int T, const int* status) {
+  if (dpv_status(status)) return;
+  for (int t = blockIdx.x; t < tri2(T); t += gridDim.x) {
+    int ti = (int)((sqrtf(8.0f * t + 1.0f) - 1.0f) * 0.5f);
+    while (tri2(ti + 1) <= t) ++ti;
+    while (tri2(ti) > t) --ti;
+    const int tj = t - tri2(ti);
+    const double2* src = reinterpret_cast<const double2*>(S + (size_t)t * TILE);
+    float2* dst = reinterpret_cast<float2*>(A + (size_t)t * TILE);
+    for (int q = threadIdx.x; q < TILE / 2; q += blockDim.x) {
+      const int r = (2 * q) / NB, c = (2 * q) % NB;
+      const double2 v = src[q];
+      const float si = sc[ti * NB + r];
+      dst[q] = make_float2(dpv_d2f_bits(v.x) * si * sc[tj * NB + c], dpv_d2f_bits(v.y) * si * sc[tj * NB + c + 1]);
+    }
   }
 }
 
@@ -538,9 +562,9 @@ __device__ void tile_gemv(const TileRegs& t, const float* v, float* out, bool tr
 // owns block rows i = b (mod grid), in both directions.
 __global__ void __launch_bounds__(LG_THREADS, 1) k_lg_solve(
     int T, int n, const float* __restrict__ A, const float* __restrict__ Linv, const float* __restrict__ invD,
-    const double* __restrict__ S, const double* __restrict__ y, float* rhs, float* xf, float* xb, double* xacc,
-    double* __restrict__ dx, float* __restrict__ dxf, int sweeps, int* flags, int* bar, int* status,
-    long long timeout) {
+    const double* __restrict__ S, const double* __restrict__ y, const float* __restrict__ sc, float* rhs, float* xf,
+    float* xb, double* xacc, double* __restrict__ dx, float* __restrict__ dxf, int sweeps, int* flags, int* bar,
+    int* conv, int* status, long long timeout) {
   __shared__ float acc[NB], vj[NB], prod[NB];
   __shared__ float part[16][NB + 1];
   __shared__ int ok;
@@ -602,9 +626,29 @@ __global__ void __launch_bounds__(LG_THREADS, 1) k_lg_solve(
     if (!grid_barrier(bar, gridDim.x, status, timeout)) return;
     // ---- accumulate the correction, then the next residual
     const int gt = blockIdx.x * LG_THREADS + tid, gs = gridDim.x * LG_THREADS;
-    for (int q = gt; q < n_pad; q += gs) xacc[q] = (sweep == 0 ? 0.0 : xacc[q]) + dpv_f2d_bits(__ldcg(xb + q));
+    // (the solve ran on the equilibrated system: x = s z); stop once the
+    // correction is below 1e-7 of the solution
+    float cmax = 0.f, xmax = 0.f;
+    for (int q = gt; q < n_pad; q += gs) {
+      const double c = dpv_f2d_bits(__ldcg(xb + q)) * dpv_f2d_bits(sc[q]);
+      const double x = (sweep == 0 ? 0.0 : xacc[q]) + c;
+      xacc[q] = x;
+      cmax = fmaxf(cmax, fabsf(dpv_d2f_bits(c)));
+      xmax = fmaxf(xmax, fabsf(dpv_d2f_bits(x)));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      cmax = fmaxf(cmax, __shfl_xor_sync(0xffffffffu, cmax, o));
+      xmax = fmaxf(xmax, __shfl_xor_sync(0xffffffffu, xmax, o));
+    }
+    if ((tid & 31) == 0) {  // non-negative floats order like their bit patterns
+      atomicMax(conv + 2 * sweep, __float_as_int(cmax));
+      atomicMax(conv + 2 * sweep + 1, __float_as_int(xmax));
+    }
     if (sweep + 1 == sweeps) break;
     if (!grid_barrier(bar, gridDim.x, status, timeout)) return;
+    if (sweep > 0 && __int_as_float(ld_acquire(conv + 2 * sweep)) <= 1e-7f * __int_as_float(ld_acquire(conv + 2 * sweep + 1)))
+      break;
     // rho = y - S xacc in FP64, one warp per row
     const int lane = tid & 31, gw = gt >> 5, nw = gs >> 5;
     for (int row = gw; row < n_pad; row += nw) {
@@ -614,7 +658,7 @@ __global__ void __launch_bounds__(LG_THREADS, 1) k_lg_solve(
           sacc += S[c <= row ? dpv_s_index(row, c, NB) : dpv_s_index(c, row, NB)] * __ldcg(xacc + c);
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, o);
-      if (lane == 0) rhs[row] = row < n ? dpv_d2f_bits(y[row] - sacc) : 0.f;
+      if (lane == 0) rhs[row] = row < n ? dpv_d2f_bits(y[row] - sacc) * sc[row] : 0.f;
     }
     if (!grid_barrier(bar, gridDim.x, status, timeout)) return;
   }
@@ -626,11 +670,11 @@ __global__ void __launch_bounds__(LG_THREADS, 1) k_lg_solve(
   }
 }
 
-__global__ void k_lg_init_rhs(int n, int n_pad, const double* __restrict__ y, float* __restrict__ rhs,
-                              const int* status) {
+__global__ void k_lg_init_rhs(int n, int n_pad, const double* __restrict__ y, const float* __restrict__ sc,
+                              float* __restrict__ rhs, const int* status) {
   if (dpv_status(status)) return;
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
-  if (q < n_pad) rhs[q] = q < n ? dpv_d2f_bits(y[q]) : 0.f;
+  if (q < n_pad) rhs[q] = q < n ? dpv_d2f_bits(y[q]) * sc[q] : 0.f;
 }
 
 // Worker task list in dependency order.  The critical-path CTA does DIAG(k),
@@ -673,8 +717,8 @@ int co_resident(ba_handle_t h, const void* fn, size_t smem = 0) {
 
 long long dpv_large_scratch_floats(int n_pad) {
   const long long T = n_pad / NB;
-  // tiles of A, inverses of the diagonal factors, D, D^-1, rhs, xf, xb
-  return (long long)tri2((int)T) * TILE + T * TILE + 5LL * n_pad;
+  // tiles of A, inverses of the diagonal factors, D, D^-1, rhs, xf, xb, equilibration scale
+  return (long long)tri2((int)T) * TILE + T * TILE + 6LL * n_pad;
 }
 
 ba_status_t dpv_solve_blocked(ba_handle_t h, const SysDesc& sd, int refine) {
@@ -706,7 +750,10 @@ ba_status_t dpv_solve_blocked(ba_handle_t h, const SysDesc& sd, int refine) {
     ntasks = tc.counts[key];
   }
   ba_status_t s;
-  const long long nsync = tri2(T) + 2LL * T + 8;  // versions, row flags, counter, barrier, critical SM
+  constexpr int MAX_SWEEPS = 16;
+  refine = std::min(refine, MAX_SWEEPS - 1);
+  // versions, row flags, counter, barrier, critical SM, convergence maxima per sweep
+  const long long nsync = tri2(T) + 2LL * T + 8 + 2 * MAX_SWEEPS;
   if ((s = dpv_grow(h, ws->lg_sync, nsync, "large solver sync"))) return s;
   float* A = ws->L.p;
   float* Linv = A + (size_t)tri2(T) * TILE;
@@ -715,19 +762,22 @@ ba_status_t dpv_solve_blocked(ba_handle_t h, const SysDesc& sd, int refine) {
   float* rhs = invD + n_pad;
   float* xf = rhs + n_pad;
   float* xb = xf + n_pad;
+  float* sc = xb + n_pad;
   int* ver = ws->lg_sync.p;
   int* flags = ver + tri2(T);
   int* ctr = flags + 2 * T;
   int* bar = ctr + 1;   // two ints
   int* dsm = bar + 2;
+  int* conv = dsm + 2;  // [2 * MAX_SWEEPS]
   int* status = ws->status;
   cudaStream_t st = h->stream;
   DPV_CUDA(h, cudaMemsetAsync(ver, 0, sizeof(int) * nsync, st));
-  const size_t count = (size_t)tri2(T) * TILE;
   const double* Sb = ws->S.p + sd.soff;
-  k_lg_convert<<<4 * h->num_sms, 256, 0, st>>>(Sb, A, count, status);
+  k_lg_scale<<<(n_pad + 255) / 256, 256, 0, st>>>(Sb, n, n_pad, sc, status);
   ++h->launches;
-  k_lg_init_rhs<<<(n_pad + 255) / 256, 256, 0, st>>>(n, n_pad, ws->y.p + sd.voff, rhs, status);
+  k_lg_convert<<<std::min(tri2(T), 8 * h->num_sms), 256, 0, st>>>(Sb, sc, A, T, status);
+  ++h->launches;
+  k_lg_init_rhs<<<(n_pad + 255) / 256, 256, 0, st>>>(n, n_pad, ws->y.p + sd.voff, sc, rhs, status);
   ++h->launches;
   long long timeout = h->opt.timeout_cycles;
   {
@@ -757,9 +807,11 @@ ba_status_t dpv_solve_blocked(ba_handle_t h, const SysDesc& sd, int refine) {
     float* dxf = ws->tmpv.p + sd.voff;
     int sweeps = refine + 1;
     int n_ = n;
-    void* args[] = {(void*)&T,   (void*)&n_,    (void*)&A,   (void*)&Linv,  (void*)&invD,   (void*)&S,
-                    (void*)&y,   (void*)&rhs,   (void*)&xf,  (void*)&xb,    (void*)&xacc,   (void*)&dx,
-                    (void*)&dxf, (void*)&sweeps, (void*)&flags, (void*)&bar, (void*)&status, (void*)&timeout};
+    const float* scc = sc;
+    void* args[] = {(void*)&T,   (void*)&n_,   (void*)&A,      (void*)&Linv,  (void*)&invD, (void*)&S,
+                    (void*)&y,   (void*)&scc,  (void*)&rhs,    (void*)&xf,    (void*)&xb,   (void*)&xacc,
+                    (void*)&dx,  (void*)&dxf,  (void*)&sweeps, (void*)&flags, (void*)&bar,  (void*)&conv,
+                    (void*)&status, (void*)&timeout};
     DPV_CUDA(h, cudaLaunchCooperativeKernel((const void*)k_lg_solve, dim3(grid), dim3(LG_THREADS), args, 0, st));
     ++h->launches;
   }

@@ -21,11 +21,20 @@
 // retraction of the poses runs in the back-substitution kernel, off this
 // single-CTA critical path.
 //
-// Refinement: sweeps of x += S^-1 (y - S x) with the same factor.  In
-// BA_FP32 one sweep computes the residual in compensated FP32 (TwoProd /
-// TwoSum) from the FP32 copy of S, which removes the factorisation error;
-// in BA_MIXED the sweeps compute it in FP64 from the FP64 S.
+// Equilibration: the FP32 copies are scaled to S' = diag(s) S diag(s) with
+// s = diag(S)^-1/2 (unit diagonal), which bounds the factorisation error by the
+// condition number of S' instead of S (the pose blocks mix rotations and
+// translations of very different scale; loop closures make S ill-conditioned).
+// The solve works on z = x / s and returns x = s z.
+//
+// Refinement: sweeps of x += S^-1 (y - S x) with the same factor, until the
+// correction is below 1e-7 of the solution.  In BA_FP32 the sweeps compute the
+// residual in compensated FP32 (TwoProd / TwoSum) from the FP32 copy of S,
+// which removes the factorisation error; in BA_MIXED they compute it in FP64
+// from the FP64 S.
 #include "internal.cuh"
+
+#include <algorithm>
 
 namespace {
 
@@ -62,6 +71,8 @@ __global__ void __launch_bounds__(small_threads(NQ)) k_solve_small(
   __shared__ float rhs[NP];
   __shared__ float xhi[NP], xlo[NP];
   __shared__ float yhi[NP], ylo[NP];
+  __shared__ float sc[NP];  // equilibration: S' = diag(sc) S diag(sc), sc = 1 / sqrt(diag S)
+  __shared__ float red[2 * NWARP];
   __shared__ int bad;
   if (dpv_status(status)) return;
   int n = n_direct;
@@ -114,6 +125,21 @@ __global__ void __launch_bounds__(small_threads(NQ)) k_solve_small(
     }
   }
   if (tid == 0) bad = 0;
+  for (int i = tid; i < NP; i += NT) {
+    const float d = dpv_d2f_bits(S[(size_t)i * NP + i]);
+    sc[i] = (i < n && d > 0.f) ? rsqrtf(d) : 1.f;
+  }
+  __syncthreads();
+  // equilibrate the FP32 copies (the FP64 refinement residual uses the FP64 S)
+  for (int i = wid; i < NP; i += NWARP)
+    for (int j = lane; j <= i; j += 32) {
+      const float f = sc[i] * sc[j];
+      Lsh[tri(i, j)] *= f;
+      if (keep_sf(NQ)) {
+        Sf[i * SFS + j] *= f;
+        if (j != i) Sf[j * SFS + i] *= f;
+      }
+    }
   // reset: leave S (lower triangle) as the next assembly expects it: zero,
   // lambda_p on the free diagonal, 1 on the padding diagonal.  Done here when
   // no refinement sweep reads S from global memory again, else at the end.
@@ -241,7 +267,7 @@ __global__ void __launch_bounds__(small_threads(NQ)) k_solve_small(
     return;
   }
   for (int q = tid; q < NP; q += NT) {
-    const double yq = q < n ? y[q] : 0.0;
+    const double yq = q < n ? y[q] * (double)sc[q] : 0.0;  // the equilibrated right-hand side
     const float yh = (float)yq;
     yhi[q] = yh;
     ylo[q] = (float)(yq - (double)yh);
@@ -294,15 +320,36 @@ __global__ void __launch_bounds__(small_threads(NQ)) k_solve_small(
       }
       __syncthreads();
     }
-    // x += correction (double-float)
+    // x += correction (double-float); stop once the correction is below
+    // 1e-7 of the solution (refinement converged)
+    float cmax = 0.f, xmax = 0.f;
     for (int q = tid; q < NP; q += NT) {
       DF a = {xhi[q], xlo[q]};
       df_add(a, rhs[q]);
       xhi[q] = a.hi;
       xlo[q] = a.lo;
+      cmax = fmaxf(cmax, fabsf(rhs[q]));
+      xmax = fmaxf(xmax, fabsf(a.hi));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      cmax = fmaxf(cmax, __shfl_xor_sync(0xffffffffu, cmax, o));
+      xmax = fmaxf(xmax, __shfl_xor_sync(0xffffffffu, xmax, o));
+    }
+    if (lane == 0) {
+      red[wid] = cmax;
+      red[NWARP + wid] = xmax;
     }
     __syncthreads();
     if (sweep + 1 == sweeps) break;
+    if (sweep > 0) {
+      float cm = 0.f, xm = 0.f;
+      for (int w = 0; w < NWARP; ++w) {
+        cm = fmaxf(cm, red[w]);
+        xm = fmaxf(xm, red[NWARP + w]);
+      }
+      if (cm <= 1e-7f * xm) break;  // the same decision in every thread
+    }
     // residual rho = y - S x
     if (sweep < refine32 && keep_sf(NQ)) {
       // compensated FP32 against the FP32 copy of S: four threads per row,
@@ -338,18 +385,19 @@ __global__ void __launch_bounds__(small_threads(NQ)) k_solve_small(
         if (r < n)
           for (int c = lane; c < n; c += 32) {
             const double sv = c <= r ? S[(size_t)r * NP + c] : S[(size_t)c * NP + r];
-            acc += sv * ((double)xhi[c] + (double)xlo[c]);
+            acc += sv * ((double)sc[c] * ((double)xhi[c] + (double)xlo[c]));
           }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (lane == 0) rhs[r] = r < n ? (float)(y[r] - acc) : 0.f;
+        if (lane == 0) rhs[r] = r < n ? (float)((y[r] - acc) * (double)sc[r]) : 0.f;
       }
     }
     __syncthreads();
   }
   for (int q = tid; q < n; q += NT) {
-    dx[q] = dpv_f2d_bits(xhi[q]) + dpv_f2d_bits(xlo[q]);
-    dxf[q] = xhi[q] + xlo[q];
+    const double xq = (dpv_f2d_bits(xhi[q]) + dpv_f2d_bits(xlo[q])) * dpv_f2d_bits(sc[q]);
+    dx[q] = xq;
+    dxf[q] = dpv_d2f_bits(xq);
   }
   if (reset) {
     if (s_read_later) {
@@ -384,7 +432,9 @@ ba_status_t dpv_solve_blocked(ba_handle_t h, const SysDesc& sd, int refine);
 // block count (one CTA per system), then the large systems.
 ba_status_t dpv_solve(ba_handle_t h, int* retracted, int reset_system) {
   // BA_FP32: one compensated-FP32 refinement sweep; BA_MIXED: FP64 sweeps
-  const int refine32 = h->opt.precision == BA_MIXED ? 0 : 1;
+  // refinement sweeps, stopped early once converged: BA_FP32 up to three
+  // compensated-FP32 sweeps (small systems), BA_MIXED FP64 sweeps
+  const int refine32 = h->opt.precision == BA_MIXED ? 0 : 3;
   const int refine64 = h->opt.precision == BA_MIXED ? h->opt.max_refine : 0;
   *retracted = 0;
   if (h->n == 0) return BA_OK;
@@ -407,9 +457,9 @@ ba_status_t dpv_solve(ba_handle_t h, int* retracted, int reset_system) {
     if (s) return s;
     off += cnt;
   }
-  // large systems: FP64 refinement sweeps (at least one)
+  // large systems: FP64 refinement sweeps until converged (at least four allowed)
   for (int b : h->large_sys)
-    if ((s = dpv_solve_blocked(h, h->sys[b], refine32 + refine64))) return s;
+    if ((s = dpv_solve_blocked(h, h->sys[b], std::max(4, refine64)))) return s;
   return BA_OK;
 }
 

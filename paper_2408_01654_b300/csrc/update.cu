@@ -36,7 +36,7 @@ __global__ void __launch_bounds__(BS_THREADS) k_backsub(
     const int o = fdx[f];
     if (o >= 0) {
       dpv_se3_retract(dx + o, poses + 7 * (size_t)f);
-      if (posef) dpv_pose_table_row(poses + 7 * (size_t)f, posef + 16 * (size_t)f);
+      if (posef) dpv_pose_table_row(poses + 7 * (size_t)f, posef + DPV_POSE_ROW * (size_t)f);
     }
   }
   const int k = blockIdx.x * BS_WARPS + (threadIdx.x >> 5);
