@@ -178,7 +178,7 @@ ba_status_t ensure_system(ba_handle_t h, int fixed) {
       h->small_nq[d.n_pad / 32].push_back(b);
     } else {
       h->large_sys.push_back(b);
-      large_scratch = std::max(large_scratch, dpv_large_scratch_floats(d.n_pad));
+      large_scratch += dpv_large_scratch_floats(d.n_pad);  // all large systems are factored together
     }
   }
   if (voff > (1LL << 30) || soff > (1LL << 40)) return dpv_fail(h, BA_ERR_UNSUPPORTED, "pose systems too large");
@@ -290,7 +290,7 @@ ba_status_t ba_destroy(ba_handle_t h) {
     release(ws->pterm); release(ws->posef);
     release(ws->tp_poses); release(ws->tp_patches); release(ws->tp_dx); release(ws->tp_dd);
     release(ws->ad_xb); release(ws->ad_w); release(ws->ad_gd); release(ws->ad_lamd); release(ws->ad_v);
-    release(ws->ad_gt); release(ws->ad_gw); release(ws->lg_sync); release(ws->fprob); release(ws->gprob);
+    release(ws->ad_gt); release(ws->ad_gw); release(ws->lg_sync); release(ws->lg_prob); release(ws->lg_rb); release(ws->fprob); release(ws->gprob);
     release(ws->fdx); release(ws->sysd); release(ws->syslist); release(ws->mii); release(ws->mjj); release(ws->mkk);
     release(ws->offs); release(ws->pcopy);
     delete ws;

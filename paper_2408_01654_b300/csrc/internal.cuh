@@ -149,6 +149,8 @@ struct Workspace {
   // blocked solver
   DBuf<float> L;                  // factor (large n)
   DBuf<int> lg_sync;              // large solver: tile versions, row flags, task counter, grid barrier
+  DBuf<long long> lg_prob;        // large solver: per-system descriptors
+  DBuf<int> lg_rb;                // large solver: system of each global row block
   DBuf<double> r64;               // [n_pad]
   DBuf<float> tmpv;               // [n_pad]
   // tape of a recorded ba_step: states before each iteration (+ the final poses) and the steps

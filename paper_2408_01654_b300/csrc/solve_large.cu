@@ -405,72 +405,87 @@ __device__ void task_update(LgShared& sm, float* A, const float* D, int i, int j
 // kernels
 // ---------------------------------------------------------------------------
 
-// equilibration scale s = diag(S)^-1/2 (1 on the padding)
-__global__ void k_lg_scale(const double* __restrict__ S, int n, int n_pad, float* __restrict__ sc,
-                           const int* status) {
+// One large pose system as the kernels see it (device copy per launch).
+struct LgProb {
+  float *A, *Linv, *D, *invD, *rhs, *xf, *xb, *sc;  // factor scratch
+  const double* S;                                 // FP64 tiled lower triangle
+  const double* y;                                 // right-hand side
+  double *xacc, *dx;                               // refinement accumulator, output
+  float* dxf;                                      // FP32 copy of the output
+  int *ver, *flags;                                // tile versions [tri(T)], row flags [2T]
+  int T, n, n_pad, rb0;                            // tiles, unknowns, padded size, first global row block
+};
+
+// equilibration scale s = diag(S)^-1/2 (1 on the padding); blockIdx.y = system
+__global__ void k_lg_scale(const LgProb* __restrict__ probs, const int* status) {
   if (dpv_status(status)) return;
+  const LgProb P = probs[blockIdx.y];
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= n_pad) return;
-  const float d = dpv_d2f_bits(S[dpv_s_index(r, r, NB)]);
-  sc[r] = (r < n && d > 0.f) ? rsqrtf(d) : 1.f;
+  if (r >= P.n_pad) return;
+  const float d = dpv_d2f_bits(P.S[dpv_s_index(r, r, NB)]);
+  P.sc[r] = (r < P.n && d > 0.f) ? rsqrtf(d) : 1.f;
+  P.rhs[r] = r < P.n ? dpv_d2f_bits(P.y[r]) * P.sc[r] : 0.f;
 }
 
 // S (FP64 tiles) -> A (FP32 tiles, identical layout), equilibrated:
-// A_ij = s_i S_ij s_j.  One CTA per tile.
-__global__ void k_lg_convert(const double* __restrict__ S, const float* __restrict__ sc, float* __restrict__ A,
-                             int T, const int* status) {
+// A_ij = s_i S_ij s_j.  CTAs stride over the tiles; blockIdx.y = system.
+__global__ void k_lg_convert(const LgProb* __restrict__ probs, const int* status) {
   if (dpv_status(status)) return;
-  for (int t = blockIdx.x; t < tri2(T); t += gridDim.x) {
+  const LgProb P = probs[blockIdx.y];
+  for (int t = blockIdx.x; t < tri2(P.T); t += gridDim.x) {
     int ti = (int)((sqrtf(8.0f * t + 1.0f) - 1.0f) * 0.5f);
     while (tri2(ti + 1) <= t) ++ti;
     while (tri2(ti) > t) --ti;
     const int tj = t - tri2(ti);
-    const double2* src = reinterpret_cast<const double2*>(S + (size_t)t * TILE);
-    float2* dst = reinterpret_cast<float2*>(A + (size_t)t * TILE);
+    const double2* src = reinterpret_cast<const double2*>(P.S + (size_t)t * TILE);
+    float2* dst = reinterpret_cast<float2*>(P.A + (size_t)t * TILE);
     for (int q = threadIdx.x; q < TILE / 2; q += blockDim.x) {
       const int r = (2 * q) / NB, c = (2 * q) % NB;
       const double2 v = src[q];
-      const float si = sc[ti * NB + r];
-      dst[q] = make_float2(dpv_d2f_bits(v.x) * si * sc[tj * NB + c], dpv_d2f_bits(v.y) * si * sc[tj * NB + c + 1]);
+      const float si = P.sc[ti * NB + r];
+      dst[q] = make_float2(dpv_d2f_bits(v.x) * si * P.sc[tj * NB + c],
+                           dpv_d2f_bits(v.y) * si * P.sc[tj * NB + c + 1]);
     }
   }
 }
 
-// The factorisation task graph.  ver[tri(T)]: tile versions; ctr: task
-// counter; dsm: the SM of the critical-path CTA (+1).  CTA 0 runs the
-// diagonal steps in order and has its SM to itself (other CTAs there leave);
-// the other CTAs take panels and updates from the list.
-__global__ void __launch_bounds__(LG_THREADS) k_lg_factor(int T, const unsigned* __restrict__ tasks, int ntasks,
-                                                          float* A, float* Linv, float* D, float* invD, int* ver,
-                                                          int* ctr, int* dsm, int* status, long long timeout) {
+// The factorisation task graphs of all large systems.  CTA p < nsys runs the
+// critical chain of system p (other CTAs on its SM leave when there are SMs
+// to spare), then joins the workers; workers take the panels and updates of
+// all systems from one list (task: system << 32 | type << 30 | k << 20 | i << 10 | j).
+__global__ void __launch_bounds__(LG_THREADS, 2) k_lg_factor(const LgProb* __restrict__ probs, int nsys,
+                                                          const unsigned long long* __restrict__ tasks, int ntasks,
+                                                          int* ctr, int* dsm, int isolate, int* status,
+                                                          long long timeout) {
   extern __shared__ __align__(16) float lg_smem[];
   LgShared& sm = *reinterpret_cast<LgShared*>(lg_smem);
   if (threadIdx.x == 0) {
     unsigned smid;
     asm("mov.u32 %0, %%smid;" : "=r"(smid));
-    if (blockIdx.x == 0) {
-      st_release(dsm, (int)smid + 1);
-      sm.task = 0;
-    } else {
-      sm.task = wait_geq(dsm, 1, status, timeout) && ld_acquire(dsm) != (int)smid + 1 ? 1 : -1;
+    sm.task = 1;
+    if ((int)blockIdx.x < nsys) {
+      st_release(dsm + blockIdx.x, (int)smid + 1);
+    } else if (isolate) {
+      for (int c = 0; c < nsys && sm.task > 0; ++c)
+        if (!wait_geq(dsm + c, 1, status, timeout) || ld_acquire(dsm + c) == (int)smid + 1) sm.task = -1;
     }
   }
   __syncthreads();
   if (sm.task < 0) return;
-  if (blockIdx.x == 0) {
-    for (int k = 0; k < T; ++k) {
+  if ((int)blockIdx.x < nsys) {
+    const LgProb& P = probs[blockIdx.x];
+    for (int k = 0; k < P.T; ++k) {
       if (dpv_status(status)) return;
-      if (!task_diag_step(sm, A, Linv, D, invD, k, ver, status, timeout)) {
+      if (!task_diag_step(sm, P.A, P.Linv, P.D, P.invD, k, P.ver, status, timeout)) {
         if (threadIdx.x == 0 && !dpv_status(status)) dpv_set_status(status, DST_NOT_SPD);
         return;
       }
       __syncthreads();
       if (threadIdx.x == 0) {
         __threadfence();
-        st_release(ver + tri2(k) + k, k + 1);
+        st_release(P.ver + tri2(k) + k, k + 1);
       }
     }
-    return;
   }
   for (;;) {
     if (threadIdx.x == 0) sm.task = dpv_status(status) ? ntasks : atomicAdd(ctr, 1);
@@ -478,9 +493,12 @@ __global__ void __launch_bounds__(LG_THREADS) k_lg_factor(int T, const unsigned*
     const int t = sm.task;
     __syncthreads();
     if (t >= ntasks) return;
-    const unsigned w = tasks[t];
+    const unsigned long long w64 = tasks[t];
+    const LgProb& P = probs[(int)(w64 >> 32)];
+    const unsigned w = (unsigned)w64;
     const int type = (int)(w >> 30), k = (int)((w >> 20) & 1023u), i = (int)((w >> 10) & 1023u),
               j = (int)(w & 1023u);
+    int* ver = P.ver;
     if (threadIdx.x == 0) {
       bool ok;
       if (type == TASK_PANEL) {
@@ -495,10 +513,10 @@ __global__ void __launch_bounds__(LG_THREADS) k_lg_factor(int T, const unsigned*
     if (sm.bad) return;
     int tv;  // the tile written
     if (type == TASK_PANEL) {
-      task_panel(sm, A, Linv, invD, i, k);
+      task_panel(sm, P.A, P.Linv, P.invD, i, k);
       tv = tri2(i) + k;
     } else {
-      task_update(sm, A, D, i, j, k);
+      task_update(sm, P.A, P.D, i, j, k);
       tv = tri2(i) + j;
     }
     __syncthreads();
@@ -555,34 +573,35 @@ __device__ void tile_gemv(const TileRegs& t, const float* v, float* out, bool tr
   __syncthreads();
 }
 
-// Triangular solves + refinement.  flags[0..T): forward rows done (value =
-// sweep + 1), flags[T..2T): backward rows done; bar[2]: grid barrier.
-// xf: forward results (unit-lower solve), xb: backward results; xacc (FP64)
-// accumulates the sweeps; rhs: right-hand side of the current sweep.  CTA b
-// owns block rows i = b (mod grid), in both directions.
-__global__ void __launch_bounds__(LG_THREADS, 1) k_lg_solve(
-    int T, int n, const float* __restrict__ A, const float* __restrict__ Linv, const float* __restrict__ invD,
-    const double* __restrict__ S, const double* __restrict__ y, const float* __restrict__ sc, float* rhs, float* xf,
-    float* xb, double* xacc, double* __restrict__ dx, float* __restrict__ dxf, int sweeps, int* flags, int* bar,
-    int* conv, int* status, long long timeout) {
+// Triangular solves + refinement of all large systems.  Global row block r
+// (system rb_sys[r], block i = r - rb0) is owned by CTA r mod grid in both
+// directions; forward rows wait for the rows above them in their system, the
+// backward rows for the rows below; a grid barrier separates the sweeps, whose
+// residual rho = y - S x is formed in FP64 from the FP64 S.  The sweeps stop
+// once every system's correction is below 1e-7 of its solution.
+__global__ void __launch_bounds__(LG_THREADS, 1) k_lg_solve(const LgProb* __restrict__ probs, int nsys,
+                                                            const int* __restrict__ rb_sys, int R, int sweeps,
+                                                            int* bar, int* conv, int* status, long long timeout) {
   __shared__ float acc[NB], vj[NB], prod[NB];
   __shared__ float part[16][NB + 1];
   __shared__ int ok;
-  const int tid = threadIdx.x;
-  const int n_pad = T * NB;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   for (int sweep = 0; sweep < sweeps; ++sweep) {
     if (dpv_status(status)) return;
     // ---- forward: L u = rhs
-    for (int i = blockIdx.x; i < T; i += gridDim.x) {
-      if (tid < NB) acc[tid] = __ldcg(rhs + i * NB + tid);
+    for (int r = blockIdx.x; r < R; r += gridDim.x) {
+      const LgProb& P = probs[rb_sys[r]];
+      const int i = r - P.rb0, T = P.T;
+      if (tid < NB) acc[tid] = __ldcg(P.rhs + i * NB + tid);
       // the tiles do not depend on the flags: each is loaded while waiting for the previous row
-      TileRegs m = load_block(i > 0 ? A + (size_t)tri2(i) * TILE : Linv + (size_t)i * TILE);
+      TileRegs m = load_block(i > 0 ? P.A + (size_t)tri2(i) * TILE : P.Linv + (size_t)i * TILE);
       for (int j = 0; j < i; ++j) {
-        const TileRegs mn = load_block(j + 1 < i ? A + (size_t)(tri2(i) + j + 1) * TILE : Linv + (size_t)i * TILE);
-        if (tid == 0) ok = wait_geq(flags + j, sweep + 1, status, timeout) ? 1 : 0;
+        const TileRegs mn =
+            load_block(j + 1 < i ? P.A + (size_t)(tri2(i) + j + 1) * TILE : P.Linv + (size_t)i * TILE);
+        if (tid == 0) ok = wait_geq(P.flags + j, sweep + 1, status, timeout) ? 1 : 0;
         __syncthreads();
         if (!ok) return;
-        if (tid < NB) vj[tid] = __ldcg(xf + j * NB + tid);
+        if (tid < NB) vj[tid] = __ldcg(P.xf + j * NB + tid);
         __syncthreads();
         tile_gemv(m, vj, prod, false, part);
         if (tid < NB) acc[tid] -= prod[tid];
@@ -590,25 +609,29 @@ __global__ void __launch_bounds__(LG_THREADS, 1) k_lg_solve(
       }
       __syncthreads();
       tile_gemv(m, acc, prod, false, part);
-      if (tid < NB) xf[i * NB + tid] = prod[tid];
+      if (tid < NB) P.xf[i * NB + tid] = prod[tid];
       __syncthreads();
       if (tid == 0) {
         __threadfence();
-        st_release(flags + i, sweep + 1);
+        st_release(P.flags + i, sweep + 1);
       }
+      (void)T;
     }
     // ---- backward: L^T x = D^-1 u, rows descending
     int last = blockIdx.x;
-    while (last + (int)gridDim.x < T) last += gridDim.x;
-    for (int i = last; i >= 0; i -= gridDim.x) {
-      if (tid < NB) acc[tid] = __ldcg(xf + i * NB + tid) * __ldcg(invD + i * NB + tid);
-      TileRegs m = load_block(i + 1 < T ? A + (size_t)(tri2(T - 1) + i) * TILE : Linv + (size_t)i * TILE);
+    while (last + (int)gridDim.x < R) last += gridDim.x;
+    for (int r = last; r >= 0; r -= gridDim.x) {
+      const LgProb& P = probs[rb_sys[r]];
+      const int i = r - P.rb0, T = P.T;
+      if (tid < NB) acc[tid] = __ldcg(P.xf + i * NB + tid) * __ldcg(P.invD + i * NB + tid);
+      TileRegs m = load_block(i + 1 < T ? P.A + (size_t)(tri2(T - 1) + i) * TILE : P.Linv + (size_t)i * TILE);
       for (int j = T - 1; j > i; --j) {
-        const TileRegs mn = load_block(j - 1 > i ? A + (size_t)(tri2(j - 1) + i) * TILE : Linv + (size_t)i * TILE);
-        if (tid == 0) ok = wait_geq(flags + T + j, sweep + 1, status, timeout) ? 1 : 0;
+        const TileRegs mn =
+            load_block(j - 1 > i ? P.A + (size_t)(tri2(j - 1) + i) * TILE : P.Linv + (size_t)i * TILE);
+        if (tid == 0) ok = wait_geq(P.flags + T + j, sweep + 1, status, timeout) ? 1 : 0;
         __syncthreads();
         if (!ok) return;
-        if (tid < NB) vj[tid] = __ldcg(xb + j * NB + tid);
+        if (tid < NB) vj[tid] = __ldcg(P.xb + j * NB + tid);
         __syncthreads();
         tile_gemv(m, vj, prod, true, part);
         if (tid < NB) acc[tid] -= prod[tid];
@@ -616,88 +639,103 @@ __global__ void __launch_bounds__(LG_THREADS, 1) k_lg_solve(
       }
       __syncthreads();
       tile_gemv(m, acc, prod, true, part);
-      if (tid < NB) xb[i * NB + tid] = prod[tid];
+      if (tid < NB) P.xb[i * NB + tid] = prod[tid];
       __syncthreads();
       if (tid == 0) {
         __threadfence();
-        st_release(flags + T + i, sweep + 1);
+        st_release(P.flags + T + i, sweep + 1);
       }
     }
     if (!grid_barrier(bar, gridDim.x, status, timeout)) return;
-    // ---- accumulate the correction, then the next residual
-    const int gt = blockIdx.x * LG_THREADS + tid, gs = gridDim.x * LG_THREADS;
-    // (the solve ran on the equilibrated system: x = s z); stop once the
-    // correction is below 1e-7 of the solution
-    float cmax = 0.f, xmax = 0.f;
-    for (int q = gt; q < n_pad; q += gs) {
-      const double c = dpv_f2d_bits(__ldcg(xb + q)) * dpv_f2d_bits(sc[q]);
-      const double x = (sweep == 0 ? 0.0 : xacc[q]) + c;
-      xacc[q] = x;
-      cmax = fmaxf(cmax, fabsf(dpv_d2f_bits(c)));
-      xmax = fmaxf(xmax, fabsf(dpv_d2f_bits(x)));
-    }
+    // ---- accumulate x += s z per row block; per-system convergence maxima
+    for (int r = blockIdx.x; r < R; r += gridDim.x) {
+      const int p = rb_sys[r];
+      const LgProb& P = probs[p];
+      const int i = r - P.rb0;
+      float cmax = 0.f, xmax = 0.f;
+      if (tid < NB) {
+        const int q = i * NB + tid;
+        const double c = dpv_f2d_bits(__ldcg(P.xb + q)) * dpv_f2d_bits(P.sc[q]);
+        const double x = (sweep == 0 ? 0.0 : P.xacc[q]) + c;
+        P.xacc[q] = x;
+        cmax = fabsf(dpv_d2f_bits(c));
+        xmax = fabsf(dpv_d2f_bits(x));
+      }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      cmax = fmaxf(cmax, __shfl_xor_sync(0xffffffffu, cmax, o));
-      xmax = fmaxf(xmax, __shfl_xor_sync(0xffffffffu, xmax, o));
-    }
-    if ((tid & 31) == 0) {  // non-negative floats order like their bit patterns
-      atomicMax(conv + 2 * sweep, __float_as_int(cmax));
-      atomicMax(conv + 2 * sweep + 1, __float_as_int(xmax));
+      for (int o = 16; o > 0; o >>= 1) {
+        cmax = fmaxf(cmax, __shfl_xor_sync(0xffffffffu, cmax, o));
+        xmax = fmaxf(xmax, __shfl_xor_sync(0xffffffffu, xmax, o));
+      }
+      if (lane == 0 && wid < 2) {  // non-negative floats order like their bit patterns
+        atomicMax(conv + 2 * (sweep * nsys + p), __float_as_int(cmax));
+        atomicMax(conv + 2 * (sweep * nsys + p) + 1, __float_as_int(xmax));
+      }
     }
     if (sweep + 1 == sweeps) break;
     if (!grid_barrier(bar, gridDim.x, status, timeout)) return;
-    if (sweep > 0 && __int_as_float(ld_acquire(conv + 2 * sweep)) <= 1e-7f * __int_as_float(ld_acquire(conv + 2 * sweep + 1)))
-      break;
-    // rho = y - S xacc in FP64, one warp per row
-    const int lane = tid & 31, gw = gt >> 5, nw = gs >> 5;
-    for (int row = gw; row < n_pad; row += nw) {
+    if (sweep > 0) {
+      bool done = true;
+      for (int p = 0; p < nsys && done; ++p)
+        done = __int_as_float(ld_acquire(conv + 2 * (sweep * nsys + p))) <=
+               1e-7f * __int_as_float(ld_acquire(conv + 2 * (sweep * nsys + p) + 1));
+      if (done) break;  // the same decision in every CTA
+    }
+    // rho = s (y - S xacc) in FP64, one warp per row of the concatenated systems
+    const int gw = (blockIdx.x * LG_THREADS + tid) >> 5, nw = (gridDim.x * LG_THREADS) >> 5;
+    for (int g = gw; g < R * NB; g += nw) {
+      const LgProb& P = probs[rb_sys[g / NB]];
+      const int row = (g / NB - P.rb0) * NB + (g % NB);
       double sacc = 0.0;
-      if (row < n)
-        for (int c = lane; c < n; c += 32)
-          sacc += S[c <= row ? dpv_s_index(row, c, NB) : dpv_s_index(c, row, NB)] * __ldcg(xacc + c);
+      if (row < P.n)
+        for (int c = lane; c < P.n; c += 32)
+          sacc += P.S[c <= row ? dpv_s_index(row, c, NB) : dpv_s_index(c, row, NB)] * __ldcg(P.xacc + c);
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, o);
-      if (lane == 0) rhs[row] = row < n ? dpv_d2f_bits(y[row] - sacc) * sc[row] : 0.f;
+      if (lane == 0) P.rhs[row] = row < P.n ? dpv_d2f_bits(P.y[row] - sacc) * P.sc[row] : 0.f;
     }
     if (!grid_barrier(bar, gridDim.x, status, timeout)) return;
   }
-  const int gt = blockIdx.x * LG_THREADS + tid, gs = gridDim.x * LG_THREADS;
-  for (int q = gt; q < n; q += gs) {
-    const double v = __ldcg(xacc + q);
-    dx[q] = v;
-    dxf[q] = dpv_d2f_bits(v);
+  // output
+  for (int r = blockIdx.x; r < R; r += gridDim.x) {
+    const LgProb& P = probs[rb_sys[r]];
+    const int q = (r - P.rb0) * NB + tid;
+    if (tid < NB && q < P.n) {
+      const double v = __ldcg(P.xacc + q);
+      P.dx[q] = v;
+      P.dxf[q] = dpv_d2f_bits(v);
+    }
   }
 }
 
-__global__ void k_lg_init_rhs(int n, int n_pad, const double* __restrict__ y, const float* __restrict__ sc,
-                              float* __restrict__ rhs, const int* status) {
-  if (dpv_status(status)) return;
-  const int q = blockIdx.x * blockDim.x + threadIdx.x;
-  if (q < n_pad) rhs[q] = q < n ? dpv_d2f_bits(y[q]) * sc[q] : 0.f;
-}
-
-// Worker task list in dependency order.  The critical-path CTA does DIAG(k),
-// PANEL(k, k-1) and UPDATE(k, k, k-1); the list holds every other panel and
-// update: step k+1's column update and panels come before the bulk of step
-// k's trailing update, whose columns run left to right.
-std::vector<unsigned> build_tasks(int T) {
-  std::vector<unsigned> v;
-  v.reserve((size_t)T * T * T / 6 + (size_t)T * T + 16);
-  for (int i = 2; i < T; ++i) v.push_back(pack_task(TASK_PANEL, 0, i, 0));
-  for (int k = 0; k + 1 < T; ++k) {
-    for (int i = k + 2; i < T; ++i) v.push_back(pack_task(TASK_UPDATE, k, i, k + 1));
-    for (int i = k + 3; i < T; ++i) v.push_back(pack_task(TASK_PANEL, k + 1, i, k + 1));
-    for (int j = k + 2; j < T; ++j)
-      for (int i = j; i < T; ++i) v.push_back(pack_task(TASK_UPDATE, k, i, j));
-  }
+// Task list of several systems, in dependency order within each system and
+// interleaved by step across systems (largest first), so that every critical
+// chain advances together.  Per system: step k+1's column update and panels
+// come before the bulk of step k's trailing update, whose columns run left to
+// right; the critical CTA does DIAG(k), PANEL(k, k-1) and UPDATE(k, k, k-1).
+std::vector<unsigned long long> build_tasks(const std::vector<int>& Ts) {
+  std::vector<unsigned long long> v;
+  auto put = [&](int p, int type, int k, int i, int j) {
+    v.push_back(((unsigned long long)p << 32) | pack_task(type, k, i, j));
+  };
+  int maxT = 0;
+  for (int T : Ts) maxT = std::max(maxT, T);
+  for (int p = 0; p < (int)Ts.size(); ++p)
+    for (int i = 2; i < Ts[p]; ++i) put(p, TASK_PANEL, 0, i, 0);
+  for (int k = 0; k + 1 < maxT; ++k)
+    for (int p = 0; p < (int)Ts.size(); ++p) {
+      const int T = Ts[p];
+      if (k + 1 >= T) continue;
+      for (int i = k + 2; i < T; ++i) put(p, TASK_UPDATE, k, i, k + 1);
+      for (int i = k + 3; i < T; ++i) put(p, TASK_PANEL, k + 1, i, k + 1);
+      for (int j = k + 2; j < T; ++j)
+        for (int i = j; i < T; ++i) put(p, TASK_UPDATE, k, i, j);
+    }
   return v;
 }
 
 struct TaskCache {
   std::mutex mu;
-  std::map<std::pair<int, int>, unsigned*> lists;  // (device, T) -> device task list
-  std::map<std::pair<int, int>, int> counts;
+  std::map<std::pair<int, std::vector<int>>, std::pair<unsigned long long*, int>> lists;  // (device, Ts)
 };
 TaskCache& task_cache() {
   static TaskCache c;
@@ -721,68 +759,107 @@ long long dpv_large_scratch_floats(int n_pad) {
   return (long long)tri2((int)T) * TILE + T * TILE + 6LL * n_pad;
 }
 
-ba_status_t dpv_solve_blocked(ba_handle_t h, const SysDesc& sd, int refine) {
+// Solve every large system (h->large_sys) with one factorisation launch and
+// one solve launch.  refine: the most refinement sweeps allowed.
+ba_status_t dpv_solve_large(ba_handle_t h, int refine) {
   Workspace* ws = h->ws;
-  const int n = sd.n, n_pad = sd.n_pad;
-  if (sd.TS != NB || n_pad % NB) return dpv_fail(h, BA_ERR_UNSUPPORTED, "large solver needs 64-row tiles");
-  const int T = n_pad / NB;
-  if (T > LG_MAX_T) return dpv_fail(h, BA_ERR_UNSUPPORTED, "pose system above 65472 unknowns");
-  // the task list of this size, built once per device
-  unsigned* tasks = nullptr;
+  const int nsys = (int)h->large_sys.size();
+  if (nsys == 0) return BA_OK;
+  constexpr int MAX_SWEEPS = 16;
+  refine = std::min(refine, MAX_SWEEPS - 1);
+  std::vector<int> Ts(nsys);
+  std::vector<LgProb> pr(nsys);
+  std::vector<int> rb_sys;
+  long long foff = 0, soff_sync = 0;
+  for (int p = 0; p < nsys; ++p) {
+    const SysDesc& sd = h->sys[h->large_sys[p]];
+    if (sd.TS != NB || sd.n_pad % NB) return dpv_fail(h, BA_ERR_UNSUPPORTED, "large solver needs 64-row tiles");
+    const int T = sd.n_pad / NB;
+    if (T > LG_MAX_T) return dpv_fail(h, BA_ERR_UNSUPPORTED, "pose system above 65472 unknowns");
+    Ts[p] = T;
+    LgProb& P = pr[p];
+    float* base = ws->L.p + foff;
+    P.A = base;
+    P.Linv = P.A + (size_t)tri2(T) * TILE;
+    P.D = P.Linv + (size_t)T * TILE;
+    P.invD = P.D + sd.n_pad;
+    P.rhs = P.invD + sd.n_pad;
+    P.xf = P.rhs + sd.n_pad;
+    P.xb = P.xf + sd.n_pad;
+    P.sc = P.xb + sd.n_pad;
+    foff += dpv_large_scratch_floats(sd.n_pad);
+    P.S = ws->S.p + sd.soff;
+    P.y = ws->y.p + sd.voff;
+    P.xacc = ws->r64.p + sd.voff;
+    P.dx = ws->dx.p + sd.voff;
+    P.dxf = ws->tmpv.p + sd.voff;
+    P.T = T;
+    P.n = sd.n;
+    P.n_pad = sd.n_pad;
+    P.rb0 = (int)rb_sys.size();
+    for (int i = 0; i < T; ++i) rb_sys.push_back(p);
+    soff_sync += tri2(T) + 2LL * T;
+  }
+  if (foff > ws->L.cap) return dpv_fail(h, BA_ERR_STATE, "large solver scratch");
+  // the task list of this set of sizes, built once per device
+  unsigned long long* tasks = nullptr;
   int ntasks = 0;
   {
     TaskCache& tc = task_cache();
     std::lock_guard<std::mutex> lk(tc.mu);
-    auto key = std::make_pair(h->device, T);
+    auto key = std::make_pair(h->device, Ts);
     auto it = tc.lists.find(key);
     if (it == tc.lists.end()) {
-      std::vector<unsigned> v = build_tasks(T);
-      unsigned* d = nullptr;
-      if (cudaMalloc(&d, sizeof(unsigned) * v.size()) != cudaSuccess) {
+      std::vector<unsigned long long> v = build_tasks(Ts);
+      unsigned long long* d = nullptr;
+      if (cudaMalloc(&d, sizeof(unsigned long long) * std::max<size_t>(v.size(), 1)) != cudaSuccess) {
         cudaGetLastError();
         return dpv_fail(h, BA_ERR_OOM, "large solver task list");
       }
-      DPV_CUDA(h, cudaMemcpy(d, v.data(), sizeof(unsigned) * v.size(), cudaMemcpyHostToDevice));
-      tc.lists[key] = d;
-      tc.counts[key] = (int)v.size();
+      if (!v.empty()) DPV_CUDA(h, cudaMemcpy(d, v.data(), sizeof(unsigned long long) * v.size(), cudaMemcpyHostToDevice));
+      it = tc.lists.emplace(key, std::make_pair(d, (int)v.size())).first;
     }
-    tasks = tc.lists[key];
-    ntasks = tc.counts[key];
+    tasks = it->second.first;
+    ntasks = it->second.second;
   }
+  // sync words: per system versions and row flags; task counter, barrier,
+  // critical SMs, convergence maxima per (sweep, system)
+  const long long nsync = soff_sync + 4 + nsys + 2LL * MAX_SWEEPS * nsys;
+  const int R = (int)rb_sys.size();
   ba_status_t s;
-  constexpr int MAX_SWEEPS = 16;
-  refine = std::min(refine, MAX_SWEEPS - 1);
-  // versions, row flags, counter, barrier, critical SM, convergence maxima per sweep
-  const long long nsync = tri2(T) + 2LL * T + 8 + 2 * MAX_SWEEPS;
-  if ((s = dpv_grow(h, ws->lg_sync, nsync, "large solver sync"))) return s;
-  float* A = ws->L.p;
-  float* Linv = A + (size_t)tri2(T) * TILE;
-  float* D = Linv + (size_t)T * TILE;
-  float* invD = D + n_pad;
-  float* rhs = invD + n_pad;
-  float* xf = rhs + n_pad;
-  float* xb = xf + n_pad;
-  float* sc = xb + n_pad;
-  int* ver = ws->lg_sync.p;
-  int* flags = ver + tri2(T);
-  int* ctr = flags + 2 * T;
+  if ((s = dpv_grow(h, ws->lg_sync, nsync, "large solver sync")) ||
+      (s = dpv_grow(h, ws->lg_prob, (long long)nsys * sizeof(LgProb) / sizeof(long long) + 1, "large systems")) ||
+      (s = dpv_grow(h, ws->lg_rb, R, "row blocks")))
+    return s;
+  int* sync = ws->lg_sync.p;
+  for (int p = 0, o = 0; p < nsys; ++p) {
+    pr[p].ver = sync + o;
+    pr[p].flags = sync + o + tri2(Ts[p]);
+    o += tri2(Ts[p]) + 2 * Ts[p];
+  }
+  int* ctr = sync + soff_sync;
   int* bar = ctr + 1;   // two ints
-  int* dsm = bar + 2;
-  int* conv = dsm + 2;  // [2 * MAX_SWEEPS]
+  int* dsm = bar + 3;   // [nsys]
+  int* conv = dsm + nsys;  // [2 MAX_SWEEPS nsys]
   int* status = ws->status;
   cudaStream_t st = h->stream;
-  DPV_CUDA(h, cudaMemsetAsync(ver, 0, sizeof(int) * nsync, st));
-  const double* Sb = ws->S.p + sd.soff;
-  k_lg_scale<<<(n_pad + 255) / 256, 256, 0, st>>>(Sb, n, n_pad, sc, status);
+  const LgProb* dprobs = reinterpret_cast<const LgProb*>(ws->lg_prob.p);
+  DPV_CUDA(h, cudaMemsetAsync(sync, 0, sizeof(int) * nsync, st));
+  DPV_CUDA(h, cudaMemcpyAsync(ws->lg_prob.p, pr.data(), sizeof(LgProb) * nsys, cudaMemcpyHostToDevice, st));
+  DPV_CUDA(h, cudaMemcpyAsync(ws->lg_rb.p, rb_sys.data(), sizeof(int) * R, cudaMemcpyHostToDevice, st));
+  int maxpad = 0, maxtiles = 0;
+  for (int T : Ts) {
+    maxpad = std::max(maxpad, T * NB);
+    maxtiles = std::max(maxtiles, tri2(T));
+  }
+  k_lg_scale<<<dim3((maxpad + 255) / 256, nsys), 256, 0, st>>>(dprobs, status);
   ++h->launches;
-  k_lg_convert<<<std::min(tri2(T), 8 * h->num_sms), 256, 0, st>>>(Sb, sc, A, T, status);
-  ++h->launches;
-  k_lg_init_rhs<<<(n_pad + 255) / 256, 256, 0, st>>>(n, n_pad, ws->y.p + sd.voff, sc, rhs, status);
+  k_lg_convert<<<dim3(std::min(maxtiles, 8 * h->num_sms), nsys), 256, 0, st>>>(dprobs, status);
   ++h->launches;
   long long timeout = h->opt.timeout_cycles;
   {
-    // at most two CTAs per SM: the single-warp pivot chain of DIAG shares its
-    // SM with fewer update CTAs
+    // at most two CTAs per SM; the critical CTAs get their SMs to themselves
+    // while at least half the SMs remain for the workers
     const size_t smem = sizeof(LgShared);
     static bool attr = false;
     if (!attr) {
@@ -790,28 +867,23 @@ ba_status_t dpv_solve_blocked(ba_handle_t h, const SysDesc& sd, int refine) {
       attr = true;
     }
     const int grid = std::min(co_resident(h, (const void*)k_lg_factor, smem), 2 * h->num_sms);
-    if (grid <= 1) return dpv_fail(h, BA_ERR_CUDA, "large solver occupancy");
-    void* args[] = {(void*)&T,   (void*)&tasks, (void*)&ntasks, (void*)&A,      (void*)&Linv,    (void*)&D,
-                    (void*)&invD, (void*)&ver,  (void*)&ctr,    (void*)&dsm,    (void*)&status, (void*)&timeout};
+    if (grid <= nsys) return dpv_fail(h, BA_ERR_UNSUPPORTED, "more large systems than the solver's resident CTAs");
+    int isolate = 2 * nsys <= h->num_sms ? 1 : 0;
+    int nsys_ = nsys;
+    void* args[] = {(void*)&dprobs, (void*)&nsys_, (void*)&tasks,  (void*)&ntasks,
+                    (void*)&ctr,    (void*)&dsm,   (void*)&isolate, (void*)&status, (void*)&timeout};
     DPV_CUDA(h, cudaLaunchCooperativeKernel((const void*)k_lg_factor, dim3(grid), dim3(LG_THREADS), args, smem, st));
     ++h->launches;
   }
   {
     const int maxg = co_resident(h, (const void*)k_lg_solve);
-    const int grid = std::min(T, maxg);
+    const int grid = std::min(R, maxg);
     if (grid <= 0) return dpv_fail(h, BA_ERR_CUDA, "large solver occupancy");
-    const double* S = Sb;
-    const double* y = ws->y.p + sd.voff;
-    double* xacc = ws->r64.p + sd.voff;
-    double* dx = ws->dx.p + sd.voff;
-    float* dxf = ws->tmpv.p + sd.voff;
     int sweeps = refine + 1;
-    int n_ = n;
-    const float* scc = sc;
-    void* args[] = {(void*)&T,   (void*)&n_,   (void*)&A,      (void*)&Linv,  (void*)&invD, (void*)&S,
-                    (void*)&y,   (void*)&scc,  (void*)&rhs,    (void*)&xf,    (void*)&xb,   (void*)&xacc,
-                    (void*)&dx,  (void*)&dxf,  (void*)&sweeps, (void*)&flags, (void*)&bar,  (void*)&conv,
-                    (void*)&status, (void*)&timeout};
+    int nsys_ = nsys, R_ = R;
+    const int* rb = ws->lg_rb.p;
+    void* args[] = {(void*)&dprobs, (void*)&nsys_, (void*)&rb,     (void*)&R_,      (void*)&sweeps,
+                    (void*)&bar,    (void*)&conv,  (void*)&status, (void*)&timeout};
     DPV_CUDA(h, cudaLaunchCooperativeKernel((const void*)k_lg_solve, dim3(grid), dim3(LG_THREADS), args, 0, st));
     ++h->launches;
   }

@@ -426,7 +426,7 @@ ba_status_t launch_small(ba_handle_t h, int count, const int* list, int refine32
 
 }  // namespace
 
-ba_status_t dpv_solve_blocked(ba_handle_t h, const SysDesc& sd, int refine);
+ba_status_t dpv_solve_large(ba_handle_t h, int refine);
 
 // Solve every pose system S_b dxi_b = y_b: one launch of the one-CTA solver per
 // block count (one CTA per system), then the large systems.
@@ -457,10 +457,8 @@ ba_status_t dpv_solve(ba_handle_t h, int* retracted, int reset_system) {
     if (s) return s;
     off += cnt;
   }
-  // large systems: FP64 refinement sweeps until converged (at least four allowed)
-  for (int b : h->large_sys)
-    if ((s = dpv_solve_blocked(h, h->sys[b], std::max(4, refine64)))) return s;
-  return BA_OK;
+  // large systems, all together: FP64 refinement sweeps until converged (at least four allowed)
+  return dpv_solve_large(h, std::max(4, refine64));
 }
 
 // Launch the one-CTA solver on a system the caller has already laid out as one

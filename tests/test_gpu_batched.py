@@ -62,6 +62,19 @@ def test_batched_step_matches_oracle_per_problem(precision):
         assert rot < TOL and tr < TOL and dep < TOL, (b, frames[b], precision, rot, tr, dep)
 
 
+def test_batched_several_large_systems():
+    # three systems above 256 unknowns factored in one launch, beside small ones
+    frames = [46, 70, 12, 52]
+    probs = problems(frames, seed=5)
+    T, offs, ba = run_batched(probs, 1, precision="mixed")
+    for b, sc in enumerate(probs):
+        want = oracle.gn_steps(sc, iters=1)[0]
+        poses, d = split(T, offs, b)
+        rot, tr = pose_error(poses, want[0])
+        dep = depth_error(d, want[1])
+        assert rot < TOL and tr < TOL and dep < TOL, (b, frames[b], rot, tr, dep)
+
+
 def test_batched_equals_separate_handles():
     frames = [9, 27, 46, 15]
     probs = problems(frames, seed=2, iters=2)
