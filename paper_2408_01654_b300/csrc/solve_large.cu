@@ -10,7 +10,12 @@
 // that runs a task graph over the tiles:
 //   DIAG(k)        factor tile (k,k): unit L_kk, D_k, and the inverse L_kk^-1
 //   PANEL(i,k)     L_ik = A_ik L_kk^-T D_k^-1                      (i > k)
-//   UPDATE(i,j,k)  A_ij -= (L_ik D_k) L_jk^T                       (k < j <= i)
+//                  and G_ik = L_ik D_k^1/2, stored pre-split for the tensor
+//                  cores (TF32 part + FP32 rest, core-matrix layout)
+//   UPDATE(i,j,k)  A_ij -= G_ik G_jk^T                             (k < j <= i)
+//                  (workers: two row tiles at a time, one 128 x 64 x 64
+//                  tcgen05 TF32 product with a three-pass split whose
+//                  operands arrive by bulk copies)
 // Each tile carries a version (the number of updates applied, +1 once it is
 // final).  The chain DIAG(k) -> PANEL(k+1,k) -> UPDATE(k+1,k+1,k) -> DIAG(k+1)
 // is the critical path, so one CTA, alone on its SM, runs it step after step
@@ -26,6 +31,7 @@
 // residual rho = y - S x is formed in FP64 from the FP64 S, until the
 // correction is below 1e-7 of the solution.
 #include "internal.cuh"
+#include "tcgen05.cuh"
 
 #include <map>
 #include <mutex>
@@ -156,6 +162,25 @@ __device__ __forceinline__ void gemm_nt(const float* X, const float* Y, const fl
   }
 }
 
+// G_ik = L_ik diag(sq) (L_ik in shared memory, padded rows) split into its
+// TF32 part and the FP32 rest, each written as one 16 KB operand in the
+// K-major core-matrix layout of the tensor cores: 16-byte slot q holds row
+// 8 (q >> 7) + (q & 7), columns 4 ((q >> 3) & 15) .. +3.  Coalesced stores.
+__device__ __forceinline__ void store_g(const float* Ls, const float* sq, float* g) {
+#pragma unroll
+  for (int u = 0; u < TILE / 4 / LG_THREADS; ++u) {
+    const int q = threadIdx.x + u * LG_THREADS;
+    const int row = ((q >> 7) << 3) | (q & 7), k0 = ((q >> 3) & 15) << 2;
+    float h[4], l[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) tc_split(Ls[row * LDS + k0 + e] * sq[k0 + e], h[e], l[e]);
+    reinterpret_cast<float4*>(g)[q] = make_float4(h[0], h[1], h[2], h[3]);
+    reinterpret_cast<float4*>(g + TILE)[q] = make_float4(l[0], l[1], l[2], l[3]);
+  }
+  tc_fence_global();  // the bulk copies that read G run in the async proxy
+}
+__device__ __forceinline__ float* g_ptr(float* G, int i, int k) { return G + (size_t)(tri2(i) + k) * 2 * TILE; }
+
 // ---------------------------------------------------------------------------
 // the tasks
 // ---------------------------------------------------------------------------
@@ -170,6 +195,7 @@ struct LgShared {
   float dd[NB];
   float dprev[NB];  // the previous diagonal step's D and D^-1 (critical-path CTA)
   float iprev[NB];
+  float sq[NB];     // D_k^1/2 of the panel being written
   int task;
   int bad;
 };
@@ -306,7 +332,7 @@ __device__ bool factor_diag(LgShared& sm, float* A, float* Linv, float* D, float
 // Critical-path step k (one dedicated CTA, in order): for k > 0 first the
 // panel of tile (k, k-1) and its update of tile (k, k), from the inverse and D
 // of step k-1 kept in shared memory; then the factorisation of tile (k, k).
-__device__ bool task_diag_step(LgShared& sm, float* A, float* Linv, float* D, float* invD, int k, int* ver,
+__device__ bool task_diag_step(LgShared& sm, float* A, float* G, float* Linv, float* D, float* invD, int k, int* ver,
                                int* status, long long timeout) {
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   if (k > 0) {
@@ -328,7 +354,12 @@ __device__ bool task_diag_step(LgShared& sm, float* A, float* Linv, float* D, fl
         sm.Z[r * LDS + c] = l;
         tp[r * NB + c] = l;
       }
-    if (tid < NB) sm.dprev[tid] = -sm.dprev[tid];
+    if (tid < NB) {
+      sm.sq[tid] = sqrtf(sm.dprev[tid]);
+      sm.dprev[tid] = -sm.dprev[tid];
+    }
+    __syncthreads();
+    store_g(sm.Z, sm.sq, g_ptr(G, k, k - 1));
     __syncthreads();
     if (tid == 0) {
       __threadfence();
@@ -360,45 +391,145 @@ __device__ bool task_diag_step(LgShared& sm, float* A, float* Linv, float* D, fl
   return factor_diag(sm, A, Linv, D, invD, k);
 }
 
-// PANEL(i,k): L_ik = A_ik L_kk^-T D_k^-1
-__device__ void task_panel(LgShared& sm, float* A, const float* Linv, const float* invD, int i, int k) {
+// PANEL(i,k): L_ik = A_ik L_kk^-T D_k^-1, and the operand G_ik = L_ik D_k^1/2
+__device__ void task_panel(LgShared& sm, float* A, float* G, const float* Linv, const float* D, const float* invD,
+                           int i, int k) {
   float* t = tile_ptr(A, i, k);
-  if (threadIdx.x < NB) sm.invd[threadIdx.x] = __ldcg(invD + k * NB + threadIdx.x);
+  if (threadIdx.x < NB) {
+    sm.invd[threadIdx.x] = __ldcg(invD + k * NB + threadIdx.x);
+    sm.sq[threadIdx.x] = sqrtf(__ldcg(D + k * NB + threadIdx.x));
+  }
   load_tiles2(sm.X, t, sm.Y, Linv + (size_t)k * TILE);
   __syncthreads();
   float acc[4][4] = {};
   gemm_nt(sm.X, sm.Y, nullptr, acc);
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  __syncthreads();  // every thread is done reading sm.X
 #pragma unroll
   for (int a = 0; a < 4; ++a)
 #pragma unroll
     for (int b = 0; b < 4; ++b) {
       const int r = ty + 16 * a, c = tx + 16 * b;
-      t[r * NB + c] = acc[a][b] * sm.invd[c];
+      const float l = acc[a][b] * sm.invd[c];
+      t[r * NB + c] = l;
+      sm.X[r * LDS + c] = l;
     }
+  __syncthreads();
+  store_g(sm.X, sm.sq, g_ptr(G, i, k));
 }
 
-// UPDATE(i,j,k): A_ij -= (L_ik D_k) L_jk^T
-__device__ void task_update(LgShared& sm, float* A, const float* D, int i, int j, int k) {
-  float* t = tile_ptr(A, i, j);
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  // this thread's outputs of the target tile, read before the operands land
-  float acc[4][4];
-#pragma unroll
-  for (int a = 0; a < 4; ++a)
-#pragma unroll
-    for (int b = 0; b < 4; ++b) acc[a][b] = __ldcg(t + (ty + 16 * a) * NB + tx + 16 * b);
-  if (threadIdx.x < NB) sm.dd[threadIdx.x] = -__ldcg(D + k * NB + threadIdx.x);
-  load_tiles2(sm.X, tile_ptr(A, i, k), sm.Y, tile_ptr(A, j, k));
-  __syncthreads();
-  gemm_nt(sm.X, sm.Y, sm.dd, acc);  // acc = C - (L_ik D_k) L_jk^T
-#pragma unroll
-  for (int a = 0; a < 4; ++a)
-#pragma unroll
-    for (int b = 0; b < 4; ++b) {
-      const int r = ty + 16 * a, c = tx + 16 * b;
-      if (i != j || c <= r) t[r * NB + c] = acc[a][b];
+
+// UPDATE of a pair of row tiles on the tensor cores: tiles (i, j) and
+// (i+1, j) (the second only when i+1 < T) at step k,
+//   [A_ij; A_i+1,j] -= [G_ik; G_i+1,k] G_jk^T,
+// as one 128 x 64 x 64 tcgen05 TF32 product with the three-pass split
+// (hi*hi + hi*lo + lo*hi, about FP32 accuracy) accumulated in tensor memory.
+// The operands, written pre-split by the panels, arrive by bulk copies into
+// shared memory (aliasing the other tasks' shared memory) while the threads
+// fetch the tiles being updated; one thread issues the 24 MMAs.  With one
+// row tile, rows 64..127 of A hold stale data whose products are not read.
+constexpr uint32_t TC_OP_BYTES = TILE * 4;  // one split part of one tile (16 KB)
+constexpr int TC_SMEM = 6 * TC_OP_BYTES;    // A hi, A lo (128 rows each), B hi, B lo
+constexpr uint32_t TC_COLS = 64;            // tensor-memory columns per CTA (the 64 output columns)
+
+struct TcState {
+  uint64_t bar_ld;    // the operand copies
+  uint64_t bar_mma;   // the MMAs
+  uint32_t tmem;
+  uint32_t ph_ld, ph_mma;
+  int bad;            // 1: the copies, 2: the MMAs did not complete in time
+};
+
+__device__ bool task_update_tc(unsigned char* tcbuf, TcState& ts, float* A, const float* G, int T, int i, int j,
+                               int k, long long timeout) {
+  const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
+  const bool two = i + 1 < T;
+  unsigned char* a_hi = tcbuf;
+  unsigned char* a_lo = a_hi + 2 * TC_OP_BYTES;
+  unsigned char* b_hi = a_lo + 2 * TC_OP_BYTES;
+  unsigned char* b_lo = b_hi + TC_OP_BYTES;
+  if (tid == 0) {
+    tc_fence_global();  // G was written by other CTAs through the generic proxy
+    tc_fence_smem();    // this CTA's earlier generic accesses of the buffer are ordered before the copies
+    tc_mbar_expect_tx(&ts.bar_ld, (two ? 6u : 4u) * TC_OP_BYTES);
+    const float* gi = g_ptr(const_cast<float*>(G), i, k);
+    const float* gj = g_ptr(const_cast<float*>(G), j, k);
+    tc_bulk_g2s(a_hi, gi, TC_OP_BYTES, &ts.bar_ld);
+    tc_bulk_g2s(a_lo, gi + TILE, TC_OP_BYTES, &ts.bar_ld);
+    if (two) {
+      const float* g1 = g_ptr(const_cast<float*>(G), i + 1, k);
+      tc_bulk_g2s(a_hi + TC_OP_BYTES, g1, TC_OP_BYTES, &ts.bar_ld);
+      tc_bulk_g2s(a_lo + TC_OP_BYTES, g1 + TILE, TC_OP_BYTES, &ts.bar_ld);
     }
+    tc_bulk_g2s(b_hi, gj, TC_OP_BYTES, &ts.bar_ld);
+    tc_bulk_g2s(b_lo, gj + TILE, TC_OP_BYTES, &ts.bar_ld);
+  }
+  // this thread's 32 outputs (row r, columns c0..c0+31; see the epilogue), read meanwhile
+  const int r = 32 * (wid & 3) + lane, c0 = 32 * (wid >> 2);
+  const bool mine = r < 64 || two;
+  float* ct = tile_ptr(A, i + (r >> 6), j) + (r & 63) * NB + c0;
+  float4 cv[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q)
+    cv[q] = mine ? __ldcg(reinterpret_cast<const float4*>(ct) + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+  if (tid == 0) {
+    if (!tc_mbar_wait(&ts.bar_ld, ts.ph_ld, timeout)) {
+      ts.bad = 1;
+    } else {
+      ts.ph_ld ^= 1u;
+      tc_fence_after_sync();
+      constexpr uint32_t idesc = tc_idesc_tf32(128, NB);
+      constexpr uint32_t LBO = 128, SBO = (NB / 4) * 128;
+      const uint32_t ah0 = tc_smem_addr(a_hi), al0 = tc_smem_addr(a_lo), bh0 = tc_smem_addr(b_hi),
+                     bl0 = tc_smem_addr(b_lo);
+#pragma unroll
+      for (int st = 0; st < NB / 8; ++st) {
+        const uint32_t off = st * 256;  // K = 8 TF32 values = two core matrices along K
+        const uint64_t ah = tc_desc(ah0 + off, LBO, SBO), al = tc_desc(al0 + off, LBO, SBO);
+        const uint64_t bh = tc_desc(bh0 + off, LBO, SBO), bl = tc_desc(bl0 + off, LBO, SBO);
+        tc_mma_tf32(ts.tmem, ah, bh, idesc, st > 0);
+        tc_mma_tf32(ts.tmem, ah, bl, idesc, 1);
+        tc_mma_tf32(ts.tmem, al, bh, idesc, 1);
+      }
+      tc_commit(&ts.bar_mma);
+      if (tc_mbar_wait(&ts.bar_mma, ts.ph_mma, timeout))
+        ts.ph_mma ^= 1u;
+      else
+        ts.bad = 2;
+    }
+  }
+  __syncthreads();
+  if (ts.bad) return false;
+  tc_fence_after_sync();
+  // epilogue: warp w holds rows 32 (w % 4) + lane, columns 32 (w / 4) .. + 31
+  {
+    float d[32];
+    tc_ld32(ts.tmem + ((uint32_t)(32 * (wid & 3)) << 16) + (uint32_t)c0, d);
+    if (mine) {
+      float* t = ct;
+      const int rr = r & 63;
+      const bool diag = (i + (r >> 6)) == j;  // a diagonal tile keeps only its lower part
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        float4 c = cv[q];
+        c.x -= d[4 * q];
+        c.y -= d[4 * q + 1];
+        c.z -= d[4 * q + 2];
+        c.w -= d[4 * q + 3];
+        if (!diag) {
+          reinterpret_cast<float4*>(t)[q] = c;
+        } else {
+          const int cc = c0 + 4 * q;
+          if (cc <= rr) t[4 * q] = c.x;
+          if (cc + 1 <= rr) t[4 * q + 1] = c.y;
+          if (cc + 2 <= rr) t[4 * q + 2] = c.z;
+          if (cc + 3 <= rr) t[4 * q + 3] = c.w;
+        }
+      }
+    }
+  }
+  tc_fence_before_sync();
+  return true;
 }
 
 // ---------------------------------------------------------------------------
@@ -408,6 +539,7 @@ __device__ void task_update(LgShared& sm, float* A, const float* D, int i, int j
 // One large pose system as the kernels see it (device copy per launch).
 struct LgProb {
   float *A, *Linv, *D, *invD, *rhs, *xf, *xb, *sc;  // factor scratch
+  float* G;                                        // pre-split update operands [tri(T)][2][64 x 64]
   const double* S;                                 // FP64 tiled lower triangle
   const double* y;                                 // right-hand side
   double *xacc, *dx;                               // refinement accumulator, output
@@ -451,34 +583,51 @@ __global__ void k_lg_convert(const LgProb* __restrict__ probs, const int* status
 
 // The factorisation task graphs of all large systems.  CTA p < nsys runs the
 // critical chain of system p (other CTAs on its SM leave when there are SMs
-// to spare), then joins the workers; workers take the panels and updates of
-// all systems from one list (task: system << 32 | type << 30 | k << 20 | i << 10 | j).
-__global__ void __launch_bounds__(LG_THREADS, 2) k_lg_factor(const LgProb* __restrict__ probs, int nsys,
+// to spare), then joins the workers; workers take the panels and the
+// tensor-core pair updates of all systems from one list (task: system << 32 |
+// type << 30 | k << 20 | i << 10 | j; an update covers row tiles i and i+1).
+// Every CTA that stays holds TC_COLS tensor-memory columns, released on every
+// way out once its MMAs have completed.
+__global__ void __maxnreg__(120) k_lg_factor(const LgProb* __restrict__ probs, int nsys,
                                                           const unsigned long long* __restrict__ tasks, int ntasks,
                                                           int* ctr, int* dsm, int isolate, int* status,
                                                           long long timeout) {
-  extern __shared__ __align__(16) float lg_smem[];
-  LgShared& sm = *reinterpret_cast<LgShared*>(lg_smem);
+  extern __shared__ __align__(1024) float lg_smem[];
+  LgShared& sm = *reinterpret_cast<LgShared*>(lg_smem);          // the CUDA-core tasks
+  unsigned char* tcbuf = reinterpret_cast<unsigned char*>(lg_smem);  // the tensor-core operands (aliased)
+  __shared__ TcState ts;
+  __shared__ int role, task, bad;
   if (threadIdx.x == 0) {
     unsigned smid;
     asm("mov.u32 %0, %%smid;" : "=r"(smid));
-    sm.task = 1;
+    role = 1;
     if ((int)blockIdx.x < nsys) {
       st_release(dsm + blockIdx.x, (int)smid + 1);
     } else if (isolate) {
-      for (int c = 0; c < nsys && sm.task > 0; ++c)
-        if (!wait_geq(dsm + c, 1, status, timeout) || ld_acquire(dsm + c) == (int)smid + 1) sm.task = -1;
+      for (int c = 0; c < nsys && role > 0; ++c)
+        if (!wait_geq(dsm + c, 1, status, timeout) || ld_acquire(dsm + c) == (int)smid + 1) role = -1;
     }
   }
   __syncthreads();
-  if (sm.task < 0) return;
+  if (role < 0) return;
+  if (threadIdx.x < 32) tc_alloc(&ts.tmem, TC_COLS);
+  if (threadIdx.x == 0) {
+    tc_mbar_init(&ts.bar_ld, 1);
+    tc_mbar_init(&ts.bar_mma, 1);
+    ts.ph_ld = ts.ph_mma = 0;
+    ts.bad = 0;
+  }
+  tc_fence_smem();
+  tc_fence_before_sync();
+  __syncthreads();
+  tc_fence_after_sync();
   if ((int)blockIdx.x < nsys) {
     const LgProb& P = probs[blockIdx.x];
     for (int k = 0; k < P.T; ++k) {
-      if (dpv_status(status)) return;
-      if (!task_diag_step(sm, P.A, P.Linv, P.D, P.invD, k, P.ver, status, timeout)) {
+      if (dpv_status(status)) goto done;
+      if (!task_diag_step(sm, P.A, P.G, P.Linv, P.D, P.invD, k, P.ver, status, timeout)) {
         if (threadIdx.x == 0 && !dpv_status(status)) dpv_set_status(status, DST_NOT_SPD);
-        return;
+        goto done;
       }
       __syncthreads();
       if (threadIdx.x == 0) {
@@ -488,17 +637,19 @@ __global__ void __launch_bounds__(LG_THREADS, 2) k_lg_factor(const LgProb* __res
     }
   }
   for (;;) {
-    if (threadIdx.x == 0) sm.task = dpv_status(status) ? ntasks : atomicAdd(ctr, 1);
+    tc_fence_smem();  // this thread's generic shared accesses before any later bulk copy into the buffer
+    if (threadIdx.x == 0) task = dpv_status(status) ? ntasks : atomicAdd(ctr, 1);
     __syncthreads();
-    const int t = sm.task;
+    const int t = task;
     __syncthreads();
-    if (t >= ntasks) return;
+    if (t >= ntasks) break;
     const unsigned long long w64 = tasks[t];
     const LgProb& P = probs[(int)(w64 >> 32)];
     const unsigned w = (unsigned)w64;
     const int type = (int)(w >> 30), k = (int)((w >> 20) & 1023u), i = (int)((w >> 10) & 1023u),
               j = (int)(w & 1023u);
     int* ver = P.ver;
+    const int T = P.T;
     if (threadIdx.x == 0) {
       bool ok;
       if (type == TASK_PANEL) {
@@ -506,25 +657,40 @@ __global__ void __launch_bounds__(LG_THREADS, 2) k_lg_factor(const LgProb* __res
       } else {
         ok = wait_geq(ver + tri2(i) + k, k + 1, status, timeout) &&
              wait_geq(ver + tri2(j) + k, k + 1, status, timeout) && wait_geq(ver + tri2(i) + j, k, status, timeout);
+        if (ok && i + 1 < T)
+          ok = wait_geq(ver + tri2(i + 1) + k, k + 1, status, timeout) &&
+               wait_geq(ver + tri2(i + 1) + j, k, status, timeout);
       }
-      sm.bad = ok ? 0 : 1;
+      bad = ok ? 0 : 1;
     }
     __syncthreads();
-    if (sm.bad) return;
-    int tv;  // the tile written
+    if (bad) break;
     if (type == TASK_PANEL) {
-      task_panel(sm, P.A, P.Linv, P.invD, i, k);
-      tv = tri2(i) + k;
-    } else {
-      task_update(sm, P.A, P.D, i, j, k);
-      tv = tri2(i) + j;
+      task_panel(sm, P.A, P.G, P.Linv, P.D, P.invD, i, k);
+    } else if (!task_update_tc(tcbuf, ts, P.A, P.G, T, i, j, k, timeout)) {
+      if (threadIdx.x == 0) dpv_set_status(status, DST_TIMEOUT);
+      break;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
       __threadfence();
-      st_release(ver + tv, k + 1);
+      if (type == TASK_PANEL) {
+        st_release(ver + tri2(i) + k, k + 1);
+      } else {
+        st_release(ver + tri2(i) + j, k + 1);
+        if (i + 1 < T) st_release(ver + tri2(i + 1) + j, k + 1);
+      }
     }
   }
+done:
+  // shared and tensor memory go back once no copy and no MMA of this CTA is in
+  // flight: after a timeout, wait (bounded) for the outstanding phase first
+  __syncthreads();
+  if (threadIdx.x == 0 && ts.bad) tc_mbar_wait(ts.bad == 1 ? &ts.bar_ld : &ts.bar_mma, ts.bad == 1 ? ts.ph_ld : ts.ph_mma, timeout);
+  tc_fence_before_sync();
+  __syncthreads();
+  tc_fence_after_sync();
+  if (threadIdx.x < 32) tc_dealloc(ts.tmem, TC_COLS);
 }
 
 // this thread's 4 x 4 block (rows 4 rg.., columns 4 cg..) of a 64 x 64 tile
@@ -721,14 +887,15 @@ std::vector<unsigned long long> build_tasks(const std::vector<int>& Ts) {
   for (int T : Ts) maxT = std::max(maxT, T);
   for (int p = 0; p < (int)Ts.size(); ++p)
     for (int i = 2; i < Ts[p]; ++i) put(p, TASK_PANEL, 0, i, 0);
+  // updates cover two row tiles (i, i+1) of one column
   for (int k = 0; k + 1 < maxT; ++k)
     for (int p = 0; p < (int)Ts.size(); ++p) {
       const int T = Ts[p];
       if (k + 1 >= T) continue;
-      for (int i = k + 2; i < T; ++i) put(p, TASK_UPDATE, k, i, k + 1);
+      for (int i = k + 2; i < T; i += 2) put(p, TASK_UPDATE, k, i, k + 1);
       for (int i = k + 3; i < T; ++i) put(p, TASK_PANEL, k + 1, i, k + 1);
       for (int j = k + 2; j < T; ++j)
-        for (int i = j; i < T; ++i) put(p, TASK_UPDATE, k, i, j);
+        for (int i = j; i < T; i += 2) put(p, TASK_UPDATE, k, i, j);
     }
   return v;
 }
@@ -755,8 +922,9 @@ int co_resident(ba_handle_t h, const void* fn, size_t smem = 0) {
 
 long long dpv_large_scratch_floats(int n_pad) {
   const long long T = n_pad / NB;
-  // tiles of A, inverses of the diagonal factors, D, D^-1, rhs, xf, xb, equilibration scale
-  return (long long)tri2((int)T) * TILE + T * TILE + 6LL * n_pad;
+  // tiles of A, inverses of the diagonal factors, D, D^-1, rhs, xf, xb,
+  // equilibration scale, the pre-split update operands
+  return (long long)tri2((int)T) * TILE + T * TILE + 6LL * n_pad + 2LL * tri2((int)T) * TILE;
 }
 
 // Solve every large system (h->large_sys) with one factorisation launch and
@@ -787,6 +955,7 @@ ba_status_t dpv_solve_large(ba_handle_t h, int refine) {
     P.xf = P.rhs + sd.n_pad;
     P.xb = P.xf + sd.n_pad;
     P.sc = P.xb + sd.n_pad;
+    P.G = P.sc + sd.n_pad;  // 256-byte aligned: every piece above is a multiple of 64 floats
     foff += dpv_large_scratch_floats(sd.n_pad);
     P.S = ws->S.p + sd.soff;
     P.y = ws->y.p + sd.voff;
@@ -860,10 +1029,12 @@ ba_status_t dpv_solve_large(ba_handle_t h, int refine) {
   {
     // at most two CTAs per SM; the critical CTAs get their SMs to themselves
     // while at least half the SMs remain for the workers
-    const size_t smem = sizeof(LgShared);
+    const size_t smem = std::max(sizeof(LgShared), (size_t)TC_SMEM);
     static bool attr = false;
     if (!attr) {
       DPV_CUDA(h, cudaFuncSetAttribute(k_lg_factor, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      // all of the unified L1 / shared storage as shared memory: two CTAs per SM
+      DPV_CUDA(h, cudaFuncSetAttribute(k_lg_factor, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
       attr = true;
     }
     const int grid = std::min(co_resident(h, (const void*)k_lg_factor, smem), 2 * h->num_sms);
