@@ -60,6 +60,8 @@ def parse():
                     help="fp32 (default) or mixed; the batched workload defaults to mixed")
     ap.add_argument("--group", type=int, default=0, help="patches per group (0 = automatic)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-capture", action="store_true", help="eager ba_step instead of CUDA-graph replay")
+    ap.add_argument("--no-autotune", action="store_true", help="skip the group-size autotuner")
     a = ap.parse_args()
     a.precision_set = a.precision is not None
     if a.precision is None:
@@ -273,6 +275,12 @@ def run_ours(args):
     stream = torch.cuda.current_stream(dev)
     ba = DPVBA(precision=args.precision, patches_per_group=args.group, stream=stream)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > L2 (126 MB)
+    ba.set_graph(**T)
+    tuning = None
+    if not args.no_autotune and args.group == 0:  # the group size, measured on this graph (untimed)
+        tuning = ba.autotune(scene.iters, scene.fixed, reps=3)
+    ba.set_capture(not args.no_capture)
+    ba.profile(True)  # before the warm-up: the replayed graph carries the event records
 
     def reset():
         T["poses"].copy_(pristine["poses"])
@@ -308,8 +316,8 @@ def run_ours(args):
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_ms = sum(step_ms)
     prof = ba.profile_read()
-    ba.profile(False)
     launches = ba.info()["launches"] - launches0
+    replays = ba.info()["graph_replays"]
     if dist:
         t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -318,6 +326,12 @@ def run_ours(args):
     value = gn_iters / (total_ms / 1e3)
 
     # ---- end to end through the C ABI with host buffers -------------------
+    # (no event records: the step runs as a user's would; the first steps
+    # after the switch re-capture, untimed)
+    ba.profile(False)
+    for _ in range(2):
+        reset()
+        one_step()
     host_in = {k: v.cpu().pin_memory() for k, v in pristine.items()}
     host_out = {"poses": torch.empty_like(host_in["poses"]).pin_memory(),
                 "patches": torch.empty_like(host_in["patches"]).pin_memory()}
@@ -412,6 +426,7 @@ def run_ours(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": desc, "N": scene.N, "P": scene.P, "E": scene.E, "iters": scene.iters,
                    "fixed": scene.fixed, "precision": args.precision, "patches_per_group": inf["G"],
+                   "autotune": tuning, "graph_replay": not args.no_capture, "graph_replays": replays,
                    "l2": "flushed between steps (256 MiB write)", "step": "ba_set_graph + ba_step"},
         "edges_per_sec": value * scene.E,
         "error_vs_oracle": err,
@@ -464,6 +479,12 @@ def run_batched(args):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     B = len(probs)
     E_tot = int(offs["edge_off"][-1])
+    ba.set_graph_batched(**T, **offs)
+    tuning = None
+    if not args.no_autotune and args.group == 0:  # the group size, measured on this batch (untimed)
+        tuning = ba.autotune(iters, fixed, reps=2)
+    ba.set_capture(not args.no_capture)
+    ba.profile(True)  # before the warm-up: the replayed graph carries the event records
 
     def reset():
         T["poses"].copy_(pristine["poses"])
@@ -479,7 +500,7 @@ def run_batched(args):
     ba.sync()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     launches0 = ba.info()["launches"]
-    ba.profile(True)
+    ba.profile(True)  # clears the warm-up's records
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
@@ -497,8 +518,8 @@ def run_batched(args):
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_ms = sum(step_ms)
     prof = ba.profile_read()
-    ba.profile(False)
     launches = ba.info()["launches"] - launches0
+    replays = ba.info()["graph_replays"]
     if dist:
         t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -532,7 +553,12 @@ def run_batched(args):
     plain_ms = sum(a.elapsed_time(b) for a, b in pev)
     plain_value = args.steps * B * iters / (plain_ms / 1e3)
 
-    # end to end through the C ABI with host buffers
+    # end to end through the C ABI with host buffers (no event records; the
+    # first steps after the switch re-capture, untimed)
+    ba.profile(False)
+    for _ in range(2):
+        reset()
+        one_step()
     host_in = {k: v.cpu().pin_memory() for k, v in pristine.items()}
     host_out = {"poses": torch.empty_like(host_in["poses"]).pin_memory(),
                 "patches": torch.empty_like(host_in["patches"]).pin_memory()}
@@ -599,6 +625,7 @@ def run_batched(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": desc, "problems": B, "frames": [sc.N for sc in probs], "E_total": E_tot,
                    "iters": iters, "fixed": fixed, "precision": precision, "patches_per_group": ba.info()["G"],
+                   "autotune": tuning, "graph_replay": not args.no_capture, "graph_replays": replays,
                    "l2": "flushed between steps (256 MiB write)", "step": "ba_set_graph_batched + ba_step"},
         "edges_per_sec": world * args.steps * E_tot * iters / (total_ms / 1e3),
         "plain_per_problem_fp32": {"value": plain_value, "unit": "problem GN it/s", "ms_per_step": plain_ms / args.steps,

@@ -145,6 +145,48 @@ DPVBA_API ba_status_t ba_set_graph_batched(ba_handle_t h, int B, const long long
  * 0 <= fixed_poses <= N, iters >= 0. */
 DPVBA_API ba_status_t ba_step(ba_handle_t h, int iters, int fixed_poses);
 
+/* ---- batched execution patterns ------------------------------------------
+ *
+ * on != 0: replay ba_step from a captured CUDA graph.  The first call for a
+ * configuration (binding pointers, sizes and offsets, workspace allocation,
+ * iters, fixed_poses, profiling on/off, stream) runs eagerly and sizes the
+ * workspace; the second captures the step on a private stream; later calls
+ * launch the graph on the handle's stream (one graph launch per ba_step).
+ * Rebinding the same buffers with the same sizes (new contents) keeps the
+ * graph.  Steps that record a tape (ba_set_record) run eagerly.  A step the
+ * runtime cannot capture keeps running eagerly for its configuration
+ * (ba_debug_info reports captures and replays).  With profiling on, each
+ * replay's event times are read before the next replay, which then waits on
+ * the host for the previous one to finish.  on == 0 releases the graph
+ * (synchronises). */
+DPVBA_API ba_status_t ba_set_capture(ba_handle_t h, int on);
+
+/* Autotune the patch-group size (patches reduced by one CTA of the assembly
+ * kernel) on the bound graph: for each candidate size in {8, 16, 24, 32, 48,
+ * 64} rebind the graph (its pointers are BORROWED again for this call: ii,
+ * jj, kk must still hold the bound edges), run one warm-up ba_step (two with
+ * graph replay), then time `reps` >= 1 calls of ba_step(iters, fixed_poses)
+ * with CUDA events on the handle's stream, restoring the caller's poses and
+ * patches (device copies) before every step; the median is the candidate's
+ * time.  A size the kernels cannot run on this graph (a group touching more
+ * than 64 frames) is infeasible (time -1).  The fastest feasible size is
+ * bound on return and recorded in a process-wide table under the binding's
+ * shape class (device, single or batched, patch and edge counts in
+ * half-octaves, precision), which the automatic choice (patches_per_group = 0)
+ * consults from then on; a handle created with an explicit size keeps the
+ * best one instead.  The poses and patches are left as they were.
+ * Outputs (host): *best_group; cand_group[i], cand_ms[i] for the first
+ * max_cand candidates (may be null when max_cand = 0); *n_cand (may be null)
+ * the number of candidates tried.  Synchronises; allocates temporaries.
+ * Errors: BA_ERR_STATE without a graph, BA_ERR_INVALID_ARG for bad
+ * arguments, BA_ERR_UNSUPPORTED if no candidate is feasible. */
+DPVBA_API ba_status_t ba_autotune(ba_handle_t h, int iters, int fixed_poses, int reps, int max_cand,
+                                  int* cand_group, float* cand_ms, int* n_cand, int* best_group);
+
+/* Forget every group size recorded by ba_autotune (the automatic choice goes
+ * back to its fixed rule).  Bound handles keep their current size. */
+DPVBA_API ba_status_t ba_autotune_clear(void);
+
 /* Wait for the handle's stream; return the first device-detected error. */
 DPVBA_API ba_status_t ba_sync(ba_handle_t h);
 
@@ -181,8 +223,9 @@ enum {
 DPVBA_API ba_status_t ba_debug_export(ba_handle_t h, int what, void* dst, long long bytes);
 
 /* Host integers describing the bound graph:
- * info[0..8] = N, P, E, patches_per_group, groups, n (last fixed), tile size, runs,
- * kernels launched by the handle so far. */
+ * info[0..11] = N, P, E, patches_per_group, groups, n (last fixed), tile size, runs,
+ * kernels launched by the handle so far, CUDA-graph captures, graph replays,
+ * kernels in one replay. */
 DPVBA_API ba_status_t ba_debug_info(ba_handle_t h, long long* info, int cap);
 
 /* Canonical pose-pose block keys of the B part of the system, computed on the

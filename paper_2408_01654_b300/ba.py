@@ -31,7 +31,8 @@ class DPVBA:
     """
 
     def __init__(self, precision: str = "fp32", lambda_pose=1e-4, lambda_depth=1e-4, z_min=0.1, d_min=1e-3,
-                 patches_per_group: int = 0, max_refine: int = 2, stream: torch.cuda.Stream | None = None):
+                 patches_per_group: int = 0, max_refine: int = 2, stream: torch.cuda.Stream | None = None,
+                 capture: bool = False):
         self._lib = capi.lib()
         self._h = ctypes.c_void_p()
         self.stream = stream if stream is not None else torch.cuda.current_stream()
@@ -42,6 +43,8 @@ class DPVBA:
         capi.check(None, self._lib.ba_create(ctypes.byref(self._h), ctypes.byref(opt)))
         self._keep = ()
         self.N = self.P = self.E = 0
+        if capture:
+            self.set_capture(True)
 
     # ------------------------------------------------------------------ core
     def set_graph(self, poses, patches, ii, jj, kk, targets, weights, intrinsics):
@@ -86,6 +89,23 @@ class DPVBA:
     def sync(self):
         capi.check(self._h, self._lib.ba_sync(self._h))
 
+    def set_capture(self, on: bool = True):
+        """Replay ``step`` from a captured CUDA graph (see ba_set_capture)."""
+        capi.check(self._h, self._lib.ba_set_capture(self._h, 1 if on else 0))
+
+    def autotune(self, iters: int, fixed: int, reps: int = 3) -> dict:
+        """Time every candidate patch-group size on the bound graph and keep
+        the fastest (see ba_autotune); returns the chosen size and the
+        candidates' median step times in ms (-1: infeasible)."""
+        cap = 16
+        groups = (ctypes.c_int * cap)()
+        ms = (ctypes.c_float * cap)()
+        n = ctypes.c_int()
+        best = ctypes.c_int()
+        capi.check(self._h, self._lib.ba_autotune(self._h, iters, fixed, reps, cap, groups, ms, ctypes.byref(n),
+                                                  ctypes.byref(best)))
+        return {"G": best.value, "candidates": {groups[i]: float(ms[i]) for i in range(min(n.value, cap))}}
+
     def close(self):
         if self._h:
             self._lib.ba_destroy(self._h)
@@ -126,9 +146,10 @@ class DPVBA:
         capi.check(self._h, self._lib.ba_linearize(self._h, fixed))
 
     def info(self) -> dict:
-        arr = (ctypes.c_longlong * 9)()
-        capi.check(self._h, self._lib.ba_debug_info(self._h, arr, 9))
-        keys = ("N", "P", "E", "G", "groups", "n", "tile", "runs", "launches")
+        arr = (ctypes.c_longlong * 12)()
+        capi.check(self._h, self._lib.ba_debug_info(self._h, arr, 12))
+        keys = ("N", "P", "E", "G", "groups", "n", "tile", "runs", "launches", "graph_captures", "graph_replays",
+                "graph_kernels")
         return dict(zip(keys, list(arr)))
 
     def export(self, what: int, count: int | None = None) -> torch.Tensor:

@@ -28,31 +28,82 @@ static cudaEvent_t pool_event(ba_handle_t h) {
   return e;
 }
 
+// While a step is captured, the pair becomes two event-record nodes of the
+// graph (every replay records them again; see prof_harvest).
 void dpv_prof_begin(ba_handle_t h, int kind) {
   if (!h->prof_on) return;
   cudaEvent_t a = pool_event(h), b = pool_event(h);
   if (!a || !b) return;
-  cudaEventRecord(a, h->stream);
-  h->prof.push_back({kind, a, b});
-  h->prof_open = (int)h->prof.size() - 1;
+  std::vector<ba_handle_s::ProfRec>& list = h->capturing ? h->gprof : h->prof;
+  if (h->capturing)
+    cudaEventRecordWithFlags(a, h->stream, cudaEventRecordExternal);
+  else
+    cudaEventRecord(a, h->stream);
+  list.push_back({kind, a, b});
+  h->prof_open = (int)list.size() - 1;
 }
 
 void dpv_prof_end(ba_handle_t h) {
   if (!h->prof_on || h->prof_open < 0) return;
-  cudaEventRecord(h->prof[h->prof_open].b, h->stream);
+  if (h->capturing)
+    cudaEventRecordWithFlags(h->gprof[h->prof_open].b, h->stream, cudaEventRecordExternal);
+  else
+    cudaEventRecord(h->prof[h->prof_open].b, h->stream);
   h->prof_open = -1;
 }
 
-static void prof_clear(ba_handle_t h) {
-  for (auto& r : h->prof) {
+static void prof_release(ba_handle_t h, std::vector<ba_handle_s::ProfRec>& list) {
+  for (auto& r : list) {
     h->ev_pool.push_back(r.a);
     h->ev_pool.push_back(r.b);
   }
-  h->prof.clear();
+  list.clear();
+}
+
+// Add the event times of the last replay to the totals (waits for that replay).
+static ba_status_t prof_harvest(ba_handle_t h) {
+  if (!h->gprof_pending) return BA_OK;
+  h->gprof_pending = 0;
+  if (h->gprof.empty()) return BA_OK;
+  DPV_CUDA(h, cudaEventSynchronize(h->gprof.back().b));
+  for (auto& r : h->gprof) {
+    float ms = 0.f;
+    DPV_CUDA(h, cudaEventElapsedTime(&ms, r.a, r.b));
+    h->prof_ms[r.kind] += ms;
+    ++h->prof_n[r.kind];
+  }
+  return BA_OK;
+}
+
+static void prof_clear(ba_handle_t h) {
+  prof_release(h, h->prof);
   h->prof_open = -1;
+  h->gprof_pending = 0;
+  for (int k = 0; k < BA_KERNEL_CLASSES; ++k) {
+    h->prof_ms[k] = 0.0;
+    h->prof_n[k] = 0;
+  }
+}
+
+static void graph_drop(ba_handle_t h) {
+  if (h->gexec) cudaGraphExecDestroy(h->gexec);
+  h->gexec = nullptr;
+  h->gprof_pending = 0;
+  prof_release(h, h->gprof);
+  h->gkey_valid = 0;
+  h->gkey_failed = 0;
+}
+
+// Record the binding's signature; a change invalidates the captured step.
+static void bind_signature(ba_handle_t h, std::vector<long long> sig) {
+  if (sig != h->bind_sig) {
+    h->bind_sig = std::move(sig);
+    ++h->bind_gen;
+  }
 }
 
 long long dpv_large_scratch_floats(int n_pad);
+ba_status_t dpv_large_reserve(ba_handle_t h);
 
 namespace {
 
@@ -82,7 +133,10 @@ void system_geometry(int n, int& TS, int& T, int& n_pad) {
   }
 }
 
-int auto_group(ba_handle_t h, int P) {
+int auto_group(ba_handle_t h, long long P, long long E, int batched) {
+  // a size measured by ba_autotune for this shape class
+  const int tuned = dpv_tuned_group(h, P, E, batched);
+  if (tuned > 0) return tuned;
   // large graphs: 32 patches per group; small ones: keep about one group
   // per SM or more (measured on the 22-frame odometry window: 16 best)
   if ((long long)P >= 32LL * 2 * h->num_sms) return 32;
@@ -207,6 +261,7 @@ ba_status_t ensure_system(ba_handle_t h, int fixed) {
                                                           ws->sysd.p, ws->fdx.p);
   ++h->launches;
   DPV_CUDA(h, cudaGetLastError());
+  if ((s = dpv_large_reserve(h))) return s;
   return BA_OK;  // (pageable-source async copies are staged before they return)
 }
 
@@ -295,6 +350,8 @@ ba_status_t ba_destroy(ba_handle_t h) {
     release(ws->offs); release(ws->pcopy);
     delete ws;
   }
+  graph_drop(h);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   prof_clear(h);
   for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
   delete h;
@@ -311,11 +368,25 @@ ba_status_t ba_profile_enable(ba_handle_t h, int on) {
   return BA_OK;
 }
 
+ba_status_t ba_set_capture(ba_handle_t h, int on) {
+  if (!h) return BA_ERR_INVALID_ARG;
+  if (!on && h->gexec) {
+    DPV_CUDA(h, cudaStreamSynchronize(h->stream));
+    ba_status_t s = prof_harvest(h);
+    graph_drop(h);
+    if (s) return s;
+  }
+  h->capture_on = on ? 1 : 0;
+  return BA_OK;
+}
+
 ba_status_t ba_profile_read(ba_handle_t h, int kind, double* total_ms, long long* launches) {
   if (!h || !total_ms || !launches || kind < 0 || kind >= BA_KERNEL_CLASSES) return BA_ERR_INVALID_ARG;
   DPV_CUDA(h, cudaStreamSynchronize(h->stream));
-  double t = 0.0;
-  long long c = 0;
+  ba_status_t s = prof_harvest(h);
+  if (s) return s;
+  double t = h->prof_ms[kind];
+  long long c = h->prof_n[kind];
   for (auto& r : h->prof) {
     if (r.kind != kind) continue;
     float ms = 0.f;
@@ -346,6 +417,18 @@ ba_status_t ba_set_graph(ba_handle_t h, int N, int P, int E, double* poses, floa
   if ((reinterpret_cast<uintptr_t>(targets) | reinterpret_cast<uintptr_t>(weights)) & 7)
     return dpv_fail(h, BA_ERR_INVALID_ARG, "ba_set_graph: targets/weights must be 8-byte aligned");
   Workspace* ws = h->ws;
+  h->bind = ba_handle_s::Bind{};
+  h->bind.N = N;
+  h->bind.P = P;
+  h->bind.E = E;
+  h->bind.poses = poses;
+  h->bind.patches = patches;
+  h->bind.ii = ii;
+  h->bind.jj = jj;
+  h->bind.kk = kk;
+  h->bind.targets = targets;
+  h->bind.weights = weights;
+  h->bind.intrinsics = intrinsics;
   h->have_graph = 0;
   // the frame -> unknown map survives a rebinding with the same frame count
   const bool same_frames = h->nprob == 1 && h->N == N && h->fixed >= 0;
@@ -361,9 +444,11 @@ ba_status_t ba_set_graph(ba_handle_t h, int N, int P, int E, double* poses, floa
   h->patches = patches;
   h->targets = targets;
   h->weights = weights;
-  h->G = h->opt.patches_per_group > 0 ? h->opt.patches_per_group : auto_group(h, P);
+  h->G = h->opt.patches_per_group > 0 ? h->opt.patches_per_group : auto_group(h, P, E, 0);
   h->ngroups = (P + h->G - 1) / h->G;
   if (!same_frames) h->fixed = -1;
+  bind_signature(h, {1, N, P, E, (long long)(uintptr_t)poses, (long long)(uintptr_t)patches,
+                     (long long)(uintptr_t)targets, (long long)(uintptr_t)weights, h->G});
   h->tape_valid = 0;
   h->kk_bits = bits_for((unsigned long long)P);
   ba_status_t s;
@@ -422,7 +507,21 @@ ba_status_t ba_set_graph_batched(ba_handle_t h, int B, const long long* frame_of
     return dpv_fail(h, BA_ERR_INVALID_ARG, "ba_set_graph_batched: targets/weights must be 8-byte aligned");
   Workspace* ws = h->ws;
   const int N = (int)Nl, E = (int)El;
-  const int G = h->opt.patches_per_group > 0 ? h->opt.patches_per_group : auto_group(h, (int)Pl);
+  const int G = h->opt.patches_per_group > 0 ? h->opt.patches_per_group : auto_group(h, Pl, El, 1);
+  h->bind = ba_handle_s::Bind{};
+  h->bind.batched = 1;
+  h->bind.B = B;
+  h->bind.frame_off.assign(frame_off, frame_off + B + 1);
+  h->bind.patch_off.assign(patch_off, patch_off + B + 1);
+  h->bind.edge_off.assign(edge_off, edge_off + B + 1);
+  h->bind.poses = poses;
+  h->bind.patches = patches;
+  h->bind.ii = ii;
+  h->bind.jj = jj;
+  h->bind.kk = kk;
+  h->bind.targets = targets;
+  h->bind.weights = weights;
+  h->bind.intrinsics = intrinsics;
   // group-aligned patch numbering: every reduction group lies inside one problem
   std::vector<long long> offs(4 * (B + 1));
   long long* foff = offs.data();
@@ -465,6 +564,12 @@ ba_status_t ba_set_graph_batched(ba_handle_t h, int B, const long long* frame_of
   h->G = G;
   h->ngroups = (P + G - 1) / G;
   h->kk_bits = bits_for((unsigned long long)P);
+  {
+    std::vector<long long> sig = {2, B, N, P, E, (long long)(uintptr_t)poses, (long long)(uintptr_t)patches,
+                                  (long long)(uintptr_t)targets, (long long)(uintptr_t)weights, G};
+    sig.insert(sig.end(), offs.begin(), offs.end());
+    bind_signature(h, std::move(sig));
+  }
   ba_status_t s;
   const long long En = std::max(E, 1);
   const long long Gn = h->ngroups + 1;
@@ -496,6 +601,7 @@ ba_status_t ba_set_graph_batched(ba_handle_t h, int B, const long long* frame_of
     cudaFree(ws->intr);
     ws->intr = p;
     ws->intr_cap = B;
+    ++h->ws_gen;
   }
   cudaStream_t st = h->stream;
   DPV_CUDA(h, cudaMemsetAsync(ws->status, 0, sizeof(int), st));
@@ -539,19 +645,9 @@ static ba_status_t check_step_args(ba_handle_t h, int fixed_poses) {
   return BA_OK;
 }
 
-ba_status_t ba_step(ba_handle_t h, int iters, int fixed_poses) {
-  ba_status_t s = check_step_args(h, fixed_poses);
-  if (s) return s;
-  if (iters < 0) return dpv_fail(h, BA_ERR_INVALID_ARG, "iters < 0");
-  if ((s = ensure_system(h, fixed_poses))) return s;
-  h->last_iters = iters;
-  const int run = (iters > 0 && h->n > 0) ? iters : 0;
-  if (h->record) {
-    // this call becomes the tape of ba_backward
-    h->tape_valid = 0;
-    h->tape_iters_pending = run;
-    if ((s = dpv_tape_reserve(h, run))) return s;
-  }
+// The work of one ba_step after its checks, enqueued on h->stream.
+static ba_status_t step_body(ba_handle_t h, int run, int fixed_poses) {
+  ba_status_t s;
   if (h->patches_padded) {  // the padded working copy follows the caller's patches
     k_patch_copy<<<(unsigned)((27LL * h->P + 255) / 256), 256, 0, h->stream>>>(h->P, h->nprob, h->ws->offs.p,
                                                                                h->user_patches, h->ws->pcopy.p, 1);
@@ -590,6 +686,87 @@ ba_status_t ba_step(ba_handle_t h, int iters, int fixed_poses) {
     DPV_CUDA(h, cudaGetLastError());
   }
   return BA_OK;
+}
+
+// ba_step replayed from a CUDA graph.  The graph holds pointers and sizes, so
+// it is keyed by the binding, the workspace allocation, iters, fixed poses,
+// profiling and the stream.  The first call of a key runs eagerly (it sizes
+// the workspace and uploads the solver tables, which a capture may not do);
+// the second captures the step on a private stream and every later call
+// launches the graph on the handle's stream.  A step that cannot be captured
+// keeps running eagerly for that key.
+static ba_status_t step_graph(ba_handle_t h, int run, int fixed_poses) {
+  const ba_handle_s::GraphKey key{h->bind_gen, h->ws_gen, run, fixed_poses, h->prof_on, h->stream};
+  const ba_handle_s::GraphKey& k = h->gkey;
+  const bool same = h->gkey_valid && k.bind_gen == key.bind_gen && k.ws_gen == key.ws_gen && k.iters == key.iters &&
+                    k.fixed == key.fixed && k.prof == key.prof && k.stream == key.stream;
+  ba_status_t s;
+  if (!same) {
+    if (h->gexec || h->gprof_pending) {  // the old graph may still run: finish it first
+      DPV_CUDA(h, cudaStreamSynchronize(h->stream));
+      if ((s = prof_harvest(h))) return s;
+    }
+    graph_drop(h);
+    h->gkey = key;
+    h->gkey_valid = 1;
+    return step_body(h, run, fixed_poses);
+  }
+  if (!h->gexec) {
+    if (h->gkey_failed) return step_body(h, run, fixed_poses);
+    if (!h->cap_stream) DPV_CUDA(h, cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+    const cudaStream_t user = h->stream;
+    const long long l0 = h->launches;
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ex = nullptr;
+    s = BA_OK;
+    h->stream = h->cap_stream;
+    cudaError_t e = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      h->capturing = 1;
+      s = step_body(h, run, fixed_poses);
+      h->capturing = 0;
+      e = cudaStreamEndCapture(h->cap_stream, &g);
+    }
+    h->stream = user;
+    if (e == cudaSuccess && s == BA_OK && g) e = cudaGraphInstantiate(&ex, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess || s != BA_OK || !ex) {
+      cudaGetLastError();
+      prof_release(h, h->gprof);
+      h->prof_open = -1;
+      h->launches = l0;
+      h->gkey_failed = 1;
+      return step_body(h, run, fixed_poses);
+    }
+    h->gexec = ex;
+    h->glaunches = h->launches - l0;
+    h->launches = l0;
+    ++h->graph_captures;
+  }
+  // the previous replay's event times are read before the events are recorded again
+  if ((s = prof_harvest(h))) return s;
+  DPV_CUDA(h, cudaGraphLaunch(h->gexec, h->stream));
+  h->launches += h->glaunches;
+  ++h->graph_replays;
+  h->gprof_pending = h->gprof.empty() ? 0 : 1;
+  return BA_OK;
+}
+
+ba_status_t ba_step(ba_handle_t h, int iters, int fixed_poses) {
+  ba_status_t s = check_step_args(h, fixed_poses);
+  if (s) return s;
+  if (iters < 0) return dpv_fail(h, BA_ERR_INVALID_ARG, "iters < 0");
+  if ((s = ensure_system(h, fixed_poses))) return s;
+  h->last_iters = iters;
+  const int run = (iters > 0 && h->n > 0) ? iters : 0;
+  if (h->record) {
+    // this call becomes the tape of ba_backward
+    h->tape_valid = 0;
+    h->tape_iters_pending = run;
+    if ((s = dpv_tape_reserve(h, run))) return s;
+  }
+  if (h->capture_on && !h->record && run > 0) return step_graph(h, run, fixed_poses);
+  return step_body(h, run, fixed_poses);
 }
 
 ba_status_t ba_linearize(ba_handle_t h, int fixed_poses) {
@@ -633,8 +810,10 @@ ba_status_t ba_debug_info(ba_handle_t h, long long* info, int cap) {
     DPV_CUDA(h, cudaMemcpy(gnr.data(), h->ws->gnr.p, sizeof(int) * h->ngroups, cudaMemcpyDeviceToHost));
     for (int v : gnr) nr += v;
   }
-  const long long v[9] = {h->N, h->P, h->E, h->G, h->ngroups, h->n, h->TS, nr, h->launches};
-  for (int q = 0; q < cap && q < 9; ++q) info[q] = v[q];
+  const long long v[12] = {h->N,  h->P,        h->E,        h->G,         h->ngroups,
+                           h->n,  h->TS,       nr,          h->launches,  h->graph_captures,
+                           h->graph_replays, h->glaunches};
+  for (int q = 0; q < cap && q < 12; ++q) info[q] = v[q];
   return BA_OK;
 }
 

@@ -93,6 +93,40 @@ struct ba_handle_s {
 
   long long launches = 0;  // kernels launched by this handle so far
 
+  // CUDA-graph replay of ba_step (ba_set_capture)
+  int capture_on = 0;       // replay ba_step from a captured graph
+  int capturing = 0;        // a capture is in progress: allocations and uploads are errors
+  long long bind_gen = 0;   // bumped when the binding (pointers, sizes, offsets, group size) changes
+  long long ws_gen = 0;     // bumped when a workspace buffer is reallocated
+  std::vector<long long> bind_sig;
+  struct GraphKey {
+    long long bind_gen, ws_gen;
+    int iters, fixed, prof;
+    cudaStream_t stream;
+  };
+  GraphKey gkey{};
+  int gkey_valid = 0;       // gkey describes the current graph (or the run that precedes its capture)
+  int gkey_failed = 0;      // capturing this key failed: run it eagerly
+  cudaGraphExec_t gexec = nullptr;
+  cudaStream_t cap_stream = nullptr;  // private stream the step is captured on
+  long long glaunches = 0;  // kernels in one replay
+  long long graph_captures = 0, graph_replays = 0;
+  std::vector<ProfRec> gprof;  // event pairs recorded by every replay (profiling on)
+  int gprof_pending = 0;       // a replay's events wait to be read
+  double prof_ms[BA_KERNEL_CLASSES] = {};
+  long long prof_n[BA_KERNEL_CLASSES] = {};
+
+  // the arguments of the last binding (ba_autotune re-binds with other group sizes)
+  struct Bind {
+    int batched = 0;
+    int B = 1, N = 0, P = 0, E = 0;
+    std::vector<long long> frame_off, patch_off, edge_off;
+    double* poses = nullptr;
+    float* patches = nullptr;
+    const int *ii = nullptr, *jj = nullptr, *kk = nullptr;
+    const float *targets = nullptr, *weights = nullptr, *intrinsics = nullptr;
+  } bind;
+
   // tape of the last recorded ba_step (ba_set_record / ba_backward)
   int record = 0;
   int tape_valid = 0;
@@ -150,6 +184,7 @@ struct Workspace {
   DBuf<float> L;                  // factor (large n)
   DBuf<int> lg_sync;              // large solver: tile versions, row flags, task counter, grid barrier
   DBuf<long long> lg_prob;        // large solver: per-system descriptors
+  std::vector<unsigned char> lg_uploaded;  // host copy of what lg_prob and lg_rb hold
   DBuf<int> lg_rb;                // large solver: system of each global row block
   DBuf<double> r64;               // [n_pad]
   DBuf<float> tmpv;               // [n_pad]
@@ -177,6 +212,8 @@ template <class T>
 ba_status_t dpv_grow(ba_handle_t h, DBuf<T>& b, long long need, const char* what) {
   need = need < 1 ? 1 : need;
   if (need <= b.cap && b.p) return BA_OK;
+  if (h->capturing) return dpv_fail(h, BA_ERR_STATE, std::string("allocating ") + what + " during graph capture");
+  ++h->ws_gen;
   if (b.p) cudaFree(b.p);
   b.p = nullptr;
   b.cap = 0;
@@ -196,6 +233,9 @@ ba_status_t dpv_grow(ba_handle_t h, DBuf<T>& b, long long need, const char* what
       return dpv_fail((h), _e == cudaErrorMemoryAllocation ? BA_ERR_OOM : BA_ERR_CUDA, \
                       std::string(#call) + ": " + cudaGetErrorString(_e));             \
   } while (0)
+
+// group size recorded by ba_autotune for this shape class (0: none)
+int dpv_tuned_group(ba_handle_t h, long long P, long long E, int batched);
 
 // event timing around a kernel class (no-ops unless profiling is enabled)
 void dpv_prof_begin(ba_handle_t h, int kind);

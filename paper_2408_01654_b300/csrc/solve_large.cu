@@ -909,6 +909,22 @@ TaskCache& task_cache() {
   return c;
 }
 
+// every CTA resident at once (the kernels wait on one another's tiles); the
+// launch attribute form is also what a CUDA-graph capture records
+cudaError_t launch_cooperative(const void* fn, int grid, size_t smem, cudaStream_t st, void** args) {
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(LG_THREADS);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelExC(&cfg, fn, args);
+}
+
 int co_resident(ba_handle_t h, const void* fn, size_t smem = 0) {
   int per_sm = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, LG_THREADS, smem) != cudaSuccess) {
@@ -927,25 +943,36 @@ long long dpv_large_scratch_floats(int n_pad) {
   return (long long)tri2((int)T) * TILE + T * TILE + 6LL * n_pad + 2LL * tri2((int)T) * TILE;
 }
 
-// Solve every large system (h->large_sys) with one factorisation launch and
-// one solve launch.  refine: the most refinement sweeps allowed.
-ba_status_t dpv_solve_large(ba_handle_t h, int refine) {
+namespace {
+
+constexpr int MAX_SWEEPS = 16;
+
+// The large systems' descriptors, row-block table, task list and sync-word
+// layout for the current pose-system layout; grows the solver's buffers.
+struct LgPlan {
+  std::vector<int> Ts;
+  std::vector<LgProb> pr;
+  std::vector<int> rb_sys;
+  long long soff_sync = 0, nsync = 0;
+  unsigned long long* tasks = nullptr;
+  int ntasks = 0;
+};
+
+ba_status_t lg_plan(ba_handle_t h, LgPlan& L) {
   Workspace* ws = h->ws;
   const int nsys = (int)h->large_sys.size();
-  if (nsys == 0) return BA_OK;
-  constexpr int MAX_SWEEPS = 16;
-  refine = std::min(refine, MAX_SWEEPS - 1);
-  std::vector<int> Ts(nsys);
-  std::vector<LgProb> pr(nsys);
-  std::vector<int> rb_sys;
-  long long foff = 0, soff_sync = 0;
+  L.Ts.assign(nsys, 0);
+  L.pr.assign(nsys, LgProb{});
+  L.rb_sys.clear();
+  long long foff = 0;
+  L.soff_sync = 0;
   for (int p = 0; p < nsys; ++p) {
     const SysDesc& sd = h->sys[h->large_sys[p]];
     if (sd.TS != NB || sd.n_pad % NB) return dpv_fail(h, BA_ERR_UNSUPPORTED, "large solver needs 64-row tiles");
     const int T = sd.n_pad / NB;
     if (T > LG_MAX_T) return dpv_fail(h, BA_ERR_UNSUPPORTED, "pose system above 65472 unknowns");
-    Ts[p] = T;
-    LgProb& P = pr[p];
+    L.Ts[p] = T;
+    LgProb& P = L.pr[p];
     float* base = ws->L.p + foff;
     P.A = base;
     P.Linv = P.A + (size_t)tri2(T) * TILE;
@@ -965,21 +992,20 @@ ba_status_t dpv_solve_large(ba_handle_t h, int refine) {
     P.T = T;
     P.n = sd.n;
     P.n_pad = sd.n_pad;
-    P.rb0 = (int)rb_sys.size();
-    for (int i = 0; i < T; ++i) rb_sys.push_back(p);
-    soff_sync += tri2(T) + 2LL * T;
+    P.rb0 = (int)L.rb_sys.size();
+    for (int i = 0; i < T; ++i) L.rb_sys.push_back(p);
+    L.soff_sync += tri2(T) + 2LL * T;
   }
   if (foff > ws->L.cap) return dpv_fail(h, BA_ERR_STATE, "large solver scratch");
   // the task list of this set of sizes, built once per device
-  unsigned long long* tasks = nullptr;
-  int ntasks = 0;
   {
     TaskCache& tc = task_cache();
     std::lock_guard<std::mutex> lk(tc.mu);
-    auto key = std::make_pair(h->device, Ts);
+    auto key = std::make_pair(h->device, L.Ts);
     auto it = tc.lists.find(key);
     if (it == tc.lists.end()) {
-      std::vector<unsigned long long> v = build_tasks(Ts);
+      if (h->capturing) return dpv_fail(h, BA_ERR_STATE, "large solver task list built during graph capture");
+      std::vector<unsigned long long> v = build_tasks(L.Ts);
       unsigned long long* d = nullptr;
       if (cudaMalloc(&d, sizeof(unsigned long long) * std::max<size_t>(v.size(), 1)) != cudaSuccess) {
         cudaGetLastError();
@@ -988,18 +1014,47 @@ ba_status_t dpv_solve_large(ba_handle_t h, int refine) {
       if (!v.empty()) DPV_CUDA(h, cudaMemcpy(d, v.data(), sizeof(unsigned long long) * v.size(), cudaMemcpyHostToDevice));
       it = tc.lists.emplace(key, std::make_pair(d, (int)v.size())).first;
     }
-    tasks = it->second.first;
-    ntasks = it->second.second;
+    L.tasks = it->second.first;
+    L.ntasks = it->second.second;
   }
   // sync words: per system versions and row flags; task counter, barrier,
   // critical SMs, convergence maxima per (sweep, system)
-  const long long nsync = soff_sync + 4 + nsys + 2LL * MAX_SWEEPS * nsys;
-  const int R = (int)rb_sys.size();
+  L.nsync = L.soff_sync + 4 + nsys + 2LL * MAX_SWEEPS * nsys;
   ba_status_t s;
-  if ((s = dpv_grow(h, ws->lg_sync, nsync, "large solver sync")) ||
+  if ((s = dpv_grow(h, ws->lg_sync, L.nsync, "large solver sync")) ||
       (s = dpv_grow(h, ws->lg_prob, (long long)nsys * sizeof(LgProb) / sizeof(long long) + 1, "large systems")) ||
-      (s = dpv_grow(h, ws->lg_rb, R, "row blocks")))
+      (s = dpv_grow(h, ws->lg_rb, (long long)L.rb_sys.size(), "row blocks")))
     return s;
+  return BA_OK;
+}
+
+}  // namespace
+
+// Size the large solver's buffers and build its task list for the current
+// layout (ahead of the steps, so that a step allocates nothing).
+ba_status_t dpv_large_reserve(ba_handle_t h) {
+  if (h->large_sys.empty()) return BA_OK;
+  LgPlan L;
+  return lg_plan(h, L);
+}
+
+// Solve every large system (h->large_sys) with one factorisation launch and
+// one solve launch.  refine: the most refinement sweeps allowed.
+ba_status_t dpv_solve_large(ba_handle_t h, int refine) {
+  Workspace* ws = h->ws;
+  const int nsys = (int)h->large_sys.size();
+  if (nsys == 0) return BA_OK;
+  refine = std::min(refine, MAX_SWEEPS - 1);
+  LgPlan L;
+  ba_status_t s;
+  if ((s = lg_plan(h, L))) return s;
+  std::vector<int>& Ts = L.Ts;
+  std::vector<LgProb>& pr = L.pr;
+  std::vector<int>& rb_sys = L.rb_sys;
+  const long long soff_sync = L.soff_sync, nsync = L.nsync;
+  unsigned long long* tasks = L.tasks;
+  int ntasks = L.ntasks;
+  const int R = (int)rb_sys.size();
   int* sync = ws->lg_sync.p;
   for (int p = 0, o = 0; p < nsys; ++p) {
     pr[p].ver = sync + o;
@@ -1014,8 +1069,26 @@ ba_status_t dpv_solve_large(ba_handle_t h, int refine) {
   cudaStream_t st = h->stream;
   const LgProb* dprobs = reinterpret_cast<const LgProb*>(ws->lg_prob.p);
   DPV_CUDA(h, cudaMemsetAsync(sync, 0, sizeof(int) * nsync, st));
-  DPV_CUDA(h, cudaMemcpyAsync(ws->lg_prob.p, pr.data(), sizeof(LgProb) * nsys, cudaMemcpyHostToDevice, st));
-  DPV_CUDA(h, cudaMemcpyAsync(ws->lg_rb.p, rb_sys.data(), sizeof(int) * R, cudaMemcpyHostToDevice, st));
+  {
+    // the descriptors change only with the systems' layout or the workspace:
+    // upload them when they differ from what the device holds (never while a
+    // step is captured into a graph)
+    // (the workspace generation too: a reallocated lg_prob holds nothing)
+    std::vector<unsigned char> up;
+    auto put = [&up](const void* p, size_t n) {
+      const unsigned char* c = static_cast<const unsigned char*>(p);
+      up.insert(up.end(), c, c + n);
+    };
+    put(pr.data(), sizeof(LgProb) * nsys);
+    put(rb_sys.data(), sizeof(int) * R);
+    put(&h->ws_gen, sizeof(long long));
+    if (up != ws->lg_uploaded) {
+      if (h->capturing) return dpv_fail(h, BA_ERR_STATE, "large solver tables changed during graph capture");
+      DPV_CUDA(h, cudaMemcpyAsync(ws->lg_prob.p, pr.data(), sizeof(LgProb) * nsys, cudaMemcpyHostToDevice, st));
+      DPV_CUDA(h, cudaMemcpyAsync(ws->lg_rb.p, rb_sys.data(), sizeof(int) * R, cudaMemcpyHostToDevice, st));
+      ws->lg_uploaded.swap(up);  // (pageable-source copies are staged before they return)
+    }
+  }
   int maxpad = 0, maxtiles = 0;
   for (int T : Ts) {
     maxpad = std::max(maxpad, T * NB);
@@ -1043,7 +1116,7 @@ ba_status_t dpv_solve_large(ba_handle_t h, int refine) {
     int nsys_ = nsys;
     void* args[] = {(void*)&dprobs, (void*)&nsys_, (void*)&tasks,  (void*)&ntasks,
                     (void*)&ctr,    (void*)&dsm,   (void*)&isolate, (void*)&status, (void*)&timeout};
-    DPV_CUDA(h, cudaLaunchCooperativeKernel((const void*)k_lg_factor, dim3(grid), dim3(LG_THREADS), args, smem, st));
+    DPV_CUDA(h, launch_cooperative((const void*)k_lg_factor, grid, smem, st, args));
     ++h->launches;
   }
   {
@@ -1055,7 +1128,7 @@ ba_status_t dpv_solve_large(ba_handle_t h, int refine) {
     const int* rb = ws->lg_rb.p;
     void* args[] = {(void*)&dprobs, (void*)&nsys_, (void*)&rb,     (void*)&R_,      (void*)&sweeps,
                     (void*)&bar,    (void*)&conv,  (void*)&status, (void*)&timeout};
-    DPV_CUDA(h, cudaLaunchCooperativeKernel((const void*)k_lg_solve, dim3(grid), dim3(LG_THREADS), args, 0, st));
+    DPV_CUDA(h, launch_cooperative((const void*)k_lg_solve, grid, 0, st, args));
     ++h->launches;
   }
   DPV_CUDA(h, cudaGetLastError());
