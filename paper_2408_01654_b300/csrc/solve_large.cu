@@ -840,10 +840,16 @@ __global__ void __launch_bounds__(LG_THREADS, 1) k_lg_solve(const LgProb* __rest
     if (sweep + 1 == sweeps) break;
     if (!grid_barrier(bar, gridDim.x, status, timeout)) return;
     if (sweep > 0) {
+      // per system: the error left in x is below 1e-7 of it (the correction
+      // bounds the previous iterate's error; the current one's is about
+      // rho c_s with rho ~ c_s / c_{s-1})
       bool done = true;
-      for (int p = 0; p < nsys && done; ++p)
-        done = __int_as_float(ld_acquire(conv + 2 * (sweep * nsys + p))) <=
-               1e-7f * __int_as_float(ld_acquire(conv + 2 * (sweep * nsys + p) + 1));
+      for (int p = 0; p < nsys && done; ++p) {
+        const float cm = __int_as_float(ld_acquire(conv + 2 * (sweep * nsys + p)));
+        const float xm = __int_as_float(ld_acquire(conv + 2 * (sweep * nsys + p) + 1));
+        const float cp = __int_as_float(ld_acquire(conv + 2 * ((sweep - 1) * nsys + p)));
+        done = cm <= 1e-7f * xm || cm * cm <= 1e-7f * xm * cp;
+      }
       if (done) break;  // the same decision in every CTA
     }
     // rho = s (y - S xacc) in FP64, one warp per row of the concatenated systems

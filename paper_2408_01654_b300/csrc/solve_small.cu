@@ -69,9 +69,11 @@ __global__ void __launch_bounds__(small_threads(NQ)) k_solve_small(
   __shared__ __align__(16) float ucol[32];  // column broadcast in the diagonal block
   __shared__ float invD[NP];
   __shared__ float rhs[NP];
+  __shared__ float sol[NP];
   __shared__ float xhi[NP], xlo[NP];
   __shared__ float yhi[NP], ylo[NP];
   __shared__ float sc[NP];  // equilibration: S' = diag(sc) S diag(sc), sc = 1 / sqrt(diag S)
+  __shared__ double xs64[NP], rs64[NP];  // FP64 residual: x and S x
   __shared__ float red[2 * NWARP];
   __shared__ int bad;
   if (dpv_status(status)) return;
@@ -89,31 +91,48 @@ __global__ void __launch_bounds__(small_threads(NQ)) k_solve_small(
     dxf += sd.voff;
   }
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  // equilibration scale from the diagonal first (one load per thread)
+  if (tid == 0) bad = 0;
+  for (int i = tid; i < NP; i += NT) {
+    const float d = dpv_d2f_bits(S[(size_t)i * NP + i]);
+    sc[i] = (i < n && d > 0.f) ? rsqrtf(d) : 1.f;
+  }
+  __syncthreads();
   {
-    // S: FP64 row-major NP x NP (lower triangle valid), read as pairs with
-    // four loads in flight per thread, rounded to FP32 with integer operations
+    // S: FP64 row-major NP x NP (lower triangle valid), read as pairs; warp w
+    // takes rows w, w + NWARP, ..., lane the pairs lane, lane + 32, ... of a
+    // row, with up to eight loads in flight per thread; each value is rounded
+    // to FP32 with integer operations and equilibrated, s_i S_ij s_j, into the
+    // packed factor storage and the square copy
     constexpr int NPH = NP / 2;
+    constexpr int RW = NP / NWARP;        // rows per warp
+    constexpr int PL = (NPH + 31) / 32;   // pairs per lane in a row
+    constexpr int RB = PL >= 8 ? 1 : 8 / PL;  // rows per batch
     const double2* S2 = reinterpret_cast<const double2*>(S);
-    for (int q0 = tid; q0 < NP * NPH; q0 += 4 * NT) {
-      double2 v[4];
+    for (int rb = 0; rb < RW; rb += RB) {
+      double2 v[RB][PL];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int q = q0 + u * NT;
-        const int i = q / NPH, p = q - (q / NPH) * NPH;
-        v[u] = (q < NP * NPH && 2 * p <= i) ? S2[q] : make_double2(0.0, 0.0);
-      }
+      for (int r = 0; r < RB; ++r)
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int q = q0 + u * NT;
-        const int i = q / NPH, p = q - (q / NPH) * NPH;
-        if (q < NP * NPH && 2 * p <= i) {
-          const float a0 = dpv_d2f_bits(v[u].x), a1 = dpv_d2f_bits(v[u].y);
+        for (int t = 0; t < PL; ++t) {
+          const int i = wid + NWARP * (rb + r), p = lane + 32 * t;
+          v[r][t] = (rb + r < RW && p < NPH && 2 * p <= i) ? S2[(size_t)i * NPH + p] : make_double2(0.0, 0.0);
+        }
+#pragma unroll
+      for (int r = 0; r < RB; ++r)
+#pragma unroll
+        for (int t = 0; t < PL; ++t) {
+          const int i = wid + NWARP * (rb + r), p = lane + 32 * t;
+          if (rb + r >= RW || p >= NPH || 2 * p > i) continue;
+          const float si = sc[i];
+          const float a0 = dpv_d2f_bits(v[r][t].x) * (si * sc[2 * p]);
           Lsh[tri(i, 2 * p)] = a0;
           if (keep_sf(NQ)) {
             Sf[i * SFS + 2 * p] = a0;
             Sf[2 * p * SFS + i] = a0;
           }
           if (2 * p + 1 <= i) {
+            const float a1 = dpv_d2f_bits(v[r][t].y) * (si * sc[2 * p + 1]);
             Lsh[tri(i, 2 * p + 1)] = a1;
             if (keep_sf(NQ)) {
               Sf[i * SFS + 2 * p + 1] = a1;
@@ -121,25 +140,8 @@ __global__ void __launch_bounds__(small_threads(NQ)) k_solve_small(
             }
           }
         }
-      }
     }
   }
-  if (tid == 0) bad = 0;
-  for (int i = tid; i < NP; i += NT) {
-    const float d = dpv_d2f_bits(S[(size_t)i * NP + i]);
-    sc[i] = (i < n && d > 0.f) ? rsqrtf(d) : 1.f;
-  }
-  __syncthreads();
-  // equilibrate the FP32 copies (the FP64 refinement residual uses the FP64 S)
-  for (int i = wid; i < NP; i += NWARP)
-    for (int j = lane; j <= i; j += 32) {
-      const float f = sc[i] * sc[j];
-      Lsh[tri(i, j)] *= f;
-      if (keep_sf(NQ)) {
-        Sf[i * SFS + j] *= f;
-        if (j != i) Sf[j * SFS + i] *= f;
-      }
-    }
   // reset: leave S (lower triangle) as the next assembly expects it: zero,
   // lambda_p on the free diagonal, 1 on the padding diagonal.  Done here when
   // no refinement sweep reads S from global memory again, else at the end.
@@ -278,48 +280,53 @@ __global__ void __launch_bounds__(small_threads(NQ)) k_solve_small(
   __syncthreads();
 
   const int sweeps = 1 + refine32 + refine64;
+  float cprev = 0.f;  // the previous sweep's largest correction
   for (int sweep = 0; sweep < sweeps; ++sweep) {
-    // forward: L u = rhs
-    for (int kb = 0; kb < NQ; ++kb) {
-      const int r0 = 32 * kb;
-      if (wid == 0) {
-        float v = 0.f;
-#pragma unroll 8
-        for (int c = 0; c < 32; ++c) v = fmaf(Linv[kb][lane][c], rhs[r0 + c], v);
+    // the two triangular solves in warp 0 (lane = row of a 32-row block);
+    // the other warps wait at the barrier.  Forward, left-looking:
+    //   u_b = L_bb^-1 (rhs_b - sum_{j<b} L_bj u_j)  (into sol)
+    if (wid == 0) {
+      float* vb = ucol;
+      for (int kb = 0; kb < NQ; ++kb) {
+        const int r0 = 32 * kb, r = r0 + lane;
+        const float* lr = Lsh + tri(r, 0);
+        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+        for (int c = 0; c < r0; c += 4) {
+          a0 = fmaf(lr[c], sol[c], a0);
+          a1 = fmaf(lr[c + 1], sol[c + 1], a1);
+          a2 = fmaf(lr[c + 2], sol[c + 2], a2);
+          a3 = fmaf(lr[c + 3], sol[c + 3], a3);
+        }
+        vb[lane] = rhs[r] - ((a0 + a1) + (a2 + a3));
         __syncwarp();
-        rhs[r0 + lane] = v;
-      }
-      __syncthreads();
-      for (int i = r0 + 32 + tid; i < NP; i += NT) {
-        float v = rhs[i];
-        const float* li = Lsh + tri(i, r0);
+        float u = 0.f;
 #pragma unroll 8
-        for (int c = 0; c < 32; ++c) v = fmaf(-li[c], rhs[r0 + c], v);
-        rhs[i] = v;
+        for (int c = 0; c < 32; ++c) u = fmaf(Linv[kb][lane][c], vb[c], u);
+        sol[r] = u;
+        __syncwarp();
       }
-      __syncthreads();
+      // backward, left-looking from the bottom (into rhs):
+      //   x_b = L_bb^-T (D_b^-1 u_b - sum_{i>b} L_ib^T x_i)
+      for (int kb = NQ - 1; kb >= 0; --kb) {
+        const int r0 = 32 * kb, r = r0 + lane;
+        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+        int i = r0 + 32;
+        for (; i + 3 < NP; i += 4) {
+          a0 = fmaf(Lsh[tri(i, r)], rhs[i], a0);
+          a1 = fmaf(Lsh[tri(i + 1, r)], rhs[i + 1], a1);
+          a2 = fmaf(Lsh[tri(i + 2, r)], rhs[i + 2], a2);
+          a3 = fmaf(Lsh[tri(i + 3, r)], rhs[i + 3], a3);
+        }
+        vb[lane] = sol[r] * invD[r] - ((a0 + a1) + (a2 + a3));
+        __syncwarp();
+        float x = 0.f;
+#pragma unroll 8
+        for (int c = 0; c < 32; ++c) x = fmaf(Linv[kb][c][lane], vb[c], x);
+        rhs[r] = x;
+        __syncwarp();
+      }
     }
-    for (int q = tid; q < NP; q += NT) rhs[q] *= invD[q];
     __syncthreads();
-    // backward: L^T x = v
-    for (int kb = NQ - 1; kb >= 0; --kb) {
-      const int r0 = 32 * kb;
-      if (wid == 0) {
-        float v = 0.f;
-#pragma unroll 8
-        for (int r = 0; r < 32; ++r) v = fmaf(Linv[kb][r][lane], rhs[r0 + r], v);
-        __syncwarp();
-        rhs[r0 + lane] = v;
-      }
-      __syncthreads();
-      for (int j = tid; j < r0; j += NT) {
-        float v = rhs[j];
-#pragma unroll 8
-        for (int r = 0; r < 32; ++r) v = fmaf(-Lsh[tri(r0 + r, j)], rhs[r0 + r], v);
-        rhs[j] = v;
-      }
-      __syncthreads();
-    }
     // x += correction (double-float); stop once the correction is below
     // 1e-7 of the solution (refinement converged)
     float cmax = 0.f, xmax = 0.f;
@@ -342,13 +349,18 @@ __global__ void __launch_bounds__(small_threads(NQ)) k_solve_small(
     }
     __syncthreads();
     if (sweep + 1 == sweeps) break;
-    if (sweep > 0) {
+    {
       float cm = 0.f, xm = 0.f;
       for (int w = 0; w < NWARP; ++w) {
         cm = fmaxf(cm, red[w]);
         xm = fmaxf(xm, red[NWARP + w]);
       }
-      if (cm <= 1e-7f * xm) break;  // the same decision in every thread
+      // stop once the error left in x is below 1e-7 of it: the correction
+      // bounds the previous iterate's error, and the current one's is about
+      // rho c_s with the contraction rate rho ~ c_s / c_{s-1}
+      // (the same decision in every thread)
+      if (sweep > 0 && (cm <= 1e-7f * xm || cm * cm <= 1e-7f * xm * cprev)) break;
+      cprev = cm;
     }
     // residual rho = y - S x
     if (sweep < refine32 && keep_sf(NQ)) {
@@ -379,18 +391,28 @@ __global__ void __launch_bounds__(small_threads(NQ)) k_solve_small(
         }
       }
     } else {
-      // FP64 from the FP64 S (lower triangle, symmetric)
-      for (int r = wid; r < NP; r += NWARP) {
+      // FP64 from the FP64 S (lower triangle, symmetric), read row by row
+      // (coalesced): entry (r, c), c < r, adds to rows r and c; x in FP64
+      for (int q = tid; q < NP; q += NT) {
+        xs64[q] = q < n ? (double)sc[q] * ((double)xhi[q] + (double)xlo[q]) : 0.0;
+        rs64[q] = 0.0;
+      }
+      __syncthreads();
+      for (int r = wid; r < n; r += NWARP) {
+        const double xr = xs64[r];
+        const double* srow = S + (size_t)r * NP;
         double acc = 0.0;
-        if (r < n)
-          for (int c = lane; c < n; c += 32) {
-            const double sv = c <= r ? S[(size_t)r * NP + c] : S[(size_t)c * NP + r];
-            acc += sv * ((double)sc[c] * ((double)xhi[c] + (double)xlo[c]));
-          }
+        for (int c = lane; c <= r; c += 32) {
+          const double sv = srow[c];
+          acc += sv * xs64[c];
+          if (c < r) atomicAdd(&rs64[c], sv * xr);
+        }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (lane == 0) rhs[r] = r < n ? (float)((y[r] - acc) * (double)sc[r]) : 0.f;
+        if (lane == 0) atomicAdd(&rs64[r], acc);
       }
+      __syncthreads();
+      for (int r = tid; r < NP; r += NT) rhs[r] = r < n ? (float)((y[r] - rs64[r]) * (double)sc[r]) : 0.f;
     }
     __syncthreads();
   }
