@@ -184,6 +184,7 @@ struct Workspace {
   DBuf<float> L;                  // factor (large n)
   DBuf<int> lg_sync;              // large solver: tile versions, row flags, task counter, grid barrier
   DBuf<long long> lg_prob;        // large solver: per-system descriptors
+  DBuf<double> lg_red;            // large solver: conjugate-gradient dot products per (iteration, system)
   std::vector<unsigned char> lg_uploaded;  // host copy of what lg_prob and lg_rb hold
   DBuf<int> lg_rb;                // large solver: system of each global row block
   DBuf<double> r64;               // [n_pad]
@@ -317,6 +318,27 @@ __device__ __forceinline__ float dpv_d2f_bits(double v) {
   unsigned r = ((unsigned)e << 23) | mant;
   if (rest > 0x10000000ull || (rest == 0x10000000ull && (mant & 1u))) r += 1u;  // may carry to infinity
   return __uint_as_float(sign | r);
+}
+
+// The double as a pair of floats, v = hi + lo up to 2^-48 |v|: hi is v
+// rounded to float, lo the rest rounded to float, with integer operations
+// (lo is 0 when v is out of the float range or the rest would underflow).
+__device__ __forceinline__ float2 dpv_d2df_bits(double v) {
+  const float hi = dpv_d2f_bits(v);
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  const int ed = (int)((b >> 52) & 0x7ff);
+  const int e = ed - 1023 + 127;
+  // the rest is a multiple of 2^(ed - 1075): a normal float scale needs
+  // 1 <= ed - 948 <= 254
+  if (ed == 0x7ff || e <= 0 || e >= 255 || ed < 949 || ed > 1202) return make_float2(hi, 0.f);
+  const unsigned long long m = b & 0xfffffffffffffull;
+  const unsigned mant = (unsigned)(m >> 29);
+  const long long rest = (long long)(m & 0x1fffffffull);
+  const bool up = rest > 0x10000000ll || (rest == 0x10000000ll && (mant & 1u));
+  const long long d = up ? rest - 0x20000000ll : rest;  // |v| - |hi| in units of 2^(ed - 1075), |d| <= 2^28
+  float lo = __ll2float_rn(d) * __int_as_float((ed - 948) << 23);
+  if (b >> 63) lo = -lo;
+  return make_float2(hi, lo);
 }
 
 // rotation matrix of a unit quaternion (x, y, z, w), FP64

@@ -540,6 +540,8 @@ __device__ bool task_update_tc(unsigned char* tcbuf, TcState& ts, float* A, cons
 struct LgProb {
   float *A, *Linv, *D, *invD, *rhs, *xf, *xb, *sc;  // factor scratch
   float* G;                                        // pre-split update operands [tri(T)][2][64 x 64]
+  float2* Sdf;                                     // S as (hi, lo) float pairs, tiled like S
+  double *r, *p0, *p1, *u;                         // conjugate gradients: residual, directions, S v
   const double* S;                                 // FP64 tiled lower triangle
   const double* y;                                 // right-hand side
   double *xacc, *dx;                               // refinement accumulator, output
@@ -557,6 +559,7 @@ __global__ void k_lg_scale(const LgProb* __restrict__ probs, const int* status) 
   const float d = dpv_d2f_bits(P.S[dpv_s_index(r, r, NB)]);
   P.sc[r] = (r < P.n && d > 0.f) ? rsqrtf(d) : 1.f;
   P.rhs[r] = r < P.n ? dpv_d2f_bits(P.y[r]) * P.sc[r] : 0.f;
+  P.u[r] = 0.0;  // the refinement's product accumulates into u
 }
 
 // S (FP64 tiles) -> A (FP32 tiles, identical layout), equilibrated:
@@ -571,12 +574,14 @@ __global__ void k_lg_convert(const LgProb* __restrict__ probs, const int* status
     const int tj = t - tri2(ti);
     const double2* src = reinterpret_cast<const double2*>(P.S + (size_t)t * TILE);
     float2* dst = reinterpret_cast<float2*>(P.A + (size_t)t * TILE);
+    float4* ddf = reinterpret_cast<float4*>(P.Sdf + (size_t)t * TILE);
     for (int q = threadIdx.x; q < TILE / 2; q += blockDim.x) {
       const int r = (2 * q) / NB, c = (2 * q) % NB;
       const double2 v = src[q];
       const float si = P.sc[ti * NB + r];
-      dst[q] = make_float2(dpv_d2f_bits(v.x) * si * P.sc[tj * NB + c],
-                           dpv_d2f_bits(v.y) * si * P.sc[tj * NB + c + 1]);
+      const float2 a = dpv_d2df_bits(v.x), b = dpv_d2df_bits(v.y);
+      dst[q] = make_float2(a.x * si * P.sc[tj * NB + c], b.x * si * P.sc[tj * NB + c + 1]);
+      ddf[q] = make_float4(a.x, a.y, b.x, b.y);
     }
   }
 }
@@ -739,17 +744,128 @@ __device__ void tile_gemv(const TileRegs& t, const float* v, float* out, bool tr
   __syncthreads();
 }
 
-// Triangular solves + refinement of all large systems.  Global row block r
-// (system rb_sys[r], block i = r - rb0) is owned by CTA r mod grid in both
-// directions; forward rows wait for the rows above them in their system, the
-// backward rows for the rows below; a grid barrier separates the sweeps, whose
-// residual rho = y - S x is formed in FP64 from the FP64 S.  The sweeps stop
-// once every system's correction is below 1e-7 of its solution.
+// --- double-float (FP32 pair) arithmetic of the refinement's products -------
+struct DFp {
+  float h, l;
+};
+// a += (xh + xl)(yh + yl) to about 2^-44 of the product (xl * yl dropped);
+// a is renormalised by the caller (df_norm) after a few terms
+__device__ __forceinline__ void df_acc_prod(DFp& a, float xh, float xl, float yh, float yl) {
+  const float p = xh * yh;
+  float e = fmaf(xh, yh, -p);
+  e = fmaf(xh, yl, e);
+  e = fmaf(xl, yh, e);
+  const float s = a.h + p;
+  const float bb = s - a.h;
+  a.l += ((a.h - (s - bb)) + (p - bb)) + e;
+  a.h = s;
+}
+__device__ __forceinline__ void df_norm(DFp& a) {
+  const float s = a.h + a.l;
+  a.l = a.l - (s - a.h);
+  a.h = s;
+}
+__device__ __forceinline__ void df_add2(DFp& a, const DFp& b) {
+  const float s = a.h + b.h;
+  const float bb = s - a.h;
+  a.l += ((a.h - (s - bb)) + (b.h - bb)) + b.l;
+  a.h = s;
+  df_norm(a);
+}
+__device__ __forceinline__ DFp df_shfl_xor(const DFp& a, int o) {
+  return DFp{__shfl_xor_sync(0xffffffffu, a.h, o), __shfl_xor_sync(0xffffffffu, a.l, o)};
+}
+__device__ __forceinline__ void red_df(double* p, const DFp& a) {  // *p += hi + lo, exactly converted
+  dpv_red_add(p, dpv_f2d_bits(a.h));
+  dpv_red_add(p, dpv_f2d_bits(a.l));
+}
+
+// One 64 x 64 tile of the symmetric product u = S v in double-float: rows of
+// tile (ti, tj) get S_t v_tj, its columns (off the diagonal) S_t^T v_ti; a
+// diagonal tile holds the lower triangle.  vr, vc: v of the tile's rows and
+// columns (DF pairs, shared memory).  Thread (ty, tx) takes the 4 x 4 block
+// at rows 4 ty, columns 4 tx; row sums reduce over tx by shuffles, column sums
+// over ty through `part`.  Adds the tile's share of v^T S v to sig (the
+// thread's own accumulator).
+__device__ void tile_symv(const float2* __restrict__ St, const DFp* vr, const DFp* vc, bool diag, double* ur,
+                          double* uc, DFp (*part)[NB], DFp& sig) {
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  float4 m[4][2];
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const float4* rowp = reinterpret_cast<const float4*>(St + (4 * ty + a) * NB + 4 * tx);
+    m[a][0] = __ldcs(rowp);
+    m[a][1] = __ldcs(rowp + 1);
+  }
+  DFp R[4], C[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) R[q] = C[q] = DFp{0.f, 0.f};
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const int r = 4 * ty + a;
+    const float sh[4] = {m[a][0].x, m[a][0].z, m[a][1].x, m[a][1].z};
+    const float sl[4] = {m[a][0].y, m[a][0].w, m[a][1].y, m[a][1].w};
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int c = 4 * tx + b;
+      if (!diag || c <= r) df_acc_prod(R[a], sh[b], sl[b], vc[c].h, vc[c].l);
+      if (!diag || c < r) df_acc_prod(C[b], sh[b], sl[b], vr[r].h, vr[r].l);
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    df_norm(R[q]);
+    df_norm(C[q]);
+  }
+  // rows: sum over the 16 tx of the half warp
+#pragma unroll
+  for (int o = 1; o < 16; o <<= 1)
+#pragma unroll
+    for (int a = 0; a < 4; ++a) df_add2(R[a], df_shfl_xor(R[a], o));
+  if (tx == 0) {
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      const int r = 4 * ty + a;
+      red_df(ur + r, R[a]);
+      df_acc_prod(sig, R[a].h, R[a].l, vr[r].h, vr[r].l);
+    }
+  }
+  // columns: sum over the 16 ty
+#pragma unroll
+  for (int b = 0; b < 4; ++b) part[ty][4 * tx + b] = C[b];
+  __syncthreads();
+  if (tid < NB) {
+    DFp cs = part[0][tid];
+#pragma unroll
+    for (int k = 1; k < 16; ++k) df_add2(cs, part[k][tid]);
+    red_df((diag ? ur : uc) + tid, cs);
+    df_acc_prod(sig, cs.h, cs.l, vc[tid].h, vc[tid].l);
+  }
+  df_norm(sig);
+  __syncthreads();
+}
+
+// Triangular solves and preconditioned conjugate gradients of all large
+// systems.  The FP32 factor M = L D L^T of the equilibrated S' = D_s S D_s
+// preconditions CG on S' z = D_s y (x = D_s z):
+//   iteration 0:  z = M^-1 y',  r = y' - S' z
+//   iteration k:  w = M^-1 r,  rho = r.w,  p = w + (rho / rho_prev) p,
+//                 q = S' p,  alpha = rho / p.q,  z += alpha p,  r -= alpha q
+// The products with S run in double-float over S_df (FP64-level accuracy
+// at FP32 throughput), tile by tile with coalesced reads; r, p, x are FP64.
+// Global row block r (system rb_sys[r], block i = r - rb0) is owned by CTA
+// r mod grid in both directions; forward rows wait for the rows above them in
+// their system, the backward rows for the rows below; grid barriers separate
+// the phases.  The iterations stop once every system's estimated error left
+// in x is below 1e-7 of it.
 __global__ void __launch_bounds__(LG_THREADS, 1) k_lg_solve(const LgProb* __restrict__ probs, int nsys,
                                                             const int* __restrict__ rb_sys, int R, int sweeps,
-                                                            int* bar, int* conv, int* status, long long timeout) {
+                                                            int* bar, int* conv, double* red, int* status,
+                                                            long long timeout) {
   __shared__ float acc[NB], vj[NB], prod[NB];
   __shared__ float part[16][NB + 1];
+  __shared__ DFp dpart[16][NB];
+  __shared__ DFp vr[NB], vc[NB];
   __shared__ int ok;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   for (int sweep = 0; sweep < sweeps; ++sweep) {
@@ -757,7 +873,7 @@ __global__ void __launch_bounds__(LG_THREADS, 1) k_lg_solve(const LgProb* __rest
     // ---- forward: L u = rhs
     for (int r = blockIdx.x; r < R; r += gridDim.x) {
       const LgProb& P = probs[rb_sys[r]];
-      const int i = r - P.rb0, T = P.T;
+      const int i = r - P.rb0;
       if (tid < NB) acc[tid] = __ldcg(P.rhs + i * NB + tid);
       // the tiles do not depend on the flags: each is loaded while waiting for the previous row
       TileRegs m = load_block(i > 0 ? P.A + (size_t)tri2(i) * TILE : P.Linv + (size_t)i * TILE);
@@ -781,13 +897,13 @@ __global__ void __launch_bounds__(LG_THREADS, 1) k_lg_solve(const LgProb* __rest
         __threadfence();
         st_release(P.flags + i, sweep + 1);
       }
-      (void)T;
     }
-    // ---- backward: L^T x = D^-1 u, rows descending
+    // ---- backward: L^T w = D^-1 u, rows descending; rho = r.w per system
     int last = blockIdx.x;
     while (last + (int)gridDim.x < R) last += gridDim.x;
     for (int r = last; r >= 0; r -= gridDim.x) {
-      const LgProb& P = probs[rb_sys[r]];
+      const int sy = rb_sys[r];
+      const LgProb& P = probs[sy];
       const int i = r - P.rb0, T = P.T;
       if (tid < NB) acc[tid] = __ldcg(P.xf + i * NB + tid) * __ldcg(P.invD + i * NB + tid);
       TileRegs m = load_block(i + 1 < T ? P.A + (size_t)(tri2(T - 1) + i) * TILE : P.Linv + (size_t)i * TILE);
@@ -806,6 +922,13 @@ __global__ void __launch_bounds__(LG_THREADS, 1) k_lg_solve(const LgProb* __rest
       __syncthreads();
       tile_gemv(m, acc, prod, true, part);
       if (tid < NB) P.xb[i * NB + tid] = prod[tid];
+      if (sweep > 0 && wid < 2) {
+        const int q = i * NB + tid;
+        double rw = __ldcg(P.r + q) * dpv_f2d_bits(prod[tid]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) rw += __shfl_xor_sync(0xffffffffu, rw, o);
+        if (lane == 0) dpv_red_add(red + 2 * (sweep * nsys + sy), rw);
+      }
       __syncthreads();
       if (tid == 0) {
         __threadfence();
@@ -813,36 +936,123 @@ __global__ void __launch_bounds__(LG_THREADS, 1) k_lg_solve(const LgProb* __rest
       }
     }
     if (!grid_barrier(bar, gridDim.x, status, timeout)) return;
-    // ---- accumulate x += s z per row block; per-system convergence maxima
-    for (int r = blockIdx.x; r < R; r += gridDim.x) {
-      const int p = rb_sys[r];
-      const LgProb& P = probs[p];
-      const int i = r - P.rb0;
-      float cmax = 0.f, xmax = 0.f;
-      if (tid < NB) {
-        const int q = i * NB + tid;
-        const double c = dpv_f2d_bits(__ldcg(P.xb + q)) * dpv_f2d_bits(P.sc[q]);
-        const double x = (sweep == 0 ? 0.0 : P.xacc[q]) + c;
-        P.xacc[q] = x;
-        cmax = fabsf(dpv_d2f_bits(c));
-        xmax = fabsf(dpv_d2f_bits(x));
-      }
+    if (sweep == 0) {
+      // ---- z = w: x = s w, the first correction
+      for (int r = blockIdx.x; r < R; r += gridDim.x) {
+        const int sy = rb_sys[r];
+        const LgProb& P = probs[sy];
+        const int q = (r - P.rb0) * NB + tid;
+        float cmax = 0.f;
+        if (tid < NB) {
+          const double x = dpv_f2d_bits(__ldcg(P.xb + q)) * dpv_f2d_bits(P.sc[q]);
+          P.xacc[q] = x;
+          cmax = fabsf(dpv_d2f_bits(x));
+        }
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        cmax = fmaxf(cmax, __shfl_xor_sync(0xffffffffu, cmax, o));
-        xmax = fmaxf(xmax, __shfl_xor_sync(0xffffffffu, xmax, o));
+        for (int o = 16; o > 0; o >>= 1) cmax = fmaxf(cmax, __shfl_xor_sync(0xffffffffu, cmax, o));
+        if (lane == 0 && wid < 2) {  // non-negative floats order like their bit patterns
+          atomicMax(conv + 2 * sy, __float_as_int(cmax));
+          atomicMax(conv + 2 * sy + 1, __float_as_int(cmax));
+        }
       }
-      if (lane == 0 && wid < 2) {  // non-negative floats order like their bit patterns
-        atomicMax(conv + 2 * (sweep * nsys + p), __float_as_int(cmax));
-        atomicMax(conv + 2 * (sweep * nsys + p) + 1, __float_as_int(xmax));
+      if (sweep + 1 == sweeps) break;
+      if (!grid_barrier(bar, gridDim.x, status, timeout)) return;
+    }
+    // ---- u = S v (double-float), v = s x (iteration 0) or s p; p = w + beta p
+    {
+      DFp sig{0.f, 0.f};
+      for (int sy = 0; sy < nsys; ++sy) {
+        const LgProb& P = probs[sy];
+        const double beta =
+            sweep > 1 ? __ldcg(red + 2 * (sweep * nsys + sy)) / __ldcg(red + 2 * ((sweep - 1) * nsys + sy)) : 0.0;
+        for (int t = blockIdx.x; t < tri2(P.T); t += gridDim.x) {
+          int ti = (int)((sqrtf(8.0f * t + 1.0f) - 1.0f) * 0.5f);
+          while (tri2(ti + 1) <= t) ++ti;
+          while (tri2(ti) > t) --ti;
+          const int tj = t - tri2(ti);
+          if (tid < NB) {
+            for (int side = 0; side < 2; ++side) {
+              const int blk = side ? tj : ti;
+              const int q = blk * NB + tid;
+              double pv;
+              if (sweep == 0) {
+                pv = __ldcg(P.xacc + q);  // (s z: already unscaled)
+              } else {
+                pv = dpv_f2d_bits(__ldcg(P.xb + q)) + (sweep > 1 ? beta * __ldcg(((sweep & 1) ? P.p1 : P.p0) + q) : 0.0);
+                // the new direction is written once, by the diagonal tile's CTA
+                if (ti == tj && side == 0) (((sweep & 1) ? P.p0 : P.p1))[q] = pv;
+                pv *= dpv_f2d_bits(P.sc[q]);
+              }
+              const float2 d = dpv_d2df_bits(pv);
+              (side ? vc : vr)[tid] = DFp{d.x, d.y};
+            }
+          }
+          __syncthreads();
+          tile_symv(P.Sdf + (size_t)t * TILE, vr, vc, ti == tj, P.u + ti * NB, P.u + tj * NB, dpart, sig);
+        }
+        if (sweep > 0) {
+          // the CTA's share of p.S'p = v.S v
+          __shared__ DFp sred[LG_THREADS / 32];
+          DFp a = sig;
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) df_add2(a, df_shfl_xor(a, o));
+          if (lane == 0) sred[wid] = a;
+          __syncthreads();
+          if (tid == 0) {
+            DFp b = sred[0];
+            for (int w = 1; w < LG_THREADS / 32; ++w) df_add2(b, sred[w]);
+            if (b.h != 0.f) red_df(red + 2 * (sweep * nsys + sy) + 1, b);
+          }
+          __syncthreads();
+        }
+        sig = DFp{0.f, 0.f};
       }
     }
-    if (sweep + 1 == sweeps) break;
+    if (!grid_barrier(bar, gridDim.x, status, timeout)) return;
+    // ---- updates: r (iteration 0: r = s (y - u)), or alpha steps of x and r
+    for (int r = blockIdx.x; r < R; r += gridDim.x) {
+      const int sy = rb_sys[r];
+      const LgProb& P = probs[sy];
+      const int q = (r - P.rb0) * NB + tid;
+      float cmax = 0.f, xmax = 0.f;
+      if (tid < NB) {
+        const double s = dpv_f2d_bits(P.sc[q]);
+        const double u = __ldcg(P.u + q);
+        double rr;
+        if (sweep == 0) {
+          rr = q < P.n ? s * (P.y[q] - u) : 0.0;
+        } else {
+          const double rho = __ldcg(red + 2 * (sweep * nsys + sy)), sg = __ldcg(red + 2 * (sweep * nsys + sy) + 1);
+          const double alpha = (rho > 0.0 && sg > 0.0) ? rho / sg : 0.0;
+          const double pv = __ldcg(((sweep & 1) ? P.p0 : P.p1) + q);
+          const double dxq = alpha * s * pv;
+          const double x = __ldcg(P.xacc + q) + dxq;
+          P.xacc[q] = x;
+          rr = q < P.n ? __ldcg(P.r + q) - alpha * s * u : 0.0;
+          cmax = fabsf(dpv_d2f_bits(dxq));
+          xmax = fabsf(dpv_d2f_bits(x));
+        }
+        P.r[q] = rr;
+        P.rhs[q] = dpv_d2f_bits(rr);
+        P.u[q] = 0.0;  // for the next product
+      }
+      if (sweep > 0) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          cmax = fmaxf(cmax, __shfl_xor_sync(0xffffffffu, cmax, o));
+          xmax = fmaxf(xmax, __shfl_xor_sync(0xffffffffu, xmax, o));
+        }
+        if (lane == 0 && wid < 2) {
+          atomicMax(conv + 2 * (sweep * nsys + sy), __float_as_int(cmax));
+          atomicMax(conv + 2 * (sweep * nsys + sy) + 1, __float_as_int(xmax));
+        }
+      }
+    }
     if (!grid_barrier(bar, gridDim.x, status, timeout)) return;
     if (sweep > 0) {
-      // per system: the error left in x is below 1e-7 of it (the correction
-      // bounds the previous iterate's error; the current one's is about
-      // rho c_s with rho ~ c_s / c_{s-1})
+      // per system: the error left in x is below 1e-7 of it (the step bounds
+      // the previous iterate's error; the current one's is about rho c_s with
+      // rho ~ c_s / c_{s-1})
       bool done = true;
       for (int p = 0; p < nsys && done; ++p) {
         const float cm = __int_as_float(ld_acquire(conv + 2 * (sweep * nsys + p)));
@@ -852,20 +1062,6 @@ __global__ void __launch_bounds__(LG_THREADS, 1) k_lg_solve(const LgProb* __rest
       }
       if (done) break;  // the same decision in every CTA
     }
-    // rho = s (y - S xacc) in FP64, one warp per row of the concatenated systems
-    const int gw = (blockIdx.x * LG_THREADS + tid) >> 5, nw = (gridDim.x * LG_THREADS) >> 5;
-    for (int g = gw; g < R * NB; g += nw) {
-      const LgProb& P = probs[rb_sys[g / NB]];
-      const int row = (g / NB - P.rb0) * NB + (g % NB);
-      double sacc = 0.0;
-      if (row < P.n)
-        for (int c = lane; c < P.n; c += 32)
-          sacc += P.S[c <= row ? dpv_s_index(row, c, NB) : dpv_s_index(c, row, NB)] * __ldcg(P.xacc + c);
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, o);
-      if (lane == 0) P.rhs[row] = row < P.n ? dpv_d2f_bits(P.y[row] - sacc) * P.sc[row] : 0.f;
-    }
-    if (!grid_barrier(bar, gridDim.x, status, timeout)) return;
   }
   // output
   for (int r = blockIdx.x; r < R; r += gridDim.x) {
@@ -945,8 +1141,10 @@ int co_resident(ba_handle_t h, const void* fn, size_t smem = 0) {
 long long dpv_large_scratch_floats(int n_pad) {
   const long long T = n_pad / NB;
   // tiles of A, inverses of the diagonal factors, D, D^-1, rhs, xf, xb,
-  // equilibration scale, the pre-split update operands
-  return (long long)tri2((int)T) * TILE + T * TILE + 6LL * n_pad + 2LL * tri2((int)T) * TILE;
+  // equilibration scale, the pre-split update operands, S as float pairs,
+  // the conjugate-gradient vectors r, p0, p1, u (FP64)
+  return (long long)tri2((int)T) * TILE + T * TILE + 6LL * n_pad + 2LL * tri2((int)T) * TILE +
+         2LL * tri2((int)T) * TILE + 8LL * n_pad;
 }
 
 namespace {
@@ -989,6 +1187,11 @@ ba_status_t lg_plan(ba_handle_t h, LgPlan& L) {
     P.xb = P.xf + sd.n_pad;
     P.sc = P.xb + sd.n_pad;
     P.G = P.sc + sd.n_pad;  // 256-byte aligned: every piece above is a multiple of 64 floats
+    P.Sdf = reinterpret_cast<float2*>(P.G + 2LL * tri2(T) * TILE);
+    P.r = reinterpret_cast<double*>(P.G + 4LL * tri2(T) * TILE);
+    P.p0 = P.r + sd.n_pad;
+    P.p1 = P.p0 + sd.n_pad;
+    P.u = P.p1 + sd.n_pad;
     foff += dpv_large_scratch_floats(sd.n_pad);
     P.S = ws->S.p + sd.soff;
     P.y = ws->y.p + sd.voff;
@@ -1028,6 +1231,7 @@ ba_status_t lg_plan(ba_handle_t h, LgPlan& L) {
   L.nsync = L.soff_sync + 4 + nsys + 2LL * MAX_SWEEPS * nsys;
   ba_status_t s;
   if ((s = dpv_grow(h, ws->lg_sync, L.nsync, "large solver sync")) ||
+      (s = dpv_grow(h, ws->lg_red, 2LL * MAX_SWEEPS * nsys, "large solver reductions")) ||
       (s = dpv_grow(h, ws->lg_prob, (long long)nsys * sizeof(LgProb) / sizeof(long long) + 1, "large systems")) ||
       (s = dpv_grow(h, ws->lg_rb, (long long)L.rb_sys.size(), "row blocks")))
     return s;
@@ -1075,6 +1279,8 @@ ba_status_t dpv_solve_large(ba_handle_t h, int refine) {
   cudaStream_t st = h->stream;
   const LgProb* dprobs = reinterpret_cast<const LgProb*>(ws->lg_prob.p);
   DPV_CUDA(h, cudaMemsetAsync(sync, 0, sizeof(int) * nsync, st));
+  DPV_CUDA(h, cudaMemsetAsync(ws->lg_red.p, 0, sizeof(double) * 2 * MAX_SWEEPS * nsys, st));
+  double* red = ws->lg_red.p;
   {
     // the descriptors change only with the systems' layout or the workspace:
     // upload them when they differ from what the device holds (never while a
@@ -1132,8 +1338,8 @@ ba_status_t dpv_solve_large(ba_handle_t h, int refine) {
     int sweeps = refine + 1;
     int nsys_ = nsys, R_ = R;
     const int* rb = ws->lg_rb.p;
-    void* args[] = {(void*)&dprobs, (void*)&nsys_, (void*)&rb,     (void*)&R_,      (void*)&sweeps,
-                    (void*)&bar,    (void*)&conv,  (void*)&status, (void*)&timeout};
+    void* args[] = {(void*)&dprobs, (void*)&nsys_, (void*)&rb,  (void*)&R_,     (void*)&sweeps,
+                    (void*)&bar,    (void*)&conv,  (void*)&red, (void*)&status, (void*)&timeout};
     DPV_CUDA(h, launch_cooperative((const void*)k_lg_solve, grid, 0, st, args));
     ++h->launches;
   }

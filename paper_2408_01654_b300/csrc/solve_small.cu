@@ -480,7 +480,7 @@ ba_status_t dpv_solve(ba_handle_t h, int* retracted, int reset_system) {
     off += cnt;
   }
   // large systems, all together: FP64 refinement sweeps until converged (at least four allowed)
-  return dpv_solve_large(h, std::max(4, refine64));
+  return dpv_solve_large(h, std::max(8, refine64));
 }
 
 // Launch the one-CTA solver on a system the caller has already laid out as one

@@ -128,12 +128,17 @@ __device__ __forceinline__ void tc_ld32(uint32_t taddr, float* v) {
   for (int q = 0; q < 32; ++q) v[q] = __uint_as_float(r[q]);
 }
 
-// split x into a TF32 part (low 13 mantissa bits cleared) and the FP32 rest:
-// x = hi + lo exactly; three TF32 products hi*hi + hi*lo + lo*hi then carry
-// the product to about FP32 accuracy
+// split x into its nearest TF32 value and the nearest TF32 value of the rest
+// (x - hi is exact in FP32): x = hi + lo up to 2^-22 |x|, with round-to-
+// nearest (unbiased) errors.  The three products hi*hi + hi*lo + lo*hi then
+// carry a product to about FP32 accuracy (lo*lo is below 2^-22 of it).
 __device__ __forceinline__ void tc_split(float x, float& hi, float& lo) {
-  hi = __uint_as_float(__float_as_uint(x) & 0xFFFFE000u);
-  lo = x - hi;
+  uint32_t h, l;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(x));
+  const float rest = x - __uint_as_float(h);
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(l) : "f"(rest));
+  hi = __uint_as_float(h);
+  lo = __uint_as_float(l);
 }
 
 // --- bulk copies (async proxy) ------------------------------------------------
