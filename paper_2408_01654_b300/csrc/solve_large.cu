@@ -25,11 +25,12 @@
 // resident (cooperative launch) and each wait is on work that is earlier in
 // the critical chain or in the list, so the schedule cannot deadlock.
 //
-// A second persistent kernel runs the triangular solves and the refinement:
-// block row i of the forward solve waits for the rows above it, the backward
-// solve for the rows below; a grid barrier separates the sweeps, whose
-// residual rho = y - S x is formed in FP64 from the FP64 S, until the
-// correction is below 1e-7 of the solution.
+// A second persistent kernel runs conjugate gradients preconditioned by the
+// factor: in the triangular solves block row i of the forward solve waits for
+// the rows above it (each solved value is published with its pass number in
+// one 64-bit word), the backward solve for the rows below; grid barriers
+// separate the phases; the products with S run in double-float, until the
+// estimated error left in x is below 1e-7 of it.
 #include "internal.cuh"
 #include "tcgen05.cuh"
 
@@ -100,6 +101,35 @@ __device__ bool grid_barrier(int* bar, int nblocks, int* status, long long timeo
   }
   __syncthreads();
   return ok != 0;
+}
+
+// A solved value published with its pass number in one 64-bit word, so that
+// a consumer polling the word receives the value with the signal (no
+// separate flag, no fence: the word is written and read whole).
+__device__ __forceinline__ void st_tagged(unsigned long long* p, unsigned tag, float v) {
+  const unsigned long long w = ((unsigned long long)tag << 32) | __float_as_uint(v);
+  asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(w) : "memory");
+}
+// Wait until *p carries `tag`, then return its value in v.  Gives up when
+// another CTA reported an error or after `timeout` cycles (DST_TIMEOUT).
+__device__ bool wait_tagged(const unsigned long long* p, unsigned tag, float& v, int* status, long long timeout) {
+  const long long t0 = clock64();
+  for (unsigned it = 0;; ++it) {
+    unsigned long long w;
+    asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(w) : "l"(p) : "memory");
+    if ((unsigned)(w >> 32) == tag) {
+      v = __uint_as_float((unsigned)w);
+      return true;
+    }
+    if ((it & 63u) == 63u) {
+      if (dpv_status(status)) return false;
+      if (clock64() - t0 > timeout) {
+        dpv_set_status(status, DST_TIMEOUT);
+        return false;
+      }
+    }
+    if (it > 32) __nanosleep(32);
+  }
 }
 
 __device__ __forceinline__ float* tile_ptr(float* A, int i, int j) { return A + (size_t)(tri2(i) + j) * TILE; }
@@ -542,11 +572,12 @@ struct LgProb {
   float* G;                                        // pre-split update operands [tri(T)][2][64 x 64]
   float2* Sdf;                                     // S as (hi, lo) float pairs, tiled like S
   double *r, *p0, *p1, *u;                         // conjugate gradients: residual, directions, S v
+  unsigned long long *tf, *tb;                     // solved rows, tagged: (pass << 32) | value bits
   const double* S;                                 // FP64 tiled lower triangle
   const double* y;                                 // right-hand side
   double *xacc, *dx;                               // refinement accumulator, output
   float* dxf;                                      // FP32 copy of the output
-  int *ver, *flags;                                // tile versions [tri(T)], row flags [2T]
+  int* ver;                                        // tile versions [tri(T)]
   int T, n, n_pad, rb0;                            // tiles, unknowns, padded size, first global row block
 };
 
@@ -560,6 +591,8 @@ __global__ void k_lg_scale(const LgProb* __restrict__ probs, const int* status) 
   P.sc[r] = (r < P.n && d > 0.f) ? rsqrtf(d) : 1.f;
   P.rhs[r] = r < P.n ? dpv_d2f_bits(P.y[r]) * P.sc[r] : 0.f;
   P.u[r] = 0.0;  // the refinement's product accumulates into u
+  P.tf[r] = 0ull;  // no row solved yet in this solve
+  P.tb[r] = 0ull;
 }
 
 // S (FP64 tiles) -> A (FP32 tiles, identical layout), equilibrated:
@@ -782,21 +815,28 @@ __device__ __forceinline__ void red_df(double* p, const DFp& a) {  // *p += hi +
 
 // One 64 x 64 tile of the symmetric product u = S v in double-float: rows of
 // tile (ti, tj) get S_t v_tj, its columns (off the diagonal) S_t^T v_ti; a
-// diagonal tile holds the lower triangle.  vr, vc: v of the tile's rows and
-// columns (DF pairs, shared memory).  Thread (ty, tx) takes the 4 x 4 block
+// diagonal tile holds the lower triangle (loaded into registers by
+// load_symv_tile).  vr, vc: v of the tile's rows and columns (DF pairs,
+// shared memory).  Thread (ty, tx) takes the 4 x 4 block
 // at rows 4 ty, columns 4 tx; row sums reduce over tx by shuffles, column sums
 // over ty through `part`.  Adds the tile's share of v^T S v to sig (the
 // thread's own accumulator).
-__device__ void tile_symv(const float2* __restrict__ St, const DFp* vr, const DFp* vc, bool diag, double* ur,
-                          double* uc, DFp (*part)[NB], DFp& sig) {
-  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+struct SymvRegs {
   float4 m[4][2];
+};
+__device__ __forceinline__ void load_symv_tile(const float2* __restrict__ St, SymvRegs& g) {
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
 #pragma unroll
   for (int a = 0; a < 4; ++a) {
     const float4* rowp = reinterpret_cast<const float4*>(St + (4 * ty + a) * NB + 4 * tx);
-    m[a][0] = __ldcs(rowp);
-    m[a][1] = __ldcs(rowp + 1);
+    g.m[a][0] = __ldcs(rowp);
+    g.m[a][1] = __ldcs(rowp + 1);
   }
+}
+__device__ void tile_symv(const SymvRegs& g, const DFp* vr, const DFp* vc, bool diag, double* ur, double* uc,
+                          DFp (*part)[NB], DFp& sig) {
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const float4(&m)[4][2] = g.m;
   DFp R[4], C[4];
 #pragma unroll
   for (int q = 0; q < 4; ++q) R[q] = C[q] = DFp{0.f, 0.f};
@@ -858,7 +898,7 @@ __device__ void tile_symv(const float2* __restrict__ St, const DFp* vr, const DF
 // their system, the backward rows for the rows below; grid barriers separate
 // the phases.  The iterations stop once every system's estimated error left
 // in x is below 1e-7 of it.
-__global__ void __launch_bounds__(LG_THREADS, 1) k_lg_solve(const LgProb* __restrict__ probs, int nsys,
+__global__ void __launch_bounds__(LG_THREADS, 2) k_lg_solve(const LgProb* __restrict__ probs, int nsys,
                                                             const int* __restrict__ rb_sys, int R, int sweeps,
                                                             int* bar, int* conv, double* red, int* status,
                                                             long long timeout) {
@@ -868,6 +908,8 @@ __global__ void __launch_bounds__(LG_THREADS, 1) k_lg_solve(const LgProb* __rest
   __shared__ DFp vr[NB], vc[NB];
   __shared__ int ok;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  if (tid == 0) ok = 1;
+  __syncthreads();
   for (int sweep = 0; sweep < sweeps; ++sweep) {
     if (dpv_status(status)) return;
     // ---- forward: L u = rhs
@@ -875,32 +917,33 @@ __global__ void __launch_bounds__(LG_THREADS, 1) k_lg_solve(const LgProb* __rest
       const LgProb& P = probs[rb_sys[r]];
       const int i = r - P.rb0;
       if (tid < NB) acc[tid] = __ldcg(P.rhs + i * NB + tid);
-      // the tiles do not depend on the flags: each is loaded while waiting for the previous row
+      // the tiles do not depend on the solved rows: each is loaded while waiting for the previous row
       TileRegs m = load_block(i > 0 ? P.A + (size_t)tri2(i) * TILE : P.Linv + (size_t)i * TILE);
       for (int j = 0; j < i; ++j) {
         const TileRegs mn =
             load_block(j + 1 < i ? P.A + (size_t)(tri2(i) + j + 1) * TILE : P.Linv + (size_t)i * TILE);
-        if (tid == 0) ok = wait_geq(P.flags + j, sweep + 1, status, timeout) ? 1 : 0;
+        if (tid < NB) {
+          float v = 0.f;
+          if (!wait_tagged(P.tf + j * NB + tid, sweep + 1, v, status, timeout)) ok = 0;
+          vj[tid] = v;
+        }
         __syncthreads();
         if (!ok) return;
-        if (tid < NB) vj[tid] = __ldcg(P.xf + j * NB + tid);
-        __syncthreads();
         tile_gemv(m, vj, prod, false, part);
         if (tid < NB) acc[tid] -= prod[tid];
         m = mn;
       }
       __syncthreads();
       tile_gemv(m, acc, prod, false, part);
-      if (tid < NB) P.xf[i * NB + tid] = prod[tid];
-      __syncthreads();
-      if (tid == 0) {
-        __threadfence();
-        st_release(P.flags + i, sweep + 1);
+      if (tid < NB) {
+        P.xf[i * NB + tid] = prod[tid];
+        st_tagged(P.tf + i * NB + tid, sweep + 1, prod[tid]);
       }
     }
     // ---- backward: L^T w = D^-1 u, rows descending; rho = r.w per system
-    int last = blockIdx.x;
-    while (last + (int)gridDim.x < R) last += gridDim.x;
+    // this CTA's last row block (none when the grid has more CTAs than rows)
+    int last = (int)blockIdx.x < R ? (int)blockIdx.x : -1;
+    while (last >= 0 && last + (int)gridDim.x < R) last += gridDim.x;
     for (int r = last; r >= 0; r -= gridDim.x) {
       const int sy = rb_sys[r];
       const LgProb& P = probs[sy];
@@ -910,29 +953,31 @@ __global__ void __launch_bounds__(LG_THREADS, 1) k_lg_solve(const LgProb* __rest
       for (int j = T - 1; j > i; --j) {
         const TileRegs mn =
             load_block(j - 1 > i ? P.A + (size_t)(tri2(j - 1) + i) * TILE : P.Linv + (size_t)i * TILE);
-        if (tid == 0) ok = wait_geq(P.flags + T + j, sweep + 1, status, timeout) ? 1 : 0;
+        if (tid < NB) {
+          float v = 0.f;
+          if (!wait_tagged(P.tb + j * NB + tid, sweep + 1, v, status, timeout)) ok = 0;
+          vj[tid] = v;
+        }
         __syncthreads();
         if (!ok) return;
-        if (tid < NB) vj[tid] = __ldcg(P.xb + j * NB + tid);
-        __syncthreads();
         tile_gemv(m, vj, prod, true, part);
         if (tid < NB) acc[tid] -= prod[tid];
         m = mn;
       }
       __syncthreads();
       tile_gemv(m, acc, prod, true, part);
-      if (tid < NB) P.xb[i * NB + tid] = prod[tid];
+      if (tid < NB) {
+        P.xb[i * NB + tid] = prod[tid];
+        st_tagged(P.tb + i * NB + tid, sweep + 1, prod[tid]);
+      }
+      // off the chain: this block's share of rho = r.w (prod is rewritten
+      // only after the next row's first CTA barrier)
       if (sweep > 0 && wid < 2) {
         const int q = i * NB + tid;
         double rw = __ldcg(P.r + q) * dpv_f2d_bits(prod[tid]);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) rw += __shfl_xor_sync(0xffffffffu, rw, o);
         if (lane == 0) dpv_red_add(red + 2 * (sweep * nsys + sy), rw);
-      }
-      __syncthreads();
-      if (tid == 0) {
-        __threadfence();
-        st_release(P.flags + T + i, sweep + 1);
       }
     }
     if (!grid_barrier(bar, gridDim.x, status, timeout)) return;
@@ -965,7 +1010,10 @@ __global__ void __launch_bounds__(LG_THREADS, 1) k_lg_solve(const LgProb* __rest
         const LgProb& P = probs[sy];
         const double beta =
             sweep > 1 ? __ldcg(red + 2 * (sweep * nsys + sy)) / __ldcg(red + 2 * ((sweep - 1) * nsys + sy)) : 0.0;
+        SymvRegs cur, nxt;
+        if ((int)blockIdx.x < tri2(P.T)) load_symv_tile(P.Sdf + (size_t)blockIdx.x * TILE, cur);
         for (int t = blockIdx.x; t < tri2(P.T); t += gridDim.x) {
+          if (t + (int)gridDim.x < tri2(P.T)) load_symv_tile(P.Sdf + (size_t)(t + gridDim.x) * TILE, nxt);
           int ti = (int)((sqrtf(8.0f * t + 1.0f) - 1.0f) * 0.5f);
           while (tri2(ti + 1) <= t) ++ti;
           while (tri2(ti) > t) --ti;
@@ -988,7 +1036,8 @@ __global__ void __launch_bounds__(LG_THREADS, 1) k_lg_solve(const LgProb* __rest
             }
           }
           __syncthreads();
-          tile_symv(P.Sdf + (size_t)t * TILE, vr, vc, ti == tj, P.u + ti * NB, P.u + tj * NB, dpart, sig);
+          tile_symv(cur, vr, vc, ti == tj, P.u + ti * NB, P.u + tj * NB, dpart, sig);
+          cur = nxt;
         }
         if (sweep > 0) {
           // the CTA's share of p.S'p = v.S v
@@ -1142,9 +1191,9 @@ long long dpv_large_scratch_floats(int n_pad) {
   const long long T = n_pad / NB;
   // tiles of A, inverses of the diagonal factors, D, D^-1, rhs, xf, xb,
   // equilibration scale, the pre-split update operands, S as float pairs,
-  // the conjugate-gradient vectors r, p0, p1, u (FP64)
+  // the conjugate-gradient vectors r, p0, p1, u (FP64), the tagged solved rows
   return (long long)tri2((int)T) * TILE + T * TILE + 6LL * n_pad + 2LL * tri2((int)T) * TILE +
-         2LL * tri2((int)T) * TILE + 8LL * n_pad;
+         2LL * tri2((int)T) * TILE + 8LL * n_pad + 4LL * n_pad;
 }
 
 namespace {
@@ -1192,6 +1241,8 @@ ba_status_t lg_plan(ba_handle_t h, LgPlan& L) {
     P.p0 = P.r + sd.n_pad;
     P.p1 = P.p0 + sd.n_pad;
     P.u = P.p1 + sd.n_pad;
+    P.tf = reinterpret_cast<unsigned long long*>(P.u + sd.n_pad);
+    P.tb = P.tf + sd.n_pad;
     foff += dpv_large_scratch_floats(sd.n_pad);
     P.S = ws->S.p + sd.soff;
     P.y = ws->y.p + sd.voff;
@@ -1203,7 +1254,7 @@ ba_status_t lg_plan(ba_handle_t h, LgPlan& L) {
     P.n_pad = sd.n_pad;
     P.rb0 = (int)L.rb_sys.size();
     for (int i = 0; i < T; ++i) L.rb_sys.push_back(p);
-    L.soff_sync += tri2(T) + 2LL * T;
+    L.soff_sync += tri2(T);
   }
   if (foff > ws->L.cap) return dpv_fail(h, BA_ERR_STATE, "large solver scratch");
   // the task list of this set of sizes, built once per device
@@ -1226,7 +1277,7 @@ ba_status_t lg_plan(ba_handle_t h, LgPlan& L) {
     L.tasks = it->second.first;
     L.ntasks = it->second.second;
   }
-  // sync words: per system versions and row flags; task counter, barrier,
+  // sync words: per system tile versions; task counter, barrier,
   // critical SMs, convergence maxima per (sweep, system)
   L.nsync = L.soff_sync + 4 + nsys + 2LL * MAX_SWEEPS * nsys;
   ba_status_t s;
@@ -1268,8 +1319,7 @@ ba_status_t dpv_solve_large(ba_handle_t h, int refine) {
   int* sync = ws->lg_sync.p;
   for (int p = 0, o = 0; p < nsys; ++p) {
     pr[p].ver = sync + o;
-    pr[p].flags = sync + o + tri2(Ts[p]);
-    o += tri2(Ts[p]) + 2 * Ts[p];
+    o += tri2(Ts[p]);
   }
   int* ctr = sync + soff_sync;
   int* bar = ctr + 1;   // two ints
@@ -1332,8 +1382,9 @@ ba_status_t dpv_solve_large(ba_handle_t h, int refine) {
     ++h->launches;
   }
   {
-    const int maxg = co_resident(h, (const void*)k_lg_solve);
-    const int grid = std::min(R, maxg);
+    // every resident CTA: the row-block chains use R of them, the products
+    // with S all of them
+    const int grid = co_resident(h, (const void*)k_lg_solve);
     if (grid <= 0) return dpv_fail(h, BA_ERR_CUDA, "large solver occupancy");
     int sweeps = refine + 1;
     int nsys_ = nsys, R_ = R;
