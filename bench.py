@@ -36,16 +36,21 @@ from paper_2408_01654_b300 import scenes  # noqa: E402
 METRIC = "GN iterations/sec and edges/sec for patch-graph BA at stated FP64-oracle error"
 UNIT = "GN it/s"
 FALLBACK_HBM = 6400.0
+FALLBACK_BF16_TFLOPS = 1800.0
+TF32_PER_BF16 = 1.1 / 2.25  # nominal dense TF32 / BF16 tensor rates
 WORKLOADS = {
     "odometry": ("odometry-window BA: 22 keyframes, 96 patches/frame, patch lifetime 13, 8% outliers, "
                  "2 GN iterations, 2 fixed poses", scenes.odometry),
     "tiny": ("tiny BA: 8 frames, 96 patches/frame, +-3 frame edges, 2 GN iterations, 2 fixed poses", scenes.tiny),
     "global": ("global loop-closure BA: 1000 keyframes, 96 patches/frame, +-6 local + proximity loop edges, "
                "4 GN iterations, 2 fixed poses", scenes.global_ba),
+    "loop400": ("loop-closure BA at the batch's largest size: 400 keyframes, 96 patches/frame, +-6 local + "
+                "proximity loop edges, 4 GN iterations, 2 fixed poses (profiling case of the large-system kernels)",
+                lambda seed=0: scenes.global_ba(seed, N=400)),
     "batched": ("batched uneven BA: 64 independent problems, frames round(exp(U[ln 8, ln 400])), 96 patches/frame, "
                 "+-6 local + proximity loop edges, 4 GN iterations each, 2 fixed poses each", scenes.batched),
 }
-KERNEL_FILES = {"assemble": "assemble.cu", "solve": "solve_small.cu", "backsub": "update.cu",
+KERNEL_FILES = {"assemble": "assemble.cu", "solve": "solve_small.cu", "factor": "solve_large.cu", "backsub": "update.cu",
                 "retract": "update.cu", "init": "assemble.cu", "preprocess": "preprocess.cu"}
 
 
@@ -80,6 +85,47 @@ def measured_peaks():
         return float(d["hbm_gbs"]), "measured"
     except Exception:
         return FALLBACK_HBM, "fallback"
+
+
+def tensor_peak_tf32():
+    """TF32 dense peak: the measured BF16 burst x the nominal TF32/BF16 ratio."""
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            return float(json.load(f)["bf16_tflops"]) * TF32_PER_BF16, "measured bf16 burst x nominal tf32/bf16"
+    except Exception:
+        return FALLBACK_BF16_TFLOPS * TF32_PER_BF16, "fallback bf16 x nominal tf32/bf16"
+
+
+def factor_flops(ns):
+    """Algorithmic flops of the LDL^T factorisations run by the persistent
+    tensor-core kernel (systems above 256 unknowns): 2 n^3 / 3 each (the
+    three-pass TF32 split issues three times as many on the tensor pipe)."""
+    return sum(2.0 * n ** 3 / 3.0 for n in ns if n > 256)
+
+
+def roofline(dom, prof, steps, bytes_fn, factor_ns, workload):
+    """Roofline object of the dominant kernel class: the persistent
+    factorisation against the TF32 tensor peak, every other class against the
+    measured HBM copy bandwidth."""
+    t_ms, cnt = prof[dom]
+    per_launch_s = t_ms / cnt / 1e3
+    per_class = {k: v[0] / steps for k, v in prof.items()}
+    if dom == "factor":
+        fl = factor_flops(factor_ns)
+        peak, kind = tensor_peak_tf32()
+        achieved = fl / per_launch_s / 1e12
+        return {"kernel": "k_lg_factor", "bound": "tensor", "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": committed_traffic(dom, workload),
+                "algorithmic_flops_per_launch": fl, "avg_launch_us": per_launch_s * 1e6, "peak_source": kind,
+                "per_class_ms_per_step": per_class}
+    ab = bytes_fn(dom)
+    peak, kind = measured_peaks()
+    achieved = ab / per_launch_s / 1e9
+    return {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": committed_traffic(dom, workload),
+            "algorithmic_bytes_per_launch": ab, "avg_launch_us": per_launch_s * 1e6, "peak_source": kind,
+            "per_class_ms_per_step": per_class}
 
 
 def algorithmic_bytes(kind, N, P, E, n):
@@ -183,6 +229,9 @@ def pose_errors(a, b):
 # --------------------------------------------------------------------------- #
 # CPU oracle timing (reference arm and cpu_baseline leg)
 # --------------------------------------------------------------------------- #
+LARGE_FRAMES = 200  # scenes this large are sampled one GN iteration at a time on the CPU
+
+
 def time_oracle(scene, budget_s=10.0, max_runs=1000):
     import oracle
     oracle.build()
@@ -221,9 +270,16 @@ def run_reference(args):
         desc += f"; oracle sample: problems of {[sc.N for sc in sample]} frames per step"
     else:
         scene = make(seed=0)
-        work = lambda: oracle.gn(scene)  # noqa: E731
-        iters_per_step = scene.iters
-    for _ in range(min(args.warmup, 1)):
+        if scene.N >= LARGE_FRAMES:
+            # one GN iteration per step (a full run of the loop-closure BA
+            # takes minutes on one core)
+            work = lambda: oracle.gn(scene, iters=1)  # noqa: E731
+            iters_per_step = 1
+            desc += "; oracle sample: one GN iteration per step"
+        else:
+            work = lambda: oracle.gn(scene)  # noqa: E731
+            iters_per_step = scene.iters
+    for _ in range(min(args.warmup, 1 if scene.N < LARGE_FRAMES else 0)):
         work()
     t0 = time.perf_counter()
     for _ in range(args.steps):
@@ -386,15 +442,8 @@ def run_ours(args):
     inf = ba.info()
     n = inf["n"]
     dom = max((k for k in prof if prof[k][1] > 0), key=lambda k: prof[k][0])
-    t_ms, cnt = prof[dom]
-    per_launch_s = t_ms / cnt / 1e3
-    ab = algorithmic_bytes(dom, scene.N, scene.P, scene.E, n)
-    peak, peak_kind = measured_peaks()
-    achieved = ab / per_launch_s / 1e9
-    roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "traffic": committed_traffic(dom, args.workload),
-            "algorithmic_bytes_per_launch": ab, "avg_launch_us": per_launch_s * 1e6, "peak_source": peak_kind,
-            "per_class_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()}}
+    roof = roofline(dom, prof, args.steps, lambda k: algorithmic_bytes(k, scene.N, scene.P, scene.E, n), [n],
+                    args.workload)
 
     # ---- error against the oracle and the CPU baseline --------------------
     err = None
@@ -405,8 +454,11 @@ def run_ours(args):
         reset()
         ba.set_graph(**T)
         errs = []
-        want = oracle.gn_steps(scene, iters=scene.iters)
-        for it in range(scene.iters):
+        err_iters = scene.iters if scene.N < LARGE_FRAMES else 1
+        t_or = time.perf_counter()
+        want = oracle.gn_steps(scene, iters=err_iters)
+        t_or = time.perf_counter() - t_or
+        for it in range(err_iters):
             ba.step(1, scene.fixed)
             ba.sync()
             rot, tr = pose_errors(T["poses"].cpu().numpy(), want[it][0])
@@ -414,11 +466,15 @@ def run_ours(args):
             dep = float(np.max(np.abs(d - want[it][1]) / np.abs(want[it][1])))
             errs.append({"iter": it + 1, "rot_rad": rot, "trans_rel": tr, "depth_rel": dep})
         err = errs
-        runs, el = time_oracle(scene, budget_s=10.0)
-        cv = runs * scene.iters / el
+        if scene.N < LARGE_FRAMES:
+            runs, el = time_oracle(scene, budget_s=10.0)
+            cv = runs * scene.iters / el
+            sample = f"{runs} full runs of the workload ({scene.iters} GN iterations each)"
+        else:  # the oracle iteration of the error check above
+            cv, el = err_iters / t_or, t_or
+            sample = f"the first GN iteration of the workload (the error check's)"
         cpu = {"value": cv, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"{runs} full runs of the workload ({scene.iters} GN iterations each), single-threaded "
-                         f"FP64 oracle (-O2) on 1 of {cpu_cores()} host cores, {el:.1f} s"}
+               "sample": f"{sample}, single-threaded FP64 oracle (-O2) on 1 of {cpu_cores()} host cores, {el:.1f} s"}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -619,6 +675,19 @@ def run_batched(args):
 
     dom = max((k for k in prof if prof[k][1] > 0), key=lambda k: prof[k][0])
     t_ms, cnt = prof[dom]
+    Nb = [sc.N for sc in probs]
+    nb = [6 * (m - fixed) for m in Nb]
+    tri_all = sum(m * (m + 1) // 2 for m in nb)
+    sizes = (sum(Nb), int(offs["patch_off"][-1]), E_tot)
+
+    def batch_bytes(k):
+        if k == "assemble":
+            return 28 * sizes[2] + 12 * sizes[1] + 56 * sizes[0] + 4 * tri_all + 4 * sum(nb) + 8 * sizes[1]
+        if k == "solve":
+            return 4 * tri_all + 16 * sum(nb) + 112 * sizes[0]
+        return algorithmic_bytes(k, sizes[0], sizes[1], sizes[2], 0)
+
+    roof = roofline(dom, prof, args.steps, batch_bytes, nb, "batched")
     line = {
         "metric": METRIC, "value": value, "unit": "problem GN it/s", "n_gpus": world, "steps": args.steps,
         "warmup": max(args.warmup, 3), "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -634,6 +703,7 @@ def run_batched(args):
         "error_vs_oracle": err,
         "per_class_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
         "dominant_class": {"kind": dom, "avg_launch_us": t_ms / cnt * 1e3},
+        "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": "problem GN it/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,

@@ -240,11 +240,12 @@ enum {
   BA_KERNEL_PREPROCESS = 0, /* every kernel of ba_set_graph                     */
   BA_KERNEL_INIT = 1,       /* clearing the pose system                          */
   BA_KERNEL_ASSEMBLE = 2,   /* linearisation + block reduction + Schur complement */
-  BA_KERNEL_SOLVE = 3,      /* Cholesky and triangular solves (+ refinement)     */
+  BA_KERNEL_SOLVE = 3,      /* pose-system solves except the large factorisation */
   BA_KERNEL_BACKSUB = 4,    /* inverse-depth back-substitution                   */
   BA_KERNEL_RETRACT = 5,    /* SE(3) retraction                                  */
   BA_KERNEL_ADJOINT = 6,    /* adjoint-only kernels of ba_backward               */
-  BA_KERNEL_CLASSES = 7
+  BA_KERNEL_FACTOR = 7,     /* the persistent factorisation of systems > 256 unknowns */
+  BA_KERNEL_CLASSES = 8
 };
 
 /* on != 0: from now on record a CUDA event pair around every launch of each

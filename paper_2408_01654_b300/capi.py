@@ -41,7 +41,7 @@ EXPORTED = [
     "ba_profile_enable", "ba_profile_read", "ba_set_record", "ba_backward", "ba_solve_pose_system_noalloc",
     "ba_set_capture", "ba_autotune", "ba_autotune_clear",
 ]
-KERNEL_CLASSES = ("preprocess", "init", "assemble", "solve", "backsub", "retract", "adjoint")
+KERNEL_CLASSES = ("preprocess", "init", "assemble", "solve", "backsub", "retract", "adjoint", "factor")
 
 
 class BAError(RuntimeError):

@@ -1378,8 +1378,13 @@ ba_status_t dpv_solve_large(ba_handle_t h, int refine) {
     int nsys_ = nsys;
     void* args[] = {(void*)&dprobs, (void*)&nsys_, (void*)&tasks,  (void*)&ntasks,
                     (void*)&ctr,    (void*)&dsm,   (void*)&isolate, (void*)&status, (void*)&timeout};
+    // timed as its own class (inside the solve class's region)
+    dpv_prof_end(h);
+    dpv_prof_begin(h, BA_KERNEL_FACTOR);
     DPV_CUDA(h, launch_cooperative((const void*)k_lg_factor, grid, smem, st, args));
     ++h->launches;
+    dpv_prof_end(h);
+    dpv_prof_begin(h, BA_KERNEL_SOLVE);
   }
   {
     // every resident CTA: the row-block chains use R of them, the products
