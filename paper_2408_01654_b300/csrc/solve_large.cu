@@ -218,9 +218,7 @@ struct LgShared {
   float X[NB * LDS];
   float Y[NB * LDS];
   float Z[NB * LDS];
-  float Li[2][32][33];
-  float W[32][33];
-  __align__(16) float ucol[LG_THREADS / 32][32];  // one column broadcast row per warp
+  __align__(16) float ucol[LG_THREADS / 32][32];  // column broadcast of the diagonal factorisation
   float invd[NB];
   float dd[NB];
   float dprev[NB];  // the previous diagonal step's D and D^-1 (critical-path CTA)
@@ -230,124 +228,84 @@ struct LgShared {
   int bad;
 };
 
-// LDL^T of the 32 x 32 block at (base, base) of Xs (lane = row); writes the
-// unit factor (strict lower), D, D^-1 and the inverse of the unit factor Li
-// (lane = column).  Every warp runs the same elimination on its own broadcast
-// row and only warp 0 stores the results: a CTA barrier after a phase in
-// which one warp worked and seven waited measured ~5x slower single-warp
-// phases afterwards on this part.  Returns false on a non-positive pivot.
-__device__ __noinline__ bool factor32(LgShared& sm, int base, float (*Li)[33]) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const bool w0 = wid == 0;
+// LDL^T of the 64 x 64 diagonal tile in sm.X (lower part) by warps 0 and 1
+// (threads 0..63, lane = row r): column c is broadcast through shared memory
+// (double-buffered by the parity of c, so one 64-thread named barrier per
+// column suffices: a buffer is rewritten two columns later, after every
+// thread passed the barrier in between) and each row updates its entries
+// right of c.  Writes the unit factor (strict lower) back to sm.X, D and D^-1
+// to sm.dd / sm.invd, then the inverse of the unit factor (lane = column,
+// forward substitution) to li (global) and sm.Y.  Returns false on a
+// non-positive pivot.
+__device__ __noinline__ bool factor64(LgShared& sm, float* li) {
+  const int r = threadIdx.x;  // < 64
   float* Xs = sm.X;
-  float* ucol = sm.ucol[wid];
-  float a[32];
+  float(*buf)[NB] = reinterpret_cast<float(*)[NB]>(&sm.ucol[0][0]);
+  float a[NB];
 #pragma unroll
-  for (int c = 0; c < 32; ++c) a[c] = c <= lane ? Xs[(base + lane) * LDS + base + c] : 0.f;
+  for (int c = 0; c < NB; ++c) a[c] = c <= r ? Xs[r * LDS + c] : 0.f;
   bool ok = true;
 #pragma unroll
-  for (int c = 0; c < 32; ++c) {
-    ucol[lane] = a[c];
-    __syncwarp();
-    const float d = ucol[c];
+  for (int c = 0; c < NB; ++c) {
+    float* u = buf[c & 1];
+    u[r] = a[c];
+    asm volatile("bar.sync 1, 64;" ::: "memory");
+    const float d = u[c];
     ok = ok && (d > 0.f);
     float inv;  // approximate reciprocal: the refinement absorbs its last-bit error
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(inv) : "f"(d));
     const float l = a[c] * inv;
-    float u[32];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const float4 v = reinterpret_cast<const float4*>(ucol)[q];
-      u[4 * q] = v.x; u[4 * q + 1] = v.y; u[4 * q + 2] = v.z; u[4 * q + 3] = v.w;
+    for (int q = (c + 1) / 4; q < NB / 4; ++q) {
+      const float4 v = reinterpret_cast<const float4*>(u)[q];
+      if (4 * q > c) a[4 * q] = fmaf(-l, v.x, a[4 * q]);
+      if (4 * q + 1 > c) a[4 * q + 1] = fmaf(-l, v.y, a[4 * q + 1]);
+      if (4 * q + 2 > c) a[4 * q + 2] = fmaf(-l, v.z, a[4 * q + 2]);
+      if (4 * q + 3 > c) a[4 * q + 3] = fmaf(-l, v.w, a[4 * q + 3]);
     }
-#pragma unroll
-    for (int j = c + 1; j < 32; ++j) a[j] = fmaf(-l, u[j], a[j]);
-    if (w0 && lane == c) {
-      sm.invd[base + c] = inv;
-      sm.dd[base + c] = d;
+    if (r == c) {
+      sm.invd[c] = inv;
+      sm.dd[c] = d;
     }
-    if (lane > c) a[c] = l;
-    __syncwarp();
+    if (r > c) a[c] = l;
   }
-  // every warp has read the block before warp 0 overwrites it
-  __syncthreads();
-  if (w0) {
 #pragma unroll
-    for (int c = 0; c < 32; ++c)
-      if (c < lane) Xs[(base + lane) * LDS + base + c] = a[c];
-  }
-  __syncthreads();
-  float x[32];
+  for (int c = 0; c < NB; ++c)
+    if (c < r) Xs[r * LDS + c] = a[c];
+  asm volatile("bar.sync 1, 64;" ::: "memory");
+  // inverse of the unit lower factor: column r, x_i = -sum_{k<i} L_ik x_k
+  float x[NB];
 #pragma unroll
-  for (int i = 0; i < 32; ++i) x[i] = (i == lane) ? 1.f : 0.f;
+  for (int i = 0; i < NB; ++i) x[i] = (i == r) ? 1.f : 0.f;
 #pragma unroll
-  for (int k = 0; k < 31; ++k)
+  for (int k = 0; k < NB - 1; ++k)
 #pragma unroll
-    for (int i = k + 1; i < 32; ++i) x[i] = fmaf(-Xs[(base + i) * LDS + base + k], x[k], x[i]);
-  if (w0) {
+    for (int i = k + 1; i < NB; ++i) x[i] = fmaf(-Xs[i * LDS + k], x[k], x[i]);
 #pragma unroll
-    for (int i = 0; i < 32; ++i) Li[i][lane] = x[i];
+  for (int i = 0; i < NB; ++i) {
+    li[i * NB + r] = x[i];
+    sm.Y[i * LDS + r] = x[i];
   }
   return ok;
 }
 
-// DIAG(k): the 64 x 64 diagonal tile as two 32-column steps, then the inverse
-// of the unit factor [[Li0, 0], [-Li1 L10 Li0, Li1]].
-// The tile is in sm.X (lower part); the inverse also stays in sm.Y and D, D^-1
-// in sm.dprev / sm.iprev for the next step.
+// DIAG(k): the 64 x 64 diagonal tile (in sm.X, lower part) factored by
+// factor64; the unit factor goes to tile (k, k), its inverse to Linv (and
+// stays in sm.Y), D and D^-1 to global and to sm.dprev / sm.iprev for the
+// next step.
 __device__ bool factor_diag(LgShared& sm, float* A, float* Linv, float* D, float* invD, int k) {
   const int tid = threadIdx.x;
   float* tk = tile_ptr(A, k, k);
   if (tid == 0) sm.bad = 0;
   __syncthreads();
-  if (!factor32(sm, 0, sm.Li[0]) && tid == 0) sm.bad = 1;
-  __syncthreads();
-  // panel rows 32..63: W = A10 Li0^T (unscaled), L10 = W D0^-1
-  for (int t = tid; t < 32 * 32; t += LG_THREADS) {
-    const int r = t >> 5, c = t & 31;
-    float w = 0.f;
-    for (int q = 0; q <= c; ++q) w = fmaf(sm.X[(32 + r) * LDS + q], sm.Li[0][c][q], w);
-    sm.W[r][c] = w;
+  if (tid < NB) {
+    const bool ok = factor64(sm, Linv + (size_t)k * TILE);
+    if (!ok && tid == 0) sm.bad = 1;
   }
-  __syncthreads();
-  for (int t = tid; t < 32 * 32; t += LG_THREADS) {
-    const int r = t >> 5, c = t & 31;
-    sm.X[(32 + r) * LDS + c] = sm.W[r][c] * sm.invd[c];
-  }
-  // trailing 32 x 32: A11 -= W D0^-1 W^T (lower)
-  for (int t = tid; t < 32 * 32; t += LG_THREADS) {
-    const int r = t >> 5, s = t & 31;
-    if (s > r) continue;
-    float acc = 0.f;
-#pragma unroll 8
-    for (int c = 0; c < 32; ++c) acc = fmaf(sm.W[r][c] * sm.invd[c], sm.W[s][c], acc);
-    sm.X[(32 + r) * LDS + 32 + s] -= acc;
-  }
-  __syncthreads();
-  if (!factor32(sm, 32, sm.Li[1]) && tid == 0) sm.bad = 1;
   __syncthreads();
   if (sm.bad) return false;
-  // off-diagonal block of the inverse: -Li1 (L10 Li0); W <- L10 Li0 first
-  for (int t = tid; t < 32 * 32; t += LG_THREADS) {
-    const int r = t >> 5, c = t & 31;
-    float v = 0.f;
-    for (int q = c; q < 32; ++q) v = fmaf(sm.X[(32 + r) * LDS + q], sm.Li[0][q][c], v);
-    sm.W[r][c] = v;
-  }
-  __syncthreads();
-  float* li = Linv + (size_t)k * TILE;
   for (int t = tid; t < TILE; t += LG_THREADS) {
     const int r = t >> 6, c = t & 63;
-    float v = 0.f;
-    if (r < 32) {
-      v = c < 32 && c <= r ? sm.Li[0][r][c] : 0.f;
-    } else if (c >= 32) {
-      v = c <= r ? sm.Li[1][r - 32][c - 32] : 0.f;
-    } else {
-      for (int q = 0; q <= r - 32; ++q) v = fmaf(-sm.Li[1][r - 32][q], sm.W[q][c], v);
-    }
-    li[t] = v;
-    sm.Y[r * LDS + c] = v;
     tk[t] = c < r ? sm.X[r * LDS + c] : (c == r ? 1.f : 0.f);
   }
   if (tid < NB) {
@@ -626,7 +584,7 @@ __global__ void k_lg_convert(const LgProb* __restrict__ probs, const int* status
 // type << 30 | k << 20 | i << 10 | j; an update covers row tiles i and i+1).
 // Every CTA that stays holds TC_COLS tensor-memory columns, released on every
 // way out once its MMAs have completed.
-__global__ void __maxnreg__(120) k_lg_factor(const LgProb* __restrict__ probs, int nsys,
+__global__ void __launch_bounds__(LG_THREADS, 1) k_lg_factor(const LgProb* __restrict__ probs, int nsys,
                                                           const unsigned long long* __restrict__ tasks, int ntasks,
                                                           int* ctr, int* dsm, int isolate, int* status,
                                                           long long timeout) {
