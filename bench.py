@@ -373,7 +373,7 @@ def run_ours(args):
     total_ms = sum(step_ms)
     prof = ba.profile_read()
     launches = ba.info()["launches"] - launches0
-    replays = ba.info()["graph_replays"]
+    replays = {"ba_step": ba.info()["graph_replays"], "binding": ba.info()["bind_replays"]}
     if dist:
         t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -575,7 +575,7 @@ def run_batched(args):
     total_ms = sum(step_ms)
     prof = ba.profile_read()
     launches = ba.info()["launches"] - launches0
-    replays = ba.info()["graph_replays"]
+    replays = {"ba_step": ba.info()["graph_replays"], "binding": ba.info()["bind_replays"]}
     if dist:
         t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)

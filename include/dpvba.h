@@ -147,18 +147,20 @@ DPVBA_API ba_status_t ba_step(ba_handle_t h, int iters, int fixed_poses);
 
 /* ---- batched execution patterns ------------------------------------------
  *
- * on != 0: replay ba_step from a captured CUDA graph.  The first call for a
- * configuration (binding pointers, sizes and offsets, workspace allocation,
- * iters, fixed_poses, profiling on/off, stream) runs eagerly and sizes the
- * workspace; the second captures the step on a private stream; later calls
- * launch the graph on the handle's stream (one graph launch per ba_step).
- * Rebinding the same buffers with the same sizes (new contents) keeps the
- * graph.  Steps that record a tape (ba_set_record) run eagerly.  A step the
- * runtime cannot capture keeps running eagerly for its configuration
- * (ba_debug_info reports captures and replays).  With profiling on, each
- * replay's event times are read before the next replay, which then waits on
- * the host for the previous one to finish.  on == 0 releases the graph
- * (synchronises). */
+ * on != 0: replay ba_step, and the device work of ba_set_graph /
+ * ba_set_graph_batched (validation, sort, grouping), from captured CUDA
+ * graphs.  The first call for a configuration (binding pointers, sizes and
+ * offsets, workspace allocation, iters, fixed_poses, profiling on/off,
+ * stream) runs eagerly and sizes the workspace; the second captures the work
+ * on a private stream; later calls launch the graph on the handle's stream
+ * (one graph launch per call).  Rebinding the same buffers with the same
+ * sizes (new contents) keeps both graphs; the intrinsics are copied outside
+ * the graph on every binding.  Steps that record a tape (ba_set_record) run
+ * eagerly.  Work the runtime cannot capture keeps running eagerly for its
+ * configuration (ba_debug_info reports captures and replays).  With
+ * profiling on, each replay's event times are read before the next replay of
+ * the same graph, which then waits on the host for the previous one to
+ * finish.  on == 0 releases the graphs (synchronises). */
 DPVBA_API ba_status_t ba_set_capture(ba_handle_t h, int on);
 
 /* Autotune the patch-group size (patches reduced by one CTA of the assembly
@@ -223,9 +225,10 @@ enum {
 DPVBA_API ba_status_t ba_debug_export(ba_handle_t h, int what, void* dst, long long bytes);
 
 /* Host integers describing the bound graph:
- * info[0..11] = N, P, E, patches_per_group, groups, n (last fixed), tile size, runs,
- * kernels launched by the handle so far, CUDA-graph captures, graph replays,
- * kernels in one replay. */
+ * info[0..14] = N, P, E, patches_per_group, groups, n (last fixed), tile size, runs,
+ * kernels launched by the handle so far; then for the CUDA graphs of
+ * ba_set_capture: ba_step captures, replays, kernels in one replay, and the
+ * same three for the binding's device work (ba_set_graph*). */
 DPVBA_API ba_status_t ba_debug_info(ba_handle_t h, long long* info, int cap);
 
 /* Canonical pose-pose block keys of the B part of the system, computed on the

@@ -146,10 +146,10 @@ class DPVBA:
         capi.check(self._h, self._lib.ba_linearize(self._h, fixed))
 
     def info(self) -> dict:
-        arr = (ctypes.c_longlong * 12)()
-        capi.check(self._h, self._lib.ba_debug_info(self._h, arr, 12))
+        arr = (ctypes.c_longlong * 15)()
+        capi.check(self._h, self._lib.ba_debug_info(self._h, arr, 15))
         keys = ("N", "P", "E", "G", "groups", "n", "tile", "runs", "launches", "graph_captures", "graph_replays",
-                "graph_kernels")
+                "graph_kernels", "bind_captures", "bind_replays", "bind_kernels")
         return dict(zip(keys, list(arr)))
 
     def export(self, what: int, count: int | None = None) -> torch.Tensor:

@@ -34,7 +34,7 @@ void dpv_prof_begin(ba_handle_t h, int kind) {
   if (!h->prof_on) return;
   cudaEvent_t a = pool_event(h), b = pool_event(h);
   if (!a || !b) return;
-  std::vector<ba_handle_s::ProfRec>& list = h->capturing ? h->gprof : h->prof;
+  std::vector<ba_handle_s::ProfRec>& list = h->capturing ? *h->cap_prof : h->prof;
   if (h->capturing)
     cudaEventRecordWithFlags(a, h->stream, cudaEventRecordExternal);
   else
@@ -46,7 +46,7 @@ void dpv_prof_begin(ba_handle_t h, int kind) {
 void dpv_prof_end(ba_handle_t h) {
   if (!h->prof_on || h->prof_open < 0) return;
   if (h->capturing)
-    cudaEventRecordWithFlags(h->gprof[h->prof_open].b, h->stream, cudaEventRecordExternal);
+    cudaEventRecordWithFlags((*h->cap_prof)[h->prof_open].b, h->stream, cudaEventRecordExternal);
   else
     cudaEventRecord(h->prof[h->prof_open].b, h->stream);
   h->prof_open = -1;
@@ -60,13 +60,13 @@ static void prof_release(ba_handle_t h, std::vector<ba_handle_s::ProfRec>& list)
   list.clear();
 }
 
-// Add the event times of the last replay to the totals (waits for that replay).
-static ba_status_t prof_harvest(ba_handle_t h) {
-  if (!h->gprof_pending) return BA_OK;
-  h->gprof_pending = 0;
-  if (h->gprof.empty()) return BA_OK;
-  DPV_CUDA(h, cudaEventSynchronize(h->gprof.back().b));
-  for (auto& r : h->gprof) {
+// Add the event times of a graph's last replay to the totals (waits for that replay).
+static ba_status_t prof_harvest(ba_handle_t h, ba_handle_s::CapGraph& g) {
+  if (!g.pending) return BA_OK;
+  g.pending = 0;
+  if (g.prof.empty()) return BA_OK;
+  DPV_CUDA(h, cudaEventSynchronize(g.prof.back().b));
+  for (auto& r : g.prof) {
     float ms = 0.f;
     DPV_CUDA(h, cudaEventElapsedTime(&ms, r.a, r.b));
     h->prof_ms[r.kind] += ms;
@@ -75,23 +75,98 @@ static ba_status_t prof_harvest(ba_handle_t h) {
   return BA_OK;
 }
 
+static ba_status_t prof_harvest_all(ba_handle_t h) {
+  ba_status_t s = prof_harvest(h, h->bind_graph);
+  if (!s) s = prof_harvest(h, h->step_graph);
+  return s;
+}
+
 static void prof_clear(ba_handle_t h) {
   prof_release(h, h->prof);
   h->prof_open = -1;
-  h->gprof_pending = 0;
+  h->step_graph.pending = 0;
+  h->bind_graph.pending = 0;
   for (int k = 0; k < BA_KERNEL_CLASSES; ++k) {
     h->prof_ms[k] = 0.0;
     h->prof_n[k] = 0;
   }
 }
 
-static void graph_drop(ba_handle_t h) {
-  if (h->gexec) cudaGraphExecDestroy(h->gexec);
-  h->gexec = nullptr;
-  h->gprof_pending = 0;
-  prof_release(h, h->gprof);
-  h->gkey_valid = 0;
-  h->gkey_failed = 0;
+static void graph_drop(ba_handle_t h, ba_handle_s::CapGraph& g) {
+  if (g.exec) cudaGraphExecDestroy(g.exec);
+  g.exec = nullptr;
+  g.pending = 0;
+  prof_release(h, g.prof);
+  g.valid = 0;
+  g.failed = 0;
+}
+
+static bool same_key(const ba_handle_s::GraphKey& a, const ba_handle_s::GraphKey& b) {
+  return a.bind_gen == b.bind_gen && a.ws_gen == b.ws_gen && a.iters == b.iters && a.fixed == b.fixed &&
+         a.prof == b.prof && a.stream == b.stream;
+}
+
+// Run `body` (work enqueued on h->stream) through the captured graph g.  The
+// graph holds pointers and sizes, so it is keyed (binding, workspace
+// allocation, iteration count, fixed poses, profiling, stream).  The first
+// call of a key runs eagerly (it sizes the workspace and uploads tables,
+// which a capture may not do); the second captures the body on a private
+// stream; later calls launch the graph on the handle's stream.  A body that
+// cannot be captured keeps running eagerly for that key.
+template <class Body>
+static ba_status_t graph_run(ba_handle_t h, ba_handle_s::CapGraph& g, const ba_handle_s::GraphKey& key, Body body) {
+  ba_status_t s;
+  if (!g.valid || !same_key(g.key, key)) {
+    if (g.exec || g.pending) {  // the old graph may still run: finish it first
+      DPV_CUDA(h, cudaStreamSynchronize(h->stream));
+      if ((s = prof_harvest(h, g))) return s;
+    }
+    graph_drop(h, g);
+    g.key = key;
+    g.valid = 1;
+    return body();
+  }
+  if (!g.exec) {
+    if (g.failed) return body();
+    if (!h->cap_stream) DPV_CUDA(h, cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+    const cudaStream_t user = h->stream;
+    const long long l0 = h->launches;
+    cudaGraph_t gr = nullptr;
+    cudaGraphExec_t ex = nullptr;
+    s = BA_OK;
+    h->stream = h->cap_stream;
+    cudaError_t e = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      h->capturing = 1;
+      h->cap_prof = &g.prof;
+      s = body();
+      h->capturing = 0;
+      h->cap_prof = nullptr;
+      e = cudaStreamEndCapture(h->cap_stream, &gr);
+    }
+    h->stream = user;
+    if (e == cudaSuccess && s == BA_OK && gr) e = cudaGraphInstantiate(&ex, gr, 0);
+    if (gr) cudaGraphDestroy(gr);
+    if (e != cudaSuccess || s != BA_OK || !ex) {
+      cudaGetLastError();
+      prof_release(h, g.prof);
+      h->prof_open = -1;
+      h->launches = l0;
+      g.failed = 1;
+      return body();
+    }
+    g.exec = ex;
+    g.kernels = h->launches - l0;
+    h->launches = l0;
+    ++g.captures;
+  }
+  // the previous replay's event times are read before the events are recorded again
+  if ((s = prof_harvest(h, g))) return s;
+  DPV_CUDA(h, cudaGraphLaunch(g.exec, h->stream));
+  h->launches += g.kernels;
+  ++g.replays;
+  g.pending = g.prof.empty() ? 0 : 1;
+  return BA_OK;
 }
 
 // Record the binding's signature; a change invalidates the captured step.
@@ -142,6 +217,16 @@ int auto_group(ba_handle_t h, long long P, long long E, int batched) {
   if ((long long)P >= 32LL * 2 * h->num_sms) return 32;
   if ((long long)P >= 8LL * h->num_sms) return 16;
   return 8;
+}
+
+// One bound problem: every frame and group belongs to problem 0, the frame
+// offsets {0, N} follow the per-frame entries; clears the device status.
+__global__ void k_single_problem(int N, int* __restrict__ fprob, int Gn, int* __restrict__ gprob, int* status) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q <= N) fprob[q] = 0;
+  if (q == N + 1) fprob[q] = N;
+  if (q < Gn) gprob[q] = 0;
+  if (q == 0) *status = 0;
 }
 
 // problem of index x for non-decreasing offsets off[0..B] (largest b with off[b] <= x)
@@ -350,7 +435,8 @@ ba_status_t ba_destroy(ba_handle_t h) {
     release(ws->offs); release(ws->pcopy);
     delete ws;
   }
-  graph_drop(h);
+  graph_drop(h, h->step_graph);
+  graph_drop(h, h->bind_graph);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   prof_clear(h);
   for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
@@ -370,10 +456,11 @@ ba_status_t ba_profile_enable(ba_handle_t h, int on) {
 
 ba_status_t ba_set_capture(ba_handle_t h, int on) {
   if (!h) return BA_ERR_INVALID_ARG;
-  if (!on && h->gexec) {
+  if (!on && (h->step_graph.exec || h->bind_graph.exec)) {
     DPV_CUDA(h, cudaStreamSynchronize(h->stream));
-    ba_status_t s = prof_harvest(h);
-    graph_drop(h);
+    ba_status_t s = prof_harvest_all(h);
+    graph_drop(h, h->step_graph);
+    graph_drop(h, h->bind_graph);
     if (s) return s;
   }
   h->capture_on = on ? 1 : 0;
@@ -383,7 +470,7 @@ ba_status_t ba_set_capture(ba_handle_t h, int on) {
 ba_status_t ba_profile_read(ba_handle_t h, int kind, double* total_ms, long long* launches) {
   if (!h || !total_ms || !launches || kind < 0 || kind >= BA_KERNEL_CLASSES) return BA_ERR_INVALID_ARG;
   DPV_CUDA(h, cudaStreamSynchronize(h->stream));
-  ba_status_t s = prof_harvest(h);
+  ba_status_t s = prof_harvest_all(h);
   if (s) return s;
   double t = h->prof_ms[kind];
   long long c = h->prof_n[kind];
@@ -448,7 +535,8 @@ ba_status_t ba_set_graph(ba_handle_t h, int N, int P, int E, double* poses, floa
   h->ngroups = (P + h->G - 1) / h->G;
   if (!same_frames) h->fixed = -1;
   bind_signature(h, {1, N, P, E, (long long)(uintptr_t)poses, (long long)(uintptr_t)patches,
-                     (long long)(uintptr_t)targets, (long long)(uintptr_t)weights, h->G});
+                     (long long)(uintptr_t)targets, (long long)(uintptr_t)weights, (long long)(uintptr_t)ii,
+                     (long long)(uintptr_t)jj, (long long)(uintptr_t)kk, h->G});
   h->tape_valid = 0;
   h->kk_bits = bits_for((unsigned long long)P);
   ba_status_t s;
@@ -468,15 +556,24 @@ ba_status_t ba_set_graph(ba_handle_t h, int N, int P, int E, double* poses, floa
       (s = dpv_grow(h, ws->pterm, 4 * En, "edge depth terms")) || (s = dpv_grow(h, ws->posef, (long long)DPV_POSE_ROW * N, "pose table")) ||
       (s = dpv_grow(h, ws->fprob, (long long)N + 2, "frame problems")) || (s = dpv_grow(h, ws->gprob, Gn, "group problems")))
     return s;
-  // one problem: every frame and group belongs to problem 0; frame_off = {0, N} follows fprob
-  DPV_CUDA(h, cudaMemsetAsync(ws->fprob.p, 0, sizeof(int) * N, h->stream));
-  DPV_CUDA(h, cudaMemcpyAsync(ws->fprob.p + N, h->frame_off.data(), sizeof(int) * 2, cudaMemcpyHostToDevice, h->stream));
-  DPV_CUDA(h, cudaMemsetAsync(ws->gprob.p, 0, sizeof(int) * Gn, h->stream));
-  DPV_CUDA(h, cudaMemsetAsync(ws->status, 0, sizeof(int), h->stream));
+  // the intrinsics may live in host memory: copied outside any graph
   DPV_CUDA(h, cudaMemcpyAsync(ws->intr, intrinsics, 4 * sizeof(float), cudaMemcpyDefault, h->stream));
-  dpv_prof_begin(h, BA_KERNEL_PREPROCESS);
-  s = dpv_preprocess(h, ii, jj, kk);
-  dpv_prof_end(h);
+  auto device_work = [&]() -> ba_status_t {
+    // one problem: every frame and group belongs to problem 0; frame_off = {0, N} follows fprob
+    const int M = std::max(N + 2, (int)Gn);
+    k_single_problem<<<(M + 255) / 256, 256, 0, h->stream>>>(N, ws->fprob.p, (int)Gn, ws->gprob.p, ws->status);
+    ++h->launches;
+    dpv_prof_begin(h, BA_KERNEL_PREPROCESS);
+    ba_status_t r = dpv_preprocess(h, ii, jj, kk);
+    dpv_prof_end(h);
+    return r;
+  };
+  if (h->capture_on) {
+    const ba_handle_s::GraphKey key{h->bind_gen, h->ws_gen, -1, -1, h->prof_on, h->stream};
+    s = graph_run(h, h->bind_graph, key, device_work);
+  } else {
+    s = device_work();
+  }
   if (s) return s;
   h->have_graph = 1;
   return BA_OK;
@@ -566,7 +663,8 @@ ba_status_t ba_set_graph_batched(ba_handle_t h, int B, const long long* frame_of
   h->kk_bits = bits_for((unsigned long long)P);
   {
     std::vector<long long> sig = {2, B, N, P, E, (long long)(uintptr_t)poses, (long long)(uintptr_t)patches,
-                                  (long long)(uintptr_t)targets, (long long)(uintptr_t)weights, G};
+                                  (long long)(uintptr_t)targets, (long long)(uintptr_t)weights,
+                                  (long long)(uintptr_t)ii, (long long)(uintptr_t)jj, (long long)(uintptr_t)kk, G};
     sig.insert(sig.end(), offs.begin(), offs.end());
     bind_signature(h, std::move(sig));
   }
@@ -603,35 +701,48 @@ ba_status_t ba_set_graph_batched(ba_handle_t h, int B, const long long* frame_of
     ws->intr_cap = B;
     ++h->ws_gen;
   }
-  cudaStream_t st = h->stream;
-  DPV_CUDA(h, cudaMemsetAsync(ws->status, 0, sizeof(int), st));
-  DPV_CUDA(h, cudaMemcpyAsync(ws->intr, intrinsics, sizeof(float) * 4 * B, cudaMemcpyDefault, st));
-  DPV_CUDA(h, cudaMemcpyAsync(ws->offs.p, offs.data(), sizeof(long long) * offs.size(), cudaMemcpyHostToDevice, st));
-  // per-frame problem, then the frame offsets (int) after it; per-group problem
-  k_frame_problems<<<(N + 255) / 256, 256, 0, st>>>(N, B, ws->offs.p, ws->fprob.p);
-  ++h->launches;
-  DPV_CUDA(h, cudaMemcpyAsync(ws->fprob.p + N, h->frame_off.data(), sizeof(int) * (B + 1), cudaMemcpyHostToDevice, st));
+  h->patches = padded ? ws->pcopy.p : patches;
+  // the intrinsics may live in host memory: copied outside any graph
+  DPV_CUDA(h, cudaMemcpyAsync(ws->intr, intrinsics, sizeof(float) * 4 * B, cudaMemcpyDefault, h->stream));
   std::vector<int> gp(h->ngroups);
   for (int g = 0, b = 0; g < h->ngroups; ++g) {
     while (b + 1 < B && (long long)g * G >= h->patch_moff[b + 1]) ++b;
     gp[g] = b;
   }
-  if (h->ngroups > 0)
-    DPV_CUDA(h, cudaMemcpyAsync(ws->gprob.p, gp.data(), sizeof(int) * h->ngroups, cudaMemcpyHostToDevice, st));
-  if (padded) {
-    k_patch_copy<<<(unsigned)((27LL * P + 255) / 256), 256, 0, st>>>(P, B, ws->offs.p, patches, ws->pcopy.p, 1);
+  auto device_work = [&]() -> ba_status_t {
+    cudaStream_t st = h->stream;
+    if (!h->capturing) {
+      // offsets, frame offsets and group problems: fixed by the binding's
+      // signature, so a captured binding finds them in place
+      DPV_CUDA(h, cudaMemcpyAsync(ws->offs.p, offs.data(), sizeof(long long) * offs.size(), cudaMemcpyHostToDevice, st));
+      DPV_CUDA(h, cudaMemcpyAsync(ws->fprob.p + N, h->frame_off.data(), sizeof(int) * (B + 1), cudaMemcpyHostToDevice,
+                                  st));
+      if (h->ngroups > 0)
+        DPV_CUDA(h, cudaMemcpyAsync(ws->gprob.p, gp.data(), sizeof(int) * h->ngroups, cudaMemcpyHostToDevice, st));
+    }
+    DPV_CUDA(h, cudaMemsetAsync(ws->status, 0, sizeof(int), st));
+    // per-frame problem (the frame offsets follow it)
+    k_frame_problems<<<(N + 255) / 256, 256, 0, st>>>(N, B, ws->offs.p, ws->fprob.p);
     ++h->launches;
-    h->patches = ws->pcopy.p;
+    if (padded) {
+      k_patch_copy<<<(unsigned)((27LL * P + 255) / 256), 256, 0, st>>>(P, B, ws->offs.p, patches, ws->pcopy.p, 1);
+      ++h->launches;
+    }
+    if (E > 0) {
+      k_remap_edges<<<(E + 255) / 256, 256, 0, st>>>(E, B, ws->offs.p, ii, jj, kk, ws->mii.p, ws->mjj.p, ws->mkk.p);
+      ++h->launches;
+    }
+    dpv_prof_begin(h, BA_KERNEL_PREPROCESS);
+    ba_status_t r = dpv_preprocess(h, ws->mii.p, ws->mjj.p, ws->mkk.p);
+    dpv_prof_end(h);
+    return r;
+  };
+  if (h->capture_on) {
+    const ba_handle_s::GraphKey key{h->bind_gen, h->ws_gen, -1, -1, h->prof_on, h->stream};
+    s = graph_run(h, h->bind_graph, key, device_work);
   } else {
-    h->patches = patches;
+    s = device_work();
   }
-  if (E > 0) {
-    k_remap_edges<<<(E + 255) / 256, 256, 0, st>>>(E, B, ws->offs.p, ii, jj, kk, ws->mii.p, ws->mjj.p, ws->mkk.p);
-    ++h->launches;
-  }
-  dpv_prof_begin(h, BA_KERNEL_PREPROCESS);
-  s = dpv_preprocess(h, ws->mii.p, ws->mjj.p, ws->mkk.p);
-  dpv_prof_end(h);
   if (s) return s;
   h->have_graph = 1;
   return BA_OK;
@@ -688,70 +799,6 @@ static ba_status_t step_body(ba_handle_t h, int run, int fixed_poses) {
   return BA_OK;
 }
 
-// ba_step replayed from a CUDA graph.  The graph holds pointers and sizes, so
-// it is keyed by the binding, the workspace allocation, iters, fixed poses,
-// profiling and the stream.  The first call of a key runs eagerly (it sizes
-// the workspace and uploads the solver tables, which a capture may not do);
-// the second captures the step on a private stream and every later call
-// launches the graph on the handle's stream.  A step that cannot be captured
-// keeps running eagerly for that key.
-static ba_status_t step_graph(ba_handle_t h, int run, int fixed_poses) {
-  const ba_handle_s::GraphKey key{h->bind_gen, h->ws_gen, run, fixed_poses, h->prof_on, h->stream};
-  const ba_handle_s::GraphKey& k = h->gkey;
-  const bool same = h->gkey_valid && k.bind_gen == key.bind_gen && k.ws_gen == key.ws_gen && k.iters == key.iters &&
-                    k.fixed == key.fixed && k.prof == key.prof && k.stream == key.stream;
-  ba_status_t s;
-  if (!same) {
-    if (h->gexec || h->gprof_pending) {  // the old graph may still run: finish it first
-      DPV_CUDA(h, cudaStreamSynchronize(h->stream));
-      if ((s = prof_harvest(h))) return s;
-    }
-    graph_drop(h);
-    h->gkey = key;
-    h->gkey_valid = 1;
-    return step_body(h, run, fixed_poses);
-  }
-  if (!h->gexec) {
-    if (h->gkey_failed) return step_body(h, run, fixed_poses);
-    if (!h->cap_stream) DPV_CUDA(h, cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
-    const cudaStream_t user = h->stream;
-    const long long l0 = h->launches;
-    cudaGraph_t g = nullptr;
-    cudaGraphExec_t ex = nullptr;
-    s = BA_OK;
-    h->stream = h->cap_stream;
-    cudaError_t e = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal);
-    if (e == cudaSuccess) {
-      h->capturing = 1;
-      s = step_body(h, run, fixed_poses);
-      h->capturing = 0;
-      e = cudaStreamEndCapture(h->cap_stream, &g);
-    }
-    h->stream = user;
-    if (e == cudaSuccess && s == BA_OK && g) e = cudaGraphInstantiate(&ex, g, 0);
-    if (g) cudaGraphDestroy(g);
-    if (e != cudaSuccess || s != BA_OK || !ex) {
-      cudaGetLastError();
-      prof_release(h, h->gprof);
-      h->prof_open = -1;
-      h->launches = l0;
-      h->gkey_failed = 1;
-      return step_body(h, run, fixed_poses);
-    }
-    h->gexec = ex;
-    h->glaunches = h->launches - l0;
-    h->launches = l0;
-    ++h->graph_captures;
-  }
-  // the previous replay's event times are read before the events are recorded again
-  if ((s = prof_harvest(h))) return s;
-  DPV_CUDA(h, cudaGraphLaunch(h->gexec, h->stream));
-  h->launches += h->glaunches;
-  ++h->graph_replays;
-  h->gprof_pending = h->gprof.empty() ? 0 : 1;
-  return BA_OK;
-}
-
 ba_status_t ba_step(ba_handle_t h, int iters, int fixed_poses) {
   ba_status_t s = check_step_args(h, fixed_poses);
   if (s) return s;
@@ -765,7 +812,10 @@ ba_status_t ba_step(ba_handle_t h, int iters, int fixed_poses) {
     h->tape_iters_pending = run;
     if ((s = dpv_tape_reserve(h, run))) return s;
   }
-  if (h->capture_on && !h->record && run > 0) return step_graph(h, run, fixed_poses);
+  if (h->capture_on && !h->record && run > 0) {
+    const ba_handle_s::GraphKey key{h->bind_gen, h->ws_gen, run, fixed_poses, h->prof_on, h->stream};
+    return graph_run(h, h->step_graph, key, [&]() { return step_body(h, run, fixed_poses); });
+  }
   return step_body(h, run, fixed_poses);
 }
 
@@ -810,10 +860,11 @@ ba_status_t ba_debug_info(ba_handle_t h, long long* info, int cap) {
     DPV_CUDA(h, cudaMemcpy(gnr.data(), h->ws->gnr.p, sizeof(int) * h->ngroups, cudaMemcpyDeviceToHost));
     for (int v : gnr) nr += v;
   }
-  const long long v[12] = {h->N,  h->P,        h->E,        h->G,         h->ngroups,
-                           h->n,  h->TS,       nr,          h->launches,  h->graph_captures,
-                           h->graph_replays, h->glaunches};
-  for (int q = 0; q < cap && q < 12; ++q) info[q] = v[q];
+  const ba_handle_s::CapGraph &sg = h->step_graph, &bg = h->bind_graph;
+  const long long v[15] = {h->N,        h->P,       h->E,        h->G,        h->ngroups,
+                           h->n,        h->TS,      nr,          h->launches, sg.captures,
+                           sg.replays,  sg.kernels, bg.captures, bg.replays,  bg.kernels};
+  for (int q = 0; q < cap && q < 15; ++q) info[q] = v[q];
   return BA_OK;
 }
 

@@ -93,8 +93,8 @@ struct ba_handle_s {
 
   long long launches = 0;  // kernels launched by this handle so far
 
-  // CUDA-graph replay of ba_step (ba_set_capture)
-  int capture_on = 0;       // replay ba_step from a captured graph
+  // CUDA-graph replay of ba_step and of ba_set_graph's device work (ba_set_capture)
+  int capture_on = 0;       // replay from captured graphs
   int capturing = 0;        // a capture is in progress: allocations and uploads are errors
   long long bind_gen = 0;   // bumped when the binding (pointers, sizes, offsets, group size) changes
   long long ws_gen = 0;     // bumped when a workspace buffer is reallocated
@@ -104,15 +104,19 @@ struct ba_handle_s {
     int iters, fixed, prof;
     cudaStream_t stream;
   };
-  GraphKey gkey{};
-  int gkey_valid = 0;       // gkey describes the current graph (or the run that precedes its capture)
-  int gkey_failed = 0;      // capturing this key failed: run it eagerly
-  cudaGraphExec_t gexec = nullptr;
-  cudaStream_t cap_stream = nullptr;  // private stream the step is captured on
-  long long glaunches = 0;  // kernels in one replay
-  long long graph_captures = 0, graph_replays = 0;
-  std::vector<ProfRec> gprof;  // event pairs recorded by every replay (profiling on)
-  int gprof_pending = 0;       // a replay's events wait to be read
+  struct CapGraph {
+    GraphKey key{};
+    int valid = 0;          // key describes this graph (or the eager run that precedes its capture)
+    int failed = 0;         // capturing this key failed: run it eagerly
+    cudaGraphExec_t exec = nullptr;
+    long long kernels = 0;  // kernels in one replay
+    std::vector<ProfRec> prof;  // event pairs recorded by every replay (profiling on)
+    int pending = 0;            // a replay's events wait to be read
+    long long captures = 0, replays = 0;
+  };
+  CapGraph step_graph, bind_graph;
+  std::vector<ProfRec>* cap_prof = nullptr;  // where event records go while capturing
+  cudaStream_t cap_stream = nullptr;         // private stream the captures run on
   double prof_ms[BA_KERNEL_CLASSES] = {};
   long long prof_n[BA_KERNEL_CLASSES] = {};
 

@@ -466,7 +466,11 @@ ba_status_t dpv_preprocess(ba_handle_t h, const int* ii, const int* jj, const in
     const int nwords = (N + 31) / 32;
     const size_t smem = sizeof(unsigned) * nwords + sizeof(int) * nwords;
     if (smem > 160 * 1024) return dpv_fail(h, BA_ERR_UNSUPPORTED, "too many frames for the window kernel");
-    DPV_CUDA(h, cudaFuncSetAttribute(k_group_build, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    static size_t smem_set = 0;  // raised once (not inside a graph capture of a later binding)
+    if (smem > smem_set) {
+      DPV_CUDA(h, cudaFuncSetAttribute(k_group_build, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      smem_set = smem;
+    }
     k_group_build<<<h->ngroups, 256, smem, st>>>(N, G, ws->gptr.p, perm0, ws->unsorted, ii, jj, kk, ws->win.p,
                                                  ws->wlen.p, ws->perm.p, ws->eslot.p, ws->pmpos.p, ws->grun.p,
                                                  ws->gnr.p, ws->status);

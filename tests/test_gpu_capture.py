@@ -38,6 +38,15 @@ def close(a, b):
     assert np.allclose(da, db, rtol=1e-6, atol=0)
 
 
+def steady(ba, before, step=True):
+    """one more call replayed both graphs (the step's only if `step`) and captured nothing"""
+    now = ba.info()
+    assert now["bind_replays"] == before["bind_replays"] + 1, (before, now)
+    assert now["graph_replays"] == before["graph_replays"] + (1 if step else 0), (before, now)
+    assert now["bind_captures"] == before["bind_captures"] and now["graph_captures"] == before["graph_captures"]
+    return now
+
+
 def run_calls(ba, T, pristine, calls, iters, fixed, batched_offs=None):
     """`calls` times: restore the state, rebind the same buffers, step."""
     for _ in range(calls):
@@ -60,9 +69,11 @@ def test_capture_odometry_matches_eager():
     run_calls(eager, Te, pristine, 1, s.iters, s.fixed)
     g = DPVBA(capture=True)
     run_calls(g, T0, pristine, 4, s.iters, s.fixed)
-    inf = g.info()
-    assert inf["graph_captures"] == 1 and inf["graph_replays"] == 3, inf
-    assert inf["graph_kernels"] > 0
+    before = g.info()
+    run_calls(g, T0, pristine, 1, s.iters, s.fixed)
+    inf = steady(g, before)
+    assert inf["graph_captures"] == 1 and inf["bind_captures"] == 1, inf
+    assert inf["graph_kernels"] > 0 and inf["bind_kernels"] > 0
     close(T0, Te)
     # the replayed step against the oracle
     want = oracle.gn_steps(s, iters=s.iters)[-1]
@@ -84,8 +95,9 @@ def test_capture_batched_with_large_systems_matches_oracle():
     run_calls(eager, Te, pristine, 1, 1, 2, offs)
     g = DPVBA(precision="mixed", capture=True)
     run_calls(g, T, pristine, 3, 1, 2, offs)
-    inf = g.info()
-    assert inf["graph_captures"] == 1 and inf["graph_replays"] == 2, inf
+    before = g.info()
+    run_calls(g, T, pristine, 1, 1, 2, offs)
+    steady(g, before)
     close(T, Te)
     for b, sc in enumerate(probs):
         want = oracle.gn_steps(sc, iters=1)[0]
@@ -101,8 +113,8 @@ def test_capture_follows_new_contents_and_rekeys():
     T = scene_tensors(s)
     pristine = {k: v.clone() for k, v in T.items()}
     g = DPVBA(capture=True)
-    run_calls(g, T, pristine, 3, s.iters, s.fixed)
-    assert g.info()["graph_captures"] == 1
+    run_calls(g, T, pristine, 4, s.iters, s.fixed)
+    before = g.info()
     # new contents in the same buffers: the graph is kept and follows them
     gen = torch.Generator(device="cpu").manual_seed(5)
     new = {k: v.clone() for k, v in pristine.items()}
@@ -112,23 +124,25 @@ def test_capture_follows_new_contents_and_rekeys():
         pristine[k].copy_(new[k])
         T[k].copy_(new[k])
     run_calls(g, T, pristine, 1, s.iters, s.fixed)
-    assert g.info()["graph_captures"] == 1 and g.info()["graph_replays"] == 3
+    steady(g, before)
     Te = {k: v.clone() for k, v in new.items()}
     e = DPVBA()
     run_calls(e, Te, {k: v.clone() for k, v in new.items()}, 1, s.iters, s.fixed)
     close(T, Te)
-    # another iteration count is another graph (eager first, then captured)
+    # another iteration count is another step graph (eager first, then captured)
     run_calls(g, T, pristine, 2, 1, s.fixed)
     assert g.info()["graph_captures"] == 2
-    # recording a tape runs eagerly
+    # recording a tape runs the step eagerly (the binding still replays)
     g.set_record(True)
-    before = g.info()["graph_replays"]
+    before = g.info()
     run_calls(g, T, pristine, 1, 1, s.fixed)
-    assert g.info()["graph_replays"] == before
+    steady(g, before, step=False)
     g.set_record(False)
     g.set_capture(False)
+    before = g.info()
     run_calls(g, T, pristine, 1, 1, s.fixed)
-    assert g.info()["graph_replays"] == before
+    now = g.info()
+    assert now["graph_replays"] == before["graph_replays"] and now["bind_replays"] == before["bind_replays"]
 
 
 def test_capture_profiling_reads_every_replay():
@@ -137,12 +151,14 @@ def test_capture_profiling_reads_every_replay():
     pristine = {k: v.clone() for k, v in T.items()}
     g = DPVBA(capture=True)
     g.profile(True)
-    run_calls(g, T, pristine, 5, s.iters, s.fixed)  # eager, capture + replay, 3 replays
+    run_calls(g, T, pristine, 6, s.iters, s.fixed)  # eager runs, captures, then replays
     prof = g.profile_read()
-    assert g.info()["graph_replays"] == 4
-    # one solve and one back-substitution per iteration in each of the 5 steps
-    assert prof["solve"][1] == 5 * s.iters and prof["backsub"][1] == 5 * s.iters, prof
-    assert prof["solve"][0] > 0 and prof["assemble"][0] > 0
+    assert g.info()["graph_replays"] >= 3 and g.info()["bind_replays"] >= 3
+    # one solve and one back-substitution per iteration in each of the 6 steps, one
+    # preprocessing pass per binding, whether eager, captured or replayed
+    assert prof["solve"][1] == 6 * s.iters and prof["backsub"][1] == 6 * s.iters, prof
+    assert prof["preprocess"][1] == 6, prof
+    assert prof["solve"][0] > 0 and prof["assemble"][0] > 0 and prof["preprocess"][0] > 0
 
 
 def test_autotune_keeps_state_and_fills_table():
