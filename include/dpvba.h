@@ -79,7 +79,11 @@ typedef struct {
   float z_min;             /* minimum depth in frame j, metres (0.1)              */
   float d_min;             /* lower clamp of inverse depth after a step (1e-3)    */
   int patches_per_group;   /* patches per reduction group; 0 = automatic          */
-  int max_refine;          /* FP64 refinement sweeps in BA_MIXED (default 2)      */
+  int max_refine;          /* FP64 refinement sweeps in BA_MIXED (default 2) for
+                              systems <= 256 unknowns; larger systems run up to
+                              max(8, max_refine) conjugate-gradient iterations
+                              preconditioned by the factor; all stop once the
+                              estimated error left in the step is < 1e-7 of it */
   long long timeout_cycles;/* bound on any device-side wait (default 2e9 cycles)  */
   void* stream;            /* cudaStream_t for all work; NULL = legacy stream      */
 } ba_options_t;

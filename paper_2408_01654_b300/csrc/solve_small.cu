@@ -16,10 +16,10 @@
 //      output (no dependency chain);
 //   4. all threads apply the rank-32 update to the trailing triangle in 4x4
 //      register tiles.
-// The block inverses also turn the triangular solves into 32-row block
-// matrix-vector products instead of 32-step dependency chains.  The
-// retraction of the poses runs in the back-substitution kernel, off this
-// single-CTA critical path.
+// The triangular solves of the refinement run left-looking in warp 0 (lane =
+// row of a 32-row block): the rows above (below) enter as a dot product, the
+// diagonal block through its inverse.  The retraction of the poses runs in
+// the back-substitution kernel, off this single-CTA critical path.
 //
 // Equilibration: the FP32 copies are scaled to S' = diag(s) S diag(s) with
 // s = diag(S)^-1/2 (unit diagonal), which bounds the factorisation error by the
@@ -28,10 +28,11 @@
 // The solve works on z = x / s and returns x = s z.
 //
 // Refinement: sweeps of x += S^-1 (y - S x) with the same factor, until the
-// correction is below 1e-7 of the solution.  In BA_FP32 the sweeps compute the
-// residual in compensated FP32 (TwoProd / TwoSum) from the FP32 copy of S,
-// which removes the factorisation error; in BA_MIXED they compute it in FP64
-// from the FP64 S.
+// estimated error left in x is below 1e-7 of it (the correction c_s, or
+// rho c_s with the contraction rho ~ c_s / c_{s-1}).  In BA_FP32 the sweeps
+// compute the residual in compensated FP32 (TwoProd / TwoSum) from the FP32
+// copy of S, which removes the factorisation error; in BA_MIXED they compute
+// it in FP64 from the FP64 S.
 #include "internal.cuh"
 
 #include <algorithm>
