@@ -48,6 +48,7 @@ constexpr int TASK_PANEL = 1, TASK_UPDATE = 2;  // worker task types (the diagon
 constexpr int LG_MAX_T = 1023;  // tiles per dimension (10-bit task fields)
 
 static_assert(NB == DPV_TILE, "the large solver works on the assembly's tiles");
+static_assert(LG_THREADS == 256, "thread layouts of the tile tasks assume 256 threads");
 
 __host__ __device__ inline int tri2(int r) { return r * (r + 1) / 2; }
 __host__ __device__ inline unsigned pack_task(int type, int k, int i, int j) {
@@ -196,7 +197,8 @@ __device__ __forceinline__ void gemm_nt(const float* X, const float* Y, const fl
 // TF32 part and the FP32 rest, each written as one 16 KB operand in the
 // K-major core-matrix layout of the tensor cores: 16-byte slot q holds row
 // 8 (q >> 7) + (q & 7), columns 4 ((q >> 3) & 15) .. +3.  Coalesced stores.
-__device__ __forceinline__ void store_g(const float* Ls, const float* sq, float* g) {
+__device__ __forceinline__ void store_g(const float* Ls, const float* sq, float* g, unsigned char* shi = nullptr,
+                                        unsigned char* slo = nullptr) {
 #pragma unroll
   for (int u = 0; u < TILE / 4 / LG_THREADS; ++u) {
     const int q = threadIdx.x + u * LG_THREADS;
@@ -204,8 +206,13 @@ __device__ __forceinline__ void store_g(const float* Ls, const float* sq, float*
     float h[4], l[4];
 #pragma unroll
     for (int e = 0; e < 4; ++e) tc_split(Ls[row * LDS + k0 + e] * sq[k0 + e], h[e], l[e]);
-    reinterpret_cast<float4*>(g)[q] = make_float4(h[0], h[1], h[2], h[3]);
-    reinterpret_cast<float4*>(g + TILE)[q] = make_float4(l[0], l[1], l[2], l[3]);
+    const float4 hv = make_float4(h[0], h[1], h[2], h[3]), lv = make_float4(l[0], l[1], l[2], l[3]);
+    reinterpret_cast<float4*>(g)[q] = hv;
+    reinterpret_cast<float4*>(g + TILE)[q] = lv;
+    if (shi) {  // the same operand for this CTA's own tensor cores
+      reinterpret_cast<float4*>(shi)[q] = hv;
+      reinterpret_cast<float4*>(slo)[q] = lv;
+    }
   }
   tc_fence_global();  // the bulk copies that read G run in the async proxy
 }
@@ -229,15 +236,13 @@ struct LgShared {
 };
 
 // LDL^T of the 64 x 64 diagonal tile in sm.X (lower part) by warps 0 and 1
-// (threads 0..63, lane = row r): column c is broadcast through shared memory
-// (double-buffered by the parity of c, so one 64-thread named barrier per
-// column suffices: a buffer is rewritten two columns later, after every
-// thread passed the barrier in between) and each row updates its entries
-// right of c.  Writes the unit factor (strict lower) back to sm.X, D and D^-1
-// to sm.dd / sm.invd, then the inverse of the unit factor (lane = column,
-// forward substitution) to li (global) and sm.Y.  Returns false on a
-// non-positive pivot.
-__device__ __noinline__ bool factor64(LgShared& sm, float* li) {
+// (threads 0..63, lane = row r, the row in registers): column c is broadcast
+// through shared memory (double-buffered by the parity of c, so one 64-thread
+// named barrier per column suffices: a buffer is rewritten two columns later,
+// after every thread passed the barrier in between) and each row updates its
+// entries right of c.  Writes the unit factor (strict lower) back to sm.X, D
+// and D^-1 to sm.dd / sm.invd.  Returns false on a non-positive pivot.
+__device__ __noinline__ bool factor64(LgShared& sm) {
   const int r = threadIdx.x;  // < 64
   float* Xs = sm.X;
   float(*buf)[NB] = reinterpret_cast<float(*)[NB]>(&sm.ucol[0][0]);
@@ -272,38 +277,78 @@ __device__ __noinline__ bool factor64(LgShared& sm, float* li) {
 #pragma unroll
   for (int c = 0; c < NB; ++c)
     if (c < r) Xs[r * LDS + c] = a[c];
-  asm volatile("bar.sync 1, 64;" ::: "memory");
-  // inverse of the unit lower factor: column r, x_i = -sum_{k<i} L_ik x_k
-  float x[NB];
-#pragma unroll
-  for (int i = 0; i < NB; ++i) x[i] = (i == r) ? 1.f : 0.f;
-#pragma unroll
-  for (int k = 0; k < NB - 1; ++k)
-#pragma unroll
-    for (int i = k + 1; i < NB; ++i) x[i] = fmaf(-Xs[i * LDS + k], x[k], x[i]);
-#pragma unroll
-  for (int i = 0; i < NB; ++i) {
-    li[i * NB + r] = x[i];
-    sm.Y[i * LDS + r] = x[i];
-  }
   return ok;
 }
 
+// Inverse of the unit lower factor in sm.X by 32-row blocks,
+//   [L00 0; L10 L11]^-1 = [L00^-1 0; -L11^-1 (L10 L00^-1) L11^-1],
+// into sm.Y (padded) and li (global, row-major): warps 0 and 1 invert the
+// diagonal blocks (lane = column, forward substitution), then all threads
+// form the off-diagonal block through sm.Z (scratch).
+__device__ void inverse64(LgShared& sm, float* li) {
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  if (wid < 2) {
+    const int b = 32 * wid;
+    float x[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) x[i] = (i == lane) ? 1.f : 0.f;
+#pragma unroll
+    for (int k = 0; k < 31; ++k)
+#pragma unroll
+      for (int i = k + 1; i < 32; ++i) x[i] = fmaf(-sm.X[(b + i) * LDS + b + k], x[k], x[i]);
+#pragma unroll
+    for (int i = 0; i < 32; ++i) sm.Y[(b + i) * LDS + b + lane] = x[i];
+  } else {
+    for (int t = tid - 64; t < 32 * 32; t += LG_THREADS - 64) sm.Y[(t >> 5) * LDS + 32 + (t & 31)] = 0.f;
+  }
+  __syncthreads();
+  // thread: row i, columns j0, j0 + 8, j0 + 16, j0 + 24 of the 32 x 32 products
+  const int i = tid >> 3, j0 = tid & 7;
+  {
+    // W = L10 L00^-1 (L00^-1 lower: only k >= j contributes; its upper part is 0)
+    float w[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 8
+    for (int k = 0; k < 32; ++k) {
+      const float x = sm.X[(32 + i) * LDS + k];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) w[e] = fmaf(x, sm.Y[k * LDS + j0 + 8 * e], w[e]);
+    }
+#pragma unroll
+    for (int e = 0; e < 4; ++e) sm.Z[i * LDS + j0 + 8 * e] = w[e];
+  }
+  __syncthreads();
+  {
+    // M10 = -L11^-1 W (L11^-1 lower: k <= i)
+    float v[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 8
+    for (int k = 0; k < 32; ++k) {
+      const float y = k <= i ? sm.Y[(32 + i) * LDS + 32 + k] : 0.f;
+#pragma unroll
+      for (int e = 0; e < 4; ++e) v[e] = fmaf(y, sm.Z[k * LDS + j0 + 8 * e], v[e]);
+    }
+#pragma unroll
+    for (int e = 0; e < 4; ++e) sm.Y[(32 + i) * LDS + j0 + 8 * e] = -v[e];
+  }
+  __syncthreads();
+  for (int t = tid; t < TILE; t += LG_THREADS) li[t] = sm.Y[(t >> 6) * LDS + (t & 63)];
+}
+
 // DIAG(k): the 64 x 64 diagonal tile (in sm.X, lower part) factored by
-// factor64; the unit factor goes to tile (k, k), its inverse to Linv (and
-// stays in sm.Y), D and D^-1 to global and to sm.dprev / sm.iprev for the
-// next step.
+// factor64 and inverted by inverse64; the unit factor goes to tile (k, k),
+// its inverse to Linv (and stays in sm.Y), D and D^-1 to global and to
+// sm.dprev / sm.iprev for the next step.
 __device__ bool factor_diag(LgShared& sm, float* A, float* Linv, float* D, float* invD, int k) {
   const int tid = threadIdx.x;
   float* tk = tile_ptr(A, k, k);
   if (tid == 0) sm.bad = 0;
   __syncthreads();
   if (tid < NB) {
-    const bool ok = factor64(sm, Linv + (size_t)k * TILE);
+    const bool ok = factor64(sm);
     if (!ok && tid == 0) sm.bad = 1;
   }
   __syncthreads();
   if (sm.bad) return false;
+  inverse64(sm, Linv + (size_t)k * TILE);
   for (int t = tid; t < TILE; t += LG_THREADS) {
     const int r = t >> 6, c = t & 63;
     tk[t] = c < r ? sm.X[r * LDS + c] : (c == r ? 1.f : 0.f);
@@ -317,37 +362,93 @@ __device__ bool factor_diag(LgShared& sm, float* A, float* Linv, float* D, float
   return true;
 }
 
+constexpr uint32_t TC_OP_BYTES = TILE * 4;  // one split part of one tile (16 KB)
+constexpr int TC_SMEM = 6 * TC_OP_BYTES;    // A hi, A lo (128 rows each), B hi, B lo
+constexpr uint32_t TC_COLS = 64;            // tensor-memory columns per CTA (the 64 output columns)
+
+struct TcState {
+  uint64_t bar_ld;    // the operand copies
+  uint64_t bar_mma;   // the MMAs
+  uint32_t tmem;
+  uint32_t ph_ld, ph_mma;
+  int bad;            // 1: the copies, 2: the MMAs did not complete in time
+};
+
+// Byte offset of the tensor-core region in the factorisation kernel's
+// dynamic shared memory (after the CUDA-core tasks' LgShared).
+constexpr size_t TC_OFF = (sizeof(LgShared) + 1023) / 1024 * 1024;
+
+// D (tensor memory, 128 x 64, FP32) = A B^T for split operands in the
+// K-major core-matrix layout (A: 128 rows, B: 64 rows, K = 64): the 24 MMAs
+// of the three-pass TF32 product (hi*hi + hi*lo + lo*hi), committed to
+// bar_mma and waited for with a bound.  Thread 0 only; false on a timeout
+// (ts.bad = 2, the MMAs may still be in flight).
+__device__ bool tc_gemm64(TcState& ts, const unsigned char* a_hi, const unsigned char* a_lo, const unsigned char* b_hi,
+                          const unsigned char* b_lo, long long timeout) {
+  constexpr uint32_t idesc = tc_idesc_tf32(128, NB);
+  constexpr uint32_t LBO = 128, SBO = (NB / 4) * 128;
+  const uint32_t ah0 = tc_smem_addr(a_hi), al0 = tc_smem_addr(a_lo), bh0 = tc_smem_addr(b_hi), bl0 = tc_smem_addr(b_lo);
+#pragma unroll
+  for (int st = 0; st < NB / 8; ++st) {
+    const uint32_t off = st * 256;  // K = 8 TF32 values = two core matrices along K
+    const uint64_t ah = tc_desc(ah0 + off, LBO, SBO), al = tc_desc(al0 + off, LBO, SBO);
+    const uint64_t bh = tc_desc(bh0 + off, LBO, SBO), bl = tc_desc(bl0 + off, LBO, SBO);
+    tc_mma_tf32(ts.tmem, ah, bh, idesc, st > 0);
+    tc_mma_tf32(ts.tmem, ah, bl, idesc, 1);
+    tc_mma_tf32(ts.tmem, al, bh, idesc, 1);
+  }
+  tc_commit(&ts.bar_mma);
+  if (!tc_mbar_wait(&ts.bar_mma, ts.ph_mma, timeout)) {
+    ts.bad = 2;
+    return false;
+  }
+  ts.ph_mma ^= 1u;
+  return true;
+}
+
 // Critical-path step k (one dedicated CTA, in order): for k > 0 first the
-// panel of tile (k, k-1) and its update of tile (k, k), from the inverse and D
-// of step k-1 kept in shared memory; then the factorisation of tile (k, k).
-__device__ bool task_diag_step(LgShared& sm, float* A, float* G, float* Linv, float* D, float* invD, int k, int* ver,
-                               int* status, long long timeout) {
-  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+// panel of tile (k, k-1), L = A_{k,k-1} L_{k-1}^-T D_{k-1}^-1 (CUDA cores,
+// from the inverse and D of step k-1 kept in shared memory), and its update
+// of tile (k, k), A_kk - G G^T with G = L D_{k-1}^1/2, on the tensor cores (G
+// is split once, for the workers' updates in global memory and for this
+// update in shared memory; the product sits in tensor-memory lanes 0..63,
+// read by warps 0, 1, 4, 5); then the factorisation of tile (k, k).
+__device__ bool task_diag_step(LgShared& sm, unsigned char* tcbuf, TcState& ts, float* A, float* G, float* Linv,
+                               float* D, float* invD, int k, int* ver, int* status, long long timeout) {
+  const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
+  unsigned char* a_hi = tcbuf;
+  unsigned char* a_lo = a_hi + 2 * TC_OP_BYTES;
+  const bool epi = (wid & 3) < 2;
+  const int r = 32 * (wid & 3) + lane, c0 = 32 * (wid >> 2);
+  const uint32_t taddr = ts.tmem + ((uint32_t)(32 * (wid & 3)) << 16) + (uint32_t)c0;
   if (k > 0) {
     if (tid == 0) sm.bad = wait_geq(ver + tri2(k) + k - 1, k - 1, status, timeout) ? 0 : 1;
     __syncthreads();
     if (sm.bad) return false;
+    // the panel on the CUDA cores (the operands would first have to be split
+    // into the tensor cores' layout: measured slower for one tile)
     float* tp = tile_ptr(A, k, k - 1);
     load_tile(sm.Z, tp, false);
     __syncthreads();
-    float acc[4][4] = {};
-    gemm_nt(sm.Z, sm.Y, nullptr, acc);  // A_{k,k-1} Linv_{k-1}^T
-    __syncthreads();
+    {
+      const int tx = tid & 15, ty = tid >> 4;
+      float acc[4][4] = {};
+      gemm_nt(sm.Z, sm.Y, nullptr, acc);  // A_{k,k-1} L_{k-1}^-T
+      __syncthreads();
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
+      for (int a = 0; a < 4; ++a)
 #pragma unroll
-      for (int b = 0; b < 4; ++b) {
-        const int r = ty + 16 * a, c = tx + 16 * b;
-        const float l = acc[a][b] * sm.iprev[c];
-        sm.Z[r * LDS + c] = l;
-        tp[r * NB + c] = l;
-      }
-    if (tid < NB) {
-      sm.sq[tid] = sqrtf(sm.dprev[tid]);
-      sm.dprev[tid] = -sm.dprev[tid];
+        for (int b = 0; b < 4; ++b) {
+          const int rr = ty + 16 * a, c = tx + 16 * b;
+          const float l = acc[a][b] * sm.iprev[c];
+          sm.Z[rr * LDS + c] = l;
+          tp[rr * NB + c] = l;
+        }
     }
+    if (tid < NB) sm.sq[tid] = sqrtf(sm.dprev[tid]);
     __syncthreads();
-    store_g(sm.Z, sm.sq, g_ptr(G, k, k - 1));
+    store_g(sm.Z, sm.sq, g_ptr(G, k, k - 1), a_hi, a_lo);
+    tc_fence_smem();
     __syncthreads();
     if (tid == 0) {
       __threadfence();
@@ -356,22 +457,32 @@ __device__ bool task_diag_step(LgShared& sm, float* A, float* G, float* Linv, fl
     }
     __syncthreads();
     if (sm.bad) return false;
-    load_tile(sm.X, tile_ptr(A, k, k), true);
+    // this thread's 32 entries of A_kk, read while the product runs
+    float4 av[8];
+    const float* tkk = tile_ptr(A, k, k);
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+      av[q] = epi ? __ldcg(reinterpret_cast<const float4*>(tkk + r * NB + c0) + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+    tc_fence_after_sync();
+    if (tid == 0 && !tc_gemm64(ts, a_hi, a_lo, a_hi, a_lo, timeout)) dpv_set_status(status, DST_TIMEOUT);
     __syncthreads();
-    // X -= (L D_{k-1}) L^T, lower part
+    if (ts.bad) return false;
+    tc_fence_after_sync();
+    if (epi) {
+      float d[32];
+      tc_ld32(taddr, d);
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
+      for (int q = 0; q < 8; ++q) {
+        const float4 v = av[q];
+        const float x[4] = {v.x - d[4 * q], v.y - d[4 * q + 1], v.z - d[4 * q + 2], v.w - d[4 * q + 3]};
 #pragma unroll
-      for (int b = 0; b < 4; ++b) acc[a][b] = sm.X[(ty + 16 * a) * LDS + tx + 16 * b];
-    gemm_nt(sm.Z, sm.Z, sm.dprev, acc);
-    __syncthreads();
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-      for (int b = 0; b < 4; ++b) {
-        const int r = ty + 16 * a, c = tx + 16 * b;
-        if (c <= r) sm.X[r * LDS + c] = acc[a][b];
+        for (int e = 0; e < 4; ++e) {
+          const int c = c0 + 4 * q + e;
+          sm.X[r * LDS + c] = c <= r ? x[e] : 0.f;
+        }
       }
+    }
+    tc_fence_before_sync();
   } else {
     load_tile(sm.X, tile_ptr(A, 0, 0), true);
   }
@@ -416,18 +527,6 @@ __device__ void task_panel(LgShared& sm, float* A, float* G, const float* Linv, 
 // shared memory (aliasing the other tasks' shared memory) while the threads
 // fetch the tiles being updated; one thread issues the 24 MMAs.  With one
 // row tile, rows 64..127 of A hold stale data whose products are not read.
-constexpr uint32_t TC_OP_BYTES = TILE * 4;  // one split part of one tile (16 KB)
-constexpr int TC_SMEM = 6 * TC_OP_BYTES;    // A hi, A lo (128 rows each), B hi, B lo
-constexpr uint32_t TC_COLS = 64;            // tensor-memory columns per CTA (the 64 output columns)
-
-struct TcState {
-  uint64_t bar_ld;    // the operand copies
-  uint64_t bar_mma;   // the MMAs
-  uint32_t tmem;
-  uint32_t ph_ld, ph_mma;
-  int bad;            // 1: the copies, 2: the MMAs did not complete in time
-};
-
 __device__ bool task_update_tc(unsigned char* tcbuf, TcState& ts, float* A, const float* G, int T, int i, int j,
                                int k, long long timeout) {
   const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
@@ -590,7 +689,7 @@ __global__ void __launch_bounds__(LG_THREADS, 1) k_lg_factor(const LgProb* __res
                                                           long long timeout) {
   extern __shared__ __align__(1024) float lg_smem[];
   LgShared& sm = *reinterpret_cast<LgShared*>(lg_smem);          // the CUDA-core tasks
-  unsigned char* tcbuf = reinterpret_cast<unsigned char*>(lg_smem);  // the tensor-core operands (aliased)
+  unsigned char* tcbuf = reinterpret_cast<unsigned char*>(lg_smem) + TC_OFF;  // the tensor-core operands
   __shared__ TcState ts;
   __shared__ int role, task, bad;
   if (threadIdx.x == 0) {
@@ -621,7 +720,7 @@ __global__ void __launch_bounds__(LG_THREADS, 1) k_lg_factor(const LgProb* __res
     const LgProb& P = probs[blockIdx.x];
     for (int k = 0; k < P.T; ++k) {
       if (dpv_status(status)) goto done;
-      if (!task_diag_step(sm, P.A, P.G, P.Linv, P.D, P.invD, k, P.ver, status, timeout)) {
+      if (!task_diag_step(sm, tcbuf, ts, P.A, P.G, P.Linv, P.D, P.invD, k, P.ver, status, timeout)) {
         if (threadIdx.x == 0 && !dpv_status(status)) dpv_set_status(status, DST_NOT_SPD);
         goto done;
       }
@@ -1322,7 +1421,7 @@ ba_status_t dpv_solve_large(ba_handle_t h, int refine) {
   {
     // at most two CTAs per SM; the critical CTAs get their SMs to themselves
     // while at least half the SMs remain for the workers
-    const size_t smem = std::max(sizeof(LgShared), (size_t)TC_SMEM);
+    const size_t smem = TC_OFF + (size_t)TC_SMEM;  // CUDA-core tasks' storage, then the tensor-core operands
     static bool attr = false;
     if (!attr) {
       DPV_CUDA(h, cudaFuncSetAttribute(k_lg_factor, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
