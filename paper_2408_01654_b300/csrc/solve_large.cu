@@ -13,7 +13,7 @@
 //                  and G_ik = L_ik D_k^1/2, stored pre-split for the tensor
 //                  cores (TF32 part + FP32 rest, core-matrix layout)
 //   UPDATE(i,j,k)  A_ij -= G_ik G_jk^T                             (k < j <= i)
-//                  (workers: two row tiles at a time, one 128 x 64 x 64
+//                  (workers: 2 x 2 tiles at a time, one 128 x 128 x 64
 //                  tcgen05 TF32 product with a three-pass split whose
 //                  operands arrive by bulk copies)
 // Each tile carries a version (the number of updates applied, +1 once it is
@@ -363,8 +363,8 @@ __device__ bool factor_diag(LgShared& sm, float* A, float* Linv, float* D, float
 }
 
 constexpr uint32_t TC_OP_BYTES = TILE * 4;  // one split part of one tile (16 KB)
-constexpr int TC_SMEM = 6 * TC_OP_BYTES;    // A hi, A lo (128 rows each), B hi, B lo
-constexpr uint32_t TC_COLS = 64;            // tensor-memory columns per CTA (the 64 output columns)
+constexpr int TC_SMEM = 8 * TC_OP_BYTES;    // A hi, A lo, B hi, B lo: 128 rows (two tiles) each
+constexpr uint32_t TC_COLS = 128;           // tensor-memory columns per CTA (128 output columns)
 
 struct TcState {
   uint64_t bar_ld;    // the operand copies
@@ -518,46 +518,56 @@ __device__ void task_panel(LgShared& sm, float* A, float* G, const float* Linv, 
 }
 
 
-// UPDATE of a pair of row tiles on the tensor cores: tiles (i, j) and
-// (i+1, j) (the second only when i+1 < T) at step k,
-//   [A_ij; A_i+1,j] -= [G_ik; G_i+1,k] G_jk^T,
-// as one 128 x 64 x 64 tcgen05 TF32 product with the three-pass split
+// UPDATE of a 2 x 2 block of tiles on the tensor cores: rows i, i+1 and
+// columns j, j+1 at step k (each tile only when it lies in the lower triangle
+// of a T x T tile grid),
+//   A_ab -= G_ak G_bk^T  for a in {i, i+1}, b in {j, j+1},
+// as one 128 x 128 x 64 tcgen05 TF32 product with the three-pass split
 // (hi*hi + hi*lo + lo*hi, about FP32 accuracy) accumulated in tensor memory.
 // The operands, written pre-split by the panels, arrive by bulk copies into
-// shared memory (aliasing the other tasks' shared memory) while the threads
-// fetch the tiles being updated; one thread issues the 24 MMAs.  With one
-// row tile, rows 64..127 of A hold stale data whose products are not read.
+// shared memory while the threads fetch the tiles being updated; one thread
+// issues the 24 MMAs.  Operand rows of a missing tile hold stale data whose
+// products are not read.
+__device__ __forceinline__ bool quad_tile(int T, int a, int b) { return a < T && b < T && b <= a; }
+
 __device__ bool task_update_tc(unsigned char* tcbuf, TcState& ts, float* A, const float* G, int T, int i, int j,
                                int k, long long timeout) {
   const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
-  const bool two = i + 1 < T;
+  const bool i2 = i + 1 < T, j2 = j + 1 < T;
   unsigned char* a_hi = tcbuf;
   unsigned char* a_lo = a_hi + 2 * TC_OP_BYTES;
   unsigned char* b_hi = a_lo + 2 * TC_OP_BYTES;
-  unsigned char* b_lo = b_hi + TC_OP_BYTES;
+  unsigned char* b_lo = b_hi + 2 * TC_OP_BYTES;
   if (tid == 0) {
     tc_fence_global();  // G was written by other CTAs through the generic proxy
     tc_fence_smem();    // this CTA's earlier generic accesses of the buffer are ordered before the copies
-    tc_mbar_expect_tx(&ts.bar_ld, (two ? 6u : 4u) * TC_OP_BYTES);
+    tc_mbar_expect_tx(&ts.bar_ld, (uint32_t)(4 + (i2 ? 2 : 0) + (j2 ? 2 : 0)) * TC_OP_BYTES);
     const float* gi = g_ptr(const_cast<float*>(G), i, k);
     const float* gj = g_ptr(const_cast<float*>(G), j, k);
     tc_bulk_g2s(a_hi, gi, TC_OP_BYTES, &ts.bar_ld);
     tc_bulk_g2s(a_lo, gi + TILE, TC_OP_BYTES, &ts.bar_ld);
-    if (two) {
+    if (i2) {
       const float* g1 = g_ptr(const_cast<float*>(G), i + 1, k);
       tc_bulk_g2s(a_hi + TC_OP_BYTES, g1, TC_OP_BYTES, &ts.bar_ld);
       tc_bulk_g2s(a_lo + TC_OP_BYTES, g1 + TILE, TC_OP_BYTES, &ts.bar_ld);
     }
     tc_bulk_g2s(b_hi, gj, TC_OP_BYTES, &ts.bar_ld);
     tc_bulk_g2s(b_lo, gj + TILE, TC_OP_BYTES, &ts.bar_ld);
+    if (j2) {
+      const float* g1 = g_ptr(const_cast<float*>(G), j + 1, k);
+      tc_bulk_g2s(b_hi + TC_OP_BYTES, g1, TC_OP_BYTES, &ts.bar_ld);
+      tc_bulk_g2s(b_lo + TC_OP_BYTES, g1 + TILE, TC_OP_BYTES, &ts.bar_ld);
+    }
   }
-  // this thread's 32 outputs (row r, columns c0..c0+31; see the epilogue), read meanwhile
-  const int r = 32 * (wid & 3) + lane, c0 = 32 * (wid >> 2);
-  const bool mine = r < 64 || two;
-  float* ct = tile_ptr(A, i + (r >> 6), j) + (r & 63) * NB + c0;
-  float4 cv[8];
+  // this thread's 64 outputs: row r of the 128 (tile row i + r / 64), the 64
+  // columns of tile column j + wid / 4; read meanwhile
+  const int r = 32 * (wid & 3) + lane, cb = wid >> 2;
+  const int ta = i + (r >> 6), tb = j + cb, rr = r & 63;
+  const bool mine = quad_tile(T, ta, tb);
+  float* ct = tile_ptr(A, mine ? ta : i, mine ? tb : j) + rr * NB;
+  float4 cv[16];
 #pragma unroll
-  for (int q = 0; q < 8; ++q)
+  for (int q = 0; q < 16; ++q)
     cv[q] = mine ? __ldcg(reinterpret_cast<const float4*>(ct) + q) : make_float4(0.f, 0.f, 0.f, 0.f);
   if (tid == 0) {
     if (!tc_mbar_wait(&ts.bar_ld, ts.ph_ld, timeout)) {
@@ -565,7 +575,7 @@ __device__ bool task_update_tc(unsigned char* tcbuf, TcState& ts, float* A, cons
     } else {
       ts.ph_ld ^= 1u;
       tc_fence_after_sync();
-      constexpr uint32_t idesc = tc_idesc_tf32(128, NB);
+      constexpr uint32_t idesc = tc_idesc_tf32(128, 2 * NB);
       constexpr uint32_t LBO = 128, SBO = (NB / 4) * 128;
       const uint32_t ah0 = tc_smem_addr(a_hi), al0 = tc_smem_addr(a_lo), bh0 = tc_smem_addr(b_hi),
                      bl0 = tc_smem_addr(b_lo);
@@ -588,29 +598,30 @@ __device__ bool task_update_tc(unsigned char* tcbuf, TcState& ts, float* A, cons
   __syncthreads();
   if (ts.bad) return false;
   tc_fence_after_sync();
-  // epilogue: warp w holds rows 32 (w % 4) + lane, columns 32 (w / 4) .. + 31
-  {
+  // epilogue: warp w reads lanes 32 (w % 4) .. + 31 (rows), columns 64 (w / 4) .. + 63
+  const uint32_t taddr = ts.tmem + ((uint32_t)(32 * (wid & 3)) << 16) + (uint32_t)(64 * cb);
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
     float d[32];
-    tc_ld32(ts.tmem + ((uint32_t)(32 * (wid & 3)) << 16) + (uint32_t)c0, d);
+    tc_ld32(taddr + 32 * h, d);
     if (mine) {
-      float* t = ct;
-      const int rr = r & 63;
-      const bool diag = (i + (r >> 6)) == j;  // a diagonal tile keeps only its lower part
+      const bool diag = ta == tb;  // a diagonal tile keeps only its lower part
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
-        float4 c = cv[q];
+        float4 c = cv[8 * h + q];
         c.x -= d[4 * q];
         c.y -= d[4 * q + 1];
         c.z -= d[4 * q + 2];
         c.w -= d[4 * q + 3];
+        float* t = ct + 32 * h + 4 * q;
         if (!diag) {
-          reinterpret_cast<float4*>(t)[q] = c;
+          *reinterpret_cast<float4*>(t) = c;
         } else {
-          const int cc = c0 + 4 * q;
-          if (cc <= rr) t[4 * q] = c.x;
-          if (cc + 1 <= rr) t[4 * q + 1] = c.y;
-          if (cc + 2 <= rr) t[4 * q + 2] = c.z;
-          if (cc + 3 <= rr) t[4 * q + 3] = c.w;
+          const int cc = 32 * h + 4 * q;
+          if (cc <= rr) t[0] = c.x;
+          if (cc + 1 <= rr) t[1] = c.y;
+          if (cc + 2 <= rr) t[2] = c.z;
+          if (cc + 3 <= rr) t[3] = c.w;
         }
       }
     }
@@ -679,8 +690,9 @@ __global__ void k_lg_convert(const LgProb* __restrict__ probs, const int* status
 // The factorisation task graphs of all large systems.  CTA p < nsys runs the
 // critical chain of system p (other CTAs on its SM leave when there are SMs
 // to spare), then joins the workers; workers take the panels and the
-// tensor-core pair updates of all systems from one list (task: system << 32 |
-// type << 30 | k << 20 | i << 10 | j; an update covers row tiles i and i+1).
+// tensor-core updates of all systems from one list (task: system << 32 |
+// type << 30 | k << 20 | i << 10 | j; an update covers rows i, i+1 and
+// columns j, j+1).
 // Every CTA that stays holds TC_COLS tensor-memory columns, released on every
 // way out once its MMAs have completed.
 __global__ void __launch_bounds__(LG_THREADS, 1) k_lg_factor(const LgProb* __restrict__ probs, int nsys,
@@ -750,11 +762,13 @@ __global__ void __launch_bounds__(LG_THREADS, 1) k_lg_factor(const LgProb* __res
       if (type == TASK_PANEL) {
         ok = wait_geq(ver + tri2(k) + k, k + 1, status, timeout) && wait_geq(ver + tri2(i) + k, k, status, timeout);
       } else {
-        ok = wait_geq(ver + tri2(i) + k, k + 1, status, timeout) &&
-             wait_geq(ver + tri2(j) + k, k + 1, status, timeout) && wait_geq(ver + tri2(i) + j, k, status, timeout);
-        if (ok && i + 1 < T)
-          ok = wait_geq(ver + tri2(i + 1) + k, k + 1, status, timeout) &&
-               wait_geq(ver + tri2(i + 1) + j, k, status, timeout);
+        // the four panels of column k (final), then the target tiles (updated through step k-1)
+        ok = true;
+        for (int a = i; a <= i + 1 && a < T && ok; ++a) ok = wait_geq(ver + tri2(a) + k, k + 1, status, timeout);
+        for (int b = j; b <= j + 1 && b < T && ok; ++b) ok = wait_geq(ver + tri2(b) + k, k + 1, status, timeout);
+        for (int a = i; a <= i + 1 && ok; ++a)
+          for (int b = j; b <= j + 1 && ok; ++b)
+            if (quad_tile(T, a, b)) ok = wait_geq(ver + tri2(a) + b, k, status, timeout);
       }
       bad = ok ? 0 : 1;
     }
@@ -772,8 +786,9 @@ __global__ void __launch_bounds__(LG_THREADS, 1) k_lg_factor(const LgProb* __res
       if (type == TASK_PANEL) {
         st_release(ver + tri2(i) + k, k + 1);
       } else {
-        st_release(ver + tri2(i) + j, k + 1);
-        if (i + 1 < T) st_release(ver + tri2(i + 1) + j, k + 1);
+        for (int a = i; a <= i + 1; ++a)
+          for (int b = j; b <= j + 1; ++b)
+            if (quad_tile(T, a, b)) st_release(ver + tri2(a) + b, k + 1);
       }
     }
   }
@@ -1182,10 +1197,11 @@ __global__ void __launch_bounds__(LG_THREADS, 2) k_lg_solve(const LgProb* __rest
 }
 
 // Task list of several systems, in dependency order within each system and
-// interleaved by step across systems (largest first), so that every critical
-// chain advances together.  Per system: step k+1's column update and panels
-// come before the bulk of step k's trailing update, whose columns run left to
-// right; the critical CTA does DIAG(k), PANEL(k, k-1) and UPDATE(k, k, k-1).
+// interleaved by step across systems, so that every critical chain advances
+// together.  Per system: step k's update of columns k+1, k+2 and the panels
+// of column k+1 come before the bulk of step k's trailing update, whose
+// column pairs run left to right; the critical CTA does DIAG(k),
+// PANEL(k, k-1) and UPDATE(k, k, k-1).
 std::vector<unsigned long long> build_tasks(const std::vector<int>& Ts) {
   std::vector<unsigned long long> v;
   auto put = [&](int p, int type, int k, int i, int j) {
@@ -1195,14 +1211,15 @@ std::vector<unsigned long long> build_tasks(const std::vector<int>& Ts) {
   for (int T : Ts) maxT = std::max(maxT, T);
   for (int p = 0; p < (int)Ts.size(); ++p)
     for (int i = 2; i < Ts[p]; ++i) put(p, TASK_PANEL, 0, i, 0);
-  // updates cover two row tiles (i, i+1) of one column
+  // updates cover 2 x 2 tiles: rows (i, i+1), columns (j, j+1)
   for (int k = 0; k + 1 < maxT; ++k)
     for (int p = 0; p < (int)Ts.size(); ++p) {
       const int T = Ts[p];
       if (k + 1 >= T) continue;
+      // columns k+1, k+2 first (tile (k+1, k+1) is the critical CTA's)
       for (int i = k + 2; i < T; i += 2) put(p, TASK_UPDATE, k, i, k + 1);
       for (int i = k + 3; i < T; ++i) put(p, TASK_PANEL, k + 1, i, k + 1);
-      for (int j = k + 2; j < T; ++j)
+      for (int j = k + 3; j < T; j += 2)
         for (int i = j; i < T; i += 2) put(p, TASK_UPDATE, k, i, j);
     }
   return v;
