@@ -438,6 +438,11 @@ ba_status_t ba_destroy(ba_handle_t h) {
   graph_drop(h, h->step_graph);
   graph_drop(h, h->bind_graph);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  for (int q = 0; q < 8; ++q) {
+    if (h->side[q]) cudaStreamDestroy(h->side[q]);
+    if (h->ev_join[q]) cudaEventDestroy(h->ev_join[q]);
+  }
+  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
   prof_clear(h);
   for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
   delete h;

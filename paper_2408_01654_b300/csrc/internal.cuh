@@ -92,6 +92,11 @@ struct ba_handle_s {
   int prof_open = -1;
 
   long long launches = 0;  // kernels launched by this handle so far
+  // side streams: the one-CTA solver launches of different block counts run
+  // concurrently (fork from and join back to the handle's stream)
+  cudaStream_t side[8] = {};
+  cudaEvent_t ev_fork = nullptr;
+  cudaEvent_t ev_join[8] = {};
 
   // CUDA-graph replay of ba_step and of ba_set_graph's device work (ba_set_capture)
   int capture_on = 0;       // replay from captured graphs

@@ -34,6 +34,7 @@
 #include "internal.cuh"
 #include "tcgen05.cuh"
 
+#include <algorithm>
 #include <map>
 #include <mutex>
 #include <vector>
@@ -965,8 +966,10 @@ __device__ void tile_symv(const SymvRegs& g, const DFp* vr, const DFp* vc, bool 
 //                 q = S' p,  alpha = rho / p.q,  z += alpha p,  r -= alpha q
 // The products with S run in double-float over S_df (FP64-level accuracy
 // at FP32 throughput), tile by tile with coalesced reads; r, p, x are FP64.
-// Global row block r (system rb_sys[r], block i = r - rb0) is owned by CTA
-// r mod grid in both directions; forward rows wait for the rows above them in
+// rb_sys[r] is the system of global row block r (block i = r - rb0);
+// rb_sys[R + q] and rb_sys[2R + q] list the row blocks in forward and
+// backward chain order (by i, and by T - 1 - i), and CTA c takes entries
+// q = c, c + grid, ... of each; forward rows wait for the rows above them in
 // their system, the backward rows for the rows below; grid barriers separate
 // the phases.  The iterations stop once every system's estimated error left
 // in x is below 1e-7 of it.
@@ -984,8 +987,11 @@ __global__ void __launch_bounds__(LG_THREADS, 2) k_lg_solve(const LgProb* __rest
   __syncthreads();
   for (int sweep = 0; sweep < sweeps; ++sweep) {
     if (dpv_status(status)) return;
-    // ---- forward: L u = rhs
-    for (int r = blockIdx.x; r < R; r += gridDim.x) {
+    // ---- forward: L u = rhs; this CTA's row blocks in chain order (all
+    // systems' first rows first), so that one system's chain never waits
+    // behind another's
+    for (int q = blockIdx.x; q < R; q += gridDim.x) {
+      const int r = rb_sys[R + q];
       const LgProb& P = probs[rb_sys[r]];
       const int i = r - P.rb0;
       if (tid < NB) acc[tid] = __ldcg(P.rhs + i * NB + tid);
@@ -1013,14 +1019,19 @@ __global__ void __launch_bounds__(LG_THREADS, 2) k_lg_solve(const LgProb* __rest
       }
     }
     // ---- backward: L^T w = D^-1 u, rows descending; rho = r.w per system
-    // this CTA's last row block (none when the grid has more CTAs than rows)
-    int last = (int)blockIdx.x < R ? (int)blockIdx.x : -1;
-    while (last >= 0 && last + (int)gridDim.x < R) last += gridDim.x;
-    for (int r = last; r >= 0; r -= gridDim.x) {
+    // (row blocks in chain order from the bottom)
+    for (int q = blockIdx.x; q < R; q += gridDim.x) {
+      const int r = rb_sys[2 * R + q];
       const int sy = rb_sys[r];
       const LgProb& P = probs[sy];
       const int i = r - P.rb0, T = P.T;
-      if (tid < NB) acc[tid] = __ldcg(P.xf + i * NB + tid) * __ldcg(P.invD + i * NB + tid);
+      // the forward result of this row (solved by whichever CTA owned it in
+      // the forward order): taken from its published word
+      if (tid < NB) {
+        float u = 0.f;
+        if (!wait_tagged(P.tf + i * NB + tid, sweep + 1, u, status, timeout)) ok = 0;
+        acc[tid] = u * __ldcg(P.invD + i * NB + tid);
+      }
       TileRegs m = load_block(i + 1 < T ? P.A + (size_t)(tri2(T - 1) + i) * TILE : P.Linv + (size_t)i * TILE);
       for (int j = T - 1; j > i; --j) {
         const TileRegs mn =
@@ -1037,6 +1048,7 @@ __global__ void __launch_bounds__(LG_THREADS, 2) k_lg_solve(const LgProb* __rest
         m = mn;
       }
       __syncthreads();
+      if (!ok) return;
       tile_gemv(m, acc, prod, true, part);
       if (tid < NB) {
         P.xb[i * NB + tid] = prod[tid];
@@ -1330,6 +1342,20 @@ ba_status_t lg_plan(ba_handle_t h, LgPlan& L) {
     for (int i = 0; i < T; ++i) L.rb_sys.push_back(p);
     L.soff_sync += tri2(T);
   }
+  {
+    // the chain orders of the triangular solves: by position in the chain,
+    // then by system
+    const int R = (int)L.rb_sys.size();
+    std::vector<int> fw(R), bw(R);
+    for (int r = 0; r < R; ++r) fw[r] = bw[r] = r;
+    auto pos = [&](int r) { return r - L.pr[L.rb_sys[r]].rb0; };
+    std::stable_sort(fw.begin(), fw.end(), [&](int a, int b) { return pos(a) < pos(b); });
+    std::stable_sort(bw.begin(), bw.end(), [&](int a, int b) {
+      return L.pr[L.rb_sys[a]].T - 1 - pos(a) < L.pr[L.rb_sys[b]].T - 1 - pos(b);
+    });
+    L.rb_sys.insert(L.rb_sys.end(), fw.begin(), fw.end());
+    L.rb_sys.insert(L.rb_sys.end(), bw.begin(), bw.end());
+  }
   if (foff > ws->L.cap) return dpv_fail(h, BA_ERR_STATE, "large solver scratch");
   // the task list of this set of sizes, built once per device
   {
@@ -1389,7 +1415,7 @@ ba_status_t dpv_solve_large(ba_handle_t h, int refine) {
   const long long soff_sync = L.soff_sync, nsync = L.nsync;
   unsigned long long* tasks = L.tasks;
   int ntasks = L.ntasks;
-  const int R = (int)rb_sys.size();
+  const int R = (int)rb_sys.size() / 3;  // systems of the row blocks, then the two chain orders
   int* sync = ws->lg_sync.p;
   for (int p = 0, o = 0; p < nsys; ++p) {
     pr[p].ver = sync + o;
@@ -1416,12 +1442,12 @@ ba_status_t dpv_solve_large(ba_handle_t h, int refine) {
       up.insert(up.end(), c, c + n);
     };
     put(pr.data(), sizeof(LgProb) * nsys);
-    put(rb_sys.data(), sizeof(int) * R);
+    put(rb_sys.data(), sizeof(int) * 3 * R);
     put(&h->ws_gen, sizeof(long long));
     if (up != ws->lg_uploaded) {
       if (h->capturing) return dpv_fail(h, BA_ERR_STATE, "large solver tables changed during graph capture");
       DPV_CUDA(h, cudaMemcpyAsync(ws->lg_prob.p, pr.data(), sizeof(LgProb) * nsys, cudaMemcpyHostToDevice, st));
-      DPV_CUDA(h, cudaMemcpyAsync(ws->lg_rb.p, rb_sys.data(), sizeof(int) * R, cudaMemcpyHostToDevice, st));
+      DPV_CUDA(h, cudaMemcpyAsync(ws->lg_rb.p, rb_sys.data(), sizeof(int) * 3 * R, cudaMemcpyHostToDevice, st));
       ws->lg_uploaded.swap(up);  // (pageable-source copies are staged before they return)
     }
   }

@@ -432,14 +432,15 @@ __global__ void __launch_bounds__(small_threads(NQ)) k_solve_small(
 }
 
 template <int NQ>
-ba_status_t launch_small(ba_handle_t h, int count, const int* list, int refine32, int refine64, int reset) {
+ba_status_t launch_small(ba_handle_t h, cudaStream_t st, int count, const int* list, int refine32, int refine64,
+                         int reset) {
   static bool attr = false;
   const size_t smem = small_smem(NQ);
   if (!attr) {
     DPV_CUDA(h, cudaFuncSetAttribute(k_solve_small<NQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     attr = true;
   }
-  k_solve_small<NQ><<<count, small_threads(NQ), smem, h->stream>>>(
+  k_solve_small<NQ><<<count, small_threads(NQ), smem, st>>>(
       h->ws->sysd.p, list, 0, h->ws->S.p, h->ws->y.p, h->ws->dx.p, h->ws->tmpv.p, refine32, refine64,
       h->opt.lambda_pose, reset, h->ws->status);
   ++h->launches;
@@ -454,7 +455,6 @@ ba_status_t dpv_solve_large(ba_handle_t h, int refine);
 // Solve every pose system S_b dxi_b = y_b: one launch of the one-CTA solver per
 // block count (one CTA per system), then the large systems.
 ba_status_t dpv_solve(ba_handle_t h, int* retracted, int reset_system) {
-  // BA_FP32: one compensated-FP32 refinement sweep; BA_MIXED: FP64 sweeps
   // refinement sweeps, stopped early once converged: BA_FP32 up to three
   // compensated-FP32 sweeps (small systems), BA_MIXED FP64 sweeps
   const int refine32 = h->opt.precision == BA_MIXED ? 0 : 3;
@@ -462,25 +462,52 @@ ba_status_t dpv_solve(ba_handle_t h, int* retracted, int reset_system) {
   *retracted = 0;
   if (h->n == 0) return BA_OK;
   ba_status_t s = BA_OK;
+  int buckets = 0;
+  for (int nq = 1; nq <= 8; ++nq) buckets += h->small_nq[nq].empty() ? 0 : 1;
+  // several block counts: one launch each on its own side stream, forked from
+  // and joined back to the handle's stream (the streams and events are made
+  // by an eager run, never inside a graph capture)
+  bool fork = buckets > 1;
+  if (fork && !h->ev_fork) {
+    if (h->capturing) {
+      fork = false;
+    } else {
+      DPV_CUDA(h, cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+      for (int q = 0; q < 8; ++q) {
+        DPV_CUDA(h, cudaStreamCreateWithFlags(&h->side[q], cudaStreamNonBlocking));
+        DPV_CUDA(h, cudaEventCreateWithFlags(&h->ev_join[q], cudaEventDisableTiming));
+      }
+    }
+  }
+  if (fork) DPV_CUDA(h, cudaEventRecord(h->ev_fork, h->stream));
   int off = 0;
   for (int nq = 1; nq <= 8; ++nq) {
     const int cnt = (int)h->small_nq[nq].size();
     if (!cnt) continue;
     const int* list = h->ws->syslist.p + off;
+    cudaStream_t st = h->stream;
+    if (fork) {
+      st = h->side[nq - 1];
+      DPV_CUDA(h, cudaStreamWaitEvent(st, h->ev_fork, 0));
+    }
     switch (nq) {
-      case 1: s = launch_small<1>(h, cnt, list, refine32, refine64, reset_system); break;
-      case 2: s = launch_small<2>(h, cnt, list, refine32, refine64, reset_system); break;
-      case 3: s = launch_small<3>(h, cnt, list, refine32, refine64, reset_system); break;
-      case 4: s = launch_small<4>(h, cnt, list, refine32, refine64, reset_system); break;
-      case 5: s = launch_small<5>(h, cnt, list, refine32, refine64, reset_system); break;
-      case 6: s = launch_small<6>(h, cnt, list, refine32, refine64, reset_system); break;
-      case 7: s = launch_small<7>(h, cnt, list, refine32, refine64, reset_system); break;
-      case 8: s = launch_small<8>(h, cnt, list, refine32, refine64, reset_system); break;
+      case 1: s = launch_small<1>(h, st, cnt, list, refine32, refine64, reset_system); break;
+      case 2: s = launch_small<2>(h, st, cnt, list, refine32, refine64, reset_system); break;
+      case 3: s = launch_small<3>(h, st, cnt, list, refine32, refine64, reset_system); break;
+      case 4: s = launch_small<4>(h, st, cnt, list, refine32, refine64, reset_system); break;
+      case 5: s = launch_small<5>(h, st, cnt, list, refine32, refine64, reset_system); break;
+      case 6: s = launch_small<6>(h, st, cnt, list, refine32, refine64, reset_system); break;
+      case 7: s = launch_small<7>(h, st, cnt, list, refine32, refine64, reset_system); break;
+      case 8: s = launch_small<8>(h, st, cnt, list, refine32, refine64, reset_system); break;
     }
     if (s) return s;
+    if (fork) {
+      DPV_CUDA(h, cudaEventRecord(h->ev_join[nq - 1], st));
+      DPV_CUDA(h, cudaStreamWaitEvent(h->stream, h->ev_join[nq - 1], 0));
+    }
     off += cnt;
   }
-  // large systems, all together: FP64 refinement sweeps until converged (at least four allowed)
+  // large systems, all together: preconditioned conjugate gradients until converged
   return dpv_solve_large(h, std::max(8, refine64));
 }
 

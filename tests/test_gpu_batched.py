@@ -93,6 +93,24 @@ def test_batched_equals_separate_handles():
         assert np.allclose(d, Ts["patches"][:, 2, 1, 1].cpu().numpy(), rtol=1e-6, atol=0), b
 
 
+def test_batched_more_row_blocks_than_solver_ctas():
+    # eight 400-frame systems: 8 x 38 = 304 row blocks, more than the solve
+    # kernel's resident CTAs, so CTAs own row blocks of several systems (the
+    # chain-ordered path); each problem must match its own handle
+    frames = [400] * 8
+    probs = problems(frames, seed=6)
+    T, offs, ba = run_batched(probs, 1, precision="mixed", patches_per_group=32)
+    for b, sc in enumerate(probs):
+        Ts = scene_tensors(sc)
+        one = DPVBA(precision="mixed", patches_per_group=32)
+        one.set_graph(**Ts)
+        one.step(1, sc.fixed)
+        one.sync()
+        poses, d = split(T, offs, b)
+        assert np.allclose(poses, Ts["poses"].cpu().numpy(), rtol=0, atol=1e-7), b
+        assert np.allclose(d, Ts["patches"][:, 2, 1, 1].cpu().numpy(), rtol=1e-5, atol=0), b
+
+
 def test_batched_padded_patch_counts_and_intrinsics():
     # patch counts that are not multiples of the group size (the padded copy)
     # and a different camera per problem

@@ -181,6 +181,27 @@ def test_gn_step_blocked_solver(frames):
         assert rot < TOL and tr < TOL and dep < TOL, (frames, precision, rot, tr, dep)
 
 
+@pytest.mark.parametrize("frames", [60, 120])
+@pytest.mark.parametrize("precision", ["fp32", "mixed"])
+def test_large_solver_matches_exact_solve_of_its_system(frames, precision):
+    # the persistent factorisation + preconditioned CG against an exact FP64
+    # solve (LAPACK) of the pose system the GPU assembled: the solver alone
+    s = scenes._build("sized", 17, frames, lambda i, n: scenes._clipped_window(i, n, 6), 2, 1, loop=True)
+    ba, T = bind(s, precision=precision)
+    ba.linearize(s.fixed)
+    ba.sync()
+    n = ba.info()["n"]
+    S = ba.export(capi.EXPORT_S).cpu().numpy().reshape(n, n)
+    S = np.tril(S) + np.tril(S, -1).T
+    y = ba.export(capi.EXPORT_Y).cpu().numpy()
+    ba2, T2 = bind(s, precision=precision)
+    ba2.step(1, s.fixed)
+    ba2.sync()
+    dx = ba2.export(capi.EXPORT_DX).cpu().numpy()
+    x = np.linalg.solve(S, y)
+    assert np.abs(dx - x).max() <= 1e-6 * np.abs(x).max(), (np.abs(dx - x).max(), np.abs(x).max())
+
+
 def test_gn_step_independent_of_input_edge_order():
     s = scenes.odometry(seed=2)
     order = np.random.default_rng(5).permutation(s.E)
