@@ -958,6 +958,20 @@ __device__ void tile_symv(const SymvRegs& g, const DFp* vr, const DFp* vc, bool 
   __syncthreads();
 }
 
+// System p finished after iteration s >= 1: the estimated error left in its
+// x is below 1e-7 of it (the last step bounds the previous iterate's error;
+// the current one's is about rho c_s with rho ~ c_s / c_{s-1}).  A finished
+// system takes no further part, so its later maxima stay 0 and it stays
+// finished.  The maxima of a completed iteration are final (grid barrier), so
+// every CTA reaches the same decision.
+__device__ __forceinline__ bool sys_finished(const int* conv, int nsys, int p, int s) {
+  if (s < 1) return false;
+  const float cm = __int_as_float(__ldcg(conv + 2 * (s * nsys + p)));
+  const float xm = __int_as_float(__ldcg(conv + 2 * (s * nsys + p) + 1));
+  const float cp = __int_as_float(__ldcg(conv + 2 * ((s - 1) * nsys + p)));
+  return cm <= 1e-7f * xm || cm * cm <= 1e-7f * xm * cp;
+}
+
 // Triangular solves and preconditioned conjugate gradients of all large
 // systems.  The FP32 factor M = L D L^T of the equilibrated S' = D_s S D_s
 // preconditions CG on S' z = D_s y (x = D_s z):
@@ -992,6 +1006,7 @@ __global__ void __launch_bounds__(LG_THREADS, 2) k_lg_solve(const LgProb* __rest
     // behind another's
     for (int q = blockIdx.x; q < R; q += gridDim.x) {
       const int r = rb_sys[R + q];
+      if (sys_finished(conv, nsys, rb_sys[r], sweep - 1)) continue;
       const LgProb& P = probs[rb_sys[r]];
       const int i = r - P.rb0;
       if (tid < NB) acc[tid] = __ldcg(P.rhs + i * NB + tid);
@@ -1023,6 +1038,7 @@ __global__ void __launch_bounds__(LG_THREADS, 2) k_lg_solve(const LgProb* __rest
     for (int q = blockIdx.x; q < R; q += gridDim.x) {
       const int r = rb_sys[2 * R + q];
       const int sy = rb_sys[r];
+      if (sys_finished(conv, nsys, sy, sweep - 1)) continue;
       const LgProb& P = probs[sy];
       const int i = r - P.rb0, T = P.T;
       // the forward result of this row (solved by whichever CTA owned it in
@@ -1091,6 +1107,7 @@ __global__ void __launch_bounds__(LG_THREADS, 2) k_lg_solve(const LgProb* __rest
     {
       DFp sig{0.f, 0.f};
       for (int sy = 0; sy < nsys; ++sy) {
+        if (sys_finished(conv, nsys, sy, sweep - 1)) continue;
         const LgProb& P = probs[sy];
         const double beta =
             sweep > 1 ? __ldcg(red + 2 * (sweep * nsys + sy)) / __ldcg(red + 2 * ((sweep - 1) * nsys + sy)) : 0.0;
@@ -1145,6 +1162,7 @@ __global__ void __launch_bounds__(LG_THREADS, 2) k_lg_solve(const LgProb* __rest
     // ---- updates: r (iteration 0: r = s (y - u)), or alpha steps of x and r
     for (int r = blockIdx.x; r < R; r += gridDim.x) {
       const int sy = rb_sys[r];
+      if (sys_finished(conv, nsys, sy, sweep - 1)) continue;
       const LgProb& P = probs[sy];
       const int q = (r - P.rb0) * NB + tid;
       float cmax = 0.f, xmax = 0.f;
@@ -1187,12 +1205,7 @@ __global__ void __launch_bounds__(LG_THREADS, 2) k_lg_solve(const LgProb* __rest
       // the previous iterate's error; the current one's is about rho c_s with
       // rho ~ c_s / c_{s-1})
       bool done = true;
-      for (int p = 0; p < nsys && done; ++p) {
-        const float cm = __int_as_float(ld_acquire(conv + 2 * (sweep * nsys + p)));
-        const float xm = __int_as_float(ld_acquire(conv + 2 * (sweep * nsys + p) + 1));
-        const float cp = __int_as_float(ld_acquire(conv + 2 * ((sweep - 1) * nsys + p)));
-        done = cm <= 1e-7f * xm || cm * cm <= 1e-7f * xm * cp;
-      }
+      for (int p = 0; p < nsys && done; ++p) done = sys_finished(conv, nsys, p, sweep);
       if (done) break;  // the same decision in every CTA
     }
   }
