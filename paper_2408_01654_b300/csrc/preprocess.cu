@@ -25,6 +25,8 @@ constexpr int RS_TILE = RS_THREADS * RS_ITEMS;
 constexpr int SCAN_THREADS = 1024;
 constexpr int SCAN_ITEMS = 4;
 constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
+constexpr int RS_SCAN_ITEMS = 4;  // the sort's own scan: 256 threads x 4 items per tile
+constexpr int RS_SCAN_TILE = RS_THREADS * RS_SCAN_ITEMS;
 
 // ---------------------------------------------------------------------------
 // exclusive scan of int32 (tile sums, scan of the sums, down-sweep)
@@ -137,33 +139,32 @@ __global__ void k_validate(int E, int N, int P, const int* __restrict__ ii, cons
 // __match_any_sync, warps are ordered through a per-digit prefix, so equal
 // keys keep their input order.
 // ---------------------------------------------------------------------------
-__global__ void k_rs_hist(const unsigned long long* __restrict__ keys, int M, int shift, int* __restrict__ hist,
-                          int nblocks, const int* run_if) {
-  __shared__ int cnt[256];
-  if (run_if && !*run_if) return;
+// one tile's digit counts: hist[digit * nblocks + tile]
+__device__ void rs_hist_tile(const unsigned long long* __restrict__ keys, int M, int shift, int* __restrict__ hist,
+                             int nblocks, int tile, int* cnt) {
   const int t = threadIdx.x;
   cnt[t] = 0;
   __syncthreads();
-  const int base = blockIdx.x * RS_TILE;
+  const int base = tile * RS_TILE;
 #pragma unroll
   for (int r = 0; r < RS_ITEMS; ++r) {
     const int idx = base + r * RS_THREADS + t;
     if (idx < M) atomicAdd(&cnt[(unsigned)(keys[idx] >> shift) & 255u], 1);
   }
   __syncthreads();
-  hist[(size_t)t * nblocks + blockIdx.x] = cnt[t];
+  hist[(size_t)t * nblocks + tile] = cnt[t];
+  __syncthreads();
 }
 
-__global__ void k_rs_scatter(const unsigned long long* __restrict__ kin, const int* __restrict__ vin,
-                             unsigned long long* __restrict__ kout, int* __restrict__ vout, int M, int shift,
-                             const int* __restrict__ offs, int nblocks, const int* run_if) {
-  __shared__ int base_off[256];
-  if (run_if && !*run_if) return;
-  __shared__ int wcnt[RS_THREADS / 32][256];
+// one tile's stable scatter to its digits' offsets
+__device__ void rs_scatter_tile(const unsigned long long* __restrict__ kin, const int* __restrict__ vin,
+                                unsigned long long* __restrict__ kout, int* __restrict__ vout, int M, int shift,
+                                const int* __restrict__ offs, int nblocks, int tile, int* base_off,
+                                int (*wcnt)[256]) {
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
-  base_off[t] = offs[(size_t)t * nblocks + blockIdx.x];
+  base_off[t] = offs[(size_t)t * nblocks + tile];
   const unsigned lt = (1u << lane) - 1u;
-  const int base = blockIdx.x * RS_TILE;
+  const int base = tile * RS_TILE;
   for (int r = 0; r < RS_ITEMS; ++r) {
 #pragma unroll
     for (int q = 0; q < RS_THREADS / 32; ++q) wcnt[q][t] = 0;
@@ -197,6 +198,122 @@ __global__ void k_rs_scatter(const unsigned long long* __restrict__ kin, const i
     }
     __syncthreads();
     base_off[t] += run;
+  }
+  __syncthreads();
+}
+
+// Grid-wide barrier of a cooperative launch (count / generation in bar[0..1],
+// count 0 on entry).  Gives up after `timeout` cycles or when another CTA
+// reported an error.  Returns success.
+__device__ bool rs_grid_barrier(int* bar, int* status, long long timeout) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ok = 1;
+    volatile int* gen = bar + 1;
+    const int g0 = *gen;
+    __threadfence();
+    if (atomicAdd(bar, 1) == (int)gridDim.x - 1) {
+      bar[0] = 0;
+      __threadfence();
+      atomicAdd(bar + 1, 1);
+    } else {
+      const long long t0 = clock64();
+      for (unsigned it = 0; *gen == g0; ++it) {
+        if ((it & 63u) == 63u && (dpv_status(status) || clock64() - t0 > timeout)) {
+          if (!dpv_status(status)) dpv_set_status(status, DST_TIMEOUT);
+          ok = 0;
+          break;
+        }
+        __nanosleep(32);
+      }
+      __threadfence();
+    }
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+// The whole stable LSD radix sort (8-bit digits, the low `bits` bits) in one
+// cooperative launch: per pass the tiles' histograms, the exclusive scan of
+// the histogram (tile sums, the sums' scan in CTA 0, down-sweep) and the
+// stable scatter, separated by grid barriers; CTAs stride over tiles.  Exits
+// at once when run_if is given and *run_if is 0 (an input already in order),
+// so that a sorted input costs one launch.  scratch: hist [256 nb], offs
+// [256 nb + 1], sums [ns + 1].
+__global__ void __launch_bounds__(RS_THREADS) k_radix_sort(unsigned long long* k0, int* v0, unsigned long long* k1,
+                                                           int* v1, int M, int bits, int* scratch, int* bar,
+                                                           const int* run_if, int* status, long long timeout) {
+  __shared__ int cnt[256];
+  __shared__ int wcnt[RS_THREADS / 32][256];
+  __shared__ int sh[32];
+  if (run_if && !*run_if) return;
+  if (dpv_status(status)) return;
+  const int nb = (M + RS_TILE - 1) / RS_TILE;
+  const int nh = 256 * nb;
+  const int ns = (nh + RS_SCAN_TILE - 1) / RS_SCAN_TILE;
+  int* hist = scratch;
+  int* offs = hist + nh;
+  int* sums = offs + nh + 1;
+  unsigned long long *kin = k0, *kout = k1;
+  int *vin = v0, *vout = v1;
+  for (int shift = 0; shift < bits; shift += 8) {
+    for (int t = blockIdx.x; t < nb; t += gridDim.x) rs_hist_tile(kin, M, shift, hist, nb, t, cnt);
+    if (!rs_grid_barrier(bar, status, timeout)) return;
+    // tile sums of the histogram
+    for (int t = blockIdx.x; t < ns; t += gridDim.x) {
+      int v = 0;
+#pragma unroll
+      for (int r = 0; r < RS_SCAN_ITEMS; ++r) {
+        const int idx = t * RS_SCAN_TILE + threadIdx.x * RS_SCAN_ITEMS + r;
+        if (idx < nh) v += hist[idx];
+      }
+      int total;
+      block_exclusive_scan(v, sh, total);
+      if (threadIdx.x == 0) sums[t] = total;
+    }
+    if (!rs_grid_barrier(bar, status, timeout)) return;
+    if (blockIdx.x == 0) {
+      const int per = (ns + RS_THREADS - 1) / RS_THREADS;
+      const int lo = threadIdx.x * per, hi = min(ns, lo + per);
+      int v = 0;
+      for (int q = lo; q < hi; ++q) v += sums[q];
+      int total;
+      int run = block_exclusive_scan(v, sh, total);
+      for (int q = lo; q < hi; ++q) {
+        const int x = sums[q];
+        sums[q] = run;
+        run += x;
+      }
+    }
+    if (!rs_grid_barrier(bar, status, timeout)) return;
+    // down-sweep: offs = exclusive scan of hist
+    for (int t = blockIdx.x; t < ns; t += gridDim.x) {
+      const int base = t * RS_SCAN_TILE + threadIdx.x * RS_SCAN_ITEMS;
+      int v[RS_SCAN_ITEMS], sum = 0;
+#pragma unroll
+      for (int r = 0; r < RS_SCAN_ITEMS; ++r) {
+        v[r] = (base + r < nh) ? hist[base + r] : 0;
+        sum += v[r];
+      }
+      int total;
+      int run = block_exclusive_scan(sum, sh, total) + sums[t];
+#pragma unroll
+      for (int r = 0; r < RS_SCAN_ITEMS; ++r) {
+        if (base + r < nh) offs[base + r] = run;
+        run += v[r];
+      }
+    }
+    if (!rs_grid_barrier(bar, status, timeout)) return;
+    for (int t = blockIdx.x; t < nb; t += gridDim.x)
+      rs_scatter_tile(kin, vin, kout, vout, M, shift, offs, nb, t, cnt, wcnt);
+    if (!rs_grid_barrier(bar, status, timeout)) return;
+    unsigned long long* tk = kin;
+    kin = kout;
+    kout = tk;
+    int* tv = vin;
+    vin = vout;
+    vout = tv;
   }
 }
 
@@ -392,36 +509,52 @@ __global__ void k_key_emit(int M, int N, const unsigned long long* __restrict__ 
 }
 
 // Sorts (k0, v0) by the low `bits` bits of the keys; `which` tells whether
-// the result ended in (k0, v0) or (k1, v1).  hist needs dpv_hist_entries(M).
+// the result ended in (k0, v0) or (k1, v1).  scratch needs dpv_hist_entries(M)
+// ints (its last two are the grid barrier's words).  One cooperative launch.
 ba_status_t radix_sort(ba_handle_t h, unsigned long long* k0, int* v0, unsigned long long* k1, int* v1, int M,
-                       int bits, int* hist, int& which, const int* run_if = nullptr) {
+                       int bits, int* scratch, int& which, const int* run_if = nullptr) {
   which = 0;
   if (M <= 1) return BA_OK;
+  which = ((bits + 7) / 8) & 1;
   const int nb = (M + RS_TILE - 1) / RS_TILE;
-  unsigned long long* kin = k0;
-  unsigned long long* kout = k1;
-  int* vin = v0;
-  int* vout = v1;
-  int* offs = hist + 256 * nb;
-  for (int shift = 0; shift < bits; shift += 8) {
-    k_rs_hist<<<nb, RS_THREADS, 0, h->stream>>>(kin, M, shift, hist, nb, run_if);
-    ++h->launches;
-    ba_status_t st = dpv_exclusive_scan(h, hist, offs, 256 * nb, run_if);
-    if (st) return st;
-    k_rs_scatter<<<nb, RS_THREADS, 0, h->stream>>>(kin, vin, kout, vout, M, shift, offs, nb, run_if);
-    ++h->launches;
-    std::swap(kin, kout);
-    std::swap(vin, vout);
-    which ^= 1;
+  int* bar = scratch + dpv_hist_entries(M) - 2;
+  static int per_sm = 0;  // co-resident CTAs per SM (queried by an eager run, never inside a graph capture)
+  if (!per_sm) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_radix_sort, RS_THREADS, 0) != cudaSuccess ||
+        per_sm < 1) {
+      cudaGetLastError();
+      per_sm = 0;
+      return dpv_fail(h, BA_ERR_CUDA, "radix sort occupancy");
+    }
   }
-  DPV_CUDA(h, cudaGetLastError());
+  int grid = std::min(nb, per_sm * h->num_sms);
+  DPV_CUDA(h, cudaMemsetAsync(bar, 0, 2 * sizeof(int), h->stream));
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(RS_THREADS);
+  cfg.stream = h->stream;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  long long timeout = h->opt.timeout_cycles;
+  int* status = h->ws->status;
+  void* args[] = {(void*)&k0,      (void*)&v0,  (void*)&k1,     (void*)&v1,     (void*)&M,      (void*)&bits,
+                  (void*)&scratch, (void*)&bar, (void*)&run_if, (void*)&status, (void*)&timeout};
+  DPV_CUDA(h, cudaLaunchKernelExC(&cfg, (const void*)k_radix_sort, args));
+  ++h->launches;
   return BA_OK;
 }
 
 }  // namespace
 
 long long dpv_scan_scratch(long long n) { return (n + SCAN_TILE - 1) / SCAN_TILE + 2; }
-long long dpv_hist_entries(long long m) { return 2 * 256 * ((m + RS_TILE - 1) / RS_TILE) + 2; }
+long long dpv_hist_entries(long long m) {
+  const long long nh = 256 * ((m + RS_TILE - 1) / RS_TILE);
+  // histogram, its exclusive scan (+ total), the scan's tile sums, two barrier words
+  return 2 * nh + 1 + (nh + RS_SCAN_TILE - 1) / RS_SCAN_TILE + 1 + 2;
+}
 
 ba_status_t dpv_exclusive_scan(ba_handle_t h, const int* in, int* out, int n, const int* run_if) {
   Workspace* ws = h->ws;
