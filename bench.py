@@ -32,6 +32,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 from paper_2408_01654_b300 import scenes  # noqa: E402
+from paper_2408_01654_b300.multi import job_throughput, max_over_ranks, problem_seed  # noqa: E402
 
 METRIC = "GN iterations/sec and edges/sec for patch-graph BA at stated FP64-oracle error"
 UNIT = "GN it/s"
@@ -336,7 +337,7 @@ def run_ours(args):
     if dist:
         dist.barrier()
     desc, make = WORKLOADS[args.workload]
-    scene = make(seed=rank)
+    scene = make(seed=problem_seed(rank))  # independent problems per rank, no data-path collective
     dev = torch.device("cuda", local)
     T = scene_tensors(scene, dev)
     pristine = {k: v.clone() for k, v in T.items()}
@@ -386,12 +387,9 @@ def run_ours(args):
     prof = ba.profile_read()
     launches = ba.info()["launches"] - launches0
     replays = {"ba_step": ba.info()["graph_replays"], "binding": ba.info()["bind_replays"]}
-    if dist:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, dev)  # the slowest rank's time
     gn_iters = world * args.steps * scene.iters
-    value = gn_iters / (total_ms / 1e3)
+    value = job_throughput(args.steps * scene.iters, world, total_ms)
 
     # ---- end to end through the C ABI with host buffers -------------------
     # (no event records: the step runs as a user's would; the first steps
@@ -417,12 +415,8 @@ def run_ours(args):
         host_out["patches"].copy_(T["patches"], non_blocking=True)
         e2e_ev[k][1].record(stream)
     torch.cuda.synchronize()
-    e2e_ms = sum(a.elapsed_time(b) for a, b in e2e_ev)
-    if dist:
-        t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    e2e_value = gn_iters / (e2e_ms / 1e3)
+    e2e_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in e2e_ev), dev)
+    e2e_value = job_throughput(args.steps * scene.iters, world, e2e_ms)
 
     # ---- adjoint of the same step (ba_backward), timed on its own ----------
     g = torch.Generator(device=dev).manual_seed(rank)
@@ -536,7 +530,7 @@ def run_batched(args):
     if dist:
         dist.barrier()
     desc, make = WORKLOADS["batched"]
-    probs = make(seed=rank)
+    probs = make(seed=problem_seed(rank))
     iters, fixed = probs[0].iters, probs[0].fixed
     dev = torch.device("cuda", local)
     T, offs = batch_tensors(probs, dev)
@@ -588,11 +582,8 @@ def run_batched(args):
     prof = ba.profile_read()
     launches = ba.info()["launches"] - launches0
     replays = {"ba_step": ba.info()["graph_replays"], "binding": ba.info()["bind_replays"]}
-    if dist:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * args.steps * B * iters / (total_ms / 1e3)
+    total_ms = max_over_ranks(total_ms, dev)  # the slowest rank's time
+    value = job_throughput(args.steps * B * iters, world, total_ms)
 
     # the plain form: one FP32 handle per problem, problem after problem
     plain_T = [scene_tensors(sc, dev) for sc in probs]
@@ -643,7 +634,7 @@ def run_batched(args):
         host_out["patches"].copy_(T["patches"], non_blocking=True)
         e2e_ev[k][1].record(stream)
     torch.cuda.synchronize()
-    e2e_value = world * args.steps * B * iters / (sum(a.elapsed_time(b) for a, b in e2e_ev) / 1e3)
+    e2e_value = job_throughput(args.steps * B * iters, world, max_over_ranks(sum(a.elapsed_time(b) for a, b in e2e_ev), dev))
     if rank != 0:
         if dist:
             dist.destroy_process_group()
