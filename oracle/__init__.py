@@ -18,6 +18,12 @@ of arxiv 2408.01654 it follows:
 * ``gn``           whole Gauss-Newton iterations: linearise, Schur-eliminate,
                    Cholesky-solve the pose system, back-substitute the depths,
                    retract the poses on SE(3).
+* ``proximity_edges`` loop edges from camera proximity (Sec. 3.2 "Proximity
+                   Loop Closure"): for each query frame the nearest older
+                   camera centre within a radius, then uni-directional edges
+                   from that frame's patches to the query frame, kept where
+                   the Eq. 2 reprojection lies in front of the camera and
+                   inside the image.
 * ``grad_fwd``     exact derivatives of a linear functional of the final state
                    with respect to single targets/weights (dual numbers through
                    the unrolled iterations).
@@ -191,3 +197,32 @@ def block_keys(ii, jj, fixed):
             if a >= fixed and b >= fixed:
                 keys.add((a, b))
     return np.array(sorted(keys), dtype=np.int32).reshape(-1, 2)
+
+
+def proximity_edges(poses, patches, intrinsics, M, b0, b1, gap=30, radius=2.0, z_min=DEFAULT_OPTS[2],
+                    width=640.0, height=480.0, cap=None):
+    """Proximity loop edges for the query frames b0 <= b < b1 (the rule is
+    stated beside ``oracle_proximity_edges`` in ba_oracle.cpp).  poses [N,7]
+    world->camera, patches [N*M,3,3,3] (patch a*M + m belongs to frame a).
+    Returns a dict: match [Q] (selected old frame or -1), dist [Q] (nearest
+    candidate distance or -1), margin [Q] (scaled distance of the query's
+    closest decision from its threshold), ii, jj, kk [n] int32 and coords
+    [n,2] float64, ordered by query frame then patch."""
+    poses = _d(poses)
+    patches = _d(patches)
+    N = len(poses)
+    if patches.shape[0] != N * M:
+        raise ValueError("patches must hold M patches per frame")
+    Q = max(0, b1 - b0)
+    cap = Q * M if cap is None else cap
+    match, dist, margin = np.empty(Q, np.int32), np.empty(Q), np.empty(Q)
+    ii, jj, kk = np.empty(cap, np.int32), np.empty(cap, np.int32), np.empty(cap, np.int32)
+    coords = np.empty((cap, 2))
+    n = ctypes.c_longlong()
+    _check(lib().oracle_proximity_edges(
+        N, M, _p(poses), _p(patches), _p(_d(intrinsics)), b0, b1, gap, ctypes.c_double(radius),
+        ctypes.c_double(z_min), ctypes.c_double(width), ctypes.c_double(height), _p(match), _p(dist),
+        _p(margin), _p(ii), _p(jj), _p(kk), _p(coords), ctypes.c_longlong(cap), ctypes.byref(n)))
+    m = min(n.value, cap)
+    return {"match": match, "dist": dist, "margin": margin, "ii": ii[:m], "jj": jj[:m], "kk": kk[:m],
+            "coords": coords[:m], "n": n.value}

@@ -127,6 +127,7 @@ template <class T> void se3_retract(const T xi[6], Pose<T>& p) {
 // per-edge reprojection, residual and Jacobians (Eq. 2 and Eq. 3)
 // ----------------------------------------------------------------------------
 template <class T> struct EdgeTerms {
+  T X[3];  // the point in frame j, homogeneous with last coordinate d: X / d in metres
   T proj[2], r[2];
   T Ji[2][6], Jj[2][6], Jd[2];
   bool valid;
@@ -149,6 +150,7 @@ void edge_terms(const Pose<T>& Pi, const Pose<T>& Pj, T u, T v, T d, const T tgt
   const T xb[3] = {(u - cx) / fx, (v - cy) / fy, T(1.0)};
   T X[3];
   for (int r = 0; r < 3; ++r) X[r] = R[3 * r] * xb[0] + R[3 * r + 1] * xb[1] + R[3 * r + 2] * xb[2] + t[r] * d;
+  for (int r = 0; r < 3; ++r) o.X[r] = X[r];
   o.valid = !self_edge && val(X[2]) > z_min * val(d);
   const T iz = 1.0 / X[2];
   o.proj[0] = fx * X[0] * iz + cx;
@@ -559,6 +561,102 @@ int oracle_grad_fwd(int N, int P, int E, const double* poses, const double* patc
     for (int k = 0; k < P; ++k) g += b[k] * pb.d[k].d;
     out[c] = g;
   }
+  return 0;
+}
+
+// Proximity loop edges (Sec. 3.2 "Proximity Loop Closure", "Constructing the
+// Patch Graph"): loops are found from how close the camera comes to a place it
+// visited before, and every loop adds uni-directional edges from the stored
+// patches of the old frame to the recent frame, so that only the recent
+// frame's dense features are needed.  The paper gives no numbers; the rule
+// taken here, for each query frame b in [b0, b1):
+//   candidates : frames a with 0 <= a and b - a > gap (strictly older);
+//   distance   : Euclidean distance between camera centres c = -R^T t of the
+//                world->camera poses (the camera positions in the world);
+//   selection  : the nearest candidate (the lowest index among equals), kept
+//                if its distance is < radius;
+//   edges      : patch k = a*M + m of that frame a, for m = 0..M-1, observed in
+//                frame b (ii = a, jj = b, kk = k), kept if its centre pixel
+//                reprojects (Eq. 2, current inverse depth) at least z_min in
+//                front of frame b and inside [0, width) x [0, height);
+//   order      : by b, then m.
+// Outputs: match[q] (the selected a, or -1), dist[q] (distance of the nearest
+// candidate, -1 if there is none), margin[q] (the smallest distance of any of
+// the query's decisions from its threshold, scaled: (second - nearest) /
+// radius, |nearest - radius| / radius, |X_z - z_min d| / (|X_z| + z_min |d|),
+// the reprojection's pixel distance to the image border / max(width, height);
+// 1e300 when there is nothing to decide), and the first `cap` edges with their
+// reprojected centres coords [.,2]; *n_out = number of edges (may exceed cap).
+int oracle_proximity_edges(int N, int M, const double* poses, const double* patches, const double* intr, int b0,
+                           int b1, int gap, double radius, double z_min, double width, double height, int* match,
+                           double* dist, double* margin, int* ii, int* jj, int* kk, double* coords,
+                           long long cap, long long* n_out) {
+  if (N < 1 || M < 1 || b0 < 0 || b1 < b0 || b1 > N || gap < 0) return 1;
+  std::vector<double> centre(3 * (size_t)N);
+  std::vector<Pose<double>> ps(N);
+  for (int a = 0; a < N; ++a) {
+    for (int r = 0; r < 3; ++r) ps[a].t[r] = poses[7 * (size_t)a + r];
+    for (int r = 0; r < 4; ++r) ps[a].q[r] = poses[7 * (size_t)a + 3 + r];
+    double R[9];
+    quat_to_rot(ps[a].q, R);
+    for (int c = 0; c < 3; ++c)  // (R^T t)_c = sum_r R[r][c] t[r]
+      centre[3 * (size_t)a + c] = -(R[c] * ps[a].t[0] + R[3 + c] * ps[a].t[1] + R[6 + c] * ps[a].t[2]);
+  }
+  long long n = 0;
+  const double tgt0[2] = {0.0, 0.0};
+  for (int b = b0; b < b1; ++b) {
+    const int q = b - b0;
+    int best = -1;
+    double d1 = 0.0, d2 = -1.0;  // nearest and second-nearest candidate distances
+    for (int a = 0; a < b - gap; ++a) {
+      double s = 0.0;
+      for (int c = 0; c < 3; ++c) {
+        const double e = centre[3 * (size_t)a + c] - centre[3 * (size_t)b + c];
+        s += e * e;
+      }
+      const double d = std::sqrt(s);
+      if (best < 0 || d < d1) {
+        d2 = best < 0 ? -1.0 : d1;
+        best = a;
+        d1 = d;
+      } else if (d2 < 0.0 || d < d2) {
+        d2 = d;
+      }
+    }
+    double mg = 1e300;
+    match[q] = -1;
+    dist[q] = best < 0 ? -1.0 : d1;
+    if (best >= 0) {
+      mg = std::min(mg, std::fabs(d1 - radius) / radius);
+      if (d1 < radius) {
+        match[q] = best;
+        if (d2 >= 0.0) mg = std::min(mg, (d2 - d1) / radius);
+        EdgeTerms<double> et;
+        for (int m = 0; m < M; ++m) {
+          const long long k = (long long)best * M + m;
+          const double* pk = patches + 27 * k;
+          const double u = pk[4], v = pk[9 + 4], d = pk[18 + 4];
+          edge_terms(ps[best], ps[b], u, v, d, tgt0, intr, z_min, false, et);
+          mg = std::min(mg, std::fabs(et.X[2] - z_min * d) / (std::fabs(et.X[2]) + z_min * std::fabs(d)));
+          if (!et.valid) continue;
+          const double x = et.proj[0], y = et.proj[1];
+          mg = std::min(mg, std::min(std::min(std::fabs(x), std::fabs(x - width)),
+                                     std::min(std::fabs(y), std::fabs(y - height))) / std::max(width, height));
+          if (!(x >= 0.0 && x < width && y >= 0.0 && y < height)) continue;
+          if (n < cap) {
+            ii[n] = best;
+            jj[n] = b;
+            kk[n] = (int)k;
+            coords[2 * n] = x;
+            coords[2 * n + 1] = y;
+          }
+          ++n;
+        }
+      }
+    }
+    margin[q] = mg;
+  }
+  *n_out = n;
   return 0;
 }
 
