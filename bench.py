@@ -48,10 +48,17 @@ WORKLOADS = {
     "loop400": ("loop-closure BA at the batch's largest size: 400 keyframes, 96 patches/frame, +-6 local + "
                 "proximity loop edges, 4 GN iterations, 2 fixed poses (profiling case of the large-system kernels)",
                 lambda seed=0: scenes.global_ba(seed, N=400)),
+    "proximity": ("proximity loop-edge construction (Sec. 3.2): 1000 keyframes, 96 patches/frame, every frame "
+                  "queried against all frames more than 30 older, radius 2 m, current pose and depth estimates of "
+                  "the global workload", scenes.global_ba),
     "batched": ("batched uneven BA: 64 independent problems, frames round(exp(U[ln 8, ln 400])), 96 patches/frame, "
                 "+-6 local + proximity loop edges, 4 GN iterations each, 2 fixed poses each", scenes.batched),
 }
-KERNEL_FILES = {"assemble": "assemble.cu", "solve": "solve_small.cu", "factor": "solve_large.cu", "backsub": "update.cu",
+PROX_METRIC = "proximity loop-edge constructions/sec (all 1000 frames queried) at bit-exact edges vs the FP64 oracle"
+PROX_UNIT = "constructions/s"
+PROX_GAP, PROX_RADIUS = 30, 2.0
+FP64_NOMINAL_TFLOPS = 1.25  # B300 FP64 (non-tensor) nominal rate
+KERNEL_FILES = {"proximity": "proximity.cu", "assemble": "assemble.cu", "solve": "solve_small.cu", "factor": "solve_large.cu", "backsub": "update.cu",
                 "retract": "update.cu", "init": "assemble.cu", "preprocess": "preprocess.cu"}
 
 
@@ -73,7 +80,8 @@ def parse():
     a = ap.parse_args()
     if a.steps is None:
         # (the reference arm's oracle steps are ~50 ms each on one core: 50 of them)
-        a.steps = 3 if a.workload not in ("odometry", "tiny") else (50 if a.impl == "reference" else 2000)
+        short = a.workload in ("odometry", "tiny", "proximity")
+        a.steps = 3 if not short else (50 if a.impl == "reference" else 2000)
     a.precision_set = a.precision is not None
     if a.precision is None:
         a.precision = "fp32"
@@ -265,10 +273,206 @@ def cpu_cores():
         return os.cpu_count()
 
 
+def prox_counts(scene, match):
+    """Algorithmic work of one construction: candidate pairs (each 3 FP64
+    differences, 3 products, 2 sums), reprojected patches of the matched
+    queries (~40 FP64 operations each: back-projection, 3x3 rotation,
+    translation, division, pinhole), frames' centres (~30 each)."""
+    N, M = scene.N, scenes.PATCHES_PER_FRAME
+    pairs = sum(max(0, b - PROX_GAP) for b in range(N))
+    matched = int(np.count_nonzero(np.asarray(match) >= 0))
+    flops = 8.0 * pairs + 40.0 * matched * M + 30.0 * N
+    return pairs, matched, flops
+
+
+def prox_oracle(scene):
+    import oracle
+    oracle.build()
+    return oracle.proximity_edges(scene.poses, scene.patches, scene.intrinsics, scenes.PATCHES_PER_FRAME, 0,
+                                  scene.N, gap=PROX_GAP, radius=PROX_RADIUS, z_min=float(np.float32(0.1)))
+
+
+def run_reference_proximity(args):
+    if int(os.environ.get("RANK", "0")) != 0:
+        return 0
+    desc, make = WORKLOADS["proximity"]
+    scene = make(seed=0)
+    for _ in range(min(args.warmup, 3)):
+        prox_oracle(scene)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        r = prox_oracle(scene)
+    el = time.perf_counter() - t0
+    value = args.steps / el
+    line = {
+        "impl": "reference", "metric": PROX_METRIC, "value": value, "unit": PROX_UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": desc, "N": scene.N, "M": scenes.PATCHES_PER_FRAME, "edges": r["n"]},
+        "loop_edges_per_sec": value * r["n"],
+        "cpu_baseline": {"value": value, "unit": PROX_UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{args.steps} full constructions, single-threaded FP64 oracle (-O2), "
+                                   f"{cpu_cores()} cores visible"},
+        "e2e": {"value": value, "unit": PROX_UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def run_proximity(args):
+    """One step = one ba_proximity_edges call over all frames of the
+    1000-frame global scene (its current, perturbed estimates)."""
+    import torch
+
+    from paper_2408_01654_b300 import build as pbuild
+    from paper_2408_01654_b300.ba import DPVBA
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    if rank == 0:
+        pbuild.build()
+    if dist:
+        dist.barrier()
+    desc, make = WORKLOADS["proximity"]
+    scene = make(seed=problem_seed(rank))
+    N, M = scene.N, scenes.PATCHES_PER_FRAME
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    poses = torch.tensor(scene.poses, device=dev)
+    patches = torch.tensor(scene.patches, device=dev)
+    intr = [float(x) for x in scene.intrinsics]
+    ba = DPVBA(stream=stream)
+    cap = N * M
+    out = {"ii": torch.empty(cap, dtype=torch.int32, device=dev), "jj": torch.empty(cap, dtype=torch.int32, device=dev),
+           "kk": torch.empty(cap, dtype=torch.int32, device=dev),
+           "coords": torch.empty((cap, 2), dtype=torch.float32, device=dev),
+           "match": torch.empty(N, dtype=torch.int32, device=dev), "count": torch.zeros(1, dtype=torch.int32, device=dev)}
+    first = ba.proximity_edges(poses, patches, intr, M, 0, N, gap=PROX_GAP, radius=PROX_RADIUS, out=out)
+    n_edges = first["n"]
+    match = first["match"].cpu().numpy()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > L2 (126 MB)
+
+    def call():
+        ba.proximity_edges(poses, patches, intr, M, 0, N, gap=PROX_GAP, radius=PROX_RADIUS, out=out, sync=False)
+
+    ba.profile(True)
+    for _ in range(max(args.warmup, 3)):
+        call()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    launches0 = ba.info()["launches"]
+    ba.profile(True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            call()
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = max_over_ranks(sum(step_ms), dev)
+    prof = ba.profile_read()
+    launches = ba.info()["launches"] - launches0
+    ba.profile(False)
+    value = job_throughput(args.steps, world, total_ms)
+
+    # end to end: poses and patches from pinned host memory, the edges back
+    host_p = torch.tensor(scene.poses).pin_memory()
+    host_t = torch.tensor(scene.patches).pin_memory()
+    back = {k: torch.empty(n_edges, dtype=torch.int32).pin_memory() for k in ("ii", "jj", "kk")}
+    back["coords"] = torch.empty((n_edges, 2), dtype=torch.float32).pin_memory()
+    back["count"] = torch.empty(1, dtype=torch.int32).pin_memory()
+    h2d = host_p.numel() * 8 + host_t.numel() * 4
+    d2h = 4 + n_edges * (12 + 8)
+    eev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for k in range(args.steps):
+        flush.zero_()
+        eev[k][0].record(stream)
+        poses.copy_(host_p, non_blocking=True)
+        patches.copy_(host_t, non_blocking=True)
+        call()
+        back["count"].copy_(out["count"], non_blocking=True)
+        for name in ("ii", "jj", "kk", "coords"):
+            back[name].copy_(out[name][:n_edges], non_blocking=True)
+        eev[k][1].record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in eev), dev)
+    e2e_value = job_throughput(args.steps, world, e2e_ms)
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return 0
+
+    pairs, matched, flops = prox_counts(scene, match)
+    t_ms, cnt = prof["proximity"]
+    per_launch_s = t_ms / cnt / 1e3
+    achieved = flops / per_launch_s / 1e12
+    ab = 56 * N + matched * M * 12 + n_edges * 20 + 4
+    roof = {"kernel": "k_prox_centres + k_prox_select + k_prox_emit (one call)", "bound": "alu",
+            "achieved": achieved, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
+            "frac": achieved / FP64_NOMINAL_TFLOPS, "traffic": committed_traffic("proximity", "proximity"),
+            "algorithmic_fp64_flops_per_launch": flops, "algorithmic_bytes_per_launch": ab,
+            "hbm_frac_of_measured": ab / per_launch_s / 1e9 / measured_peaks()[0],
+            "avg_launch_us": per_launch_s * 1e6, "peak_source": "nominal FP64 rate (no measured FP64 peak)"}
+
+    parity = None
+    cpu = None
+    if not args.no_cpu_baseline:
+        t0 = time.perf_counter()
+        want = prox_oracle(scene)
+        runs = 1
+        while time.perf_counter() - t0 < 10.0:
+            prox_oracle(scene)
+            runs += 1
+        el = time.perf_counter() - t0
+        got = {k: out[k][:n_edges].cpu().numpy() for k in ("ii", "jj", "kk")}
+        exact = (want["n"] == n_edges and np.array_equal(want["match"], match)
+                 and all(np.array_equal(got[k], want[k]) for k in ("ii", "jj", "kk")))
+        px = float(np.abs(out["coords"][:n_edges].cpu().numpy().astype(np.float64) - want["coords"]).max(initial=0.0))
+        parity = {"edges": n_edges, "oracle_edges": want["n"], "matched_queries": matched, "indices_exact": bool(exact),
+                  "max_pixel_diff": px, "min_decision_margin": float(want["margin"].min())}
+        cpu = {"value": runs / el, "unit": PROX_UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{runs} full constructions, single-threaded FP64 oracle (-O2) on 1 of {cpu_cores()} "
+                         f"host cores, {el:.1f} s"}
+    line = {
+        "metric": PROX_METRIC, "value": value, "unit": PROX_UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": desc, "N": N, "M": M, "gap": PROX_GAP, "radius_m": PROX_RADIUS,
+                   "candidate_pairs": pairs, "l2": "flushed between steps (256 MiB write)",
+                   "step": "ba_proximity_edges (queued, count left on the device)"},
+        "loop_edges_per_sec": value * n_edges,
+        "parity_vs_oracle": parity,
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": PROX_UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "clocks": clk.summary(),
+        "step_ms": {"min": min(step_ms), "median": statistics.median(step_ms), "max": max(step_ms)},
+    }
+    print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
+    if args.workload == "proximity":
+        return run_reference_proximity(args)
     desc, make = WORKLOADS[args.workload]
     import oracle
     oracle.build()
@@ -724,6 +928,8 @@ def main():
         return run_reference(args)
     if args.workload == "batched":
         return run_batched(args)
+    if args.workload == "proximity":
+        return run_proximity(args)
     return run_ours(args)
 
 

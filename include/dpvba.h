@@ -252,7 +252,8 @@ enum {
   BA_KERNEL_RETRACT = 5,    /* SE(3) retraction                                  */
   BA_KERNEL_ADJOINT = 6,    /* adjoint-only kernels of ba_backward               */
   BA_KERNEL_FACTOR = 7,     /* the persistent factorisation of systems > 256 unknowns */
-  BA_KERNEL_CLASSES = 8
+  BA_KERNEL_PROXIMITY = 8,  /* ba_proximity_edges                                */
+  BA_KERNEL_CLASSES = 9
 };
 
 /* on != 0: from now on record a CUDA event pair around every launch of each
@@ -303,6 +304,49 @@ DPVBA_API ba_status_t ba_set_record(ba_handle_t h, int on);
 DPVBA_API ba_status_t ba_backward(ba_handle_t h, const double* grad_poses, const float* grad_depths,
                                   float* grad_targets, float* grad_weights, double* grad_tangent0,
                                   float* grad_depths0);
+
+/* ---- proximity loop edges ----------------------------------------------- */
+
+/* Loop-closure edges from camera proximity (Sec. 3.2 "Proximity Loop Closure"
+ * and "Constructing the Patch Graph"): a loop is detected when the camera
+ * comes close to where an older frame was, and it is closed with
+ * uni-directional edges from that old frame's stored patches to the recent
+ * frame (so only recent frames need dense features).  For every query frame
+ * b in [b0, b1):
+ *   - the candidates are the frames a with b - a > gap;
+ *   - the selected frame is the candidate whose camera centre c = -R^T t is
+ *     nearest to frame b's (lowest index among equal distances), if the
+ *     squared distance is < radius^2 (FP64);
+ *   - its patches m = 0..M-1 (patch index k = a*M + m) become edges
+ *     (ii, jj, kk) = (a, b, k) if the centre pixel reprojects by Eq. 2, at
+ *     the patch's current inverse depth, more than the handle's z_min in
+ *     front of frame b and inside [0, width) x [0, height) (FP64).
+ * Edges are written in the order (b, m), at most `cap` of them.
+ *   poses      : device float64 [N,7] world->camera (as for ba_set_graph).
+ *   patches    : device float32 [N*M,3,3,3]; patch a*M + m belongs to frame a.
+ *   intrinsics : HOST float32 [4] (fx, fy, cx, cy), read during the call.
+ *   ii, jj, kk : device int32 [cap] (may be null when cap == 0); pointing them
+ *                past the local edges of a graph appends the loop edges.
+ *   coords     : device float32 [cap,2], 8-byte aligned, or null: the
+ *                reprojected centre pixel of each edge (FP64 rounded).
+ *   match      : device int32 [b1-b0] or null: selected frame of each query,
+ *                -1 if none.
+ *   count      : device int32 [1]: the number of edges found (may exceed cap;
+ *                only the first cap are written).
+ *   n_host     : host or null.  Non-null: the call waits for its work and
+ *                stores the count; returns BA_ERR_INVALID_ARG if it exceeds
+ *                cap (the first cap edges are still written).  Null: the
+ *                call only queues work and may be captured into a CUDA graph
+ *                once a first call of the same or larger size has sized the
+ *                handle's scratch.
+ * Limits: 1 <= M <= 1024, N*M < 2^31, 0 <= b0 <= b1 <= N, gap >= 0,
+ * 0 <= radius < inf, width, height > 0; anything else returns
+ * BA_ERR_INVALID_ARG at once and queues nothing.  cap >= (b1-b0)*M always
+ * suffices.  Uses the handle's stream and scratch; needs no bound graph. */
+DPVBA_API ba_status_t ba_proximity_edges(ba_handle_t h, int N, int M, const double* poses, const float* patches,
+                                         const float* intrinsics, int b0, int b1, int gap, double radius,
+                                         double width, double height, int* ii, int* jj, int* kk, float* coords,
+                                         long long cap, int* match, int* count, long long* n_host);
 
 /* ---- allocation-free pose-system solve ---------------------------------- */
 

@@ -141,6 +141,69 @@ class DPVBA:
                                                   _ptr(x0), _ptr(d0)))
         return (gT, gW, x0, d0) if initial else (gT, gW)
 
+    # ------------------------------------------------------- loop closure
+    def proximity_edges(self, poses, patches, intrinsics, M: int, b0: int = 0, b1: int | None = None,
+                        gap: int = 30, radius: float = 2.0, width: float = 640.0, height: float = 480.0,
+                        out: dict | None = None, sync: bool = True) -> dict:
+        """Proximity loop edges for the query frames b0 <= b < b1 (see
+        ba_proximity_edges): poses float64 [N,7], patches float32 [N*M,3,3,3]
+        on the device; intrinsics 4 numbers (any tensor or sequence).
+
+        ``out`` may supply the output tensors (int32 ``ii``, ``jj``, ``kk`` of
+        equal length = the capacity, optional float32 [cap,2] ``coords``,
+        int32 [b1-b0] ``match``, int32 [1] ``count``), e.g. views past a
+        graph's local edges; missing ones are allocated with capacity
+        (b1-b0)*M.  ``sync=True`` waits and returns the first n edges (n
+        from the count); ``sync=False`` only queues the work (capturable)
+        and returns the full buffers with the device-side count."""
+        N = poses.shape[0]
+        b1 = N if b1 is None else b1
+        for name, t, dt in (("poses", poses, torch.float64), ("patches", patches, torch.float32)):
+            if t.dtype != dt or not t.is_contiguous() or not t.is_cuda:
+                raise TypeError(f"{name}: need a contiguous CUDA {dt} tensor")
+        if patches.shape[0] < N * M:
+            raise ValueError("patches must hold M patches for each of the N frames")
+        if isinstance(intrinsics, torch.Tensor):
+            intrinsics = intrinsics.detach().cpu().tolist()
+        intr = (ctypes.c_float * 4)(*[float(x) for x in intrinsics])
+        Q = max(0, b1 - b0)
+        dev = poses.device
+        out = dict(out or {})
+        if "ii" not in out:
+            cap = Q * M
+            for name in ("ii", "jj", "kk"):
+                out[name] = torch.empty(cap, dtype=torch.int32, device=dev)
+            out.setdefault("coords", torch.empty((cap, 2), dtype=torch.float32, device=dev))
+        cap = out["ii"].shape[0]
+        out.setdefault("match", torch.empty(max(Q, 1), dtype=torch.int32, device=dev))
+        out.setdefault("count", torch.zeros(1, dtype=torch.int32, device=dev))
+        for name in ("ii", "jj", "kk", "match", "count"):
+            t = out[name]
+            if t.dtype != torch.int32 or not t.is_contiguous() or not t.is_cuda:
+                raise TypeError(f"{name}: need a contiguous CUDA int32 tensor")
+        if out["jj"].shape[0] < cap or out["kk"].shape[0] < cap or out["match"].shape[0] < Q:
+            raise ValueError("output tensors too short")
+        coords = out.get("coords")
+        if coords is not None and (coords.dtype != torch.float32 or not coords.is_contiguous()
+                                   or coords.shape[0] < cap):
+            raise TypeError("coords: need a contiguous CUDA float32 [cap,2] tensor")
+        self._prox_keep = (poses, patches, out)
+        n = ctypes.c_longlong(-1)
+        capi.check(self._h, self._lib.ba_proximity_edges(
+            self._h, N, M, _ptr(poses), _ptr(patches), intr, b0, b1, gap, ctypes.c_double(radius),
+            ctypes.c_double(width), ctypes.c_double(height), _ptr(out["ii"]), _ptr(out["jj"]), _ptr(out["kk"]),
+            _ptr(coords), ctypes.c_longlong(cap), _ptr(out["match"]), _ptr(out["count"]),
+            ctypes.byref(n) if sync else None))
+        if not sync:
+            return out
+        m = n.value
+        res = {k: out[k][:m] for k in ("ii", "jj", "kk")}
+        if coords is not None:
+            res["coords"] = coords[:m]
+        res["match"] = out["match"][:Q]
+        res["n"] = m
+        return res
+
     # ------------------------------------------------------------ inspection
     def linearize(self, fixed: int):
         capi.check(self._h, self._lib.ba_linearize(self._h, fixed))
