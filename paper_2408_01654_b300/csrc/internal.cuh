@@ -207,7 +207,8 @@ struct Workspace {
   DBuf<double> ad_xb;             // [2][N][6] pose cotangents (tangent space), double-buffered
   DBuf<float> ad_w;               // [2][P] depth cotangents that pass the clamp, double-buffered
   DBuf<float> ad_gd;              // [E] per-edge depth cotangents, patch-major
-  DBuf<unsigned char> prox;       // ba_proximity_edges scratch (centres, selections, masks, pixels)
+  DBuf<unsigned char> prox;       // ba_proximity_edges scratch (counters, CTA flags, centres, transforms)
+  long long prox_blocks = 0, prox_frames = 0;  // what its layout holds
   DBuf<float> ad_lamd;            // [P] depth part of the adjoint solve
   DBuf<double> ad_v;              // [n_pad] pose part of the adjoint right-hand side
   DBuf<float> ad_gt, ad_gw;       // [E][2] scratch when the caller passes no output

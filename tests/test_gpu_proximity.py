@@ -169,6 +169,9 @@ def test_invalid_arguments(kw):
     out = None
     if M < 1 or M > 1024:
         out = {k: torch.zeros(8, dtype=torch.int32, device="cuda") for k in ("ii", "jj", "kk")}
+        if M > 1024:  # patches enough for the size, so the library itself refuses it
+            P, T = P[:2], torch.zeros((2 * M, 3, 3, 3), dtype=torch.float32, device="cuda")
+            args["b1"] = 2
     with pytest.raises(capi.BAError) as e:
         DPVBA().proximity_edges(P, T, intr, M, out=out, **args)
     assert e.value.status == capi.BA_ERR_INVALID_ARG
