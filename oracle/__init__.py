@@ -24,6 +24,11 @@ of arxiv 2408.01654 it follows:
                    from that frame's patches to the query frame, kept where
                    the Eq. 2 reprojection lies in front of the camera and
                    inside the image.
+* ``patch_correlation`` Eq. 4 (Sec. 3.1 "Patch correlation"): for every edge
+                   and patch pixel, dot products of the patch's correlation
+                   features with the target frame's feature map bilinearly
+                   sampled on a 7x7 grid of integer offsets around the
+                   reprojected pixel (zero outside the map).
 * ``grad_fwd``     exact derivatives of a linear functional of the final state
                    with respect to single targets/weights (dual numbers through
                    the unrolled iterations).
@@ -226,3 +231,25 @@ def proximity_edges(poses, patches, intrinsics, M, b0, b1, gap=30, radius=2.0, z
     m = min(n.value, cap)
     return {"match": match, "dist": dist, "margin": margin, "ii": ii[:m], "jj": jj[:m], "kk": kk[:m],
             "coords": coords[:m], "n": n.value}
+
+
+def patch_correlation(fmap, gmap, kk, jj, coords, radius=3, bound=False):
+    """Eq. 4 correlation volume: fmap [Nf,H,W,D] and gmap [P,p,p,D] float32
+    (channels last), kk/jj [E] (patch, target frame), coords [E,p,p,2] float32
+    (x, y) in feature-map pixels.  Returns C [E,p,p,2R+1,2R+1] float64 (row
+    offset, then column offset), and with ``bound`` also the same sums of
+    |g||f| (the scale of any summation order's rounding error)."""
+    fmap = np.ascontiguousarray(fmap, dtype=np.float32)
+    gmap = np.ascontiguousarray(gmap, dtype=np.float32)
+    coords = np.ascontiguousarray(coords, dtype=np.float32)
+    kk, jj = _i(kk), _i(jj)
+    Nf, H, W, D = fmap.shape
+    P, p = gmap.shape[0], gmap.shape[1]
+    E = len(kk)
+    G = 2 * radius + 1
+    out = np.empty((E, p, p, G, G))
+    bnd = np.empty((E, p, p, G, G)) if bound else None
+    _check(lib().oracle_patch_correlation(
+        Nf, H, W, D, P, p, E, _p(fmap), _p(gmap), _p(kk), _p(jj), _p(coords), radius, _p(out),
+        _p(bnd) if bound else None))
+    return (out, bnd) if bound else out

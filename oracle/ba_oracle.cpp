@@ -660,4 +660,62 @@ int oracle_proximity_edges(int N, int M, const double* poses, const double* patc
   return 0;
 }
 
+// Patch correlation (Sec. 3.1 "Patch correlation", Eq. 4):
+//   C(e, v, u, a, b) = < g_kk[e](v, u), f_jj[e](P'_e(v, u) + Delta_ab) >
+// for every edge e, patch pixel (row v, column u) of the p x p patch, and the
+// (2R+1) x (2R+1) integer offsets Delta_ab = (b - R, a - R) (a the row offset,
+// b the column offset).  g: the patch's correlation features [P, p, p, D];
+// f: the target frame's dense feature map [Nf, H, W, D] (channels last);
+// P': the reprojected pixel [E, p, p, 2] as (x, y) in feature-map pixels,
+// integer coordinates at pixel centres.  f(x, y) is bilinear sampling from the
+// four pixels around (x, y) with weights (1-ax)(1-ay), ax(1-ay), (1-ax)ay, ax ay
+// (x0 = floor x, ax = x - x0, likewise y); pixels outside the map are zero.
+// out [E, p, p, 2R+1, 2R+1]; bound (same shape, may be null) is the same sum
+// with |g| and |f| (the scale of the rounding error of any summation order).
+int oracle_patch_correlation(int Nf, int H, int W, int D, int P, int p, int E, const float* fmap,
+                             const float* gmap, const int* kk, const int* jj, const float* coords, int R,
+                             double* out, double* bound) {
+  for (int e = 0; e < E; ++e)
+    if (kk[e] < 0 || kk[e] >= P || jj[e] < 0 || jj[e] >= Nf) return 1;
+  const int G = 2 * R + 1;
+  auto tap = [&](int j, int y, int x) -> const float* {
+    if (x < 0 || x >= W || y < 0 || y >= H) return nullptr;
+    return fmap + (((size_t)j * H + y) * W + x) * D;
+  };
+  for (int e = 0; e < E; ++e) {
+    const int j = jj[e];
+    for (int v = 0; v < p; ++v)
+      for (int u = 0; u < p; ++u) {
+        const float* g = gmap + (((size_t)kk[e] * p + v) * p + u) * D;
+        const double x = coords[(((size_t)e * p + v) * p + u) * 2];
+        const double y = coords[(((size_t)e * p + v) * p + u) * 2 + 1];
+        for (int a = 0; a < G; ++a)
+          for (int b = 0; b < G; ++b) {
+            const double sx = x + (b - R), sy = y + (a - R);
+            const double fx0 = std::floor(sx), fy0 = std::floor(sy);
+            const double ax = sx - fx0, ay = sy - fy0;
+            const int x0 = (int)fx0, y0 = (int)fy0;
+            const double wts[4] = {(1 - ax) * (1 - ay), ax * (1 - ay), (1 - ax) * ay, ax * ay};
+            const int xs[4] = {x0, x0 + 1, x0, x0 + 1}, ys[4] = {y0, y0, y0 + 1, y0 + 1};
+            double c = 0.0, cb = 0.0;
+            for (int q = 0; q < 4; ++q) {
+              const float* f = tap(j, ys[q], xs[q]);
+              if (!f) continue;
+              double dot = 0.0, adot = 0.0;
+              for (int d = 0; d < D; ++d) {
+                dot += (double)g[d] * (double)f[d];
+                adot += std::fabs((double)g[d] * (double)f[d]);
+              }
+              c += wts[q] * dot;
+              cb += wts[q] * adot;
+            }
+            const size_t o = ((((size_t)e * p + v) * p + u) * G + a) * G + b;
+            out[o] = c;
+            if (bound) bound[o] = cb;
+          }
+      }
+  }
+  return 0;
+}
+
 }  // extern "C"
