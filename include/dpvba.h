@@ -253,7 +253,8 @@ enum {
   BA_KERNEL_ADJOINT = 6,    /* adjoint-only kernels of ba_backward               */
   BA_KERNEL_FACTOR = 7,     /* the persistent factorisation of systems > 256 unknowns */
   BA_KERNEL_PROXIMITY = 8,  /* ba_proximity_edges                                */
-  BA_KERNEL_CLASSES = 9
+  BA_KERNEL_CORRELATION = 9,/* ba_patch_correlation                              */
+  BA_KERNEL_CLASSES = 10
 };
 
 /* on != 0: from now on record a CUDA event pair around every launch of each
@@ -347,6 +348,36 @@ DPVBA_API ba_status_t ba_proximity_edges(ba_handle_t h, int N, int M, const doub
                                          const float* intrinsics, int b0, int b1, int gap, double radius,
                                          double width, double height, int* ii, int* jj, int* kk, float* coords,
                                          long long cap, int* match, int* count, long long* n_host);
+
+/* ---- patch correlation --------------------------------------------------- */
+
+/* The correlation volume of Eq. 4 (Sec. 3.1 "Patch correlation"): for every
+ * edge e and pixel (v, u) of its p x p patch,
+ *   out[e][v][u][a][b] = < gmap[kk[e]][v][u][:],
+ *                          f_jj[e](coords[e][v][u] + (b - R, a - R)) >,
+ * a, b in 0..2R, where f_j(x, y) samples fmap[j] bilinearly from the four
+ * pixels around (x, y) (x0 = floor x, weight x - x0; likewise y; integer
+ * coordinates are pixel centres; pixels outside the map count as zero).
+ *   fmap   : device float32 [Nf, H, W, D], channels last (the dense
+ *            correlation feature maps of the target frames).
+ *   gmap   : device float32 [P, p, p, D] (each patch's correlation features).
+ *   kk, jj : device int32 [E] (source patch, target frame of each edge).
+ *   coords : device float32 [E, p, p, 2], (x, y) in feature-map pixels (the
+ *            reprojected patch pixels P', Eq. 2, at the maps' resolution).
+ *   out    : device float32 [E, p, p, 2R+1, 2R+1] (row offset a, column b).
+ * Limits: 1 <= p <= 3, 0 <= R <= 4, D a multiple of 32, E >= 0, fmap and
+ * gmap 16-byte aligned (BA_ERR_INVALID_ARG otherwise); a (2R+2)^2 block of
+ * D-channel map pixels must fit the ~72 KB staging buffer (D <= 224 for
+ * R = 3), and Nf <= 51,199, else BA_ERR_UNSUPPORTED.  An edge with kk or jj
+ * out of range gets zeros and sets the handle's device status (ba_sync
+ * returns BA_ERR_INVALID_ARG; like any device-detected error it makes the
+ * next ba_step skip its work).  FP32 arithmetic; queued on the handle's
+ * stream; needs no bound graph.  The handle keeps a scratch of
+ * 4 (2 Nf + E + 2) bytes for ordering the edges by target frame, grown by a
+ * call that needs more (not while its stream is being captured). */
+DPVBA_API ba_status_t ba_patch_correlation(ba_handle_t h, int Nf, int H, int W, int D, int P, int p, int E,
+                                           const float* fmap, const float* gmap, const int* kk, const int* jj,
+                                           const float* coords, int radius, float* out);
 
 /* ---- allocation-free pose-system solve ---------------------------------- */
 

@@ -204,6 +204,32 @@ class DPVBA:
         res["n"] = m
         return res
 
+    # ---------------------------------------------------------- correlation
+    def patch_correlation(self, fmap, gmap, kk, jj, coords, radius: int = 3, out=None):
+        """Eq. 4 correlation volume (see ba_patch_correlation): fmap float32
+        [Nf,H,W,D] and gmap float32 [P,p,p,D] (channels last), kk/jj int32
+        [E], coords float32 [E,p,p,2] (x, y) in feature-map pixels.  Returns
+        (or fills) float32 [E,p,p,2R+1,2R+1]; queued on the handle's stream."""
+        for name, t, dt in (("fmap", fmap, torch.float32), ("gmap", gmap, torch.float32), ("kk", kk, torch.int32),
+                            ("jj", jj, torch.int32), ("coords", coords, torch.float32)):
+            if t.dtype != dt or not t.is_contiguous() or not t.is_cuda:
+                raise TypeError(f"{name}: need a contiguous CUDA {dt} tensor")
+        Nf, H, W, D = fmap.shape
+        P, p = gmap.shape[0], gmap.shape[1]
+        E = kk.shape[0]
+        if gmap.shape != (P, p, p, D) or jj.shape[0] != E or coords.shape != (E, p, p, 2):
+            raise ValueError("inconsistent shapes")
+        G = 2 * radius + 1
+        if out is None:
+            out = torch.empty((E, p, p, G, G), dtype=torch.float32, device=fmap.device)
+        elif out.dtype != torch.float32 or not out.is_contiguous() or out.shape != (E, p, p, G, G):
+            raise TypeError("out: need a contiguous float32 [E,p,p,2R+1,2R+1] tensor")
+        self._corr_keep = (fmap, gmap, kk, jj, coords, out)
+        capi.check(self._h, self._lib.ba_patch_correlation(
+            self._h, Nf, H, W, D, P, p, E, _ptr(fmap), _ptr(gmap), _ptr(kk), _ptr(jj), _ptr(coords), radius,
+            _ptr(out)))
+        return out
+
     # ------------------------------------------------------------ inspection
     def linearize(self, fixed: int):
         capi.check(self._h, self._lib.ba_linearize(self._h, fixed))

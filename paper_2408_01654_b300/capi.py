@@ -39,10 +39,10 @@ EXPORTED = [
     "ba_step", "ba_sync",
     "ba_last_error", "ba_status_string", "ba_linearize", "ba_debug_export", "ba_debug_info", "ba_debug_keys",
     "ba_profile_enable", "ba_profile_read", "ba_set_record", "ba_backward", "ba_solve_pose_system_noalloc",
-    "ba_set_capture", "ba_autotune", "ba_autotune_clear", "ba_proximity_edges",
+    "ba_set_capture", "ba_autotune", "ba_autotune_clear", "ba_proximity_edges", "ba_patch_correlation",
 ]
 KERNEL_CLASSES = ("preprocess", "init", "assemble", "solve", "backsub", "retract", "adjoint", "factor",
-                  "proximity")
+                  "proximity", "correlation")
 
 
 class BAError(RuntimeError):

@@ -432,7 +432,7 @@ ba_status_t ba_destroy(ba_handle_t h) {
     release(ws->ad_xb); release(ws->ad_w); release(ws->ad_gd); release(ws->ad_lamd); release(ws->ad_v);
     release(ws->ad_gt); release(ws->ad_gw); release(ws->lg_sync); release(ws->lg_red); release(ws->lg_prob); release(ws->lg_rb); release(ws->fprob); release(ws->gprob);
     release(ws->fdx); release(ws->sysd); release(ws->syslist); release(ws->mii); release(ws->mjj); release(ws->mkk);
-    release(ws->offs); release(ws->pcopy); release(ws->prox);
+    release(ws->offs); release(ws->pcopy); release(ws->prox); release(ws->corr);
     delete ws;
   }
   graph_drop(h, h->step_graph);

@@ -209,6 +209,7 @@ struct Workspace {
   DBuf<float> ad_gd;              // [E] per-edge depth cotangents, patch-major
   DBuf<unsigned char> prox;       // ba_proximity_edges scratch (counters, CTA flags, centres, transforms)
   long long prox_blocks = 0, prox_frames = 0;  // what its layout holds
+  DBuf<int> corr;                 // ba_patch_correlation: frame histogram, cursors, edge order
   DBuf<float> ad_lamd;            // [P] depth part of the adjoint solve
   DBuf<double> ad_v;              // [n_pad] pose part of the adjoint right-hand side
   DBuf<float> ad_gt, ad_gw;       // [E][2] scratch when the caller passes no output

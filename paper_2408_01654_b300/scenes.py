@@ -278,3 +278,47 @@ def noise_free(scene: Scene) -> Scene:
 
 
 WORKLOADS = {"tiny": tiny, "odometry": odometry, "global": global_ba}
+
+
+def correlation_inputs(scene: Scene, D: int = 128, scale: int = 4, noise_px: float = 1.0, seed: int = 0) -> dict:
+    """Inputs of the patch correlation (Eq. 4) for a scene's edges, at the
+    feature maps' 1/``scale`` resolution (DPVO's maps are 1/4 of the frame,
+    Sec. 3.1 "Patch extraction"):
+
+    * ``fmap``   float32 [N, HEIGHT/scale, WIDTH/scale, D]: random N(0, 1/D)
+      feature maps (channels last), one per frame;
+    * ``gmap``   float32 [P, 3, 3, D]: random patch features, same scale;
+    * ``coords`` float32 [E, 3, 3, 2]: where each of the nine pixels of the
+      edge's patch (the 3x3 grid one feature-map pixel apart around the patch
+      centre) lands in the target frame (ground-truth camera model at the
+      ground-truth inverse depth, as ``proj_gt`` for the centre), divided by
+      ``scale``, plus N(0, (noise_px/scale)^2) per axis -- the estimate's
+      drift.
+
+    D = 128 float32 channels is the size that matches the paper's storage
+    figure for patch features (~0.6 GB per 1000 frames with 96 patches of
+    3x3 pixels, plus the context features)."""
+    rng = np.random.default_rng(seed)
+    N, P, E = scene.N, scene.P, scene.E
+    Hf, Wf = HEIGHT // scale, WIDTH // scale
+    fmap = rng.standard_normal((N, Hf, Wf, D), dtype=np.float32) / np.float32(math.sqrt(D))
+    gmap = rng.standard_normal((P, 3, 3, D), dtype=np.float32) / np.float32(math.sqrt(D))
+    Rq = Rotation.from_quat(scene.poses_gt[:, 3:]).as_matrix()  # world -> camera
+    t = scene.poses_gt[:, :3]
+    ii, jj, kk = scene.ii.astype(np.int64), scene.jj.astype(np.int64), scene.kk.astype(np.int64)
+    uc = scene.patches[kk, 0, 1, 1].astype(np.float64)
+    vc = scene.patches[kk, 1, 1, 1].astype(np.float64)
+    d = scene.depth_gt[kk]
+    off = np.array([-1.0, 0.0, 1.0]) * scale  # the patch's pixels are one feature-map pixel apart
+    u = np.broadcast_to(uc[:, None, None] + off[None, None, :], (E, 3, 3))
+    v = np.broadcast_to(vc[:, None, None] + off[None, :, None], (E, 3, 3))
+    pc = _camera_points(u, v, np.broadcast_to(d[:, None, None], (E, 3, 3)))       # [E,3,3,3] in frame i
+    pw = np.einsum("eji,evuj->evui", Rq[ii], pc - t[ii][:, None, None, :])           # R_i^T (p - t_i)
+    pcj = np.einsum("eij,evuj->evui", Rq[jj], pw) + t[jj][:, None, None, :]
+    z = pcj[..., 2]
+    with np.errstate(divide="ignore", invalid="ignore"):
+        x = FX * pcj[..., 0] / z + CX
+        y = FY * pcj[..., 1] / z + CY
+    coords = np.stack([x, y], -1) / scale + rng.normal(0.0, noise_px / scale, size=(E, 3, 3, 2))
+    coords = np.where(np.isfinite(coords), coords, -1.0e4).astype(np.float32)
+    return {"fmap": fmap, "gmap": gmap, "coords": coords}
