@@ -47,25 +47,27 @@ __device__ __forceinline__ void cr_cp16(float* dst, const float* src) {
 
 // stage the box [by0, by0 + bh) x [bx0, bx0 + bw) of frame j, and the feature
 // vectors of the pixels first .. first + npx - 1: one warp per box row (a row
-// of the box is contiguous in the map), lanes over the 16-byte chunks of a tap
+// of the box is contiguous in the map), lanes over the 16-byte chunks of a
+// tap; the addresses advance by a tap per step and the taps outside the map
+// (a prefix and a suffix of the row) are zero-filled
 __device__ void cr_stage(const CorrArgs& A, const float* __restrict__ fmap, const float* __restrict__ gmap, int j,
                          int k, int by0, int bx0, int bh, int bw, int first, int npx, float* s_f, float* s_g) {
   const int c4n = A.D / 4;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int tlo = max(0, -bx0), thi = min(bw, A.W - bx0);  // taps inside the map: [tlo, thi)
+  const unsigned s_base = (unsigned)__cvta_generic_to_shared(s_f);
   for (int r = w; r < bh; r += CR_THREADS / 32) {
     const int y = by0 + r;
     const bool row_in = y >= 0 && y < A.H;
-    const float* grow = fmap + ((size_t)j * A.H + (row_in ? y : 0)) * A.W * A.D;
-    float* srow = s_f + (size_t)r * bw * A.DS;
-    for (int t = 0; t < bw; ++t) {
-      const int x = bx0 + t;
-      const bool in = row_in && x >= 0 && x < A.W;
-      for (int c4 = lane; c4 < c4n; c4 += 32) {
-        float* dst = srow + (size_t)t * A.DS + 4 * c4;
-        if (in)
-          cr_cp16(dst, grow + (size_t)x * A.D + 4 * c4);
+    for (int c4 = lane; c4 < c4n; c4 += 32) {
+      unsigned sa = s_base + (unsigned)(((size_t)r * bw * A.DS + 4 * c4) * sizeof(float));
+      const unsigned sstep = (unsigned)(A.DS * sizeof(float));
+      const float* gp = fmap + (((size_t)j * A.H + (row_in ? y : 0)) * A.W + bx0) * A.D + 4 * c4;
+      for (int t = 0; t < bw; ++t, sa += sstep, gp += A.D) {
+        if (row_in && t >= tlo && t < thi)
+          asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gp) : "memory");
         else
-          *reinterpret_cast<float4*>(dst) = make_float4(0.f, 0.f, 0.f, 0.f);
+          asm volatile("st.shared.v4.f32 [%0], {%1, %1, %1, %1};" ::"r"(sa), "f"(0.f) : "memory");
       }
     }
   }
@@ -109,19 +111,22 @@ __device__ void cr_dots(const CorrArgs& A, int ntap, const float* s_f, const flo
   __syncthreads();
 }
 
-// outputs of the pixels first .. first + npx - 1 from the tap products
+// outputs of the pixels first .. first + npx - 1 from the tap products: a
+// thread owns one grid offset (a, b) and walks the pixels
 __device__ void cr_combine(const CorrArgs& A, int e, int by0, int bx0, int bw, int first, int npx, const int* x0,
                            const int* y0, const float* ax, const float* ay, const float* s_dot,
                            float* __restrict__ out) {
   const int G = 2 * A.R + 1, G2 = G * G;
-  for (int o = threadIdx.x; o < npx * G2; o += CR_THREADS) {
-    const int q = o / G2, ab = o - q * G2, a = ab / G, b = ab - a * G;
-    const int pq = first + q;
-    const int ty = y0[pq] - A.R + a - by0, tx = x0[pq] - A.R + b - bx0;
-    const float* d = s_dot + (size_t)q * A.cap + ty * bw + tx;
-    const float wx = ax[pq], wy = ay[pq];
-    const float c = (1.f - wy) * ((1.f - wx) * d[0] + wx * d[1]) + wy * ((1.f - wx) * d[bw] + wx * d[bw + 1]);
-    out[((size_t)e * A.p * A.p + pq) * G2 + ab] = c;
+  for (int ab = threadIdx.x; ab < G2; ab += CR_THREADS) {
+    const int a = ab / G, b = ab - a * G;
+    float* o = out + ((size_t)e * A.p * A.p + first) * G2 + ab;
+    for (int q = 0; q < npx; ++q, o += G2) {
+      const int pq = first + q;
+      const int ty = y0[pq] - A.R + a - by0, tx = x0[pq] - A.R + b - bx0;
+      const float* d = s_dot + (size_t)q * A.cap + ty * bw + tx;
+      const float wx = ax[pq], wy = ay[pq];
+      *o = (1.f - wy) * ((1.f - wx) * d[0] + wx * d[1]) + wy * ((1.f - wx) * d[bw] + wx * d[bw + 1]);
+    }
   }
 }
 
