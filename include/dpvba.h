@@ -146,7 +146,9 @@ DPVBA_API ba_status_t ba_set_graph_batched(ba_handle_t h, int B, const long long
  * linearise every edge, reduce into the block system, eliminate the inverse
  * depths, factor and solve the pose system, back-substitute the depths,
  * retract the poses.  Poses [0, fixed_poses) are held constant (gauge).
- * 0 <= fixed_poses <= N, iters >= 0. */
+ * 0 <= fixed_poses <= N, iters >= 0.  fixed_poses = N holds every pose: the
+ * iterations then solve for the inverse depths alone (structure-only BA,
+ * Sec. 3.3, e.g. to triangulate patches for known cameras). */
 DPVBA_API ba_status_t ba_step(ba_handle_t h, int iters, int fixed_poses);
 
 /* ---- batched execution patterns ------------------------------------------

@@ -810,7 +810,9 @@ ba_status_t ba_step(ba_handle_t h, int iters, int fixed_poses) {
   if (iters < 0) return dpv_fail(h, BA_ERR_INVALID_ARG, "iters < 0");
   if ((s = ensure_system(h, fixed_poses))) return s;
   h->last_iters = iters;
-  const int run = (iters > 0 && h->n > 0) ? iters : 0;
+  // fixed_poses = N leaves no pose unknowns: the iterations then update the
+  // inverse depths only (structure-only bundle adjustment)
+  const int run = iters > 0 ? iters : 0;
   if (h->record) {
     // this call becomes the tape of ba_backward
     h->tape_valid = 0;
