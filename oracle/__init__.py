@@ -29,6 +29,12 @@ of arxiv 2408.01654 it follows:
                    features with the target frame's feature map bilinearly
                    sampled on a 7x7 grid of integer offsets around the
                    reprojected pixel (zero outside the map).
+* ``pgo_lm``       Sim(3) pose-graph optimisation (Sec. 3.3 "Optimization",
+                   Eqs. 5-7): smoothness factors log(dS^-1 Sa^-1 Sb) and loop
+                   factors log(dS Sa^-1 Sb), Levenberg-Marquardt with
+                   central-difference Jacobians and a dense Cholesky solve,
+                   the first similarity held; with ``sim3_exp``/``sim3_log``
+                   and ``pgo_residuals``.
 * ``grad_fwd``     exact derivatives of a linear functional of the final state
                    with respect to single targets/weights (dual numbers through
                    the unrolled iterations).
@@ -253,3 +259,40 @@ def patch_correlation(fmap, gmap, kk, jj, coords, radius=3, bound=False):
         Nf, H, W, D, P, p, E, _p(fmap), _p(gmap), _p(kk), _p(jj), _p(coords), radius, _p(out),
         _p(bnd) if bound else None))
     return (out, bnd) if bound else out
+
+
+def sim3_exp(xi):
+    """Exp of a Sim(3) tangent vector (rho, phi, sigma) [7] -> (t, q xyzw, s) [8]."""
+    out = np.empty(8)
+    lib().oracle_sim3_exp(_p(_d(xi)), _p(out))
+    return out
+
+
+def sim3_log(S):
+    """Log of a similarity (t, q xyzw, s) [8] -> (rho, phi, sigma) [7]."""
+    out = np.empty(7)
+    lib().oracle_sim3_log(_p(_d(S)), _p(out))
+    return out
+
+
+def pgo_residuals(S, dS, fa, fb, loop):
+    """[F,7] factor residuals (Eq. 5 for loop = 0, Eq. 6 for loop = 1) at the
+    similarities S [N,8], measurements dS [F,8], factor endpoints fa/fb [F]."""
+    S, dS = _d(S), _d(dS)
+    fa, fb, loop = _i(fa), _i(fb), _i(loop)
+    r = np.empty((len(fa), 7))
+    lib().oracle_pgo_residuals(len(S), len(fa), _p(S), _p(dS), _p(fa), _p(fb), _p(loop), _p(r))
+    return r
+
+
+def pgo_lm(S, dS, fa, fb, loop, iters=20, lambda0=1e-4, h=1e-6):
+    """Levenberg-Marquardt on Eq. 7 from the similarities S [N,8] (S[0] held).
+    Returns dict(S [N,8], cost [iters+1], accepted [iters])."""
+    S = _d(S).copy()
+    dS = _d(dS)
+    fa, fb, loop = _i(fa), _i(fb), _i(loop)
+    cost = np.empty(iters + 1)
+    acc = np.empty(iters, np.int32)
+    _check(lib().oracle_pgo_lm(len(S), len(fa), _p(S), _p(dS), _p(fa), _p(fb), _p(loop), iters,
+                               ctypes.c_double(lambda0), ctypes.c_double(h), _p(cost), _p(acc)))
+    return dict(S=S, cost=cost, accepted=acc.astype(bool))

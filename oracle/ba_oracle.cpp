@@ -719,3 +719,269 @@ int oracle_patch_correlation(int Nf, int H, int W, int D, int P, int p, int E, c
 }
 
 }  // extern "C"
+
+namespace {
+// ---------------------------------------------------------------------------
+// Sim(3) pose-graph optimisation (Sec. 3.3 "Optimization", Eqs. 5-7)
+// ---------------------------------------------------------------------------
+// A similarity S = (q, t, s) maps x to s R(q) x + t (camera to world, as the
+// paper's G_i with a scale), stored as 8 doubles (tx, ty, tz, qx, qy, qz, qw, s).
+// Its tangent vector xi = (rho, phi, sigma) is the matrix [[phi]x + sigma I, rho;
+// 0, 0]; Exp gives R = exp([phi]x), s = e^sigma, t = W rho with
+//   W = int_0^1 exp(tau ([phi]x + sigma I)) dtau = a I + b [phi]x + c [phi]x^2,
+//   a = int e^{sigma tau}, b = int e^{sigma tau} sin(theta tau) / theta,
+//   c = int e^{sigma tau} (1 - cos(theta tau)) / theta^2  (tau over [0, 1]).
+struct Sim3 {
+  double q[4], t[3], s;
+};
+
+Sim3 sim3_load(const double* v) {
+  Sim3 S;
+  for (int k = 0; k < 3; ++k) S.t[k] = v[k];
+  for (int k = 0; k < 4; ++k) S.q[k] = v[3 + k];
+  S.s = v[7];
+  return S;
+}
+
+void sim3_store(const Sim3& S, double* v) {
+  for (int k = 0; k < 3; ++k) v[k] = S.t[k];
+  for (int k = 0; k < 4; ++k) v[3 + k] = S.q[k];
+  v[7] = S.s;
+}
+
+void rot_apply(const double q[4], const double x[3], double y[3]) {
+  double R[9];
+  quat_to_rot(q, R);
+  for (int r = 0; r < 3; ++r) y[r] = R[3 * r] * x[0] + R[3 * r + 1] * x[1] + R[3 * r + 2] * x[2];
+}
+
+Sim3 sim3_mul(const Sim3& A, const Sim3& B) {  // A B: x -> A(B(x))
+  Sim3 C;
+  quat_mul(A.q, B.q, C.q);
+  double Rt[3];
+  rot_apply(A.q, B.t, Rt);
+  for (int k = 0; k < 3; ++k) C.t[k] = A.s * Rt[k] + A.t[k];
+  C.s = A.s * B.s;
+  return C;
+}
+
+Sim3 sim3_inv(const Sim3& A) {
+  Sim3 B;
+  B.q[0] = -A.q[0];
+  B.q[1] = -A.q[1];
+  B.q[2] = -A.q[2];
+  B.q[3] = A.q[3];
+  double Rt[3];
+  rot_apply(B.q, A.t, Rt);
+  for (int k = 0; k < 3; ++k) B.t[k] = -Rt[k] / A.s;
+  B.s = 1.0 / A.s;
+  return B;
+}
+
+// m_k(sigma) = int_0^1 tau^k e^{sigma tau} dtau
+double moment(int k, double sg) {
+  if (std::fabs(sg) < 2.0) {
+    double term = 1.0, sum = 0.0;  // sum_j sigma^j / (j! (k + j + 1))
+    for (int j = 0; j < 40; ++j) {
+      sum += term / (k + j + 1);
+      term *= sg / (j + 1);
+    }
+    return sum;
+  }
+  double m = std::expm1(sg) / sg;
+  for (int i = 1; i <= k; ++i) m = (std::exp(sg) - i * m) / sg;
+  return m;
+}
+
+// coefficients of W = a I + b [phi]x + c [phi]x^2
+void w_coeffs(double th, double sg, double& a, double& b, double& c) {
+  a = moment(0, sg);
+  if (th < 1e-4) {
+    b = moment(1, sg) - th * th / 6.0 * moment(3, sg);
+    c = moment(2, sg) / 2.0 - th * th / 24.0 * moment(4, sg);
+    return;
+  }
+  const double es = std::exp(sg), den = sg * sg + th * th;
+  b = (es * (sg * std::sin(th) - th * std::cos(th)) + th) / (th * den);
+  c = (a - (es * (sg * std::cos(th) + th * std::sin(th)) - sg) / den) / (th * th);
+}
+
+void w_apply(const double phi[3], double a, double b, double c, const double x[3], double y[3]) {
+  const double px[3] = {phi[1] * x[2] - phi[2] * x[1], phi[2] * x[0] - phi[0] * x[2], phi[0] * x[1] - phi[1] * x[0]};
+  const double ppx[3] = {phi[1] * px[2] - phi[2] * px[1], phi[2] * px[0] - phi[0] * px[2],
+                         phi[0] * px[1] - phi[1] * px[0]};
+  for (int k = 0; k < 3; ++k) y[k] = a * x[k] + b * px[k] + c * ppx[k];
+}
+
+Sim3 sim3_exp(const double xi[7]) {
+  const double* rho = xi;
+  const double* phi = xi + 3;
+  const double sg = xi[6];
+  const double th = std::sqrt(phi[0] * phi[0] + phi[1] * phi[1] + phi[2] * phi[2]);
+  Sim3 S;
+  const double h = th < 1e-8 ? 0.5 - th * th / 48.0 : std::sin(0.5 * th) / th;  // sin(th/2)/th
+  for (int k = 0; k < 3; ++k) S.q[k] = h * phi[k];
+  S.q[3] = std::cos(0.5 * th);
+  double a, b, c;
+  w_coeffs(th, sg, a, b, c);
+  w_apply(phi, a, b, c, rho, S.t);
+  S.s = std::exp(sg);
+  return S;
+}
+
+void sim3_log(const Sim3& S, double xi[7]) {
+  double q[4] = {S.q[0], S.q[1], S.q[2], S.q[3]};
+  if (q[3] < 0.0)
+    for (double& v : q) v = -v;
+  const double vn = std::sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2]);
+  const double th = 2.0 * std::atan2(vn, q[3]);
+  const double f = vn > 1e-12 ? th / vn : 2.0 / q[3];
+  double* phi = xi + 3;
+  for (int k = 0; k < 3; ++k) phi[k] = f * q[k];
+  const double sg = std::log(S.s);
+  xi[6] = sg;
+  double a, b, c;
+  w_coeffs(th, sg, a, b, c);
+  // W as a 3x3 matrix, then rho = W^-1 t (adjugate)
+  double Wm[9];
+  for (int col = 0; col < 3; ++col) {
+    double e[3] = {0.0, 0.0, 0.0}, y[3];
+    e[col] = 1.0;
+    w_apply(phi, a, b, c, e, y);
+    for (int r = 0; r < 3; ++r) Wm[3 * r + col] = y[r];
+  }
+  const double A00 = Wm[4] * Wm[8] - Wm[5] * Wm[7], A01 = Wm[2] * Wm[7] - Wm[1] * Wm[8],
+               A02 = Wm[1] * Wm[5] - Wm[2] * Wm[4];
+  const double A10 = Wm[5] * Wm[6] - Wm[3] * Wm[8], A11 = Wm[0] * Wm[8] - Wm[2] * Wm[6],
+               A12 = Wm[2] * Wm[3] - Wm[0] * Wm[5];
+  const double A20 = Wm[3] * Wm[7] - Wm[4] * Wm[6], A21 = Wm[1] * Wm[6] - Wm[0] * Wm[7],
+               A22 = Wm[0] * Wm[4] - Wm[1] * Wm[3];
+  const double det = Wm[0] * A00 + Wm[1] * A10 + Wm[2] * A20;
+  const double* t = S.t;
+  xi[0] = (A00 * t[0] + A01 * t[1] + A02 * t[2]) / det;
+  xi[1] = (A10 * t[0] + A11 * t[1] + A12 * t[2]) / det;
+  xi[2] = (A20 * t[0] + A21 * t[1] + A22 * t[2]) / det;
+}
+
+// Eq. 5 (smoothness, loop = 0): log(dS^-1 Sa^-1 Sb); Eq. 6 (loop = 1): log(dS Sa^-1 Sb)
+void pgo_residual(const Sim3& dS, const Sim3& Sa, const Sim3& Sb, int loop, double r[7]) {
+  const Sim3 rel = sim3_mul(sim3_inv(Sa), Sb);
+  sim3_log(sim3_mul(loop ? dS : sim3_inv(dS), rel), r);
+}
+
+struct PgoProblem {
+  int N, F;
+  std::vector<Sim3> S, dS;
+  std::vector<int> fa, fb, loop;
+};
+
+double pgo_cost(const PgoProblem& P, const std::vector<Sim3>& S) {
+  double c = 0.0, r[7];
+  for (int f = 0; f < P.F; ++f) {
+    pgo_residual(P.dS[f], S[P.fa[f]], S[P.fb[f]], P.loop[f], r);
+    for (double v : r) c += v * v;
+  }
+  return c;
+}
+
+}  // namespace
+
+extern "C" {
+
+void oracle_sim3_exp(const double* xi, double* out) { sim3_store(sim3_exp(xi), out); }
+
+void oracle_sim3_log(const double* S, double* xi) { sim3_log(sim3_load(S), xi); }
+
+// residuals [F,7] of the factors at the given similarities
+void oracle_pgo_residuals(int N, int F, const double* S, const double* dS, const int* fa, const int* fb,
+                          const int* loop, double* r) {
+  for (int f = 0; f < F; ++f)
+    pgo_residual(sim3_load(dS + 8 * (size_t)f), sim3_load(S + 8 * (size_t)fa[f]), sim3_load(S + 8 * (size_t)fb[f]),
+                 loop[f], r + 7 * (size_t)f);
+}
+
+// Levenberg-Marquardt on Eq. 7 (Sec. 3.3): S_0 held (gauge), S_i <- S_i Exp(d_i)
+// for i >= 1; Jacobians by central differences (step h) of each factor's
+// residual in the 7 coordinates of each of its two similarities; normal
+// equations H = J^T J, g = J^T r; step from (H + lambda diag(H)) d = -g;
+// accepted (lambda /= 10) if it lowers the cost, else rejected (lambda *= 10).
+// S [N,8] in place; cost [iters+1] (the cost before each iteration and at the
+// end), accepted [iters].  Returns 4 if a system is not positive definite.
+int oracle_pgo_lm(int N, int F, double* S, const double* dS, const int* fa, const int* fb, const int* loop,
+                  int iters, double lambda0, double h, double* cost, int* accepted) {
+  for (int f = 0; f < F; ++f)
+    if (fa[f] < 0 || fa[f] >= N || fb[f] < 0 || fb[f] >= N) return 1;
+  PgoProblem P;
+  P.N = N;
+  P.F = F;
+  for (int i = 0; i < N; ++i) P.S.push_back(sim3_load(S + 8 * (size_t)i));
+  for (int f = 0; f < F; ++f) {
+    P.dS.push_back(sim3_load(dS + 8 * (size_t)f));
+    P.fa.push_back(fa[f]);
+    P.fb.push_back(fb[f]);
+    P.loop.push_back(loop[f]);
+  }
+  const int n = 7 * (N - 1);
+  double lambda = lambda0;
+  double cur = pgo_cost(P, P.S);
+  for (int it = 0; it < iters; ++it) {
+    cost[it] = cur;
+    std::vector<double> H((size_t)n * n, 0.0), g(n, 0.0);
+    for (int f = 0; f < F; ++f) {
+      const int ab[2] = {P.fa[f], P.fb[f]};
+      double r[7], J[2][7][7];  // J[side][residual row][coordinate]
+      pgo_residual(P.dS[f], P.S[ab[0]], P.S[ab[1]], P.loop[f], r);
+      for (int side = 0; side < 2; ++side)
+        for (int m = 0; m < 7; ++m) {
+          double d[7] = {0, 0, 0, 0, 0, 0, 0}, rp[7], rm[7];
+          d[m] = h;
+          Sim3 Sp = sim3_mul(P.S[ab[side]], sim3_exp(d));
+          d[m] = -h;
+          Sim3 Sm = sim3_mul(P.S[ab[side]], sim3_exp(d));
+          pgo_residual(P.dS[f], side == 0 ? Sp : P.S[ab[0]], side == 1 ? Sp : P.S[ab[1]], P.loop[f], rp);
+          pgo_residual(P.dS[f], side == 0 ? Sm : P.S[ab[0]], side == 1 ? Sm : P.S[ab[1]], P.loop[f], rm);
+          for (int row = 0; row < 7; ++row) J[side][row][m] = (rp[row] - rm[row]) / (2.0 * h);
+        }
+      for (int sa = 0; sa < 2; ++sa) {
+        if (ab[sa] == 0) continue;
+        const int oa = 7 * (ab[sa] - 1);
+        for (int m = 0; m < 7; ++m) {
+          double gm = 0.0;
+          for (int row = 0; row < 7; ++row) gm += J[sa][row][m] * r[row];
+          g[oa + m] += gm;
+        }
+        for (int sb = 0; sb < 2; ++sb) {
+          if (ab[sb] == 0) continue;
+          const int ob = 7 * (ab[sb] - 1);
+          for (int m = 0; m < 7; ++m)
+            for (int k = 0; k < 7; ++k) {
+              double hv = 0.0;
+              for (int row = 0; row < 7; ++row) hv += J[sa][row][m] * J[sb][row][k];
+              H[(size_t)(oa + m) * n + ob + k] += hv;
+            }
+        }
+      }
+    }
+    for (int i = 0; i < n; ++i) H[(size_t)i * n + i] *= 1.0 + lambda;
+    std::vector<double> rhs(n), d;
+    for (int i = 0; i < n; ++i) rhs[i] = -g[i];
+    if (cholesky_solve(H, n, rhs, d)) return 4;
+    std::vector<Sim3> cand = P.S;
+    for (int i = 1; i < N; ++i) cand[i] = sim3_mul(P.S[i], sim3_exp(&d[7 * (i - 1)]));
+    const double c = pgo_cost(P, cand);
+    if (c < cur) {
+      P.S = cand;
+      cur = c;
+      lambda /= 10.0;
+      accepted[it] = 1;
+    } else {
+      lambda *= 10.0;
+      accepted[it] = 0;
+    }
+  }
+  cost[iters] = cur;
+  for (int i = 0; i < N; ++i) sim3_store(P.S[i], S + 8 * (size_t)i);
+  return 0;
+}
+
+}  // extern "C"
