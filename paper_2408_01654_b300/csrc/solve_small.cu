@@ -92,26 +92,22 @@ __global__ void __launch_bounds__(small_threads(NQ)) k_solve_small(
     dxf += sd.voff;
   }
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  // equilibration scale from the diagonal first (one load per thread)
   if (tid == 0) bad = 0;
-  for (int i = tid; i < NP; i += NT) {
-    const float d = dpv_d2f_bits(S[(size_t)i * NP + i]);
-    sc[i] = (i < n && d > 0.f) ? rsqrtf(d) : 1.f;
-  }
-  __syncthreads();
   {
     // S: FP64 row-major NP x NP (lower triangle valid), read as pairs; warp w
     // takes rows w, w + NWARP, ..., lane the pairs lane, lane + 32, ... of a
-    // row, with up to eight loads in flight per thread; each value is rounded
-    // to FP32 with integer operations and equilibrated, s_i S_ij s_j, into the
-    // packed factor storage and the square copy
+    // row.  The loads of the diagonal (for the equilibration scale) and of
+    // every row the thread handles are all issued before the first barrier
+    // (one memory round trip, up to 16 pairs in flight per thread); then each
+    // value is rounded to FP32 with integer operations and equilibrated,
+    // s_i S_ij s_j, into the packed factor storage and the square copy.
     constexpr int NPH = NP / 2;
     constexpr int RW = NP / NWARP;        // rows per warp
     constexpr int PL = (NPH + 31) / 32;   // pairs per lane in a row
-    constexpr int RB = PL >= 8 ? 1 : 8 / PL;  // rows per batch
+    constexpr int RB = RW * PL <= 16 ? RW : (PL >= 8 ? 1 : 8 / PL);  // rows per batch
     const double2* S2 = reinterpret_cast<const double2*>(S);
-    for (int rb = 0; rb < RW; rb += RB) {
-      double2 v[RB][PL];
+    double2 v[RB][PL];
+    auto load_batch = [&](int rb) {
 #pragma unroll
       for (int r = 0; r < RB; ++r)
 #pragma unroll
@@ -119,6 +115,15 @@ __global__ void __launch_bounds__(small_threads(NQ)) k_solve_small(
           const int i = wid + NWARP * (rb + r), p = lane + 32 * t;
           v[r][t] = (rb + r < RW && p < NPH && 2 * p <= i) ? S2[(size_t)i * NPH + p] : make_double2(0.0, 0.0);
         }
+    };
+    load_batch(0);
+    for (int i = tid; i < NP; i += NT) {
+      const float d = dpv_d2f_bits(S[(size_t)i * NP + i]);
+      sc[i] = (i < n && d > 0.f) ? rsqrtf(d) : 1.f;
+    }
+    __syncthreads();
+    for (int rb = 0; rb < RW; rb += RB) {
+      if (rb > 0) load_batch(rb);
 #pragma unroll
       for (int r = 0; r < RB; ++r)
 #pragma unroll
