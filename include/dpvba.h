@@ -256,7 +256,8 @@ enum {
   BA_KERNEL_FACTOR = 7,     /* the persistent factorisation of systems > 256 unknowns */
   BA_KERNEL_PROXIMITY = 8,  /* ba_proximity_edges                                */
   BA_KERNEL_CORRELATION = 9,/* ba_patch_correlation                              */
-  BA_KERNEL_CLASSES = 10
+  BA_KERNEL_PGO = 10,       /* ba_pgo_lm, its pose-system solves included        */
+  BA_KERNEL_CLASSES = 11
 };
 
 /* on != 0: from now on record a CUDA event pair around every launch of each
@@ -380,6 +381,43 @@ DPVBA_API ba_status_t ba_proximity_edges(ba_handle_t h, int N, int M, const doub
 DPVBA_API ba_status_t ba_patch_correlation(ba_handle_t h, int Nf, int H, int W, int D, int P, int p, int E,
                                            const float* fmap, const float* gmap, const int* kk, const int* jj,
                                            const float* coords, int radius, float* out);
+
+/* ---- Sim(3) pose-graph optimisation -------------------------------------- */
+
+#define BA_PGO_MAX_FRAMES 4096
+
+/* Levenberg-Marquardt on the Sim(3) pose graph of Sec. 3.3 "Optimization"
+ * (Eqs. 5-7): minimise sum_f |r_f|^2 over the similarities S_1..S_{N-1}
+ * (S_0 held, fixing the gauge), with
+ *   r_f = log(dS_f^-1 S_a^-1 S_b)   for a smoothness factor (loop[f] = 0, Eq. 5),
+ *   r_f = log(dS_f    S_a^-1 S_b)   for a loop factor       (loop[f] = 1, Eq. 6),
+ * a = fa[f], b = fb[f].  A similarity is 8 doubles (tx, ty, tz, qx, qy, qz, qw,
+ * s) mapping x to s R(q) x + t; log/Exp use the tangent (rho, phi, sigma) with
+ * t = W rho, W = int_0^1 exp(tau([phi]x + sigma I)) dtau.  Each iteration
+ * linearises every factor by central differences of step fd_step in the
+ * coordinates of S <- S Exp(d) of both endpoints, solves
+ * (H + lambda diag(H)) d = -J^T r with the library's dense pose solver (the
+ * handle's precision option applies), and keeps S Exp(d) if it lowers the
+ * cost (lambda /= 10) or rejects it (lambda *= 10).
+ *   S        : device float64 [N,8], updated in place (S[0] never changes).
+ *   dS       : device float64 [F,8] measurements.
+ *   fa, fb   : device int32 [F] endpoints, 0 <= fa, fb < N, fa != fb.
+ *   loop     : device int32 [F], 0 (Eq. 5) or 1 (Eq. 6).
+ *   cost     : device float64 [iters+1]: the cost before each iteration and
+ *              after the last.
+ *   accepted : device int32 [iters] or null: 1 where the step was kept.
+ * Limits: 1 <= N <= BA_PGO_MAX_FRAMES, F >= 0, iters >= 0, lambda0 > 0,
+ * 0 < fd_step < 1e-2, else BA_ERR_INVALID_ARG at once.  A factor with an
+ * endpoint out of range, or fa == fb, sets the device status (ba_sync returns
+ * BA_ERR_INVALID_ARG); a damped system that is not positive definite (a
+ * similarity no factor touches) makes ba_sync return BA_ERR_NOT_SPD.  The
+ * work is queued on the handle's stream with no host round trip; the call
+ * borrows the handle's pose-system buffers (the next ba_step lays its own
+ * system out again) and keeps 8 (3 + 8N + F) bytes of scratch.  Needs no
+ * bound graph. */
+DPVBA_API ba_status_t ba_pgo_lm(ba_handle_t h, int N, int F, double* S, const double* dS, const int* fa,
+                                const int* fb, const int* loop, int iters, double lambda0, double fd_step,
+                                double* cost, int* accepted);
 
 /* ---- allocation-free pose-system solve ---------------------------------- */
 

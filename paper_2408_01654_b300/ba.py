@@ -230,6 +230,32 @@ class DPVBA:
             _ptr(out)))
         return out
 
+    # -------------------------------------------------- pose-graph optimisation
+    def pgo_lm(self, S, dS, fa, fb, loop, iters: int = 20, lambda0: float = 1e-4, fd_step: float = 1e-6,
+               cost=None, accepted=None):
+        """Sim(3) pose-graph Levenberg-Marquardt (see ba_pgo_lm): S float64
+        [N,8] (t, q xyzw, s), updated in place; dS float64 [F,8]; fa/fb/loop
+        int32 [F].  Returns (cost float64 [iters+1], accepted int32 [iters]),
+        queued on the handle's stream."""
+        for name, t, dt in (("S", S, torch.float64), ("dS", dS, torch.float64), ("fa", fa, torch.int32),
+                            ("fb", fb, torch.int32), ("loop", loop, torch.int32)):
+            if t.dtype != dt or not t.is_contiguous() or not t.is_cuda:
+                raise TypeError(f"{name}: need a contiguous CUDA {dt} tensor")
+        N, F = S.shape[0], fa.shape[0]
+        if S.shape != (N, 8) or dS.shape != (F, 8) or fb.shape[0] != F or loop.shape[0] != F:
+            raise ValueError("inconsistent shapes")
+        if cost is None:
+            cost = torch.empty(iters + 1, dtype=torch.float64, device=S.device)
+        if accepted is None:
+            accepted = torch.empty(max(iters, 1), dtype=torch.int32, device=S.device)
+        if cost.dtype != torch.float64 or cost.numel() < iters + 1 or accepted.dtype != torch.int32 \
+                or accepted.numel() < iters:
+            raise TypeError("cost: float64 [iters+1], accepted: int32 [iters]")
+        self._pgo_keep = (S, dS, fa, fb, loop, cost, accepted)
+        capi.check(self._h, self._lib.ba_pgo_lm(self._h, N, F, _ptr(S), _ptr(dS), _ptr(fa), _ptr(fb), _ptr(loop),
+                                                iters, lambda0, fd_step, _ptr(cost), _ptr(accepted)))
+        return cost, accepted[:iters]
+
     # ------------------------------------------------------------ inspection
     def linearize(self, fixed: int):
         capi.check(self._h, self._lib.ba_linearize(self._h, fixed))

@@ -39,10 +39,10 @@ EXPORTED = [
     "ba_step", "ba_sync",
     "ba_last_error", "ba_status_string", "ba_linearize", "ba_debug_export", "ba_debug_info", "ba_debug_keys",
     "ba_profile_enable", "ba_profile_read", "ba_set_record", "ba_backward", "ba_solve_pose_system_noalloc",
-    "ba_set_capture", "ba_autotune", "ba_autotune_clear", "ba_proximity_edges", "ba_patch_correlation",
+    "ba_set_capture", "ba_autotune", "ba_autotune_clear", "ba_proximity_edges", "ba_patch_correlation", "ba_pgo_lm",
 ]
 KERNEL_CLASSES = ("preprocess", "init", "assemble", "solve", "backsub", "retract", "adjoint", "factor",
-                  "proximity", "correlation")
+                  "proximity", "correlation", "pgo")
 
 
 class BAError(RuntimeError):
@@ -85,6 +85,7 @@ def lib():
         L.ba_set_record.argtypes = [H, i]
         L.ba_backward.argtypes = [H, P, P, P, P, P, P]
         L.ba_solve_pose_system_noalloc.argtypes = [i, P, P, P, i, P]
+        L.ba_pgo_lm.argtypes = [H, i, i, P, P, P, P, P, i, ctypes.c_double, ctypes.c_double, P, P]
         for name in EXPORTED:
             if name not in ("ba_last_error", "ba_status_string"):
                 getattr(L, name).restype = ctypes.c_int

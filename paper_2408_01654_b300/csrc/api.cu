@@ -354,6 +354,47 @@ ba_status_t ensure_system(ba_handle_t h, int fixed) {
 
 ba_status_t dpv_ensure_system(ba_handle_t h, int fixed) { return ensure_system(h, fixed); }
 
+// Lay out one dense system of n unknowns that is not a bundle-adjustment pose
+// system (the pose-graph optimisation's), in the same buffers and with the
+// same solver selection.  The next ba_step lays out its own system again.
+ba_status_t dpv_ensure_generic_system(ba_handle_t h, int n) {
+  Workspace* ws = h->ws;
+  h->fixed = -1;
+  h->sys.assign(1, SysDesc{});
+  for (auto& v : h->small_nq) v.clear();
+  h->large_sys.clear();
+  SysDesc& d = h->sys[0];
+  d.problem = 0;
+  d.n = n;
+  system_geometry(n, d.TS, d.T, d.n_pad);
+  d.soff = 0;
+  d.voff = 0;
+  const long long soff = (long long)d.T * (d.T + 1) / 2 * d.TS * d.TS;
+  long long large_scratch = 0;
+  if (n > 0 && n <= DPV_SMALL_N) {
+    h->small_nq[d.n_pad / 32].push_back(0);
+  } else if (n > 0) {
+    h->large_sys.push_back(0);
+    large_scratch = dpv_large_scratch_floats(d.n_pad);
+  }
+  h->n = n;
+  h->n_pad = d.n_pad;
+  h->nS = soff;
+  h->TS = d.TS;
+  h->T = d.T;
+  ba_status_t s;
+  if ((s = dpv_grow(h, ws->S, soff, "pose system")) || (s = dpv_grow(h, ws->y, d.n_pad, "rhs")) ||
+      (s = dpv_grow(h, ws->dx, d.n_pad, "step")) || (s = dpv_grow(h, ws->r64, d.n_pad, "residual")) ||
+      (s = dpv_grow(h, ws->tmpv, d.n_pad, "vector")) || (s = dpv_grow(h, ws->sysd, 1, "system table")) ||
+      (s = dpv_grow(h, ws->syslist, 1, "system lists")))
+    return s;
+  if (large_scratch > 0 && (s = dpv_grow(h, ws->L, large_scratch, "factor"))) return s;
+  const int zero = 0;
+  DPV_CUDA(h, cudaMemcpyAsync(ws->sysd.p, h->sys.data(), sizeof(SysDesc), cudaMemcpyHostToDevice, h->stream));
+  DPV_CUDA(h, cudaMemcpyAsync(ws->syslist.p, &zero, sizeof(int), cudaMemcpyHostToDevice, h->stream));
+  return dpv_large_reserve(h);
+}
+
 extern "C" {
 
 const char* ba_status_string(ba_status_t s) {
@@ -432,7 +473,7 @@ ba_status_t ba_destroy(ba_handle_t h) {
     release(ws->ad_xb); release(ws->ad_w); release(ws->ad_gd); release(ws->ad_lamd); release(ws->ad_v);
     release(ws->ad_gt); release(ws->ad_gw); release(ws->lg_sync); release(ws->lg_red); release(ws->lg_prob); release(ws->lg_rb); release(ws->fprob); release(ws->gprob);
     release(ws->fdx); release(ws->sysd); release(ws->syslist); release(ws->mii); release(ws->mjj); release(ws->mkk);
-    release(ws->offs); release(ws->pcopy); release(ws->prox); release(ws->corr);
+    release(ws->offs); release(ws->pcopy); release(ws->prox); release(ws->corr); release(ws->pgo);
     delete ws;
   }
   graph_drop(h, h->step_graph);

@@ -210,6 +210,7 @@ struct Workspace {
   DBuf<unsigned char> prox;       // ba_proximity_edges scratch (counters, CTA flags, centres, transforms)
   long long prox_blocks = 0, prox_frames = 0;  // what its layout holds
   DBuf<int> corr;                 // ba_patch_correlation: frame histogram, cursors, edge order
+  DBuf<double> pgo;               // ba_pgo_lm: LM state (3), candidate similarities [N][8], factor costs [F]
   DBuf<float> ad_lamd;            // [P] depth part of the adjoint solve
   DBuf<double> ad_v;              // [n_pad] pose part of the adjoint right-hand side
   DBuf<float> ad_gt, ad_gw;       // [E][2] scratch when the caller passes no output
@@ -267,6 +268,7 @@ long long dpv_hist_entries(long long m);
 ba_status_t dpv_assemble(ba_handle_t h, int it, int skip_init);
 ba_status_t dpv_assemble_ext(ba_handle_t h, int it, const double* v_ext, const float* w_ext);
 ba_status_t dpv_ensure_system(ba_handle_t h, int fixed);
+ba_status_t dpv_ensure_generic_system(ba_handle_t h, int n);  // one dense system of n unknowns
 ba_status_t dpv_tape_reserve(ba_handle_t h, int iters);
 ba_status_t dpv_tape_state(ba_handle_t h, int it);
 ba_status_t dpv_tape_step(ba_handle_t h, int it);

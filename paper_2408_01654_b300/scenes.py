@@ -322,3 +322,65 @@ def correlation_inputs(scene: Scene, D: int = 128, scale: int = 4, noise_px: flo
     coords = np.stack([x, y], -1) / scale + rng.normal(0.0, noise_px / scale, size=(E, 3, 3, 2))
     coords = np.where(np.isfinite(coords), coords, -1.0e4).astype(np.float32)
     return {"fmap": fmap, "gmap": gmap, "coords": coords}
+
+
+def _sim_matrix(R: np.ndarray, t: np.ndarray, s: float) -> np.ndarray:
+    M = np.eye(4)
+    M[:3, :3] = s * R
+    M[:3, 3] = t
+    return M
+
+
+def _sim_vec(M: np.ndarray) -> np.ndarray:
+    """4x4 similarity matrix -> (t, q xyzw, s)."""
+    s = float(np.cbrt(np.linalg.det(M[:3, :3])))
+    return np.concatenate([M[:3, 3], Rotation.from_matrix(M[:3, :3] / s).as_quat(), [s]])
+
+
+def pose_graph(seed: int = 0, N: int = 1000, laps: float = 2.0, loop_every: int = 40, loop_noise: float = 0.0,
+               drift_scale: float = 0.3, odo_rot_deg: float = 0.1, odo_trans: float = 0.01) -> dict:
+    """A Sim(3) pose graph shaped like the classical backend's (Sec. 3.3
+    "Optimization"): N keyframes along a trajectory that circles the same
+    ground `laps` times, a smoothness factor between consecutive keyframes
+    and loop factors between keyframes one lap apart.
+
+    The true similarities S*_i carry a slowly varying scale (the odometry's
+    scale drift, exp(drift_scale sin(2 pi i / N))).  The odometry estimate
+    composes the true relative motions with the scale ratio removed and small
+    rotation / relative-translation noise, and starts every keyframe at scale
+    1 (the paper's initialisation).  Smoothness measurements are the
+    estimate's own relative motions; loop measurements the inverse true
+    relative similarity (the Eq. 6 convention) with optional noise.
+
+    Plain 4x4 matrices and scipy rotations only.  Returns dict(S [N,8] the
+    start, gt [N,8] the true similarities, dS [F,8], fa, fb, loop int32 [F]);
+    similarities are (tx, ty, tz, qx, qy, qz, qw, s) mapping x to s R x + t."""
+    rng = np.random.default_rng(seed)
+    u = np.arange(N) / N
+    ang = 2 * np.pi * laps * u
+    pos = np.stack([20 * np.cos(ang), 20 * np.sin(ang), 0.5 * np.sin(3 * ang)], 1)
+    rot = Rotation.from_euler("zyx", np.stack([ang + np.pi / 2, 0.05 * np.sin(5 * ang), 0.03 * np.cos(7 * ang)], 1))
+    scale = np.exp(drift_scale * np.sin(2 * np.pi * u))
+    gt = np.stack([_sim_matrix(rot[i].as_matrix(), pos[i], scale[i]) for i in range(N)])
+    est = [_sim_matrix(gt[0][:3, :3] / scale[0], gt[0][:3, 3], 1.0)]
+    for i in range(N - 1):
+        rel = np.linalg.inv(gt[i]) @ gt[i + 1]
+        s = np.cbrt(np.linalg.det(rel[:3, :3]))
+        R = Rotation.from_rotvec(np.deg2rad(odo_rot_deg) * rng.normal(size=3)).as_matrix() @ (rel[:3, :3] / s)
+        t = rel[:3, 3] * (1 + odo_trans * rng.normal()) + odo_trans * np.linalg.norm(rel[:3, 3]) * rng.normal(size=3)
+        est.append(est[-1] @ _sim_matrix(R, t, 1.0))
+    fa, fb, loop, dS = [], [], [], []
+    for i in range(N - 1):
+        fa.append(i), fb.append(i + 1), loop.append(0)
+        dS.append(_sim_vec(np.linalg.inv(est[i]) @ est[i + 1]))
+    lap = int(round(N / laps)) if laps > 1 else N - 1
+    for j in range(0, N - lap, max(1, loop_every)):
+        k = j + lap
+        meas = np.linalg.inv(np.linalg.inv(gt[j]) @ gt[k])
+        if loop_noise:
+            R = Rotation.from_rotvec(loop_noise * rng.normal(size=3)).as_matrix()
+            meas = _sim_matrix(R, loop_noise * rng.normal(size=3), float(np.exp(loop_noise * rng.normal()))) @ meas
+        fa.append(j), fb.append(k), loop.append(1), dS.append(_sim_vec(meas))
+    i32 = lambda a: np.asarray(a, np.int32)  # noqa: E731
+    return dict(S=np.stack([_sim_vec(M) for M in est]), gt=np.stack([_sim_vec(M) for M in gt]),
+                dS=np.asarray(dS), fa=i32(fa), fb=i32(fb), loop=i32(loop))
