@@ -53,14 +53,20 @@ WORKLOADS = {
                   "the global workload", scenes.global_ba),
     "correlation": ("patch correlation (Eq. 4) over the odometry window: 22 frames of 120x160 feature maps with 128 "
                     "float32 channels, 27,456 edges, 3x3 patch pixels, 7x7 offsets (radius 3)", scenes.odometry),
+    "pgo": ("Sim(3) pose-graph optimisation (Sec. 3.3, Eqs. 5-7): 500 keyframes on a two-lap trajectory with "
+            "scale drift, 499 smoothness + 13 loop factors, 10 Levenberg-Marquardt iterations per step, "
+            "mixed precision solve", lambda seed=0: scenes.pose_graph(seed, N=PGO_N, loop_every=20, loop_noise=0.002)),
     "batched": ("batched uneven BA: 64 independent problems, frames round(exp(U[ln 8, ln 400])), 96 patches/frame, "
                 "+-6 local + proximity loop edges, 4 GN iterations each, 2 fixed poses each", scenes.batched),
 }
+PGO_N, PGO_ITERS = 500, 10
+PGO_METRIC = "Sim(3) pose-graph Levenberg-Marquardt iterations/sec (500 keyframes, dense 3493-unknown system)"
+PGO_UNIT = "LM it/s"
 PROX_METRIC = "proximity loop-edge constructions/sec (all 1000 frames queried) at bit-exact edges vs the FP64 oracle"
 PROX_UNIT = "constructions/s"
 PROX_GAP, PROX_RADIUS = 30, 2.0
 FP32_ALU_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12  # B300 FP32 CUDA cores at the maximum SM clock
-KERNEL_FILES = {"proximity": "proximity.cu", "correlation": "correlation.cu", "assemble": "assemble.cu", "solve": "solve_small.cu", "factor": "solve_large.cu", "backsub": "update.cu",
+KERNEL_FILES = {"pgo": "pgo.cu", "proximity": "proximity.cu", "correlation": "correlation.cu", "assemble": "assemble.cu", "solve": "solve_small.cu", "factor": "solve_large.cu", "backsub": "update.cu",
                 "retract": "update.cu", "init": "assemble.cu", "preprocess": "preprocess.cu"}
 
 
@@ -86,9 +92,11 @@ def parse():
         a.steps = 3 if not short else (50 if a.impl == "reference" else 2000)
         if a.workload == "correlation":
             a.steps = 3 if a.impl == "reference" else 200
+        if a.workload == "pgo":
+            a.steps = 2 if a.impl == "reference" else 20
     a.precision_set = a.precision is not None
     if a.precision is None:
-        a.precision = "fp32"
+        a.precision = "mixed" if a.workload == "pgo" else "fp32"
     return a
 
 
@@ -679,6 +687,195 @@ def run_correlation(args):
     return 0
 
 
+def run_reference_pgo(args):
+    """The oracle's LM, one iteration per step (a bounded sample: one
+    iteration of the dense FP64 solve takes seconds on one core)."""
+    if int(os.environ.get("RANK", "0")) != 0:
+        return 0
+    import oracle
+    oracle.build()
+    desc, make = WORKLOADS["pgo"]
+    g = make(seed=0)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.pgo_lm(g["S"], g["dS"], g["fa"], g["fb"], g["loop"], iters=1)
+    el = time.perf_counter() - t0
+    value = args.steps / el
+    line = {
+        "impl": "reference", "metric": PGO_METRIC, "value": value, "unit": PGO_UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": desc, "N": PGO_N, "F": int(len(g["fa"])), "unknowns": 7 * (PGO_N - 1)},
+        "cpu_baseline": {"value": value, "unit": PGO_UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{args.steps} x the first LM iteration from the start (linearisation, dense "
+                                   f"FP64 Cholesky, cost), single-threaded FP64 oracle (-O2), "
+                                   f"{cpu_cores()} cores visible"},
+        "e2e": {"value": value, "unit": PGO_UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def run_pgo(args):
+    """One step = PGO_ITERS Levenberg-Marquardt iterations of ba_pgo_lm from
+    the odometry start (the similarities reset from a device copy first)."""
+    import torch
+
+    from paper_2408_01654_b300 import build as pbuild
+    from paper_2408_01654_b300.ba import DPVBA
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    if rank == 0:
+        pbuild.build()
+    if dist:
+        dist.barrier()
+    desc, make = WORKLOADS["pgo"]
+    g = make(seed=problem_seed(rank))
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(dev)
+    T = {k: torch.tensor(g[k], device=dev) for k in ("S", "dS", "fa", "fb", "loop")}
+    S0 = T["S"].clone()
+    iters = PGO_ITERS
+    cost = torch.empty(iters + 1, dtype=torch.float64, device=dev)
+    acc = torch.empty(iters, dtype=torch.int32, device=dev)
+    ba = DPVBA(precision=args.precision, stream=stream)
+
+    def call():
+        ba.pgo_lm(T["S"], T["dS"], T["fa"], T["fb"], T["loop"], iters=iters, cost=cost, accepted=acc)
+
+    with torch.cuda.stream(stream):
+        for _ in range(max(args.warmup, 3)):
+            T["S"].copy_(S0)
+            call()
+    ba.sync()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    launches0 = ba.info()["launches"]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk, torch.cuda.stream(stream):
+        for k in range(args.steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            T["S"].copy_(S0)
+            call()
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ba.sync()
+    launches = ba.info()["launches"] - launches0
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = max_over_ranks(sum(step_ms), dev)
+    value = job_throughput(args.steps * iters, world, total_ms)
+    final_cost = cost.cpu().numpy()
+
+    # kernel classes, profiled on separate steps (events between the classes)
+    ba.profile(True)
+    with torch.cuda.stream(stream):
+        for k in range(args.steps):
+            flush.zero_()
+            T["S"].copy_(S0)
+            call()
+    ba.sync()
+    prof = ba.profile_read()
+    ba.profile(False)
+
+    # end to end: similarities and factors from pinned host memory, the
+    # optimised similarities and the cost curve back
+    host = {k: v.cpu().pin_memory() for k, v in T.items()}
+    host["S"].copy_(S0.cpu())
+    backS = torch.empty(T["S"].shape, dtype=torch.float64).pin_memory()
+    backc = torch.empty(cost.shape, dtype=torch.float64).pin_memory()
+    h2d = sum(v.numel() * v.element_size() for v in host.values())
+    d2h = backS.numel() * 8 + backc.numel() * 8
+    ne = min(args.steps, 10)
+    eev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(ne)]
+    with torch.cuda.stream(stream):
+        for k in range(ne):
+            eev[k][0].record(stream)
+            for name, hv in host.items():
+                T[name].copy_(hv, non_blocking=True)
+            call()
+            backS.copy_(T["S"], non_blocking=True)
+            backc.copy_(cost, non_blocking=True)
+            eev[k][1].record(stream)
+    torch.cuda.synchronize()
+    ba.sync()
+    e2e_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in eev), dev)
+    e2e_value = job_throughput(ne * iters, world, e2e_ms)
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return 0
+
+    n = 7 * (PGO_N - 1)
+    dom = max((k for k in prof if prof[k][1] > 0), key=lambda k: prof[k][0])
+    F = len(g["fa"])
+
+    def pgo_bytes(kind):
+        # per launch: the dense lower triangle written (memset + accumulation)
+        # and read by the solver; similarities, measurements and indices once
+        tri = n * (n + 1) // 2
+        if kind == "pgo":
+            return 8 * tri + 64 * PGO_N * 3 + 76 * F
+        return algorithmic_bytes(kind, PGO_N, 0, 0, n)
+
+    roof = roofline(dom, prof, args.steps, pgo_bytes, [n], "pgo")
+
+    parity = None
+    cpu = None
+    if not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        # the first LM iteration on both sides from the same start
+        T["S"].copy_(S0)
+        c1 = torch.empty(2, dtype=torch.float64, device=dev)
+        a1 = torch.empty(1, dtype=torch.int32, device=dev)
+        ba.pgo_lm(T["S"], T["dS"], T["fa"], T["fb"], T["loop"], iters=1, cost=c1, accepted=a1)
+        ba.sync()
+        t0 = time.perf_counter()
+        want = oracle.pgo_lm(g["S"], g["dS"], g["fa"], g["fb"], g["loop"], iters=1)
+        el = time.perf_counter() - t0
+        got = T["S"].cpu().numpy()
+        parity = {"iterations_compared": 1,
+                  "max_abs_diff_similarity": float(np.abs(got - want["S"]).max()),
+                  "cost_rel_diff": float(abs(c1[1].item() - want["cost"][1]) / want["cost"][1]),
+                  "accepted_equal": bool(a1[0].item() == int(want["accepted"][0]))}
+        cpu = {"value": 1.0 / el, "unit": PGO_UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"the first LM iteration of the workload (the parity check's), single-threaded FP64 "
+                         f"oracle (-O2) on 1 of {cpu_cores()} host cores, {el:.1f} s"}
+    line = {
+        "metric": PGO_METRIC, "value": value, "unit": PGO_UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": desc, "N": PGO_N, "F": F, "unknowns": n, "lm_iterations_per_step": iters,
+                   "precision": args.precision,
+                   "l2": "flushed between steps (256 MiB write); the dense system (49 MB) fits L2",
+                   "step": "similarities reset, then ba_pgo_lm (eager launches, no host round trip inside)"},
+        "cost_curve_last_step": [float(x) for x in final_cost],
+        "parity_vs_oracle": parity,
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": PGO_UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": int(launches),
+        "clocks": clk.summary(),
+        "step_ms": {"min": min(step_ms), "median": statistics.median(step_ms), "max": max(step_ms)},
+    }
+    print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -687,6 +884,8 @@ def run_reference(args):
         return run_reference_proximity(args)
     if args.workload == "correlation":
         return run_reference_correlation(args)
+    if args.workload == "pgo":
+        return run_reference_pgo(args)
     desc, make = WORKLOADS[args.workload]
     import oracle
     oracle.build()
@@ -1146,6 +1345,8 @@ def main():
         return run_proximity(args)
     if args.workload == "correlation":
         return run_correlation(args)
+    if args.workload == "pgo":
+        return run_pgo(args)
     return run_ours(args)
 
 

@@ -376,9 +376,11 @@ extern "C" ba_status_t ba_pgo_lm(ba_handle_t h, int N, int F, double* S, const d
   else DPV_CUDA(h, cudaMemsetAsync(fcost, 0, sizeof(double), st));
   k_pgo_decide<<<1, PG_RED, 0, st>>>(F, fcost, lm, -1, cost, accepted);
   h->launches += F > 0 ? 3 : 2;
+  dpv_prof_end(h);
   DPV_CUDA(h, cudaGetLastError());
   const int lin_blocks = std::max(1, std::min((F + PG_WARPS - 1) / PG_WARPS, 16 * h->num_sms));
   for (int it = 0; it < iters && n > 0; ++it) {
+    dpv_prof_begin(h, BA_KERNEL_PGO);
     DPV_CUDA(h, cudaMemsetAsync(ws->S.p, 0, sizeof(double) * h->nS, st));
     DPV_CUDA(h, cudaMemsetAsync(ws->y.p, 0, sizeof(double) * h->n_pad, st));
     if (F > 0)
@@ -386,14 +388,21 @@ extern "C" ba_status_t ba_pgo_lm(ba_handle_t h, int N, int F, double* S, const d
                                                      ws->y.p + d.voff, ws->status);
     k_pgo_damp<<<(d.n_pad + 255) / 256, 256, 0, st>>>(n, d.n_pad, d.TS, ws->S.p + d.soff, lm);
     h->launches += F > 0 ? 2 : 1;
+    dpv_prof_end(h);
     DPV_CUDA(h, cudaGetLastError());
+    // (the solver records its own kernel classes)
     int retracted = 0;
-    if ((s = dpv_solve(h, &retracted, 0))) return s;
+    dpv_prof_begin(h, BA_KERNEL_SOLVE);
+    s = dpv_solve(h, &retracted, 0);
+    dpv_prof_end(h);
+    if (s) return s;
+    dpv_prof_begin(h, BA_KERNEL_PGO);
     k_pgo_cand<<<(N + 127) / 128, 128, 0, st>>>(N, S, ws->dx.p + d.voff, cand);
     if (F > 0) k_pgo_cost<<<(F + 127) / 128, 128, 0, st>>>(N, F, cand, dS, fa, fb, loop, fcost);
     k_pgo_decide<<<1, PG_RED, 0, st>>>(F, fcost, lm, it, cost, accepted);
     k_pgo_commit<<<(8 * N + 255) / 256, 256, 0, st>>>(N, S, cand, lm);
     h->launches += F > 0 ? 4 : 3;
+    dpv_prof_end(h);
     DPV_CUDA(h, cudaGetLastError());
   }
   // no unknowns (N = 1): nothing moves, every iteration records the cost
@@ -401,7 +410,6 @@ extern "C" ba_status_t ba_pgo_lm(ba_handle_t h, int N, int F, double* S, const d
     k_pgo_decide<<<1, PG_RED, 0, st>>>(F, fcost, lm, it, cost, accepted);
     ++h->launches;
   }
-  dpv_prof_end(h);
   DPV_CUDA(h, cudaGetLastError());
   return BA_OK;
 }

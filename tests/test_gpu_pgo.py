@@ -134,7 +134,8 @@ def test_edge_cases_and_errors():
 
 def test_bundle_adjustment_after_pgo_on_the_same_handle():
     # the pose-graph call borrows the handle's pose-system buffers; a later
-    # ba_step lays its own system out again and gives the same result
+    # ba_step lays its own system out again and gives the same result as a
+    # fresh handle
     s = scenes.tiny(0)
     fresh = DPVBA(precision="mixed")
     t = scene_tensors(s)
@@ -152,4 +153,6 @@ def test_bundle_adjustment_after_pgo_on_the_same_handle():
     gpu(ba, scenes.pose_graph(2, N=60, loop_every=5), 3)  # n = 413: the large solver's layout
     ba.step(2, s.fixed)
     ba.sync()
-    assert np.array_equal(t2["poses"].cpu().numpy(), want)
+    # (the assembly's floating-point atomics make repeated runs agree to
+    # rounding, not bit for bit)
+    assert np.abs(t2["poses"].cpu().numpy() - want).max() < 1e-6
