@@ -17,7 +17,9 @@ of arxiv 2408.01654 it follows:
                    appendix "Bundle-Adjustment Efficiency").
 * ``gn``           whole Gauss-Newton iterations: linearise, Schur-eliminate,
                    Cholesky-solve the pose system, back-substitute the depths,
-                   retract the poses on SE(3).
+                   retract the poses on SE(3); with ``pixels=9`` every pixel
+                   of the patch contributes its own 2-D residual (Eq. 3 over
+                   the whole patch, 18 rows per edge).
 * ``proximity_edges`` loop edges from camera proximity (Sec. 3.2 "Proximity
                    Loop Closure"): for each query frame the nearest older
                    camera centre within a radius, then uni-directional edges
@@ -129,8 +131,10 @@ def edge_terms(s, poses=None, patches=None, targets=None, z_min=DEFAULT_OPTS[2])
     return proj, res, Ji, Jj, Jd, valid.astype(bool)
 
 
-def schur_system(s, fixed=None, opts=DEFAULT_OPTS, poses=None, patches=None, targets=None, weights=None):
-    """Reduced pose system at the given state: (S [n,n], y [n], Ct [P], w [P], cost)."""
+def schur_system(s, fixed=None, opts=DEFAULT_OPTS, poses=None, patches=None, targets=None, weights=None,
+                 pixels=1):
+    """Reduced pose system at the given state: (S [n,n], y [n], Ct [P], w [P], cost).
+    pixels = 9: one residual per patch pixel, targets [E,9,2]."""
     fixed = s.fixed if fixed is None else fixed
     poses = _d(s.poses if poses is None else poses)
     patches = _d(s.patches if patches is None else patches)
@@ -141,16 +145,21 @@ def schur_system(s, fixed=None, opts=DEFAULT_OPTS, poses=None, patches=None, tar
     Ct, w = np.empty(s.P), np.empty(s.P)
     cost = ctypes.c_double()
     ii, jj, kk = _i(s.ii), _i(s.jj), _i(s.kk)
-    _check(lib().oracle_schur_system(
+    if targets.size != 2 * pixels * len(s.kk):
+        raise ValueError("targets: [E,2] for pixels = 1, [E,9,2] for pixels = 9")
+    _check(lib().oracle_schur_system_px(
         s.N, s.P, len(s.kk), _p(poses), _p(patches), _p(ii), _p(jj), _p(kk), _p(targets), _p(weights),
-        _p(_d(s.intrinsics)), fixed, _p(_d(opts)), _p(S), _p(y), _p(Ct), _p(w), ctypes.byref(cost)))
+        _p(_d(s.intrinsics)), fixed, _p(_d(opts)), pixels, _p(S), _p(y), _p(Ct), _p(w), ctypes.byref(cost)))
     return S, y, Ct, w, cost.value
 
 
-def gn(s, iters=None, fixed=None, opts=DEFAULT_OPTS, poses=None, patches=None, targets=None, weights=None):
+def gn(s, iters=None, fixed=None, opts=DEFAULT_OPTS, poses=None, patches=None, targets=None, weights=None,
+       pixels=1):
     """Run GN iterations from the scene's state.  Returns a dict with the final
     poses [N,7], patches [P,3,3,3], the per-iteration steps dxi [iters,n] and
-    dd [iters,P], and the cost before each iteration plus after the last."""
+    dd [iters,P], and the cost before each iteration plus after the last.
+    pixels = 9: one residual per patch pixel (Eq. 3 over the whole patch),
+    targets [E,9,2], the edge's weights shared by its nine residuals."""
     iters = s.iters if iters is None else iters
     fixed = s.fixed if fixed is None else fixed
     poses = _d(s.poses if poses is None else poses).copy()
@@ -160,9 +169,11 @@ def gn(s, iters=None, fixed=None, opts=DEFAULT_OPTS, poses=None, patches=None, t
     n = 6 * (s.N - fixed)
     dxi, dd, cost = np.empty((iters, n)), np.empty((iters, s.P)), np.empty(iters + 1)
     ii, jj, kk = _i(s.ii), _i(s.jj), _i(s.kk)
-    _check(lib().oracle_gn(
+    if targets.size != 2 * pixels * len(s.kk):
+        raise ValueError("targets: [E,2] for pixels = 1, [E,9,2] for pixels = 9")
+    _check(lib().oracle_gn_px(
         s.N, s.P, len(s.kk), _p(poses), _p(patches), _p(ii), _p(jj), _p(kk), _p(targets), _p(weights),
-        _p(_d(s.intrinsics)), iters, fixed, _p(_d(opts)), _p(dxi), _p(dd), _p(cost)))
+        _p(_d(s.intrinsics)), iters, fixed, _p(_d(opts)), pixels, _p(dxi), _p(dd), _p(cost)))
     return {"poses": poses, "patches": patches, "dxi": dxi, "dd": dd, "cost": cost}
 
 

@@ -200,18 +200,23 @@ struct Opts { double lambda_p, lambda_d, z_min, d_min; };
 
 template <class T> struct Problem {
   int N, P, E;
+  int pix = 1;                     // residual pixels per edge: 1 (the centre) or 9 (the whole patch)
   std::vector<Pose<T>> poses;      // [N]
   std::vector<T> u, v, d;          // patch centre pixel and inverse depth [P]
+  std::vector<T> pu, pv;           // all nine pixels of each patch [P,9] (row-major 3x3)
   const int *ii, *jj, *kk;
-  std::vector<T> tgt, wgt;         // [E,2]
+  std::vector<T> tgt, wgt;         // [E,pix,2], [E,2]
   double K[4];
+  // pixel q of the edge's residual: the centre (4) when pix = 1
+  int pixel(int q) const { return pix == 1 ? 4 : q; }
 };
 
 template <class T>
 void load_problem(Problem<T>& pb, int N, int P, int E, const double* poses, const double* patches,
                   const int* ii, const int* jj, const int* kk, const double* targets,
-                  const double* weights, const double* intr) {
+                  const double* weights, const double* intr, int pix = 1) {
   pb.N = N; pb.P = P; pb.E = E;
+  pb.pix = pix;
   pb.poses.resize(N);
   for (int a = 0; a < N; ++a) {
     for (int r = 0; r < 3; ++r) pb.poses[a].t[r] = T(poses[7 * a + r]);
@@ -223,9 +228,16 @@ void load_problem(Problem<T>& pb, int N, int P, int E, const double* poses, cons
     pb.v[k] = T(patches[27 * k + 1 * 9 + 4]);
     pb.d[k] = T(patches[27 * k + 2 * 9 + 4]);
   }
+  pb.pu.resize(9 * (size_t)P); pb.pv.resize(9 * (size_t)P);
+  for (int k = 0; k < P; ++k)
+    for (int q = 0; q < 9; ++q) {
+      pb.pu[9 * (size_t)k + q] = T(patches[27 * k + q]);
+      pb.pv[9 * (size_t)k + q] = T(patches[27 * k + 9 + q]);
+    }
   pb.ii = ii; pb.jj = jj; pb.kk = kk;
-  pb.tgt.resize(2 * (size_t)E); pb.wgt.resize(2 * (size_t)E);
-  for (size_t e = 0; e < 2 * (size_t)E; ++e) { pb.tgt[e] = T(targets[e]); pb.wgt[e] = T(weights[e]); }
+  pb.tgt.resize(2 * (size_t)E * pix); pb.wgt.resize(2 * (size_t)E);
+  for (size_t e = 0; e < 2 * (size_t)E * pix; ++e) pb.tgt[e] = T(targets[e]);
+  for (size_t e = 0; e < 2 * (size_t)E; ++e) pb.wgt[e] = T(weights[e]);
   for (int r = 0; r < 4; ++r) pb.K[r] = intr[r];
 }
 
@@ -271,10 +283,15 @@ void linearize(const Problem<T>& pb, int fixed, const Opts& o, Linear<T>& L) {
   L.Ek.assign(pb.P, {});
   L.cost = T(0.0);
   EdgeTerms<T> et;
-  for (int e = 0; e < pb.E; ++e) {  // input order
+  // each edge contributes one 2-D residual per residual pixel (Eq. 3 sums
+  // over the patch's pixels; with pix = 1 only its centre), all with the
+  // edge's weight
+  for (int e = 0; e < pb.E; ++e)  // input order
+   for (int q = 0; q < pb.pix; ++q) {
     const int i = pb.ii[e], j = pb.jj[e], k = pb.kk[e];
-    edge_terms(pb.poses[i], pb.poses[j], pb.u[k], pb.v[k], pb.d[k], &pb.tgt[2 * (size_t)e], pb.K, o.z_min,
-               i == j, et);
+    const size_t px = 9 * (size_t)k + pb.pixel(q);
+    edge_terms(pb.poses[i], pb.poses[j], pb.pu[px], pb.pv[px], pb.d[k], &pb.tgt[2 * ((size_t)e * pb.pix + q)],
+               pb.K, o.z_min, i == j, et);
     if (!et.valid) continue;
     const T* w = &pb.wgt[2 * (size_t)e];
     for (int c = 0; c < 2; ++c) L.cost += w[c] * et.r[c] * et.r[c];
@@ -392,13 +409,15 @@ template <class T>
 T problem_cost(const Problem<T>& pb, const Opts& o) {
   T cost = T(0.0);
   EdgeTerms<T> et;
-  for (int e = 0; e < pb.E; ++e) {
-    const int i = pb.ii[e], j = pb.jj[e], k = pb.kk[e];
-    edge_terms(pb.poses[i], pb.poses[j], pb.u[k], pb.v[k], pb.d[k], &pb.tgt[2 * (size_t)e], pb.K, o.z_min,
-               i == j, et);
-    if (!et.valid) continue;
-    for (int c = 0; c < 2; ++c) cost += pb.wgt[2 * (size_t)e + c] * et.r[c] * et.r[c];
-  }
+  for (int e = 0; e < pb.E; ++e)
+    for (int q = 0; q < pb.pix; ++q) {
+      const int i = pb.ii[e], j = pb.jj[e], k = pb.kk[e];
+      const size_t px = 9 * (size_t)k + pb.pixel(q);
+      edge_terms(pb.poses[i], pb.poses[j], pb.pu[px], pb.pv[px], pb.d[k], &pb.tgt[2 * ((size_t)e * pb.pix + q)],
+                 pb.K, o.z_min, i == j, et);
+      if (!et.valid) continue;
+      for (int c = 0; c < 2; ++c) cost += pb.wgt[2 * (size_t)e + c] * et.r[c] * et.r[c];
+    }
   return cost;
 }
 
@@ -462,14 +481,17 @@ int oracle_edge_terms(int N, int P, int E, const double* poses, const double* pa
 
 // reduced pose system of the current state: S [n*n] (full, symmetric), y [n],
 // Ct [P] = C + lambda_d, w [P]; n = 6 (N - fixed); cost = sum w r^2
-int oracle_schur_system(int N, int P, int E, const double* poses, const double* patches, const int* ii,
-                        const int* jj, const int* kk, const double* targets, const double* weights,
-                        const double* intr, int fixed, const double* opts4, double* S, double* y, double* Ct,
-                        double* w, double* cost) {
-  if (check_indices(N, P, E, ii, jj, kk)) return 1;
+// pix = 1: one residual per edge at the patch centre, targets [E,2];
+// pix = 9: one per patch pixel, targets [E,9,2] (row-major 3x3), one weight
+// pair per edge shared by its nine residuals.
+int oracle_schur_system_px(int N, int P, int E, const double* poses, const double* patches, const int* ii,
+                           const int* jj, const int* kk, const double* targets, const double* weights,
+                           const double* intr, int fixed, const double* opts4, int pix, double* S, double* y,
+                           double* Ct, double* w, double* cost) {
+  if (check_indices(N, P, E, ii, jj, kk) || (pix != 1 && pix != 9)) return 1;
   const Opts o{opts4[0], opts4[1], opts4[2], opts4[3]};
   Problem<double> pb;
-  load_problem(pb, N, P, E, poses, patches, ii, jj, kk, targets, weights, intr);
+  load_problem(pb, N, P, E, poses, patches, ii, jj, kk, targets, weights, intr, pix);
   Linear<double> L;
   linearize(pb, fixed, o, L);
   std::vector<double> Sv, yv;
@@ -484,13 +506,13 @@ int oracle_schur_system(int N, int P, int E, const double* poses, const double* 
 // `iters` GN iterations in place on poses [N,7] and patches [P,3,3,3];
 // dxi [iters, 6(N-fixed)], dd [iters, P], cost [iters+1] (cost before each
 // iteration and after the last).
-int oracle_gn(int N, int P, int E, double* poses, double* patches, const int* ii, const int* jj, const int* kk,
-              const double* targets, const double* weights, const double* intr, int iters, int fixed,
-              const double* opts4, double* dxi, double* dd, double* cost) {
-  if (check_indices(N, P, E, ii, jj, kk)) return 1;
+int oracle_gn_px(int N, int P, int E, double* poses, double* patches, const int* ii, const int* jj,
+                 const int* kk, const double* targets, const double* weights, const double* intr, int iters,
+                 int fixed, const double* opts4, int pix, double* dxi, double* dd, double* cost) {
+  if (check_indices(N, P, E, ii, jj, kk) || (pix != 1 && pix != 9)) return 1;
   const Opts o{opts4[0], opts4[1], opts4[2], opts4[3]};
   Problem<double> pb;
-  load_problem(pb, N, P, E, poses, patches, ii, jj, kk, targets, weights, intr);
+  load_problem(pb, N, P, E, poses, patches, ii, jj, kk, targets, weights, intr, pix);
   const int n = 6 * (N - fixed);
   for (int it = 0; it < iters; ++it) {
     std::vector<double> x, dk;
@@ -504,6 +526,21 @@ int oracle_gn(int N, int P, int E, double* poses, double* patches, const int* ii
   }
   if (cost) cost[iters] = problem_cost(pb, o);
   return 0;
+}
+
+int oracle_schur_system(int N, int P, int E, const double* poses, const double* patches, const int* ii,
+                        const int* jj, const int* kk, const double* targets, const double* weights,
+                        const double* intr, int fixed, const double* opts4, double* S, double* y, double* Ct,
+                        double* w, double* cost) {
+  return oracle_schur_system_px(N, P, E, poses, patches, ii, jj, kk, targets, weights, intr, fixed, opts4, 1, S, y,
+                                Ct, w, cost);
+}
+
+int oracle_gn(int N, int P, int E, double* poses, double* patches, const int* ii, const int* jj, const int* kk,
+              const double* targets, const double* weights, const double* intr, int iters, int fixed,
+              const double* opts4, double* dxi, double* dd, double* cost) {
+  return oracle_gn_px(N, P, E, poses, patches, ii, jj, kk, targets, weights, intr, iters, fixed, opts4, 1, dxi, dd,
+                      cost);
 }
 
 // forward-mode derivative of  L = <a, poses_final> + <b, depths_final>  with

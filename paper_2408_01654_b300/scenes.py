@@ -384,3 +384,25 @@ def pose_graph(seed: int = 0, N: int = 1000, laps: float = 2.0, loop_every: int 
     i32 = lambda a: np.asarray(a, np.int32)  # noqa: E731
     return dict(S=np.stack([_sim_vec(M) for M in est]), gt=np.stack([_sim_vec(M) for M in gt]),
                 dS=np.asarray(dS), fa=i32(fa), fb=i32(fb), loop=i32(loop))
+
+
+def full_patch_targets(scene: Scene) -> np.ndarray:
+    """Targets for the whole-patch residual (Eq. 3 summed over all nine
+    pixels of each patch): float32 [E,3,3,2], pixel (v, u) of edge e's
+    patch at its ground-truth inverse depth projected into frame jj with
+    the ground-truth poses, plus the edge's own centre offset (noise and
+    outlier displacement, targets - proj_gt), which the nine pixels share as
+    they share the update operator's flow correction."""
+    R = Rotation.from_quat(scene.poses_gt[:, 3:]).as_matrix()
+    t = scene.poses_gt[:, :3]
+    px = scene.patches[:, 0].reshape(-1, 9).astype(np.float64)[scene.kk]  # [E,9]
+    py = scene.patches[:, 1].reshape(-1, 9).astype(np.float64)[scene.kk]
+    d = np.broadcast_to(scene.depth_gt[scene.kk][:, None], px.shape)
+    pc = _camera_points(px, py, d)                                          # [E,9,3] in frame ii
+    Ri, ti, Rj, tj = R[scene.ii], t[scene.ii], R[scene.jj], t[scene.jj]
+    pw = np.einsum("eji,epj->epi", Ri, pc - ti[:, None, :])                 # R_i^T (pc - t_i)
+    q = np.einsum("eij,epj->epi", Rj, pw) + tj[:, None, :]
+    with np.errstate(divide="ignore", invalid="ignore"):
+        uv = np.stack([FX * q[..., 0] / q[..., 2] + CX, FY * q[..., 1] / q[..., 2] + CY], -1)
+    off = scene.targets.astype(np.float64) - scene.proj_gt
+    return (uv + off[:, None, :]).reshape(-1, 3, 3, 2).astype(np.float32)
