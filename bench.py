@@ -42,6 +42,9 @@ TF32_PER_BF16 = 1.1 / 2.25  # nominal dense TF32 / BF16 tensor rates
 WORKLOADS = {
     "odometry": ("odometry-window BA: 22 keyframes, 96 patches/frame, patch lifetime 13, 8% outliers, "
                  "2 GN iterations, 2 fixed poses", scenes.odometry),
+    "odometry_full": ("odometry-window BA with the whole-patch residual (Eq. 3 over all nine patch pixels, 18 rows "
+                      "per edge): 22 keyframes, 96 patches/frame, patch lifetime 13, 8% outliers, 2 GN iterations, "
+                      "2 fixed poses", lambda seed=0: full_patch_scene(scenes.odometry(seed))),
     "tiny": ("tiny BA: 8 frames, 96 patches/frame, +-3 frame edges, 2 GN iterations, 2 fixed poses", scenes.tiny),
     "global": ("global loop-closure BA: 1000 keyframes, 96 patches/frame, +-6 local + proximity loop edges, "
                "4 GN iterations, 2 fixed poses", scenes.global_ba),
@@ -60,6 +63,16 @@ WORKLOADS = {
                 "+-6 local + proximity loop edges, 4 GN iterations each, 2 fixed poses each", scenes.batched),
 }
 PGO_N, PGO_ITERS = 500, 10
+
+
+def full_patch_scene(s):
+    """The scene with one target per patch pixel ([E,3,3,2])."""
+    import dataclasses
+    return dataclasses.replace(s, targets=scenes.full_patch_targets(s))
+
+
+def residual_pixels(workload):
+    return 9 if workload == "odometry_full" else 1
 PGO_METRIC = "Sim(3) pose-graph Levenberg-Marquardt iterations/sec (500 keyframes, dense 3493-unknown system)"
 PGO_UNIT = "LM it/s"
 PROX_METRIC = "proximity loop-edge constructions/sec (all 1000 frames queried) at bit-exact edges vs the FP64 oracle"
@@ -88,7 +101,7 @@ def parse():
     a = ap.parse_args()
     if a.steps is None:
         # (the reference arm's oracle steps are ~50 ms each on one core: 50 of them)
-        short = a.workload in ("odometry", "tiny", "proximity", "correlation")
+        short = a.workload in ("odometry", "odometry_full", "tiny", "proximity", "correlation")
         a.steps = 3 if not short else (50 if a.impl == "reference" else 2000)
         if a.workload == "correlation":
             a.steps = 3 if a.impl == "reference" else 200
@@ -265,12 +278,12 @@ def pose_errors(a, b):
 LARGE_FRAMES = 200  # scenes this large are sampled one GN iteration at a time on the CPU
 
 
-def time_oracle(scene, budget_s=10.0, max_runs=1000):
+def time_oracle(scene, budget_s=10.0, max_runs=1000, pixels=1):
     import oracle
     oracle.build()
     runs, t0 = 0, time.perf_counter()
     while True:
-        oracle.gn(scene)
+        oracle.gn(scene, pixels=pixels)
         runs += 1
         el = time.perf_counter() - t0
         if el >= budget_s or runs >= max_runs:
@@ -903,11 +916,11 @@ def run_reference(args):
         if scene.N >= LARGE_FRAMES:
             # one GN iteration per step (a full run of the loop-closure BA
             # takes minutes on one core)
-            work = lambda: oracle.gn(scene, iters=1)  # noqa: E731
+            work = lambda: oracle.gn(scene, iters=1, pixels=residual_pixels(args.workload))  # noqa: E731
             iters_per_step = 1
             desc += "; oracle sample: one GN iteration per step"
         else:
-            work = lambda: oracle.gn(scene)  # noqa: E731
+            work = lambda: oracle.gn(scene, pixels=residual_pixels(args.workload))  # noqa: E731
             iters_per_step = scene.iters
     for _ in range(min(args.warmup, 1 if scene.N < LARGE_FRAMES else 0)):
         work()
@@ -959,7 +972,8 @@ def run_ours(args):
     T = scene_tensors(scene, dev)
     pristine = {k: v.clone() for k, v in T.items()}
     stream = torch.cuda.current_stream(dev)
-    ba = DPVBA(precision=args.precision, patches_per_group=args.group, stream=stream)
+    ba = DPVBA(precision=args.precision, patches_per_group=args.group, stream=stream,
+               residual_pixels=residual_pixels(args.workload))
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > L2 (126 MB)
     ba.set_graph(**T)
     tuning = None
@@ -1036,25 +1050,28 @@ def run_ours(args):
     e2e_value = job_throughput(args.steps * scene.iters, world, e2e_ms)
 
     # ---- adjoint of the same step (ba_backward), timed on its own ----------
-    g = torch.Generator(device=dev).manual_seed(rank)
-    gp = torch.randn((scene.N, 7), dtype=torch.float64, device=dev, generator=g)
-    gd = torch.randn(scene.P, dtype=torch.float32, device=dev, generator=g)
-    nb = min(args.steps, 20)
-    bev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(nb)]
-    ba.set_record(True)
-    for k in range(nb + 2):
-        reset()
-        flush.zero_()
-        one_step()
-        if k >= 2:
-            bev[k - 2][0].record(stream)
-        ba.backward(gp, gd)
-        if k >= 2:
-            bev[k - 2][1].record(stream)
-    torch.cuda.synchronize()
-    ba.set_record(False)
-    ba.sync()
-    bwd_ms = statistics.median(a.elapsed_time(b) for a, b in bev)
+    # (the adjoint covers the patch-centre residual only)
+    bwd_ms, nb = None, 0
+    if residual_pixels(args.workload) == 1:
+        g = torch.Generator(device=dev).manual_seed(rank)
+        gp = torch.randn((scene.N, 7), dtype=torch.float64, device=dev, generator=g)
+        gd = torch.randn(scene.P, dtype=torch.float32, device=dev, generator=g)
+        nb = min(args.steps, 20)
+        bev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(nb)]
+        ba.set_record(True)
+        for k in range(nb + 2):
+            reset()
+            flush.zero_()
+            one_step()
+            if k >= 2:
+                bev[k - 2][0].record(stream)
+            ba.backward(gp, gd)
+            if k >= 2:
+                bev[k - 2][1].record(stream)
+        torch.cuda.synchronize()
+        ba.set_record(False)
+        ba.sync()
+        bwd_ms = statistics.median(a.elapsed_time(b) for a, b in bev)
 
     if rank != 0:
         if dist:
@@ -1079,7 +1096,7 @@ def run_ours(args):
         errs = []
         err_iters = scene.iters if scene.N < LARGE_FRAMES else 1
         t_or = time.perf_counter()
-        want = oracle.gn_steps(scene, iters=err_iters)
+        want = oracle.gn_steps(scene, iters=err_iters, pixels=residual_pixels(args.workload))
         t_or = time.perf_counter() - t_or
         for it in range(err_iters):
             ba.step(1, scene.fixed)
@@ -1090,7 +1107,7 @@ def run_ours(args):
             errs.append({"iter": it + 1, "rot_rad": rot, "trans_rel": tr, "depth_rel": dep})
         err = errs
         if scene.N < LARGE_FRAMES:
-            runs, el = time_oracle(scene, budget_s=10.0)
+            runs, el = time_oracle(scene, budget_s=10.0, pixels=residual_pixels(args.workload))
             cv = runs * scene.iters / el
             sample = f"{runs} full runs of the workload ({scene.iters} GN iterations each)"
         else:  # the oracle iteration of the error check above
@@ -1115,7 +1132,7 @@ def run_ours(args):
         "gpu_launches": launches,
         "clocks": clk.summary(),
         "step_ms": {"min": min(step_ms), "median": statistics.median(step_ms), "max": max(step_ms)},
-        "adjoint": {"backward_ms_per_step": bwd_ms, "forward_ms_per_step": statistics.median(step_ms),
+        "adjoint": None if bwd_ms is None else {"backward_ms_per_step": bwd_ms, "forward_ms_per_step": statistics.median(step_ms),
                     "what": "ba_backward over the recorded ba_step (grad of targets and weights), median of "
                             f"{nb}, L2 flushed before each forward"},
     }

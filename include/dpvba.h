@@ -86,6 +86,13 @@ typedef struct {
                               estimated error left in the step is < 1e-7 of it */
   long long timeout_cycles;/* bound on any device-side wait (default 2e9 cycles)  */
   void* stream;            /* cudaStream_t for all work; NULL = legacy stream      */
+  int residual_pixels;     /* residual rows per edge: 1 = the patch centre (2-D,
+                              default); 9 = every pixel of the 3x3 patch (18-D,
+                              Eq. 3 summed over the patch): the targets passed to
+                              ba_set_graph* are then float32 [E,9,2] (row-major
+                              pixel order), the weights stay [E,2] and are shared
+                              by the edge's nine residuals; ba_backward returns
+                              BA_ERR_UNSUPPORTED                                   */
 } ba_options_t;
 
 /* Fill *opt with the defaults above. */

@@ -177,12 +177,12 @@ def gn(s, iters=None, fixed=None, opts=DEFAULT_OPTS, poses=None, patches=None, t
     return {"poses": poses, "patches": patches, "dxi": dxi, "dd": dd, "cost": cost}
 
 
-def gn_steps(s, iters=None, fixed=None, opts=DEFAULT_OPTS):
+def gn_steps(s, iters=None, fixed=None, opts=DEFAULT_OPTS, pixels=1):
     """States after each GN iteration: list of (poses, depths) of length iters."""
     iters = s.iters if iters is None else iters
     out, poses, patches = [], s.poses, s.patches
     for _ in range(iters):
-        r = gn(s, 1, fixed, opts, poses=poses, patches=patches)
+        r = gn(s, 1, fixed, opts, poses=poses, patches=patches, pixels=pixels)
         poses, patches = r["poses"], r["patches"]
         out.append((poses.copy(), patches[:, 2, 1, 1].copy()))
     return out

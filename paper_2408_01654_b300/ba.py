@@ -32,14 +32,15 @@ class DPVBA:
 
     def __init__(self, precision: str = "fp32", lambda_pose=1e-4, lambda_depth=1e-4, z_min=0.1, d_min=1e-3,
                  patches_per_group: int = 0, max_refine: int = 2, stream: torch.cuda.Stream | None = None,
-                 capture: bool = False):
+                 capture: bool = False, residual_pixels: int = 1):
         self._lib = capi.lib()
         self._h = ctypes.c_void_p()
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         opt = capi.default_options(
             precision=capi.BA_MIXED if precision == "mixed" else capi.BA_FP32, lambda_pose=lambda_pose,
             lambda_depth=lambda_depth, z_min=z_min, d_min=d_min, patches_per_group=patches_per_group,
-            max_refine=max_refine, stream=self.stream.cuda_stream)
+            max_refine=max_refine, stream=self.stream.cuda_stream, residual_pixels=residual_pixels)
+        self.residual_pixels = residual_pixels
         capi.check(None, self._lib.ba_create(ctypes.byref(self._h), ctypes.byref(opt)))
         self._keep = ()
         self.N = self.P = self.E = 0
@@ -55,6 +56,8 @@ class DPVBA:
             if t.dtype != dt or not t.is_contiguous() or not t.is_cuda:
                 raise TypeError(f"{name}: need a contiguous CUDA {dt} tensor")
         N, P, E = poses.shape[0], patches.shape[0], ii.shape[0]
+        if targets.numel() != 2 * self.residual_pixels * E:
+            raise ValueError("targets: [E,2], or [E,9,2] with residual_pixels=9")
         self._keep = (poses, patches, ii, jj, kk, targets, weights, intrinsics)
         self.N, self.P, self.E = N, P, E
         capi.check(self._h, self._lib.ba_set_graph(
@@ -72,6 +75,8 @@ class DPVBA:
                             ("intrinsics", intrinsics, torch.float32)):
             if t.dtype != dt or not t.is_contiguous() or not t.is_cuda:
                 raise TypeError(f"{name}: need a contiguous CUDA {dt} tensor")
+        if targets.numel() != 2 * self.residual_pixels * ii.shape[0]:
+            raise ValueError("targets: [E,2], or [E,9,2] with residual_pixels=9")
         offs = [np.ascontiguousarray(np.asarray(o, dtype=np.int64)) for o in (frame_off, patch_off, edge_off)]
         B = len(offs[0]) - 1
         self._keep = (poses, patches, ii, jj, kk, targets, weights, intrinsics, offs)

@@ -31,6 +31,7 @@ class BAOptions(ctypes.Structure):
         ("max_refine", ctypes.c_int),
         ("timeout_cycles", ctypes.c_longlong),
         ("stream", ctypes.c_void_p),
+        ("residual_pixels", ctypes.c_int),
     ]
 
 

@@ -415,6 +415,8 @@ extern "C" ba_status_t ba_backward(ba_handle_t h, const double* grad_poses, cons
   if (!h) return BA_ERR_INVALID_ARG;
   if (!h->have_graph || !h->tape_valid)
     return dpv_fail(h, BA_ERR_STATE, "ba_backward: no recorded ba_step (call ba_set_record(h, 1) before ba_step)");
+  if (h->opt.residual_pixels != 1)
+    return dpv_fail(h, BA_ERR_UNSUPPORTED, "ba_backward: the adjoint covers the patch-centre residual only");
   if ((reinterpret_cast<uintptr_t>(grad_targets) | reinterpret_cast<uintptr_t>(grad_weights)) & 7)
     return dpv_fail(h, BA_ERR_INVALID_ARG, "ba_backward: grad_targets/grad_weights must be 8-byte aligned");
   Workspace* ws = h->ws;

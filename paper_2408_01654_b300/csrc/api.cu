@@ -422,6 +422,7 @@ ba_status_t ba_default_options(ba_options_t* opt) {
   opt->max_refine = 2;
   opt->timeout_cycles = 2000000000LL;
   opt->stream = nullptr;
+  opt->residual_pixels = 1;
   return BA_OK;
 }
 
@@ -434,6 +435,7 @@ ba_status_t ba_create(ba_handle_t* out, const ba_options_t* opt) {
   else ba_default_options(&h->opt);
   if (h->opt.patches_per_group < 0 || h->opt.patches_per_group > DPV_GMAX ||
       (h->opt.precision != BA_FP32 && h->opt.precision != BA_MIXED) || h->opt.max_refine < 0 ||
+      (h->opt.residual_pixels != 1 && h->opt.residual_pixels != 9) ||
       h->opt.max_refine > 16) {
     delete h;
     return BA_ERR_INVALID_ARG;

@@ -57,9 +57,13 @@ __host__ __device__ constexpr int tri(int r, int c) { return r * (r + 1) / 2 + c
 static_assert(DPV_WMAX * DPV_WMAX + 8 * (DPV_WMAX * 21 + DPV_WMAX * 6) <= 4 * AS_WARPS * 32 * ROWF,
               "phase-2b tables exceed the staging space");
 
-size_t assemble_smem_bytes(int G) {
+// staged floats per patch: (xb0, xb1, d) of the centre, or the nine pixels'
+// xb0, then their xb1, then d (whole-patch residual)
+__host__ __device__ constexpr int pd_stride(int pix) { return pix == 1 ? 3 : 19; }
+
+size_t assemble_smem_bytes(int G, int pix) {
   return sizeof(float) * ((size_t)DPV_RMAX * NV * 2 + (size_t)DPV_RMAX * 21 + (size_t)G * EH_STRIDE + 2 * G +
-                          3 * G + (size_t)AS_WARPS * 32 * ROWF) +
+                          (size_t)pd_stride(pix) * G + (size_t)AS_WARPS * 32 * ROWF) +
          sizeof(int) * (DPV_RMAX + 2 * DPV_WMAX);
 }
 
@@ -70,6 +74,9 @@ __device__ __forceinline__ int tri_row(int t) {
   return a;
 }
 
+// PIX residual pixels per edge: 1 (the patch centre) or 9 (the whole patch,
+// targets [E,9,2], the edge's weights shared by its pixels)
+template <int PIX>
 __global__ void __launch_bounds__(AS_THREADS) k_assemble(
     int G, int P, const int* __restrict__ fdx, const int* __restrict__ gprob, const SysDesc* __restrict__ sysd,
     float lambda_d, float z_min, const int* __restrict__ gptr,
@@ -93,8 +100,9 @@ __global__ void __launch_bounds__(AS_THREADS) k_assemble(
   float* rpose = sm + DPV_RMAX * NV * 2;                    // [RMAX][21]
   float* Eh = rpose + DPV_RMAX * 21;                        // [G][EH_STRIDE]
   float* sc = Eh + (size_t)G * EH_STRIDE;                   // [G][2]  Ct^-1/2, w Ct^-1/2
-  float* pd = sc + 2 * G;                                   // [G][3]  xb0, xb1, d
-  float* rows = pd + 3 * G;                                 // [warps][32][ROWF]
+  constexpr int PDS = pd_stride(PIX);
+  float* pd = sc + 2 * G;                                   // [G][PDS]  xb0, xb1, d
+  float* rows = pd + PDS * G;                               // [warps][32][ROWF]
   int* rsl = reinterpret_cast<int*>(rows + AS_WARPS * 32 * ROWF);  // [RMAX] si | sj << 8
   int* wf = rsl + DPV_RMAX;                                 // [W] window frames
   int* fr = wf + DPV_WMAX;                                  // [W] unknown row in the group's system, -1 fixed
@@ -113,18 +121,35 @@ __global__ void __launch_bounds__(AS_THREADS) k_assemble(
     wf[q] = f;
     fr[q] = o < 0 ? -1 : o - sd.voff;
   }
-  for (int q = tid; q < G; q += AS_THREADS) {
-    const int k = g * G + q;
-    float x0 = 0.f, x1 = 0.f, d = 1.f;
-    if (k < P) {
-      const float* pk = patches + 27 * (size_t)k;
-      x0 = (pk[4] - K[2]) / K[0];
-      x1 = (pk[13] - K[3]) / K[1];
-      d = pk[22];
+  if (PIX == 1) {
+    for (int q = tid; q < G; q += AS_THREADS) {
+      const int k = g * G + q;
+      float x0 = 0.f, x1 = 0.f, d = 1.f;
+      if (k < P) {
+        const float* pk = patches + 27 * (size_t)k;
+        x0 = (pk[4] - K[2]) / K[0];
+        x1 = (pk[13] - K[3]) / K[1];
+        d = pk[22];
+      }
+      pd[3 * q] = x0;
+      pd[3 * q + 1] = x1;
+      pd[3 * q + 2] = d;
     }
-    pd[3 * q] = x0;
-    pd[3 * q + 1] = x1;
-    pd[3 * q + 2] = d;
+  } else {
+    for (int t = tid; t < G * 9; t += AS_THREADS) {
+      const int q = t / 9, px = t - 9 * q;
+      const int k = g * G + q;
+      float x0 = 0.f, x1 = 0.f, d = 1.f;
+      if (k < P) {
+        const float* pk = patches + 27 * (size_t)k;
+        x0 = (pk[px] - K[2]) / K[0];
+        x1 = (pk[9 + px] - K[3]) / K[1];
+        d = pk[22];
+      }
+      pd[PDS * q + px] = x0;
+      pd[PDS * q + 9 + px] = x1;
+      if (px == 4) pd[PDS * q + 18] = d;
+    }
   }
   __syncthreads();
   for (int r = tid; r < nruns; r += AS_THREADS) {
@@ -176,59 +201,73 @@ __global__ void __launch_bounds__(AS_THREADS) k_assemble(
       const int s = b + lane;
       const int nb = min(32, s1 - b);
       float* row = rw + lane * ROWF;
+      int kl = 0, e = 0;
+      float2 wt = make_float2(0.f, 0.f);
       if (s < s1) {
-        const int kl = dpv_slot_k(eslot[s]);
-        const int e = perm[s];
-        const float2 tg = *reinterpret_cast<const float2*>(targets + 2 * (size_t)e);
-        const float2 wt = *reinterpret_cast<const float2*>(weights + 2 * (size_t)e);
-        EdgeLin L;
-        dpv_edge_linearize(T, pd[3 * kl], pd[3 * kl + 1], pd[3 * kl + 2], tg.x, tg.y, K, z_min, self_run, L);
-        float Ei[6], Ej[6], Ce = 0.f, we = 0.f;
-        if (L.valid) {
-          const float wc[2] = {wt.x, wt.y};
-          cst += wc[0] * L.r[0] * L.r[0] + wc[1] * L.r[1] * L.r[1];
-          const float wJd0 = wc[0] * L.Jd[0], wJd1 = wc[1] * L.Jd[1];
-          Ce = wJd0 * L.Jd[0] + wJd1 * L.Jd[1];
-          we = wJd0 * L.r[0] + wJd1 * L.r[1];
+        kl = dpv_slot_k(eslot[s]);
+        e = perm[s];
+        wt = *reinterpret_cast<const float2*>(weights + 2 * (size_t)e);
+      }
+      float Ei[6], Ej[6], Ce = 0.f, we = 0.f;
 #pragma unroll
-          for (int m = 0; m < 6; ++m) {
-            Ei[m] = L.Ji[0][m] * wJd0 + L.Ji[1][m] * wJd1;
-            Ej[m] = L.Jj[0][m] * wJd0 + L.Jj[1][m] * wJd1;
-          }
-#pragma unroll
-          for (int c = 0; c < 2; ++c) {
-            const float sw = sqrtf(wc[c]);
+      for (int m = 0; m < 6; ++m) Ei[m] = Ej[m] = 0.f;
+      // one residual pixel at a time: each lane stages its edge's two rows,
+      // then the warp adds every staged edge's products to the run's blocks
+#pragma unroll 1
+      for (int px = 0; px < PIX; ++px) {
+        if (s < s1) {
+          const float2 tg = *reinterpret_cast<const float2*>(targets + 2 * ((size_t)e * PIX + px));
+          const float xb0 = PIX == 1 ? pd[3 * kl] : pd[PDS * kl + px];
+          const float xb1 = PIX == 1 ? pd[3 * kl + 1] : pd[PDS * kl + 9 + px];
+          const float dk = PIX == 1 ? pd[3 * kl + 2] : pd[PDS * kl + 18];
+          EdgeLin L;
+          dpv_edge_linearize(T, xb0, xb1, dk, tg.x, tg.y, K, z_min, self_run, L);
+          if (L.valid) {
+            const float wc[2] = {wt.x, wt.y};
+            cst += wc[0] * L.r[0] * L.r[0] + wc[1] * L.r[1] * L.r[1];
+            const float wJd0 = wc[0] * L.Jd[0], wJd1 = wc[1] * L.Jd[1];
+            Ce += wJd0 * L.Jd[0] + wJd1 * L.Jd[1];
+            we += wJd0 * L.r[0] + wJd1 * L.r[1];
 #pragma unroll
             for (int m = 0; m < 6; ++m) {
-              row[13 * c + m] = sw * L.Ji[c][m];
-              row[13 * c + 6 + m] = sw * L.Jj[c][m];
+              Ei[m] += L.Ji[0][m] * wJd0 + L.Ji[1][m] * wJd1;
+              Ej[m] += L.Jj[0][m] * wJd0 + L.Jj[1][m] * wJd1;
             }
-            row[13 * c + 12] = sw * L.r[c];
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+              const float sw = sqrtf(wc[c]);
+#pragma unroll
+              for (int m = 0; m < 6; ++m) {
+                row[13 * c + m] = sw * L.Ji[c][m];
+                row[13 * c + 6 + m] = sw * L.Jj[c][m];
+              }
+              row[13 * c + 12] = sw * L.r[c];
+            }
+          } else {
+#pragma unroll
+            for (int m = 0; m < 26; ++m) row[m] = 0.f;
           }
-        } else {
-#pragma unroll
-          for (int m = 0; m < 6; ++m) Ei[m] = Ej[m] = 0.f;
-#pragma unroll
-          for (int m = 0; m < 26; ++m) row[m] = 0.f;
         }
+        __syncwarp();
+        for (int q = 0; q < nb; ++q) {
+          const float* re = rw + q * ROWF;
+#pragma unroll
+          for (int t = 0; t < 3; ++t) {
+            if (lane + 32 * t < NV) {
+              ks_fma(acc[t], re[pa[t]], re[pb[t]]);
+              ks_fma(acc[t], re[13 + pa[t]], re[13 + pb[t]]);
+            }
+          }
+        }
+        __syncwarp();
+      }
+      if (s < s1) {
         float4* pt = pterm + 4 * (size_t)pmpos[s];
         pt[0] = make_float4(Ei[0], Ei[1], Ei[2], Ei[3]);
         pt[1] = make_float4(Ei[4], Ei[5], Ej[0], Ej[1]);
         pt[2] = make_float4(Ej[2], Ej[3], Ej[4], Ej[5]);
         pt[3] = make_float4(Ce, we, __int_as_float(si | (sj << 8)), 0.f);
       }
-      __syncwarp();
-      for (int e = 0; e < nb; ++e) {
-        const float* re = rw + e * ROWF;
-#pragma unroll
-        for (int t = 0; t < 3; ++t) {
-          if (lane + 32 * t < NV) {
-            ks_fma(acc[t], re[pa[t]], re[pb[t]]);
-            ks_fma(acc[t], re[13 + pa[t]], re[13 + pb[t]]);
-          }
-        }
-      }
-      __syncwarp();
     }
 #pragma unroll
     for (int t = 0; t < 3; ++t) {
@@ -462,8 +501,10 @@ ba_status_t upload_tables(ba_handle_t h) {
   for (int a = 0; a < 6; ++a, ++q) { pa[q] = 6 + a; pb[q] = 12; }        // vj
   DPV_CUDA(h, cudaMemcpyToSymbol(c_pa, pa, NV));
   DPV_CUDA(h, cudaMemcpyToSymbol(c_pb, pb, NV));
-  DPV_CUDA(h, cudaFuncSetAttribute(k_assemble, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)assemble_smem_bytes(DPV_GMAX)));
+  DPV_CUDA(h, cudaFuncSetAttribute(k_assemble<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)assemble_smem_bytes(DPV_GMAX, 1)));
+  DPV_CUDA(h, cudaFuncSetAttribute(k_assemble<9>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)assemble_smem_bytes(DPV_GMAX, 9)));
   g_tables_ready = true;
   return BA_OK;
 }
@@ -504,7 +545,8 @@ ba_status_t assemble_impl(ba_handle_t h, int it, const double* v_ext, const floa
   }
   double* cost = it < 0 ? nullptr : ws->cost + (it < ws->cost_cap ? it : ws->cost_cap - 1);
   dpv_prof_begin(h, BA_KERNEL_ASSEMBLE);
-  k_assemble<<<h->ngroups, AS_THREADS, assemble_smem_bytes(h->G), h->stream>>>(
+  auto kern = h->opt.residual_pixels == 9 ? k_assemble<9> : k_assemble<1>;
+  kern<<<h->ngroups, AS_THREADS, assemble_smem_bytes(h->G, h->opt.residual_pixels), h->stream>>>(
       h->G, h->P, ws->fdx.p, ws->gprob.p, ws->sysd.p, h->opt.lambda_depth, h->opt.z_min, ws->gptr.p, ws->grun.p,
       ws->gnr.p, ws->eslot.p,
       ws->perm.p, ws->pmpos.p, ws->pptr.p, ws->win.p, ws->wlen.p, ws->posef.p, h->patches, h->targets, h->weights,
