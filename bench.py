@@ -167,14 +167,15 @@ def roofline(dom, prof, steps, bytes_fn, factor_ns, workload):
             "per_class_ms_per_step": per_class}
 
 
-def algorithmic_bytes(kind, N, P, E, n):
+def algorithmic_bytes(kind, N, P, E, n, pixels=1):
     """Bytes a kernel class must move per launch at minimum (inputs read once,
     outputs written once)."""
     tri = n * (n + 1) // 2
     if kind == "assemble":
-        # edges: ii, jj, kk, target, weight (28 B); patches: centre + depth (12 B);
-        # poses (56 B); outputs: lower triangle of S, y, Ct and w
-        return 28 * E + 12 * P + 56 * N + 4 * tri + 4 * n + 8 * P
+        # edges: ii, jj, kk, weight (20 B) and a target per residual pixel (8 B);
+        # patches: the residual pixels + depth; poses (56 B); outputs: lower
+        # triangle of S, y, Ct and w
+        return (20 + 8 * pixels) * E + (8 * pixels + 4) * P + 56 * N + 4 * tri + 4 * n + 8 * P
     if kind == "backsub":
         # per edge the two 6-vectors J^T W Jd (48 B); per patch Ct, w, the depth
         # (12 B) and the nine updated depths (36 B); the pose step
@@ -1082,7 +1083,8 @@ def run_ours(args):
     inf = ba.info()
     n = inf["n"]
     dom = max((k for k in prof if prof[k][1] > 0), key=lambda k: prof[k][0])
-    roof = roofline(dom, prof, args.steps, lambda k: algorithmic_bytes(k, scene.N, scene.P, scene.E, n), [n],
+    roof = roofline(dom, prof, args.steps, lambda k: algorithmic_bytes(k, scene.N, scene.P, scene.E, n,
+                                                                 residual_pixels(args.workload)), [n],
                     args.workload)
 
     # ---- error against the oracle and the CPU baseline --------------------
