@@ -9,7 +9,9 @@ Each LM step therefore agrees to ~1e-9 relative; accepted iterations move the
 costs by far more, so the cost curves agree to 1e-6 relative and the
 accept/reject decisions agree wherever the cost changed by more than that
 (at convergence both sides reject steps whose gain is rounding noise, in
-either order).  The final similarities agree to 1e-7 (their matrices).
+either order).  The final similarities agree to 1e-7 (their matrices,
+relative to the largest entry: the solvers stop once the error left in a step
+is below 1e-7 of it).
 """
 import numpy as np
 import pytest
@@ -54,7 +56,9 @@ def compare(got, want, tol=1e-7):
     assert np.allclose(cost, want["cost"], rtol=1e-6, atol=1e-12), (cost, want["cost"])
     decisive = np.abs(np.diff(want["cost"])) > 1e-6 * want["cost"][1:]
     assert np.array_equal(acc[decisive], want["accepted"][decisive])
-    err = max(np.abs(as_matrix(a) - as_matrix(b)).max() for a, b in zip(S, want["S"]))
+    # relative to the matrix's largest entry (translations reach 20 m here)
+    err = max(np.abs(as_matrix(a) - as_matrix(b)).max() / max(1.0, np.abs(as_matrix(b)).max())
+              for a, b in zip(S, want["S"]))
     assert err < tol, err
     assert np.array_equal(S[0], want["S"][0])
 
