@@ -6,8 +6,8 @@
 // Every iteration runs on the device with no host round trip:
 //   k_pgo_lin     one warp per factor: the residual and its 7x14 Jacobian by
 //                 central differences in the right-perturbation coordinates
-//                 S <- S Exp(d) of both similarities (lanes 0-13 one column
-//                 each, lane 14 the residual), then J^T J and -J^T r
+//                 S <- S Exp(d) of both similarities (lanes 0-27 one probe
+//                 each, lane 28 the residual), then J^T J and -J^T r
 //                 accumulated into the tiled FP64 lower triangle and the
 //                 right-hand side of the library's dense pose system;
 //   k_pgo_damp    H + lambda diag(H), identity on the padding;
@@ -198,13 +198,39 @@ __device__ __forceinline__ Sim pg_left(const double* dS, int loop) {
   return loop ? m : pg_inv(m);
 }
 
+// Exp of x times the m-th tangent axis (the central-difference probes):
+// rho_m gives the translation x e_m exactly; phi_m the rotation by x about
+// axis m (sin(x/2), cos(x/2) by their series, |x| << 1e-4); sigma the scale
+// e^x.  Exp(-x e_m) is the inverse of Exp(x e_m).
+__device__ __forceinline__ Sim pg_exp_axis(int m, double x) {
+  Sim E;
+  E.t[0] = E.t[1] = E.t[2] = 0.0;
+  E.q[0] = E.q[1] = E.q[2] = 0.0;
+  E.q[3] = 1.0;
+  E.s = 1.0;
+  if (m < 3) {
+    E.t[m] = x;
+  } else if (m < 6) {
+    const double x2 = x * x;
+    E.q[m - 3] = x * (0.5 - x2 / 48.0);
+    E.q[3] = 1.0 - x2 / 8.0;
+  } else {
+    E.s = exp(x);
+  }
+  return E;
+}
+
 __global__ void __launch_bounds__(32 * PG_WARPS) k_pgo_lin(int N, int F, const double* __restrict__ S,
                                                              const double* __restrict__ dS,
                                                              const int* __restrict__ fa, const int* __restrict__ fb,
                                                              const int* __restrict__ loop, double h, double* Sys,
                                                              int TS, double* y, int* status) {
-  __shared__ double Jsh[PG_WARPS][15][8];  // columns 0-13 of J (7 rows each), then the residual
+  // residuals of the 28 probes (column c = l / 2 of J, sign + for even l),
+  // then the unperturbed one; then the columns of J and the residual
+  __shared__ double Rsh[PG_WARPS][29][8];
+  __shared__ double Jsh[PG_WARPS][15][8];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  double (*R)[8] = Rsh[wid];
   double (*J)[8] = Jsh[wid];
   for (int f = blockIdx.x * PG_WARPS + wid; f < F; f += gridDim.x * PG_WARPS) {
     const int a = fa[f], b = fb[f];
@@ -212,33 +238,29 @@ __global__ void __launch_bounds__(32 * PG_WARPS) k_pgo_lin(int N, int F, const d
       if (lane == 0) dpv_set_status(status, DST_BAD_INDEX);
       continue;
     }
-    if (lane < 15) {
+    if (lane < 29) {
+      // r = log(L Sa^-1 Sb) with L = dS^-1 (Eq. 5) or dS (Eq. 6); with
+      // M = Sa^-1 Sb the probes are log(L M E) for Sb <- Sb E and
+      // log(L E^-1 M) for Sa <- Sa E
       const Sim L = pg_left(dS + 8 * (size_t)f, loop[f]);
-      Sim Sa = pg_load(S + 8 * (size_t)a), Sb = pg_load(S + 8 * (size_t)b);
-      if (lane == 14) {
-        double r[7];
-        pg_residual(L, Sa, Sb, r);
-#pragma unroll
-        for (int k = 0; k < 7; ++k) J[14][k] = r[k];
+      const Sim M = pg_mul(pg_inv(pg_load(S + 8 * (size_t)a)), pg_load(S + 8 * (size_t)b));
+      double r[7];
+      if (lane == 28) {
+        pg_log(pg_mul(L, M), r);
       } else {
-        const int side = lane / 7, m = lane - 7 * side;
-        double d[7] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0}, rp[7], rm[7];
-        const Sim base = side ? Sb : Sa;
-        d[m] = h;
-        const Sim P = pg_mul(base, pg_exp(d));
-        d[m] = -h;
-        const Sim M = pg_mul(base, pg_exp(d));
-        if (side) {
-          pg_residual(L, Sa, P, rp);
-          pg_residual(L, Sa, M, rm);
-        } else {
-          pg_residual(L, P, Sb, rp);
-          pg_residual(L, M, Sb, rm);
-        }
-        const double ih = 0.5 / h;
-#pragma unroll
-        for (int k = 0; k < 7; ++k) J[lane][k] = (rp[k] - rm[k]) * ih;
+        const int c = lane >> 1, side = c / 7, m = c - 7 * side;
+        const double x = (lane & 1) ? -h : h;
+        if (side) pg_log(pg_mul(L, pg_mul(M, pg_exp_axis(m, x))), r);
+        else pg_log(pg_mul(L, pg_mul(pg_exp_axis(m, -x), M)), r);
       }
+#pragma unroll
+      for (int k = 0; k < 7; ++k) R[lane][k] = r[k];
+    }
+    __syncwarp();
+    if (lane < 15) {
+      const double ih = 0.5 / h;
+#pragma unroll
+      for (int k = 0; k < 7; ++k) J[lane][k] = lane == 14 ? R[28][k] : (R[2 * lane][k] - R[2 * lane + 1][k]) * ih;
     }
     __syncwarp();
     // unknowns: frame i >= 1 at 7 (i - 1); frame 0 is held
@@ -257,12 +279,12 @@ __global__ void __launch_bounds__(32 * PG_WARPS) k_pgo_lin(int N, int F, const d
       const int u = e / 14, v = e - 14 * (e / 14);
       const int ou = u < 7 ? oa : ob, ov = v < 7 ? oa : ob;
       if (ou < 0 || ov < 0) continue;
-      const int R = ou + (u < 7 ? u : u - 7), C = ov + (v < 7 ? v : v - 7);
-      if (R < C) continue;  // lower triangle only
+      const int Rr = ou + (u < 7 ? u : u - 7), Cc = ov + (v < 7 ? v : v - 7);
+      if (Rr < Cc) continue;  // lower triangle only
       double hv = 0.0;
 #pragma unroll
       for (int k = 0; k < 7; ++k) hv += J[u][k] * J[v][k];
-      dpv_red_add(Sys + dpv_s_index(R, C, TS), hv);
+      dpv_red_add(Sys + dpv_s_index(Rr, Cc, TS), hv);
     }
     __syncwarp();
   }
