@@ -88,6 +88,7 @@ __global__ void __launch_bounds__(AS_THREADS) k_assemble(
     float4* __restrict__ pterm, double* __restrict__ S, double* __restrict__ y, float* __restrict__ Ct_out,
     float* __restrict__ wk_out, double* __restrict__ cost, const float* __restrict__ w_ext, int* status) {
   extern __shared__ float sm[];
+  dpv_pdl_enter();
   if (dpv_status(status)) return;
   const int g = blockIdx.x;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
@@ -460,6 +461,7 @@ __global__ void __launch_bounds__(AS_THREADS) k_assemble(
 __global__ void k_init_system(double* __restrict__ S, size_t nS, double* __restrict__ y, int nv,
                               const double* __restrict__ y_init, const double* __restrict__ poses, int N,
                               float* __restrict__ posef, const int* status) {
+  dpv_pdl_enter();
   if (dpv_status(status)) return;
   const size_t stride = (size_t)gridDim.x * blockDim.x;
   const size_t gid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -472,6 +474,7 @@ __global__ void k_init_system(double* __restrict__ S, size_t nS, double* __restr
 // lambda_p on the free diagonal of every system, 1 on its padding diagonal (blockIdx.y = system)
 __global__ void k_init_diag(double* __restrict__ S, const SysDesc* __restrict__ sysd, float lambda_p,
                             const int* status) {
+  dpv_pdl_enter();
   if (dpv_status(status)) return;
   const SysDesc sd = sysd[blockIdx.y];
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
@@ -533,24 +536,26 @@ ba_status_t assemble_impl(ba_handle_t h, int it, const double* v_ext, const floa
   const size_t nS = (size_t)h->nS;
   if (!skip_init) {
     dpv_prof_begin(h, BA_KERNEL_INIT);
-    k_init_system<<<2 * h->num_sms, 256, 0, h->stream>>>(ws->S.p, nS, ws->y.p, h->n_pad, v_ext, h->poses, h->N,
-                                                          ws->posef.p, ws->status);
+    DPV_CUDA(h, dpv_launch_pdl(k_init_system, dim3(2 * h->num_sms), dim3(256), 0, h->stream, ws->S.p, nS, ws->y.p,
+                               h->n_pad, v_ext, (const double*)h->poses, h->N, ws->posef.p,
+                               (const int*)ws->status));
     ++h->launches;
     int maxpad = 0;
     for (const SysDesc& d : h->sys) maxpad = std::max(maxpad, d.n_pad);
-    k_init_diag<<<dim3((maxpad + 255) / 256, h->nprob), 256, 0, h->stream>>>(ws->S.p, ws->sysd.p,
-                                                                              h->opt.lambda_pose, ws->status);
+    DPV_CUDA(h, dpv_launch_pdl(k_init_diag, dim3((maxpad + 255) / 256, h->nprob), dim3(256), 0, h->stream, ws->S.p,
+                               (const SysDesc*)ws->sysd.p, h->opt.lambda_pose, (const int*)ws->status));
     ++h->launches;
     dpv_prof_end(h);
   }
   double* cost = it < 0 ? nullptr : ws->cost + (it < ws->cost_cap ? it : ws->cost_cap - 1);
   dpv_prof_begin(h, BA_KERNEL_ASSEMBLE);
   auto kern = h->opt.residual_pixels == 9 ? k_assemble<9> : k_assemble<1>;
-  kern<<<h->ngroups, AS_THREADS, assemble_smem_bytes(h->G, h->opt.residual_pixels), h->stream>>>(
-      h->G, h->P, ws->fdx.p, ws->gprob.p, ws->sysd.p, h->opt.lambda_depth, h->opt.z_min, ws->gptr.p, ws->grun.p,
-      ws->gnr.p, ws->eslot.p,
-      ws->perm.p, ws->pmpos.p, ws->pptr.p, ws->win.p, ws->wlen.p, ws->posef.p, h->patches, h->targets, h->weights,
-      ws->intr, ws->pterm.p, ws->S.p, ws->y.p, ws->Ct.p, ws->wk.p, cost, w_ext, ws->status);
+  DPV_CUDA(h, dpv_launch_pdl(kern, dim3(h->ngroups), dim3(AS_THREADS),
+                             assemble_smem_bytes(h->G, h->opt.residual_pixels), h->stream, h->G, h->P, ws->fdx.p,
+                             ws->gprob.p, ws->sysd.p, h->opt.lambda_depth, h->opt.z_min, ws->gptr.p, ws->grun.p,
+                             ws->gnr.p, ws->eslot.p, ws->perm.p, ws->pmpos.p, ws->pptr.p, ws->win.p, ws->wlen.p,
+                             ws->posef.p, h->patches, h->targets, h->weights, ws->intr, ws->pterm.p, ws->S.p,
+                             ws->y.p, ws->Ct.p, ws->wk.p, cost, w_ext, ws->status));
   ++h->launches;
   dpv_prof_end(h);
   DPV_CUDA(h, cudaGetLastError());

@@ -281,6 +281,33 @@ ba_status_t dpv_export_S(ba_handle_t h, double* dst);
 // device helpers
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void dpv_set_status(int* status, int code) { atomicCAS(status, 0, code); }
+
+// Programmatic dependent launch between the kernels of a step: a kernel
+// launched by dpv_launch_pdl may become resident while its predecessor in the
+// stream still runs; its first statement, dpv_pdl_enter(), waits until the
+// predecessor has completed and its writes are visible (a no-op when the
+// kernel was launched without the attribute), then lets its own successor
+// launch.  Only the launch latency overlaps; no data is read early.
+__device__ __forceinline__ void dpv_pdl_enter() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+cudaError_t dpv_launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                           Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
 __device__ __forceinline__ int dpv_status(const int* status) { return *(volatile const int*)status; }
 
 // Tiled lower-triangular storage of the pose system: tile (ti, tj), ti >= tj,

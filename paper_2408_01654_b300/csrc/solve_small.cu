@@ -77,6 +77,7 @@ __global__ void __launch_bounds__(small_threads(NQ)) k_solve_small(
   __shared__ double xs64[NP], rs64[NP];  // FP64 residual: x and S x
   __shared__ float red[2 * NWARP];
   __shared__ int bad;
+  dpv_pdl_enter();
   if (dpv_status(status)) return;
   int n = n_direct;
   double* S = S_;
@@ -445,9 +446,9 @@ ba_status_t launch_small(ba_handle_t h, cudaStream_t st, int count, const int* l
     DPV_CUDA(h, cudaFuncSetAttribute(k_solve_small<NQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     attr = true;
   }
-  k_solve_small<NQ><<<count, small_threads(NQ), smem, st>>>(
-      h->ws->sysd.p, list, 0, h->ws->S.p, h->ws->y.p, h->ws->dx.p, h->ws->tmpv.p, refine32, refine64,
-      h->opt.lambda_pose, reset, h->ws->status);
+  DPV_CUDA(h, dpv_launch_pdl(k_solve_small<NQ>, dim3(count), dim3(small_threads(NQ)), smem, st, h->ws->sysd.p, list,
+                             0, h->ws->S.p, h->ws->y.p, h->ws->dx.p, h->ws->tmpv.p, refine32, refine64,
+                             h->opt.lambda_pose, reset, h->ws->status));
   ++h->launches;
   DPV_CUDA(h, cudaGetLastError());
   return BA_OK;

@@ -29,6 +29,7 @@ __global__ void __launch_bounds__(BS_THREADS) k_backsub(
     const float* __restrict__ Ct, const float* __restrict__ wk, float* __restrict__ patches,
     float* __restrict__ dd_out, int N, int retract, const double* __restrict__ dx, double* __restrict__ poses,
     float* __restrict__ posef, int write_depth, const int* status) {
+  dpv_pdl_enter();
   if (dpv_status(status)) return;
   const int lane = threadIdx.x & 31;
   if (retract && threadIdx.x == 0 && (int)blockIdx.x < N) {
@@ -89,9 +90,10 @@ unsigned backsub_grid(ba_handle_t h, int retract) {
 // poses and their rows of the linearisation table.
 ba_status_t dpv_backsub(ba_handle_t h, int retract) {
   Workspace* ws = h->ws;
-  k_backsub<<<backsub_grid(h, retract), BS_THREADS, 0, h->stream>>>(
-      h->P, h->G, ws->fdx.p, h->opt.d_min, ws->pptr.p, ws->pterm.p, ws->win.p, ws->tmpv.p, ws->Ct.p, ws->wk.p,
-      h->patches, ws->dd.p, h->N, retract, ws->dx.p, h->poses, ws->posef.p, 1, ws->status);
+  DPV_CUDA(h, dpv_launch_pdl(k_backsub, dim3(backsub_grid(h, retract)), dim3(BS_THREADS), 0, h->stream, h->P, h->G,
+                             ws->fdx.p, h->opt.d_min, ws->pptr.p, ws->pterm.p, ws->win.p, ws->tmpv.p, ws->Ct.p,
+                             ws->wk.p, h->patches, ws->dd.p, h->N, retract, ws->dx.p, h->poses, ws->posef.p, 1,
+                             ws->status));
   ++h->launches;
   DPV_CUDA(h, cudaGetLastError());
   return BA_OK;
