@@ -418,10 +418,11 @@ DPVBA_API ba_status_t ba_patch_correlation(ba_handle_t h, int Nf, int H, int W, 
  * endpoint out of range, or fa == fb, sets the device status (ba_sync returns
  * BA_ERR_INVALID_ARG); a damped system that is not positive definite (a
  * similarity no factor touches) makes ba_sync return BA_ERR_NOT_SPD.  The
- * work is queued on the handle's stream with no host round trip; the call
- * borrows the handle's pose-system buffers (the next ba_step lays its own
- * system out again) and keeps 8 (3 + 8N + F) bytes of scratch.  Needs no
- * bound graph. */
+ * work is queued on the handle's stream with no host round trip inside the
+ * iterations (the call itself uploads the system layout from the host, so it
+ * is not captured into a CUDA graph); it borrows the handle's pose-system
+ * buffers (the next ba_step lays its own system out again) and keeps
+ * 8 (3 + 8N + F) bytes of scratch.  Needs no bound graph. */
 DPVBA_API ba_status_t ba_pgo_lm(ba_handle_t h, int N, int F, double* S, const double* dS, const int* fa,
                                 const int* fb, const int* loop, int iters, double lambda0, double fd_step,
                                 double* cost, int* accepted);
