@@ -457,17 +457,29 @@ __global__ void __launch_bounds__(AS_THREADS) k_assemble(
 }
 
 // S <- 0, y <- 0 (or the given right-hand side), and the per-pose table for
-// this iteration (R and the camera centre as double-float pairs).
+// this iteration (R and the camera centre as double-float pairs).  With
+// diag_pad > 0 (one system held in one tile of edge diag_pad) the diagonal is
+// written here as well: lambda_p on the first diag_n entries, 1 on the
+// padding; otherwise k_init_diag follows.
 __global__ void k_init_system(double* __restrict__ S, size_t nS, double* __restrict__ y, int nv,
                               const double* __restrict__ y_init, const double* __restrict__ poses, int N,
-                              float* __restrict__ posef, const int* status) {
+                              float* __restrict__ posef, int diag_n, int diag_pad, float lambda_p,
+                              const int* status) {
   dpv_pdl_enter();
   if (dpv_status(status)) return;
   const size_t stride = (size_t)gridDim.x * blockDim.x;
   const size_t gid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (gid < (size_t)N) dpv_pose_table_row(poses + 7 * gid, posef + DPV_POSE_ROW * gid);
   double2* S2 = reinterpret_cast<double2*>(S);
-  for (size_t q = gid; q < nS / 2; q += stride) S2[q] = make_double2(0.0, 0.0);
+  const size_t dstep = (size_t)diag_pad + 1;
+  for (size_t q = gid; q < nS / 2; q += stride) {
+    double2 v = make_double2(0.0, 0.0);
+    if (diag_pad > 0) {
+      if ((2 * q) % dstep == 0) v.x = (2 * q) / dstep < (size_t)diag_n ? (double)lambda_p : 1.0;
+      if ((2 * q + 1) % dstep == 0) v.y = (2 * q + 1) / dstep < (size_t)diag_n ? (double)lambda_p : 1.0;
+    }
+    S2[q] = v;
+  }
   for (size_t q = gid; q < (size_t)nv; q += stride) y[q] = y_init ? y_init[q] : 0.0;
 }
 
@@ -536,15 +548,20 @@ ba_status_t assemble_impl(ba_handle_t h, int it, const double* v_ext, const floa
   const size_t nS = (size_t)h->nS;
   if (!skip_init) {
     dpv_prof_begin(h, BA_KERNEL_INIT);
+    // one system in one tile: its diagonal is written by the same launch
+    const bool one_tile = h->sys.size() == 1 && h->sys[0].T == 1 && h->sys[0].soff == 0;
     DPV_CUDA(h, dpv_launch_pdl(k_init_system, dim3(2 * h->num_sms), dim3(256), 0, h->stream, ws->S.p, nS, ws->y.p,
                                h->n_pad, v_ext, (const double*)h->poses, h->N, ws->posef.p,
+                               one_tile ? h->sys[0].n : 0, one_tile ? h->sys[0].n_pad : 0, h->opt.lambda_pose,
                                (const int*)ws->status));
     ++h->launches;
-    int maxpad = 0;
-    for (const SysDesc& d : h->sys) maxpad = std::max(maxpad, d.n_pad);
-    DPV_CUDA(h, dpv_launch_pdl(k_init_diag, dim3((maxpad + 255) / 256, h->nprob), dim3(256), 0, h->stream, ws->S.p,
-                               (const SysDesc*)ws->sysd.p, h->opt.lambda_pose, (const int*)ws->status));
-    ++h->launches;
+    if (!one_tile) {
+      int maxpad = 0;
+      for (const SysDesc& d : h->sys) maxpad = std::max(maxpad, d.n_pad);
+      DPV_CUDA(h, dpv_launch_pdl(k_init_diag, dim3((maxpad + 255) / 256, h->nprob), dim3(256), 0, h->stream,
+                                 ws->S.p, (const SysDesc*)ws->sysd.p, h->opt.lambda_pose, (const int*)ws->status));
+      ++h->launches;
+    }
     dpv_prof_end(h);
   }
   double* cost = it < 0 ? nullptr : ws->cost + (it < ws->cost_cap ? it : ws->cost_cap - 1);
