@@ -188,7 +188,7 @@ def gn_steps(s, iters=None, fixed=None, opts=DEFAULT_OPTS, pixels=1):
     return out
 
 
-def grad_fwd(s, a, b, kind, index, iters=None, fixed=None, opts=DEFAULT_OPTS):
+def grad_fwd(s, a, b, kind, index, iters=None, fixed=None, opts=DEFAULT_OPTS, pixels=1):
     """d/d(input coordinate) of <a, poses_final> + <b, depths_final>, one value
     per coordinate; kind 0 = target, 1 = weight (index into the flat [E,2]),
     2 = initial inverse depth (index = patch), 3 = left perturbation
@@ -200,9 +200,9 @@ def grad_fwd(s, a, b, kind, index, iters=None, fixed=None, opts=DEFAULT_OPTS):
     index = np.ascontiguousarray(index, dtype=np.int64)
     out = np.empty(len(kind))
     ii, jj, kk = _i(s.ii), _i(s.jj), _i(s.kk)
-    _check(lib().oracle_grad_fwd(
+    _check(lib().oracle_grad_fwd_px(
         s.N, s.P, len(s.kk), _p(_d(s.poses)), _p(_d(s.patches)), _p(ii), _p(jj), _p(kk), _p(_d(s.targets)),
-        _p(_d(s.weights)), _p(_d(s.intrinsics)), iters, fixed, _p(_d(opts)), _p(_d(a)), _p(_d(b)),
+        _p(_d(s.weights)), _p(_d(s.intrinsics)), iters, fixed, _p(_d(opts)), pixels, _p(_d(a)), _p(_d(b)),
         len(kind), _p(kind), _p(index), _p(out)))
     return out
 

@@ -551,19 +551,20 @@ int oracle_gn(int N, int P, int E, double* poses, double* patches, const int* ii
 // T <- Exp(xi) T, xi = (rho, phi), of initial pose a = index[c] / 6, whose
 // first-order change is dt = rho + phi x t, dq = (phi/2, 0) (x) q.
 // One dual-number GN run per coordinate.
-int oracle_grad_fwd(int N, int P, int E, const double* poses, const double* patches, const int* ii,
-                    const int* jj, const int* kk, const double* targets, const double* weights,
-                    const double* intr, int iters, int fixed, const double* opts4, const double* a,
-                    const double* b, int ncoord, const int* kind, const long long* index, double* out) {
-  if (check_indices(N, P, E, ii, jj, kk)) return 1;
+// pix residual pixels per edge (1 or 9; targets [E,pix,2], kind 0 indexes them)
+int oracle_grad_fwd_px(int N, int P, int E, const double* poses, const double* patches, const int* ii,
+                       const int* jj, const int* kk, const double* targets, const double* weights,
+                       const double* intr, int iters, int fixed, const double* opts4, int pix, const double* a,
+                       const double* b, int ncoord, const int* kind, const long long* index, double* out) {
+  if (check_indices(N, P, E, ii, jj, kk) || (pix != 1 && pix != 9)) return 1;
   const Opts o{opts4[0], opts4[1], opts4[2], opts4[3]};
   for (int c = 0; c < ncoord; ++c) {
-    const long long lim = kind[c] <= 1 ? 2LL * E : (kind[c] == 2 ? (long long)P : 6LL * N);
+    const long long lim = kind[c] == 0 ? 2LL * E * pix : kind[c] == 1 ? 2LL * E : (kind[c] == 2 ? (long long)P : 6LL * N);
     if (kind[c] < 0 || kind[c] > 3 || index[c] < 0 || index[c] >= lim) return 1;
   }
   for (int c = 0; c < ncoord; ++c) {
     Problem<Dual> pb;
-    load_problem(pb, N, P, E, poses, patches, ii, jj, kk, targets, weights, intr);
+    load_problem(pb, N, P, E, poses, patches, ii, jj, kk, targets, weights, intr, pix);
     if (kind[c] == 0) {
       pb.tgt[index[c]].d = 1.0;
     } else if (kind[c] == 1) {
@@ -599,6 +600,14 @@ int oracle_grad_fwd(int N, int P, int E, const double* poses, const double* patc
     out[c] = g;
   }
   return 0;
+}
+
+int oracle_grad_fwd(int N, int P, int E, const double* poses, const double* patches, const int* ii,
+                    const int* jj, const int* kk, const double* targets, const double* weights,
+                    const double* intr, int iters, int fixed, const double* opts4, const double* a,
+                    const double* b, int ncoord, const int* kind, const long long* index, double* out) {
+  return oracle_grad_fwd_px(N, P, E, poses, patches, ii, jj, kk, targets, weights, intr, iters, fixed, opts4, 1, a,
+                            b, ncoord, kind, index, out);
 }
 
 // Proximity loop edges (Sec. 3.2 "Proximity Loop Closure", "Constructing the

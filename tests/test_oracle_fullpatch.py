@@ -138,3 +138,33 @@ def test_noise_free_whole_patch_targets_are_reached():
     assert rot < 1e-6 and tr < 1e-6, (rot, tr)
     assert np.abs(r["patches"][:, 2, 1, 1] / s.depth_gt - 1).max() < 1e-5
     assert r["cost"][-1] < 1e-6 * r["cost"][0]
+
+
+def test_dual_gradient_matches_central_fd():
+    # exact derivatives of the unrolled whole-patch iterations with respect to
+    # single pixel targets and edge weights, against central differences
+    s = small_graph(seed=3, N=6, M=8)
+    s.iters = 2
+    s.targets = noisy_targets(s, 2)
+    rng = np.random.default_rng(0)
+    a = rng.normal(size=(s.N, 7))
+    b = rng.normal(size=s.P)
+
+    def L(targets=None, weights=None):
+        r = oracle.gn(s, targets=targets, weights=weights, pixels=9)
+        return (a * r["poses"]).sum() + (b * r["patches"][:, 2, 1, 1]).sum()
+
+    kind = np.r_[np.zeros(10, int), np.ones(6, int)]
+    index = np.r_[rng.choice(18 * s.E, 10, replace=False), rng.choice(2 * s.E, 6, replace=False)]
+    g = oracle.grad_fwd(s, a, b, kind, index, pixels=9)
+    eps = 1e-3
+    for c in range(len(kind)):
+        base = (s.targets if kind[c] == 0 else s.weights).copy()
+        p, m = base.copy(), base.copy()
+        p.reshape(-1)[index[c]] += eps
+        m.reshape(-1)[index[c]] -= eps
+        if kind[c] == 0:
+            fd = (L(targets=p) - L(targets=m)) / (2 * eps)
+        else:
+            fd = (L(weights=p) - L(weights=m)) / (2 * eps)
+        assert abs(g[c] - fd) <= 1e-5 * max(1.0, abs(fd)), (c, g[c], fd)
