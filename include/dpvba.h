@@ -91,8 +91,8 @@ typedef struct {
                               Eq. 3 summed over the patch): the targets passed to
                               ba_set_graph* are then float32 [E,9,2] (row-major
                               pixel order), the weights stay [E,2] and are shared
-                              by the edge's nine residuals; ba_backward returns
-                              BA_ERR_UNSUPPORTED                                   */
+                              by the edge's nine residuals; ba_backward's target
+                              cotangents take the targets' layout                  */
 } ba_options_t;
 
 /* Fill *opt with the defaults above. */
@@ -304,7 +304,8 @@ DPVBA_API ba_status_t ba_set_record(ba_handle_t h, int on);
  *   grad_depths : float32 [P], dL/d(inverse depth) of the final patches.
  * Outputs (device, may be null = not wanted):
  *   grad_targets, grad_weights : float32 [E,2] in input edge order,
- *                 8-byte aligned, overwritten;
+ *                 8-byte aligned, overwritten (grad_targets [E,9,2] when
+ *                 the handle's residual_pixels is 9);
  *   grad_tangent0 : float64 [N,6], dL/dxi of the initial poses under the left
  *                 perturbation T <- Exp(xi) T, xi = (rho, phi) (0 for fixed);
  *   grad_depths0  : float32 [P], dL/d(initial inverse depth).

@@ -129,7 +129,8 @@ class DPVBA:
 
     def backward(self, grad_poses=None, grad_depths=None, initial: bool = False):
         """Reverse-mode pass over the recorded step: returns (grad_targets,
-        grad_weights) as float32 [E,2]; with ``initial`` also the cotangents of
+        grad_weights) as float32 [E,2] (grad_targets [E,3,3,2] with
+        residual_pixels=9); with ``initial`` also the cotangents of
         the initial state, (grad_tangent0 float64 [N,6], grad_depths0 float32 [P]).
         ``grad_poses`` is float64 [N,7] (d loss / d(t, q) of the final poses),
         ``grad_depths`` float32 [P] (d loss / d final inverse depth)."""
@@ -138,7 +139,8 @@ class DPVBA:
             grad_poses = grad_poses.to(device=dev, dtype=torch.float64).contiguous()
         if grad_depths is not None:
             grad_depths = grad_depths.to(device=dev, dtype=torch.float32).contiguous()
-        gT = torch.empty((self.E, 2), dtype=torch.float32, device=dev)
+        gT = torch.empty((self.E, 2) if self.residual_pixels == 1 else (self.E, 3, 3, 2), dtype=torch.float32,
+                         device=dev)
         gW = torch.empty((self.E, 2), dtype=torch.float32, device=dev)
         x0 = torch.empty((self.N, 6), dtype=torch.float64, device=dev) if initial else None
         d0 = torch.empty(self.P, dtype=torch.float32, device=dev) if initial else None

@@ -219,6 +219,10 @@ __device__ __forceinline__ void adjoint_apply(const RelPose& T, const float* v, 
 
 // Step 3 for iteration s: one CTA per patch group, one warp per (source,
 // target) run, one lane per edge.
+// PIX residual pixels per edge (1: the patch centre; 9: the whole patch,
+// targets and their cotangents [E,9,2]): the edge's terms are the sums over
+// its pixels, each pixel masked on its own as in the forward assembly.
+template <int PIX>
 __global__ void __launch_bounds__(ADJ_THREADS) k_adj_edges(
     int G, int P, const int* __restrict__ fdx, const int* __restrict__ gprob, float z_min,
     const int* __restrict__ gptr,
@@ -266,76 +270,84 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_edges(
       const int k = g * G + kl;
       const int e = perm[s];
       const float* pk = patches + 27 * (size_t)k;
-      const float xb0 = (pk[4] - cx) / fx, xb1 = (pk[13] - cy) / fy, d = pk[22];
-      // the forward step's point and mask, bit for bit
-      const float X = fmaf(T.R[0], xb0, fmaf(T.R[1], xb1, fmaf(T.t[0], d, T.R[2])));
-      const float Y = fmaf(T.R[3], xb0, fmaf(T.R[4], xb1, fmaf(T.t[1], d, T.R[5])));
-      const float Z = fmaf(T.R[6], xb0, fmaf(T.R[7], xb1, fmaf(T.t[2], d, T.R[8])));
-      if (!(Z > z_min * d)) {
-        gd[pmpos[s]] = 0.f;
-        continue;
-      }
-      const float2 tg = *reinterpret_cast<const float2*>(targets + 2 * (size_t)e);
+      const float d = pk[22];
       const float2 wt = *reinterpret_cast<const float2*>(weights + 2 * (size_t)e);
       const float ld = lam_d[k], Dd = dd_s[k];
-      // point, translation and depth as duals in (rho, phi, d)
-      const float Xv[3] = {X, Y, Z};
-      D7 Xd[3], td[3], dd;
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        Xd[c] = dual_const<float, 7>(Xv[c]);
-        Xd[c].g[c] = d;
-        td[c] = dual_const<float, 7>(T.t[c]);
-        td[c].g[c] = 1.f;
-        Xd[c].g[6] = T.t[c];
-      }
-#pragma unroll
-      for (int q = 0; q < 3; ++q) {
-        float ex[3], et[3];
-        ecross(q, Xv, ex);
-        ecross(q, T.t, et);
+      float gdk = 0.f, gw0 = 0.f, gw1 = 0.f;
+#pragma unroll 1
+      for (int px = 0; px < PIX; ++px) {
+        const int pp = PIX == 1 ? 4 : px;
+        const float xb0 = (pk[pp] - cx) / fx, xb1 = (pk[9 + pp] - cy) / fy;
+        // the forward step's point and mask, bit for bit
+        const float X = fmaf(T.R[0], xb0, fmaf(T.R[1], xb1, fmaf(T.t[0], d, T.R[2])));
+        const float Y = fmaf(T.R[3], xb0, fmaf(T.R[4], xb1, fmaf(T.t[1], d, T.R[5])));
+        const float Z = fmaf(T.R[6], xb0, fmaf(T.R[7], xb1, fmaf(T.t[2], d, T.R[8])));
+        if (!(Z > z_min * d)) continue;
+        const size_t te = (size_t)e * PIX + px;
+        const float2 tg = *reinterpret_cast<const float2*>(targets + 2 * te);
+        // point, translation and depth as duals in (rho, phi, d)
+        const float Xv[3] = {X, Y, Z};
+        D7 Xd[3], td[3], dd;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-          Xd[c].g[3 + q] = ex[c];
-          td[c].g[3 + q] = et[c];
+          Xd[c] = dual_const<float, 7>(Xv[c]);
+          Xd[c].g[c] = d;
+          td[c] = dual_const<float, 7>(T.t[c]);
+          td[c].g[c] = 1.f;
+          Xd[c].g[6] = T.t[c];
         }
-      }
-      dd = dual_const<float, 7>(d);
-      dd.g[6] = 1.f;
-      // A = d mu_rho + mu_phi x X + lambda_d t (a = D A), B likewise with the step
-      D7 A[3], B[3];
-      {
-        D7 mu[6], cr[3];
-        perturbed_diff(lj, ml, mu);
-        dcross(mu + 3, Xd, cr);
 #pragma unroll
-        for (int c = 0; c < 3; ++c) A[c] = dd * mu[c] + cr[c] + ld * td[c];
-        perturbed_diff(dj, md, mu);
-        dcross(mu + 3, Xd, cr);
+        for (int q = 0; q < 3; ++q) {
+          float ex[3], et[3];
+          ecross(q, Xv, ex);
+          ecross(q, T.t, et);
 #pragma unroll
-        for (int c = 0; c < 3; ++c) B[c] = dd * mu[c] + cr[c] + Dd * td[c];
+          for (int c = 0; c < 3; ++c) {
+            Xd[c].g[3 + q] = ex[c];
+            td[c].g[3 + q] = et[c];
+          }
+        }
+        dd = dual_const<float, 7>(d);
+        dd.g[6] = 1.f;
+        // A = d mu_rho + mu_phi x X + lambda_d t (a = D A), B likewise with the step
+        D7 A[3], B[3];
+        {
+          D7 mu[6], cr[3];
+          perturbed_diff(lj, ml, mu);
+          dcross(mu + 3, Xd, cr);
+#pragma unroll
+          for (int c = 0; c < 3; ++c) A[c] = dd * mu[c] + cr[c] + ld * td[c];
+          perturbed_diff(dj, md, mu);
+          dcross(mu + 3, Xd, cr);
+#pragma unroll
+          for (int c = 0; c < 3; ++c) B[c] = dd * mu[c] + cr[c] + Dd * td[c];
+        }
+        const D7 iz = 1.f / Xd[2];
+        const D7 u = Xd[0] * iz, v = Xd[1] * iz;
+        const D7 a0 = fx * iz * (A[0] - u * A[2]), a1 = fy * iz * (A[1] - v * A[2]);
+        const D7 b0 = fx * iz * (B[0] - u * B[2]), b1 = fy * iz * (B[1] - v * B[2]);
+        D7 r0 = tg.x - (fx * u + cx), r1 = tg.y - (fy * v + cy);
+        const float izv = 1.0f / Z;  // the forward step's residual value
+        r0.v = tg.x - fmaf(fx * X, izv, cx);
+        r1.v = tg.y - fmaf(fy * Y, izv, cy);
+        const D7 phi = wt.x * (a0 * (r0 - b0)) + wt.y * (a1 * (r1 - b1));
+        float2* pT = reinterpret_cast<float2*>(gT + 2 * te);
+        float2 t2 = *pT;
+        t2.x += wt.x * a0.v;
+        t2.y += wt.y * a1.v;
+        *pT = t2;
+        gw0 += a0.v * (r0.v - b0.v);
+        gw1 += a1.v * (r1.v - b1.v);
+        gdk += phi.g[6];
+#pragma unroll
+        for (int m = 0; m < 6; ++m) gdel[m] += phi.g[m];
       }
-      const D7 iz = 1.f / Xd[2];
-      const D7 u = Xd[0] * iz, v = Xd[1] * iz;
-      const D7 a0 = fx * iz * (A[0] - u * A[2]), a1 = fy * iz * (A[1] - v * A[2]);
-      const D7 b0 = fx * iz * (B[0] - u * B[2]), b1 = fy * iz * (B[1] - v * B[2]);
-      D7 r0 = tg.x - (fx * u + cx), r1 = tg.y - (fy * v + cy);
-      const float izv = 1.0f / Z;  // the forward step's residual value
-      r0.v = tg.x - fmaf(fx * X, izv, cx);
-      r1.v = tg.y - fmaf(fy * Y, izv, cy);
-      const D7 phi = wt.x * (a0 * (r0 - b0)) + wt.y * (a1 * (r1 - b1));
-      float2* pT = reinterpret_cast<float2*>(gT + 2 * (size_t)e);
       float2* pW = reinterpret_cast<float2*>(gW + 2 * (size_t)e);
-      float2 t2 = *pT, w2 = *pW;
-      t2.x += wt.x * a0.v;
-      t2.y += wt.y * a1.v;
-      w2.x += a0.v * (r0.v - b0.v);
-      w2.y += a1.v * (r1.v - b1.v);
-      *pT = t2;
+      float2 w2 = *pW;
+      w2.x += gw0;
+      w2.y += gw1;
       *pW = w2;
-      gd[pmpos[s]] = phi.g[6];
-#pragma unroll
-      for (int m = 0; m < 6; ++m) gdel[m] += phi.g[m];
+      gd[pmpos[s]] = gdk;
     }
 #pragma unroll
     for (int m = 0; m < 6; ++m)
@@ -415,8 +427,6 @@ extern "C" ba_status_t ba_backward(ba_handle_t h, const double* grad_poses, cons
   if (!h) return BA_ERR_INVALID_ARG;
   if (!h->have_graph || !h->tape_valid)
     return dpv_fail(h, BA_ERR_STATE, "ba_backward: no recorded ba_step (call ba_set_record(h, 1) before ba_step)");
-  if (h->opt.residual_pixels != 1)
-    return dpv_fail(h, BA_ERR_UNSUPPORTED, "ba_backward: the adjoint covers the patch-centre residual only");
   if ((reinterpret_cast<uintptr_t>(grad_targets) | reinterpret_cast<uintptr_t>(grad_weights)) & 7)
     return dpv_fail(h, BA_ERR_INVALID_ARG, "ba_backward: grad_targets/grad_weights must be 8-byte aligned");
   Workspace* ws = h->ws;
@@ -431,14 +441,14 @@ extern "C" ba_status_t ba_backward(ba_handle_t h, const double* grad_poses, cons
       (s = dpv_grow(h, ws->ad_gd, E > 0 ? E : 1, "edge depth cotangents")) ||
       (s = dpv_grow(h, ws->ad_lamd, P, "depth multipliers")) ||
       (s = dpv_grow(h, ws->ad_v, h->n_pad, "adjoint rhs")) ||
-      (!grad_targets && (s = dpv_grow(h, ws->ad_gt, E2, "target cotangents"))) ||
+      (!grad_targets && (s = dpv_grow(h, ws->ad_gt, E2 * h->opt.residual_pixels, "target cotangents"))) ||
       (!grad_weights && (s = dpv_grow(h, ws->ad_gw, E2, "weight cotangents"))))
     return s;
   DPV_CUDA(h, cudaMemsetAsync(ws->ad_v.p, 0, sizeof(double) * h->n_pad, h->stream));
   float* gT = grad_targets ? grad_targets : ws->ad_gt.p;
   float* gW = grad_weights ? grad_weights : ws->ad_gw.p;
   if (E > 0) {
-    DPV_CUDA(h, cudaMemsetAsync(gT, 0, sizeof(float) * 2 * E, h->stream));
+    DPV_CUDA(h, cudaMemsetAsync(gT, 0, sizeof(float) * 2 * E * h->opt.residual_pixels, h->stream));
     DPV_CUDA(h, cudaMemsetAsync(gW, 0, sizeof(float) * 2 * E, h->stream));
   }
   double* xbn = ws->ad_xb.p;
@@ -486,7 +496,8 @@ extern "C" ba_status_t ba_backward(ba_handle_t h, const double* grad_poses, cons
     dpv_prof_end(h);
     if (s) return s;
     dpv_prof_begin(h, BA_KERNEL_ADJOINT);
-    k_adj_edges<<<h->ngroups, ADJ_THREADS, 0, h->stream>>>(
+    auto adj_edges = h->opt.residual_pixels == 9 ? k_adj_edges<9> : k_adj_edges<1>;
+    adj_edges<<<h->ngroups, ADJ_THREADS, 0, h->stream>>>(
         h->G, P, fdx, ws->gprob.p, h->opt.z_min, ws->gptr.p, ws->grun.p, ws->gnr.p, ws->eslot.p, ws->perm.p, ws->pmpos.p,
         ws->win.p, ws->posef.p, patches_s, h->targets, h->weights, ws->intr, ws->tmpv.p, ws->ad_lamd.p, dx_s, dd_s,
         gT, gW, ws->ad_gd.p, xbc, ws->status);

@@ -132,12 +132,30 @@ def test_centre_only_unchanged_and_errors():
     with pytest.raises(capi.BAError) as e:
         DPVBA(residual_pixels=4)
     assert e.value.status == capi.BA_ERR_INVALID_ARG
-    # the adjoint covers the centre residual only
-    sf = full(s)
-    ba, T = bind(sf)
+
+
+@pytest.mark.parametrize("make,precision", [(scenes.tiny, "fp32"), (scenes.tiny, "mixed"), (scenes.odometry, "mixed")])
+def test_backward_matches_oracle(make, precision):
+    # ba_backward over recorded whole-patch iterations against the oracle's
+    # dual-number derivatives of single pixel targets and edge weights; the
+    # tolerance of the centre-only adjoint tests (1e-4 of the sample's
+    # largest gradient, 1e-3 on its 2-norm)
+    s = full(make(seed=0))
+    rng = np.random.default_rng(0)
+    a, b = rng.normal(size=(s.N, 7)), rng.normal(size=s.P)
+    ba, T = bind(s, precision=precision)
     ba.set_record(True)
-    ba.step(1, sf.fixed)
-    with pytest.raises(capi.BAError) as e:
-        ba.backward(torch.zeros((sf.N, 7), dtype=torch.float64, device="cuda"),
-                    torch.zeros(sf.P, dtype=torch.float32, device="cuda"))
-    assert e.value.status == capi.BA_ERR_UNSUPPORTED
+    ba.step(s.iters, s.fixed)
+    gT, gW = ba.backward(torch.as_tensor(a, dtype=torch.float64).cuda(),
+                         torch.as_tensor(b, dtype=torch.float32).cuda())
+    ba.sync()
+    assert gT.shape == (s.E, 3, 3, 2)
+    n = 40 if s.E > 10000 else 120
+    kind = np.r_[np.zeros(n // 2, int), np.ones(n - n // 2, int)]
+    index = np.r_[rng.choice(18 * s.E, n // 2, replace=False), rng.choice(2 * s.E, n - n // 2, replace=False)]
+    want = oracle.grad_fwd(s, a, b, kind, index, pixels=9)
+    gTn, gWn = gT.cpu().numpy().astype(np.float64), gW.cpu().numpy().astype(np.float64)
+    got = np.r_[gTn.reshape(-1)[index[:n // 2]], gWn.reshape(-1)[index[n // 2:]]]
+    err = np.abs(got - want).max() / np.abs(want).max()
+    nerr = np.linalg.norm(got - want) / np.linalg.norm(want)
+    assert err < 1e-4 and nerr < 1e-3, (err, nerr)
