@@ -1051,28 +1051,25 @@ def run_ours(args):
     e2e_value = job_throughput(args.steps * scene.iters, world, e2e_ms)
 
     # ---- adjoint of the same step (ba_backward), timed on its own ----------
-    # (the adjoint covers the patch-centre residual only)
-    bwd_ms, nb = None, 0
-    if residual_pixels(args.workload) == 1:
-        g = torch.Generator(device=dev).manual_seed(rank)
-        gp = torch.randn((scene.N, 7), dtype=torch.float64, device=dev, generator=g)
-        gd = torch.randn(scene.P, dtype=torch.float32, device=dev, generator=g)
-        nb = min(args.steps, 20)
-        bev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(nb)]
-        ba.set_record(True)
-        for k in range(nb + 2):
-            reset()
-            flush.zero_()
-            one_step()
-            if k >= 2:
-                bev[k - 2][0].record(stream)
-            ba.backward(gp, gd)
-            if k >= 2:
-                bev[k - 2][1].record(stream)
-        torch.cuda.synchronize()
-        ba.set_record(False)
-        ba.sync()
-        bwd_ms = statistics.median(a.elapsed_time(b) for a, b in bev)
+    g = torch.Generator(device=dev).manual_seed(rank)
+    gp = torch.randn((scene.N, 7), dtype=torch.float64, device=dev, generator=g)
+    gd = torch.randn(scene.P, dtype=torch.float32, device=dev, generator=g)
+    nb = min(args.steps, 20)
+    bev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(nb)]
+    ba.set_record(True)
+    for k in range(nb + 2):
+        reset()
+        flush.zero_()
+        one_step()
+        if k >= 2:
+            bev[k - 2][0].record(stream)
+        ba.backward(gp, gd)
+        if k >= 2:
+            bev[k - 2][1].record(stream)
+    torch.cuda.synchronize()
+    ba.set_record(False)
+    ba.sync()
+    bwd_ms = statistics.median(a.elapsed_time(b) for a, b in bev)
 
     if rank != 0:
         if dist:
