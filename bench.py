@@ -8,8 +8,12 @@ pose Cholesky + solves, depth back-substitution, SE(3) retraction).
 Metric: GN iterations per second (and edges per second) over all ranks, with
 the per-step pose/depth error against the FP64 oracle stated beside it.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload odometry]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload global]
     python bench.py --impl reference      # the FP64 CPU oracle, same workload
+
+The default workload is the global loop-closure BA (1000 keyframes, ~1.2M
+edges, 5988-unknown pose system, mixed precision, 4 GN iterations): the
+largest single-GPU configuration and the paper's named bottleneck.
 
 Under torchrun each rank solves its own independent problem (seed = rank):
 weak scaling, no collective on the data path.
@@ -91,9 +95,10 @@ def parse():
                          "near half a second with several clock samples; 3 for the loop-closure and batched workloads)")
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="odometry")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="global")
     ap.add_argument("--precision", choices=["fp32", "mixed"], default=None,
-                    help="fp32 (default) or mixed; the batched workload defaults to mixed")
+                    help="fp32 or mixed; the loop-closure (global, loop400), batched and pgo workloads default "
+                         "to mixed, the others to fp32")
     ap.add_argument("--group", type=int, default=0, help="patches per group (0 = automatic)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-capture", action="store_true", help="eager ba_step instead of CUDA-graph replay")
@@ -103,13 +108,15 @@ def parse():
         # (the reference arm's oracle steps are ~50 ms each on one core: 50 of them)
         short = a.workload in ("odometry", "odometry_full", "tiny", "proximity", "correlation")
         a.steps = 3 if not short else (50 if a.impl == "reference" else 2000)
+        if a.workload in ("global", "loop400") and a.impl == "ours":
+            a.steps = 20  # ~0.5 s of timed steps: several clock samples
         if a.workload == "correlation":
             a.steps = 3 if a.impl == "reference" else 200
         if a.workload == "pgo":
             a.steps = 2 if a.impl == "reference" else 20
     a.precision_set = a.precision is not None
     if a.precision is None:
-        a.precision = "mixed" if a.workload == "pgo" else "fp32"
+        a.precision = "mixed" if a.workload in ("pgo", "global", "loop400", "batched") else "fp32"
     return a
 
 
@@ -126,8 +133,14 @@ def measured_peaks():
         return FALLBACK_HBM, "fallback"
 
 
+RUN_PEAKS = {}  # peaks measured by this run (measure_peaks)
+
+
 def tensor_peak_tf32():
-    """TF32 dense peak: the measured BF16 burst x the nominal TF32/BF16 ratio."""
+    """TF32 dense peak: measured in this run (a cuBLAS TF32 GEMM, best of 10)
+    when available, else the measured BF16 burst x the nominal TF32/BF16 ratio."""
+    if RUN_PEAKS.get("tf32_tflops"):
+        return RUN_PEAKS["tf32_tflops"], "measured in this run: torch.matmul TF32 8192^3 (2 n^3 flops), best of 10"
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
         with open(p) as f:
@@ -136,11 +149,49 @@ def tensor_peak_tf32():
         return FALLBACK_BF16_TFLOPS * TF32_PER_BF16, "fallback bf16 x nominal tf32/bf16"
 
 
+def measure_peaks(dev):
+    """Dense TF32, FP32 and FP64 GEMM rates of this GPU (cuBLAS through
+    torch.matmul, CUDA events, best of several): the denominators of the
+    factorisation's roofline (TF32) and context for the FP32/FP64 CUDA-core
+    work.  Takes ~2 s."""
+    import torch
+    out = {}
+    old_tf32 = torch.backends.cuda.matmul.allow_tf32
+    try:
+        for key, dt, n, reps, tf32 in (("tf32_tflops", torch.float32, 8192, 10, True),
+                                        ("fp32_tflops", torch.float32, 8192, 4, False),
+                                        ("fp64_tflops", torch.float64, 4096, 3, False)):
+            torch.backends.cuda.matmul.allow_tf32 = tf32
+            a = torch.randn(n, n, device=dev, dtype=dt)
+            b = torch.randn(n, n, device=dev, dtype=dt)
+            c = a @ b
+            torch.cuda.synchronize()
+            best = float("inf")
+            for _ in range(reps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                torch.matmul(a, b, out=c)
+                e1.record()
+                torch.cuda.synchronize()
+                best = min(best, e0.elapsed_time(e1) / 1e3)
+            out[key] = 2.0 * n ** 3 / best / 1e12
+            del a, b, c
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = old_tf32
+        torch.cuda.empty_cache()
+    out["how"] = ("torch.matmul (cuBLAS) n^3 GEMMs, 2 n^3 flops, CUDA events, best of reps: TF32 (allow_tf32) and "
+                  "FP32 (CUDA cores) at n = 8192, FP64 at n = 4096")
+    RUN_PEAKS.update(out)
+    return out
+
+
 def factor_flops(ns):
     """Algorithmic flops of the LDL^T factorisations run by the persistent
-    tensor-core kernel (systems above 256 unknowns): 2 n^3 / 3 each (the
-    three-pass TF32 split issues three times as many on the tensor pipe)."""
-    return sum(2.0 * n ** 3 / 3.0 for n in ns if n > 256)
+    tensor-core kernel (systems above 256 unknowns): n^3 / 3 each (one
+    multiply-add per entry of the trailing updates, counted as two flops:
+    sum_k 2 (n - k)^2 / 2; the three-pass TF32 split issues three times as
+    many on the tensor pipe)."""
+    return sum(n ** 3 / 3.0 for n in ns if n > 256)
 
 
 def roofline(dom, prof, steps, bytes_fn, factor_ns, workload):
@@ -264,6 +315,24 @@ class ClockSampler:
         reasons = sorted({names[k] for r in self.rows for k in range(4) if len(r) > 4 + k and r[4 + k] == "Active"})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
                 "reasons": reasons, "samples": len(self.rows)}
+
+
+def gt_errors(poses, depths, scene):
+    """Error of a state against the scene's ground truth (the gauge is held by
+    the fixed poses, which start at ground truth): RMS and largest rotation
+    (rad) and camera-centre (m) errors over the frames, median relative
+    inverse-depth error."""
+    from scipy.spatial.transform import Rotation
+    Rg = Rotation.from_quat(scene.poses_gt[:, 3:])
+    R = Rotation.from_quat(poses[:, 3:])
+    rot = (R * Rg.inv()).magnitude()
+    c = -R.inv().apply(poses[:, :3])
+    cg = -Rg.inv().apply(scene.poses_gt[:, :3])
+    tr = np.linalg.norm(c - cg, axis=1)
+    dep = np.abs(np.asarray(depths, np.float64) - scene.depth_gt) / scene.depth_gt
+    return {"rot_rmse_rad": float(np.sqrt(np.mean(rot ** 2))), "rot_max_rad": float(rot.max()),
+            "centre_rmse_m": float(np.sqrt(np.mean(tr ** 2))), "centre_max_m": float(tr.max()),
+            "depth_median_rel": float(np.median(dep))}
 
 
 def pose_errors(a, b):
@@ -925,10 +994,21 @@ def run_reference(args):
             iters_per_step = scene.iters
     for _ in range(min(args.warmup, 1 if scene.N < LARGE_FRAMES else 0)):
         work()
+    # the oracle is deterministic single-threaded code: a time budget bounds
+    # the run (the 1000-frame GN iteration takes ~25 s on one core); at least
+    # one step always runs, and the line reports the steps that ran
+    budget_s = 150.0
     t0 = time.perf_counter()
+    steps_run = 0
     for _ in range(args.steps):
         work()
+        steps_run += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
     el = time.perf_counter() - t0
+    if steps_run < args.steps:
+        desc += f"; {steps_run} of the {args.steps} requested steps ran within a {budget_s:.0f} s budget"
+    args.steps = steps_run
     value = args.steps * iters_per_step / el
     unit = "problem GN it/s" if args.workload == "batched" else UNIT
     line = {
@@ -970,6 +1050,7 @@ def run_ours(args):
     desc, make = WORKLOADS[args.workload]
     scene = make(seed=problem_seed(rank))  # independent problems per rank, no data-path collective
     dev = torch.device("cuda", local)
+    peaks = measure_peaks(dev)
     T = scene_tensors(scene, dev)
     pristine = {k: v.clone() for k, v in T.items()}
     stream = torch.cuda.current_stream(dev)
@@ -1086,6 +1167,7 @@ def run_ours(args):
 
     # ---- error against the oracle and the CPU baseline --------------------
     err = None
+    gt = None
     cpu = None
     if not args.no_cpu_baseline:
         import oracle
@@ -1093,7 +1175,10 @@ def run_ours(args):
         reset()
         ba.set_graph(**T)
         errs = []
-        err_iters = scene.iters if scene.N < LARGE_FRAMES else 1
+        # every iteration of the workload, each GPU step from the GPU's state
+        # and each oracle step from the oracle's (at 1000 frames ~25 s per
+        # oracle iteration on one core)
+        err_iters = scene.iters
         t_or = time.perf_counter()
         want = oracle.gn_steps(scene, iters=err_iters, pixels=residual_pixels(args.workload))
         t_or = time.perf_counter() - t_or
@@ -1102,16 +1187,20 @@ def run_ours(args):
             ba.sync()
             rot, tr = pose_errors(T["poses"].cpu().numpy(), want[it][0])
             d = T["patches"][:, 2, 1, 1].cpu().numpy().astype(np.float64)
-            dep = float(np.max(np.abs(d - want[it][1]) / np.abs(want[it][1])))
-            errs.append({"iter": it + 1, "rot_rad": rot, "trans_rel": tr, "depth_rel": dep})
+            rel = np.abs(d - want[it][1]) / np.abs(want[it][1])
+            errs.append({"iter": it + 1, "rot_rad": rot, "trans_rel": tr, "depth_rel": float(rel.max()),
+                         "depth_rel_p99": float(np.percentile(rel, 99))})
         err = errs
+        gt = {"initial": gt_errors(scene.poses, scene.patches[:, 2, 1, 1], scene),
+              "gpu": gt_errors(T["poses"].cpu().numpy(), T["patches"][:, 2, 1, 1].cpu().numpy(), scene),
+              "oracle": gt_errors(want[-1][0], want[-1][1], scene), "after_iters": err_iters}
         if scene.N < LARGE_FRAMES:
             runs, el = time_oracle(scene, budget_s=10.0, pixels=residual_pixels(args.workload))
             cv = runs * scene.iters / el
             sample = f"{runs} full runs of the workload ({scene.iters} GN iterations each)"
-        else:  # the oracle iteration of the error check above
+        else:  # the oracle iterations of the error check above
             cv, el = err_iters / t_or, t_or
-            sample = f"the first GN iteration of the workload (the error check's)"
+            sample = f"the {err_iters} GN iterations of the workload (the error check's)"
         cpu = {"value": cv, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"{sample}, single-threaded FP64 oracle (-O2) on 1 of {cpu_cores()} host cores, {el:.1f} s"}
 
@@ -1125,6 +1214,8 @@ def run_ours(args):
                    "l2": "flushed between steps (256 MiB write)", "step": "ba_set_graph + ba_step"},
         "edges_per_sec": value * scene.E,
         "error_vs_oracle": err,
+        "ground_truth_error": gt,
+        "peaks_measured": peaks,
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},

@@ -32,15 +32,19 @@ def headers():
 def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(OBJ, exist_ok=True)
     newest_hdr = max(os.path.getmtime(h) for h in headers())
-    objs = []
+    objs, cmds = [], []
     for src in sources():
         obj = os.path.join(OBJ, os.path.basename(src)[:-3] + ".o")
         objs.append(obj)
         if force or not os.path.exists(obj) or os.path.getmtime(obj) < max(os.path.getmtime(src), newest_hdr):
-            cmd = ["nvcc", *ARCH, *FLAGS, "-c", src, "-o", obj]
+            cmds.append(["nvcc", *ARCH, *FLAGS, "-c", src, "-o", obj])
+    if cmds:  # one nvcc per stale source, in parallel
+        from concurrent.futures import ThreadPoolExecutor
+        for c in cmds:
             if verbose:
-                print(" ".join(cmd), file=sys.stderr)
-            subprocess.check_call(cmd)
+                print(" ".join(c), file=sys.stderr)
+        with ThreadPoolExecutor(max_workers=min(len(cmds), os.cpu_count() or 1)) as ex:
+            list(ex.map(subprocess.check_call, cmds))
     if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < max(os.path.getmtime(o) for o in objs):
         cmd = ["nvcc", *ARCH, "-shared", "-cudart", "shared", "-o", LIB, *objs]
         if verbose:

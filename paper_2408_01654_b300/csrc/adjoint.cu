@@ -427,6 +427,11 @@ extern "C" ba_status_t ba_backward(ba_handle_t h, const double* grad_poses, cons
   if (!h) return BA_ERR_INVALID_ARG;
   if (!h->have_graph || !h->tape_valid)
     return dpv_fail(h, BA_ERR_STATE, "ba_backward: no recorded ba_step (call ba_set_record(h, 1) before ba_step)");
+  if (h->patches_padded)
+    return dpv_fail(h, BA_ERR_UNSUPPORTED,
+                    "ba_backward: a batched binding whose patch counts are not multiples of the group size "
+                    "(the library works on a padded copy of the patches) has no adjoint; choose a group size "
+                    "that divides every problem's patch count");
   if ((reinterpret_cast<uintptr_t>(grad_targets) | reinterpret_cast<uintptr_t>(grad_weights)) & 7)
     return dpv_fail(h, BA_ERR_INVALID_ARG, "ba_backward: grad_targets/grad_weights must be 8-byte aligned");
   Workspace* ws = h->ws;

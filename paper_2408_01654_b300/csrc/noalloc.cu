@@ -11,15 +11,14 @@
 //
 // That array is a file-scope __device__ variable: every GPU that loads the
 // library holds it (about 0.5 MB) until the process exits.  Host code cannot
-// use its name as a device address, so the first call on each device looks
-// its address up with cudaGetSymbolAddress (with that device current) and
-// caches it; make that first call before any stream capture.  All calls on a
+// use its name as a device address, so every call looks the address up with
+// cudaGetSymbolAddress on the current device (a lookup in the loaded module,
+// no allocation; not cached, because cudaDeviceReset reloads the module and
+// may move the array).  All calls on a
 // device share the array and it keeps the previous call's contents, so the
 // staging kernel rewrites every entry the solver reads (and clears the status
 // word) on each call, and calls whose GPU work overlaps race on it.
 #include "internal.cuh"
-
-#include <mutex>
 
 #define DPV_NOALLOC_MAX_N 256  // largest n accepted (= the one-CTA solver's limit)
 
@@ -40,10 +39,6 @@ ba_status_t dpv_launch_small_solver(cudaStream_t st, int n, int n_pad, const dou
                                     float* dxf, int refine, int* status);
 
 namespace {
-
-constexpr int MAX_DEVICES = 64;
-double* g_scratch[MAX_DEVICES] = {};
-std::mutex g_mutex;
 
 // Copy the caller's dense n x n system (lower triangle of a row-major array)
 // into the padded tile the solver reads: identity on the padding, zeros above
@@ -68,20 +63,15 @@ __global__ void k_noalloc_stage(int n, int n_pad, const double* __restrict__ S_i
   if (gid == 0) *reinterpret_cast<int*>(scr + SCR_STATUS) = 0;
 }
 
+// The array's device address on the current device (looked up on every call).
 ba_status_t scratch_for_current_device(double** out) {
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES) return BA_ERR_CUDA;
-  std::lock_guard<std::mutex> lock(g_mutex);
-  if (!g_scratch[dev]) {
-    void* p = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&p, dpv_noalloc_scratch);
-    if (e != cudaSuccess || !p) {
-      cudaGetLastError();
-      return BA_ERR_CUDA;
-    }
-    g_scratch[dev] = static_cast<double*>(p);
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, dpv_noalloc_scratch);
+  if (e != cudaSuccess || !p) {
+    cudaGetLastError();
+    return BA_ERR_CUDA;
   }
-  *out = g_scratch[dev];
+  *out = static_cast<double*>(p);
   return BA_OK;
 }
 

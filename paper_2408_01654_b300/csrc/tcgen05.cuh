@@ -80,6 +80,16 @@ __device__ __forceinline__ void tc_mbar_init(uint64_t* mbar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(tc_smem_addr(mbar)), "r"(count) : "memory");
 }
 // Wait for phase `parity` to complete; false after `timeout` cycles.
+// The bound on a wait for this CTA's own bulk copies or MMAs: the caller's
+// budget for waits on other CTAs, but never less than ~0.1 s at 2 GHz.  Such
+// an operation completes in microseconds, and abandoning it while it is still
+// in flight would let the CTA release shared or tensor memory under it; a
+// short budget (for waits on other CTAs) must not cut these waits short.
+constexpr long long TC_HW_WAIT_MIN = 200000000LL;
+__device__ __forceinline__ long long tc_hw_bound(long long timeout) {
+  return timeout > TC_HW_WAIT_MIN ? timeout : TC_HW_WAIT_MIN;
+}
+
 __device__ __forceinline__ bool tc_mbar_wait(uint64_t* mbar, uint32_t parity, long long timeout) {
   const uint32_t a = tc_smem_addr(mbar);
   const long long t0 = clock64();

@@ -19,7 +19,7 @@ pytestmark = pytest.mark.gpu
 
 import oracle  # noqa: E402
 from paper_2408_01654_b300 import capi, scenes  # noqa: E402
-from paper_2408_01654_b300.ba import DPVBA, batch_tensors, scene_tensors  # noqa: E402
+from paper_2408_01654_b300.ba import DPVBA, batch_tensors, bundle_adjust, scene_tensors  # noqa: E402
 
 from test_gpu_parity import depth_error, pose_error  # noqa: E402
 
@@ -159,3 +159,56 @@ def test_backward_matches_oracle(make, precision):
     err = np.abs(got - want).max() / np.abs(want).max()
     nerr = np.linalg.norm(got - want) / np.linalg.norm(want)
     assert err < 1e-4 and nerr < 1e-3, (err, nerr)
+
+
+def test_backward_initial_state_matches_oracle():
+    # cotangents of the initial state through the whole-patch iterations: the
+    # pose tangents (through the retraction's adjoint and every edge's nine
+    # pixels) and the inverse depths (nine pixels per edge summed), against
+    # the oracle's dual numbers of kinds 2 (initial depth) and 3 (initial
+    # left pose perturbation) in the whole-patch mode
+    s = full(scenes.tiny(seed=1))
+    rng = np.random.default_rng(2)
+    a, b = rng.normal(size=(s.N, 7)), rng.normal(size=s.P)
+    ba, T = bind(s, precision="mixed")
+    ba.set_record(True)
+    ba.step(s.iters, s.fixed)
+    gT, gW, x0, d0 = ba.backward(torch.as_tensor(a, dtype=torch.float64).cuda(),
+                                 torch.as_tensor(b, dtype=torch.float32).cuda(), initial=True)
+    ba.sync()
+    kp = rng.choice(s.P, 24, replace=False)
+    kx = rng.choice(np.arange(6 * s.fixed, 6 * s.N), 24, replace=False)
+    want_d = oracle.grad_fwd(s, a, b, np.full(24, 2), kp, pixels=9)
+    want_x = oracle.grad_fwd(s, a, b, np.full(24, 3), kx, pixels=9)
+    for got, want in ((d0.cpu().numpy().astype(np.float64)[kp], want_d),
+                      (x0.cpu().numpy().reshape(-1)[kx], want_x)):
+        err = np.abs(got - want).max() / np.abs(want).max()
+        nerr = np.linalg.norm(got - want) / np.linalg.norm(want)
+        assert err < 1e-4 and nerr < 1e-3, (err, nerr)
+    assert np.all(x0.cpu().numpy()[: s.fixed] == 0.0)
+
+
+@pytest.mark.parametrize("layout", ["E92", "E332"])
+def test_autograd_function_keeps_the_target_layout(layout):
+    # the differentiable layer returns target gradients in the layout of the
+    # targets it was given ([E,9,2] or [E,3,3,2]) and equal to ba_backward's
+    s = full(scenes.tiny(seed=3))
+    T = scene_tensors(s)
+    shape = (s.E, 9, 2) if layout == "E92" else (s.E, 3, 3, 2)
+    tg = T["targets"].reshape(shape).clone().requires_grad_(True)
+    wt = T["weights"].clone().requires_grad_(True)
+    rng = np.random.default_rng(4)
+    a, b = rng.normal(size=(s.N, 7)), rng.normal(size=s.P)
+    poses, depths = bundle_adjust(tg, wt, T["poses"], T["patches"], T["ii"], T["jj"], T["kk"], T["intrinsics"],
+                                  s.iters, s.fixed, residual_pixels=9)
+    L = (torch.as_tensor(a).cuda() * poses).sum() + (torch.as_tensor(b, dtype=torch.float32).cuda() * depths).sum()
+    L.backward()
+    assert tg.grad.shape == shape and wt.grad.shape == (s.E, 2)
+    ba, T2 = bind(s)
+    ba.set_record(True)
+    ba.step(s.iters, s.fixed)
+    gT, gW = ba.backward(torch.as_tensor(a, dtype=torch.float64).cuda(), torch.as_tensor(b, dtype=torch.float32).cuda())
+    ba.sync()
+    gTn = gT.reshape(shape)
+    assert torch.allclose(tg.grad, gTn, rtol=1e-5, atol=1e-6 * float(gTn.abs().max()))
+    assert torch.allclose(wt.grad, gW, rtol=1e-5, atol=1e-6 * float(gW.abs().max()))
