@@ -68,8 +68,15 @@ typedef enum {
 } ba_status_t;
 
 typedef enum {
-  BA_FP32 = 0, /* FP32 linearisation, reduction and factorisation; FP64 retraction  */
-  BA_MIXED = 1 /* as BA_FP32, plus FP64 iterative refinement of the pose solve      */
+  BA_FP32 = 0, /* FP32 linearisation with compensated sums, FP32 factorisation with
+                  compensated-FP32 refinement; FP64 retraction                       */
+  BA_MIXED = 1 /* the linearisation (reprojection, Jacobians, block products, Schur
+                  complement, back-substitution) in double-float arithmetic (pairs
+                  of FP32, ~48 bits), the FP32/TF32 factorisation with FP64
+                  refinement (one-CTA systems) or preconditioned conjugate
+                  gradients on a double-float copy of S (larger systems): the step
+                  of an FP64 Gauss-Newton to ~1e-9 on ill-conditioned loop-closure
+                  systems                                                           */
 } ba_precision_t;
 
 typedef struct {
@@ -78,12 +85,14 @@ typedef struct {
   float lambda_depth;      /* added to every inverse-depth diagonal (1e-4)        */
   float z_min;             /* minimum depth in frame j, metres (0.1)              */
   float d_min;             /* lower clamp of inverse depth after a step (1e-3)    */
-  int patches_per_group;   /* patches per reduction group; 0 = automatic          */
-  int max_refine;          /* FP64 refinement sweeps in BA_MIXED (default 2) for
+  int patches_per_group;   /* patches per reduction group; 0 = automatic; at most
+                              64 (BA_FP32) or 32 (BA_MIXED)                      */
+  int max_refine;          /* FP64 refinement sweeps in BA_MIXED (default 3) for
                               systems <= 256 unknowns; larger systems run up to
                               max(8, max_refine) conjugate-gradient iterations
                               preconditioned by the factor; all stop once the
-                              estimated error left in the step is < 1e-7 of it */
+                              estimated error left in the step is < 1e-7 of it
+                              (BA_FP32) or < 1e-10 of it (BA_MIXED)             */
   long long timeout_cycles;/* bound on any device-side wait (default 2e9 cycles)  */
   void* stream;            /* cudaStream_t for all work; NULL = legacy stream      */
   int residual_pixels;     /* residual rows per edge: 1 = the patch centre (2-D,
@@ -310,9 +319,13 @@ DPVBA_API ba_status_t ba_set_record(ba_handle_t h, int on);
  *                 perturbation T <- Exp(xi) T, xi = (rho, phi) (0 for fixed);
  *   grad_depths0  : float32 [P], dL/d(initial inverse depth).
  * The bound targets/weights buffers must hold the values the tape was
- * recorded with; the poses/patches buffers are not read.  Errors:
- * BA_ERR_STATE without a tape, BA_ERR_INVALID_ARG for misaligned outputs,
- * BA_ERR_OOM; device-detected errors (BA_ERR_NOT_SPD) come from ba_sync. */
+ * recorded with; the poses/patches buffers are not read.  A handle bound by
+ * ba_set_graph_batched is differentiated over all its problems at once (the
+ * arrays above are the concatenated ones).  Errors: BA_ERR_STATE without a
+ * tape, BA_ERR_INVALID_ARG for misaligned outputs, BA_ERR_UNSUPPORTED for a
+ * batched binding that works on a padded patch copy (a problem's patch count
+ * not a multiple of the group size), BA_ERR_OOM; device-detected errors
+ * (BA_ERR_NOT_SPD) come from ba_sync. */
 DPVBA_API ba_status_t ba_backward(ba_handle_t h, const double* grad_poses, const float* grad_depths,
                                   float* grad_targets, float* grad_weights, double* grad_tangent0,
                                   float* grad_depths0);
@@ -444,9 +457,10 @@ DPVBA_API ba_status_t ba_pgo_lm(ba_handle_t h, int N, int F, double* S, const do
  * The call waits for its work and returns BA_ERR_NOT_SPD if S is not positive
  * definite.  Its working copy lives in a fixed ~0.5 MB device array inside the
  * library, held by every GPU that loads the library until the process exits.
- * The first call on each device looks up that array's device address (a
- * runtime lookup, no allocation); make it before any stream capture.  All
- * calls share the array, so calls whose GPU work overlaps race. */
+ * Every call looks up that array's device address on the current device (a
+ * lookup in the loaded module, no allocation), so the address stays right
+ * after cudaDeviceReset.  All calls share the array, so calls whose GPU work
+ * overlaps race. */
 DPVBA_API ba_status_t ba_solve_pose_system_noalloc(int n, const double* S, const double* y, double* x, int refine,
                                                    void* stream);
 

@@ -31,15 +31,16 @@ class DPVBA:
     """
 
     def __init__(self, precision: str = "fp32", lambda_pose=1e-4, lambda_depth=1e-4, z_min=0.1, d_min=1e-3,
-                 patches_per_group: int = 0, max_refine: int = 2, stream: torch.cuda.Stream | None = None,
-                 capture: bool = False, residual_pixels: int = 1):
+                 patches_per_group: int = 0, max_refine: int = 3, stream: torch.cuda.Stream | None = None,
+                 capture: bool = False, residual_pixels: int = 1, timeout_cycles: int | None = None):
         self._lib = capi.lib()
         self._h = ctypes.c_void_p()
         self.stream = stream if stream is not None else torch.cuda.current_stream()
+        extra = {} if timeout_cycles is None else {"timeout_cycles": int(timeout_cycles)}
         opt = capi.default_options(
             precision=capi.BA_MIXED if precision == "mixed" else capi.BA_FP32, lambda_pose=lambda_pose,
             lambda_depth=lambda_depth, z_min=z_min, d_min=d_min, patches_per_group=patches_per_group,
-            max_refine=max_refine, stream=self.stream.cuda_stream, residual_pixels=residual_pixels)
+            max_refine=max_refine, stream=self.stream.cuda_stream, residual_pixels=residual_pixels, **extra)
         self.residual_pixels = residual_pixels
         capi.check(None, self._lib.ba_create(ctypes.byref(self._h), ctypes.byref(opt)))
         self._keep = ()
@@ -331,6 +332,7 @@ class BAFunction(torch.autograd.Function):
         ba.step(iters, fixed)
         ba.sync()
         ctx.ba = ba
+        ctx.target_shape = targets.shape  # [E,2], or [E,9,2] / [E,3,3,2] with residual_pixels=9
         return T, Pt[:, 2, 1, 1].clone()
 
     @staticmethod
@@ -338,12 +340,53 @@ class BAFunction(torch.autograd.Function):
         ba = ctx.ba
         gT, gW = ba.backward(grad_poses, grad_depths)
         ba.sync()
-        return gT, gW, None, None, None, None, None, None, None, None, None
+        return gT.reshape(ctx.target_shape), gW, None, None, None, None, None, None, None, None, None
+
+
+class BAFunctionBatched(torch.autograd.Function):
+    """``BAFunction`` over many independent problems bound to one handle
+    (``set_graph_batched``: one launch of each kernel over all problems), e.g.
+    a training batch of odometry windows.  The tensors are the problems'
+    arrays concatenated (ii, jj, kk local to each problem, intrinsics [B,4]),
+    ``offsets`` = (frame_off, patch_off, edge_off), each of length B+1.
+    Returns the final poses [sum N,7] and inverse depths [sum P]; gradients
+    flow to ``targets`` and ``weights``."""
+
+    @staticmethod
+    def forward(ctx, targets, weights, poses, patches, ii, jj, kk, intrinsics, offsets, iters, fixed, opts):
+        targets = targets.detach().contiguous()
+        weights = weights.detach().contiguous()
+        T = poses.detach().clone().contiguous()
+        Pt = patches.detach().clone().contiguous()
+        ba = DPVBA(**(opts or {}))
+        frame_off, patch_off, edge_off = offsets
+        ba.set_graph_batched(T, Pt, ii.contiguous(), jj.contiguous(), kk.contiguous(), targets, weights,
+                             intrinsics.contiguous(), frame_off, patch_off, edge_off)
+        ba.set_record(True)
+        ba.step(iters, fixed)
+        ba.sync()
+        ctx.ba = ba
+        ctx.target_shape = targets.shape
+        return T, Pt[:, 2, 1, 1].clone()
+
+    @staticmethod
+    def backward(ctx, grad_poses, grad_depths):
+        ba = ctx.ba
+        gT, gW = ba.backward(grad_poses, grad_depths)
+        ba.sync()
+        return gT.reshape(ctx.target_shape), gW, None, None, None, None, None, None, None, None, None, None
 
 
 def bundle_adjust(targets, weights, poses, patches, ii, jj, kk, intrinsics, iters, fixed, **opts):
     """Functional form of ``BAFunction`` (keyword options as for ``DPVBA``)."""
     return BAFunction.apply(targets, weights, poses, patches, ii, jj, kk, intrinsics, iters, fixed, opts)
+
+
+def bundle_adjust_batched(targets, weights, poses, patches, ii, jj, kk, intrinsics, frame_off, patch_off, edge_off,
+                          iters, fixed, **opts):
+    """Functional form of ``BAFunctionBatched``."""
+    return BAFunctionBatched.apply(targets, weights, poses, patches, ii, jj, kk, intrinsics,
+                                   (frame_off, patch_off, edge_off), iters, fixed, opts)
 
 
 def batch_tensors(scene_list, device="cuda") -> tuple[dict, dict]:

@@ -211,7 +211,7 @@ void system_geometry(int n, int& TS, int& T, int& n_pad) {
 int auto_group(ba_handle_t h, long long P, long long E, int batched) {
   // a size measured by ba_autotune for this shape class
   const int tuned = dpv_tuned_group(h, P, E, batched);
-  if (tuned > 0) return tuned;
+  if (tuned > 0) return std::min(tuned, dpv_max_group(h));
   // large graphs: 32 patches per group; small ones: keep about one group
   // per SM or more (measured on the 22-frame odometry window: 16 best)
   if ((long long)P >= 32LL * 2 * h->num_sms) return 32;
@@ -419,7 +419,7 @@ ba_status_t ba_default_options(ba_options_t* opt) {
   opt->z_min = 0.1f;
   opt->d_min = 1e-3f;
   opt->patches_per_group = 0;
-  opt->max_refine = 2;
+  opt->max_refine = 3;
   opt->timeout_cycles = 2000000000LL;
   opt->stream = nullptr;
   opt->residual_pixels = 1;
@@ -433,7 +433,7 @@ ba_status_t ba_create(ba_handle_t* out, const ba_options_t* opt) {
   if (!h) return BA_ERR_OOM;
   if (opt) h->opt = *opt;
   else ba_default_options(&h->opt);
-  if (h->opt.patches_per_group < 0 || h->opt.patches_per_group > DPV_GMAX ||
+  if (h->opt.patches_per_group < 0 || h->opt.patches_per_group > dpv_max_group(h) ||
       (h->opt.precision != BA_FP32 && h->opt.precision != BA_MIXED) || h->opt.max_refine < 0 ||
       (h->opt.residual_pixels != 1 && h->opt.residual_pixels != 9) ||
       h->opt.max_refine > 16) {
@@ -470,7 +470,7 @@ ba_status_t ba_destroy(ba_handle_t h) {
     release(ws->gptr); release(ws->win); release(ws->wlen);
     release(ws->scan); release(ws->S); release(ws->y); release(ws->dx); release(ws->Ct); release(ws->wk);
     release(ws->dd); release(ws->L); release(ws->r64); release(ws->tmpv); release(ws->pmpos); release(ws->pptr);
-    release(ws->pterm); release(ws->posef);
+    release(ws->pterm); release(ws->posef); release(ws->Ct2); release(ws->wk2);
     release(ws->tp_poses); release(ws->tp_patches); release(ws->tp_dx); release(ws->tp_dd);
     release(ws->ad_xb); release(ws->ad_w); release(ws->ad_gd); release(ws->ad_lamd); release(ws->ad_v);
     release(ws->ad_gt); release(ws->ad_gw); release(ws->lg_sync); release(ws->lg_red); release(ws->lg_prob); release(ws->lg_rb); release(ws->fprob); release(ws->gprob);
@@ -592,6 +592,7 @@ ba_status_t ba_set_graph(ba_handle_t h, int N, int P, int E, double* poses, floa
   const long long Gn = h->ngroups + 1;
   const long long scan_need = std::max(dpv_scan_scratch(En + 1), dpv_scan_scratch(dpv_hist_entries(En)));
   if ((s = dpv_grow(h, ws->src, P, "patch table")) || (s = dpv_grow(h, ws->Ct, P, "Ct")) || (s = dpv_grow(h, ws->wk, P, "w")) ||
+      (s = dpv_grow(h, ws->Ct2, P, "Ct pairs")) || (s = dpv_grow(h, ws->wk2, P, "w pairs")) ||
       (s = dpv_grow(h, ws->dd, P, "dd")) || (s = dpv_grow(h, ws->keys0, En, "sort keys")) ||
       (s = dpv_grow(h, ws->keys1, En, "sort keys")) || (s = dpv_grow(h, ws->vals0, En, "sort values")) ||
       (s = dpv_grow(h, ws->vals1, En, "sort values")) || (s = dpv_grow(h, ws->perm, En, "permutation")) ||
@@ -601,7 +602,7 @@ ba_status_t ba_set_graph(ba_handle_t h, int N, int P, int E, double* poses, floa
       (s = dpv_grow(h, ws->gptr, Gn, "groups")) ||
       (s = dpv_grow(h, ws->win, Gn * DPV_WMAX, "windows")) || (s = dpv_grow(h, ws->wlen, Gn, "windows")) ||
       (s = dpv_grow(h, ws->pmpos, En, "patch-major positions")) || (s = dpv_grow(h, ws->pptr, (long long)P + 1, "patch CSR")) ||
-      (s = dpv_grow(h, ws->pterm, 4 * En, "edge depth terms")) || (s = dpv_grow(h, ws->posef, (long long)DPV_POSE_ROW * N, "pose table")) ||
+      (s = dpv_grow(h, ws->pterm, dpv_pterm_width(h) * En, "edge depth terms")) || (s = dpv_grow(h, ws->posef, (long long)DPV_POSE_ROW * N, "pose table")) ||
       (s = dpv_grow(h, ws->fprob, (long long)N + 2, "frame problems")) || (s = dpv_grow(h, ws->gprob, Gn, "group problems")))
     return s;
   // the intrinsics may live in host memory: copied outside any graph
@@ -721,6 +722,7 @@ ba_status_t ba_set_graph_batched(ba_handle_t h, int B, const long long* frame_of
   const long long Gn = h->ngroups + 1;
   const long long scan_need = std::max(dpv_scan_scratch(En + 1), dpv_scan_scratch(dpv_hist_entries(En)));
   if ((s = dpv_grow(h, ws->src, P, "patch table")) || (s = dpv_grow(h, ws->Ct, P, "Ct")) ||
+      (s = dpv_grow(h, ws->Ct2, P, "Ct pairs")) || (s = dpv_grow(h, ws->wk2, P, "w pairs")) ||
       (s = dpv_grow(h, ws->wk, P, "w")) || (s = dpv_grow(h, ws->dd, P, "dd")) ||
       (s = dpv_grow(h, ws->keys0, En, "sort keys")) || (s = dpv_grow(h, ws->keys1, En, "sort keys")) ||
       (s = dpv_grow(h, ws->vals0, En, "sort values")) || (s = dpv_grow(h, ws->vals1, En, "sort values")) ||
@@ -729,7 +731,7 @@ ba_status_t ba_set_graph_batched(ba_handle_t h, int B, const long long* frame_of
       (s = dpv_grow(h, ws->hist, dpv_hist_entries(En), "histograms")) || (s = dpv_grow(h, ws->scan, scan_need, "scan")) ||
       (s = dpv_grow(h, ws->gptr, Gn, "groups")) || (s = dpv_grow(h, ws->win, Gn * DPV_WMAX, "windows")) ||
       (s = dpv_grow(h, ws->wlen, Gn, "windows")) || (s = dpv_grow(h, ws->pmpos, En, "patch-major positions")) ||
-      (s = dpv_grow(h, ws->pptr, (long long)P + 1, "patch CSR")) || (s = dpv_grow(h, ws->pterm, 4 * En, "edge depth terms")) ||
+      (s = dpv_grow(h, ws->pptr, (long long)P + 1, "patch CSR")) || (s = dpv_grow(h, ws->pterm, dpv_pterm_width(h) * En, "edge depth terms")) ||
       (s = dpv_grow(h, ws->posef, (long long)DPV_POSE_ROW * N, "pose table")) ||
       (s = dpv_grow(h, ws->fprob, (long long)N + B + 1, "frame problems")) ||
       (s = dpv_grow(h, ws->gprob, Gn, "group problems")) || (s = dpv_grow(h, ws->mii, En, "edge frames")) ||

@@ -566,6 +566,13 @@ ba_status_t assemble_impl(ba_handle_t h, int it, const double* v_ext, const floa
   }
   double* cost = it < 0 ? nullptr : ws->cost + (it < ws->cost_cap ? it : ws->cost_cap - 1);
   dpv_prof_begin(h, BA_KERNEL_ASSEMBLE);
+  if (h->opt.precision == BA_MIXED) {  // the double-float linearisation (assemble_df.cu)
+    ba_status_t s2 = dpv_assemble_dd(h, cost, w_ext);
+    dpv_prof_end(h);
+    if (s2) return s2;
+    DPV_CUDA(h, cudaGetLastError());
+    return BA_OK;
+  }
   auto kern = h->opt.residual_pixels == 9 ? k_assemble<9> : k_assemble<1>;
   DPV_CUDA(h, dpv_launch_pdl(kern, dim3(h->ngroups), dim3(AS_THREADS),
                              assemble_smem_bytes(h->G, h->opt.residual_pixels), h->stream, h->G, h->P, ws->fdx.p,

@@ -102,7 +102,7 @@ ba_status_t ba_autotune(ba_handle_t h, int iters, int fixed_poses, int reps, int
   int best = 0, nc = 0;
   float best_ms = 0.f;
   for (int G : CANDIDATES) {
-    if (G > DPV_GMAX) continue;
+    if (G > dpv_max_group(h)) continue;
     float ms = -1.f;  // infeasible
     ba_status_t c = rebind(G);
     // warm-up: one eager step, and with graph replay on also the capture

@@ -12,6 +12,7 @@
 // ---------------------------------------------------------------------------
 #define DPV_WMAX 64          // frames in one group window (slots fit in 8 bits)
 #define DPV_GMAX 64          // patches per group
+#define DPV_GMAX_DD 32       // patches per group of the double-float (BA_MIXED) assembly
 #define DPV_SMALL_N 256      // pose systems up to this size use the one-CTA solver
 #define DPV_TILE 64          // tile edge of the blocked pose system (large n)
 #define DPV_RMAX 64          // (source, target) runs in one group
@@ -187,8 +188,10 @@ struct Workspace {
   DBuf<double> y;                 // [n_pad]
   DBuf<double> dx;                // [n_pad]
   DBuf<float> Ct, wk, dd;         // [P]
+  DBuf<float2> Ct2, wk2;          // [P] Ct and w as double-float pairs (BA_MIXED)
   DBuf<float> posef;              // [N][16] R (9), camera centre hi (3), lo (3)
-  DBuf<float4> pterm;             // [E][4] per-edge depth terms, patch-major (see assemble.cu)
+  DBuf<float4> pterm;             // [E][4] per-edge depth terms, patch-major (see assemble.cu);
+                                  // [E][8] as double-float pairs with BA_MIXED (assemble_df.cu)
   // blocked solver
   DBuf<float> L;                  // factor (large n)
   DBuf<int> lg_sync;              // large solver: tile versions, row flags, task counter, grid barrier
@@ -267,6 +270,17 @@ long long dpv_hist_entries(long long m);
 // of the previous iteration re-zeroed S and y, the retraction refreshed the table)
 ba_status_t dpv_assemble(ba_handle_t h, int it, int skip_init);
 ba_status_t dpv_assemble_ext(ba_handle_t h, int it, const double* v_ext, const float* w_ext);
+ba_status_t dpv_assemble_dd(ba_handle_t h, double* cost, const float* w_ext);  // assemble_df.cu
+// largest patches-per-group the handle's assembly kernel supports
+inline int dpv_max_group(ba_handle_t h) { return h->opt.precision == BA_MIXED ? DPV_GMAX_DD : DPV_GMAX; }
+// The solvers stop once the estimated error left in the pose step is below
+// this fraction of it: 1e-7 with the FP32 linearisation, 1e-10 with the
+// double-float one (BA_MIXED), whose steps are compared with an FP64
+// solution on ill-conditioned loop-closure systems (a 1e-7 error of the step
+// there moves near-clamp inverse depths by ~2e-5, relative).
+inline float dpv_solve_tol(ba_handle_t h) { return h->opt.precision == BA_MIXED ? 1e-10f : 1e-7f; }
+// pterm float4 per edge for the handle's precision
+inline int dpv_pterm_width(ba_handle_t h) { return h->opt.precision == BA_MIXED ? 8 : 4; }
 ba_status_t dpv_ensure_system(ba_handle_t h, int fixed);
 ba_status_t dpv_ensure_generic_system(ba_handle_t h, int n);  // one dense system of n unknowns
 ba_status_t dpv_tape_reserve(ba_handle_t h, int iters);

@@ -30,7 +30,7 @@
 // the rows above it (each solved value is published with its pass number in
 // one 64-bit word), the backward solve for the rows below; grid barriers
 // separate the phases; the products with S run in double-float, until the
-// estimated error left in x is below 1e-7 of it.
+// estimated error left in x is below 1e-7 of it (1e-10 with BA_MIXED).
 #include "internal.cuh"
 #include "tcgen05.cuh"
 
@@ -399,7 +399,7 @@ __device__ bool tc_gemm64(TcState& ts, const unsigned char* a_hi, const unsigned
     tc_mma_tf32(ts.tmem, al, bh, idesc, 1);
   }
   tc_commit(&ts.bar_mma);
-  if (!tc_mbar_wait(&ts.bar_mma, ts.ph_mma, timeout)) {
+  if (!tc_mbar_wait(&ts.bar_mma, ts.ph_mma, tc_hw_bound(timeout))) {
     ts.bad = 2;
     return false;
   }
@@ -571,7 +571,7 @@ __device__ bool task_update_tc(unsigned char* tcbuf, TcState& ts, float* A, cons
   for (int q = 0; q < 16; ++q)
     cv[q] = mine ? __ldcg(reinterpret_cast<const float4*>(ct) + q) : make_float4(0.f, 0.f, 0.f, 0.f);
   if (tid == 0) {
-    if (!tc_mbar_wait(&ts.bar_ld, ts.ph_ld, timeout)) {
+    if (!tc_mbar_wait(&ts.bar_ld, ts.ph_ld, tc_hw_bound(timeout))) {
       ts.bad = 1;
     } else {
       ts.ph_ld ^= 1u;
@@ -590,7 +590,7 @@ __device__ bool task_update_tc(unsigned char* tcbuf, TcState& ts, float* A, cons
         tc_mma_tf32(ts.tmem, al, bh, idesc, 1);
       }
       tc_commit(&ts.bar_mma);
-      if (tc_mbar_wait(&ts.bar_mma, ts.ph_mma, timeout))
+      if (tc_mbar_wait(&ts.bar_mma, ts.ph_mma, tc_hw_bound(timeout)))
         ts.ph_mma ^= 1u;
       else
         ts.bad = 2;
@@ -797,7 +797,8 @@ done:
   // shared and tensor memory go back once no copy and no MMA of this CTA is in
   // flight: after a timeout, wait (bounded) for the outstanding phase first
   __syncthreads();
-  if (threadIdx.x == 0 && ts.bad) tc_mbar_wait(ts.bad == 1 ? &ts.bar_ld : &ts.bar_mma, ts.bad == 1 ? ts.ph_ld : ts.ph_mma, timeout);
+  if (threadIdx.x == 0 && ts.bad) tc_mbar_wait(ts.bad == 1 ? &ts.bar_ld : &ts.bar_mma, ts.bad == 1 ? ts.ph_ld : ts.ph_mma,
+                                          tc_hw_bound(timeout));
   tc_fence_before_sync();
   __syncthreads();
   tc_fence_after_sync();
@@ -959,17 +960,17 @@ __device__ void tile_symv(const SymvRegs& g, const DFp* vr, const DFp* vc, bool 
 }
 
 // System p finished after iteration s >= 1: the estimated error left in its
-// x is below 1e-7 of it (the last step bounds the previous iterate's error;
+// x is below tol of it (the last step bounds the previous iterate's error;
 // the current one's is about rho c_s with rho ~ c_s / c_{s-1}).  A finished
 // system takes no further part, so its later maxima stay 0 and it stays
 // finished.  The maxima of a completed iteration are final (grid barrier), so
 // every CTA reaches the same decision.
-__device__ __forceinline__ bool sys_finished(const int* conv, int nsys, int p, int s) {
+__device__ __forceinline__ bool sys_finished(const int* conv, int nsys, int p, int s, float tol) {
   if (s < 1) return false;
   const float cm = __int_as_float(__ldcg(conv + 2 * (s * nsys + p)));
   const float xm = __int_as_float(__ldcg(conv + 2 * (s * nsys + p) + 1));
   const float cp = __int_as_float(__ldcg(conv + 2 * ((s - 1) * nsys + p)));
-  return cm <= 1e-7f * xm || cm * cm <= 1e-7f * xm * cp;
+  return cm <= tol * xm || cm * cm <= tol * xm * cp;
 }
 
 // Triangular solves and preconditioned conjugate gradients of all large
@@ -986,11 +987,11 @@ __device__ __forceinline__ bool sys_finished(const int* conv, int nsys, int p, i
 // q = c, c + grid, ... of each; forward rows wait for the rows above them in
 // their system, the backward rows for the rows below; grid barriers separate
 // the phases.  The iterations stop once every system's estimated error left
-// in x is below 1e-7 of it.
+// in x is below tol of it (dpv_solve_tol).
 __global__ void __launch_bounds__(LG_THREADS, 2) k_lg_solve(const LgProb* __restrict__ probs, int nsys,
                                                             const int* __restrict__ rb_sys, int R, int sweeps,
-                                                            int* bar, int* conv, double* red, int* status,
-                                                            long long timeout) {
+                                                            int* bar, int* conv, double* red, float tol,
+                                                            int* status, long long timeout) {
   __shared__ float acc[NB], vj[NB], prod[NB];
   __shared__ float part[16][NB + 1];
   __shared__ DFp dpart[16][NB];
@@ -1006,7 +1007,7 @@ __global__ void __launch_bounds__(LG_THREADS, 2) k_lg_solve(const LgProb* __rest
     // behind another's
     for (int q = blockIdx.x; q < R; q += gridDim.x) {
       const int r = rb_sys[R + q];
-      if (sys_finished(conv, nsys, rb_sys[r], sweep - 1)) continue;
+      if (sys_finished(conv, nsys, rb_sys[r], sweep - 1, tol)) continue;
       const LgProb& P = probs[rb_sys[r]];
       const int i = r - P.rb0;
       if (tid < NB) acc[tid] = __ldcg(P.rhs + i * NB + tid);
@@ -1038,7 +1039,7 @@ __global__ void __launch_bounds__(LG_THREADS, 2) k_lg_solve(const LgProb* __rest
     for (int q = blockIdx.x; q < R; q += gridDim.x) {
       const int r = rb_sys[2 * R + q];
       const int sy = rb_sys[r];
-      if (sys_finished(conv, nsys, sy, sweep - 1)) continue;
+      if (sys_finished(conv, nsys, sy, sweep - 1, tol)) continue;
       const LgProb& P = probs[sy];
       const int i = r - P.rb0, T = P.T;
       // the forward result of this row (solved by whichever CTA owned it in
@@ -1107,7 +1108,7 @@ __global__ void __launch_bounds__(LG_THREADS, 2) k_lg_solve(const LgProb* __rest
     {
       DFp sig{0.f, 0.f};
       for (int sy = 0; sy < nsys; ++sy) {
-        if (sys_finished(conv, nsys, sy, sweep - 1)) continue;
+        if (sys_finished(conv, nsys, sy, sweep - 1, tol)) continue;
         const LgProb& P = probs[sy];
         const double beta =
             sweep > 1 ? __ldcg(red + 2 * (sweep * nsys + sy)) / __ldcg(red + 2 * ((sweep - 1) * nsys + sy)) : 0.0;
@@ -1162,7 +1163,7 @@ __global__ void __launch_bounds__(LG_THREADS, 2) k_lg_solve(const LgProb* __rest
     // ---- updates: r (iteration 0: r = s (y - u)), or alpha steps of x and r
     for (int r = blockIdx.x; r < R; r += gridDim.x) {
       const int sy = rb_sys[r];
-      if (sys_finished(conv, nsys, sy, sweep - 1)) continue;
+      if (sys_finished(conv, nsys, sy, sweep - 1, tol)) continue;
       const LgProb& P = probs[sy];
       const int q = (r - P.rb0) * NB + tid;
       float cmax = 0.f, xmax = 0.f;
@@ -1201,11 +1202,11 @@ __global__ void __launch_bounds__(LG_THREADS, 2) k_lg_solve(const LgProb* __rest
     }
     if (!grid_barrier(bar, gridDim.x, status, timeout)) return;
     if (sweep > 0) {
-      // per system: the error left in x is below 1e-7 of it (the step bounds
+      // per system: the error left in x is below tol of it (the step bounds
       // the previous iterate's error; the current one's is about rho c_s with
       // rho ~ c_s / c_{s-1})
       bool done = true;
-      for (int p = 0; p < nsys && done; ++p) done = sys_finished(conv, nsys, p, sweep);
+      for (int p = 0; p < nsys && done; ++p) done = sys_finished(conv, nsys, p, sweep, tol);
       if (done) break;  // the same decision in every CTA
     }
   }
@@ -1507,8 +1508,9 @@ ba_status_t dpv_solve_large(ba_handle_t h, int refine) {
     int sweeps = refine + 1;
     int nsys_ = nsys, R_ = R;
     const int* rb = ws->lg_rb.p;
-    void* args[] = {(void*)&dprobs, (void*)&nsys_, (void*)&rb,  (void*)&R_,     (void*)&sweeps,
-                    (void*)&bar,    (void*)&conv,  (void*)&red, (void*)&status, (void*)&timeout};
+    float tol = dpv_solve_tol(h);
+    void* args[] = {(void*)&dprobs, (void*)&nsys_, (void*)&rb,  (void*)&R_,     (void*)&sweeps, (void*)&bar,
+                    (void*)&conv,   (void*)&red,   (void*)&tol, (void*)&status, (void*)&timeout};
     DPV_CUDA(h, launch_cooperative((const void*)k_lg_solve, grid, 0, st, args));
     ++h->launches;
   }

@@ -58,7 +58,7 @@ template <int NQ>  // NP = 32 NQ
 __global__ void __launch_bounds__(small_threads(NQ)) k_solve_small(
     const SysDesc* __restrict__ sysd, const int* __restrict__ list, int n_direct, double* __restrict__ S_,
     double* __restrict__ y_, double* __restrict__ dx_, float* __restrict__ dxf_, int refine32, int refine64,
-    float lambda_p, int reset, int* status) {
+    float tol, float lambda_p, int reset, int* status) {
   constexpr int NP = 32 * NQ;
   constexpr int NT = small_threads(NQ);
   constexpr int NWARP = NT / 32;
@@ -335,7 +335,7 @@ __global__ void __launch_bounds__(small_threads(NQ)) k_solve_small(
     }
     __syncthreads();
     // x += correction (double-float); stop once the correction is below
-    // 1e-7 of the solution (refinement converged)
+    // tol of the solution (refinement converged)
     float cmax = 0.f, xmax = 0.f;
     for (int q = tid; q < NP; q += NT) {
       DF a = {xhi[q], xlo[q]};
@@ -362,11 +362,11 @@ __global__ void __launch_bounds__(small_threads(NQ)) k_solve_small(
         cm = fmaxf(cm, red[w]);
         xm = fmaxf(xm, red[NWARP + w]);
       }
-      // stop once the error left in x is below 1e-7 of it: the correction
+      // stop once the error left in x is below tol of it: the correction
       // bounds the previous iterate's error, and the current one's is about
       // rho c_s with the contraction rate rho ~ c_s / c_{s-1}
       // (the same decision in every thread)
-      if (sweep > 0 && (cm <= 1e-7f * xm || cm * cm <= 1e-7f * xm * cprev)) break;
+      if (sweep > 0 && (cm <= tol * xm || cm * cm <= tol * xm * cprev)) break;
       cprev = cm;
     }
     // residual rho = y - S x
@@ -448,7 +448,7 @@ ba_status_t launch_small(ba_handle_t h, cudaStream_t st, int count, const int* l
   }
   DPV_CUDA(h, dpv_launch_pdl(k_solve_small<NQ>, dim3(count), dim3(small_threads(NQ)), smem, st, h->ws->sysd.p, list,
                              0, h->ws->S.p, h->ws->y.p, h->ws->dx.p, h->ws->tmpv.p, refine32, refine64,
-                             h->opt.lambda_pose, reset, h->ws->status));
+                             dpv_solve_tol(h), h->opt.lambda_pose, reset, h->ws->status));
   ++h->launches;
   DPV_CUDA(h, cudaGetLastError());
   return BA_OK;
@@ -530,7 +530,8 @@ ba_status_t launch_small_raw(cudaStream_t st, int n, const double* S, const doub
     return BA_ERR_CUDA;
   // reset = 0: the kernel only reads S and y
   k_solve_small<NQ><<<1, small_threads(NQ), smem, st>>>(nullptr, nullptr, n, const_cast<double*>(S),
-                                                        const_cast<double*>(y), dx, dxf, 0, refine, 0.f, 0, status);
+                                                        const_cast<double*>(y), dx, dxf, 0, refine, 1e-7f, 0.f, 0,
+                                                        status);
   return cudaGetLastError() == cudaSuccess ? BA_OK : BA_ERR_CUDA;
 }
 }  // namespace

@@ -9,6 +9,7 @@
 // kernel wrote in patch-major order (J_i^T W Jd, J_j^T W Jd for every edge,
 // 64 bytes per edge, contiguous per patch), so it needs neither the poses nor
 // a second linearisation.
+#include "dfloat.cuh"
 #include "internal.cuh"
 
 #include "retract.cuh"
@@ -78,6 +79,67 @@ __global__ void __launch_bounds__(BS_THREADS) k_backsub(
   }
 }
 
+// The same in double-float (the BA_MIXED path): the depth terms are pairs
+// (128 bytes per edge, assemble_df.cu), the pose step is read in FP64 and
+// split into pairs, Ct and w are pairs, and the new depth d + dd is rounded
+// to float once.
+__global__ void __launch_bounds__(BS_THREADS) k_backsub_dd(
+    int P, int G, const int* __restrict__ fdx, float d_min, const int* __restrict__ pptr,
+    const float4* __restrict__ pterm, const int* __restrict__ win, const double* __restrict__ dxv,
+    const float2* __restrict__ Ct2, const float2* __restrict__ wk2, const float* __restrict__ w_ext,
+    float* __restrict__ patches, float* __restrict__ dd_out, int N, int retract, const double* __restrict__ dx,
+    double* __restrict__ poses, float* __restrict__ posef, int write_depth, const int* status) {
+  dpv_pdl_enter();
+  if (dpv_status(status)) return;
+  const int lane = threadIdx.x & 31;
+  if (retract && threadIdx.x == 0 && (int)blockIdx.x < N) {
+    const int f = blockIdx.x;
+    const int o = fdx[f];
+    if (o >= 0) {
+      dpv_se3_retract(dx + o, poses + 7 * (size_t)f);
+      if (posef) dpv_pose_table_row(poses + 7 * (size_t)f, posef + DPV_POSE_ROW * (size_t)f);
+    }
+  }
+  const int k = blockIdx.x * BS_WARPS + (threadIdx.x >> 5);
+  if (k >= P) return;
+  const int* wf = win + (k / G) * DPV_WMAX;
+  DF acc = {0.f, 0.f};
+  for (int p = pptr[k] + lane; p < pptr[k + 1]; p += 32) {
+    const float4* t4 = pterm + 8 * (size_t)p;
+    const int sl = __float_as_int(t4[7].x);
+    const int fi = fdx[wf[sl & 0xff]], fj = fdx[wf[sl >> 8]];
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+      const int fo = side == 0 ? fi : fj;
+      if (fo < 0) continue;
+      const float4* e4 = t4 + 3 * side;
+      const double* x = dxv + fo;
+#pragma unroll
+      for (int h2 = 0; h2 < 3; ++h2) {
+        const float4 v = e4[h2];
+        const float2 x0 = dpv_d2df_bits(x[2 * h2]), x1 = dpv_d2df_bits(x[2 * h2 + 1]);
+        dd_acc(acc, DF{-v.x, -v.y}, DF{x0.x, x0.y});
+        dd_acc(acc, DF{-v.z, -v.w}, DF{x1.x, x1.y});
+      }
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) dd_acc_add(acc, DF{__shfl_xor_sync(0xffffffffu, acc.hi, o),
+                                                     __shfl_xor_sync(0xffffffffu, acc.lo, o)});
+  if (lane == 0) {
+    const DF wv = w_ext ? DF{w_ext[k], 0.f} : dd_ld(wk2[k]);
+    const DF ddk = dd_div(dd_add(dd_norm(acc), wv), dd_ld(Ct2[k]));
+    dd_out[k] = ddk.hi + ddk.lo;
+    if (write_depth) {
+      float* pk = patches + 27 * (size_t)k;
+      const DF s = dd_add_f(ddk, pk[22]);
+      const float dn = fmaxf(s.hi + s.lo, d_min);
+#pragma unroll
+      for (int m = 18; m < 27; ++m) pk[m] = dn;
+    }
+  }
+}
+
 unsigned backsub_grid(ba_handle_t h, int retract) {
   const long long wb = ((long long)h->P + BS_WARPS - 1) / BS_WARPS;
   const long long rb = retract ? (long long)h->N : 0;
@@ -90,6 +152,16 @@ unsigned backsub_grid(ba_handle_t h, int retract) {
 // poses and their rows of the linearisation table.
 ba_status_t dpv_backsub(ba_handle_t h, int retract) {
   Workspace* ws = h->ws;
+  if (h->opt.precision == BA_MIXED) {
+    DPV_CUDA(h, dpv_launch_pdl(k_backsub_dd, dim3(backsub_grid(h, retract)), dim3(BS_THREADS), 0, h->stream, h->P,
+                               h->G, ws->fdx.p, h->opt.d_min, ws->pptr.p, ws->pterm.p, ws->win.p,
+                               (const double*)ws->dx.p, (const float2*)ws->Ct2.p, (const float2*)ws->wk2.p,
+                               (const float*)nullptr, h->patches, ws->dd.p, h->N, retract, (const double*)ws->dx.p,
+                               h->poses, ws->posef.p, 1, (const int*)ws->status));
+    ++h->launches;
+    DPV_CUDA(h, cudaGetLastError());
+    return BA_OK;
+  }
   DPV_CUDA(h, dpv_launch_pdl(k_backsub, dim3(backsub_grid(h, retract)), dim3(BS_THREADS), 0, h->stream, h->P, h->G,
                              ws->fdx.p, h->opt.d_min, ws->pptr.p, ws->pterm.p, ws->win.p, ws->tmpv.p, ws->Ct.p,
                              ws->wk.p, h->patches, ws->dd.p, h->N, retract, ws->dx.p, h->poses, ws->posef.p, 1,
@@ -103,6 +175,14 @@ ba_status_t dpv_backsub(ba_handle_t h, int retract) {
 // with lambda_a in the solver's output; no state is changed.
 ba_status_t dpv_backsub_ext(ba_handle_t h, const float* w_ext, float* out) {
   Workspace* ws = h->ws;
+  if (h->opt.precision == BA_MIXED) {
+    k_backsub_dd<<<backsub_grid(h, 0), BS_THREADS, 0, h->stream>>>(
+        h->P, h->G, ws->fdx.p, h->opt.d_min, ws->pptr.p, ws->pterm.p, ws->win.p, ws->dx.p, ws->Ct2.p, ws->wk2.p,
+        w_ext, h->patches, out, h->N, 0, ws->dx.p, h->poses, nullptr, 0, ws->status);
+    ++h->launches;
+    DPV_CUDA(h, cudaGetLastError());
+    return BA_OK;
+  }
   k_backsub<<<backsub_grid(h, 0), BS_THREADS, 0, h->stream>>>(
       h->P, h->G, ws->fdx.p, h->opt.d_min, ws->pptr.p, ws->pterm.p, ws->win.p, ws->tmpv.p, ws->Ct.p, w_ext,
       h->patches, out, h->N, 0, ws->dx.p, h->poses, nullptr, 0, ws->status);
