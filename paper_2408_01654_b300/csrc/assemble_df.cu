@@ -8,11 +8,16 @@
 //
 //   phase 0  the double-float relative pose of each (source, target) run;
 //   phase 1  one warp per run, one lane per edge: the double-float residual
-//            and Jacobians (dfloat.cuh), the sqrt(w)-scaled rows staged in
-//            shared memory as pairs, the run's 6x6 blocks and vectors summed
-//            as double-float products; the edge's depth terms (J^T W Jd,
-//            Jd^T W Jd, Jd^T W r) written to the patch-major table as pairs;
-//   phase 2  one warp per patch: e_k, C_k, w_k summed as pairs (edges of one
+//            and target-pose Jacobian J_j (dfloat.cuh), the sqrt(w)-scaled
+//            rows [J_j, r] staged in shared memory as pairs, and the run's
+//            H_jj (21 entries) and v_j (6) summed as double-float products,
+//            one entry per lane.  Every edge of a run shares T_ij and
+//            J_i = -J_j Ad(T_ij), so the rest of the run's blocks follow once
+//            per run: H_ij = -Ad^T H_jj, H_ii = -H_ij Ad, v_i = -Ad^T v_j
+//            (a third of the per-edge products of summing all 90 entries).
+//            The edge's depth terms e_j = J_j^T W Jd, e_i = -Ad^T e_j,
+//            Jd^T W Jd and Jd^T W r go to the patch-major table as pairs;
+//   phase 2  16 lanes per patch: e_k, C_k, w_k summed as pairs (edges of one
 //            patch that share a target frame are summed by the first lane of
 //            each such set, found with __match_any_sync), the column
 //            e_k / sqrt(Ct_k) formed in double-float;
@@ -20,9 +25,10 @@
 //            B_ab - sum_k e_a e_b / Ct_k in double-float, added to the global
 //            FP64 S with red.global.add.f64 (likewise y).
 //
-// Shared memory per CTA is ~213 KB at G = 32 (the pairs double the staging
-// and the window columns), so the path supports G <= DPV_GMAX_DD patches per
-// group and runs 256 threads.  The patch-major table holds 128 bytes per edge
+// Shared memory per CTA is ~219 KB at G = 32 (the pairs double the window
+// columns), so the path supports G <= DPV_GMAX_DD patches per group; it runs
+// 512 threads (one CTA per SM, at most 128 registers per thread).  The
+// patch-major table holds 128 bytes per edge
 // (two float4 per 6-vector pair of e_i, e_j; C, w; the slots), read again by
 // the double-float back-substitution (update.cu).
 #include "dfloat.cuh"
@@ -31,14 +37,15 @@
 
 namespace {
 
-constexpr int AD_THREADS = 256;
+constexpr int AD_THREADS = 512;
 constexpr int AD_WARPS = AD_THREADS / 32;
 constexpr int EH_STRIDE = 6 * DPV_WMAX + 1;  // pairs per patch column of E_hat
 constexpr int NV = 90;                       // run block entries: Hii 21, Hij 36, Hjj 21, vi 6, vj 6
-constexpr int ROWP = 27;                     // staged pairs per edge: 13 per residual component + pad
+constexpr int NJ = 27;                       // per-edge run entries: Hjj 21 (lower), vj 6
+constexpr int ROWP = 15;                     // staged pairs per edge: [Jj, r] per residual component + pad
 constexpr int RPOSE = 42;                    // floats per run's relative pose: R, t, [t]x R as pairs
 
-__constant__ unsigned char c_qa[NV], c_qb[NV];
+__constant__ unsigned char c_qa[NJ], c_qb[NJ];
 
 __host__ __device__ constexpr int tri(int r, int c) { return r * (r + 1) / 2 + c; }
 
@@ -47,10 +54,11 @@ __host__ __device__ constexpr int tri(int r, int c) { return r * (r + 1) / 2 + c
 __host__ __device__ constexpr int pd_stride(int pix) { return pix == 1 ? 5 : 37; }
 
 // phase-2b tables (window run map, diagonal and y sums as pairs) and the
-// phase-2 duplicate-target scratch live in the phase-1 staging rows
+// phase-2 scratch of the lanes' target terms live in the phase-1 staging rows
 static_assert(DPV_WMAX * DPV_WMAX + 8 * (DPV_WMAX * 21 + DPV_WMAX * 6) <= 8 * AD_WARPS * 32 * ROWP,
               "phase-2b tables exceed the staging space");
-static_assert(AD_WARPS * 32 * 12 <= 2 * AD_WARPS * 32 * ROWP, "phase-2 scratch exceeds the staging space");
+static_assert(2 * 36 + 6 <= 32 * ROWP, "run-transform scratch exceeds a warp's staging rows");
+static_assert(32 * 12 <= 2 * 32 * ROWP, "phase-2 scratch exceeds a warp's staging rows");
 
 size_t assemble_dd_smem_bytes(int G, int pix) {
   return sizeof(float2) * ((size_t)DPV_RMAX * NV + (size_t)G * EH_STRIDE + 2 * G + (size_t)AD_WARPS * 32 * ROWP) +
@@ -65,12 +73,8 @@ __device__ __forceinline__ int tri_row(int t) {
   return a;
 }
 
-__device__ __forceinline__ DF shfl_dd(DF v, int o) {
-  return DF{__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
-}
-
 template <int PIX>
-__global__ void __launch_bounds__(AD_THREADS) k_assemble_dd(
+__global__ void __launch_bounds__(AD_THREADS, 1) k_assemble_dd(
     int G, int P, const int* __restrict__ fdx, const int* __restrict__ gprob, const SysDesc* __restrict__ sysd,
     float lambda_d, float z_min, const int* __restrict__ gptr, const int* __restrict__ grun,
     const int* __restrict__ gnr, const unsigned* __restrict__ eslot, const int* __restrict__ perm,
@@ -154,30 +158,14 @@ __global__ void __launch_bounds__(AD_THREADS) k_assemble_dd(
   // ---- phase 1: one warp per run ------------------------------------------
   float cst = 0.f;
   float2* rw = rows + wid * 32 * ROWP;
-  int pa[3], pb[3];
-#pragma unroll
-  for (int t = 0; t < 3; ++t) {
-    const int q = lane + 32 * t;
-    pa[t] = q < NV ? c_qa[q] : 0;
-    pb[t] = q < NV ? c_qb[q] : 0;
-  }
+  const bool own = lane < NJ;  // this lane's run entry: Hjj (lower) or vj
+  const int pa = own ? c_qa[lane] : 0, pb = own ? c_qb[lane] : 0;
   for (int r = wid; r < nruns; r += AD_WARPS) {
     const int s0 = gs + runptr[r], s1 = gs + runptr[r + 1];
     const int si = rsl[r] & 0xff, sj = rsl[r] >> 8;
     const bool self_run = si == sj;
-    RelPoseDD T;
-    {
-      const float* o = rpose + RPOSE * r;
-#pragma unroll
-      for (int m = 0; m < 9; ++m) T.R[m] = DF{o[2 * m], o[2 * m + 1]};
-#pragma unroll
-      for (int m = 0; m < 3; ++m) T.t[m] = DF{o[18 + 2 * m], o[19 + 2 * m]};
-#pragma unroll
-      for (int m = 0; m < 9; ++m) T.txR[m] = DF{o[24 + 2 * m], o[25 + 2 * m]};
-    }
-    DF acc[3];
-#pragma unroll
-    for (int t = 0; t < 3; ++t) acc[t] = DF{0.f, 0.f};
+    const float* T = rpose + RPOSE * r;
+    DF acc0 = {0.f, 0.f}, acc1 = {0.f, 0.f};  // the two residual components
     for (int b = s0; b < s1; b += 32) {
       const int s = b + lane;
       const int nb = min(32, s1 - b);
@@ -189,9 +177,9 @@ __global__ void __launch_bounds__(AD_THREADS) k_assemble_dd(
         e = perm[s];
         wt = *reinterpret_cast<const float2*>(weights + 2 * (size_t)e);
       }
-      DF Ei[6], Ej[6], Ce = {0.f, 0.f}, we = {0.f, 0.f};
+      DF Ej[6], Ce = {0.f, 0.f}, we = {0.f, 0.f};
 #pragma unroll
-      for (int m = 0; m < 6; ++m) Ei[m] = Ej[m] = DF{0.f, 0.f};
+      for (int m = 0; m < 6; ++m) Ej[m] = DF{0.f, 0.f};
 #pragma unroll 1
       for (int px = 0; px < PIX; ++px) {
         if (s < s1) {
@@ -210,10 +198,10 @@ __global__ void __launch_bounds__(AD_THREADS) k_assemble_dd(
             dd_acc(Ce, wJd1, L.Jd[1]);
             dd_acc(we, wJd0, L.r[0]);
             dd_acc(we, wJd1, L.r[1]);
+            dd_acc(Ej[0], L.Jj[0][0], wJd0);
+            dd_acc(Ej[1], L.Jj[1][1], wJd1);
 #pragma unroll
-            for (int m = 0; m < 6; ++m) {
-              dd_acc(Ei[m], L.Ji[0][m], wJd0);
-              dd_acc(Ei[m], L.Ji[1][m], wJd1);
+            for (int m = 2; m < 6; ++m) {
               dd_acc(Ej[m], L.Jj[0][m], wJd0);
               dd_acc(Ej[m], L.Jj[1][m], wJd1);
             }
@@ -221,42 +209,35 @@ __global__ void __launch_bounds__(AD_THREADS) k_assemble_dd(
             for (int c = 0; c < 2; ++c) {
               const DF sw = dd_sqrt(DF{wc[c], 0.f});
 #pragma unroll
-              for (int m = 0; m < 6; ++m) {
-                row[13 * c + m] = dd_st(dd_mul(sw, L.Ji[c][m]));
-                row[13 * c + 6 + m] = dd_st(dd_mul(sw, L.Jj[c][m]));
-              }
-              row[13 * c + 12] = dd_st(dd_mul(sw, L.r[c]));
+              for (int m = 0; m < 6; ++m) row[7 * c + m] = dd_st(dd_mul(sw, L.Jj[c][m]));
+              row[7 * c + 6] = dd_st(dd_mul(sw, L.r[c]));
             }
           } else {
 #pragma unroll
-            for (int m = 0; m < 26; ++m) row[m] = make_float2(0.f, 0.f);
+            for (int m = 0; m < 14; ++m) row[m] = make_float2(0.f, 0.f);
           }
         }
         __syncwarp();
-        for (int q = 0; q < nb; ++q) {
-          const float2* re = rw + q * ROWP;
-#pragma unroll
-          for (int t = 0; t < 3; ++t) {
-            if (lane + 32 * t < NV) {
-              dd_acc(acc[t], dd_ld(re[pa[t]]), dd_ld(re[pb[t]]));
-              dd_acc(acc[t], dd_ld(re[13 + pa[t]]), dd_ld(re[13 + pb[t]]));
-            }
+        if (own) {
+          for (int q = 0; q < nb; ++q) {
+            const float2* re = rw + q * ROWP;
+            dd_acc(acc0, dd_ld(re[pa]), dd_ld(re[pb]));
+            dd_acc(acc1, dd_ld(re[7 + pa]), dd_ld(re[7 + pb]));
           }
         }
         __syncwarp();
       }
       if (s < s1) {
-        float4* pt = pterm + 8 * (size_t)pmpos[s];
 #pragma unroll
-        for (int m = 0; m < 6; ++m) {
-          Ei[m] = dd_norm(Ei[m]);
-          Ej[m] = dd_norm(Ej[m]);
-        }
+        for (int m = 0; m < 6; ++m) Ej[m] = dd_norm(Ej[m]);
+        DF Ei[6];
+        dpv_adT_dd(T, Ej, Ei);  // e_i = -Ad^T e_j
         Ce = dd_norm(Ce);
         we = dd_norm(we);
-        pt[0] = make_float4(Ei[0].hi, Ei[0].lo, Ei[1].hi, Ei[1].lo);
-        pt[1] = make_float4(Ei[2].hi, Ei[2].lo, Ei[3].hi, Ei[3].lo);
-        pt[2] = make_float4(Ei[4].hi, Ei[4].lo, Ei[5].hi, Ei[5].lo);
+        float4* pt = pterm + 8 * (size_t)pmpos[s];
+        pt[0] = make_float4(-Ei[0].hi, -Ei[0].lo, -Ei[1].hi, -Ei[1].lo);
+        pt[1] = make_float4(-Ei[2].hi, -Ei[2].lo, -Ei[3].hi, -Ei[3].lo);
+        pt[2] = make_float4(-Ei[4].hi, -Ei[4].lo, -Ei[5].hi, -Ei[5].lo);
         pt[3] = make_float4(Ej[0].hi, Ej[0].lo, Ej[1].hi, Ej[1].lo);
         pt[4] = make_float4(Ej[2].hi, Ej[2].lo, Ej[3].hi, Ej[3].lo);
         pt[5] = make_float4(Ej[4].hi, Ej[4].lo, Ej[5].hi, Ej[5].lo);
@@ -264,11 +245,50 @@ __global__ void __launch_bounds__(AD_THREADS) k_assemble_dd(
         pt[7] = make_float4(__int_as_float(si | (sj << 8)), 0.f, 0.f, 0.f);
       }
     }
-#pragma unroll
-    for (int t = 0; t < 3; ++t) {
-      const int q = lane + 32 * t;
-      if (q < NV) runv[r * NV + q] = dd_st(dd_norm(acc[t]));
+    // the run's blocks from Hjj and vj: Hij = -Ad^T Hjj, Hii = -Hij Ad
+    // (row a: -Ad^T applied to row a of Hij), vi = -Ad^T vj; in the warp's
+    // staging rows: Hjj full [36], vj [6], Hij [36]
+    const DF hq = dd_norm(dd_add(acc0, acc1));
+    float2* hs = rw;
+    __syncwarp();
+    if (own) {
+      if (lane < 21) {
+        hs[6 * pa + pb] = dd_st(hq);
+        hs[6 * pb + pa] = dd_st(hq);
+        runv[r * NV + 57 + lane] = dd_st(hq);
+      } else {
+        hs[36 + pa] = dd_st(hq);
+        runv[r * NV + 84 + pa] = dd_st(hq);
+      }
     }
+    __syncwarp();
+    if (lane < 7) {  // lanes 0..5: column `lane` of Hij; lane 6: vi
+      DF v[6], o[6];
+#pragma unroll
+      for (int m = 0; m < 6; ++m) v[m] = dd_ld(lane < 6 ? hs[6 * m + lane] : hs[36 + m]);
+      dpv_adT_dd(T, v, o);
+#pragma unroll
+      for (int m = 0; m < 6; ++m) {
+        const float2 x = dd_st(dd_neg(o[m]));
+        if (lane < 6) {
+          hs[42 + 6 * m + lane] = x;
+          runv[r * NV + 21 + 6 * m + lane] = x;
+        } else {
+          runv[r * NV + 78 + m] = x;
+        }
+      }
+    }
+    __syncwarp();
+    if (lane < 6) {  // row `lane` of Hii, lower part
+      DF v[6], o[6];
+#pragma unroll
+      for (int m = 0; m < 6; ++m) v[m] = dd_ld(hs[42 + 6 * lane + m]);
+      dpv_adT_dd(T, v, o);
+#pragma unroll
+      for (int m = 0; m < 6; ++m)
+        if (m <= lane) runv[r * NV + tri(lane, m)] = dd_st(dd_neg(o[m]));
+    }
+    __syncwarp();
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) cst += __shfl_xor_sync(0xffffffffu, cst, o);
@@ -276,88 +296,105 @@ __global__ void __launch_bounds__(AD_THREADS) k_assemble_dd(
   __syncthreads();
 
   // ---- phase 2: per patch e_k, C_k, w_k as pairs ----------------------------
-  // (the warp's staging rows hold each lane's target-frame terms while the
-  // first lane of every set of edges with the same target adds them up)
-  float* scr = reinterpret_cast<float*>(rows) + wid * 32 * 12;
-  for (int q = wid; q < G; q += AD_WARPS) {
-    const int k = g * G + q;
-    float2* col = Eh + (size_t)q * EH_STRIDE;
-    DF ei[6], C = {0.f, 0.f}, wv = {0.f, 0.f};
+  // 16 lanes per patch (two patches per warp), one lane per edge: the
+  // source-frame column and C, w summed over the lanes (pairs), the
+  // target-frame 6-vectors added to their slots of the patch's column by the
+  // first lane of each set of edges with the same target (found with
+  // __match_any_sync; the lanes' terms wait in the warp's staging rows)
+  {
+    float* scr = reinterpret_cast<float*>(rows) + wid * 32 * 12;
+    const int half = lane >> 4, hl = lane & 15;
+    for (int q0 = 2 * wid; q0 < G; q0 += 2 * AD_WARPS) {
+      const int q = q0 + half;
+      const int k = g * G + q;
+      const bool mine = q < G && k < P;
+      float2* col = Eh + (size_t)(q < G ? q : q0) * EH_STRIDE;
+      DF ei[6], C = {0.f, 0.f}, wv = {0.f, 0.f};
 #pragma unroll
-    for (int m = 0; m < 6; ++m) ei[m] = DF{0.f, 0.f};
-    int si = -1;
-    const int p0 = k < P ? pptr[k] : 0, p1 = k < P ? pptr[k + 1] : 0;
-    for (int pb0 = p0; pb0 < p1; pb0 += 32) {
-      const int p = pb0 + lane;
-      int sj = -1 - lane;  // a key no other lane has
-      if (p < p1) {
-        const float4* t4 = pterm + 8 * (size_t)p;
-        const float4 a = t4[0], b = t4[1], c = t4[2], d3 = t4[3], d4 = t4[4], d5 = t4[5], d6 = t4[6],
-                     d7 = t4[7];
-        const int sl = __float_as_int(d7.x);
-        si = sl & 0xff;
-        sj = sl >> 8;
-        dd_acc_add(ei[0], DF{a.x, a.y}); dd_acc_add(ei[1], DF{a.z, a.w});
-        dd_acc_add(ei[2], DF{b.x, b.y}); dd_acc_add(ei[3], DF{b.z, b.w});
-        dd_acc_add(ei[4], DF{c.x, c.y}); dd_acc_add(ei[5], DF{c.z, c.w});
-        dd_acc_add(C, DF{d6.x, d6.y});
-        dd_acc_add(wv, DF{d6.z, d6.w});
-        float* sl12 = scr + 12 * lane;
-        sl12[0] = d3.x; sl12[1] = d3.y; sl12[2] = d3.z; sl12[3] = d3.w;
-        sl12[4] = d4.x; sl12[5] = d4.y; sl12[6] = d4.z; sl12[7] = d4.w;
-        sl12[8] = d5.x; sl12[9] = d5.y; sl12[10] = d5.z; sl12[11] = d5.w;
-      }
-      const unsigned same = __match_any_sync(0xffffffffu, sj);
-      __syncwarp();
-      if (p < p1 && (int)(__ffs(same) - 1) == lane) {
-        DF tj[6];
-#pragma unroll
-        for (int m = 0; m < 6; ++m) tj[m] = DF{0.f, 0.f};
-        for (unsigned bits = same; bits; bits &= bits - 1) {
-          const float* o = scr + 12 * (__ffs(bits) - 1);
-#pragma unroll
-          for (int m = 0; m < 6; ++m) dd_acc_add(tj[m], DF{o[2 * m], o[2 * m + 1]});
+      for (int m = 0; m < 6; ++m) ei[m] = DF{0.f, 0.f};
+      int si = -1;
+      const int p0 = mine ? pptr[k] : 0, cnt = mine ? pptr[k + 1] - p0 : 0;
+      const int most = max(cnt, __shfl_xor_sync(0xffffffffu, cnt, 16));
+      for (int base = 0; base < most; base += 16) {
+        const bool act = base + hl < cnt;
+        int key = -1 - lane;  // a key no other lane has
+        int sj = 0;
+        if (act) {
+          const float4* t4 = pterm + 8 * (size_t)(p0 + base + hl);
+          const float4 a = t4[0], b = t4[1], c = t4[2], d3 = t4[3], d4 = t4[4], d5 = t4[5], d6 = t4[6],
+                       d7 = t4[7];
+          const int sl = __float_as_int(d7.x);
+          si = sl & 0xff;
+          sj = sl >> 8;
+          key = (half << 8) | sj;
+          dd_acc_add(ei[0], DF{a.x, a.y}); dd_acc_add(ei[1], DF{a.z, a.w});
+          dd_acc_add(ei[2], DF{b.x, b.y}); dd_acc_add(ei[3], DF{b.z, b.w});
+          dd_acc_add(ei[4], DF{c.x, c.y}); dd_acc_add(ei[5], DF{c.z, c.w});
+          dd_acc_add(C, DF{d6.x, d6.y});
+          dd_acc_add(wv, DF{d6.z, d6.w});
+          float* o = scr + 12 * lane;
+          o[0] = d3.x; o[1] = d3.y; o[2] = d3.z; o[3] = d3.w;
+          o[4] = d4.x; o[5] = d4.y; o[6] = d4.z; o[7] = d4.w;
+          o[8] = d5.x; o[9] = d5.y; o[10] = d5.z; o[11] = d5.w;
         }
-        float2* cj = col + 6 * sj;
+        const unsigned same = __match_any_sync(0xffffffffu, key);
+        __syncwarp();
+        if (act && (int)(__ffs(same) - 1) == lane) {
+          DF tj[6];
 #pragma unroll
-        for (int m = 0; m < 6; ++m) cj[m] = dd_st(dd_add(dd_ld(cj[m]), dd_norm(tj[m])));
+          for (int m = 0; m < 6; ++m) tj[m] = DF{0.f, 0.f};
+          for (unsigned bits = same; bits; bits &= bits - 1) {
+            const float* o = scr + 12 * (__ffs(bits) - 1);
+#pragma unroll
+            for (int m = 0; m < 6; ++m) dd_acc_add(tj[m], DF{o[2 * m], o[2 * m + 1]});
+          }
+          float2* cj = col + 6 * sj;
+#pragma unroll
+          for (int m = 0; m < 6; ++m) cj[m] = dd_st(dd_add(dd_ld(cj[m]), dd_norm(tj[m])));
+        }
+        __syncwarp();
+      }
+#pragma unroll
+      for (int o = 8; o > 0; o >>= 1) {
+#pragma unroll
+        for (int m = 0; m < 6; ++m)
+          dd_acc_add(ei[m], DF{__shfl_xor_sync(0xffffffffu, ei[m].hi, o), __shfl_xor_sync(0xffffffffu, ei[m].lo, o)});
+        dd_acc_add(C, DF{__shfl_xor_sync(0xffffffffu, C.hi, o), __shfl_xor_sync(0xffffffffu, C.lo, o)});
+        dd_acc_add(wv, DF{__shfl_xor_sync(0xffffffffu, wv.hi, o), __shfl_xor_sync(0xffffffffu, wv.lo, o)});
+        si = max(si, __shfl_xor_sync(0xffffffffu, si, o));
+      }
+      // the first lane of each half's sums for the whole half (the butterfly
+      // may differ in the last bit across lanes)
+      const int src = half << 4;
+      DF ct = dd_add_f(dd_norm(C), lambda_d);
+      ct = DF{__shfl_sync(0xffffffffu, ct.hi, src), __shfl_sync(0xffffffffu, ct.lo, src)};
+      DF wf_;
+      if (w_ext) {
+        wf_ = DF{mine ? w_ext[k] : 0.f, 0.f};
+      } else {
+        wf_ = dd_norm(wv);
+        wf_ = DF{__shfl_sync(0xffffffffu, wf_.hi, src), __shfl_sync(0xffffffffu, wf_.lo, src)};
+      }
+      if (hl == 0 && q < G && si >= 0) {
+#pragma unroll
+        for (int m = 0; m < 6; ++m) col[6 * si + m] = dd_st(dd_add(dd_ld(col[6 * si + m]), dd_norm(ei[m])));
       }
       __syncwarp();
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-#pragma unroll
-      for (int m = 0; m < 6; ++m) dd_acc_add(ei[m], shfl_dd(ei[m], o));
-      dd_acc_add(C, shfl_dd(C, o));
-      dd_acc_add(wv, shfl_dd(wv, o));
-      si = max(si, __shfl_xor_sync(0xffffffffu, si, o));
-    }
-    // lane 0's sums for every lane (the butterfly may differ in the last bit across lanes)
-    DF ct = dd_add_f(dd_norm(C), lambda_d);
-    ct = DF{__shfl_sync(0xffffffffu, ct.hi, 0), __shfl_sync(0xffffffffu, ct.lo, 0)};
-    DF wf_;
-    if (w_ext) {
-      wf_ = DF{k < P ? w_ext[k] : 0.f, 0.f};
-    } else {
-      wf_ = dd_norm(wv);
-      wf_ = DF{__shfl_sync(0xffffffffu, wf_.hi, 0), __shfl_sync(0xffffffffu, wf_.lo, 0)};
-    }
-    if (lane == 0 && si >= 0) {
-#pragma unroll
-      for (int m = 0; m < 6; ++m) col[6 * si + m] = dd_st(dd_add(dd_ld(col[6 * si + m]), dd_norm(ei[m])));
-    }
-    __syncwarp();
-    const DF sq = dd_rcp(dd_sqrt(ct));
-    for (int m = lane; m < nr; m += 32) col[m] = dd_st(dd_mul(dd_ld(col[m]), sq));
-    if (lane == 0) {
-      sc[2 * q] = dd_st(sq);
-      sc[2 * q + 1] = dd_st(dd_mul(wf_, sq));
-      if (k < P) {
-        Ct_out[k] = ct.hi + ct.lo;
-        wk_out[k] = wf_.hi + wf_.lo;
-        Ct2_out[k] = dd_st(ct);
-        wk2_out[k] = dd_st(wf_);
+      if (q < G) {
+        const DF sq = dd_rcp(dd_sqrt(ct));
+        for (int m = hl; m < nr; m += 16) col[m] = dd_st(dd_mul(dd_ld(col[m]), sq));
+        if (hl == 0) {
+          sc[2 * q] = dd_st(sq);
+          sc[2 * q + 1] = dd_st(dd_mul(wf_, sq));
+          if (k < P) {
+            Ct_out[k] = ct.hi + ct.lo;
+            wk_out[k] = wf_.hi + wf_.lo;
+            Ct2_out[k] = dd_st(ct);
+            wk2_out[k] = dd_st(wf_);
+          }
+        }
       }
+      __syncwarp();
     }
   }
   __syncthreads();
@@ -461,18 +498,13 @@ bool g_dd_ready = false;
 
 ba_status_t setup_dd(ba_handle_t h) {
   if (g_dd_ready) return BA_OK;
-  unsigned char pa[NV], pb[NV];
+  unsigned char pa[NJ], pb[NJ];
   int q = 0;
   for (int a = 0; a < 6; ++a)
-    for (int b = 0; b <= a; ++b, ++q) { pa[q] = a; pb[q] = b; }          // Hii (lower)
-  for (int a = 0; a < 6; ++a)
-    for (int b = 0; b < 6; ++b, ++q) { pa[q] = a; pb[q] = 6 + b; }       // Hij
-  for (int a = 0; a < 6; ++a)
-    for (int b = 0; b <= a; ++b, ++q) { pa[q] = 6 + a; pb[q] = 6 + b; }  // Hjj (lower)
-  for (int a = 0; a < 6; ++a, ++q) { pa[q] = a; pb[q] = 12; }            // vi
-  for (int a = 0; a < 6; ++a, ++q) { pa[q] = 6 + a; pb[q] = 12; }        // vj
-  DPV_CUDA(h, cudaMemcpyToSymbol(c_qa, pa, NV));
-  DPV_CUDA(h, cudaMemcpyToSymbol(c_qb, pb, NV));
+    for (int b = 0; b <= a; ++b, ++q) { pa[q] = a; pb[q] = b; }  // Hjj (lower)
+  for (int a = 0; a < 6; ++a, ++q) { pa[q] = a; pb[q] = 6; }     // vj
+  DPV_CUDA(h, cudaMemcpyToSymbol(c_qa, pa, NJ));
+  DPV_CUDA(h, cudaMemcpyToSymbol(c_qb, pb, NJ));
   DPV_CUDA(h, cudaFuncSetAttribute(k_assemble_dd<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)assemble_dd_smem_bytes(DPV_GMAX_DD, 1)));
   DPV_CUDA(h, cudaFuncSetAttribute(k_assemble_dd<9>, cudaFuncAttributeMaxDynamicSharedMemorySize,

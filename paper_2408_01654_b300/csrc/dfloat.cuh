@@ -135,29 +135,35 @@ __device__ __forceinline__ void dpv_relative_pose_dd(const float* Pi, const floa
   }
 }
 
-// ---- per-edge linearisation of Eq. 3 in double-float -----------------------
+// ---- per-edge linearisation of Eq. 3 in double-float (target side) -------
 //   X = R xb + t d  (xb = ((u-cx)/fx, (v-cy)/fy, 1), homogeneous 4th entry d)
 //   r = (target - c) - f X/Z   (per component)
-//   Jj = dproj/dX [ d I | -[X]x ],  Ji = -Jj Ad(T_ij),  Jd = dproj/dX t
+//   Jj = dproj/dX [ d I | -[X]x ],  Jd = dproj/dX t
 // written with x = X/Z, y = Y/Z:  dproj/dX [d I] = f/Z [d, 0, -x d], the
 // rotation part f [-x y, 1 + x^2, -y] (u row) and f [-(1 + y^2), x y, x]
-// (v row), and Jd = f/Z (t_0 - x t_2, t_1 - y t_2).
+// (v row), and Jd = f/Z (t_0 - x t_2, t_1 - y t_2).  The source-pose Jacobian
+// Ji = -Jj Ad(T_ij) is not formed: every product with it is taken through
+// Ad(T_ij)^T once per run or per edge (dpv_adT_dd).
+// T: the relative pose as pairs in shared memory, floats [2m, 2m+1] for
+// R[m] (row-major), [18 + 2m, 19 + 2m] for t[m], [24 + 2m, 25 + 2m] for
+// ([t]x R)[m].
 struct EdgeLinDD {
   DF r[2];
-  DF Ji[2][6], Jj[2][6], Jd[2];
+  DF Jj[2][6], Jd[2];  // Jj[0][1] = Jj[1][0] = 0
   bool valid;
 };
 
-__device__ __forceinline__ void dpv_edge_linearize_dd(const RelPoseDD& T, DF xb0, DF xb1, float d, float tu,
-                                                      float tv, const float* K, float z_min, bool self_edge,
-                                                      EdgeLinDD& o) {
+__device__ __forceinline__ DF dd_sm(const float* T, int i) { return DF{T[2 * i], T[2 * i + 1]}; }
+
+__device__ __forceinline__ void dpv_edge_linearize_dd(const float* T, DF xb0, DF xb1, float d, float tu, float tv,
+                                                      const float* K, float z_min, bool self_edge, EdgeLinDD& o) {
   DF X[3];
 #pragma unroll
   for (int r = 0; r < 3; ++r) {
-    DF acc = T.R[3 * r + 2];
-    dd_acc(acc, T.R[3 * r], xb0);
-    dd_acc(acc, T.R[3 * r + 1], xb1);
-    dd_acc(acc, T.t[r], DF{d, 0.f});
+    DF acc = dd_sm(T, 3 * r + 2);
+    dd_acc(acc, dd_sm(T, 3 * r), xb0);
+    dd_acc(acc, dd_sm(T, 3 * r + 1), xb1);
+    dd_acc(acc, dd_sm(T, 9 + r), DF{d, 0.f});
     X[r] = dd_norm(acc);
   }
   o.valid = !self_edge && (X[2].hi > z_min * d);
@@ -167,42 +173,40 @@ __device__ __forceinline__ void dpv_edge_linearize_dd(const RelPoseDD& T, DF xb0
   o.r[0] = dd_sub(dd_two_sum(tu, -K[2]), dd_mul_f(xz, fx));
   o.r[1] = dd_sub(dd_two_sum(tv, -K[3]), dd_mul_f(yz, fy));
   const DF id = dd_mul_f(iz, d);
-  const DF xid = dd_mul(xz, id), yid = dd_mul(yz, id), xy = dd_mul(xz, yz);
-  const DF xx1 = dd_add_f(dd_mul(xz, xz), 1.f), yy1 = dd_add_f(dd_mul(yz, yz), 1.f);
+  const DF xy = dd_mul(xz, yz);
   const DF zero = {0.f, 0.f};
   o.Jj[0][0] = dd_mul_f(id, fx);
   o.Jj[0][1] = zero;
-  o.Jj[0][2] = dd_neg(dd_mul_f(xid, fx));
+  o.Jj[0][2] = dd_neg(dd_mul_f(dd_mul(xz, id), fx));
   o.Jj[0][3] = dd_neg(dd_mul_f(xy, fx));
-  o.Jj[0][4] = dd_mul_f(xx1, fx);
+  o.Jj[0][4] = dd_mul_f(dd_add_f(dd_mul(xz, xz), 1.f), fx);
   o.Jj[0][5] = dd_neg(dd_mul_f(yz, fx));
   o.Jj[1][0] = zero;
   o.Jj[1][1] = dd_mul_f(id, fy);
-  o.Jj[1][2] = dd_neg(dd_mul_f(yid, fy));
-  o.Jj[1][3] = dd_neg(dd_mul_f(yy1, fy));
+  o.Jj[1][2] = dd_neg(dd_mul_f(dd_mul(yz, id), fy));
+  o.Jj[1][3] = dd_neg(dd_mul_f(dd_add_f(dd_mul(yz, yz), 1.f), fy));
   o.Jj[1][4] = dd_mul_f(xy, fy);
   o.Jj[1][5] = dd_mul_f(xz, fy);
+  o.Jd[0] = dd_mul(dd_mul_f(iz, fx), dd_sub(dd_sm(T, 9), dd_mul(xz, dd_sm(T, 11))));
+  o.Jd[1] = dd_mul(dd_mul_f(iz, fy), dd_sub(dd_sm(T, 10), dd_mul(yz, dd_sm(T, 11))));
+}
+
+// out = Ad(T_ij)^T v for a 6-vector v (translation part first):
+// Ad = [ R  [t]x R ; 0  R ]  =>  out[c] = sum_m R[m][c] v[m],
+// out[3 + c] = sum_m (([t]x R)[m][c] v[m] + R[m][c] v[3 + m]).
+__device__ __forceinline__ void dpv_adT_dd(const float* T, const DF* v, DF* out) {
 #pragma unroll
-  for (int a = 0; a < 2; ++a) {
-    // the zero translation entry of the row (Jj[0][1], Jj[1][0]) is skipped
-    const int m0 = a == 0 ? 0 : 1;
+  for (int c = 0; c < 3; ++c) {
+    DF a = {0.f, 0.f}, b = {0.f, 0.f};
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      DF jr = {0.f, 0.f}, jt = {0.f, 0.f};
-      dd_acc(jr, o.Jj[a][m0], T.R[3 * m0 + c]);
-      dd_acc(jr, o.Jj[a][2], T.R[6 + c]);
-      dd_acc(jt, o.Jj[a][m0], T.txR[3 * m0 + c]);
-      dd_acc(jt, o.Jj[a][2], T.txR[6 + c]);
-      dd_acc(jt, o.Jj[a][3], T.R[c]);
-      dd_acc(jt, o.Jj[a][4], T.R[3 + c]);
-      dd_acc(jt, o.Jj[a][5], T.R[6 + c]);
-      o.Ji[a][c] = dd_neg(dd_norm(jr));
-      o.Ji[a][3 + c] = dd_neg(dd_norm(jt));
+    for (int m = 0; m < 3; ++m) {
+      dd_acc(a, dd_sm(T, 3 * m + c), v[m]);
+      dd_acc(b, dd_sm(T, 12 + 3 * m + c), v[m]);
+      dd_acc(b, dd_sm(T, 3 * m + c), v[3 + m]);
     }
+    out[c] = dd_norm(a);
+    out[3 + c] = dd_norm(b);
   }
-  const DF fiz = dd_mul_f(iz, fx), giz = dd_mul_f(iz, fy);
-  o.Jd[0] = dd_mul(fiz, dd_sub(T.t[0], dd_mul(xz, T.t[2])));
-  o.Jd[1] = dd_mul(giz, dd_sub(T.t[1], dd_mul(yz, T.t[2])));
 }
 
 // The back-projected ray coordinate (p - c) / f of a float pixel p in
