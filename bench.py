@@ -65,6 +65,10 @@ WORKLOADS = {
             "mixed precision solve", lambda seed=0: scenes.pose_graph(seed, N=PGO_N, loop_every=20, loop_noise=0.002)),
     "batched": ("batched uneven BA: 64 independent problems, frames round(exp(U[ln 8, ln 400])), 96 patches/frame, "
                 "+-6 local + proximity loop edges, 4 GN iterations each, 2 fixed poses each", scenes.batched),
+    "diff16": ("differentiable BA: a batch of 16 odometry windows (22 keyframes, 96 patches/frame, patch lifetime 13, "
+               "8% outliers, ~27k edges each) bound as one batch, 2 recorded GN steps and the reverse pass "
+               "(ba_backward: gradients of a linear loss of the final poses and depths w.r.t. targets and weights)",
+               lambda seed=0: [scenes.odometry(seed=16 * seed + b) for b in range(16)]),
 }
 PGO_N, PGO_ITERS = 500, 10
 
@@ -110,6 +114,8 @@ def parse():
         a.steps = 3 if not short else (50 if a.impl == "reference" else 2000)
         if a.workload in ("global", "loop400") and a.impl == "ours":
             a.steps = 20  # ~0.5 s of timed steps: several clock samples
+        if a.workload == "diff16":
+            a.steps = 50 if a.impl == "ours" else 3
         if a.workload == "correlation":
             a.steps = 3 if a.impl == "reference" else 200
         if a.workload == "pgo":
@@ -359,6 +365,42 @@ def time_oracle(scene, budget_s=10.0, max_runs=1000, pixels=1):
         if el >= budget_s or runs >= max_runs:
             break
     return runs, el
+
+
+def _pool_gn(item):
+    """Pool worker: the oracle's GN on one problem; returns its own duration."""
+    import oracle
+    sc, pixels = item
+    t0 = time.perf_counter()
+    oracle.gn(sc, pixels=pixels)
+    return time.perf_counter() - t0
+
+
+def _pool_init():
+    import oracle
+    oracle.build()
+    oracle.lib()
+
+
+def oracle_pool_rate(problems, steps, budget_s=150.0, pixels=1):
+    """The oracle on independent problems over every affine host core (a
+    process pool started with spawn): each step solves every problem once.
+    Returns (problem GN it/s over all cores, the same on one core from the
+    workers' own durations, cores, steps run)."""
+    import multiprocessing as mp
+    cores = cpu_cores()
+    iters = sum(sc.iters for sc in problems)
+    items = [(sc, pixels) for sc in sorted(problems, key=lambda sc: -sc.N)]  # longest first
+    with mp.get_context("spawn").Pool(cores, initializer=_pool_init) as pool:
+        wall, busy, ran = 0.0, 0.0, 0
+        for _ in range(steps):
+            t0 = time.perf_counter()
+            busy += sum(pool.map(_pool_gn, items, chunksize=1))
+            wall += time.perf_counter() - t0
+            ran += 1
+            if wall > budget_s:
+                break
+    return ran * iters / wall, ran * iters / busy, cores, ran
 
 
 def cpu_cores():
@@ -972,26 +1014,38 @@ def run_reference(args):
     desc, make = WORKLOADS[args.workload]
     import oracle
     oracle.build()
-    if args.workload == "batched":
-        # a bounded sample of the batch: six problems spread over the size range
+    if args.workload in ("batched", "diff16"):
+        # independent problems: the whole batch per step, over every host
+        # core (the differentiable batch forward only: the oracle's
+        # derivatives are forward-mode, one run per coordinate)
         probs = make(seed=0)
-        order = np.argsort([sc.N for sc in probs])
-        sample = [probs[int(b)] for b in order[:: max(1, len(probs) // 6)]][:6]
-        work = lambda: [oracle.gn(sc) for sc in sample]  # noqa: E731
-        iters_per_step = sum(sc.iters for sc in sample)
-        scene = sample[0]
-        desc += f"; oracle sample: problems of {[sc.N for sc in sample]} frames per step"
+        value, one_core, cores, ran = oracle_pool_rate(probs, args.steps)
+        unit = "problem GN it/s"
+        sample = (f"{ran} steps of the whole batch ({len(probs)} problems, {sum(sc.iters for sc in probs)} problem GN "
+                  f"iterations per step{', forward only' if args.workload == 'diff16' else ''}), FP64 oracle (-O2) "
+                  f"in a process pool over {cores} host cores; {one_core:.2f} {unit} on one core (the workers' own "
+                  f"durations)")
+        line = {
+            "impl": "reference", "metric": METRIC, "value": value, "unit": unit, "n_gpus": args.gpus, "steps": ran,
+            "warmup": 0, "ms_per_step": 1e3 * sum(sc.iters for sc in probs) / value, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": desc, "problems": len(probs), "E_total": int(sum(sc.E for sc in probs))},
+            "cpu_baseline": {"value": value, "unit": unit, "cores": cores, "kind": "oracle", "sample": sample,
+                             "one_core_value": one_core},
+            "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        }
+        print(json.dumps(line))
+        return 0
+    scene = make(seed=0)
+    if scene.N >= LARGE_FRAMES:
+        # one GN iteration per step (a full run of the loop-closure BA
+        # takes minutes on one core)
+        work = lambda: oracle.gn(scene, iters=1, pixels=residual_pixels(args.workload))  # noqa: E731
+        iters_per_step = 1
+        desc += "; oracle sample: one GN iteration per step"
     else:
-        scene = make(seed=0)
-        if scene.N >= LARGE_FRAMES:
-            # one GN iteration per step (a full run of the loop-closure BA
-            # takes minutes on one core)
-            work = lambda: oracle.gn(scene, iters=1, pixels=residual_pixels(args.workload))  # noqa: E731
-            iters_per_step = 1
-            desc += "; oracle sample: one GN iteration per step"
-        else:
-            work = lambda: oracle.gn(scene, pixels=residual_pixels(args.workload))  # noqa: E731
-            iters_per_step = scene.iters
+        work = lambda: oracle.gn(scene, pixels=residual_pixels(args.workload))  # noqa: E731
+        iters_per_step = scene.iters
     for _ in range(min(args.warmup, 1 if scene.N < LARGE_FRAMES else 0)):
         work()
     # the oracle is deterministic single-threaded code: a time budget bounds
@@ -1010,7 +1064,7 @@ def run_reference(args):
         desc += f"; {steps_run} of the {args.steps} requested steps ran within a {budget_s:.0f} s budget"
     args.steps = steps_run
     value = args.steps * iters_per_step / el
-    unit = "problem GN it/s" if args.workload == "batched" else UNIT
+    unit = UNIT
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": unit, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
@@ -1359,6 +1413,28 @@ def run_batched(args):
         e2e_ev[k][1].record(stream)
     torch.cuda.synchronize()
     e2e_value = job_throughput(args.steps * B * iters, world, max_over_ranks(sum(a.elapsed_time(b) for a, b in e2e_ev), dev))
+    # ground-truth error of every problem after the workload's iterations, for
+    # the batched (mixed-precision) form and the plain per-problem FP32 form
+    # (both hold the state of their last timed step)
+    fo, po = offs["frame_off"], offs["patch_off"]
+    gt_b = [gt_errors(T["poses"][fo[b]:fo[b + 1]].cpu().numpy(), T["patches"][po[b]:po[b + 1], 2, 1, 1].cpu().numpy(),
+                      probs[b]) for b in range(B)]
+    gt_p = [gt_errors(plain_T[b]["poses"].cpu().numpy(), plain_T[b]["patches"][:, 2, 1, 1].cpu().numpy(), probs[b])
+            for b in range(B)]
+
+    def gt_summary(g):
+        return {"rot_rmse_rad_mean": float(np.mean([x["rot_rmse_rad"] for x in g])),
+                "centre_rmse_m_mean": float(np.mean([x["centre_rmse_m"] for x in g])),
+                "rot_rmse_rad_max": float(np.max([x["rot_rmse_rad"] for x in g])),
+                "centre_rmse_m_max": float(np.max([x["centre_rmse_m"] for x in g]))}
+
+    rel = [max(abs(a["rot_rmse_rad"] - b["rot_rmse_rad"]) / b["rot_rmse_rad"],
+               abs(a["centre_rmse_m"] - b["centre_rmse_m"]) / b["centre_rmse_m"]) for a, b in zip(gt_b, gt_p)]
+    worst = int(np.argmax(rel))
+    equal_error = {"after_iters": iters, "batched_mixed": gt_summary(gt_b), "plain_fp32": gt_summary(gt_p),
+                   "max_rel_diff_per_problem": float(rel[worst]), "at_problem": worst, "frames": probs[worst].N,
+                   "what": "RMS rotation and camera-centre error against ground truth after the iterations, per "
+                           "problem; the two forms compared problem by problem"}
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -1376,6 +1452,8 @@ def run_batched(args):
         ba.sync()
         order = np.argsort([sc.N for sc in probs])
         sample = [int(b) for b in order[:: max(1, B // 6)]][:6]
+        if int(order[-1]) not in sample:
+            sample.append(int(order[-1]))  # the largest problem too
         errs = []
         t0 = time.perf_counter()
         for b in sample:
@@ -1387,18 +1465,13 @@ def run_batched(args):
             errs.append({"problem": b, "frames": probs[b].N, "rot_rad": rot, "trans_rel": tr,
                          "depth_rel": float(np.max(np.abs(d - want[1]) / np.abs(want[1])))})
         err = errs
-        # oracle throughput on the same sample (problem GN iterations per second)
-        runs, el = 0, 0.0
-        t1 = time.perf_counter()
-        for b in sample:
-            oracle.gn(probs[b])
-            runs += probs[b].iters
-            if time.perf_counter() - t1 > 20.0:
-                break
-        el = time.perf_counter() - t1
-        cpu = {"value": runs / el, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"problems {sample[:len(sample)]} of the batch ({runs} problem GN iterations), "
-                         f"single-threaded FP64 oracle (-O2) on 1 of {cpu_cores()} host cores, {el:.1f} s"}
+        # oracle throughput on the whole batch (independent problems over every
+        # host core, a spawn-started process pool)
+        cv, one_core, cores, ran = oracle_pool_rate(probs, 1, budget_s=60.0)
+        cpu = {"value": cv, "unit": "problem GN it/s", "cores": cores, "kind": "oracle", "one_core_value": one_core,
+               "sample": f"the whole batch once ({B} problems, {B * iters} problem GN iterations), FP64 oracle "
+                         f"(-O2) in a process pool over {cores} host cores; {one_core:.2f} problem GN it/s on one "
+                         f"core (the workers' own durations)"}
 
     dom = max((k for k in prof if prof[k][1] > 0), key=lambda k: prof[k][0])
     t_ms, cnt = prof[dom]
@@ -1427,9 +1500,193 @@ def run_batched(args):
         "plain_per_problem_fp32": {"value": plain_value, "unit": "problem GN it/s", "ms_per_step": plain_ms / args.steps,
                                    "what": "one FP32 handle per problem, set_graph + step, problem after problem"},
         "batched_vs_plain": value / plain_value,
+        "final_ground_truth_error": equal_error,
         "error_vs_oracle": err,
         "per_class_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
         "dominant_class": {"kind": dom, "avg_launch_us": t_ms / cnt * 1e3},
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": "problem GN it/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def run_diff16(args):
+    """The differentiable workload: one step = binding the 16 windows as one
+    batch, 2 GN iterations recorded, and ba_backward over them."""
+    import torch
+
+    from paper_2408_01654_b300 import build as pbuild
+    from paper_2408_01654_b300.ba import DPVBA, batch_tensors
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    if rank == 0:
+        pbuild.build()
+    if dist:
+        dist.barrier()
+    desc, make = WORKLOADS["diff16"]
+    probs = make(seed=problem_seed(rank))
+    iters, fixed = probs[0].iters, probs[0].fixed
+    B = len(probs)
+    dev = torch.device("cuda", local)
+    T, offs = batch_tensors(probs, dev)
+    pristine = {k: v.clone() for k, v in T.items()}
+    E_tot = int(offs["edge_off"][-1])
+    stream = torch.cuda.current_stream(dev)
+    ba = DPVBA(precision=args.precision, patches_per_group=args.group, stream=stream)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    rng = np.random.default_rng(rank)
+    a_np, b_np = rng.normal(size=(T["poses"].shape[0], 7)), rng.normal(size=T["patches"].shape[0])
+    gp = torch.as_tensor(a_np, dtype=torch.float64, device=dev)
+    gd = torch.as_tensor(b_np, dtype=torch.float32, device=dev)
+    gT = torch.empty((E_tot, 2), dtype=torch.float32, device=dev)
+    gW = torch.empty((E_tot, 2), dtype=torch.float32, device=dev)
+
+    def reset():
+        T["poses"].copy_(pristine["poses"])
+        T["patches"].copy_(pristine["patches"])
+
+    def forward():
+        ba.set_graph_batched(**T, **offs)
+        ba.set_record(True)
+        ba.step(iters, fixed)
+
+    def backward():
+        capi.check(ba._h, ba._lib.ba_backward(ba._h, ctypes.c_void_p(gp.data_ptr()), ctypes.c_void_p(gd.data_ptr()),
+                                              ctypes.c_void_p(gT.data_ptr()), ctypes.c_void_p(gW.data_ptr()),
+                                              None, None))
+
+    import ctypes
+
+    from paper_2408_01654_b300 import capi
+    ba.profile(True)
+    for _ in range(max(args.warmup, 3)):
+        reset()
+        forward()
+        backward()
+    ba.sync()
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    launches0 = ba.info()["launches"]
+    ba.profile(True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            reset()
+            flush.zero_()
+            ev[k][0].record(stream)
+            forward()
+            ev[k][1].record(stream)
+            backward()
+            ev[k][2].record(stream)
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ba.sync()
+    step_ms = [e[0].elapsed_time(e[2]) for e in ev]
+    fwd_ms = [e[0].elapsed_time(e[1]) for e in ev]
+    bwd_ms = [e[1].elapsed_time(e[2]) for e in ev]
+    prof = ba.profile_read()
+    launches = ba.info()["launches"] - launches0
+    total_ms = max_over_ranks(sum(step_ms), dev)
+    value = job_throughput(args.steps * B * iters, world, total_ms)
+
+    # end to end: targets, weights, poses and patches from pinned host memory,
+    # the final poses and depths and both gradients back
+    ba.profile(False)
+    names = ("poses", "patches", "targets", "weights")
+    host_in = {k: pristine[k].cpu().pin_memory() for k in names}
+    host_out = [torch.empty_like(x, device="cpu").pin_memory() for x in (T["poses"], T["patches"], gT, gW)]
+    h2d = sum(v.numel() * v.element_size() for v in host_in.values())
+    d2h = sum(v.numel() * v.element_size() for v in host_out)
+    eev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for k in range(args.steps):
+        flush.zero_()
+        eev[k][0].record(stream)
+        for name, hv in host_in.items():
+            T[name].copy_(hv, non_blocking=True)
+        forward()
+        backward()
+        for dst, src in zip(host_out, (T["poses"], T["patches"], gT, gW)):
+            dst.copy_(src, non_blocking=True)
+        eev[k][1].record(stream)
+    torch.cuda.synchronize()
+    e2e_value = job_throughput(args.steps * B * iters, world, max_over_ranks(sum(a.elapsed_time(b) for a, b in eev), dev))
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return 0
+
+    grad = None
+    cpu = None
+    if not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        gTn, gWn = gT.cpu().numpy().astype(np.float64), gW.cpu().numpy().astype(np.float64)
+        got, want = [], []
+        fo, po, eo = offs["frame_off"], offs["patch_off"], offs["edge_off"]
+        t0 = time.perf_counter()
+        for bb, pr in enumerate(probs):
+            kind = np.array([0, 1])
+            index = rng.choice(2 * pr.E, 2, replace=False)
+            w = oracle.grad_fwd(pr, a_np[fo[bb]:fo[bb + 1]], b_np[po[bb]:po[bb + 1]], kind, index)
+            g = np.where(kind == 0, gTn[eo[bb]:eo[bb + 1]].reshape(-1)[index], gWn[eo[bb]:eo[bb + 1]].reshape(-1)[index])
+            got.append(g)
+            want.append(w)
+        t_grad = time.perf_counter() - t0
+        got, want = np.concatenate(got), np.concatenate(want)
+        grad = {"coordinates": int(len(got)), "max_err_of_max_grad": float(np.abs(got - want).max() / np.abs(want).max()),
+                "norm_err": float(np.linalg.norm(got - want) / np.linalg.norm(want)),
+                "what": "target and weight gradients of 2 sampled coordinates per window against the oracle's "
+                        "forward-mode (dual-number) FP64 derivatives of the same loss"}
+        cv, one_core, cores, ran = oracle_pool_rate(probs, 3, budget_s=30.0)
+        cpu = {"value": cv, "unit": "problem GN it/s", "cores": cores, "kind": "oracle", "one_core_value": one_core,
+               "sample": f"{ran} passes of the 16 windows' forward GN ({iters} iterations each; the oracle's "
+                         f"derivatives are forward-mode, one dual-number run per coordinate: {len(got)} of them took "
+                         f"{t_grad:.1f} s on one core), FP64 oracle (-O2) in a process pool over {cores} host cores; "
+                         f"{one_core:.2f} problem GN it/s on one core"}
+
+    Nb = [sc.N for sc in probs]
+    nb = [6 * (m - fixed) for m in Nb]
+    tri_all = sum(m * (m + 1) // 2 for m in nb)
+    sizes = (sum(Nb), int(offs["patch_off"][-1]), E_tot)
+
+    def diff_bytes(k):
+        if k == "assemble":
+            return 28 * sizes[2] + 12 * sizes[1] + 56 * sizes[0] + 4 * tri_all + 4 * sum(nb) + 8 * sizes[1]
+        if k == "solve":
+            return 4 * tri_all + 16 * sum(nb) + 112 * sizes[0]
+        if k == "adjoint":  # targets, weights in; their gradients out; the recorded state
+            return 32 * sizes[2] + 108 * sizes[1] + 56 * sizes[0]
+        return algorithmic_bytes(k, sizes[0], sizes[1], sizes[2], 0)
+
+    dom = max((k for k in prof if prof[k][1] > 0), key=lambda k: prof[k][0])
+    roof = roofline(dom, prof, args.steps, diff_bytes, nb, "diff16")
+    line = {
+        "metric": METRIC + " (forward + reverse pass)", "value": value, "unit": "problem GN it/s", "n_gpus": world,
+        "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if args.precision == "fp32" else "f32 pairs (double-float)", "data": "synthetic",
+        "config": {"workload": desc, "problems": B, "E_total": E_tot, "iters": iters, "fixed": fixed,
+                   "precision": args.precision, "patches_per_group": ba.info()["G"],
+                   "l2": "flushed between steps (256 MiB write)",
+                   "step": "ba_set_graph_batched + ba_set_record + ba_step + ba_backward"},
+        "forward_ms_per_step": statistics.median(fwd_ms), "backward_ms_per_step": statistics.median(bwd_ms),
+        "gradient_vs_oracle": grad,
+        "per_class_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": "problem GN it/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
@@ -1448,6 +1705,8 @@ def main():
         return run_reference(args)
     if args.workload == "batched":
         return run_batched(args)
+    if args.workload == "diff16":
+        return run_diff16(args)
     if args.workload == "proximity":
         return run_proximity(args)
     if args.workload == "correlation":

@@ -744,10 +744,16 @@ __global__ void __launch_bounds__(LG_THREADS, 1) k_lg_factor(const LgProb* __res
       }
     }
   }
+  // Each CTA claims its next task while it works on the current one (the
+  // claim is an L2 round trip); the versions a task reads are polled by one
+  // lane each, and the versions it publishes are released by one lane each.
+  // A claimed task waits only for tasks earlier in the list, and the earliest
+  // unfinished task is always some CTA's current one, so claiming ahead
+  // cannot deadlock.
+  if (threadIdx.x == 0) task = dpv_status(status) ? ntasks : atomicAdd(ctr, 1);
+  __syncthreads();
   for (;;) {
     tc_fence_smem();  // this thread's generic shared accesses before any later bulk copy into the buffer
-    if (threadIdx.x == 0) task = dpv_status(status) ? ntasks : atomicAdd(ctr, 1);
-    __syncthreads();
     const int t = task;
     __syncthreads();
     if (t >= ntasks) break;
@@ -758,20 +764,31 @@ __global__ void __launch_bounds__(LG_THREADS, 1) k_lg_factor(const LgProb* __res
               j = (int)(w & 1023u);
     int* ver = P.ver;
     const int T = P.T;
-    if (threadIdx.x == 0) {
-      bool ok;
+    if (threadIdx.x < 32) {
+      const int lane = threadIdx.x;
+      // lane q waits for the q-th version this task reads: a panel the
+      // diagonal tile of column k (final) and its own tile (updated through
+      // step k-1); an update the panels of rows i, i+1 and j, j+1 of column
+      // k (final), then the target tiles (updated through step k-1)
+      const int* vp = nullptr;
+      int want = 0;
       if (type == TASK_PANEL) {
-        ok = wait_geq(ver + tri2(k) + k, k + 1, status, timeout) && wait_geq(ver + tri2(i) + k, k, status, timeout);
-      } else {
-        // the four panels of column k (final), then the target tiles (updated through step k-1)
-        ok = true;
-        for (int a = i; a <= i + 1 && a < T && ok; ++a) ok = wait_geq(ver + tri2(a) + k, k + 1, status, timeout);
-        for (int b = j; b <= j + 1 && b < T && ok; ++b) ok = wait_geq(ver + tri2(b) + k, k + 1, status, timeout);
-        for (int a = i; a <= i + 1 && ok; ++a)
-          for (int b = j; b <= j + 1 && ok; ++b)
-            if (quad_tile(T, a, b)) ok = wait_geq(ver + tri2(a) + b, k, status, timeout);
+        if (lane == 0) { vp = ver + tri2(k) + k; want = k + 1; }
+        if (lane == 1) { vp = ver + tri2(i) + k; want = k; }
+      } else if (lane < 4) {  // lanes 0, 1: rows i, i+1; lanes 2, 3: rows j, j+1
+        const int a = (lane < 2 ? i : j) + (lane & 1);
+        if (a < T) { vp = ver + tri2(a) + k; want = k + 1; }
+      } else if (lane < 8) {  // the target tiles (i + (lane >> 1 & 1), j + (lane & 1))
+        const int a = i + ((lane >> 1) & 1), b = j + (lane & 1);
+        if (quad_tile(T, a, b)) { vp = ver + tri2(a) + b; want = k; }
       }
-      bad = ok ? 0 : 1;
+      const bool ok = vp ? wait_geq(vp, want, status, timeout) : true;
+      const bool all_ok = __all_sync(0xffffffffu, ok);
+      if (lane == 0) {
+        bad = all_ok ? 0 : 1;
+        // claim the next task now; it is read after this one completes
+        task = (!all_ok || dpv_status(status)) ? ntasks : atomicAdd(ctr, 1);
+      }
     }
     __syncthreads();
     if (bad) break;
@@ -782,14 +799,19 @@ __global__ void __launch_bounds__(LG_THREADS, 1) k_lg_factor(const LgProb* __res
       break;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-      __threadfence();
+    if (threadIdx.x < 4) {
+      const int q = threadIdx.x;
       if (type == TASK_PANEL) {
-        st_release(ver + tri2(i) + k, k + 1);
+        if (q == 0) {
+          __threadfence();
+          st_release(ver + tri2(i) + k, k + 1);
+        }
       } else {
-        for (int a = i; a <= i + 1; ++a)
-          for (int b = j; b <= j + 1; ++b)
-            if (quad_tile(T, a, b)) st_release(ver + tri2(a) + b, k + 1);
+        const int a = i + (q >> 1), b = j + (q & 1);
+        if (quad_tile(T, a, b)) {
+          __threadfence();
+          st_release(ver + tri2(a) + b, k + 1);
+        }
       }
     }
   }
