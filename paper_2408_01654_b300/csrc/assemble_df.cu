@@ -1,69 +1,61 @@
 // Linearisation + block reduction + Schur complement in double-float
-// arithmetic (the BA_MIXED path): the kernel of assemble.cu with every
-// quantity of the linearisation carried as a pair of floats.
+// arithmetic (the BA_MIXED path): what k_assemble (assemble.cu) computes, with
+// every quantity of the linearisation carried as a pair of floats, in two
+// kernels (Sec. 3.1 Eq. 2-3, the Schur form of Sec. 3.2 "Efficient Global
+// Optimization"):
 //
-// Same structure and outputs as k_assemble (Sec. 3.1 Eq. 2-3, the Schur
-// form of Sec. 3.2 "Efficient Global Optimization"): a CTA owns one group of
-// G consecutive patches and the window of frames its edges touch;
+//   H = [ B  E ; E^T  C ],  g = [ v ; w ],   S = B + lambda_p I - E Ct^-1 E^T,
+//   y = v - E Ct^-1 w,  Ct = C + lambda_d.
 //
-//   phase 0  the double-float relative pose of each (source, target) run;
-//   phase 1  one warp per run, one lane per edge: the double-float residual
-//            and target-pose Jacobian J_j (dfloat.cuh), the sqrt(w)-scaled
-//            rows [J_j, r] staged in shared memory as pairs, and the run's
-//            H_jj (21 entries) and v_j (6) summed as double-float products,
-//            one entry per lane.  Every edge of a run shares T_ij and
-//            J_i = -J_j Ad(T_ij), so the rest of the run's blocks follow once
-//            per run: H_ij = -Ad^T H_jj, H_ii = -H_ij Ad, v_i = -Ad^T v_j
-//            (a third of the per-edge products of summing all 90 entries).
-//            The edge's depth terms e_j = J_j^T W Jd, e_i = -Ad^T e_j,
-//            Jd^T W Jd and Jd^T W r go to the patch-major table as pairs;
-//   phase 2  16 lanes per patch: e_k, C_k, w_k summed as pairs (edges of one
-//            patch that share a target frame are summed by the first lane of
-//            each such set, found with __match_any_sync), the column
-//            e_k / sqrt(Ct_k) formed in double-float;
-//   phase 3  one thread per 3x3 sub-block of the window's lower triangle:
-//            B_ab - sum_k e_a e_b / Ct_k in double-float, added to the global
-//            FP64 S with red.global.add.f64 (likewise y).
+// k_runs_dd: one warp per (source, target) run of a patch group, four
+//   independent warps per CTA.  The warp forms the run's relative pose T_ij
+//   in double-float (lanes in parallel), each lane linearises one edge (the
+//   residual, the target-pose Jacobian J_j and J_d, dfloat.cuh), the
+//   sqrt(w)-scaled rows [J_j, r] are staged in shared memory as pairs and the
+//   lanes sum the run's H_jj (21 entries) and v_j (6) as double-float
+//   products, one entry per lane.  Every edge of a run shares T_ij and
+//   J_i = -J_j Ad(T_ij), so the run's other blocks follow once per run:
+//   H_ij = -Ad^T H_jj, H_ii = -H_ij Ad, v_i = -Ad^T v_j.  The run's B blocks
+//   and v go straight into the FP64 S and y (red.global.add.f64); the edge's
+//   depth terms e_j = J_j^T W J_d, e_i = -Ad^T e_j, J_d^T W J_d and J_d^T W r
+//   go to the patch-major table as pairs (128 bytes per edge).
+// k_schur_dd: one CTA per patch group (G <= DPV_GMAX_DD patches and the
+//   window of frames their edges touch): 16 lanes per patch sum e_k, C_k, w_k
+//   as pairs (edges of one patch that share a target frame are summed by the
+//   first lane of each such set, found with __match_any_sync) and form the
+//   column e_k / sqrt(Ct_k); one thread per 3x3 sub-block of the window's
+//   lower triangle then adds -sum_k e_a e_b^T / Ct_k (double-float) to the
+//   FP64 S with red.global.add.f64, and likewise -E Ct^-1 w to y.
 //
-// Shared memory per CTA is ~219 KB at G = 32 (the pairs double the window
-// columns), so the path supports G <= DPV_GMAX_DD patches per group; it runs
-// 512 threads (one CTA per SM, at most 128 registers per thread).  The
-// patch-major table holds 128 bytes per edge
-// (two float4 per 6-vector pair of e_i, e_j; C, w; the slots), read again by
-// the double-float back-substitution (update.cu).
+// The two parts of each S entry (B, and the Schur product that nearly
+// cancels it) reach the FP64 S separately, each accurate to ~48 bits, so
+// their difference keeps the double-float accuracy.  Splitting the work this
+// way lets four run CTAs and two Schur CTAs share an SM (~16 KB and ~111 KB
+// of shared memory) instead of one CTA doing all phases behind barriers.
 #include "dfloat.cuh"
 
 #include <algorithm>
 
 namespace {
 
-constexpr int AD_THREADS = 512;
-constexpr int AD_WARPS = AD_THREADS / 32;
+constexpr int RW = 4;                        // warps (runs in flight) per run CTA
+constexpr int SC_THREADS = 256;
+constexpr int SC_WARPS = SC_THREADS / 32;
 constexpr int EH_STRIDE = 6 * DPV_WMAX + 1;  // pairs per patch column of E_hat
-constexpr int NV = 90;                       // run block entries: Hii 21, Hij 36, Hjj 21, vi 6, vj 6
 constexpr int NJ = 27;                       // per-edge run entries: Hjj 21 (lower), vj 6
 constexpr int ROWP = 15;                     // staged pairs per edge: [Jj, r] per residual component + pad
-constexpr int RPOSE = 42;                    // floats per run's relative pose: R, t, [t]x R as pairs
+constexpr int RPOSE = 42;                    // floats of a run's relative pose: R, t, [t]x R as pairs
 
 __constant__ unsigned char c_qa[NJ], c_qb[NJ];
 
 __host__ __device__ constexpr int tri(int r, int c) { return r * (r + 1) / 2 + c; }
 
-// staged floats per patch: the centre's ray (x hi, x lo, y hi, y lo) and d,
-// or the nine pixels' rays (x pairs, then y pairs) and d
-__host__ __device__ constexpr int pd_stride(int pix) { return pix == 1 ? 5 : 37; }
-
-// phase-2b tables (window run map, diagonal and y sums as pairs) and the
-// phase-2 scratch of the lanes' target terms live in the phase-1 staging rows
-static_assert(DPV_WMAX * DPV_WMAX + 8 * (DPV_WMAX * 21 + DPV_WMAX * 6) <= 8 * AD_WARPS * 32 * ROWP,
-              "phase-2b tables exceed the staging space");
 static_assert(2 * 36 + 6 <= 32 * ROWP, "run-transform scratch exceeds a warp's staging rows");
-static_assert(32 * 12 <= 2 * 32 * ROWP, "phase-2 scratch exceeds a warp's staging rows");
 
-size_t assemble_dd_smem_bytes(int G, int pix) {
-  return sizeof(float2) * ((size_t)DPV_RMAX * NV + (size_t)G * EH_STRIDE + 2 * G + (size_t)AD_WARPS * 32 * ROWP) +
-         sizeof(float) * ((size_t)DPV_RMAX * RPOSE + (size_t)pd_stride(pix) * G) +
-         sizeof(int) * (DPV_RMAX + 2 * DPV_WMAX);
+size_t runs_smem_bytes() { return (size_t)RW * (sizeof(float2) * 32 * ROWP + sizeof(float) * RPOSE); }
+size_t schur_smem_bytes(int G) {
+  return sizeof(float2) * ((size_t)G * EH_STRIDE + 2 * G) + sizeof(float) * SC_WARPS * 32 * 12 +
+         sizeof(int) * DPV_WMAX;
 }
 
 __device__ __forceinline__ int tri_row(int t) {
@@ -73,107 +65,87 @@ __device__ __forceinline__ int tri_row(int t) {
   return a;
 }
 
+// The run's relative pose T_ij = T_j T_i^-1 from two rows of the pose table
+// (R and the camera centre as pairs) into T (RPOSE floats: R, t, [t]x R as
+// pairs) by the lanes of one warp: R_ij = R_j R_i^T (lanes 0..8),
+// t = R_j (c_i - c_j) (lanes 9..11), then [t]x R (lanes 0..8).
+__device__ __forceinline__ void rel_pose_warp(const float* __restrict__ Pi, const float* __restrict__ Pj, float* T,
+                                              int lane) {
+  if (lane < 9) {
+    const int r = lane / 3, c = lane - 3 * r;
+    DF acc = {0.f, 0.f};
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+      dd_acc(acc, DF{Pj[3 * r + k], Pj[9 + 3 * r + k]}, DF{Pi[3 * c + k], Pi[9 + 3 * c + k]});
+    const DF v = dd_norm(acc);
+    T[2 * lane] = v.hi;
+    T[2 * lane + 1] = v.lo;
+  } else if (lane < 12) {
+    const int r = lane - 9;
+    DF acc = {0.f, 0.f};
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+      dd_acc(acc, DF{Pj[3 * r + k], Pj[9 + 3 * r + k]},
+             dd_sub(DF{Pi[18 + k], Pi[21 + k]}, DF{Pj[18 + k], Pj[21 + k]}));
+    const DF v = dd_norm(acc);
+    T[18 + 2 * r] = v.hi;
+    T[19 + 2 * r] = v.lo;
+  }
+  __syncwarp();
+  if (lane < 9) {  // ([t]x R)[a][c] = t_{a+1} R[a+2][c] - t_{a+2} R[a+1][c] (indices mod 3)
+    const int a = lane / 3, c = lane - 3 * a;
+    const int a1 = (a + 1) % 3, a2 = (a + 2) % 3;
+    const DF v = dd_sub(dd_mul(dd_sm(T, 9 + a1), dd_sm(T, 3 * a2 + c)), dd_mul(dd_sm(T, 9 + a2), dd_sm(T, 3 * a1 + c)));
+    T[24 + 2 * lane] = v.hi;
+    T[25 + 2 * lane] = v.lo;
+  }
+  __syncwarp();
+}
+
+// PIX residual pixels per edge: 1 (the patch centre) or 9 (the whole patch)
 template <int PIX>
-__global__ void __launch_bounds__(AD_THREADS, 1) k_assemble_dd(
+__global__ void __launch_bounds__(RW * 32) k_runs_dd(
     int G, int P, const int* __restrict__ fdx, const int* __restrict__ gprob, const SysDesc* __restrict__ sysd,
-    float lambda_d, float z_min, const int* __restrict__ gptr, const int* __restrict__ grun,
-    const int* __restrict__ gnr, const unsigned* __restrict__ eslot, const int* __restrict__ perm,
-    const int* __restrict__ pmpos, const int* __restrict__ pptr, const int* __restrict__ win,
-    const int* __restrict__ wlen, const float* __restrict__ posef, const float* __restrict__ patches,
+    float z_min, const int* __restrict__ gptr, const int* __restrict__ grun, const int* __restrict__ gnr,
+    const unsigned* __restrict__ eslot, const int* __restrict__ perm, const int* __restrict__ pmpos,
+    const int* __restrict__ win, const float* __restrict__ posef, const float* __restrict__ patches,
     const float* __restrict__ targets, const float* __restrict__ weights, const float* __restrict__ intr,
-    float4* __restrict__ pterm, double* __restrict__ S, double* __restrict__ y, float* __restrict__ Ct_out,
-    float* __restrict__ wk_out, float2* __restrict__ Ct2_out, float2* __restrict__ wk2_out, double* __restrict__ cost,
-    const float* __restrict__ w_ext, int* status) {
-  extern __shared__ float2 smd[];
+    float4* __restrict__ pterm, double* __restrict__ S, double* __restrict__ y, double* __restrict__ cost,
+    int add_v, int* status) {
+  extern __shared__ float2 smr[];
   dpv_pdl_enter();
   if (dpv_status(status)) return;
   const int g = blockIdx.x;
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  const int w = wlen[g];
-  const int nr = 6 * w;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int gs = gptr[g], nruns = gnr[g];
   const int* runptr = grun + (size_t)g * (DPV_RMAX + 1);
-
-  float2* runv = smd;                                        // [RMAX][NV]
-  float2* Eh = runv + DPV_RMAX * NV;                         // [G][EH_STRIDE]
-  float2* sc = Eh + (size_t)G * EH_STRIDE;                   // [G][2]  Ct^-1/2, w Ct^-1/2
-  float2* rows = sc + 2 * G;                                 // [warps][32][ROWP]
-  float* rpose = reinterpret_cast<float*>(rows + AD_WARPS * 32 * ROWP);  // [RMAX][RPOSE]
-  constexpr int PDS = pd_stride(PIX);
-  float* pd = rpose + DPV_RMAX * RPOSE;                      // [G][PDS]
-  int* rsl = reinterpret_cast<int*>(pd + PDS * G);           // [RMAX] si | sj << 8
-  int* wf = rsl + DPV_RMAX;                                  // [W] window frames
-  int* fr = wf + DPV_WMAX;                                   // [W] unknown row in the group's system, -1 fixed
-  const SysDesc sd = sysd[gprob[g]];
-
+  const int* wf = win + (size_t)g * DPV_WMAX;
+  float2* rw = smr + wid * 32 * ROWP;
+  float* T = reinterpret_cast<float*>(smr + RW * 32 * ROWP) + wid * RPOSE;
+  const int prob = gprob[g];
+  const SysDesc sd = sysd[prob];
   float K[4];
 #pragma unroll
-  for (int q = 0; q < 4; ++q) K[q] = intr[4 * gprob[g] + q];
-
-  // ---- phase 0 ------------------------------------------------------------
-  for (int q = tid; q < G * EH_STRIDE; q += AD_THREADS) Eh[q] = make_float2(0.f, 0.f);
-  for (int q = tid; q < w; q += AD_THREADS) {
-    const int f = win[g * DPV_WMAX + q];
-    const int o = fdx[f];
-    wf[q] = f;
-    fr[q] = o < 0 ? -1 : o - sd.voff;
-  }
-  for (int t = tid; t < G * PIX; t += AD_THREADS) {
-    const int q = t / PIX, px = t - PIX * q;
-    const int k = g * G + q;
-    DF x0 = {0.f, 0.f}, x1 = {0.f, 0.f};
-    float d = 1.f;
-    if (k < P) {
-      const float* pk = patches + 27 * (size_t)k;
-      const int pix = PIX == 1 ? 4 : px;
-      x0 = dpv_ray_dd(pk[pix], K[2], K[0]);
-      x1 = dpv_ray_dd(pk[9 + pix], K[3], K[1]);
-      d = pk[22];
-    }
-    float* o = pd + PDS * q;
-    if (PIX == 1) {
-      o[0] = x0.hi; o[1] = x0.lo; o[2] = x1.hi; o[3] = x1.lo; o[4] = d;
-    } else {
-      o[2 * px] = x0.hi; o[2 * px + 1] = x0.lo; o[18 + 2 * px] = x1.hi; o[19 + 2 * px] = x1.lo;
-      if (px == 4) o[36] = d;
-    }
-  }
-  __syncthreads();
-  for (int r = tid; r < nruns; r += AD_THREADS) {
-    const unsigned sw = eslot[gs + runptr[r]];
-    const int si = dpv_slot_i(sw), sj = dpv_slot_j(sw);
-    rsl[r] = si | (sj << 8);
-    RelPoseDD T;
-    dpv_relative_pose_dd(posef + DPV_POSE_ROW * (size_t)wf[si], posef + DPV_POSE_ROW * (size_t)wf[sj], T);
-    float* o = rpose + RPOSE * r;
-#pragma unroll
-    for (int m = 0; m < 9; ++m) { o[2 * m] = T.R[m].hi; o[2 * m + 1] = T.R[m].lo; }
-#pragma unroll
-    for (int m = 0; m < 3; ++m) { o[18 + 2 * m] = T.t[m].hi; o[19 + 2 * m] = T.t[m].lo; }
-#pragma unroll
-    for (int m = 0; m < 9; ++m) { o[24 + 2 * m] = T.txR[m].hi; o[25 + 2 * m] = T.txR[m].lo; }
-  }
-  __syncthreads();
-
-  // ---- phase 1: one warp per run ------------------------------------------
-  float cst = 0.f;
-  float2* rw = rows + wid * 32 * ROWP;
+  for (int q = 0; q < 4; ++q) K[q] = intr[4 * prob + q];
   const bool own = lane < NJ;  // this lane's run entry: Hjj (lower) or vj
   const int pa = own ? c_qa[lane] : 0, pb = own ? c_qb[lane] : 0;
-  for (int r = wid; r < nruns; r += AD_WARPS) {
+  float cst = 0.f;
+  for (int r = wid; r < nruns; r += RW) {
     const int s0 = gs + runptr[r], s1 = gs + runptr[r + 1];
-    const int si = rsl[r] & 0xff, sj = rsl[r] >> 8;
+    const unsigned sw0 = eslot[s0];
+    const int si = dpv_slot_i(sw0), sj = dpv_slot_j(sw0);
+    const int fi = wf[si], fj = wf[sj];
     const bool self_run = si == sj;
-    const float* T = rpose + RPOSE * r;
+    rel_pose_warp(posef + DPV_POSE_ROW * (size_t)fi, posef + DPV_POSE_ROW * (size_t)fj, T, lane);
     DF acc0 = {0.f, 0.f}, acc1 = {0.f, 0.f};  // the two residual components
     for (int b = s0; b < s1; b += 32) {
       const int s = b + lane;
       const int nb = min(32, s1 - b);
       float2* row = rw + lane * ROWP;
-      int kl = 0, e = 0;
+      int k = 0, e = 0;
       float2 wt = make_float2(0.f, 0.f);
       if (s < s1) {
-        kl = dpv_slot_k(eslot[s]);
+        k = g * G + dpv_slot_k(eslot[s]);
         e = perm[s];
         wt = *reinterpret_cast<const float2*>(weights + 2 * (size_t)e);
       }
@@ -184,12 +156,12 @@ __global__ void __launch_bounds__(AD_THREADS, 1) k_assemble_dd(
       for (int px = 0; px < PIX; ++px) {
         if (s < s1) {
           const float2 tg = *reinterpret_cast<const float2*>(targets + 2 * ((size_t)e * PIX + px));
-          const float* pq = pd + PDS * kl;
-          const DF xb0 = PIX == 1 ? DF{pq[0], pq[1]} : DF{pq[2 * px], pq[2 * px + 1]};
-          const DF xb1 = PIX == 1 ? DF{pq[2], pq[3]} : DF{pq[18 + 2 * px], pq[19 + 2 * px]};
-          const float dk = PIX == 1 ? pq[4] : pq[36];
+          const float* pk = patches + 27 * (size_t)k;
+          const int pix = PIX == 1 ? 4 : px;
+          const DF xb0 = dpv_ray_dd(pk[pix], K[2], K[0]);
+          const DF xb1 = dpv_ray_dd(pk[9 + pix], K[3], K[1]);
           EdgeLinDD L;
-          dpv_edge_linearize_dd(T, xb0, xb1, dk, tg.x, tg.y, K, z_min, self_run, L);
+          dpv_edge_linearize_dd(T, xb0, xb1, pk[22], tg.x, tg.y, K, z_min, self_run, L);
           if (L.valid) {
             const float wc[2] = {wt.x, wt.y};
             cst += wc[0] * L.r[0].hi * L.r[0].hi + wc[1] * L.r[1].hi * L.r[1].hi;
@@ -207,10 +179,10 @@ __global__ void __launch_bounds__(AD_THREADS, 1) k_assemble_dd(
             }
 #pragma unroll
             for (int c = 0; c < 2; ++c) {
-              const DF sw = dd_sqrt(DF{wc[c], 0.f});
+              const DF swc = dd_sqrt(DF{wc[c], 0.f});
 #pragma unroll
-              for (int m = 0; m < 6; ++m) row[7 * c + m] = dd_st(dd_mul(sw, L.Jj[c][m]));
-              row[7 * c + 6] = dd_st(dd_mul(sw, L.r[c]));
+              for (int m = 0; m < 6; ++m) row[7 * c + m] = dd_st(dd_mul(swc, L.Jj[c][m]));
+              row[7 * c + 6] = dd_st(dd_mul(swc, L.r[c]));
             }
           } else {
 #pragma unroll
@@ -245,9 +217,13 @@ __global__ void __launch_bounds__(AD_THREADS, 1) k_assemble_dd(
         pt[7] = make_float4(__int_as_float(si | (sj << 8)), 0.f, 0.f, 0.f);
       }
     }
-    // the run's blocks from Hjj and vj: Hij = -Ad^T Hjj, Hii = -Hij Ad
-    // (row a: -Ad^T applied to row a of Hij), vi = -Ad^T vj; in the warp's
-    // staging rows: Hjj full [36], vj [6], Hij [36]
+    if (self_run) continue;  // masked edges: nothing to add (warp-uniform)
+    // the run's blocks from Hjj and vj into S and y: Hjj full [36], vj [6],
+    // then Hij [36] in the warp's staging rows
+    const int o0 = fdx[fi], o1 = fdx[fj];
+    const int oi = o0 < 0 ? -1 : o0 - sd.voff, oj = o1 < 0 ? -1 : o1 - sd.voff;
+    if (oi < 0 && oj < 0) continue;  // both poses held (warp-uniform)
+    double* Sg = S + sd.soff;
     const DF hq = dd_norm(dd_add(acc0, acc1));
     float2* hs = rw;
     __syncwarp();
@@ -255,56 +231,80 @@ __global__ void __launch_bounds__(AD_THREADS, 1) k_assemble_dd(
       if (lane < 21) {
         hs[6 * pa + pb] = dd_st(hq);
         hs[6 * pb + pa] = dd_st(hq);
-        runv[r * NV + 57 + lane] = dd_st(hq);
+        if (oj >= 0) dpv_red_add(Sg + dpv_s_index(oj + pa, oj + pb, sd.TS), dd_to_f64(hq));
       } else {
         hs[36 + pa] = dd_st(hq);
-        runv[r * NV + 84 + pa] = dd_st(hq);
+        if (oj >= 0 && add_v) dpv_red_add(y + sd.voff + oj + pa, dd_to_f64(hq));
       }
     }
     __syncwarp();
-    if (lane < 7) {  // lanes 0..5: column `lane` of Hij; lane 6: vi
+    if (lane < 7) {  // lanes 0..5: column `lane` of Hij = -Ad^T Hjj; lane 6: vi = -Ad^T vj
       DF v[6], o[6];
 #pragma unroll
       for (int m = 0; m < 6; ++m) v[m] = dd_ld(lane < 6 ? hs[6 * m + lane] : hs[36 + m]);
       dpv_adT_dd(T, v, o);
 #pragma unroll
       for (int m = 0; m < 6; ++m) {
-        const float2 x = dd_st(dd_neg(o[m]));
+        const DF x = dd_neg(o[m]);
         if (lane < 6) {
-          hs[42 + 6 * m + lane] = x;
-          runv[r * NV + 21 + 6 * m + lane] = x;
-        } else {
-          runv[r * NV + 78 + m] = x;
+          hs[42 + 6 * m + lane] = dd_st(x);
+          // Hij[m][lane]: row m of frame i, column `lane` of frame j, into the lower triangle of S
+          if (oi >= 0 && oj >= 0) {
+            const size_t at = oi > oj ? dpv_s_index(oi + m, oj + lane, sd.TS) : dpv_s_index(oj + lane, oi + m, sd.TS);
+            dpv_red_add(Sg + at, dd_to_f64(x));
+          }
+        } else if (oi >= 0 && add_v) {
+          dpv_red_add(y + sd.voff + oi + m, dd_to_f64(x));
         }
       }
     }
     __syncwarp();
-    if (lane < 6) {  // row `lane` of Hii, lower part
+    if (lane < 6 && oi >= 0) {  // row `lane` of Hii = -Hij Ad, lower part
       DF v[6], o[6];
 #pragma unroll
       for (int m = 0; m < 6; ++m) v[m] = dd_ld(hs[42 + 6 * lane + m]);
       dpv_adT_dd(T, v, o);
 #pragma unroll
       for (int m = 0; m < 6; ++m)
-        if (m <= lane) runv[r * NV + tri(lane, m)] = dd_st(dd_neg(o[m]));
+        if (m <= lane) dpv_red_add(Sg + dpv_s_index(oi + lane, oi + m, sd.TS), dd_to_f64(dd_neg(o[m])));
     }
     __syncwarp();
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) cst += __shfl_xor_sync(0xffffffffu, cst, o);
   if (cost && lane == 0 && cst != 0.f) atomicAdd(cost, (double)cst);
+}
+
+__global__ void __launch_bounds__(SC_THREADS) k_schur_dd(
+    int G, int P, const int* __restrict__ fdx, const int* __restrict__ gprob, const SysDesc* __restrict__ sysd,
+    float lambda_d, const int* __restrict__ pptr, const int* __restrict__ win, const int* __restrict__ wlen,
+    const float4* __restrict__ pterm, double* __restrict__ S, double* __restrict__ y, float* __restrict__ Ct_out,
+    float* __restrict__ wk_out, float2* __restrict__ Ct2_out, float2* __restrict__ wk2_out,
+    const float* __restrict__ w_ext, int* status) {
+  extern __shared__ float2 sms[];
+  dpv_pdl_enter();
+  if (dpv_status(status)) return;
+  const int g = blockIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int w = wlen[g];
+  const int nr = 6 * w;
+  float2* Eh = sms;                                       // [G][EH_STRIDE]
+  float2* sc = Eh + (size_t)G * EH_STRIDE;                // [G][2]  Ct^-1/2, w Ct^-1/2
+  float* scr_all = reinterpret_cast<float*>(sc + 2 * G);  // [warps][32][12]
+  int* fr = reinterpret_cast<int*>(scr_all + SC_WARPS * 32 * 12);  // [W] unknown row in the group's system, -1 fixed
+  const SysDesc sd = sysd[gprob[g]];
+  for (int q = tid; q < G * EH_STRIDE; q += SC_THREADS) Eh[q] = make_float2(0.f, 0.f);
+  for (int q = tid; q < w; q += SC_THREADS) {
+    const int o = fdx[win[g * DPV_WMAX + q]];
+    fr[q] = o < 0 ? -1 : o - sd.voff;
+  }
   __syncthreads();
 
-  // ---- phase 2: per patch e_k, C_k, w_k as pairs ----------------------------
-  // 16 lanes per patch (two patches per warp), one lane per edge: the
-  // source-frame column and C, w summed over the lanes (pairs), the
-  // target-frame 6-vectors added to their slots of the patch's column by the
-  // first lane of each set of edges with the same target (found with
-  // __match_any_sync; the lanes' terms wait in the warp's staging rows)
+  // ---- per patch e_k, C_k, w_k as pairs: 16 lanes per patch -----------------
   {
-    float* scr = reinterpret_cast<float*>(rows) + wid * 32 * 12;
+    float* scr = scr_all + wid * 32 * 12;
     const int half = lane >> 4, hl = lane & 15;
-    for (int q0 = 2 * wid; q0 < G; q0 += 2 * AD_WARPS) {
+    for (int q0 = 2 * wid; q0 < G; q0 += 2 * SC_WARPS) {
       const int q = q0 + half;
       const int k = g * G + q;
       const bool mine = q < G && k < P;
@@ -399,35 +399,12 @@ __global__ void __launch_bounds__(AD_THREADS, 1) k_assemble_dd(
   }
   __syncthreads();
 
-  // ---- phase 2b: run sums per window block (in the staging space) ----------
-  signed char* prt = reinterpret_cast<signed char*>(rows);
-  float2* dgb = rows + DPV_WMAX * DPV_WMAX / 8;
-  float2* yrn = dgb + DPV_WMAX * 21;
-  for (int q = tid; q < w * w; q += AD_THREADS) prt[q] = -1;
-  __syncthreads();
-  for (int r = tid; r < nruns; r += AD_THREADS) {
-    const int si = rsl[r] & 0xff, sj = rsl[r] >> 8;
-    if (si != sj) prt[si * w + sj] = (signed char)r;
-  }
-  for (int q = tid; q < 27 * w; q += AD_THREADS) {
-    const int a = q / 27, e = q - 27 * a;
-    const int oi = e < 21 ? e : 78 + (e - 21), oj = e < 21 ? 57 + e : 84 + (e - 21);
-    DF acc = {0.f, 0.f};
-    for (int r = 0; r < nruns; ++r) {
-      const int si = rsl[r] & 0xff, sj = rsl[r] >> 8;
-      if (si == sj) continue;
-      const float2* rv = runv + r * NV;
-      if (si == a) dd_acc_add(acc, dd_ld(rv[oi]));
-      if (sj == a) dd_acc_add(acc, dd_ld(rv[oj]));
-    }
-    if (e < 21) dgb[a * 21 + e] = dd_st(dd_norm(acc));
-    else yrn[a * 6 + (e - 21)] = dd_st(dd_norm(acc));
-  }
-  __syncthreads();
-
-  // ---- phase 3: window Schur complement into the global S and y -----------
+  // ---- the window's Schur product into S and y ------------------------------
+  // one thread per 3x3 sub-block (rows 3ha.. of frame a, columns 3hb.. of
+  // frame b, a >= b): nine independent double-float sums over the patches
   const int nblk = tri(w, 0);
-  for (int t = tid; t < 4 * nblk; t += AD_THREADS) {
+  double* Sg = S + sd.soff;
+  for (int t = tid; t < 4 * nblk; t += SC_THREADS) {
     const int blk = t >> 2, ha = (t >> 1) & 1, hb = t & 1;
     const int a = tri_row(blk), b = blk - tri(a, 0);
     if (a == b && hb > ha) continue;
@@ -452,31 +429,7 @@ __global__ void __launch_bounds__(AD_THREADS, 1) k_assemble_dd(
 #pragma unroll
         for (int j = 0; j < 3; ++j) dd_acc(acc[i][j], er[i], ec[j]);
     }
-    if (a == b) {
-#pragma unroll
-      for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int j = 0; j < 3; ++j)
-          if (3 * hb + j <= 3 * ha + i) dd_acc_add(acc[i][j], dd_ld(dgb[a * 21 + tri(3 * ha + i, 3 * hb + j)]));
-    } else {
-      const int r1 = prt[a * w + b], r2 = prt[b * w + a];
-      if (r1 >= 0) {  // run a -> b: Hij rows belong to a
-        const float2* rv = runv + r1 * NV + 21;
-#pragma unroll
-        for (int i = 0; i < 3; ++i)
-#pragma unroll
-          for (int j = 0; j < 3; ++j) dd_acc_add(acc[i][j], dd_ld(rv[6 * (3 * ha + i) + 3 * hb + j]));
-      }
-      if (r2 >= 0) {  // run b -> a: Hij rows belong to b (transposed)
-        const float2* rv = runv + r2 * NV + 21;
-#pragma unroll
-        for (int i = 0; i < 3; ++i)
-#pragma unroll
-          for (int j = 0; j < 3; ++j) dd_acc_add(acc[i][j], dd_ld(rv[6 * (3 * hb + j) + 3 * ha + i]));
-      }
-    }
     const int gr = ra0 + 3 * ha, gc = rb0 + 3 * hb;
-    double* Sg = S + sd.soff;
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
@@ -484,11 +437,10 @@ __global__ void __launch_bounds__(AD_THREADS, 1) k_assemble_dd(
         if (a != b || 3 * hb + j <= 3 * ha + i)
           dpv_red_add(Sg + dpv_s_index(gr + i, gc + j, sd.TS), dd_to_f64(dd_norm(acc[i][j])));
   }
-  for (int R = tid; R < nr; R += AD_THREADS) {
+  for (int R = tid; R < nr; R += SC_THREADS) {
     const int a = R / 6, ra = R - 6 * a;
     if (fr[a] < 0) continue;
     DF acc = {0.f, 0.f};
-    if (!w_ext) acc = dd_ld(yrn[R]);  // with an external right-hand side v comes from y's init
     for (int kl = 0; kl < G; ++kl) dd_acc(acc, dd_neg(dd_ld(Eh[(size_t)kl * EH_STRIDE + R])), dd_ld(sc[2 * kl + 1]));
     dpv_red_add(y + sd.voff + fr[a] + ra, dd_to_f64(dd_norm(acc)));
   }
@@ -505,31 +457,39 @@ ba_status_t setup_dd(ba_handle_t h) {
   for (int a = 0; a < 6; ++a, ++q) { pa[q] = a; pb[q] = 6; }     // vj
   DPV_CUDA(h, cudaMemcpyToSymbol(c_qa, pa, NJ));
   DPV_CUDA(h, cudaMemcpyToSymbol(c_qb, pb, NJ));
-  DPV_CUDA(h, cudaFuncSetAttribute(k_assemble_dd<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)assemble_dd_smem_bytes(DPV_GMAX_DD, 1)));
-  DPV_CUDA(h, cudaFuncSetAttribute(k_assemble_dd<9>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)assemble_dd_smem_bytes(DPV_GMAX_DD, 9)));
+  DPV_CUDA(h, cudaFuncSetAttribute(k_schur_dd, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)schur_smem_bytes(DPV_GMAX_DD)));
+  // all of the unified L1 / shared storage as shared memory: two Schur CTAs per SM at G = 32
+  DPV_CUDA(h, cudaFuncSetAttribute(k_schur_dd, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
   g_dd_ready = true;
   return BA_OK;
 }
 
 }  // namespace
 
-// The double-float assembly launch (BA_MIXED); the caller has prepared S, y
-// and the pose table as for k_assemble.
+// The double-float assembly launches (BA_MIXED); the caller has prepared S,
+// y and the pose table as for k_assemble.  With an external right-hand side
+// (w_ext, the adjoint) the runs add no v: y's initial contents stand for it.
 ba_status_t dpv_assemble_dd(ba_handle_t h, double* cost, const float* w_ext) {
   Workspace* ws = h->ws;
   ba_status_t s = setup_dd(h);
   if (s) return s;
   if (h->G > DPV_GMAX_DD)
     return dpv_fail(h, BA_ERR_UNSUPPORTED, "the mixed-precision assembly takes at most 32 patches per group");
-  auto kern = h->opt.residual_pixels == 9 ? k_assemble_dd<9> : k_assemble_dd<1>;
-  DPV_CUDA(h, dpv_launch_pdl(kern, dim3(h->ngroups), dim3(AD_THREADS),
-                             assemble_dd_smem_bytes(h->G, h->opt.residual_pixels), h->stream, h->G, h->P, ws->fdx.p,
-                             ws->gprob.p, ws->sysd.p, h->opt.lambda_depth, h->opt.z_min, ws->gptr.p, ws->grun.p,
-                             ws->gnr.p, ws->eslot.p, ws->perm.p, ws->pmpos.p, ws->pptr.p, ws->win.p, ws->wlen.p,
-                             ws->posef.p, h->patches, h->targets, h->weights, ws->intr, ws->pterm.p, ws->S.p,
-                             ws->y.p, ws->Ct.p, ws->wk.p, ws->Ct2.p, ws->wk2.p, cost, w_ext, ws->status));
+  auto kern = h->opt.residual_pixels == 9 ? k_runs_dd<9> : k_runs_dd<1>;
+  DPV_CUDA(h, dpv_launch_pdl(kern, dim3(h->ngroups), dim3(RW * 32), runs_smem_bytes(), h->stream, h->G, h->P,
+                             (const int*)ws->fdx.p, (const int*)ws->gprob.p, (const SysDesc*)ws->sysd.p,
+                             h->opt.z_min, (const int*)ws->gptr.p, (const int*)ws->grun.p, (const int*)ws->gnr.p,
+                             (const unsigned*)ws->eslot.p, (const int*)ws->perm.p, (const int*)ws->pmpos.p,
+                             (const int*)ws->win.p, (const float*)ws->posef.p, (const float*)h->patches, h->targets,
+                             h->weights, (const float*)ws->intr, ws->pterm.p, ws->S.p, ws->y.p, cost, w_ext ? 0 : 1,
+                             ws->status));
+  ++h->launches;
+  DPV_CUDA(h, dpv_launch_pdl(k_schur_dd, dim3(h->ngroups), dim3(SC_THREADS), schur_smem_bytes(h->G), h->stream, h->G,
+                             h->P, (const int*)ws->fdx.p, (const int*)ws->gprob.p, (const SysDesc*)ws->sysd.p,
+                             h->opt.lambda_depth, (const int*)ws->pptr.p, (const int*)ws->win.p,
+                             (const int*)ws->wlen.p, (const float4*)ws->pterm.p, ws->S.p, ws->y.p, ws->Ct.p, ws->wk.p,
+                             ws->Ct2.p, ws->wk2.p, w_ext, ws->status));
   ++h->launches;
   return BA_OK;
 }
