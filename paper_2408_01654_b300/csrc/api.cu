@@ -329,7 +329,8 @@ ba_status_t ensure_system(ba_handle_t h, int fixed) {
   ba_status_t s;
   if ((s = dpv_grow(h, ws->S, soff, "pose system")) || (s = dpv_grow(h, ws->y, voff, "rhs")) ||
       (s = dpv_grow(h, ws->dx, voff, "step")) || (s = dpv_grow(h, ws->r64, voff, "residual")) ||
-      (s = dpv_grow(h, ws->tmpv, voff, "vector")) || (s = dpv_grow(h, ws->sysd, B, "system table")) ||
+      (s = dpv_grow(h, ws->tmpv, voff, "vector")) || (s = dpv_grow(h, ws->dx2, voff, "step pairs")) ||
+      (s = dpv_grow(h, ws->sysd, B, "system table")) ||
       (s = dpv_grow(h, ws->syslist, B, "system lists")) || (s = dpv_grow(h, ws->fdx, h->N, "frame map")))
     return s;
   if (large_scratch > 0 && (s = dpv_grow(h, ws->L, large_scratch, "factor"))) return s;
@@ -385,7 +386,8 @@ ba_status_t dpv_ensure_generic_system(ba_handle_t h, int n) {
   ba_status_t s;
   if ((s = dpv_grow(h, ws->S, soff, "pose system")) || (s = dpv_grow(h, ws->y, d.n_pad, "rhs")) ||
       (s = dpv_grow(h, ws->dx, d.n_pad, "step")) || (s = dpv_grow(h, ws->r64, d.n_pad, "residual")) ||
-      (s = dpv_grow(h, ws->tmpv, d.n_pad, "vector")) || (s = dpv_grow(h, ws->sysd, 1, "system table")) ||
+      (s = dpv_grow(h, ws->tmpv, d.n_pad, "vector")) || (s = dpv_grow(h, ws->dx2, d.n_pad, "step pairs")) ||
+      (s = dpv_grow(h, ws->sysd, 1, "system table")) ||
       (s = dpv_grow(h, ws->syslist, 1, "system lists")))
     return s;
   if (large_scratch > 0 && (s = dpv_grow(h, ws->L, large_scratch, "factor"))) return s;
@@ -470,7 +472,7 @@ ba_status_t ba_destroy(ba_handle_t h) {
     release(ws->gptr); release(ws->win); release(ws->wlen);
     release(ws->scan); release(ws->S); release(ws->y); release(ws->dx); release(ws->Ct); release(ws->wk);
     release(ws->dd); release(ws->L); release(ws->r64); release(ws->tmpv); release(ws->pmpos); release(ws->pptr);
-    release(ws->pterm); release(ws->posef); release(ws->Ct2); release(ws->wk2);
+    release(ws->pterm); release(ws->posef); release(ws->Ct2); release(ws->wk2); release(ws->dx2);
     release(ws->tp_poses); release(ws->tp_patches); release(ws->tp_dx); release(ws->tp_dd);
     release(ws->ad_xb); release(ws->ad_w); release(ws->ad_gd); release(ws->ad_lamd); release(ws->ad_v);
     release(ws->ad_gt); release(ws->ad_gw); release(ws->lg_sync); release(ws->lg_red); release(ws->lg_prob); release(ws->lg_rb); release(ws->fprob); release(ws->gprob);

@@ -187,6 +187,7 @@ struct Workspace {
   DBuf<double> S;                 // tiled lower triangle of the pose system (FP64 accumulation)
   DBuf<double> y;                 // [n_pad]
   DBuf<double> dx;                // [n_pad]
+  DBuf<float2> dx2;               // [n_pad] the step as double-float pairs (BA_MIXED back-substitution)
   DBuf<float> Ct, wk, dd;         // [P]
   DBuf<float2> Ct2, wk2;          // [P] Ct and w as double-float pairs (BA_MIXED)
   DBuf<float> posef;              // [N][16] R (9), camera centre hi (3), lo (3)

@@ -79,13 +79,22 @@ __global__ void __launch_bounds__(BS_THREADS) k_backsub(
   }
 }
 
+// The pose step as double-float pairs (once per solve, for the double-float
+// back-substitution: splitting it there would repeat the split for every edge).
+__global__ void k_dx_pairs(int n, const double* __restrict__ dx, float2* __restrict__ dx2, const int* status) {
+  dpv_pdl_enter();
+  if (dpv_status(status)) return;
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q < n) dx2[q] = dpv_d2df_bits(dx[q]);
+}
+
 // The same in double-float (the BA_MIXED path): the depth terms are pairs
-// (128 bytes per edge, assemble_df.cu), the pose step is read in FP64 and
-// split into pairs, Ct and w are pairs, and the new depth d + dd is rounded
-// to float once.
+// (128 bytes per edge, assemble_df.cu), the pose step comes as pairs
+// (k_dx_pairs), Ct and w are pairs, and the new depth d + dd is rounded to
+// float once.
 __global__ void __launch_bounds__(BS_THREADS) k_backsub_dd(
     int P, int G, const int* __restrict__ fdx, float d_min, const int* __restrict__ pptr,
-    const float4* __restrict__ pterm, const int* __restrict__ win, const double* __restrict__ dxv,
+    const float4* __restrict__ pterm, const int* __restrict__ win, const float2* __restrict__ dxv,
     const float2* __restrict__ Ct2, const float2* __restrict__ wk2, const float* __restrict__ w_ext,
     float* __restrict__ patches, float* __restrict__ dd_out, int N, int retract, const double* __restrict__ dx,
     double* __restrict__ poses, float* __restrict__ posef, int write_depth, const int* status) {
@@ -113,13 +122,12 @@ __global__ void __launch_bounds__(BS_THREADS) k_backsub_dd(
       const int fo = side == 0 ? fi : fj;
       if (fo < 0) continue;
       const float4* e4 = t4 + 3 * side;
-      const double* x = dxv + fo;
+      const float4* x = reinterpret_cast<const float4*>(dxv + fo);  // fo is even: 16-byte aligned
 #pragma unroll
       for (int h2 = 0; h2 < 3; ++h2) {
-        const float4 v = e4[h2];
-        const float2 x0 = dpv_d2df_bits(x[2 * h2]), x1 = dpv_d2df_bits(x[2 * h2 + 1]);
-        dd_acc(acc, DF{-v.x, -v.y}, DF{x0.x, x0.y});
-        dd_acc(acc, DF{-v.z, -v.w}, DF{x1.x, x1.y});
+        const float4 v = e4[h2], xv = x[h2];
+        dd_acc(acc, DF{-v.x, -v.y}, DF{xv.x, xv.y});
+        dd_acc(acc, DF{-v.z, -v.w}, DF{xv.z, xv.w});
       }
     }
   }
@@ -153,9 +161,12 @@ unsigned backsub_grid(ba_handle_t h, int retract) {
 ba_status_t dpv_backsub(ba_handle_t h, int retract) {
   Workspace* ws = h->ws;
   if (h->opt.precision == BA_MIXED) {
+    DPV_CUDA(h, dpv_launch_pdl(k_dx_pairs, dim3((h->n_pad + 255) / 256), dim3(256), 0, h->stream, h->n_pad,
+                               (const double*)ws->dx.p, ws->dx2.p, (const int*)ws->status));
+    ++h->launches;
     DPV_CUDA(h, dpv_launch_pdl(k_backsub_dd, dim3(backsub_grid(h, retract)), dim3(BS_THREADS), 0, h->stream, h->P,
                                h->G, ws->fdx.p, h->opt.d_min, ws->pptr.p, ws->pterm.p, ws->win.p,
-                               (const double*)ws->dx.p, (const float2*)ws->Ct2.p, (const float2*)ws->wk2.p,
+                               (const float2*)ws->dx2.p, (const float2*)ws->Ct2.p, (const float2*)ws->wk2.p,
                                (const float*)nullptr, h->patches, ws->dd.p, h->N, retract, (const double*)ws->dx.p,
                                h->poses, ws->posef.p, 1, (const int*)ws->status));
     ++h->launches;
@@ -176,8 +187,10 @@ ba_status_t dpv_backsub(ba_handle_t h, int retract) {
 ba_status_t dpv_backsub_ext(ba_handle_t h, const float* w_ext, float* out) {
   Workspace* ws = h->ws;
   if (h->opt.precision == BA_MIXED) {
+    k_dx_pairs<<<(h->n_pad + 255) / 256, 256, 0, h->stream>>>(h->n_pad, ws->dx.p, ws->dx2.p, ws->status);
+    ++h->launches;
     k_backsub_dd<<<backsub_grid(h, 0), BS_THREADS, 0, h->stream>>>(
-        h->P, h->G, ws->fdx.p, h->opt.d_min, ws->pptr.p, ws->pterm.p, ws->win.p, ws->dx.p, ws->Ct2.p, ws->wk2.p,
+        h->P, h->G, ws->fdx.p, h->opt.d_min, ws->pptr.p, ws->pterm.p, ws->win.p, ws->dx2.p, ws->Ct2.p, ws->wk2.p,
         w_ext, h->patches, out, h->N, 0, ws->dx.p, h->poses, nullptr, 0, ws->status);
     ++h->launches;
     DPV_CUDA(h, cudaGetLastError());
