@@ -49,6 +49,9 @@ WORKLOADS = {
     "odometry_full": ("odometry-window BA with the whole-patch residual (Eq. 3 over all nine patch pixels, 18 rows "
                       "per edge): 22 keyframes, 96 patches/frame, patch lifetime 13, 8% outliers, 2 GN iterations, "
                       "2 fixed poses", lambda seed=0: full_patch_scene(scenes.odometry(seed))),
+    "window": ("odometry-style window BA of --frames keyframes: 96 patches/frame, patch lifetime 13, no outliers, "
+               "2 GN iterations, 2 fixed poses (graph-size sweep of the dense and block-sparse forms)",
+               scenes.window),
     "tiny": ("tiny BA: 8 frames, 96 patches/frame, +-3 frame edges, 2 GN iterations, 2 fixed poses", scenes.tiny),
     "global": ("global loop-closure BA: 1000 keyframes, 96 patches/frame, +-6 local + proximity loop edges, "
                "4 GN iterations, 2 fixed poses", scenes.global_ba),
@@ -104,13 +107,17 @@ def parse():
                     help="fp32 or mixed; the loop-closure (global, loop400), batched and pgo workloads default "
                          "to mixed, the others to fp32")
     ap.add_argument("--group", type=int, default=0, help="patches per group (0 = automatic)")
+    ap.add_argument("--frames", type=int, default=22, help="keyframes of the window workload")
+    ap.add_argument("--dense", choices=["auto", "always", "never"], default="auto",
+                    help="dense or block-sparse iteration (ba_options_t.dense_policy; the dense form applies to "
+                         "single FP32 problems of at most 256 pose unknowns with the centre residual)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-capture", action="store_true", help="eager ba_step instead of CUDA-graph replay")
     ap.add_argument("--no-autotune", action="store_true", help="skip the group-size autotuner")
     a = ap.parse_args()
     if a.steps is None:
         # (the reference arm's oracle steps are ~50 ms each on one core: 50 of them)
-        short = a.workload in ("odometry", "odometry_full", "tiny", "proximity", "correlation")
+        short = a.workload in ("odometry", "odometry_full", "tiny", "window", "proximity", "correlation")
         a.steps = 3 if not short else (50 if a.impl == "reference" else 2000)
         if a.workload in ("global", "loop400") and a.impl == "ours":
             a.steps = 20  # ~0.5 s of timed steps: several clock samples
@@ -1036,7 +1043,9 @@ def run_reference(args):
         }
         print(json.dumps(line))
         return 0
-    scene = make(seed=0)
+    scene = make(seed=0, N=args.frames) if args.workload == "window" else make(seed=0)
+    if args.workload == "window":
+        desc = desc.replace("--frames", str(args.frames))
     if scene.N >= LARGE_FRAMES:
         # one GN iteration per step (a full run of the loop-closure BA
         # takes minutes on one core)
@@ -1102,14 +1111,19 @@ def run_ours(args):
     if dist:
         dist.barrier()
     desc, make = WORKLOADS[args.workload]
-    scene = make(seed=problem_seed(rank))  # independent problems per rank, no data-path collective
+    # independent problems per rank, no data-path collective
+    if args.workload == "window":
+        desc = desc.replace("--frames", str(args.frames))
+        scene = make(seed=problem_seed(rank), N=args.frames)
+    else:
+        scene = make(seed=problem_seed(rank))
     dev = torch.device("cuda", local)
     peaks = measure_peaks(dev)
     T = scene_tensors(scene, dev)
     pristine = {k: v.clone() for k, v in T.items()}
     stream = torch.cuda.current_stream(dev)
     ba = DPVBA(precision=args.precision, patches_per_group=args.group, stream=stream,
-               residual_pixels=residual_pixels(args.workload))
+               residual_pixels=residual_pixels(args.workload), dense=args.dense)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > L2 (126 MB)
     ba.set_graph(**T)
     tuning = None
@@ -1153,6 +1167,7 @@ def run_ours(args):
     total_ms = sum(step_ms)
     prof = ba.profile_read()
     launches = ba.info()["launches"] - launches0
+    form = "dense" if ba.info()["dense"] else "block-sparse"  # of the timed steps
     replays = {"ba_step": ba.info()["graph_replays"], "binding": ba.info()["bind_replays"]}
     total_ms = max_over_ranks(total_ms, dev)  # the slowest rank's time
     gn_iters = world * args.steps * scene.iters
@@ -1264,6 +1279,7 @@ def run_ours(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": desc, "N": scene.N, "P": scene.P, "E": scene.E, "iters": scene.iters,
                    "fixed": scene.fixed, "precision": args.precision, "patches_per_group": inf["G"],
+                   "dense_policy": args.dense, "form": form,
                    "autotune": tuning, "graph_replay": not args.no_capture, "graph_replays": replays,
                    "l2": "flushed between steps (256 MiB write)", "step": "ba_set_graph + ba_step"},
         "edges_per_sec": value * scene.E,

@@ -102,7 +102,29 @@ typedef struct {
                               pixel order), the weights stay [E,2] and are shared
                               by the edge's nine residuals; ba_backward's target
                               cotangents take the targets' layout                  */
+  int dense_policy;        /* ba_dense_policy_t: the dense or the block-sparse form
+                              of an iteration (default BA_DENSE_AUTO)              */
 } ba_options_t;
+
+/* The two forms of a Gauss-Newton iteration (the appendix "Bundle-Adjustment
+ * Efficiency" compares DPVO's dense bundle adjustment with the block-sparse
+ * one and switches between them on the fly by graph size).  The dense form
+ * scatters every edge's products into dense arrays (the pose system, the
+ * pose-depth matrix E with one column per patch, C and w) and forms
+ * S = B - E Ct^-1 E^T as one dense product; the block-sparse form reduces
+ * each (source, target) run and each patch group's window and adds only the
+ * window blocks to S.  The dense form applies to one problem bound by
+ * ba_set_graph with BA_FP32, residual_pixels = 1, 6 to 256 pose unknowns and
+ * no tape being recorded (the adjoint runs on the block-sparse form); in any
+ * other case the block-sparse form runs. */
+typedef enum {
+  BA_DENSE_AUTO = 0,   /* dense where it applies and the graph has at most the
+                          measured crossover number of edges; on B300 the
+                          block-sparse form measured faster at every size (8
+                          to 44 keyframes), so this selects block-sparse       */
+  BA_DENSE_ALWAYS = 1, /* dense wherever it applies                             */
+  BA_DENSE_NEVER = 2   /* block-sparse always                                   */
+} ba_dense_policy_t;
 
 /* Fill *opt with the defaults above. */
 DPVBA_API ba_status_t ba_default_options(ba_options_t* opt);
@@ -250,7 +272,8 @@ DPVBA_API ba_status_t ba_debug_export(ba_handle_t h, int what, void* dst, long l
  * info[0..14] = N, P, E, patches_per_group, groups, n (last fixed), tile size, runs,
  * kernels launched by the handle so far; then for the CUDA graphs of
  * ba_set_capture: ba_step captures, replays, kernels in one replay, and the
- * same three for the binding's device work (ba_set_graph*). */
+ * same three for the binding's device work (ba_set_graph*); info[15] = 1 if
+ * the last ba_step ran the dense form (ba_dense_policy_t), else 0. */
 DPVBA_API ba_status_t ba_debug_info(ba_handle_t h, long long* info, int cap);
 
 /* Canonical pose-pose block keys of the B part of the system, computed on the

@@ -32,11 +32,14 @@ class DPVBA:
 
     def __init__(self, precision: str = "fp32", lambda_pose=1e-4, lambda_depth=1e-4, z_min=0.1, d_min=1e-3,
                  patches_per_group: int = 0, max_refine: int = 3, stream: torch.cuda.Stream | None = None,
-                 capture: bool = False, residual_pixels: int = 1, timeout_cycles: int | None = None):
+                 capture: bool = False, residual_pixels: int = 1, timeout_cycles: int | None = None,
+                 dense: str = "auto"):
         self._lib = capi.lib()
         self._h = ctypes.c_void_p()
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         extra = {} if timeout_cycles is None else {"timeout_cycles": int(timeout_cycles)}
+        extra["dense_policy"] = {"auto": capi.BA_DENSE_AUTO, "always": capi.BA_DENSE_ALWAYS,
+                                 "never": capi.BA_DENSE_NEVER}[dense]
         opt = capi.default_options(
             precision=capi.BA_MIXED if precision == "mixed" else capi.BA_FP32, lambda_pose=lambda_pose,
             lambda_depth=lambda_depth, z_min=z_min, d_min=d_min, patches_per_group=patches_per_group,
@@ -269,10 +272,10 @@ class DPVBA:
         capi.check(self._h, self._lib.ba_linearize(self._h, fixed))
 
     def info(self) -> dict:
-        arr = (ctypes.c_longlong * 15)()
-        capi.check(self._h, self._lib.ba_debug_info(self._h, arr, 15))
+        arr = (ctypes.c_longlong * 16)()
+        capi.check(self._h, self._lib.ba_debug_info(self._h, arr, 16))
         keys = ("N", "P", "E", "G", "groups", "n", "tile", "runs", "launches", "graph_captures", "graph_replays",
-                "graph_kernels", "bind_captures", "bind_replays", "bind_kernels")
+                "graph_kernels", "bind_captures", "bind_replays", "bind_kernels", "dense")
         return dict(zip(keys, list(arr)))
 
     def export(self, what: int, count: int | None = None) -> torch.Tensor:

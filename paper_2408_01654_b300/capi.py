@@ -20,6 +20,9 @@ BA_FP32, BA_MIXED = 0, 1
 WMAX = 64
 
 
+BA_DENSE_AUTO, BA_DENSE_ALWAYS, BA_DENSE_NEVER = 0, 1, 2
+
+
 class BAOptions(ctypes.Structure):
     _fields_ = [
         ("precision", ctypes.c_int),
@@ -32,6 +35,7 @@ class BAOptions(ctypes.Structure):
         ("timeout_cycles", ctypes.c_longlong),
         ("stream", ctypes.c_void_p),
         ("residual_pixels", ctypes.c_int),
+        ("dense_policy", ctypes.c_int),
     ]
 
 

@@ -425,6 +425,7 @@ ba_status_t ba_default_options(ba_options_t* opt) {
   opt->timeout_cycles = 2000000000LL;
   opt->stream = nullptr;
   opt->residual_pixels = 1;
+  opt->dense_policy = BA_DENSE_AUTO;
   return BA_OK;
 }
 
@@ -437,7 +438,8 @@ ba_status_t ba_create(ba_handle_t* out, const ba_options_t* opt) {
   else ba_default_options(&h->opt);
   if (h->opt.patches_per_group < 0 || h->opt.patches_per_group > dpv_max_group(h) ||
       (h->opt.precision != BA_FP32 && h->opt.precision != BA_MIXED) || h->opt.max_refine < 0 ||
-      (h->opt.residual_pixels != 1 && h->opt.residual_pixels != 9) ||
+      (h->opt.residual_pixels != 1 && h->opt.residual_pixels != 9) || h->opt.dense_policy < 0 ||
+      h->opt.dense_policy > BA_DENSE_NEVER ||
       h->opt.max_refine > 16) {
     delete h;
     return BA_ERR_INVALID_ARG;
@@ -473,6 +475,7 @@ ba_status_t ba_destroy(ba_handle_t h) {
     release(ws->scan); release(ws->S); release(ws->y); release(ws->dx); release(ws->Ct); release(ws->wk);
     release(ws->dd); release(ws->L); release(ws->r64); release(ws->tmpv); release(ws->pmpos); release(ws->pptr);
     release(ws->pterm); release(ws->posef); release(ws->Ct2); release(ws->wk2); release(ws->dx2);
+    release(ws->dE); release(ws->dCw);
     release(ws->tp_poses); release(ws->tp_patches); release(ws->tp_dx); release(ws->tp_dd);
     release(ws->ad_xb); release(ws->ad_w); release(ws->ad_gd); release(ws->ad_lamd); release(ws->ad_v);
     release(ws->ad_gt); release(ws->ad_gw); release(ws->lg_sync); release(ws->lg_red); release(ws->lg_prob); release(ws->lg_rb); release(ws->fprob); release(ws->gprob);
@@ -857,6 +860,7 @@ ba_status_t ba_step(ba_handle_t h, int iters, int fixed_poses) {
   if (iters < 0) return dpv_fail(h, BA_ERR_INVALID_ARG, "iters < 0");
   if ((s = ensure_system(h, fixed_poses))) return s;
   h->last_iters = iters;
+  h->last_dense = dpv_use_dense(h) ? 1 : 0;
   // fixed_poses = N leaves no pose unknowns: the iterations then update the
   // inverse depths only (structure-only bundle adjustment)
   const int run = iters > 0 ? iters : 0;
@@ -915,10 +919,11 @@ ba_status_t ba_debug_info(ba_handle_t h, long long* info, int cap) {
     for (int v : gnr) nr += v;
   }
   const ba_handle_s::CapGraph &sg = h->step_graph, &bg = h->bind_graph;
-  const long long v[15] = {h->N,        h->P,       h->E,        h->G,        h->ngroups,
+  const long long v[16] = {h->N,        h->P,       h->E,        h->G,        h->ngroups,
                            h->n,        h->TS,      nr,          h->launches, sg.captures,
-                           sg.replays,  sg.kernels, bg.captures, bg.replays,  bg.kernels};
-  for (int q = 0; q < cap && q < 15; ++q) info[q] = v[q];
+                           sg.replays,  sg.kernels, bg.captures, bg.replays,  bg.kernels,
+                           h->last_dense};
+  for (int q = 0; q < cap && q < 16; ++q) info[q] = v[q];
   return BA_OK;
 }
 

@@ -566,6 +566,11 @@ ba_status_t assemble_impl(ba_handle_t h, int it, const double* v_ext, const floa
   }
   double* cost = it < 0 ? nullptr : ws->cost + (it < ws->cost_cap ? it : ws->cost_cap - 1);
   dpv_prof_begin(h, BA_KERNEL_ASSEMBLE);
+  if (!v_ext && !w_ext && dpv_use_dense(h)) {  // the dense form of small graphs (dense.cu)
+    ba_status_t s2 = dpv_dense_assemble(h, cost);
+    dpv_prof_end(h);
+    return s2;
+  }
   if (h->opt.precision == BA_MIXED) {  // the double-float linearisation (assemble_df.cu)
     ba_status_t s2 = dpv_assemble_dd(h, cost, w_ext);
     dpv_prof_end(h);

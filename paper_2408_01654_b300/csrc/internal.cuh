@@ -13,6 +13,13 @@
 #define DPV_WMAX 64          // frames in one group window (slots fit in 8 bits)
 #define DPV_GMAX 64          // patches per group
 #define DPV_GMAX_DD 32       // patches per group of the double-float (BA_MIXED) assembly
+#define DPV_DENSE_MAX_ENTRIES (8LL << 20)  // dense pose-depth matrix of the dense form: n_pad x P entries at most
+// BA_DENSE_AUTO takes the dense form up to this many edges: the measured
+// crossover on B300 is below the smallest graph measured (8 keyframes, 5,376
+// edges: 237 us dense vs 172 us block-sparse per two-iteration step, the
+// block-sparse form ahead at every size up to 44 keyframes), so automatic
+// selection keeps the block-sparse form
+#define DPV_DENSE_AUTO_EDGES 0
 #define DPV_SMALL_N 256      // pose systems up to this size use the one-CTA solver
 #define DPV_TILE 64          // tile edge of the blocked pose system (large n)
 #define DPV_RMAX 64          // (source, target) runs in one group
@@ -79,6 +86,7 @@ struct ba_handle_s {
   std::vector<int> small_nq[9];   // systems solved by the one-CTA solver, by 32-row blocks
   std::vector<int> large_sys;     // systems solved by the persistent tiled solver
   int last_iters = 0;
+  int last_dense = 0;   // the last ba_step ran the dense form
 
   Workspace* ws = nullptr;
 
@@ -190,6 +198,8 @@ struct Workspace {
   DBuf<float2> dx2;               // [n_pad] the step as double-float pairs (BA_MIXED back-substitution)
   DBuf<float> Ct, wk, dd;         // [P]
   DBuf<float2> Ct2, wk2;          // [P] Ct and w as double-float pairs (BA_MIXED)
+  DBuf<double> dE;                // [P][n_pad] the dense form's pose-depth columns
+  DBuf<double> dCw;               // [P][2] the dense form's C and w
   DBuf<float> posef;              // [N][16] R (9), camera centre hi (3), lo (3)
   DBuf<float4> pterm;             // [E][4] per-edge depth terms, patch-major (see assemble.cu);
                                   // [E][8] as double-float pairs with BA_MIXED (assemble_df.cu)
@@ -272,6 +282,9 @@ long long dpv_hist_entries(long long m);
 ba_status_t dpv_assemble(ba_handle_t h, int it, int skip_init);
 ba_status_t dpv_assemble_ext(ba_handle_t h, int it, const double* v_ext, const float* w_ext);
 ba_status_t dpv_assemble_dd(ba_handle_t h, double* cost, const float* w_ext);  // assemble_df.cu
+bool dpv_use_dense(ba_handle_t h);                       // dense.cu: the dense form for the next iterations
+ba_status_t dpv_dense_assemble(ba_handle_t h, double* cost);
+ba_status_t dpv_dense_backsub(ba_handle_t h);
 // largest patches-per-group the handle's assembly kernel supports
 inline int dpv_max_group(ba_handle_t h) { return h->opt.precision == BA_MIXED ? DPV_GMAX_DD : DPV_GMAX; }
 // The solvers stop once the estimated error left in the pose step is below

@@ -160,6 +160,7 @@ unsigned backsub_grid(ba_handle_t h, int retract) {
 // poses and their rows of the linearisation table.
 ba_status_t dpv_backsub(ba_handle_t h, int retract) {
   Workspace* ws = h->ws;
+  if (retract && dpv_use_dense(h)) return dpv_dense_backsub(h);  // the dense form (dense.cu)
   if (h->opt.precision == BA_MIXED) {
     DPV_CUDA(h, dpv_launch_pdl(k_dx_pairs, dim3((h->n_pad + 255) / 256), dim3(256), 0, h->stream, h->n_pad,
                                (const double*)ws->dx.p, ws->dx2.p, (const int*)ws->status));

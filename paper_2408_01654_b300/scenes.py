@@ -251,6 +251,14 @@ def odometry(seed: int = 0) -> Scene:
                   2, 2, outlier_frac=0.08)
 
 
+def window(seed: int = 0, N: int = 22) -> Scene:
+    """Odometry-style window of N keyframes: patch lifetime 13 (each patch
+    linked to the 13 frames of a 14-frame window around its source), no
+    outliers, 2 GN iterations, 2 fixed poses (the graph-size sweep of the
+    dense and block-sparse forms)."""
+    return _build("window", seed, N, lambda i, n: _shifted_window(i, n, 14), 2, 2)
+
+
 def global_ba(seed: int = 0, N: int = 1000) -> Scene:
     """Global loop-closure BA: 1000 keyframes, local edges within +-6 frames
     plus proximity loop edges, 4 GN iterations."""
