@@ -198,16 +198,34 @@ def measure_peaks(dev):
     return out
 
 
-def factor_flops(ns):
+def factor_flops(envs):
     """Algorithmic flops of the LDL^T factorisations run by the persistent
-    tensor-core kernel (systems above 256 unknowns): n^3 / 3 each (one
-    multiply-add per entry of the trailing updates, counted as two flops:
-    sum_k 2 (n - k)^2 / 2; the three-pass TF32 split issues three times as
-    many on the tensor pipe)."""
-    return sum(n ** 3 / 3.0 for n in ns if n > 256)
+    tensor-core kernel (systems above 256 unknowns), restricted to each
+    system's row envelope (ba_debug_envelope: L is zero left of it) at the
+    kernel's 64 x 64 tile granularity: per step k with m tile rows of the
+    envelope below the diagonal, the diagonal tile (b^3 / 3), m panels (b^3
+    each: a triangular solve) and the trailing update of the m(m+1)/2 tiles
+    (b^3 each for the diagonal ones, 2 b^3 for the others: one multiply-add
+    counted as two flops), b = 64.  A full envelope gives n^3 / 3; the
+    three-pass TF32 split issues three times the update flops on the tensor
+    pipe."""
+    b3 = 64.0 ** 3
+    fl = 0.0
+    for env in envs:
+        env = np.asarray(env)
+        T = len(env)
+        for k in range(T):
+            m = int(np.count_nonzero(env[k + 1:] <= k))
+            fl += b3 / 3 + m * b3 + m * m * b3
+    return fl
 
 
-def roofline(dom, prof, steps, bytes_fn, factor_ns, workload):
+def envelopes(ba):
+    """The large systems' row envelopes of the handle's last factorisation."""
+    return ba.envelope()
+
+
+def roofline(dom, prof, steps, bytes_fn, factor_envs, workload):
     """Roofline object of the dominant kernel class: the persistent
     factorisation against the TF32 tensor peak, every other class against the
     measured HBM copy bandwidth."""
@@ -215,12 +233,15 @@ def roofline(dom, prof, steps, bytes_fn, factor_ns, workload):
     per_launch_s = t_ms / cnt / 1e3
     per_class = {k: v[0] / steps for k, v in prof.items()}
     if dom == "factor":
-        fl = factor_flops(factor_ns)
+        fl = factor_flops(factor_envs)
         peak, kind = tensor_peak_tf32()
         achieved = fl / per_launch_s / 1e12
+        dense = factor_flops([np.zeros(len(e), dtype=np.int64) for e in factor_envs])
         return {"kernel": "k_lg_factor", "bound": "tensor", "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": achieved / peak, "traffic": committed_traffic(dom, workload),
-                "algorithmic_flops_per_launch": fl, "avg_launch_us": per_launch_s * 1e6, "peak_source": kind,
+                "algorithmic_flops_per_launch": fl, "dense_flops_per_launch": dense,
+                "diagonal_steps": [len(e) for e in factor_envs],
+                "avg_launch_us": per_launch_s * 1e6, "peak_source": kind,
                 "per_class_ms_per_step": per_class}
     ab = bytes_fn(dom)
     peak, kind = measured_peaks()
@@ -961,7 +982,7 @@ def run_pgo(args):
             return 8 * tri + 64 * PGO_N * 3 + 76 * F
         return algorithmic_bytes(kind, PGO_N, 0, 0, n)
 
-    roof = roofline(dom, prof, args.steps, pgo_bytes, [n], "pgo")
+    roof = roofline(dom, prof, args.steps, pgo_bytes, envelopes(ba), "pgo")
 
     parity = None
     cpu = None
@@ -1231,7 +1252,7 @@ def run_ours(args):
     n = inf["n"]
     dom = max((k for k in prof if prof[k][1] > 0), key=lambda k: prof[k][0])
     roof = roofline(dom, prof, args.steps, lambda k: algorithmic_bytes(k, scene.N, scene.P, scene.E, n,
-                                                                 residual_pixels(args.workload)), [n],
+                                                                 residual_pixels(args.workload)), envelopes(ba),
                     args.workload)
 
     # ---- error against the oracle and the CPU baseline --------------------
@@ -1503,7 +1524,7 @@ def run_batched(args):
             return 4 * tri_all + 16 * sum(nb) + 112 * sizes[0]
         return algorithmic_bytes(k, sizes[0], sizes[1], sizes[2], 0)
 
-    roof = roofline(dom, prof, args.steps, batch_bytes, nb, "batched")
+    roof = roofline(dom, prof, args.steps, batch_bytes, envelopes(ba), "batched")
     line = {
         "metric": METRIC, "value": value, "unit": "problem GN it/s", "n_gpus": world, "steps": args.steps,
         "warmup": max(args.warmup, 3), "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -1690,7 +1711,7 @@ def run_diff16(args):
         return algorithmic_bytes(k, sizes[0], sizes[1], sizes[2], 0)
 
     dom = max((k for k in prof if prof[k][1] > 0), key=lambda k: prof[k][0])
-    roof = roofline(dom, prof, args.steps, diff_bytes, nb, "diff16")
+    roof = roofline(dom, prof, args.steps, diff_bytes, envelopes(ba), "diff16")
     line = {
         "metric": METRIC + " (forward + reverse pass)", "value": value, "unit": "problem GN it/s", "n_gpus": world,
         "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": total_ms / args.steps,

@@ -276,6 +276,18 @@ DPVBA_API ba_status_t ba_debug_export(ba_handle_t h, int what, void* dst, long l
  * the last ba_step ran the dense form (ba_dense_policy_t), else 0. */
 DPVBA_API ba_status_t ba_debug_info(ba_handle_t h, long long* info, int cap);
 
+/* The row envelope of every pose system above 256 unknowns, as the last
+ * factorisation found it (the block-sparse structure of the reduced system,
+ * Sec. 3.2): out (host) receives the number of such systems B, then per
+ * system its tile count T (64-row tiles) followed by T integers env[a] = the
+ * first tile column holding a nonzero in tile row a of S (env[a] <= a; the
+ * factor L is zero left of it, and the factorisation and the solves visit
+ * only the tiles of the envelope).  cap: integers available at out;
+ * *count (host) receives the integers needed; a smaller cap writes nothing
+ * (BA_ERR_INVALID_ARG).  BA_ERR_STATE before the bound systems were first
+ * factored.  Synchronises the handle's stream. */
+DPVBA_API ba_status_t ba_debug_envelope(ba_handle_t h, int* out, long long cap, long long* count);
+
 /* Canonical pose-pose block keys of the B part of the system, computed on the
  * GPU: sorted unique (a,b), a <= b, over (i,i), (j,j), (min,max) of each
  * non-self edge with both poses free.  keys_out: device int32 [cap,2];

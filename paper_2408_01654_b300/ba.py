@@ -307,6 +307,25 @@ class DPVBA:
             out[name] = (t.value, n.value)
         return out
 
+    def envelope(self) -> list:
+        """Row envelope of each pose system above 256 unknowns as the last
+        factorisation found it (ba_debug_envelope): one int32 numpy array per
+        system, env[a] = first 64-column tile holding a nonzero in tile row a."""
+        import numpy as np
+        n = ctypes.c_longlong()
+        st = self._lib.ba_debug_envelope(self._h, None, 0, ctypes.byref(n))
+        if st not in (capi.BA_OK, capi.BA_ERR_INVALID_ARG):
+            capi.check(self._h, st)
+        buf = (ctypes.c_int * n.value)()
+        capi.check(self._h, self._lib.ba_debug_envelope(self._h, buf, n.value, ctypes.byref(n)))
+        v = np.frombuffer(buf, dtype=np.int32).copy()
+        out, w = [], 1
+        for _ in range(int(v[0])):
+            T = int(v[w])
+            out.append(v[w + 1:w + 1 + T])
+            w += 1 + T
+        return out
+
     def block_keys(self, fixed: int, cap: int | None = None) -> torch.Tensor:
         cap = 3 * self.E + 1 if cap is None else cap
         out = torch.empty((cap, 2), dtype=torch.int32, device=self._keep[0].device)

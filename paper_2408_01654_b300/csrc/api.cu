@@ -179,6 +179,7 @@ static void bind_signature(ba_handle_t h, std::vector<long long> sig) {
 
 long long dpv_large_scratch_floats(int n_pad);
 ba_status_t dpv_large_reserve(ba_handle_t h);
+ba_status_t dpv_large_envelope(ba_handle_t h, int* out, long long cap, long long* count);
 
 namespace {
 
@@ -478,7 +479,7 @@ ba_status_t ba_destroy(ba_handle_t h) {
     release(ws->dE); release(ws->dCw);
     release(ws->tp_poses); release(ws->tp_patches); release(ws->tp_dx); release(ws->tp_dd);
     release(ws->ad_xb); release(ws->ad_w); release(ws->ad_gd); release(ws->ad_lamd); release(ws->ad_v);
-    release(ws->ad_gt); release(ws->ad_gw); release(ws->lg_sync); release(ws->lg_red); release(ws->lg_prob); release(ws->lg_rb); release(ws->fprob); release(ws->gprob);
+    release(ws->ad_gt); release(ws->ad_gw); release(ws->lg_sync); release(ws->lg_red); release(ws->lg_prob); release(ws->lg_rb); release(ws->lg_live); release(ws->fprob); release(ws->gprob);
     release(ws->fdx); release(ws->sysd); release(ws->syslist); release(ws->mii); release(ws->mjj); release(ws->mkk);
     release(ws->offs); release(ws->pcopy); release(ws->prox); release(ws->corr); release(ws->pgo);
     delete ws;
@@ -961,6 +962,12 @@ ba_status_t ba_debug_export(ba_handle_t h, int what, void* dst, long long bytes)
   }
   DPV_CUDA(h, cudaStreamSynchronize(h->stream));
   return BA_OK;
+}
+
+ba_status_t ba_debug_envelope(ba_handle_t h, int* out, long long cap, long long* count) {
+  if (!h || !count || (cap > 0 && !out)) return BA_ERR_INVALID_ARG;
+  if (!h->have_graph) return dpv_fail(h, BA_ERR_STATE, "no graph bound");
+  return dpv_large_envelope(h, out, cap, count);
 }
 
 ba_status_t ba_debug_keys(ba_handle_t h, int fixed_poses, int* keys_out, int cap, int* n_out) {

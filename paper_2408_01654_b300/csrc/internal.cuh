@@ -210,6 +210,7 @@ struct Workspace {
   DBuf<double> lg_red;            // large solver: conjugate-gradient dot products per (iteration, system)
   std::vector<unsigned char> lg_uploaded;  // host copy of what lg_prob and lg_rb hold
   DBuf<int> lg_rb;                // large solver: system of each global row block
+  DBuf<unsigned long long> lg_live;  // large solver: the factorisation tasks inside the envelope (+ count)
   DBuf<double> r64;               // [n_pad]
   DBuf<float> tmpv;               // [n_pad]
   // tape of a recorded ba_step: states before each iteration (+ the final poses) and the steps

@@ -415,14 +415,15 @@ __device__ bool tc_gemm64(TcState& ts, const unsigned char* a_hi, const unsigned
 // update in shared memory; the product sits in tensor-memory lanes 0..63,
 // read by warps 0, 1, 4, 5); then the factorisation of tile (k, k).
 __device__ bool task_diag_step(LgShared& sm, unsigned char* tcbuf, TcState& ts, float* A, float* G, float* Linv,
-                               float* D, float* invD, int k, int* ver, int* status, long long timeout) {
+                               float* D, float* invD, int k, int* ver, const int* env, int* status,
+                               long long timeout) {
   const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
   unsigned char* a_hi = tcbuf;
   unsigned char* a_lo = a_hi + 2 * TC_OP_BYTES;
   const bool epi = (wid & 3) < 2;
   const int r = 32 * (wid & 3) + lane, c0 = 32 * (wid >> 2);
   const uint32_t taddr = ts.tmem + ((uint32_t)(32 * (wid & 3)) << 16) + (uint32_t)c0;
-  if (k > 0) {
+  if (k > 0 && __ldg(env + k) < k) {  // (otherwise tile (k, k-1) lies outside the envelope: no panel, no update)
     if (tid == 0) sm.bad = wait_geq(ver + tri2(k) + k - 1, k - 1, status, timeout) ? 0 : 1;
     __syncthreads();
     if (sm.bad) return false;
@@ -485,7 +486,7 @@ __device__ bool task_diag_step(LgShared& sm, unsigned char* tcbuf, TcState& ts, 
     }
     tc_fence_before_sync();
   } else {
-    load_tile(sm.X, tile_ptr(A, 0, 0), true);
+    load_tile(sm.X, tile_ptr(A, k, k), true);
   }
   __syncthreads();
   return factor_diag(sm, A, Linv, D, invD, k);
@@ -527,44 +528,49 @@ __device__ void task_panel(LgShared& sm, float* A, float* G, const float* Linv, 
 // (hi*hi + hi*lo + lo*hi, about FP32 accuracy) accumulated in tensor memory.
 // The operands, written pre-split by the panels, arrive by bulk copies into
 // shared memory while the threads fetch the tiles being updated; one thread
-// issues the 24 MMAs.  Operand rows of a missing tile hold stale data whose
-// products are not read.
+// issues the 24 MMAs.  Operand rows of a missing tile, or of a row whose
+// tile in column k lies outside the envelope, hold stale data whose products
+// are not read.
 __device__ __forceinline__ bool quad_tile(int T, int a, int b) { return a < T && b < T && b <= a; }
 
-__device__ bool task_update_tc(unsigned char* tcbuf, TcState& ts, float* A, const float* G, int T, int i, int j,
-                               int k, long long timeout) {
+__device__ bool task_update_tc(unsigned char* tcbuf, TcState& ts, float* A, const float* G, const int* env, int T,
+                               int i, int j, int k, long long timeout) {
   const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
-  const bool i2 = i + 1 < T, j2 = j + 1 < T;
   unsigned char* a_hi = tcbuf;
   unsigned char* a_lo = a_hi + 2 * TC_OP_BYTES;
   unsigned char* b_hi = a_lo + 2 * TC_OP_BYTES;
   unsigned char* b_lo = b_hi + 2 * TC_OP_BYTES;
   if (tid == 0) {
+    // the operand rows i, i+1 (A) and j, j+1 (B) whose G_ak is nonzero
+    // (inside the envelope); the others are not copied
+    unsigned rok = 0;  // bit q: row (q < 2 ? i : j) + (q & 1)
+    uint32_t bytes = 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int a = (q < 2 ? i : j) + (q & 1);
+      if (a < T && __ldg(env + a) <= k) {
+        rok |= 1u << q;
+        bytes += 2 * TC_OP_BYTES;
+      }
+    }
     tc_fence_global();  // G was written by other CTAs through the generic proxy
     tc_fence_smem();    // this CTA's earlier generic accesses of the buffer are ordered before the copies
-    tc_mbar_expect_tx(&ts.bar_ld, (uint32_t)(4 + (i2 ? 2 : 0) + (j2 ? 2 : 0)) * TC_OP_BYTES);
-    const float* gi = g_ptr(const_cast<float*>(G), i, k);
-    const float* gj = g_ptr(const_cast<float*>(G), j, k);
-    tc_bulk_g2s(a_hi, gi, TC_OP_BYTES, &ts.bar_ld);
-    tc_bulk_g2s(a_lo, gi + TILE, TC_OP_BYTES, &ts.bar_ld);
-    if (i2) {
-      const float* g1 = g_ptr(const_cast<float*>(G), i + 1, k);
-      tc_bulk_g2s(a_hi + TC_OP_BYTES, g1, TC_OP_BYTES, &ts.bar_ld);
-      tc_bulk_g2s(a_lo + TC_OP_BYTES, g1 + TILE, TC_OP_BYTES, &ts.bar_ld);
-    }
-    tc_bulk_g2s(b_hi, gj, TC_OP_BYTES, &ts.bar_ld);
-    tc_bulk_g2s(b_lo, gj + TILE, TC_OP_BYTES, &ts.bar_ld);
-    if (j2) {
-      const float* g1 = g_ptr(const_cast<float*>(G), j + 1, k);
-      tc_bulk_g2s(b_hi + TC_OP_BYTES, g1, TC_OP_BYTES, &ts.bar_ld);
-      tc_bulk_g2s(b_lo + TC_OP_BYTES, g1 + TILE, TC_OP_BYTES, &ts.bar_ld);
-    }
+    tc_mbar_expect_tx(&ts.bar_ld, bytes);
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      if (rok & (1u << q)) {
+        const float* g = g_ptr(const_cast<float*>(G), (q < 2 ? i : j) + (q & 1), k);
+        unsigned char* d = (q < 2 ? a_hi : b_hi) + (q & 1) * TC_OP_BYTES;
+        tc_bulk_g2s(d, g, TC_OP_BYTES, &ts.bar_ld);                            // TF32 part
+        tc_bulk_g2s(d + 2 * TC_OP_BYTES, g + TILE, TC_OP_BYTES, &ts.bar_ld);  // FP32 rest
+      }
   }
   // this thread's 64 outputs: row r of the 128 (tile row i + r / 64), the 64
-  // columns of tile column j + wid / 4; read meanwhile
+  // columns of tile column j + wid / 4; read meanwhile (only a tile that
+  // receives this step: both of its operand rows inside the envelope)
   const int r = 32 * (wid & 3) + lane, cb = wid >> 2;
   const int ta = i + (r >> 6), tb = j + cb, rr = r & 63;
-  const bool mine = quad_tile(T, ta, tb);
+  const bool mine = quad_tile(T, ta, tb) && max(__ldg(env + ta), __ldg(env + tb)) <= k;
   float* ct = tile_ptr(A, mine ? ta : i, mine ? tb : j) + rr * NB;
   float4 cv[16];
 #pragma unroll
@@ -647,6 +653,9 @@ struct LgProb {
   double *xacc, *dx;                               // refinement accumulator, output
   float* dxf;                                      // FP32 copy of the output
   int* ver;                                        // tile versions [tri(T)]
+  int* env;                                        // [T] first tile column of each tile row of S that holds
+                                                   // a nonzero (the row envelope; the factor's fill stays in it)
+  int* eoff;                                       // [T+1] tiles of the envelope before each tile row
   int T, n, n_pad, rb0;                            // tiles, unknowns, padded size, first global row block
 };
 
@@ -658,6 +667,7 @@ __global__ void k_lg_scale(const LgProb* __restrict__ probs, const int* status) 
   if (r >= P.n_pad) return;
   const float d = dpv_d2f_bits(P.S[dpv_s_index(r, r, NB)]);
   P.sc[r] = (r < P.n && d > 0.f) ? rsqrtf(d) : 1.f;
+  if (r % NB == 0) P.env[r / NB] = r / NB;  // lowered by k_lg_convert
   P.rhs[r] = r < P.n ? dpv_d2f_bits(P.y[r]) * P.sc[r] : 0.f;
   P.u[r] = 0.0;  // the refinement's product accumulates into u
   P.tf[r] = 0ull;  // no row solved yet in this solve
@@ -677,15 +687,109 @@ __global__ void k_lg_convert(const LgProb* __restrict__ probs, const int* status
     const double2* src = reinterpret_cast<const double2*>(P.S + (size_t)t * TILE);
     float2* dst = reinterpret_cast<float2*>(P.A + (size_t)t * TILE);
     float4* ddf = reinterpret_cast<float4*>(P.Sdf + (size_t)t * TILE);
+    int nz = 0;
     for (int q = threadIdx.x; q < TILE / 2; q += blockDim.x) {
       const int r = (2 * q) / NB, c = (2 * q) % NB;
       const double2 v = src[q];
+      nz |= (v.x != 0.0) | (v.y != 0.0);
       const float si = P.sc[ti * NB + r];
       const float2 a = dpv_d2df_bits(v.x), b = dpv_d2df_bits(v.y);
       dst[q] = make_float2(a.x * si * P.sc[tj * NB + c], b.x * si * P.sc[tj * NB + c + 1]);
       ddf[q] = make_float4(a.x, a.y, b.x, b.y);
     }
+    // the row envelope: the first tile column holding a nonzero
+    if (__syncthreads_or(nz) && threadIdx.x == 0 && tj < ti) atomicMin(P.env + ti, tj);
   }
+}
+
+// Whether a factorisation task touches the envelope: PANEL(i,k) when tile
+// (i,k) lies in it, an update of rows i, i+1 and columns j, j+1 at step k
+// when one of its tiles (a,b) receives that step (both G_ak and G_bk nonzero:
+// env_a <= k and env_b <= k).  Outside the envelope L is zero, so a task that
+// touches nothing there would only subtract exact zeros.
+__device__ __forceinline__ bool task_live(const LgProb* __restrict__ probs, unsigned long long w64) {
+  const LgProb& P = probs[(int)(w64 >> 32)];
+  const unsigned w = (unsigned)w64;
+  const int type = (int)(w >> 30), k = (int)((w >> 20) & 1023u), i = (int)((w >> 10) & 1023u),
+            j = (int)(w & 1023u);
+  if (type == TASK_PANEL) return __ldg(P.env + i) <= k;
+  for (int a = i; a < i + 2 && a < P.T; ++a) {
+    if (__ldg(P.env + a) > k) continue;
+    for (int b = j; b < j + 2 && b <= a; ++b)
+      if (__ldg(P.env + b) <= k) return true;
+  }
+  return false;
+}
+
+constexpr int ENV_THREADS = 1024;
+
+// The envelope's bookkeeping (one CTA, after k_lg_convert has found each tile
+// row's first nonzero tile): per system the envelope's tile offsets (the
+// products with S visit only its tiles) and the initial tile versions (a
+// tile (a,b) of the envelope receives the updates of steps
+// max(env_a, env_b) .. b-1 and starts at the first of them), then the tasks
+// of the dense list that touch the envelope, compacted in list order, their
+// count in live[ntasks].
+__global__ void __launch_bounds__(ENV_THREADS) k_lg_envelope(const LgProb* __restrict__ probs, int nsys,
+                                                             const int* __restrict__ rb_sys, int R,
+                                                             const unsigned long long* __restrict__ tasks, int ntasks,
+                                                             unsigned long long* __restrict__ live, const int* status) {
+  __shared__ int wsum[ENV_THREADS / 32];
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  if (dpv_status(status)) {
+    if (tid == 0) live[ntasks] = 0ull;
+    return;
+  }
+  for (int p = wid; p < nsys; p += ENV_THREADS / 32) {  // offsets: one warp per system
+    const LgProb& P = probs[p];
+    int base = 0;
+    for (int a0 = 0; a0 < P.T; a0 += 32) {
+      const int a = a0 + lane;
+      int v = a < P.T ? a - P.env[a] + 1 : 0;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += u;
+      }
+      if (a < P.T) P.eoff[a + 1] = base + v;
+      base += __shfl_sync(0xffffffffu, v, 31);
+    }
+    if (lane == 0) P.eoff[0] = 0;
+  }
+  for (int r = wid; r < R; r += ENV_THREADS / 32) {  // versions: one warp per tile row
+    const LgProb& P = probs[rb_sys[r]];
+    const int a = r - P.rb0, ea = P.env[a];
+    for (int b = ea + lane; b <= a; b += 32) P.ver[tri2(a) + b] = max(ea, P.env[b]);
+  }
+  // compaction: each thread a contiguous share of the list
+  const int per = (ntasks + ENV_THREADS - 1) / ENV_THREADS;
+  const int t0 = min(ntasks, tid * per), t1 = min(ntasks, t0 + per);
+  int cnt = 0;
+  for (int t = t0; t < t1; ++t) cnt += task_live(probs, tasks[t]) ? 1 : 0;
+  int v = cnt;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int u = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += u;
+  }
+  if (lane == 31) wsum[wid] = v;
+  __syncthreads();
+  if (wid == 0) {
+    int x = wsum[lane];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int u = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += u;
+    }
+    wsum[lane] = x;
+  }
+  __syncthreads();
+  int off = v - cnt + (wid ? wsum[wid - 1] : 0);
+  for (int t = t0; t < t1; ++t) {
+    const unsigned long long w = tasks[t];
+    if (task_live(probs, w)) live[off++] = w;
+  }
+  if (tid == ENV_THREADS - 1) live[ntasks] = (unsigned long long)off;
 }
 
 // The factorisation task graphs of all large systems.  CTA p < nsys runs the
@@ -697,9 +801,10 @@ __global__ void k_lg_convert(const LgProb* __restrict__ probs, const int* status
 // Every CTA that stays holds TC_COLS tensor-memory columns, released on every
 // way out once its MMAs have completed.
 __global__ void __launch_bounds__(LG_THREADS, 1) k_lg_factor(const LgProb* __restrict__ probs, int nsys,
-                                                          const unsigned long long* __restrict__ tasks, int ntasks,
+                                                          const unsigned long long* __restrict__ tasks, int cap,
                                                           int* ctr, int* dsm, int isolate, int* status,
                                                           long long timeout) {
+  const int ntasks = (int)tasks[cap];  // the live tasks (k_lg_envelope)
   extern __shared__ __align__(1024) float lg_smem[];
   LgShared& sm = *reinterpret_cast<LgShared*>(lg_smem);          // the CUDA-core tasks
   unsigned char* tcbuf = reinterpret_cast<unsigned char*>(lg_smem) + TC_OFF;  // the tensor-core operands
@@ -733,7 +838,7 @@ __global__ void __launch_bounds__(LG_THREADS, 1) k_lg_factor(const LgProb* __res
     const LgProb& P = probs[blockIdx.x];
     for (int k = 0; k < P.T; ++k) {
       if (dpv_status(status)) goto done;
-      if (!task_diag_step(sm, tcbuf, ts, P.A, P.G, P.Linv, P.D, P.invD, k, P.ver, status, timeout)) {
+      if (!task_diag_step(sm, tcbuf, ts, P.A, P.G, P.Linv, P.D, P.invD, k, P.ver, P.env, status, timeout)) {
         if (threadIdx.x == 0 && !dpv_status(status)) dpv_set_status(status, DST_NOT_SPD);
         goto done;
       }
@@ -775,12 +880,12 @@ __global__ void __launch_bounds__(LG_THREADS, 1) k_lg_factor(const LgProb* __res
       if (type == TASK_PANEL) {
         if (lane == 0) { vp = ver + tri2(k) + k; want = k + 1; }
         if (lane == 1) { vp = ver + tri2(i) + k; want = k; }
-      } else if (lane < 4) {  // lanes 0, 1: rows i, i+1; lanes 2, 3: rows j, j+1
+      } else if (lane < 4) {  // lanes 0, 1: rows i, i+1; lanes 2, 3: rows j, j+1 (inside the envelope)
         const int a = (lane < 2 ? i : j) + (lane & 1);
-        if (a < T) { vp = ver + tri2(a) + k; want = k + 1; }
-      } else if (lane < 8) {  // the target tiles (i + (lane >> 1 & 1), j + (lane & 1))
+        if (a < T && __ldg(P.env + a) <= k) { vp = ver + tri2(a) + k; want = k + 1; }
+      } else if (lane < 8) {  // the target tiles (i + (lane >> 1 & 1), j + (lane & 1)) that receive step k
         const int a = i + ((lane >> 1) & 1), b = j + (lane & 1);
-        if (quad_tile(T, a, b)) { vp = ver + tri2(a) + b; want = k; }
+        if (quad_tile(T, a, b) && max(__ldg(P.env + a), __ldg(P.env + b)) <= k) { vp = ver + tri2(a) + b; want = k; }
       }
       const bool ok = vp ? wait_geq(vp, want, status, timeout) : true;
       const bool all_ok = __all_sync(0xffffffffu, ok);
@@ -794,7 +899,7 @@ __global__ void __launch_bounds__(LG_THREADS, 1) k_lg_factor(const LgProb* __res
     if (bad) break;
     if (type == TASK_PANEL) {
       task_panel(sm, P.A, P.G, P.Linv, P.D, P.invD, i, k);
-    } else if (!task_update_tc(tcbuf, ts, P.A, P.G, T, i, j, k, timeout)) {
+    } else if (!task_update_tc(tcbuf, ts, P.A, P.G, P.env, T, i, j, k, timeout)) {
       if (threadIdx.x == 0) dpv_set_status(status, DST_TIMEOUT);
       break;
     }
@@ -808,7 +913,7 @@ __global__ void __launch_bounds__(LG_THREADS, 1) k_lg_factor(const LgProb* __res
         }
       } else {
         const int a = i + (q >> 1), b = j + (q & 1);
-        if (quad_tile(T, a, b)) {
+        if (quad_tile(T, a, b) && max(__ldg(P.env + a), __ldg(P.env + b)) <= k) {
           __threadfence();
           st_release(ver + tri2(a) + b, k + 1);
         }
@@ -987,6 +1092,22 @@ __device__ void tile_symv(const SymvRegs& g, const DFp* vr, const DFp* vc, bool 
 // system takes no further part, so its later maxima stay 0 and it stays
 // finished.  The maxima of a completed iteration are final (grid barrier), so
 // every CTA reaches the same decision.
+// The t-th tile of the envelope in row-major order: its tile row ti and
+// column tj, and its index in the tiled lower triangle.
+__device__ __forceinline__ int env_tile(const LgProb& P, int t, int& ti, int& tj) {
+  int lo = 0, hi = P.T - 1;  // the last row whose envelope starts at or before t
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (__ldg(P.eoff + mid) <= t)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  ti = lo;
+  tj = __ldg(P.env + lo) + (t - __ldg(P.eoff + lo));
+  return tri2(ti) + tj;
+}
+
 __device__ __forceinline__ bool sys_finished(const int* conv, int nsys, int p, int s, float tol) {
   if (s < 1) return false;
   const float cm = __int_as_float(__ldcg(conv + 2 * (s * nsys + p)));
@@ -1033,9 +1154,11 @@ __global__ void __launch_bounds__(LG_THREADS, 2) k_lg_solve(const LgProb* __rest
       const LgProb& P = probs[rb_sys[r]];
       const int i = r - P.rb0;
       if (tid < NB) acc[tid] = __ldcg(P.rhs + i * NB + tid);
-      // the tiles do not depend on the solved rows: each is loaded while waiting for the previous row
-      TileRegs m = load_block(i > 0 ? P.A + (size_t)tri2(i) * TILE : P.Linv + (size_t)i * TILE);
-      for (int j = 0; j < i; ++j) {
+      // the tiles do not depend on the solved rows: each is loaded while
+      // waiting for the previous row; the row's tiles start at its envelope
+      const int j0 = __ldg(P.env + i);
+      TileRegs m = load_block(i > j0 ? P.A + (size_t)(tri2(i) + j0) * TILE : P.Linv + (size_t)i * TILE);
+      for (int j = j0; j < i; ++j) {
         const TileRegs mn =
             load_block(j + 1 < i ? P.A + (size_t)(tri2(i) + j + 1) * TILE : P.Linv + (size_t)i * TILE);
         if (tid < NB) {
@@ -1071,10 +1194,14 @@ __global__ void __launch_bounds__(LG_THREADS, 2) k_lg_solve(const LgProb* __rest
         if (!wait_tagged(P.tf + i * NB + tid, sweep + 1, u, status, timeout)) ok = 0;
         acc[tid] = u * __ldcg(P.invD + i * NB + tid);
       }
-      TileRegs m = load_block(i + 1 < T ? P.A + (size_t)(tri2(T - 1) + i) * TILE : P.Linv + (size_t)i * TILE);
-      for (int j = T - 1; j > i; --j) {
-        const TileRegs mn =
-            load_block(j - 1 > i ? P.A + (size_t)(tri2(j - 1) + i) * TILE : P.Linv + (size_t)i * TILE);
+      // the rows below whose envelope reaches column i (L is zero elsewhere)
+      int j = T - 1;
+      while (j > i && __ldg(P.env + j) > i) --j;
+      TileRegs m = load_block(j > i ? P.A + (size_t)(tri2(j) + i) * TILE : P.Linv + (size_t)i * TILE);
+      while (j > i) {
+        int jn = j - 1;
+        while (jn > i && __ldg(P.env + jn) > i) --jn;
+        const TileRegs mn = load_block(jn > i ? P.A + (size_t)(tri2(jn) + i) * TILE : P.Linv + (size_t)i * TILE);
         if (tid < NB) {
           float v = 0.f;
           if (!wait_tagged(P.tb + j * NB + tid, sweep + 1, v, status, timeout)) ok = 0;
@@ -1085,6 +1212,7 @@ __global__ void __launch_bounds__(LG_THREADS, 2) k_lg_solve(const LgProb* __rest
         tile_gemv(m, vj, prod, true, part);
         if (tid < NB) acc[tid] -= prod[tid];
         m = mn;
+        j = jn;
       }
       __syncthreads();
       if (!ok) return;
@@ -1134,14 +1262,16 @@ __global__ void __launch_bounds__(LG_THREADS, 2) k_lg_solve(const LgProb* __rest
         const LgProb& P = probs[sy];
         const double beta =
             sweep > 1 ? __ldcg(red + 2 * (sweep * nsys + sy)) / __ldcg(red + 2 * ((sweep - 1) * nsys + sy)) : 0.0;
+        // the tiles of the envelope only (S is zero outside it)
+        const int ntile = __ldg(P.eoff + P.T);
         SymvRegs cur, nxt;
-        if ((int)blockIdx.x < tri2(P.T)) load_symv_tile(P.Sdf + (size_t)blockIdx.x * TILE, cur);
-        for (int t = blockIdx.x; t < tri2(P.T); t += gridDim.x) {
-          if (t + (int)gridDim.x < tri2(P.T)) load_symv_tile(P.Sdf + (size_t)(t + gridDim.x) * TILE, nxt);
-          int ti = (int)((sqrtf(8.0f * t + 1.0f) - 1.0f) * 0.5f);
-          while (tri2(ti + 1) <= t) ++ti;
-          while (tri2(ti) > t) --ti;
-          const int tj = t - tri2(ti);
+        int ti, tj;
+        if ((int)blockIdx.x < ntile) load_symv_tile(P.Sdf + (size_t)env_tile(P, blockIdx.x, ti, tj) * TILE, cur);
+        for (int t = blockIdx.x; t < ntile; t += gridDim.x) {
+          int ti2, tj2;
+          if (t + (int)gridDim.x < ntile)
+            load_symv_tile(P.Sdf + (size_t)env_tile(P, t + gridDim.x, ti2, tj2) * TILE, nxt);
+          env_tile(P, t, ti, tj);
           if (tid < NB) {
             for (int side = 0; side < 2; ++side) {
               const int blk = side ? tj : ti;
@@ -1376,7 +1506,7 @@ ba_status_t lg_plan(ba_handle_t h, LgPlan& L) {
     P.n_pad = sd.n_pad;
     P.rb0 = (int)L.rb_sys.size();
     for (int i = 0; i < T; ++i) L.rb_sys.push_back(p);
-    L.soff_sync += tri2(T);
+    L.soff_sync += tri2(T) + 2 * T + 1;  // versions, envelope, envelope offsets
   }
   {
     // the chain orders of the triangular solves: by position in the chain,
@@ -1420,12 +1550,42 @@ ba_status_t lg_plan(ba_handle_t h, LgPlan& L) {
   if ((s = dpv_grow(h, ws->lg_sync, L.nsync, "large solver sync")) ||
       (s = dpv_grow(h, ws->lg_red, 2LL * MAX_SWEEPS * nsys, "large solver reductions")) ||
       (s = dpv_grow(h, ws->lg_prob, (long long)nsys * sizeof(LgProb) / sizeof(long long) + 1, "large systems")) ||
-      (s = dpv_grow(h, ws->lg_rb, (long long)L.rb_sys.size(), "row blocks")))
+      (s = dpv_grow(h, ws->lg_rb, (long long)L.rb_sys.size(), "row blocks")) ||
+      (s = dpv_grow(h, ws->lg_live, (long long)L.ntasks + 1, "live factorisation tasks")))
     return s;
   return BA_OK;
 }
 
 }  // namespace
+
+// The row envelopes of the large systems as the last factorisation found
+// them: out[0] = systems, then per system its tile count T and env[0..T-1].
+ba_status_t dpv_large_envelope(ba_handle_t h, int* out, long long cap, long long* count) {
+  const int nsys = (int)h->large_sys.size();
+  std::vector<int> Ts(nsys);
+  long long need = 1, words = 0;
+  for (int p = 0; p < nsys; ++p) {
+    Ts[p] = h->sys[h->large_sys[p]].n_pad / NB;
+    need += 1 + Ts[p];
+    words += tri2(Ts[p]) + 2 * Ts[p] + 1;
+  }
+  *count = need;
+  if (cap < need) return dpv_fail(h, BA_ERR_INVALID_ARG, "envelope buffer too small");
+  out[0] = nsys;
+  if (nsys == 0) return BA_OK;
+  if (!h->ws->lg_sync.p || h->ws->lg_sync.cap < words)
+    return dpv_fail(h, BA_ERR_STATE, "no factorisation of the bound systems yet");
+  DPV_CUDA(h, cudaStreamSynchronize(h->stream));
+  long long o = 0, w = 1;
+  for (int p = 0; p < nsys; ++p) {
+    out[w] = Ts[p];
+    DPV_CUDA(h, cudaMemcpy(out + w + 1, h->ws->lg_sync.p + o + tri2(Ts[p]), sizeof(int) * Ts[p],
+                           cudaMemcpyDeviceToHost));
+    w += 1 + Ts[p];
+    o += tri2(Ts[p]) + 2 * Ts[p] + 1;
+  }
+  return BA_OK;
+}
 
 // Size the large solver's buffers and build its task list for the current
 // layout (ahead of the steps, so that a step allocates nothing).
@@ -1455,7 +1615,9 @@ ba_status_t dpv_solve_large(ba_handle_t h, int refine) {
   int* sync = ws->lg_sync.p;
   for (int p = 0, o = 0; p < nsys; ++p) {
     pr[p].ver = sync + o;
-    o += tri2(Ts[p]);
+    pr[p].env = pr[p].ver + tri2(Ts[p]);
+    pr[p].eoff = pr[p].env + Ts[p];
+    o += tri2(Ts[p]) + 2 * Ts[p] + 1;
   }
   int* ctr = sync + soff_sync;
   int* bar = ctr + 1;   // two ints
@@ -1496,6 +1658,10 @@ ba_status_t dpv_solve_large(ba_handle_t h, int refine) {
   ++h->launches;
   k_lg_convert<<<dim3(std::min(maxtiles, 8 * h->num_sms), nsys), 256, 0, st>>>(dprobs, status);
   ++h->launches;
+  // the factorisation's live tasks and initial versions, the envelope offsets
+  unsigned long long* live = ws->lg_live.p;
+  k_lg_envelope<<<1, ENV_THREADS, 0, st>>>(dprobs, nsys, ws->lg_rb.p, R, tasks, ntasks, live, status);
+  ++h->launches;
   long long timeout = h->opt.timeout_cycles;
   {
     // at most two CTAs per SM; the critical CTAs get their SMs to themselves
@@ -1512,7 +1678,7 @@ ba_status_t dpv_solve_large(ba_handle_t h, int refine) {
     if (grid <= nsys) return dpv_fail(h, BA_ERR_UNSUPPORTED, "more large systems than the solver's resident CTAs");
     int isolate = 2 * nsys <= h->num_sms ? 1 : 0;
     int nsys_ = nsys;
-    void* args[] = {(void*)&dprobs, (void*)&nsys_, (void*)&tasks,  (void*)&ntasks,
+    void* args[] = {(void*)&dprobs, (void*)&nsys_, (void*)&live,   (void*)&ntasks,
                     (void*)&ctr,    (void*)&dsm,   (void*)&isolate, (void*)&status, (void*)&timeout};
     // timed as its own class (inside the solve class's region)
     dpv_prof_end(h);
