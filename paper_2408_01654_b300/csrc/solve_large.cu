@@ -43,7 +43,10 @@ namespace {
 
 constexpr int NB = 64;  // tile edge, equal to the assembly's tile for n > DPV_SMALL_N
 constexpr int TILE = NB * NB;
-constexpr int LDS = NB + 1;  // padded shared-memory row
+constexpr int LDX = NB + 1;  // padded row of the tile being factored (column reads by row threads: conflict free)
+constexpr int LDS = NB + 4;  // padded row of the product operands: 16-byte rows, and 128-bit accesses of a
+                             // quarter warp to 8 consecutive rows hit distinct banks (68 = 4 mod 32)
+constexpr int LDC = NB + 1;  // padded row of the solve's staging buffers
 constexpr int LG_THREADS = 256;
 constexpr int TASK_PANEL = 1, TASK_UPDATE = 2;  // worker task types (the diagonal steps are not listed)
 constexpr int LG_MAX_T = 1023;  // tiles per dimension (10-bit task fields)
@@ -134,10 +137,44 @@ __device__ bool wait_tagged(const unsigned long long* p, unsigned tag, float& v,
   }
 }
 
+// Two consecutive words p[0], p[1] (see wait_tagged).
+__device__ bool wait_tagged2(const unsigned long long* p, unsigned tag, float& v0, float& v1, int* status,
+                             long long timeout) {
+  const long long t0 = clock64();
+  bool h0 = false, h1 = false;
+  for (unsigned it = 0;; ++it) {
+    unsigned long long w;
+    if (!h0) {
+      asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(w) : "l"(p) : "memory");
+      if ((unsigned)(w >> 32) == tag) {
+        v0 = __uint_as_float((unsigned)w);
+        h0 = true;
+      }
+    }
+    if (!h1) {
+      asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(w) : "l"(p + 1) : "memory");
+      if ((unsigned)(w >> 32) == tag) {
+        v1 = __uint_as_float((unsigned)w);
+        h1 = true;
+      }
+    }
+    if (h0 && h1) return true;
+    if ((it & 63u) == 63u) {
+      if (dpv_status(status)) return false;
+      if (clock64() - t0 > timeout) {
+        dpv_set_status(status, DST_TIMEOUT);
+        return false;
+      }
+    }
+    if (it > 32) __nanosleep(32);
+  }
+}
+
 __device__ __forceinline__ float* tile_ptr(float* A, int i, int j) { return A + (size_t)(tri2(i) + j) * TILE; }
 
 // tile (64 x 64, row-major in global memory, read through L2) -> padded
 // shared; all four loads of a thread are issued before the stores
+template <int LD>
 __device__ __forceinline__ void load_tile(float* dst, const float* src, bool lower_only) {
   constexpr int PER = TILE / 4 / LG_THREADS;
   float4 v[PER];
@@ -147,15 +184,20 @@ __device__ __forceinline__ void load_tile(float* dst, const float* src, bool low
   for (int u = 0; u < PER; ++u) {
     const int q = threadIdx.x + u * LG_THREADS;
     const int r = (4 * q) / NB, c = (4 * q) % NB;
-    float* d = dst + r * LDS + c;
-    d[0] = (!lower_only || c <= r) ? v[u].x : 0.f;
-    d[1] = (!lower_only || c + 1 <= r) ? v[u].y : 0.f;
-    d[2] = (!lower_only || c + 2 <= r) ? v[u].z : 0.f;
-    d[3] = (!lower_only || c + 3 <= r) ? v[u].w : 0.f;
+    float* d = dst + r * LD + c;
+    if (LD % 4 == 0 && !lower_only) {
+      *reinterpret_cast<float4*>(d) = v[u];
+    } else {
+      d[0] = (!lower_only || c <= r) ? v[u].x : 0.f;
+      d[1] = (!lower_only || c + 1 <= r) ? v[u].y : 0.f;
+      d[2] = (!lower_only || c + 2 <= r) ? v[u].z : 0.f;
+      d[3] = (!lower_only || c + 3 <= r) ? v[u].w : 0.f;
+    }
   }
 }
 
 // two tiles, eight loads in flight per thread
+template <int LD>
 __device__ __forceinline__ void load_tiles2(float* d0, const float* s0, float* d1, const float* s1) {
   constexpr int PER = TILE / 4 / LG_THREADS;
   float4 v[2 * PER];
@@ -168,29 +210,69 @@ __device__ __forceinline__ void load_tiles2(float* d0, const float* s0, float* d
   for (int u = 0; u < 2 * PER; ++u) {
     const int q = threadIdx.x + (u % PER) * LG_THREADS;
     const int r = (4 * q) / NB, c = (4 * q) % NB;
-    float* d = (u < PER ? d0 : d1) + r * LDS + c;
-    d[0] = v[u].x;
-    d[1] = v[u].y;
-    d[2] = v[u].z;
-    d[3] = v[u].w;
+    float* d = (u < PER ? d0 : d1) + r * LD + c;
+    if (LD % 4 == 0) {
+      *reinterpret_cast<float4*>(d) = v[u];
+    } else {
+      d[0] = v[u].x;
+      d[1] = v[u].y;
+      d[2] = v[u].z;
+      d[3] = v[u].w;
+    }
   }
 }
 
-// acc[a][b] += sum_c X[r][c] w[c] Y[s][c] for r = ty + 16a, s = tx + 16b (w may be null)
-__device__ __forceinline__ void gemm_nt(const float* X, const float* Y, const float* w, float acc[4][4]) {
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-#pragma unroll 4
-  for (int c = 0; c < NB; ++c) {
-    const float wc = w ? w[c] : 1.f;
-    float xa[4], yb[4];
+// acc[a][e] += sum_c X[8w + a][c] Y[l + 32e][c] w[c] for warp w, lane l (X, Y
+// with LDS-padded rows, w 16-byte aligned or null): the rows of X are read
+// as warp-wide broadcasts, those of Y by quarter warps from distinct banks,
+// four values of c per 128-bit load, summed in ascending c.
+// LOWER_Y: Y is lower triangular (Y[s][c] = 0 for c > s), so the rows s < 32
+// take no products for c >= 32 (exact zeros: the sums are unchanged).
+template <bool LOWER_Y>
+__device__ __forceinline__ void gemm_rows8(const float* X, const float* Y, const float* w, float acc[8][2]) {
+  const int lane = threadIdx.x & 31, wr = threadIdx.x >> 5;
+  const float* xr = X + 8 * wr * LDS;
+  const float* y0 = Y + lane * LDS;
+  const float* y1 = Y + (lane + 32) * LDS;
+#pragma unroll 2
+  for (int c = 0; c < (LOWER_Y ? NB / 2 : NB); c += 4) {
+    float4 b0 = *reinterpret_cast<const float4*>(y0 + c), b1 = *reinterpret_cast<const float4*>(y1 + c);
+    if (w) {
+      const float4 wc = *reinterpret_cast<const float4*>(w + c);
+      b0.x *= wc.x;
+      b0.y *= wc.y;
+      b0.z *= wc.z;
+      b0.w *= wc.w;
+      b1.x *= wc.x;
+      b1.y *= wc.y;
+      b1.z *= wc.z;
+      b1.w *= wc.w;
+    }
 #pragma unroll
-    for (int a = 0; a < 4; ++a) xa[a] = X[(ty + 16 * a) * LDS + c] * wc;
+    for (int a = 0; a < 8; ++a) {
+      const float4 x = *reinterpret_cast<const float4*>(xr + a * LDS + c);
+      float t0 = fmaf(x.x, b0.x, acc[a][0]), t1 = fmaf(x.x, b1.x, acc[a][1]);
+      t0 = fmaf(x.y, b0.y, t0);
+      t1 = fmaf(x.y, b1.y, t1);
+      t0 = fmaf(x.z, b0.z, t0);
+      t1 = fmaf(x.z, b1.z, t1);
+      acc[a][0] = fmaf(x.w, b0.w, t0);
+      acc[a][1] = fmaf(x.w, b1.w, t1);
+    }
+  }
+  if (LOWER_Y) {  // (w is null here)
+#pragma unroll 2
+    for (int c = NB / 2; c < NB; c += 4) {
+      const float4 b1 = *reinterpret_cast<const float4*>(y1 + c);
 #pragma unroll
-    for (int b = 0; b < 4; ++b) yb[b] = Y[(tx + 16 * b) * LDS + c];
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-      for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(xa[a], yb[b], acc[a][b]);
+      for (int a = 0; a < 8; ++a) {
+        const float4 x = *reinterpret_cast<const float4*>(xr + a * LDS + c);
+        float t1 = fmaf(x.x, b1.x, acc[a][1]);
+        t1 = fmaf(x.y, b1.y, t1);
+        t1 = fmaf(x.z, b1.z, t1);
+        acc[a][1] = fmaf(x.w, b1.w, t1);
+      }
+    }
   }
 }
 
@@ -223,71 +305,71 @@ __device__ __forceinline__ float* g_ptr(float* G, int i, int k) { return G + (si
 // the tasks
 // ---------------------------------------------------------------------------
 struct LgShared {
-  float X[NB * LDS];
-  float Y[NB * LDS];
-  float Z[NB * LDS];
+  float X[NB * LDX];                  // the diagonal tile being factored
+  __align__(16) float Y[NB * LDS];    // product operands
+  __align__(16) float Z[NB * LDS];
   __align__(16) float ucol[LG_THREADS / 32][32];  // column broadcast of the diagonal factorisation
   float invd[NB];
   float dd[NB];
-  float dprev[NB];  // the previous diagonal step's D and D^-1 (critical-path CTA)
+  __align__(16) float dprev[NB];  // the previous diagonal step's D and D^-1 (critical-path CTA)
   float iprev[NB];
   float sq[NB];     // D_k^1/2 of the panel being written
   int task;
   int bad;
+  int pf;  // critical CTA: bit 0 / 1 = tile (k, k-1) / (k, k) of the next step already fetched
 };
 
-// LDL^T of the 64 x 64 diagonal tile in sm.X (lower part) by warps 0 and 1
-// (threads 0..63, lane = row r, the row in registers): column c is broadcast
-// through shared memory (double-buffered by the parity of c, so one 64-thread
-// named barrier per column suffices: a buffer is rewritten two columns later,
-// after every thread passed the barrier in between) and each row updates its
-// entries right of c.  Writes the unit factor (strict lower) back to sm.X, D
-// and D^-1 to sm.dd / sm.invd.  Returns false on a non-positive pivot.
+// LDL^T of the 64 x 64 diagonal tile in sm.X (lower part) by warps 0-3: row
+// r = tid % 64 in registers, split by column parity between two threads
+// (tid / 64 = the parity, uniform per warp), so that each column's update of
+// the entries right of it is shared evenly.  Column c is broadcast through
+// shared memory by the threads owning it (double-buffered by the parity of
+// c, so one 128-thread named barrier per column suffices: a buffer is
+// rewritten two columns later, after every thread passed the barrier in
+// between); every thread takes its row's multiplier from the broadcast.
+// Writes the unit factor (strict lower) back to sm.X, D and D^-1 to sm.dd /
+// sm.invd.  Returns false on a non-positive pivot.
 __device__ __noinline__ bool factor64(LgShared& sm) {
-  const int r = threadIdx.x;  // < 64
+  const int r = threadIdx.x & (NB - 1), h = threadIdx.x >> 6;  // threadIdx.x < 128
   float* Xs = sm.X;
   float(*buf)[NB] = reinterpret_cast<float(*)[NB]>(&sm.ucol[0][0]);
-  float a[NB];
+  float a[NB / 2];  // a[j]: column 2j + h
 #pragma unroll
-  for (int c = 0; c < NB; ++c) a[c] = c <= r ? Xs[r * LDS + c] : 0.f;
+  for (int j = 0; j < NB / 2; ++j) a[j] = 2 * j + h <= r ? Xs[r * LDX + 2 * j + h] : 0.f;
   bool ok = true;
 #pragma unroll
   for (int c = 0; c < NB; ++c) {
     float* u = buf[c & 1];
-    u[r] = a[c];
-    asm volatile("bar.sync 1, 64;" ::: "memory");
+    if (h == (c & 1)) u[r] = a[c >> 1];
+    asm volatile("bar.sync 1, 128;" ::: "memory");
     const float d = u[c];
     ok = ok && (d > 0.f);
     float inv;  // approximate reciprocal: the refinement absorbs its last-bit error
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(inv) : "f"(d));
-    const float l = a[c] * inv;
+    const float l = u[r] * inv;
 #pragma unroll
-    for (int q = (c + 1) / 4; q < NB / 4; ++q) {
-      const float4 v = reinterpret_cast<const float4*>(u)[q];
-      if (4 * q > c) a[4 * q] = fmaf(-l, v.x, a[4 * q]);
-      if (4 * q + 1 > c) a[4 * q + 1] = fmaf(-l, v.y, a[4 * q + 1]);
-      if (4 * q + 2 > c) a[4 * q + 2] = fmaf(-l, v.z, a[4 * q + 2]);
-      if (4 * q + 3 > c) a[4 * q + 3] = fmaf(-l, v.w, a[4 * q + 3]);
-    }
-    if (r == c) {
+    for (int j = c >> 1; j < NB / 2; ++j)  // this thread's columns 2j + h right of c
+      if (2 * j > c || (2 * j == c && h == 1)) a[j] = fmaf(-l, u[2 * j + h], a[j]);
+    if (h == (c & 1) && r > c) a[c >> 1] = l;
+    if (r == c && h == 0) {
       sm.invd[c] = inv;
       sm.dd[c] = d;
     }
-    if (r > c) a[c] = l;
   }
 #pragma unroll
-  for (int c = 0; c < NB; ++c)
-    if (c < r) Xs[r * LDS + c] = a[c];
+  for (int j = 0; j < NB / 2; ++j)
+    if (2 * j + h < r) Xs[r * LDX + 2 * j + h] = a[j];
   return ok;
 }
 
 // Inverse of the unit lower factor in sm.X by 32-row blocks,
 //   [L00 0; L10 L11]^-1 = [L00^-1 0; -L11^-1 (L10 L00^-1) L11^-1],
-// into sm.Y (padded) and li (global, row-major): warps 0 and 1 invert the
-// diagonal blocks (lane = column, forward substitution), then all threads
+// into sm.Y (padded) and li (global, row-major), by warps 0-3 (a 128-thread
+// named barrier, so that warps 4-7 stay free): warps 0 and 1 invert the
+// diagonal blocks (lane = column, forward substitution), then the four warps
 // form the off-diagonal block through sm.Z (scratch).
 __device__ void inverse64(LgShared& sm, float* li) {
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;  // tid < 128
   if (wid < 2) {
     const int b = 32 * wid;
     float x[32];
@@ -296,71 +378,113 @@ __device__ void inverse64(LgShared& sm, float* li) {
 #pragma unroll
     for (int k = 0; k < 31; ++k)
 #pragma unroll
-      for (int i = k + 1; i < 32; ++i) x[i] = fmaf(-sm.X[(b + i) * LDS + b + k], x[k], x[i]);
+      for (int i = k + 1; i < 32; ++i) x[i] = fmaf(-sm.X[(b + i) * LDX + b + k], x[k], x[i]);
 #pragma unroll
     for (int i = 0; i < 32; ++i) sm.Y[(b + i) * LDS + b + lane] = x[i];
   } else {
-    for (int t = tid - 64; t < 32 * 32; t += LG_THREADS - 64) sm.Y[(t >> 5) * LDS + 32 + (t & 31)] = 0.f;
+    for (int t = tid - 64; t < 32 * 32; t += 64) sm.Y[(t >> 5) * LDS + 32 + (t & 31)] = 0.f;
   }
-  __syncthreads();
-  // thread: row i, columns j0, j0 + 8, j0 + 16, j0 + 24 of the 32 x 32 products
-  const int i = tid >> 3, j0 = tid & 7;
+  asm volatile("bar.sync 3, 128;" ::: "memory");
+  // thread: row i, columns j0 + 4e (e < 8) of the 32 x 32 products
+  const int i = tid >> 2, j0 = tid & 3;
   {
     // W = L10 L00^-1 (L00^-1 lower: only k >= j contributes; its upper part is 0)
-    float w[4] = {0.f, 0.f, 0.f, 0.f};
+    float w[8] = {};
 #pragma unroll 8
     for (int k = 0; k < 32; ++k) {
-      const float x = sm.X[(32 + i) * LDS + k];
+      const float x = sm.X[(32 + i) * LDX + k];
 #pragma unroll
-      for (int e = 0; e < 4; ++e) w[e] = fmaf(x, sm.Y[k * LDS + j0 + 8 * e], w[e]);
+      for (int e = 0; e < 8; ++e) w[e] = fmaf(x, sm.Y[k * LDS + j0 + 4 * e], w[e]);
     }
 #pragma unroll
-    for (int e = 0; e < 4; ++e) sm.Z[i * LDS + j0 + 8 * e] = w[e];
+    for (int e = 0; e < 8; ++e) sm.Z[i * LDS + j0 + 4 * e] = w[e];
   }
-  __syncthreads();
+  asm volatile("bar.sync 3, 128;" ::: "memory");
   {
     // M10 = -L11^-1 W (L11^-1 lower: k <= i)
-    float v[4] = {0.f, 0.f, 0.f, 0.f};
+    float v[8] = {};
 #pragma unroll 8
     for (int k = 0; k < 32; ++k) {
       const float y = k <= i ? sm.Y[(32 + i) * LDS + 32 + k] : 0.f;
 #pragma unroll
-      for (int e = 0; e < 4; ++e) v[e] = fmaf(y, sm.Z[k * LDS + j0 + 8 * e], v[e]);
+      for (int e = 0; e < 8; ++e) v[e] = fmaf(y, sm.Z[k * LDS + j0 + 4 * e], v[e]);
     }
 #pragma unroll
-    for (int e = 0; e < 4; ++e) sm.Y[(32 + i) * LDS + j0 + 8 * e] = -v[e];
+    for (int e = 0; e < 8; ++e) sm.Y[(32 + i) * LDS + j0 + 4 * e] = -v[e];
   }
-  __syncthreads();
-  for (int t = tid; t < TILE; t += LG_THREADS) li[t] = sm.Y[(t >> 6) * LDS + (t & 63)];
+  asm volatile("bar.sync 3, 128;" ::: "memory");
+  for (int t = tid; t < TILE; t += 2 * NB) li[t] = sm.Y[(t >> 6) * LDS + (t & 63)];
 }
 
 // DIAG(k): the 64 x 64 diagonal tile (in sm.X, lower part) factored by
 // factor64 and inverted by inverse64; the unit factor goes to tile (k, k),
 // its inverse to Linv (and stays in sm.Y), D and D^-1 to global and to
 // sm.dprev / sm.iprev for the next step.
-__device__ bool factor_diag(LgShared& sm, float* A, float* Linv, float* D, float* invD, int k) {
+// The critical CTA's buffers for the tiles of its next step, fetched ahead
+struct DiagPre {
+  float* pa;  // tile (k, k-1), padded rows
+  float* pb;  // tile (k, k)
+};
+
+// tile (64 x 64, row-major, through L2) -> padded shared, by threads 128..255
+__device__ __forceinline__ void load_tile128(float* dst, const float* src) {
+  const int t = threadIdx.x - 2 * NB;
+  float4 v[8];
+#pragma unroll
+  for (int u = 0; u < 8; ++u) v[u] = __ldcg(reinterpret_cast<const float4*>(src) + t + u * 2 * NB);
+#pragma unroll
+  for (int u = 0; u < 8; ++u) {
+    const int q = t + u * 2 * NB;
+    const int r = (4 * q) / NB, c = (4 * q) % NB;
+    *reinterpret_cast<float4*>(dst + r * LDS + c) = v[u];
+  }
+}
+__device__ bool factor_diag(LgShared& sm, const DiagPre& pre, float* A, float* Linv, float* D, float* invD, int k,
+                            int T, int* ver, const int* env, int* status, long long timeout) {
   const int tid = threadIdx.x;
   float* tk = tile_ptr(A, k, k);
   if (tid == 0) sm.bad = 0;
   __syncthreads();
-  if (tid < NB) {
+  if (tid < 2 * NB) {  // warps 0-3: the factor, its inverse and their writes
     const bool ok = factor64(sm);
     if (!ok && tid == 0) sm.bad = 1;
+    asm volatile("bar.sync 3, 128;" ::: "memory");
+    if (!sm.bad) {
+      inverse64(sm, Linv + (size_t)k * TILE);
+      for (int t = tid; t < TILE; t += 2 * NB) {
+        const int r = t >> 6, c = t & 63;
+        tk[t] = c < r ? sm.X[r * LDX + c] : (c == r ? 1.f : 0.f);
+      }
+      if (tid < NB) {
+        D[k * NB + tid] = sm.dd[tid];
+        invD[k * NB + tid] = sm.invd[tid];
+        sm.dprev[tid] = sm.dd[tid];
+        sm.iprev[tid] = sm.invd[tid];
+      }
+    }
+  } else {
+    // meanwhile warps 4-7 fetch the next step's tiles (k+1, k) and (k+1, k+1)
+    // once the workers' updates through step k-1 are complete (those depend
+    // only on work published before this step's factorisation)
+    if (tid == 2 * NB) {
+      int f = 0;
+      if (k + 1 < T) {
+        bool ok = true;
+        if (__ldg(env + k + 1) <= k) {
+          ok = wait_geq(ver + tri2(k + 1) + k, k, status, timeout);
+          if (ok) f |= 1;
+        }
+        if (ok && wait_geq(ver + tri2(k + 1) + k + 1, k, status, timeout)) f |= 2;
+      }
+      sm.pf = f;
+    }
+    asm volatile("bar.sync 2, 128;" ::: "memory");
+    const int f = sm.pf;
+    if (f & 1) load_tile128(pre.pa, tile_ptr(A, k + 1, k));
+    if (f & 2) load_tile128(pre.pb, tile_ptr(A, k + 1, k + 1));
   }
   __syncthreads();
-  if (sm.bad) return false;
-  inverse64(sm, Linv + (size_t)k * TILE);
-  for (int t = tid; t < TILE; t += LG_THREADS) {
-    const int r = t >> 6, c = t & 63;
-    tk[t] = c < r ? sm.X[r * LDS + c] : (c == r ? 1.f : 0.f);
-  }
-  if (tid < NB) {
-    D[k * NB + tid] = sm.dd[tid];
-    invD[k * NB + tid] = sm.invd[tid];
-    sm.dprev[tid] = sm.dd[tid];
-    sm.iprev[tid] = sm.invd[tid];
-  }
-  return true;
+  return !sm.bad;
 }
 
 constexpr uint32_t TC_OP_BYTES = TILE * 4;  // one split part of one tile (16 KB)
@@ -379,117 +503,71 @@ struct TcState {
 // dynamic shared memory (after the CUDA-core tasks' LgShared).
 constexpr size_t TC_OFF = (sizeof(LgShared) + 1023) / 1024 * 1024;
 
-// D (tensor memory, 128 x 64, FP32) = A B^T for split operands in the
-// K-major core-matrix layout (A: 128 rows, B: 64 rows, K = 64): the 24 MMAs
-// of the three-pass TF32 product (hi*hi + hi*lo + lo*hi), committed to
-// bar_mma and waited for with a bound.  Thread 0 only; false on a timeout
-// (ts.bad = 2, the MMAs may still be in flight).
-__device__ bool tc_gemm64(TcState& ts, const unsigned char* a_hi, const unsigned char* a_lo, const unsigned char* b_hi,
-                          const unsigned char* b_lo, long long timeout) {
-  constexpr uint32_t idesc = tc_idesc_tf32(128, NB);
-  constexpr uint32_t LBO = 128, SBO = (NB / 4) * 128;
-  const uint32_t ah0 = tc_smem_addr(a_hi), al0 = tc_smem_addr(a_lo), bh0 = tc_smem_addr(b_hi), bl0 = tc_smem_addr(b_lo);
-#pragma unroll
-  for (int st = 0; st < NB / 8; ++st) {
-    const uint32_t off = st * 256;  // K = 8 TF32 values = two core matrices along K
-    const uint64_t ah = tc_desc(ah0 + off, LBO, SBO), al = tc_desc(al0 + off, LBO, SBO);
-    const uint64_t bh = tc_desc(bh0 + off, LBO, SBO), bl = tc_desc(bl0 + off, LBO, SBO);
-    tc_mma_tf32(ts.tmem, ah, bh, idesc, st > 0);
-    tc_mma_tf32(ts.tmem, ah, bl, idesc, 1);
-    tc_mma_tf32(ts.tmem, al, bh, idesc, 1);
-  }
-  tc_commit(&ts.bar_mma);
-  if (!tc_mbar_wait(&ts.bar_mma, ts.ph_mma, tc_hw_bound(timeout))) {
-    ts.bad = 2;
-    return false;
-  }
-  ts.ph_mma ^= 1u;
-  return true;
-}
-
 // Critical-path step k (one dedicated CTA, in order): for k > 0 first the
-// panel of tile (k, k-1), L = A_{k,k-1} L_{k-1}^-T D_{k-1}^-1 (CUDA cores,
-// from the inverse and D of step k-1 kept in shared memory), and its update
-// of tile (k, k), A_kk - G G^T with G = L D_{k-1}^1/2, on the tensor cores (G
-// is split once, for the workers' updates in global memory and for this
-// update in shared memory; the product sits in tensor-memory lanes 0..63,
-// read by warps 0, 1, 4, 5); then the factorisation of tile (k, k).
-__device__ bool task_diag_step(LgShared& sm, unsigned char* tcbuf, TcState& ts, float* A, float* G, float* Linv,
-                               float* D, float* invD, int k, int* ver, const int* env, int* status,
-                               long long timeout) {
-  const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
-  unsigned char* a_hi = tcbuf;
-  unsigned char* a_lo = a_hi + 2 * TC_OP_BYTES;
-  const bool epi = (wid & 3) < 2;
-  const int r = 32 * (wid & 3) + lane, c0 = 32 * (wid >> 2);
-  const uint32_t taddr = ts.tmem + ((uint32_t)(32 * (wid & 3)) << 16) + (uint32_t)c0;
+// panel of tile (k, k-1), L = A_{k,k-1} L_{k-1}^-T D_{k-1}^-1 (from the
+// inverse and D of step k-1 kept in shared memory), with its operand G for
+// the workers' updates, then the update of tile (k, k) by it, A_kk - L D L^T
+// (both on the CUDA cores: one 64 x 64 x 64 product each, no operand split);
+// then the factorisation of tile (k, k).  The two tiles the step reads were
+// usually fetched during the previous step's elimination (pre.pa / pre.pb
+// below, flags in sm.pf); otherwise they are waited for and loaded here.
+__device__ bool task_diag_step(LgShared& sm, const DiagPre& pre, float* A, float* G, float* Linv, float* D,
+                               float* invD, int k, int T, int* ver, const int* env, int* status, long long timeout) {
+  const int tid = threadIdx.x;
+  const int pf = sm.pf;  // (written before the previous step's last barrier)
   if (k > 0 && __ldg(env + k) < k) {  // (otherwise tile (k, k-1) lies outside the envelope: no panel, no update)
-    if (tid == 0) sm.bad = wait_geq(ver + tri2(k) + k - 1, k - 1, status, timeout) ? 0 : 1;
-    __syncthreads();
-    if (sm.bad) return false;
-    // the panel on the CUDA cores (the operands would first have to be split
-    // into the tensor cores' layout: measured slower for one tile)
     float* tp = tile_ptr(A, k, k - 1);
-    load_tile(sm.Z, tp, false);
-    __syncthreads();
-    {
-      const int tx = tid & 15, ty = tid >> 4;
-      float acc[4][4] = {};
-      gemm_nt(sm.Z, sm.Y, nullptr, acc);  // A_{k,k-1} L_{k-1}^-T
+    if (!(pf & 1)) {
+      if (tid == 0) sm.bad = wait_geq(ver + tri2(k) + k - 1, k - 1, status, timeout) ? 0 : 1;
       __syncthreads();
+      if (sm.bad) return false;
+      load_tile<LDS>(pre.pa, tp, false);
+    }
+    __syncthreads();
+    const int lane = tid & 31, r0 = 8 * (tid >> 5);  // (the layout of gemm_rows8)
+    {
+      float acc[8][2] = {};
+      gemm_rows8<true>(pre.pa, sm.Y, nullptr, acc);  // A_{k,k-1} L_{k-1}^-T
 #pragma unroll
-      for (int a = 0; a < 4; ++a)
+      for (int a = 0; a < 8; ++a)
 #pragma unroll
-        for (int b = 0; b < 4; ++b) {
-          const int rr = ty + 16 * a, c = tx + 16 * b;
-          const float l = acc[a][b] * sm.iprev[c];
+        for (int e = 0; e < 2; ++e) {
+          const int rr = r0 + a, c = lane + 32 * e;
+          const float l = acc[a][e] * sm.iprev[c];
           sm.Z[rr * LDS + c] = l;
           tp[rr * NB + c] = l;
         }
     }
     if (tid < NB) sm.sq[tid] = sqrtf(sm.dprev[tid]);
     __syncthreads();
-    store_g(sm.Z, sm.sq, g_ptr(G, k, k - 1), a_hi, a_lo);
-    tc_fence_smem();
+    store_g(sm.Z, sm.sq, g_ptr(G, k, k - 1));
     __syncthreads();
     if (tid == 0) {
       __threadfence();
       st_release(ver + tri2(k) + k - 1, k);  // tile (k, k-1) final
-      sm.bad = wait_geq(ver + tri2(k) + k, k - 1, status, timeout) ? 0 : 1;
+      sm.bad = (pf & 2) || wait_geq(ver + tri2(k) + k, k - 1, status, timeout) ? 0 : 1;
     }
     __syncthreads();
     if (sm.bad) return false;
-    // this thread's 32 entries of A_kk, read while the product runs
-    float4 av[8];
-    const float* tkk = tile_ptr(A, k, k);
-#pragma unroll
-    for (int q = 0; q < 8; ++q)
-      av[q] = epi ? __ldcg(reinterpret_cast<const float4*>(tkk + r * NB + c0) + q) : make_float4(0.f, 0.f, 0.f, 0.f);
-    tc_fence_after_sync();
-    if (tid == 0 && !tc_gemm64(ts, a_hi, a_lo, a_hi, a_lo, timeout)) dpv_set_status(status, DST_TIMEOUT);
-    __syncthreads();
-    if (ts.bad) return false;
-    tc_fence_after_sync();
-    if (epi) {
-      float d[32];
-      tc_ld32(taddr, d);
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const float4 v = av[q];
-        const float x[4] = {v.x - d[4 * q], v.y - d[4 * q + 1], v.z - d[4 * q + 2], v.w - d[4 * q + 3]};
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const int c = c0 + 4 * q + e;
-          sm.X[r * LDS + c] = c <= r ? x[e] : 0.f;
-        }
-      }
+    if (!(pf & 2)) {
+      load_tile<LDS>(pre.pb, tile_ptr(A, k, k), false);
+      __syncthreads();
     }
-    tc_fence_before_sync();
+    // A_kk - L D L^T, lower part
+    float acc[8][2] = {};
+    gemm_rows8<false>(sm.Z, sm.Z, sm.dprev, acc);
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        const int rr = r0 + a, c = lane + 32 * e;
+        sm.X[rr * LDX + c] = c <= rr ? pre.pb[rr * LDS + c] - acc[a][e] : 0.f;
+      }
   } else {
-    load_tile(sm.X, tile_ptr(A, k, k), true);
+    load_tile<LDX>(sm.X, tile_ptr(A, k, k), true);
   }
   __syncthreads();
-  return factor_diag(sm, A, Linv, D, invD, k);
+  return factor_diag(sm, pre, A, Linv, D, invD, k, T, ver, env, status, timeout);
 }
 
 // PANEL(i,k): L_ik = A_ik L_kk^-T D_k^-1, and the operand G_ik = L_ik D_k^1/2
@@ -500,23 +578,23 @@ __device__ void task_panel(LgShared& sm, float* A, float* G, const float* Linv, 
     sm.invd[threadIdx.x] = __ldcg(invD + k * NB + threadIdx.x);
     sm.sq[threadIdx.x] = sqrtf(__ldcg(D + k * NB + threadIdx.x));
   }
-  load_tiles2(sm.X, t, sm.Y, Linv + (size_t)k * TILE);
+  load_tiles2<LDS>(sm.Z, t, sm.Y, Linv + (size_t)k * TILE);
   __syncthreads();
-  float acc[4][4] = {};
-  gemm_nt(sm.X, sm.Y, nullptr, acc);
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  __syncthreads();  // every thread is done reading sm.X
+  float acc[8][2] = {};
+  gemm_rows8<true>(sm.Z, sm.Y, nullptr, acc);
+  const int lane = threadIdx.x & 31, r0 = 8 * (threadIdx.x >> 5);
+  __syncthreads();  // every thread is done reading sm.Z
 #pragma unroll
-  for (int a = 0; a < 4; ++a)
+  for (int a = 0; a < 8; ++a)
 #pragma unroll
-    for (int b = 0; b < 4; ++b) {
-      const int r = ty + 16 * a, c = tx + 16 * b;
-      const float l = acc[a][b] * sm.invd[c];
+    for (int e = 0; e < 2; ++e) {
+      const int r = r0 + a, c = lane + 32 * e;
+      const float l = acc[a][e] * sm.invd[c];
       t[r * NB + c] = l;
-      sm.X[r * LDS + c] = l;
+      sm.Z[r * LDS + c] = l;
     }
   __syncthreads();
-  store_g(sm.X, sm.sq, g_ptr(G, i, k));
+  store_g(sm.Z, sm.sq, g_ptr(G, i, k));
 }
 
 
@@ -533,41 +611,17 @@ __device__ void task_panel(LgShared& sm, float* A, float* G, const float* Linv, 
 // are not read.
 __device__ __forceinline__ bool quad_tile(int T, int a, int b) { return a < T && b < T && b <= a; }
 
-__device__ bool task_update_tc(unsigned char* tcbuf, TcState& ts, float* A, const float* G, const int* env, int T,
-                               int i, int j, int k, long long timeout) {
+__device__ bool task_update_tc(unsigned char* tcbuf, TcState& ts, float* A, const float* G, const int* env,
+                               const int* ver, int T, int i, int j, int k, int* status, long long timeout) {
   const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
   unsigned char* a_hi = tcbuf;
   unsigned char* a_lo = a_hi + 2 * TC_OP_BYTES;
   unsigned char* b_hi = a_lo + 2 * TC_OP_BYTES;
   unsigned char* b_lo = b_hi + 2 * TC_OP_BYTES;
-  if (tid == 0) {
-    // the operand rows i, i+1 (A) and j, j+1 (B) whose G_ak is nonzero
-    // (inside the envelope); the others are not copied
-    unsigned rok = 0;  // bit q: row (q < 2 ? i : j) + (q & 1)
-    uint32_t bytes = 0;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int a = (q < 2 ? i : j) + (q & 1);
-      if (a < T && __ldg(env + a) <= k) {
-        rok |= 1u << q;
-        bytes += 2 * TC_OP_BYTES;
-      }
-    }
-    tc_fence_global();  // G was written by other CTAs through the generic proxy
-    tc_fence_smem();    // this CTA's earlier generic accesses of the buffer are ordered before the copies
-    tc_mbar_expect_tx(&ts.bar_ld, bytes);
-#pragma unroll
-    for (int q = 0; q < 4; ++q)
-      if (rok & (1u << q)) {
-        const float* g = g_ptr(const_cast<float*>(G), (q < 2 ? i : j) + (q & 1), k);
-        unsigned char* d = (q < 2 ? a_hi : b_hi) + (q & 1) * TC_OP_BYTES;
-        tc_bulk_g2s(d, g, TC_OP_BYTES, &ts.bar_ld);                            // TF32 part
-        tc_bulk_g2s(d + 2 * TC_OP_BYTES, g + TILE, TC_OP_BYTES, &ts.bar_ld);  // FP32 rest
-      }
-  }
   // this thread's 64 outputs: row r of the 128 (tile row i + r / 64), the 64
-  // columns of tile column j + wid / 4; read meanwhile (only a tile that
-  // receives this step: both of its operand rows inside the envelope)
+  // columns of tile column j + wid / 4, read first (only a tile that receives
+  // this step: both of its operand rows inside the envelope; the tiles'
+  // versions were waited for before the task)
   const int r = 32 * (wid & 3) + lane, cb = wid >> 2;
   const int ta = i + (r >> 6), tb = j + cb, rr = r & 63;
   const bool mine = quad_tile(T, ta, tb) && max(__ldg(env + ta), __ldg(env + tb)) <= k;
@@ -577,6 +631,46 @@ __device__ bool task_update_tc(unsigned char* tcbuf, TcState& ts, float* A, cons
   for (int q = 0; q < 16; ++q)
     cv[q] = mine ? __ldcg(reinterpret_cast<const float4*>(ct) + q) : make_float4(0.f, 0.f, 0.f, 0.f);
   if (tid == 0) {
+    // the operand rows i, i+1 (A) and j, j+1 (B) whose G_ak is nonzero
+    // (inside the envelope; the others are not copied), each copied as soon
+    // as its panel is final, so that a task waiting for the critical chain's
+    // panel has everything else in flight already
+    unsigned pending = 0;  // bit q: row (q < 2 ? i : j) + (q & 1)
+    uint32_t bytes = 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int a = (q < 2 ? i : j) + (q & 1);
+      if (a < T && __ldg(env + a) <= k) {
+        pending |= 1u << q;
+        bytes += 2 * TC_OP_BYTES;
+      }
+    }
+    tc_fence_smem();  // this CTA's earlier generic accesses of the buffer are ordered before the copies
+    tc_mbar_expect_tx(&ts.bar_ld, bytes);
+    const long long t0 = clock64();
+    for (unsigned it = 0; pending; ++it) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int a = (q < 2 ? i : j) + (q & 1);
+        if ((pending & (1u << q)) && ld_acquire(ver + tri2(a) + k) >= k + 1) {
+          tc_fence_global();  // G was written by other CTAs through the generic proxy
+          const float* g = g_ptr(const_cast<float*>(G), a, k);
+          unsigned char* d = (q < 2 ? a_hi : b_hi) + (q & 1) * TC_OP_BYTES;
+          tc_bulk_g2s(d, g, TC_OP_BYTES, &ts.bar_ld);                            // TF32 part
+          tc_bulk_g2s(d + 2 * TC_OP_BYTES, g + TILE, TC_OP_BYTES, &ts.bar_ld);  // FP32 rest
+          pending &= ~(1u << q);
+        }
+      }
+      if (!pending) break;
+      if ((it & 63u) == 63u && (dpv_status(status) || clock64() - t0 > timeout)) {
+        dpv_set_status(status, DST_TIMEOUT);
+        ts.bad = 1;  // (the copies issued so far are waited for, bounded, on the way out)
+        break;
+      }
+      __nanosleep(64);
+    }
+  }
+  if (tid == 0 && !ts.bad) {
     if (!tc_mbar_wait(&ts.bar_ld, ts.ph_ld, tc_hw_bound(timeout))) {
       ts.bad = 1;
     } else {
@@ -836,9 +930,13 @@ __global__ void __launch_bounds__(LG_THREADS, 1) k_lg_factor(const LgProb* __res
   tc_fence_after_sync();
   if ((int)blockIdx.x < nsys) {
     const LgProb& P = probs[blockIdx.x];
+    // (the tensor-core operand buffers hold the prefetched tiles on this CTA)
+    const DiagPre pre{reinterpret_cast<float*>(tcbuf), reinterpret_cast<float*>(tcbuf) + NB * LDS};
+    if (threadIdx.x == 0) sm.pf = 0;
+    __syncthreads();
     for (int k = 0; k < P.T; ++k) {
       if (dpv_status(status)) goto done;
-      if (!task_diag_step(sm, tcbuf, ts, P.A, P.G, P.Linv, P.D, P.invD, k, P.ver, P.env, status, timeout)) {
+      if (!task_diag_step(sm, pre, P.A, P.G, P.Linv, P.D, P.invD, k, P.T, P.ver, P.env, status, timeout)) {
         if (threadIdx.x == 0 && !dpv_status(status)) dpv_set_status(status, DST_NOT_SPD);
         goto done;
       }
@@ -873,17 +971,14 @@ __global__ void __launch_bounds__(LG_THREADS, 1) k_lg_factor(const LgProb* __res
       const int lane = threadIdx.x;
       // lane q waits for the q-th version this task reads: a panel the
       // diagonal tile of column k (final) and its own tile (updated through
-      // step k-1); an update the panels of rows i, i+1 and j, j+1 of column
-      // k (final), then the target tiles (updated through step k-1)
+      // step k-1); an update its target tiles (updated through step k-1; the
+      // panels of its operand rows are waited for inside the task)
       const int* vp = nullptr;
       int want = 0;
       if (type == TASK_PANEL) {
         if (lane == 0) { vp = ver + tri2(k) + k; want = k + 1; }
         if (lane == 1) { vp = ver + tri2(i) + k; want = k; }
-      } else if (lane < 4) {  // lanes 0, 1: rows i, i+1; lanes 2, 3: rows j, j+1 (inside the envelope)
-        const int a = (lane < 2 ? i : j) + (lane & 1);
-        if (a < T && __ldg(P.env + a) <= k) { vp = ver + tri2(a) + k; want = k + 1; }
-      } else if (lane < 8) {  // the target tiles (i + (lane >> 1 & 1), j + (lane & 1)) that receive step k
+      } else if (lane >= 4 && lane < 8) {  // the target tiles (i + (lane >> 1 & 1), j + (lane & 1)) that receive step k
         const int a = i + ((lane >> 1) & 1), b = j + (lane & 1);
         if (quad_tile(T, a, b) && max(__ldg(P.env + a), __ldg(P.env + b)) <= k) { vp = ver + tri2(a) + b; want = k; }
       }
@@ -899,7 +994,7 @@ __global__ void __launch_bounds__(LG_THREADS, 1) k_lg_factor(const LgProb* __res
     if (bad) break;
     if (type == TASK_PANEL) {
       task_panel(sm, P.A, P.G, P.Linv, P.D, P.invD, i, k);
-    } else if (!task_update_tc(tcbuf, ts, P.A, P.G, P.env, T, i, j, k, timeout)) {
+    } else if (!task_update_tc(tcbuf, ts, P.A, P.G, P.env, ver, T, i, j, k, status, timeout)) {
       if (threadIdx.x == 0) dpv_set_status(status, DST_TIMEOUT);
       break;
     }
@@ -975,6 +1070,82 @@ __device__ void tile_gemv(const TileRegs& t, const float* v, float* out, bool tr
     for (int g = 0; g < 16; ++g) acc += part[g][tid];
     out[tid] = acc;
   }
+  __syncthreads();
+}
+
+// The chains' one product on the critical path, u_i -= M u_{i-1} (and its
+// backward counterpart), without a block barrier: M is staged in shared
+// memory (row-major, unpadded), warp w takes rows 8w .. 8w+7 and lane l the
+// columns 2l, 2l+1, and the lanes read the published vector words
+// themselves.
+__device__ __forceinline__ void stage_chain(float* dst, const float* M) {
+#pragma unroll
+  for (int u = 0; u < TILE / 4 / LG_THREADS; ++u)
+    reinterpret_cast<float4*>(dst)[threadIdx.x + u * LG_THREADS] =
+        __ldcg(reinterpret_cast<const float4*>(M) + threadIdx.x + u * LG_THREADS);
+}
+// sum_c M[8w + (lane >> 2)][c] x[c] for x[2l] = x0, x[2l+1] = x1 of lane l:
+// the eight row partials of each lane are reduced across the warp by halving
+// exchanges (lane bits 4, 3, 2 pick the row, bits 1, 0 finish the sum)
+__device__ __forceinline__ float chain_product(const float* Ms, float x0, float x1) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const float2* M2 = reinterpret_cast<const float2*>(Ms) + (8 * w) * (NB / 2) + lane;
+  float s[8];
+#pragma unroll
+  for (int r = 0; r < 8; ++r) {
+    const float2 m = M2[r * (NB / 2)];
+    s[r] = fmaf(m.x, x0, m.y * x1);
+  }
+  float t4[4];
+  {
+    const bool up = lane & 16;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float send = up ? s[q] : s[q + 4], keep = up ? s[q + 4] : s[q];
+      t4[q] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+  }
+  float t2[2];
+  {
+    const bool up = lane & 8;
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const float send = up ? t4[q] : t4[q + 2], keep = up ? t4[q + 2] : t4[q];
+      t2[q] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+  }
+  const bool up = lane & 4;
+  float t1 = (up ? t2[1] : t2[0]) + __shfl_xor_sync(0xffffffffu, up ? t2[0] : t2[1], 4);
+  t1 += __shfl_xor_sync(0xffffffffu, t1, 2);
+  t1 += __shfl_xor_sync(0xffffffffu, t1, 1);
+  return t1;
+}
+// M = X Y (trans = false) or (X Y)^T, 64 x 64 row-major tiles in global
+// memory, staged through gx, gy (padded rows)
+__device__ void chain_matrix(const float* X, const float* Y, float* out, bool trans, float* gx, float* gy) {
+  load_tiles2<LDC>(gx, X, gy, Y);
+  __syncthreads();
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  float acc[4][4] = {};
+#pragma unroll 4
+  for (int k = 0; k < NB; ++k) {
+    float xa[4], yb[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) xa[a] = gx[(ty + 16 * a) * LDC + k];
+#pragma unroll
+    for (int b = 0; b < 4; ++b) yb[b] = gy[k * LDC + tx + 16 * b];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(xa[a], yb[b], acc[a][b]);
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int r = ty + 16 * a, c = tx + 16 * b;
+      out[trans ? c * NB + r : r * NB + c] = acc[a][b];
+    }
   __syncthreads();
 }
 
@@ -1139,28 +1310,55 @@ __global__ void __launch_bounds__(LG_THREADS, 2) k_lg_solve(const LgProb* __rest
   __shared__ float part[16][NB + 1];
   __shared__ DFp dpart[16][NB];
   __shared__ DFp vr[NB], vc[NB];
+  __shared__ float wfin[NB];
+  __shared__ __align__(16) float gx[NB * LDC];  // (float4 stores, float2 loads: 16-byte aligned)
+  __shared__ __align__(16) float gy[NB * LDC];
   __shared__ int ok;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   if (tid == 0) ok = 1;
   __syncthreads();
+  if (dpv_status(status)) return;
+  // the chains' matrices of this CTA's rows, into the update-operand storage
+  // G (free once the factorisation is done): Mf_i = L_ii^-1 L_{i,i-1}
+  // (forward, tile (i, i-1) in the envelope) at tile i, Mb_i = (L_{i+1,i}
+  // L_ii^-1)^T (backward, tile (i+1, i) in the envelope) at tile T + i
+  for (int q = blockIdx.x; q < R; q += gridDim.x) {
+    const int r = rb_sys[R + q];
+    const LgProb& P = probs[rb_sys[r]];
+    const int i = r - P.rb0;
+    if (__ldg(P.env + i) < i)
+      chain_matrix(P.Linv + (size_t)i * TILE, P.A + (size_t)(tri2(i) + i - 1) * TILE, P.G + (size_t)i * TILE, false,
+                   gx, gy);
+  }
+  for (int q = blockIdx.x; q < R; q += gridDim.x) {
+    const int r = rb_sys[2 * R + q];
+    const LgProb& P = probs[rb_sys[r]];
+    const int i = r - P.rb0;
+    if (i + 1 < P.T && __ldg(P.env + i + 1) <= i)
+      chain_matrix(P.A + (size_t)(tri2(i + 1) + i) * TILE, P.Linv + (size_t)i * TILE, P.G + (size_t)(P.T + i) * TILE,
+                   true, gx, gy);
+  }
   for (int sweep = 0; sweep < sweeps; ++sweep) {
     if (dpv_status(status)) return;
     // ---- forward: L u = rhs; this CTA's row blocks in chain order (all
     // systems' first rows first), so that one system's chain never waits
-    // behind another's
+    // behind another's.  Row i: c_i = L_ii^-1 (rhs_i - sum_{j < i-1} L_ij u_j)
+    // while the rows above are solved, then u_i = c_i - Mf_i u_{i-1} as soon
+    // as the row above is published (one warp-local product, no barrier)
     for (int q = blockIdx.x; q < R; q += gridDim.x) {
       const int r = rb_sys[R + q];
       if (sys_finished(conv, nsys, rb_sys[r], sweep - 1, tol)) continue;
       const LgProb& P = probs[rb_sys[r]];
       const int i = r - P.rb0;
-      if (tid < NB) acc[tid] = __ldcg(P.rhs + i * NB + tid);
-      // the tiles do not depend on the solved rows: each is loaded while
-      // waiting for the previous row; the row's tiles start at its envelope
       const int j0 = __ldg(P.env + i);
-      TileRegs m = load_block(i > j0 ? P.A + (size_t)(tri2(i) + j0) * TILE : P.Linv + (size_t)i * TILE);
-      for (int j = j0; j < i; ++j) {
+      const bool dep = j0 < i;  // tile (i, i-1) lies in the envelope
+      if (dep) stage_chain(gx, P.G + (size_t)i * TILE);  // (read after the barriers below)
+      if (tid < NB) acc[tid] = __ldcg(P.rhs + i * NB + tid);
+      // the tiles do not depend on the solved rows: each is loaded while waiting for the previous row
+      TileRegs m = load_block(j0 < i - 1 ? P.A + (size_t)(tri2(i) + j0) * TILE : P.Linv + (size_t)i * TILE);
+      for (int j = j0; j < i - 1; ++j) {
         const TileRegs mn =
-            load_block(j + 1 < i ? P.A + (size_t)(tri2(i) + j + 1) * TILE : P.Linv + (size_t)i * TILE);
+            load_block(j + 1 < i - 1 ? P.A + (size_t)(tri2(i) + j + 1) * TILE : P.Linv + (size_t)i * TILE);
         if (tid < NB) {
           float v = 0.f;
           if (!wait_tagged(P.tf + j * NB + tid, sweep + 1, v, status, timeout)) ok = 0;
@@ -1173,20 +1371,37 @@ __global__ void __launch_bounds__(LG_THREADS, 2) k_lg_solve(const LgProb* __rest
         m = mn;
       }
       __syncthreads();
-      tile_gemv(m, acc, prod, false, part);
-      if (tid < NB) {
-        P.xf[i * NB + tid] = prod[tid];
-        st_tagged(P.tf + i * NB + tid, sweep + 1, prod[tid]);
+      tile_gemv(m, acc, prod, false, part);  // c_i
+      if (!dep) {
+        if (tid < NB) {
+          P.xf[i * NB + tid] = prod[tid];
+          st_tagged(P.tf + i * NB + tid, sweep + 1, prod[tid]);
+        }
+      } else {
+        float x0 = 0.f, x1 = 0.f;
+        if (!wait_tagged2(P.tf + (i - 1) * NB + 2 * lane, sweep + 1, x0, x1, status, timeout)) ok = 0;
+        const float sum = chain_product(gx, x0, x1);
+        const int row = 8 * wid + (lane >> 2);
+        if ((lane & 3) == 0) {
+          const float v = prod[row] - sum;
+          P.xf[i * NB + row] = v;
+          st_tagged(P.tf + i * NB + row, sweep + 1, v);
+        }
       }
+      __syncthreads();
+      if (!ok) return;
     }
     // ---- backward: L^T w = D^-1 u, rows descending; rho = r.w per system
-    // (row blocks in chain order from the bottom)
+    // (row blocks in chain order from the bottom).  Row i: c_i = L_ii^-T
+    // (D_i^-1 u_i - sum_{j > i+1} L_ji^T w_j), then w_i = c_i - Mb_i w_{i+1}
     for (int q = blockIdx.x; q < R; q += gridDim.x) {
       const int r = rb_sys[2 * R + q];
       const int sy = rb_sys[r];
       if (sys_finished(conv, nsys, sy, sweep - 1, tol)) continue;
       const LgProb& P = probs[sy];
       const int i = r - P.rb0, T = P.T;
+      const bool dep = i + 1 < T && __ldg(P.env + i + 1) <= i;  // tile (i+1, i) lies in the envelope
+      if (dep) stage_chain(gy, P.G + (size_t)(T + i) * TILE);
       // the forward result of this row (solved by whichever CTA owned it in
       // the forward order): taken from its published word
       if (tid < NB) {
@@ -1194,14 +1409,15 @@ __global__ void __launch_bounds__(LG_THREADS, 2) k_lg_solve(const LgProb* __rest
         if (!wait_tagged(P.tf + i * NB + tid, sweep + 1, u, status, timeout)) ok = 0;
         acc[tid] = u * __ldcg(P.invD + i * NB + tid);
       }
-      // the rows below whose envelope reaches column i (L is zero elsewhere)
-      int j = T - 1;
-      while (j > i && __ldg(P.env + j) > i) --j;
-      TileRegs m = load_block(j > i ? P.A + (size_t)(tri2(j) + i) * TILE : P.Linv + (size_t)i * TILE);
-      while (j > i) {
-        int jn = j - 1;
-        while (jn > i && __ldg(P.env + jn) > i) --jn;
-        const TileRegs mn = load_block(jn > i ? P.A + (size_t)(tri2(jn) + i) * TILE : P.Linv + (size_t)i * TILE);
+      // the rows j > i+1 whose envelope reaches column i (L is zero elsewhere)
+      int j = T;
+      do { --j; } while (j > i + 1 && __ldg(P.env + j) > i);
+      TileRegs m = load_block(j > i + 1 ? P.A + (size_t)(tri2(j) + i) * TILE : P.Linv + (size_t)i * TILE);
+      while (j > i + 1) {
+        int jn = j;
+        do { --jn; } while (jn > i + 1 && __ldg(P.env + jn) > i);
+        const TileRegs mn =
+            load_block(jn > i + 1 ? P.A + (size_t)(tri2(jn) + i) * TILE : P.Linv + (size_t)i * TILE);
         if (tid < NB) {
           float v = 0.f;
           if (!wait_tagged(P.tb + j * NB + tid, sweep + 1, v, status, timeout)) ok = 0;
@@ -1216,16 +1432,32 @@ __global__ void __launch_bounds__(LG_THREADS, 2) k_lg_solve(const LgProb* __rest
       }
       __syncthreads();
       if (!ok) return;
-      tile_gemv(m, acc, prod, true, part);
-      if (tid < NB) {
-        P.xb[i * NB + tid] = prod[tid];
-        st_tagged(P.tb + i * NB + tid, sweep + 1, prod[tid]);
+      tile_gemv(m, acc, prod, true, part);  // c_i
+      if (!dep) {
+        if (tid < NB) {
+          P.xb[i * NB + tid] = prod[tid];
+          st_tagged(P.tb + i * NB + tid, sweep + 1, prod[tid]);
+          wfin[tid] = prod[tid];
+        }
+      } else {
+        float x0 = 0.f, x1 = 0.f;
+        if (!wait_tagged2(P.tb + (i + 1) * NB + 2 * lane, sweep + 1, x0, x1, status, timeout)) ok = 0;
+        const float sum = chain_product(gy, x0, x1);
+        const int row = 8 * wid + (lane >> 2);
+        if ((lane & 3) == 0) {
+          const float v = prod[row] - sum;
+          P.xb[i * NB + row] = v;
+          st_tagged(P.tb + i * NB + row, sweep + 1, v);
+          wfin[row] = v;
+        }
       }
-      // off the chain: this block's share of rho = r.w (prod is rewritten
+      __syncthreads();
+      if (!ok) return;
+      // off the chain: this block's share of rho = r.w (wfin is rewritten
       // only after the next row's first CTA barrier)
       if (sweep > 0 && wid < 2) {
-        const int q = i * NB + tid;
-        double rw = __ldcg(P.r + q) * dpv_f2d_bits(prod[tid]);
+        const int qq = i * NB + tid;
+        double rw = __ldcg(P.r + qq) * dpv_f2d_bits(wfin[tid]);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) rw += __shfl_xor_sync(0xffffffffu, rw, o);
         if (lane == 0) dpv_red_add(red + 2 * (sweep * nsys + sy), rw);
