@@ -34,6 +34,8 @@
 #include "internal.cuh"
 #include "tcgen05.cuh"
 
+#include <cooperative_groups.h>
+
 #include <algorithm>
 #include <map>
 #include <mutex>
@@ -1303,8 +1305,9 @@ __device__ __forceinline__ bool sys_finished(const int* conv, int nsys, int p, i
 // the phases.  The iterations stop once every system's estimated error left
 // in x is below tol of it (dpv_solve_tol).
 __global__ void __launch_bounds__(LG_THREADS, 2) k_lg_solve(const LgProb* __restrict__ probs, int nsys,
-                                                            const int* __restrict__ rb_sys, int R, int sweeps,
-                                                            int* bar, int* conv, double* red, float tol,
+                                                            const int* __restrict__ rb_sys, int R, int s0, int s1,
+                                                            int sweeps, int ext, int* bar, int* conv, double* red,
+                                                            float tol,
                                                             int* status, long long timeout) {
   __shared__ float acc[NB], vj[NB], prod[NB];
   __shared__ float part[16][NB + 1];
@@ -1318,11 +1321,17 @@ __global__ void __launch_bounds__(LG_THREADS, 2) k_lg_solve(const LgProb* __rest
   if (tid == 0) ok = 1;
   __syncthreads();
   if (dpv_status(status)) return;
+  if (ext && s0 > 0) {  // a sweep after every system converged: nothing to do (the same in every CTA)
+    bool done = true;
+    for (int p = 0; p < nsys && done; ++p) done = sys_finished(conv, nsys, p, s0 - 1, tol);
+    if (done) return;
+  }
   // the chains' matrices of this CTA's rows, into the update-operand storage
   // G (free once the factorisation is done): Mf_i = L_ii^-1 L_{i,i-1}
   // (forward, tile (i, i-1) in the envelope) at tile i, Mb_i = (L_{i+1,i}
   // L_ii^-1)^T (backward, tile (i+1, i) in the envelope) at tile T + i
-  for (int q = blockIdx.x; q < R; q += gridDim.x) {
+  // (ext: the chains run in k_lg_chain, sweeps s0 .. sweeps-1 here)
+  for (int q = blockIdx.x; q < R && !ext; q += gridDim.x) {
     const int r = rb_sys[R + q];
     const LgProb& P = probs[rb_sys[r]];
     const int i = r - P.rb0;
@@ -1330,7 +1339,7 @@ __global__ void __launch_bounds__(LG_THREADS, 2) k_lg_solve(const LgProb* __rest
       chain_matrix(P.Linv + (size_t)i * TILE, P.A + (size_t)(tri2(i) + i - 1) * TILE, P.G + (size_t)i * TILE, false,
                    gx, gy);
   }
-  for (int q = blockIdx.x; q < R; q += gridDim.x) {
+  for (int q = blockIdx.x; q < R && !ext; q += gridDim.x) {
     const int r = rb_sys[2 * R + q];
     const LgProb& P = probs[rb_sys[r]];
     const int i = r - P.rb0;
@@ -1338,8 +1347,9 @@ __global__ void __launch_bounds__(LG_THREADS, 2) k_lg_solve(const LgProb* __rest
       chain_matrix(P.A + (size_t)(tri2(i + 1) + i) * TILE, P.Linv + (size_t)i * TILE, P.G + (size_t)(P.T + i) * TILE,
                    true, gx, gy);
   }
-  for (int sweep = 0; sweep < sweeps; ++sweep) {
+  for (int sweep = s0; sweep < s1; ++sweep) {
     if (dpv_status(status)) return;
+    if (!ext) {
     // ---- forward: L u = rhs; this CTA's row blocks in chain order (all
     // systems' first rows first), so that one system's chain never waits
     // behind another's.  Row i: c_i = L_ii^-1 (rhs_i - sum_{j < i-1} L_ij u_j)
@@ -1464,6 +1474,7 @@ __global__ void __launch_bounds__(LG_THREADS, 2) k_lg_solve(const LgProb* __rest
       }
     }
     if (!grid_barrier(bar, gridDim.x, status, timeout)) return;
+    }  // !ext
     if (sweep == 0) {
       // ---- z = w: x = s w, the first correction
       for (int r = blockIdx.x; r < R; r += gridDim.x) {
@@ -1606,6 +1617,277 @@ __global__ void __launch_bounds__(LG_THREADS, 2) k_lg_solve(const LgProb* __rest
   }
 }
 
+// ---------------------------------------------------------------------------
+// The triangular-solve chains in one thread-block cluster per system
+// ---------------------------------------------------------------------------
+// The forward and backward chains of one CG sweep move one 64-row block per
+// step from the CTA that solved it to the next; through global memory each
+// step costs an L2 round trip of the published words (~1 us per row block
+// on this part).  Here the CTAs of one cluster take the row blocks of one
+// system round robin (block i on cluster rank i mod C), every CTA holds the
+// whole vector as tagged words in its shared memory, and a solved block is
+// stored into every CTA's copy through distributed shared memory; the
+// consumers poll their own shared memory.  Each solved block is formed from
+// per-tile products with the blocks it depends on, the tiles premultiplied
+// by the diagonal block's inverse (k_lg_chainmat), so that a warp finishes
+// its rows without waiting for the rest of its CTA.
+
+// The chains' matrices, one per tile of the envelope and one CTA per matrix
+// (blockIdx.y = system), into the update-operand storage G (free once the
+// factorisation is done), indexed by the envelope's tile order e(a, b) =
+// eoff_a + b - env_a:
+//   forward   G[e(i, j)]      = L_ii^-1 L_ij       (j < i),  L_ii^-1    (j = i)
+//   backward  G[E + e(j, i)]  = (L_ji L_ii^-1)^T   (j > i),  L_ii^-T    (j = i)
+// (E = the envelope's tile count), so that a solved row block is
+//   u_i = L_ii^-1 b_i - sum_j (L_ii^-1 L_ij) u_j,
+//   w_i = L_ii^-T c_i - sum_j (L_ji L_ii^-1)^T w_j.
+__global__ void __launch_bounds__(LG_THREADS) k_lg_chainmat(const LgProb* __restrict__ probs, const int* status) {
+  __shared__ __align__(16) float gx[NB * LDC];
+  __shared__ __align__(16) float gy[NB * LDC];
+  if (dpv_status(status)) return;
+  const LgProb& P = probs[blockIdx.y];
+  const int E = __ldg(P.eoff + P.T);
+  const bool bwd = (int)blockIdx.x >= E;
+  const int t = bwd ? (int)blockIdx.x - E : (int)blockIdx.x;
+  if (t >= E) return;
+  int a, b;
+  env_tile(P, t, a, b);  // tile (a, b) of the envelope, b <= a
+  float* out = P.G + (size_t)blockIdx.x * TILE;
+  if (a == b) {  // L_aa^-1, or its transpose
+    const float* li = P.Linv + (size_t)a * TILE;
+    for (int q = threadIdx.x; q < TILE; q += LG_THREADS) {
+      const int r = q >> 6, c = q & 63;
+      out[q] = bwd ? __ldcg(li + c * NB + r) : __ldcg(li + q);
+    }
+  } else if (!bwd) {
+    chain_matrix(P.Linv + (size_t)a * TILE, P.A + (size_t)(tri2(a) + b) * TILE, out, false, gx, gy);
+  } else {
+    chain_matrix(P.A + (size_t)(tri2(a) + b) * TILE, P.Linv + (size_t)b * TILE, out, true, gx, gy);
+  }
+}
+
+// Wait (bounded) until the tagged word p of this CTA's shared memory carries
+// tag; its value in v.
+__device__ __forceinline__ bool wait_local(const unsigned long long* p, unsigned tag, float& v, int* status,
+                                           long long timeout) {
+  const long long t0 = clock64();
+  for (unsigned it = 0;; ++it) {
+    const unsigned long long w = *reinterpret_cast<const volatile unsigned long long*>(p);
+    if ((unsigned)(w >> 32) == tag) {
+      v = __uint_as_float((unsigned)w);
+      return true;
+    }
+    if ((it & 255u) == 255u) {
+      if (dpv_status(status)) return false;
+      if (clock64() - t0 > timeout) {
+        dpv_set_status(status, DST_TIMEOUT);
+        return false;
+      }
+    }
+    if (it > 64) __nanosleep(16);
+  }
+}
+
+// This lane's slice of a chain matrix: rows 8w .. 8w+7, columns 2l, 2l+1.
+struct ChainSlice {
+  float2 m[8];
+};
+__device__ __forceinline__ ChainSlice load_slice(const float* M) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  ChainSlice c;
+#pragma unroll
+  for (int r = 0; r < 8; ++r) c.m[r] = __ldcg(reinterpret_cast<const float2*>(M + (8 * w + r) * NB) + lane);
+  return c;
+}
+// the sum over the warp of the eight row partials (see chain_product): lane
+// l ends with row 8w + (l >> 2)
+__device__ __forceinline__ float reduce_rows8(const float (&s)[8]) {
+  const int lane = threadIdx.x & 31;
+  float t4[4];
+  {
+    const bool up = lane & 16;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float send = up ? s[q] : s[q + 4], keep = up ? s[q + 4] : s[q];
+      t4[q] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+  }
+  float t2[2];
+  {
+    const bool up = lane & 8;
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const float send = up ? t4[q] : t4[q + 2], keep = up ? t4[q + 2] : t4[q];
+      t2[q] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+  }
+  const bool up = lane & 4;
+  float t1 = (up ? t2[1] : t2[0]) + __shfl_xor_sync(0xffffffffu, up ? t2[0] : t2[1], 4);
+  t1 += __shfl_xor_sync(0xffffffffu, t1, 2);
+  t1 += __shfl_xor_sync(0xffffffffu, t1, 1);
+  return t1;
+}
+
+constexpr int CH_MAX_T = 128;  // tile rows of a system whose chains run in a cluster (2 x 64 KB of tagged words)
+// The cluster form costs two launches per CG sweep instead of one kernel for
+// all sweeps; it pays where the chains are long (measured: 1000 keyframes,
+// 94 tile rows, 180 -> 130 us per sweep), not for the 64-problem batch
+// (at most 38 tile rows: 8.55k -> 8.14k problem GN it/s).
+constexpr int CH_MIN_T = 64;
+constexpr unsigned CH_TAG = 1;  // tag of a solved value (the copies are cleared to tag 0 by each launch)
+
+// One sweep's chains: cluster b solves system b (forward L u = rhs, then
+// backward L^T w = D^-1 u), writing u to xf and w to xb, and adds its rows'
+// shares of rho = r.w (sweeps > 0).  Systems already converged are skipped.
+// Row block i belongs to cluster rank i mod C; within it warp w takes rows
+// 8w .. 8w+7 and works on its own (no block barrier): per tile of the
+// envelope its lanes read the two solved values they need from their
+// shared memory and multiply them into the slice of the chain matrix that
+// was loaded meanwhile.
+__global__ void __launch_bounds__(LG_THREADS) k_lg_chain(const LgProb* __restrict__ probs, int nsys, int sweep,
+                                                         const int* conv, double* red, float tol, int* status,
+                                                         long long timeout) {
+  // this CTA's copies of the forward and the backward vectors, tagged; each
+  // word is written once per launch (a word written twice by one thread
+  // through the cluster could be observed in either order)
+  extern __shared__ __align__(16) unsigned long long xs[];  // [2][T * NB]
+  namespace cgr = cooperative_groups;
+  cgr::cluster_group cl = cgr::this_cluster();
+  const int C = (int)cl.num_blocks(), rank = (int)cl.block_rank();
+  const int sy = blockIdx.x / C;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  // (the same decision in every CTA of the cluster: the convergence words
+  // are final; an error reported meanwhile ends the waits below)
+  if (sy >= nsys || sys_finished(conv, nsys, sy, sweep - 1, tol)) return;
+  const LgProb& P = probs[sy];
+  const int T = P.T, E = __ldg(P.eoff + T);
+  unsigned long long* xf = xs;           // forward values u
+  unsigned long long* xb = xs + T * NB;  // backward values w
+  for (int q = tid; q < 2 * T * NB; q += LG_THREADS) xs[q] = 0ull;
+  cl.sync();  // every copy is cleared before any CTA stores into it
+  const int row = 8 * wid + (lane >> 2);  // the row this lane reports after the reduction
+  // (remote stores go to every CTA of the cluster, this one included: lanes
+  // l, l+1, l+2, l+3 hold the same row value and share the destinations)
+  auto publish = [&](unsigned long long* vec, int i, float v) {
+    const unsigned long long w = ((unsigned long long)CH_TAG << 32) | __float_as_uint(v);
+    for (int d = lane & 3; d < C; d += 4) {
+      unsigned long long* rx = cl.map_shared_rank(vec, (unsigned)d);
+      reinterpret_cast<volatile unsigned long long*>(rx)[i * NB + row] = w;
+    }
+  };
+  bool good = true;
+  // ---- forward: row blocks rank, rank + C, ...
+  for (int i = rank; i < T && good; i += C) {
+    const int j0 = __ldg(P.env + i);
+    const float* Nr = P.G + (size_t)(__ldg(P.eoff + i) - j0) * TILE;  // N_ij at Nr + j * TILE
+    float s[8];
+    {
+      const ChainSlice li = load_slice(Nr + (size_t)i * TILE);
+      const float2 b = __ldcg(reinterpret_cast<const float2*>(P.rhs + i * NB) + lane);
+#pragma unroll
+      for (int r = 0; r < 8; ++r) s[r] = fmaf(li.m[r].x, b.x, li.m[r].y * b.y);
+    }
+    // the tiles j0 .. i-1, their slices loaded two tiles ahead
+    const int jc = i;  // (the end of the list)
+    ChainSlice b[2];
+#pragma unroll
+    for (int q = 0; q < 2; ++q)
+      if (j0 + q < jc) b[q] = load_slice(Nr + (size_t)(j0 + q) * TILE);
+    for (int j = j0; j < jc && good; j += 2) {
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const int jj = j + q;
+        if (jj < jc && good) {
+          float x0 = 0.f, x1 = 0.f;
+          if (!wait_local(xf + jj * NB + 2 * lane, CH_TAG, x0, status, timeout) ||
+              !wait_local(xf + jj * NB + 2 * lane + 1, CH_TAG, x1, status, timeout)) {
+            good = false;
+          } else {
+#pragma unroll
+            for (int r = 0; r < 8; ++r) s[r] = fmaf(-b[q].m[r].x, x0, fmaf(-b[q].m[r].y, x1, s[r]));
+            if (jj + 2 < jc) b[q] = load_slice(Nr + (size_t)(jj + 2) * TILE);
+          }
+        }
+      }
+    }
+    good = __all_sync(0xffffffffu, good);
+    if (!good) break;
+    const float v = reduce_rows8(s);
+    publish(xf, i, v);
+    if ((lane & 3) == 0) P.xf[i * NB + row] = v;
+  }
+  // ---- backward: row blocks of this rank, descending
+  for (int i = rank + C * ((T - 1 - rank) / C); i >= 0 && rank < T && good; i -= C) {
+    float s[8];
+    {
+      const ChainSlice lt = load_slice(P.G + (size_t)(E + __ldg(P.eoff + i) + i - __ldg(P.env + i)) * TILE);
+      float u0 = 0.f, u1 = 0.f;
+      if (!wait_local(xf + i * NB + 2 * lane, CH_TAG, u0, status, timeout) ||
+          !wait_local(xf + i * NB + 2 * lane + 1, CH_TAG, u1, status, timeout))
+        good = false;
+      const float2 dv = __ldcg(reinterpret_cast<const float2*>(P.invD + i * NB) + lane);
+      u0 *= dv.x;
+      u1 *= dv.y;
+#pragma unroll
+      for (int r = 0; r < 8; ++r) s[r] = fmaf(lt.m[r].x, u0, lt.m[r].y * u1);
+    }
+    // the rows j > i whose envelope reaches column i, bottom up, their
+    // slices loaded two rows ahead (next_row: the next such row below j)
+    const int lo = i;  // the ring takes the rows above lo
+    auto next_row = [&](int j) {
+      do { --j; } while (j > lo && __ldg(P.env + j) > i);
+      return j;
+    };
+    auto bslice = [&](int j) { return P.G + (size_t)(E + __ldg(P.eoff + j) + i - __ldg(P.env + j)) * TILE; };
+    int jr[2];  // the rows whose slices sit in b[0..1] (lo: none)
+    ChainSlice b[2];
+    {
+      int j = T;
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        j = j > lo ? next_row(j) : lo;
+        jr[q] = j;
+        if (j > lo) b[q] = load_slice(bslice(j));
+      }
+    }
+    while (good && jr[0] > lo) {
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const int j = jr[q];
+        if (j > lo && good) {
+          float x0 = 0.f, x1 = 0.f;
+          if (!wait_local(xb + j * NB + 2 * lane, CH_TAG, x0, status, timeout) ||
+              !wait_local(xb + j * NB + 2 * lane + 1, CH_TAG, x1, status, timeout)) {
+            good = false;
+          } else {
+#pragma unroll
+            for (int r = 0; r < 8; ++r) s[r] = fmaf(-b[q].m[r].x, x0, fmaf(-b[q].m[r].y, x1, s[r]));
+            // the row two places further down the list
+            const int last = jr[q ^ 1];
+            const int jn = last > lo ? next_row(last) : lo;
+            jr[q] = jn;
+            if (jn > lo) b[q] = load_slice(bslice(jn));
+          }
+        } else {
+          jr[q] = lo;
+        }
+      }
+    }
+    good = __all_sync(0xffffffffu, good);
+    if (!good) break;
+    const float v = reduce_rows8(s);
+    publish(xb, i, v);
+    if ((lane & 3) == 0) P.xb[i * NB + row] = v;
+    if (sweep > 0) {  // this warp's share of rho = r.w
+      double rw = (lane & 3) == 0 ? __ldcg(P.r + i * NB + row) * dpv_f2d_bits(v) : 0.0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) rw += __shfl_xor_sync(0xffffffffu, rw, o);
+      if (lane == 0) dpv_red_add(red + 2 * (sweep * nsys + sy), rw);
+    }
+  }
+  cl.sync();  // no CTA leaves while another may still store into its copy
+}
+
 // Task list of several systems, in dependency order within each system and
 // interleaved by step across systems, so that every critical chain advances
 // together.  Per system: step k's update of columns k+1, k+2 and the panels
@@ -1683,6 +1965,42 @@ long long dpv_large_scratch_floats(int n_pad) {
 namespace {
 
 constexpr int MAX_SWEEPS = 16;
+
+// The cluster size of k_lg_chain on this device: 16 CTAs (a non-portable
+// size) where one such cluster fits, else 8; 0 when neither does (the chains
+// then run in k_lg_solve).  Found once.
+int chain_cluster(ba_handle_t h) {
+  static int C = -1;
+  if (C >= 0) return C;
+  C = 0;
+  const int smem = (int)(2 * sizeof(unsigned long long) * CH_MAX_T * NB);
+  if (cudaFuncSetAttribute(k_lg_chain, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess ||
+      cudaFuncSetAttribute(k_lg_chain, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+    cudaGetLastError();
+    return C;
+  }
+  for (int c : {16, 8}) {
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = (unsigned)c;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3((unsigned)c);
+    cfg.blockDim = dim3(LG_THREADS);
+    cfg.dynamicSmemBytes = (size_t)smem;
+    cfg.stream = h->stream;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, k_lg_chain, &cfg) == cudaSuccess && n > 0) {
+      C = c;
+      break;
+    }
+    cudaGetLastError();
+  }
+  return C;
+}
 
 // The large systems' descriptors, row-block table, task list and sync-word
 // layout for the current pose-system layout; grows the solver's buffers.
@@ -1929,10 +2247,47 @@ ba_status_t dpv_solve_large(ba_handle_t h, int refine) {
     int nsys_ = nsys, R_ = R;
     const int* rb = ws->lg_rb.p;
     float tol = dpv_solve_tol(h);
-    void* args[] = {(void*)&dprobs, (void*)&nsys_, (void*)&rb,  (void*)&R_,     (void*)&sweeps, (void*)&bar,
-                    (void*)&conv,   (void*)&red,   (void*)&tol, (void*)&status, (void*)&timeout};
-    DPV_CUDA(h, launch_cooperative((const void*)k_lg_solve, grid, 0, st, args));
-    ++h->launches;
+    int maxT = 0, maxE = 0;
+    for (int T : Ts) {
+      maxT = std::max(maxT, T);
+      maxE = std::max(maxE, tri2(T));  // (the envelope has at most tri(T) tiles; the rest of the grid returns)
+    }
+    const int C = maxT >= CH_MIN_T && maxT <= CH_MAX_T ? chain_cluster(h) : 0;
+    if (C > 0) {
+      // the chains in clusters, the rest of each sweep in the cooperative kernel
+      k_lg_chainmat<<<dim3(2 * maxE, nsys), LG_THREADS, 0, st>>>(dprobs, status);
+      ++h->launches;
+      for (int sw = 0; sw < sweeps; ++sw) {
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = (unsigned)C;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.gridDim = dim3((unsigned)(nsys * C));
+        cfg.blockDim = dim3(LG_THREADS);
+        cfg.dynamicSmemBytes = 2 * sizeof(unsigned long long) * (size_t)maxT * NB;
+        cfg.stream = st;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        DPV_CUDA(h, cudaLaunchKernelEx(&cfg, k_lg_chain, dprobs, nsys, sw, (const int*)conv, red, tol, status,
+                                       timeout));
+        ++h->launches;
+        int s0 = sw, s1 = sw + 1, ext = 1;
+        void* args[] = {(void*)&dprobs, (void*)&nsys_, (void*)&rb,  (void*)&R_,  (void*)&s0,
+                        (void*)&s1,     (void*)&sweeps, (void*)&ext, (void*)&bar, (void*)&conv,
+                        (void*)&red,    (void*)&tol,    (void*)&status, (void*)&timeout};
+        DPV_CUDA(h, launch_cooperative((const void*)k_lg_solve, grid, 0, st, args));
+        ++h->launches;
+      }
+    } else {
+      int s0 = 0, ext = 0;
+      void* args[] = {(void*)&dprobs, (void*)&nsys_,  (void*)&rb,  (void*)&R_,  (void*)&s0,
+                      (void*)&sweeps, (void*)&sweeps, (void*)&ext, (void*)&bar, (void*)&conv,
+                      (void*)&red,    (void*)&tol,    (void*)&status, (void*)&timeout};
+      DPV_CUDA(h, launch_cooperative((const void*)k_lg_solve, grid, 0, st, args));
+      ++h->launches;
+    }
   }
   DPV_CUDA(h, cudaGetLastError());
   return BA_OK;
