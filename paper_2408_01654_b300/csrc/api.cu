@@ -966,8 +966,7 @@ ba_status_t ba_debug_export(ba_handle_t h, int what, void* dst, long long bytes)
 
 ba_status_t ba_debug_envelope(ba_handle_t h, int* out, long long cap, long long* count) {
   if (!h || !count || (cap > 0 && !out)) return BA_ERR_INVALID_ARG;
-  if (!h->have_graph) return dpv_fail(h, BA_ERR_STATE, "no graph bound");
-  return dpv_large_envelope(h, out, cap, count);
+  return dpv_large_envelope(h, out, cap, count);  // (also the pose graph of ba_pgo_lm)
 }
 
 ba_status_t ba_debug_keys(ba_handle_t h, int fixed_poses, int* keys_out, int cap, int* n_out) {
