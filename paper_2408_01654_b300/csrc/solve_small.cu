@@ -153,9 +153,9 @@ __global__ void __launch_bounds__(small_threads(NQ)) k_solve_small(
   // lambda_p on the free diagonal, 1 on the padding diagonal.  Done here when
   // no refinement sweep reads S from global memory again, else at the end.
   const bool s_read_later = refine64 > 0 || (refine32 > 0 && !keep_sf(NQ));
-  auto reset_S = [&]() {
+  auto reset_S = [&](int t0, int nt) {
     double2* S2w = reinterpret_cast<double2*>(S);
-    for (int q = tid; q < NP * (NP / 2); q += NT) {
+    for (int q = t0; q < NP * (NP / 2); q += nt) {
       const int i = q / (NP / 2), p = q - (q / (NP / 2)) * (NP / 2);
       if (2 * p > i) continue;
       double2 v = make_double2(0.0, 0.0);
@@ -165,10 +165,58 @@ __global__ void __launch_bounds__(small_threads(NQ)) k_solve_small(
     }
   };
   __syncthreads();
-  if (reset && !s_read_later) reset_S();
 
+  // 4. trailing update by the panel of block r0p, A[i][j] -= sum_c Pb[i][c]
+  // L[j][r0p + c] for i >= j >= r0p + 32, on the 4 x 4 tiles whose columns
+  // lie in [c0, c1), threads t0, t0 + nt, ...
+  auto update_tiles = [&](int r0p, int c0, int c1, int t0, int nt) {
+    const int p1 = r0p + 32, mt = (NP - p1) / 4;
+    const int b0 = (c0 - p1) / 4, b1 = (c1 - p1) / 4;
+    int total = 0;
+    for (int bj = b0; bj < b1; ++bj) total += mt - bj;
+    for (int t = t0; t < total; t += nt) {
+      int bj = b0, bi = t;
+      while (bi >= mt - bj) {
+        bi -= mt - bj;
+        ++bj;
+      }
+      bi += bj;
+      const int i0 = p1 + 4 * bi, j0 = p1 + 4 * bj;
+      float acc[4][4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
+#pragma unroll 4
+      for (int c = 0; c < 32; ++c) {
+        float pa[4], lb[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) pa[a] = Pb[i0 + a][c];
+#pragma unroll
+        for (int b = 0; b < 4; ++b) lb[b] = Lsh[tri(j0 + b, r0p) + c];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(pa[a], lb[b], acc[a][b]);
+      }
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+          if (i0 + a >= j0 + b) Lsh[tri(i0 + a, j0 + b)] -= acc[a][b];
+    }
+  };
+  // Right-looking with one block of lookahead: before block kb is eliminated
+  // its own columns receive the previous panel's update (all threads); then
+  // warp 0 eliminates and inverts the diagonal block while the other warps
+  // apply the previous panel to the columns beyond it (and, for the first
+  // block, reset S for the next assembly).
   for (int r0 = 0; r0 < NP; r0 += 32) {
     const int kb = r0 / 32;
+    if (kb > 0) {
+      update_tiles(r0 - 32, r0, r0 + 32, tid, NT);
+      __syncthreads();
+    }
     // 1. diagonal block, lane = row r0 + lane
     if (wid == 0) {
       float a[32];
@@ -211,9 +259,13 @@ __global__ void __launch_bounds__(small_threads(NQ)) k_solve_small(
         for (int i = k + 1; i < 32; ++i) x[i] = fmaf(-Lsh[tri(r0 + i, r0 + k)], x[k], x[i]);
 #pragma unroll
       for (int i = 0; i < 32; ++i) Linv[kb][i][lane] = x[i];
+    } else {
+      if (kb > 0 && r0 + 32 < NP) update_tiles(r0 - 32, r0 + 32, NP, tid - 32, NT - 32);
+      if (kb == 0 && reset && !s_read_later) reset_S(tid - 32, NT - 32);
     }
     __syncthreads();
     if (bad) break;
+    if (r0 + 32 == NP) break;
     // 3. panel rows below the block: P = A_panel L_kk^-T (lane = output column)
     // (three rows per warp at a time: independent dependency chains)
     for (int i0 = r0 + 32 + wid; i0 < NP; i0 += 3 * NWARP) {
@@ -236,38 +288,6 @@ __global__ void __launch_bounds__(small_threads(NQ)) k_solve_small(
           Lsh[tri(i, r0 + lane)] = p[u] * invD[r0 + lane];
         }
       }
-    }
-    __syncthreads();
-    // 4. trailing update A[i][j] -= sum_c Pb[i][c] L[j][r0 + c], i >= j >= r0 + 32, 4x4 tiles
-    const int p1 = r0 + 32, m = NP - p1, mt = m / 4;
-    for (int t = tid; t < tri(mt, 0); t += NT) {  // lower tiles only (bi >= bj)
-      int bi = (int)((sqrtf(8.0f * t + 1.0f) - 1.0f) * 0.5f);
-      while (tri(bi + 1, 0) <= t) ++bi;
-      while (tri(bi, 0) > t) --bi;
-      const int bj = t - tri(bi, 0);
-      const int i0 = p1 + 4 * bi, j0 = p1 + 4 * bj;
-      float acc[4][4];
-#pragma unroll
-      for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
-#pragma unroll 4
-      for (int c = 0; c < 32; ++c) {
-        float pa[4], lb[4];
-#pragma unroll
-        for (int a = 0; a < 4; ++a) pa[a] = Pb[i0 + a][c];
-#pragma unroll
-        for (int b = 0; b < 4; ++b) lb[b] = Lsh[tri(j0 + b, r0) + c];
-#pragma unroll
-        for (int a = 0; a < 4; ++a)
-#pragma unroll
-          for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(pa[a], lb[b], acc[a][b]);
-      }
-#pragma unroll
-      for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int b = 0; b < 4; ++b)
-          if (i0 + a >= j0 + b) Lsh[tri(i0 + a, j0 + b)] -= acc[a][b];
     }
     __syncthreads();
   }
@@ -306,10 +326,15 @@ __global__ void __launch_bounds__(small_threads(NQ)) k_solve_small(
         }
         vb[lane] = rhs[r] - ((a0 + a1) + (a2 + a3));
         __syncwarp();
-        float u = 0.f;
-#pragma unroll 8
-        for (int c = 0; c < 32; ++c) u = fmaf(Linv[kb][lane][c], vb[c], u);
-        sol[r] = u;
+        float u0 = 0.f, u1 = 0.f, u2 = 0.f, u3 = 0.f;
+#pragma unroll
+        for (int c = 0; c < 32; c += 4) {
+          u0 = fmaf(Linv[kb][lane][c], vb[c], u0);
+          u1 = fmaf(Linv[kb][lane][c + 1], vb[c + 1], u1);
+          u2 = fmaf(Linv[kb][lane][c + 2], vb[c + 2], u2);
+          u3 = fmaf(Linv[kb][lane][c + 3], vb[c + 3], u3);
+        }
+        sol[r] = (u0 + u1) + (u2 + u3);
         __syncwarp();
       }
       // backward, left-looking from the bottom (into rhs):
@@ -326,10 +351,15 @@ __global__ void __launch_bounds__(small_threads(NQ)) k_solve_small(
         }
         vb[lane] = sol[r] * invD[r] - ((a0 + a1) + (a2 + a3));
         __syncwarp();
-        float x = 0.f;
-#pragma unroll 8
-        for (int c = 0; c < 32; ++c) x = fmaf(Linv[kb][c][lane], vb[c], x);
-        rhs[r] = x;
+        float x0 = 0.f, x1 = 0.f, x2 = 0.f, x3 = 0.f;
+#pragma unroll
+        for (int c = 0; c < 32; c += 4) {
+          x0 = fmaf(Linv[kb][c][lane], vb[c], x0);
+          x1 = fmaf(Linv[kb][c + 1][lane], vb[c + 1], x1);
+          x2 = fmaf(Linv[kb][c + 2][lane], vb[c + 2], x2);
+          x3 = fmaf(Linv[kb][c + 3][lane], vb[c + 3], x3);
+        }
+        rhs[r] = (x0 + x1) + (x2 + x3);
         __syncwarp();
       }
     }
@@ -431,7 +461,7 @@ __global__ void __launch_bounds__(small_threads(NQ)) k_solve_small(
   if (reset) {
     if (s_read_later) {
       __syncthreads();
-      reset_S();
+      reset_S(tid, NT);
     }
     for (int q = tid; q < NP; q += NT) y[q] = 0.0;
   }
