@@ -447,27 +447,34 @@ __device__ bool factor_diag(LgShared& sm, const DiagPre& pre, float* A, float* L
   float* tk = tile_ptr(A, k, k);
   if (tid == 0) sm.bad = 0;
   __syncthreads();
-  if (tid < 2 * NB) {  // warps 0-3: the factor, its inverse and their writes
+  if (tid < 2 * NB) {  // warps 0-3: the factor and its inverse
     const bool ok = factor64(sm);
     if (!ok && tid == 0) sm.bad = 1;
     asm volatile("bar.sync 3, 128;" ::: "memory");
+    asm volatile("bar.arrive 4, 256;" ::: "memory");  // (the factor is complete: warps 4-7 store it)
     if (!sm.bad) {
       inverse64(sm, Linv + (size_t)k * TILE);
-      for (int t = tid; t < TILE; t += 2 * NB) {
-        const int r = t >> 6, c = t & 63;
-        tk[t] = c < r ? sm.X[r * LDX + c] : (c == r ? 1.f : 0.f);
-      }
       if (tid < NB) {
-        D[k * NB + tid] = sm.dd[tid];
-        invD[k * NB + tid] = sm.invd[tid];
         sm.dprev[tid] = sm.dd[tid];
         sm.iprev[tid] = sm.invd[tid];
       }
     }
   } else {
-    // meanwhile warps 4-7 fetch the next step's tiles (k+1, k) and (k+1, k+1)
+    // meanwhile warps 4-7 store the factor (tile (k, k), D, D^-1) once it is
+    // complete, then fetch the next step's tiles (k+1, k) and (k+1, k+1)
     // once the workers' updates through step k-1 are complete (those depend
     // only on work published before this step's factorisation)
+    asm volatile("bar.sync 4, 256;" ::: "memory");
+    if (!sm.bad) {
+      for (int t = tid - 2 * NB; t < TILE; t += 2 * NB) {
+        const int r = t >> 6, c = t & 63;
+        tk[t] = c < r ? sm.X[r * LDX + c] : (c == r ? 1.f : 0.f);
+      }
+      if (tid < 3 * NB) {
+        D[k * NB + tid - 2 * NB] = sm.dd[tid - 2 * NB];
+        invD[k * NB + tid - 2 * NB] = sm.invd[tid - 2 * NB];
+      }
+    }
     if (tid == 2 * NB) {
       int f = 0;
       if (k + 1 < T) {
@@ -817,26 +824,26 @@ __device__ __forceinline__ bool task_live(const LgProb* __restrict__ probs, unsi
   return false;
 }
 
-constexpr int ENV_THREADS = 1024;
+constexpr int ENV_THREADS = 256;
+constexpr int ENV_MAX_CTAS = 1024;  // CTAs of the envelope's bookkeeping (their counts live in the sync words)
 
-// The envelope's bookkeeping (one CTA, after k_lg_convert has found each tile
-// row's first nonzero tile): per system the envelope's tile offsets (the
-// products with S visit only its tiles) and the initial tile versions (a
-// tile (a,b) of the envelope receives the updates of steps
-// max(env_a, env_b) .. b-1 and starts at the first of them), then the tasks
-// of the dense list that touch the envelope, compacted in list order, their
-// count in live[ntasks].
+// The envelope's bookkeeping, in two launches over env_ctas CTAs (after
+// k_lg_convert has found each tile row's first nonzero tile).  First:
+// per system the envelope's tile offsets (the products with S visit only
+// its tiles; one warp per system) and the initial tile versions (a tile
+// (a,b) of the envelope receives the updates of steps max(env_a, env_b) ..
+// b-1 and starts at the first of them; one warp per tile row), and per CTA
+// the number of tasks of its share of the dense list that touch the
+// envelope (a contiguous share, in list order).
 __global__ void __launch_bounds__(ENV_THREADS) k_lg_envelope(const LgProb* __restrict__ probs, int nsys,
                                                              const int* __restrict__ rb_sys, int R,
                                                              const unsigned long long* __restrict__ tasks, int ntasks,
-                                                             unsigned long long* __restrict__ live, const int* status) {
-  __shared__ int wsum[ENV_THREADS / 32];
+                                                             int* __restrict__ counts, const int* status) {
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  if (dpv_status(status)) {
-    if (tid == 0) live[ntasks] = 0ull;
-    return;
-  }
-  for (int p = wid; p < nsys; p += ENV_THREADS / 32) {  // offsets: one warp per system
+  constexpr int NW = ENV_THREADS / 32;
+  if (dpv_status(status)) return;
+  const int gw = blockIdx.x * NW + wid, nw = gridDim.x * NW;  // this warp among all
+  for (int p = gw; p < nsys; p += nw) {  // offsets: one warp per system
     const LgProb& P = probs[p];
     int base = 0;
     for (int a0 = 0; a0 < P.T; a0 += 32) {
@@ -852,40 +859,67 @@ __global__ void __launch_bounds__(ENV_THREADS) k_lg_envelope(const LgProb* __res
     }
     if (lane == 0) P.eoff[0] = 0;
   }
-  for (int r = wid; r < R; r += ENV_THREADS / 32) {  // versions: one warp per tile row
+  for (int r = gw; r < R; r += nw) {  // versions: one warp per tile row
     const LgProb& P = probs[rb_sys[r]];
     const int a = r - P.rb0, ea = P.env[a];
     for (int b = ea + lane; b <= a; b += 32) P.ver[tri2(a) + b] = max(ea, P.env[b]);
   }
-  // compaction: each thread a contiguous share of the list
-  const int per = (ntasks + ENV_THREADS - 1) / ENV_THREADS;
-  const int t0 = min(ntasks, tid * per), t1 = min(ntasks, t0 + per);
+  const int per = (ntasks + gridDim.x - 1) / gridDim.x;
+  const int t0 = min(ntasks, (int)blockIdx.x * per), t1 = min(ntasks, t0 + per);
   int cnt = 0;
-  for (int t = t0; t < t1; ++t) cnt += task_live(probs, tasks[t]) ? 1 : 0;
-  int v = cnt;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int u = __shfl_up_sync(0xffffffffu, v, o);
-    if (lane >= o) v += u;
-  }
-  if (lane == 31) wsum[wid] = v;
+  for (int t = t0 + tid; t < t1; t += ENV_THREADS) cnt += task_live(probs, tasks[t]) ? 1 : 0;
+  cnt = __reduce_add_sync(0xffffffffu, cnt);
+  __shared__ int wsum[NW];
+  if (lane == 0) wsum[wid] = cnt;
   __syncthreads();
-  if (wid == 0) {
-    int x = wsum[lane];
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int u = __shfl_up_sync(0xffffffffu, x, o);
-      if (lane >= o) x += u;
+  if (tid == 0) {
+    int c = 0;
+    for (int w = 0; w < NW; ++w) c += wsum[w];
+    counts[blockIdx.x] = c;
+  }
+}
+
+// Second: each CTA writes the live tasks of its share, in list order, after
+// those of the CTAs before it; the last writes the count to live[ntasks].
+__global__ void __launch_bounds__(ENV_THREADS) k_lg_compact(const LgProb* __restrict__ probs,
+                                                            const unsigned long long* __restrict__ tasks, int ntasks,
+                                                            const int* __restrict__ counts,
+                                                            unsigned long long* __restrict__ live, const int* status) {
+  __shared__ int wsum[ENV_THREADS / 32 + 1];
+  __shared__ int base;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  constexpr int NW = ENV_THREADS / 32;
+  if (dpv_status(status)) {
+    if (blockIdx.x == 0 && tid == 0) live[ntasks] = 0ull;
+    return;
+  }
+  if (tid == 0) {
+    int b = 0;
+    for (int c = 0; c < (int)blockIdx.x; ++c) b += counts[c];
+    base = b;
+  }
+  __syncthreads();
+  const int per = (ntasks + gridDim.x - 1) / gridDim.x;
+  const int t0 = min(ntasks, (int)blockIdx.x * per), t1 = min(ntasks, t0 + per);
+  for (int r0 = t0; r0 < t1; r0 += ENV_THREADS) {
+    const int t = r0 + tid;
+    unsigned long long w = 0ull;
+    const bool lv = t < t1 && task_live(probs, w = tasks[t]);
+    const unsigned m = __ballot_sync(0xffffffffu, lv);
+    if (lane == 0) wsum[wid] = __popc(m);
+    __syncthreads();
+    int before = base;
+    for (int q = 0; q < wid; ++q) before += wsum[q];
+    if (lv) live[before + __popc(m & ((1u << lane) - 1u))] = w;
+    __syncthreads();
+    if (tid == 0) {
+      int c = 0;
+      for (int q = 0; q < NW; ++q) c += wsum[q];
+      base += c;
     }
-    wsum[lane] = x;
+    __syncthreads();
   }
-  __syncthreads();
-  int off = v - cnt + (wid ? wsum[wid - 1] : 0);
-  for (int t = t0; t < t1; ++t) {
-    const unsigned long long w = tasks[t];
-    if (task_live(probs, w)) live[off++] = w;
-  }
-  if (tid == ENV_THREADS - 1) live[ntasks] = (unsigned long long)off;
+  if (blockIdx.x == gridDim.x - 1 && tid == 0) live[ntasks] = (unsigned long long)base;
 }
 
 // The factorisation task graphs of all large systems.  CTA p < nsys runs the
@@ -2093,9 +2127,10 @@ ba_status_t lg_plan(ba_handle_t h, LgPlan& L) {
     L.tasks = it->second.first;
     L.ntasks = it->second.second;
   }
-  // sync words: per system tile versions; task counter, barrier,
-  // critical SMs, convergence maxima per (sweep, system)
-  L.nsync = L.soff_sync + 4 + nsys + 2LL * MAX_SWEEPS * nsys;
+  // sync words: per system tile versions, envelope and its offsets; task
+  // counter, barrier, critical SMs, convergence maxima per (sweep, system),
+  // the envelope compaction's counts
+  L.nsync = L.soff_sync + 4 + nsys + 2LL * MAX_SWEEPS * nsys + ENV_MAX_CTAS;
   ba_status_t s;
   if ((s = dpv_grow(h, ws->lg_sync, L.nsync, "large solver sync")) ||
       (s = dpv_grow(h, ws->lg_red, 2LL * MAX_SWEEPS * nsys, "large solver reductions")) ||
@@ -2210,8 +2245,14 @@ ba_status_t dpv_solve_large(ba_handle_t h, int refine) {
   ++h->launches;
   // the factorisation's live tasks and initial versions, the envelope offsets
   unsigned long long* live = ws->lg_live.p;
-  k_lg_envelope<<<1, ENV_THREADS, 0, st>>>(dprobs, nsys, ws->lg_rb.p, R, tasks, ntasks, live, status);
-  ++h->launches;
+  {
+    int* counts = sync + nsync - ENV_MAX_CTAS;
+    const int g = std::max(1, std::min({ENV_MAX_CTAS, h->num_sms, (ntasks + ENV_THREADS - 1) / ENV_THREADS}));
+    k_lg_envelope<<<g, ENV_THREADS, 0, st>>>(dprobs, nsys, ws->lg_rb.p, R, tasks, ntasks, counts, status);
+    ++h->launches;
+    k_lg_compact<<<g, ENV_THREADS, 0, st>>>(dprobs, tasks, ntasks, counts, live, status);
+    ++h->launches;
+  }
   long long timeout = h->opt.timeout_cycles;
   {
     // at most two CTAs per SM; the critical CTAs get their SMs to themselves
