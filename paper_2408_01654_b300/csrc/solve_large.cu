@@ -459,6 +459,13 @@ __device__ bool factor_diag(LgShared& sm, const DiagPre& pre, float* A, float* L
         sm.iprev[tid] = sm.invd[tid];
       }
     }
+    // tile (k, k) final once warps 4-7 have stored the factor too: released
+    // here, ahead of the next step's tiles
+    asm volatile("bar.sync 6, 256;" ::: "memory");
+    if (tid == 0 && !sm.bad) {
+      __threadfence();
+      st_release(ver + tri2(k) + k, k + 1);
+    }
   } else {
     // meanwhile warps 4-7 store the factor (tile (k, k), D, D^-1) once it is
     // complete, then fetch the next step's tiles (k+1, k) and (k+1, k+1)
@@ -475,6 +482,7 @@ __device__ bool factor_diag(LgShared& sm, const DiagPre& pre, float* A, float* L
         invD[k * NB + tid - 2 * NB] = sm.invd[tid - 2 * NB];
       }
     }
+    asm volatile("bar.arrive 6, 256;" ::: "memory");  // (the stores of the factor are issued)
     if (tid == 2 * NB) {
       int f = 0;
       if (k + 1 < T) {
@@ -976,11 +984,7 @@ __global__ void __launch_bounds__(LG_THREADS, 1) k_lg_factor(const LgProb* __res
         if (threadIdx.x == 0 && !dpv_status(status)) dpv_set_status(status, DST_NOT_SPD);
         goto done;
       }
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        __threadfence();
-        st_release(P.ver + tri2(k) + k, k + 1);
-      }
+      // (tile (k, k) was released inside the step)
     }
   }
   // Each CTA claims its next task while it works on the current one (the
