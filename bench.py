@@ -122,7 +122,7 @@ def parse():
         if a.workload in ("global", "loop400") and a.impl == "ours":
             a.steps = 20  # ~0.5 s of timed steps: several clock samples
         if a.workload == "diff16":
-            a.steps = 50 if a.impl == "ours" else 3
+            a.steps = 300 if a.impl == "ours" else 3  # (~0.5 s of timed steps: several clock samples)
         if a.workload == "correlation":
             a.steps = 3 if a.impl == "reference" else 200
         if a.workload == "pgo":

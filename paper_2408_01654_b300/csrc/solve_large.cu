@@ -1731,7 +1731,7 @@ struct ChainSlice {
   float2 m[8];
 };
 __device__ __forceinline__ ChainSlice load_slice(const float* M) {
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31, w = (threadIdx.x >> 5) & 7;  // (the warp within its group of 8)
   ChainSlice c;
 #pragma unroll
   for (int r = 0; r < 8; ++r) c.m[r] = __ldcg(reinterpret_cast<const float2*>(M + (8 * w + r) * NB) + lane);
@@ -1767,6 +1767,7 @@ __device__ __forceinline__ float reduce_rows8(const float (&s)[8]) {
 }
 
 constexpr int CH_MAX_T = 128;  // tile rows of a system whose chains run in a cluster (2 x 64 KB of tagged words)
+constexpr int CH_THREADS = 512;  // two groups of 8 warps: the two row blocks of a pair
 // The cluster form costs two launches per CG sweep instead of one kernel for
 // all sweeps; it pays where the chains are long (measured: 1000 keyframes,
 // 94 tile rows, 180 -> 130 us per sweep), not for the 64-problem batch
@@ -1782,7 +1783,7 @@ constexpr unsigned CH_TAG = 1;  // tag of a solved value (the copies are cleared
 // envelope its lanes read the two solved values they need from their
 // shared memory and multiply them into the slice of the chain matrix that
 // was loaded meanwhile.
-__global__ void __launch_bounds__(LG_THREADS) k_lg_chain(const LgProb* __restrict__ probs, int nsys, int sweep,
+__global__ void __launch_bounds__(CH_THREADS) k_lg_chain(const LgProb* __restrict__ probs, int nsys, int sweep,
                                                          const int* conv, double* red, float tol, int* status,
                                                          long long timeout) {
   // this CTA's copies of the forward and the backward vectors, tagged; each
@@ -1793,7 +1794,7 @@ __global__ void __launch_bounds__(LG_THREADS) k_lg_chain(const LgProb* __restric
   cgr::cluster_group cl = cgr::this_cluster();
   const int C = (int)cl.num_blocks(), rank = (int)cl.block_rank();
   const int sy = blockIdx.x / C;
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int tid = threadIdx.x, lane = tid & 31, wid = (tid >> 5) & 7, grp = tid >> 8;
   // (the same decision in every CTA of the cluster: the convergence words
   // are final; an error reported meanwhile ends the waits below)
   if (sy >= nsys || sys_finished(conv, nsys, sy, sweep - 1, tol)) return;
@@ -1801,7 +1802,7 @@ __global__ void __launch_bounds__(LG_THREADS) k_lg_chain(const LgProb* __restric
   const int T = P.T, E = __ldg(P.eoff + T);
   unsigned long long* xf = xs;           // forward values u
   unsigned long long* xb = xs + T * NB;  // backward values w
-  for (int q = tid; q < 2 * T * NB; q += LG_THREADS) xs[q] = 0ull;
+  for (int q = tid; q < 2 * T * NB; q += CH_THREADS) xs[q] = 0ull;
   cl.sync();  // every copy is cleared before any CTA stores into it
   const int row = 8 * wid + (lane >> 2);  // the row this lane reports after the reduction
   // (remote stores go to every CTA of the cluster, this one included: lanes
@@ -1809,13 +1810,19 @@ __global__ void __launch_bounds__(LG_THREADS) k_lg_chain(const LgProb* __restric
   auto publish = [&](unsigned long long* vec, int i, float v) {
     const unsigned long long w = ((unsigned long long)CH_TAG << 32) | __float_as_uint(v);
     for (int d = lane & 3; d < C; d += 4) {
-      unsigned long long* rx = cl.map_shared_rank(vec, (unsigned)d);
+      unsigned long long* rx = d == rank ? vec : cl.map_shared_rank(vec, (unsigned)d);
       reinterpret_cast<volatile unsigned long long*>(rx)[i * NB + row] = w;
     }
   };
+  // the row blocks come in pairs (2p, 2p+1) on cluster rank p mod C, one per
+  // group of 8 warps: the second block's dependency on the first stays in
+  // this CTA's shared memory
+  const int npairs = (T + 1) / 2;
   bool good = true;
-  // ---- forward: row blocks rank, rank + C, ...
-  for (int i = rank; i < T && good; i += C) {
+  // ---- forward: the pairs rank, rank + C, ...
+  for (int pp = rank; pp < npairs && good; pp += C) {
+    const int i = 2 * pp + grp;
+    if (i >= T) break;
     const int j0 = __ldg(P.env + i);
     const float* Nr = P.G + (size_t)(__ldg(P.eoff + i) - j0) * TILE;  // N_ij at Nr + j * TILE
     float s[8];
@@ -1854,8 +1861,10 @@ __global__ void __launch_bounds__(LG_THREADS) k_lg_chain(const LgProb* __restric
     publish(xf, i, v);
     if ((lane & 3) == 0) P.xf[i * NB + row] = v;
   }
-  // ---- backward: row blocks of this rank, descending
-  for (int i = rank + C * ((T - 1 - rank) / C); i >= 0 && rank < T && good; i -= C) {
+  // ---- backward: the pairs of this rank, descending
+  for (int pp = rank + C * ((npairs - 1 - rank) / C); pp >= 0 && rank < npairs && good; pp -= C) {
+    const int i = 2 * pp + grp;
+    if (i >= T) continue;
     float s[8];
     {
       const ChainSlice lt = load_slice(P.G + (size_t)(E + __ldg(P.eoff + i) + i - __ldg(P.env + i)) * TILE);
@@ -2025,7 +2034,7 @@ int chain_cluster(ba_handle_t h) {
     at[0].val.clusterDim.y = 1;
     at[0].val.clusterDim.z = 1;
     cfg.gridDim = dim3((unsigned)c);
-    cfg.blockDim = dim3(LG_THREADS);
+    cfg.blockDim = dim3(CH_THREADS);
     cfg.dynamicSmemBytes = (size_t)smem;
     cfg.stream = h->stream;
     cfg.attrs = at;
@@ -2310,7 +2319,7 @@ ba_status_t dpv_solve_large(ba_handle_t h, int refine) {
         at[0].val.clusterDim.y = 1;
         at[0].val.clusterDim.z = 1;
         cfg.gridDim = dim3((unsigned)(nsys * C));
-        cfg.blockDim = dim3(LG_THREADS);
+        cfg.blockDim = dim3(CH_THREADS);
         cfg.dynamicSmemBytes = 2 * sizeof(unsigned long long) * (size_t)maxT * NB;
         cfg.stream = st;
         cfg.attrs = at;
