@@ -1767,7 +1767,8 @@ __device__ __forceinline__ float reduce_rows8(const float (&s)[8]) {
 }
 
 constexpr int CH_MAX_T = 128;  // tile rows of a system whose chains run in a cluster (2 x 64 KB of tagged words)
-constexpr int CH_THREADS = 512;  // two groups of 8 warps: the two row blocks of a pair
+constexpr int CH_GROUPS = 3;                 // groups of 8 warps: consecutive row blocks of one CTA
+constexpr int CH_THREADS = 256 * CH_GROUPS;
 // The cluster form costs two launches per CG sweep instead of one kernel for
 // all sweeps; it pays where the chains are long (measured: 1000 keyframes,
 // 94 tile rows, 180 -> 130 us per sweep), not for the 64-problem batch
@@ -1814,14 +1815,14 @@ __global__ void __launch_bounds__(CH_THREADS) k_lg_chain(const LgProb* __restric
       reinterpret_cast<volatile unsigned long long*>(rx)[i * NB + row] = w;
     }
   };
-  // the row blocks come in pairs (2p, 2p+1) on cluster rank p mod C, one per
-  // group of 8 warps: the second block's dependency on the first stays in
-  // this CTA's shared memory
-  const int npairs = (T + 1) / 2;
+  // the row blocks come in runs of CH_GROUPS consecutive blocks (run p on
+  // cluster rank p mod C), one per group of 8 warps: the dependencies inside
+  // a run stay in this CTA's shared memory
+  const int nruns = (T + CH_GROUPS - 1) / CH_GROUPS;
   bool good = true;
-  // ---- forward: the pairs rank, rank + C, ...
-  for (int pp = rank; pp < npairs && good; pp += C) {
-    const int i = 2 * pp + grp;
+  // ---- forward: the runs rank, rank + C, ...
+  for (int pp = rank; pp < nruns && good; pp += C) {
+    const int i = CH_GROUPS * pp + grp;
     if (i >= T) break;
     const int j0 = __ldg(P.env + i);
     const float* Nr = P.G + (size_t)(__ldg(P.eoff + i) - j0) * TILE;  // N_ij at Nr + j * TILE
@@ -1861,9 +1862,9 @@ __global__ void __launch_bounds__(CH_THREADS) k_lg_chain(const LgProb* __restric
     publish(xf, i, v);
     if ((lane & 3) == 0) P.xf[i * NB + row] = v;
   }
-  // ---- backward: the pairs of this rank, descending
-  for (int pp = rank + C * ((npairs - 1 - rank) / C); pp >= 0 && rank < npairs && good; pp -= C) {
-    const int i = 2 * pp + grp;
+  // ---- backward: the runs of this rank, descending
+  for (int pp = rank + C * ((nruns - 1 - rank) / C); pp >= 0 && rank < nruns && good; pp -= C) {
+    const int i = CH_GROUPS * pp + grp;
     if (i >= T) continue;
     float s[8];
     {
