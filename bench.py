@@ -225,13 +225,46 @@ def envelopes(ba):
     return ba.envelope()
 
 
-def roofline(dom, prof, steps, bytes_fn, factor_envs, workload):
+def dominant_class(prof):
+    """The kernel class with the largest summed event time."""
+    return max((k for k in prof if prof[k][1] > 0), key=lambda k: prof[k][0])
+
+
+def time_dominant_only(ba, dom, step):
+    """From here on only the dominant class's launches are bracketed by event
+    records (the others keep their programmatic early launches inside the
+    captured step); two untimed steps re-capture the graph."""
+    ba.profile(True, classes=[dom])
+    for _ in range(2):
+        step()
+    ba.sync()
+
+
+def class_breakdown(ba, step, n):
+    """Event time per step of every kernel class, over n untimed steps with
+    every class between event records.  The records add a few microseconds at
+    each class boundary, so the sum exceeds the timed region's step time."""
+    ba.profile(True)
+    for _ in range(2):  # re-capture with every class recorded
+        step()
+    ba.profile(True)  # clears the re-capture's records
+    for _ in range(n):
+        step()
+    p = ba.profile_read()
+    ba.profile(False)
+    return {k: v[0] / n for k, v in p.items()}
+
+
+def roofline(dom, prof, steps, bytes_fn, factor_envs, workload, per_class=None):
     """Roofline object of the dominant kernel class: the persistent
     factorisation against the TF32 tensor peak, every other class against the
-    measured HBM copy bandwidth."""
+    measured HBM copy bandwidth.  prof[dom] holds the dominant class's event
+    time and launches over the timed region; per_class (ms per step of every
+    class) comes from a separate profiled pass when given."""
     t_ms, cnt = prof[dom]
     per_launch_s = t_ms / cnt / 1e3
-    per_class = {k: v[0] / steps for k, v in prof.items()}
+    if per_class is None:
+        per_class = {k: v[0] / steps for k, v in prof.items()}
     if dom == "factor":
         fl = factor_flops(factor_envs)
         peak, kind = tensor_peak_tf32()
@@ -903,14 +936,17 @@ def run_pgo(args):
     def call():
         ba.pgo_lm(T["S"], T["dS"], T["fa"], T["fb"], T["loop"], iters=iters, cost=cost, accepted=acc)
 
+    ba.profile(True)  # the warm-up records every kernel class: it picks the dominant one
     with torch.cuda.stream(stream):
         for _ in range(max(args.warmup, 3)):
             T["S"].copy_(S0)
             call()
     ba.sync()
+    dom = dominant_class(ba.profile_read())
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     launches0 = ba.info()["launches"]
+    ba.profile(True, classes=[dom])  # the timed region: event records around the dominant class only
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
@@ -926,6 +962,7 @@ def run_pgo(args):
         dist.barrier()
     ba.sync()
     launches = ba.info()["launches"] - launches0
+    prof = ba.profile_read()  # the dominant class over the timed region
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_ms = max_over_ranks(sum(step_ms), dev)
     value = job_throughput(args.steps * iters, world, total_ms)
@@ -939,7 +976,7 @@ def run_pgo(args):
             T["S"].copy_(S0)
             call()
     ba.sync()
-    prof = ba.profile_read()
+    per_class = {k: v[0] / args.steps for k, v in ba.profile_read().items()}
     ba.profile(False)
 
     # end to end: similarities and factors from pinned host memory, the
@@ -971,7 +1008,6 @@ def run_pgo(args):
         return 0
 
     n = 7 * (PGO_N - 1)
-    dom = max((k for k in prof if prof[k][1] > 0), key=lambda k: prof[k][0])
     F = len(g["fa"])
 
     def pgo_bytes(kind):
@@ -982,7 +1018,7 @@ def run_pgo(args):
             return 8 * tri + 64 * PGO_N * 3 + 76 * F
         return algorithmic_bytes(kind, PGO_N, 0, 0, n)
 
-    roof = roofline(dom, prof, args.steps, pgo_bytes, envelopes(ba), "pgo")
+    roof = roofline(dom, prof, args.steps, pgo_bytes, envelopes(ba), "pgo", per_class)
 
     parity = None
     cpu = None
@@ -1151,7 +1187,7 @@ def run_ours(args):
     if not args.no_autotune and args.group == 0:  # the group size, measured on this graph (untimed)
         tuning = ba.autotune(scene.iters, scene.fixed, reps=3)
     ba.set_capture(not args.no_capture)
-    ba.profile(True)  # before the warm-up: the replayed graph carries the event records
+    ba.profile(True)  # the warm-up records every kernel class: it picks the dominant one
 
     def reset():
         T["poses"].copy_(pristine["poses"])
@@ -1165,11 +1201,13 @@ def run_ours(args):
         reset()
         one_step()
     ba.sync()
+    dom = dominant_class(ba.profile_read())
+    time_dominant_only(ba, dom, lambda: (reset(), one_step()))
 
     # ---- timed region: per-step events, L2 flushed between steps ----------
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     launches0 = ba.info()["launches"]
-    ba.profile(True)
+    ba.profile(True, classes=[dom])
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
@@ -1193,6 +1231,7 @@ def run_ours(args):
     total_ms = max_over_ranks(total_ms, dev)  # the slowest rank's time
     gn_iters = world * args.steps * scene.iters
     value = job_throughput(args.steps * scene.iters, world, total_ms)
+    per_class = class_breakdown(ba, lambda: (reset(), flush.zero_(), one_step()), args.steps)
 
     # ---- end to end through the C ABI with host buffers -------------------
     # (no event records: the step runs as a user's would; the first steps
@@ -1250,10 +1289,9 @@ def run_ours(args):
     # ---- roofline of the dominant kernel ----------------------------------
     inf = ba.info()
     n = inf["n"]
-    dom = max((k for k in prof if prof[k][1] > 0), key=lambda k: prof[k][0])
     roof = roofline(dom, prof, args.steps, lambda k: algorithmic_bytes(k, scene.N, scene.P, scene.E, n,
                                                                  residual_pixels(args.workload)), envelopes(ba),
-                    args.workload)
+                    args.workload, per_class)
 
     # ---- error against the oracle and the CPU baseline --------------------
     err = None
@@ -1361,7 +1399,7 @@ def run_batched(args):
     if not args.no_autotune and args.group == 0:  # the group size, measured on this batch (untimed)
         tuning = ba.autotune(iters, fixed, reps=2)
     ba.set_capture(not args.no_capture)
-    ba.profile(True)  # before the warm-up: the replayed graph carries the event records
+    ba.profile(True)  # the warm-up records every kernel class: it picks the dominant one
 
     def reset():
         T["poses"].copy_(pristine["poses"])
@@ -1375,9 +1413,11 @@ def run_batched(args):
         reset()
         one_step()
     ba.sync()
+    dom = dominant_class(ba.profile_read())
+    time_dominant_only(ba, dom, lambda: (reset(), one_step()))
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     launches0 = ba.info()["launches"]
-    ba.profile(True)  # clears the warm-up's records
+    ba.profile(True, classes=[dom])  # clears the warm-up's records
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
@@ -1399,6 +1439,7 @@ def run_batched(args):
     replays = {"ba_step": ba.info()["graph_replays"], "binding": ba.info()["bind_replays"]}
     total_ms = max_over_ranks(total_ms, dev)  # the slowest rank's time
     value = job_throughput(args.steps * B * iters, world, total_ms)
+    per_class = class_breakdown(ba, lambda: (reset(), flush.zero_(), one_step()), args.steps)
 
     # the plain form: one FP32 handle per problem, problem after problem
     plain_T = [scene_tensors(sc, dev) for sc in probs]
@@ -1510,7 +1551,6 @@ def run_batched(args):
                          f"(-O2) in a process pool over {cores} host cores; {one_core:.2f} problem GN it/s on one "
                          f"core (the workers' own durations)"}
 
-    dom = max((k for k in prof if prof[k][1] > 0), key=lambda k: prof[k][0])
     t_ms, cnt = prof[dom]
     Nb = [sc.N for sc in probs]
     nb = [6 * (m - fixed) for m in Nb]
@@ -1524,7 +1564,7 @@ def run_batched(args):
             return 4 * tri_all + 16 * sum(nb) + 112 * sizes[0]
         return algorithmic_bytes(k, sizes[0], sizes[1], sizes[2], 0)
 
-    roof = roofline(dom, prof, args.steps, batch_bytes, envelopes(ba), "batched")
+    roof = roofline(dom, prof, args.steps, batch_bytes, envelopes(ba), "batched", per_class)
     line = {
         "metric": METRIC, "value": value, "unit": "problem GN it/s", "n_gpus": world, "steps": args.steps,
         "warmup": max(args.warmup, 3), "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -1539,7 +1579,7 @@ def run_batched(args):
         "batched_vs_plain": value / plain_value,
         "final_ground_truth_error": equal_error,
         "error_vs_oracle": err,
-        "per_class_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
+        "per_class_ms_per_step": per_class,
         "dominant_class": {"kind": dom, "avg_launch_us": t_ms / cnt * 1e3},
         "roofline": roof,
         "cpu_baseline": cpu,
@@ -1608,15 +1648,17 @@ def run_diff16(args):
     import ctypes
 
     from paper_2408_01654_b300 import capi
-    ba.profile(True)
+    ba.profile(True)  # the warm-up records every kernel class: it picks the dominant one
     for _ in range(max(args.warmup, 3)):
         reset()
         forward()
         backward()
     ba.sync()
+    dom = dominant_class(ba.profile_read())
+    time_dominant_only(ba, dom, lambda: (reset(), forward(), backward()))
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
     launches0 = ba.info()["launches"]
-    ba.profile(True)
+    ba.profile(True, classes=[dom])
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
@@ -1640,6 +1682,7 @@ def run_diff16(args):
     launches = ba.info()["launches"] - launches0
     total_ms = max_over_ranks(sum(step_ms), dev)
     value = job_throughput(args.steps * B * iters, world, total_ms)
+    per_class = class_breakdown(ba, lambda: (reset(), flush.zero_(), forward(), backward()), args.steps)
 
     # end to end: targets, weights, poses and patches from pinned host memory,
     # the final poses and depths and both gradients back
@@ -1710,8 +1753,7 @@ def run_diff16(args):
             return 32 * sizes[2] + 108 * sizes[1] + 56 * sizes[0]
         return algorithmic_bytes(k, sizes[0], sizes[1], sizes[2], 0)
 
-    dom = max((k for k in prof if prof[k][1] > 0), key=lambda k: prof[k][0])
-    roof = roofline(dom, prof, args.steps, diff_bytes, envelopes(ba), "diff16")
+    roof = roofline(dom, prof, args.steps, diff_bytes, envelopes(ba), "diff16", per_class)
     line = {
         "metric": METRIC + " (forward + reverse pass)", "value": value, "unit": "problem GN it/s", "n_gpus": world,
         "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": total_ms / args.steps,
@@ -1723,7 +1765,7 @@ def run_diff16(args):
                    "step": "ba_set_graph_batched + ba_set_record + ba_step + ba_backward"},
         "forward_ms_per_step": statistics.median(fwd_ms), "backward_ms_per_step": statistics.median(bwd_ms),
         "gradient_vs_oracle": grad,
-        "per_class_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
+        "per_class_ms_per_step": per_class,
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": "problem GN it/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},

@@ -315,6 +315,14 @@ enum {
  * kernel class above (and clear earlier records); on == 0: stop recording. */
 DPVBA_API ba_status_t ba_profile_enable(ba_handle_t h, int on);
 
+/* As ba_profile_enable, for the kernel classes whose bits are set in `mask`
+ * (bit k = the class BA_KERNEL_* numbered k above; 0 stops recording).
+ * Launches of the other classes run without event records, so a captured
+ * step keeps their programmatic (early-launch) dependencies; a changed mask
+ * re-captures the step's graph on the next call.  BA_ERR_INVALID_ARG for a
+ * bit at or above BA_KERNEL_CLASSES. */
+DPVBA_API ba_status_t ba_profile_classes(ba_handle_t h, unsigned mask);
+
 /* Synchronise, then report for kernel class `kind` the summed event time of
  * its recorded launches (*total_ms) and their number (*launches). */
 DPVBA_API ba_status_t ba_profile_read(ba_handle_t h, int kind, double* total_ms, long long* launches);

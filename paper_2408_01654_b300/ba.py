@@ -295,8 +295,16 @@ class DPVBA:
                                                        out.numel() * out.element_size()))
         return out
 
-    def profile(self, on: bool = True):
-        capi.check(self._h, self._lib.ba_profile_enable(self._h, 1 if on else 0))
+    def profile(self, on: bool = True, classes=None):
+        """Event records around every kernel class (on), none (off), or only
+        the named classes (`classes`: names from capi.KERNEL_CLASSES)."""
+        if classes is None:
+            capi.check(self._h, self._lib.ba_profile_enable(self._h, 1 if on else 0))
+            return
+        mask = 0
+        for name in classes:
+            mask |= 1 << capi.KERNEL_CLASSES.index(name)
+        capi.check(self._h, self._lib.ba_profile_classes(self._h, mask if on else 0))
 
     def profile_read(self) -> dict:
         """{kernel class: (total event ms, launches)} since profiling was enabled."""

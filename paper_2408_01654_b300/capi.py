@@ -43,7 +43,7 @@ EXPORTED = [
     "ba_default_options", "ba_create", "ba_destroy", "ba_set_stream", "ba_set_graph", "ba_set_graph_batched",
     "ba_step", "ba_sync",
     "ba_last_error", "ba_status_string", "ba_linearize", "ba_debug_export", "ba_debug_info", "ba_debug_keys", "ba_debug_envelope",
-    "ba_profile_enable", "ba_profile_read", "ba_set_record", "ba_backward", "ba_solve_pose_system_noalloc",
+    "ba_profile_enable", "ba_profile_classes", "ba_profile_read", "ba_set_record", "ba_backward", "ba_solve_pose_system_noalloc",
     "ba_set_capture", "ba_autotune", "ba_autotune_clear", "ba_proximity_edges", "ba_patch_correlation", "ba_pgo_lm",
 ]
 KERNEL_CLASSES = ("preprocess", "init", "assemble", "solve", "backsub", "retract", "adjoint", "factor",
@@ -88,6 +88,7 @@ def lib():
         L.ba_debug_envelope.argtypes = [H, ctypes.POINTER(ctypes.c_int), ctypes.c_longlong,
                                         ctypes.POINTER(ctypes.c_longlong)]
         L.ba_profile_enable.argtypes = [H, i]
+        L.ba_profile_classes.argtypes = [H, ctypes.c_uint]
         L.ba_profile_read.argtypes = [H, i, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]
         L.ba_set_record.argtypes = [H, i]
         L.ba_backward.argtypes = [H, P, P, P, P, P, P]

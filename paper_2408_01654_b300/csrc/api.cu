@@ -28,28 +28,47 @@ static cudaEvent_t pool_event(ba_handle_t h) {
   return e;
 }
 
-// While a step is captured, the pair becomes two event-record nodes of the
-// graph (every replay records them again; see prof_harvest).
+// Record e once the work enqueued so far on the handle's stream is done, on
+// the profiling side stream forked at this point: the next kernel on the
+// handle's stream keeps its programmatic dependency on the previous one (an
+// event record between them would serialise the pair).  While a step is
+// captured the record is an event-record node on a side branch of the graph
+// (every replay records it again; see prof_harvest).
+static void prof_record(ba_handle_t h, cudaEvent_t e) {
+  const unsigned flags = h->capturing ? cudaEventRecordExternal : 0u;
+  if (!h->prof_side || !h->prof_fork) {
+    cudaEventRecordWithFlags(e, h->stream, flags);
+    return;
+  }
+  cudaEventRecord(h->prof_fork, h->stream);
+  cudaStreamWaitEvent(h->prof_side, h->prof_fork, 0);
+  cudaEventRecordWithFlags(e, h->prof_side, flags);
+  if (h->capturing) h->prof_side_used = 1;
+}
+
 void dpv_prof_begin(ba_handle_t h, int kind) {
-  if (!h->prof_on) return;
+  if (!((h->prof_on >> kind) & 1)) return;
   cudaEvent_t a = pool_event(h), b = pool_event(h);
   if (!a || !b) return;
   std::vector<ba_handle_s::ProfRec>& list = h->capturing ? *h->cap_prof : h->prof;
-  if (h->capturing)
-    cudaEventRecordWithFlags(a, h->stream, cudaEventRecordExternal);
-  else
-    cudaEventRecord(a, h->stream);
+  prof_record(h, a);
   list.push_back({kind, a, b});
   h->prof_open = (int)list.size() - 1;
 }
 
 void dpv_prof_end(ba_handle_t h) {
   if (!h->prof_on || h->prof_open < 0) return;
-  if (h->capturing)
-    cudaEventRecordWithFlags((*h->cap_prof)[h->prof_open].b, h->stream, cudaEventRecordExternal);
-  else
-    cudaEventRecord(h->prof[h->prof_open].b, h->stream);
+  prof_record(h, h->capturing ? (*h->cap_prof)[h->prof_open].b : h->prof[h->prof_open].b);
   h->prof_open = -1;
+}
+
+// A capture that forked the profiling side stream joins it back into the
+// captured stream (a capture must end with every forked stream joined).
+void dpv_prof_join(ba_handle_t h) {
+  if (!h->prof_side_used) return;
+  cudaEventRecord(h->prof_fork, h->prof_side);
+  cudaStreamWaitEvent(h->stream, h->prof_fork, 0);
+  h->prof_side_used = 0;
 }
 
 static void prof_release(ba_handle_t h, std::vector<ba_handle_s::ProfRec>& list) {
@@ -139,7 +158,9 @@ static ba_status_t graph_run(ba_handle_t h, ba_handle_s::CapGraph& g, const ba_h
     if (e == cudaSuccess) {
       h->capturing = 1;
       h->cap_prof = &g.prof;
+      h->prof_side_used = 0;
       s = body();
+      dpv_prof_join(h);
       h->capturing = 0;
       h->cap_prof = nullptr;
       e = cudaStreamEndCapture(h->cap_stream, &gr);
@@ -218,16 +239,6 @@ int auto_group(ba_handle_t h, long long P, long long E, int batched) {
   if ((long long)P >= 32LL * 2 * h->num_sms) return 32;
   if ((long long)P >= 8LL * h->num_sms) return 16;
   return 8;
-}
-
-// One bound problem: every frame and group belongs to problem 0, the frame
-// offsets {0, N} follow the per-frame entries; clears the device status.
-__global__ void k_single_problem(int N, int* __restrict__ fprob, int Gn, int* __restrict__ gprob, int* status) {
-  const int q = blockIdx.x * blockDim.x + threadIdx.x;
-  if (q <= N) fprob[q] = 0;
-  if (q == N + 1) fprob[q] = N;
-  if (q < Gn) gprob[q] = 0;
-  if (q == 0) *status = 0;
 }
 
 // problem of index x for non-decreasing offsets off[0..B] (largest b with off[b] <= x)
@@ -487,6 +498,8 @@ ba_status_t ba_destroy(ba_handle_t h) {
   graph_drop(h, h->step_graph);
   graph_drop(h, h->bind_graph);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  if (h->prof_side) cudaStreamDestroy(h->prof_side);
+  if (h->prof_fork) cudaEventDestroy(h->prof_fork);
   for (int q = 0; q < 8; ++q) {
     if (h->side[q]) cudaStreamDestroy(h->side[q]);
     if (h->ev_join[q]) cudaEventDestroy(h->ev_join[q]);
@@ -498,14 +511,21 @@ ba_status_t ba_destroy(ba_handle_t h) {
   return BA_OK;
 }
 
-ba_status_t ba_profile_enable(ba_handle_t h, int on) {
-  if (!h) return BA_ERR_INVALID_ARG;
-  if (on) {
+ba_status_t ba_profile_classes(ba_handle_t h, unsigned mask) {
+  if (!h || (mask >> BA_KERNEL_CLASSES)) return BA_ERR_INVALID_ARG;
+  if (mask) {
     DPV_CUDA(h, cudaStreamSynchronize(h->stream));
+    if (h->prof_side) DPV_CUDA(h, cudaStreamSynchronize(h->prof_side));
     prof_clear(h);
+    if (!h->prof_side) DPV_CUDA(h, cudaStreamCreateWithFlags(&h->prof_side, cudaStreamNonBlocking));
+    if (!h->prof_fork) DPV_CUDA(h, cudaEventCreateWithFlags(&h->prof_fork, cudaEventDisableTiming));
   }
-  h->prof_on = on ? 1 : 0;
+  h->prof_on = (int)mask;
   return BA_OK;
+}
+
+ba_status_t ba_profile_enable(ba_handle_t h, int on) {
+  return ba_profile_classes(h, on ? (1u << BA_KERNEL_CLASSES) - 1u : 0u);
 }
 
 ba_status_t ba_set_capture(ba_handle_t h, int on) {
@@ -524,6 +544,7 @@ ba_status_t ba_set_capture(ba_handle_t h, int on) {
 ba_status_t ba_profile_read(ba_handle_t h, int kind, double* total_ms, long long* launches) {
   if (!h || !total_ms || !launches || kind < 0 || kind >= BA_KERNEL_CLASSES) return BA_ERR_INVALID_ARG;
   DPV_CUDA(h, cudaStreamSynchronize(h->stream));
+  if (h->prof_side) DPV_CUDA(h, cudaStreamSynchronize(h->prof_side));  // the eager records
   ba_status_t s = prof_harvest_all(h);
   if (s) return s;
   double t = h->prof_ms[kind];
@@ -588,9 +609,16 @@ ba_status_t ba_set_graph(ba_handle_t h, int N, int P, int E, double* poses, floa
   h->G = h->opt.patches_per_group > 0 ? h->opt.patches_per_group : auto_group(h, P, E, 0);
   h->ngroups = (P + h->G - 1) / h->G;
   if (!same_frames) h->fixed = -1;
+  // intrinsics in device memory are copied by the binding's first kernel (so
+  // the pointer joins the signature); host memory is copied outside any graph
+  cudaPointerAttributes pa = {};
+  const bool intr_dev = cudaPointerGetAttributes(&pa, intrinsics) == cudaSuccess &&
+                        (pa.type == cudaMemoryTypeDevice || pa.type == cudaMemoryTypeManaged);
+  cudaGetLastError();
   bind_signature(h, {1, N, P, E, (long long)(uintptr_t)poses, (long long)(uintptr_t)patches,
                      (long long)(uintptr_t)targets, (long long)(uintptr_t)weights, (long long)(uintptr_t)ii,
-                     (long long)(uintptr_t)jj, (long long)(uintptr_t)kk, h->G});
+                     (long long)(uintptr_t)jj, (long long)(uintptr_t)kk, h->G,
+                     intr_dev ? (long long)(uintptr_t)intrinsics : 0LL});
   h->tape_valid = 0;
   h->kk_bits = bits_for((unsigned long long)P);
   ba_status_t s;
@@ -611,15 +639,13 @@ ba_status_t ba_set_graph(ba_handle_t h, int N, int P, int E, double* poses, floa
       (s = dpv_grow(h, ws->pterm, dpv_pterm_width(h) * En, "edge depth terms")) || (s = dpv_grow(h, ws->posef, (long long)DPV_POSE_ROW * N, "pose table")) ||
       (s = dpv_grow(h, ws->fprob, (long long)N + 2, "frame problems")) || (s = dpv_grow(h, ws->gprob, Gn, "group problems")))
     return s;
-  // the intrinsics may live in host memory: copied outside any graph
-  DPV_CUDA(h, cudaMemcpyAsync(ws->intr, intrinsics, 4 * sizeof(float), cudaMemcpyDefault, h->stream));
+  if (!intr_dev)
+    DPV_CUDA(h, cudaMemcpyAsync(ws->intr, intrinsics, 4 * sizeof(float), cudaMemcpyDefault, h->stream));
   auto device_work = [&]() -> ba_status_t {
-    // one problem: every frame and group belongs to problem 0; frame_off = {0, N} follows fprob
-    const int M = std::max(N + 2, (int)Gn);
-    k_single_problem<<<(M + 255) / 256, 256, 0, h->stream>>>(N, ws->fprob.p, (int)Gn, ws->gprob.p, ws->status);
-    ++h->launches;
+    // one problem: every frame and group belongs to problem 0 (written by the
+    // preprocessing's first kernel, which also clears the device status)
     dpv_prof_begin(h, BA_KERNEL_PREPROCESS);
-    ba_status_t r = dpv_preprocess(h, ii, jj, kk);
+    ba_status_t r = dpv_preprocess(h, ii, jj, kk, 1, intr_dev ? intrinsics : nullptr);
     dpv_prof_end(h);
     return r;
   };
@@ -789,7 +815,7 @@ ba_status_t ba_set_graph_batched(ba_handle_t h, int B, const long long* frame_of
       ++h->launches;
     }
     dpv_prof_begin(h, BA_KERNEL_PREPROCESS);
-    ba_status_t r = dpv_preprocess(h, ws->mii.p, ws->mjj.p, ws->mkk.p);
+    ba_status_t r = dpv_preprocess(h, ws->mii.p, ws->mjj.p, ws->mkk.p, 0, nullptr);
     dpv_prof_end(h);
     return r;
   };
@@ -820,7 +846,7 @@ static ba_status_t step_body(ba_handle_t h, int run, int fixed_poses) {
                                                                                h->user_patches, h->ws->pcopy.p, 1);
     ++h->launches;
   }
-  if (run > 0) DPV_CUDA(h, cudaMemsetAsync(h->ws->cost, 0, sizeof(double) * h->ws->cost_cap, h->stream));
+  // the cost slots are cleared by the first iteration's k_init_system
   int prepared = 0;  // S, y and the pose table already set up by the previous iteration
   for (int it = 0; it < run; ++it) {
     if (h->record && (s = dpv_tape_state(h, it))) return s;

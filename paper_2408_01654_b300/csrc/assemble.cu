@@ -460,15 +460,17 @@ __global__ void __launch_bounds__(AS_THREADS) k_assemble(
 // this iteration (R and the camera centre as double-float pairs).  With
 // diag_pad > 0 (one system held in one tile of edge diag_pad) the diagonal is
 // written here as well: lambda_p on the first diag_n entries, 1 on the
-// padding; otherwise k_init_diag follows.
+// padding; otherwise k_init_diag follows.  The first iteration of a step also
+// clears the step's ncost cost slots (cost_zero).
 __global__ void k_init_system(double* __restrict__ S, size_t nS, double* __restrict__ y, int nv,
                               const double* __restrict__ y_init, const double* __restrict__ poses, int N,
                               float* __restrict__ posef, int diag_n, int diag_pad, float lambda_p,
-                              const int* status) {
+                              double* __restrict__ cost_zero, int ncost, const int* status) {
   dpv_pdl_enter();
   if (dpv_status(status)) return;
   const size_t stride = (size_t)gridDim.x * blockDim.x;
   const size_t gid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (cost_zero && gid < (size_t)ncost) cost_zero[gid] = 0.0;
   if (gid < (size_t)N) dpv_pose_table_row(poses + 7 * gid, posef + DPV_POSE_ROW * gid);
   double2* S2 = reinterpret_cast<double2*>(S);
   const size_t dstep = (size_t)diag_pad + 1;
@@ -550,9 +552,12 @@ ba_status_t assemble_impl(ba_handle_t h, int it, const double* v_ext, const floa
     dpv_prof_begin(h, BA_KERNEL_INIT);
     // one system in one tile: its diagonal is written by the same launch
     const bool one_tile = h->sys.size() == 1 && h->sys[0].T == 1 && h->sys[0].soff == 0;
+    // the first iteration of a forward step clears the step's cost slots
+    const bool zero_cost = it == 0 && !v_ext && !w_ext;
     DPV_CUDA(h, dpv_launch_pdl(k_init_system, dim3(2 * h->num_sms), dim3(256), 0, h->stream, ws->S.p, nS, ws->y.p,
                                h->n_pad, v_ext, (const double*)h->poses, h->N, ws->posef.p,
                                one_tile ? h->sys[0].n : 0, one_tile ? h->sys[0].n_pad : 0, h->opt.lambda_pose,
+                               zero_cost ? ws->cost : (double*)nullptr, (int)ws->cost_cap,
                                (const int*)ws->status));
     ++h->launches;
     if (!one_tile) {

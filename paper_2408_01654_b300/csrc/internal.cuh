@@ -90,7 +90,8 @@ struct ba_handle_s {
 
   Workspace* ws = nullptr;
 
-  // event timing of kernel classes (ba_profile_enable)
+  // event timing of kernel classes (ba_profile_enable, ba_profile_classes):
+  // bit k set = launches of class k are bracketed by an event pair; 0 = off
   int prof_on = 0;
   struct ProfRec {
     int kind;
@@ -99,6 +100,11 @@ struct ba_handle_s {
   std::vector<ProfRec> prof;
   std::vector<cudaEvent_t> ev_pool;
   int prof_open = -1;
+  // the records go on a side stream forked at each record point, so that the
+  // kernels keep their programmatic dependencies on one another
+  cudaStream_t prof_side = nullptr;
+  cudaEvent_t prof_fork = nullptr;
+  int prof_side_used = 0;  // a capture forked the side stream: join it before the capture ends
 
   long long launches = 0;  // kernels launched by this handle so far
   // side streams: the one-CTA solver launches of different block counts run
@@ -269,9 +275,11 @@ int dpv_tuned_group(ba_handle_t h, long long P, long long E, int batched);
 // event timing around a kernel class (no-ops unless profiling is enabled)
 void dpv_prof_begin(ba_handle_t h, int kind);
 void dpv_prof_end(ba_handle_t h);
+void dpv_prof_join(ba_handle_t h);
 
 // preprocessing (preprocess.cu)
-ba_status_t dpv_preprocess(ba_handle_t h, const int* ii, const int* jj, const int* kk);
+ba_status_t dpv_preprocess(ba_handle_t h, const int* ii, const int* jj, const int* kk, int single,
+                           const float* intr_src);
 ba_status_t dpv_block_keys(ba_handle_t h, int fixed, int* keys_out, int cap, int* n_out);
 // out has n+1 entries; when run_if is given the kernels do nothing unless *run_if != 0
 ba_status_t dpv_exclusive_scan(ba_handle_t h, const int* in, int* out, int n, const int* run_if = nullptr);

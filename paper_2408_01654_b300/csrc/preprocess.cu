@@ -13,9 +13,14 @@
 //     (source frame, target frame) pair is one contiguous "run"; the run
 //     table is per group (at most DPV_RMAX runs), so no global scan is needed.
 // The resulting edge order is the stable sort by (group, ii, jj, kk).
+// A graph whose groups and 256-edge blocks fit in one co-resident wave (an
+// odometry window) is bound by two launches: k_bind_init, then k_bind with
+// the steps above as phases between grid barriers; larger graphs take one
+// launch per step at full occupancy.
 #include "internal.cuh"
 
 #include <algorithm>
+#include <map>
 
 namespace {
 
@@ -115,11 +120,12 @@ __global__ void k_scan_down(const int* __restrict__ in, int n, const int* __rest
 // ---------------------------------------------------------------------------
 // validation and sort keys
 // ---------------------------------------------------------------------------
-__global__ void k_validate(int E, int N, int P, const int* __restrict__ ii, const int* __restrict__ jj,
-                           const int* __restrict__ kk, int* __restrict__ src, unsigned long long* __restrict__ keys,
-                           int* __restrict__ vals, int* __restrict__ unsorted, int* status) {
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= E) return;
+// Edge e: its sort key (kk) and value (e), the "kk not non-decreasing" flag,
+// index checks, and the patch's source frame (every edge of patch k must
+// leave the same frame i; src[] holds -1 on entry).
+__device__ void validate_edge(int e, int E, int N, int P, const int* __restrict__ ii, const int* __restrict__ jj,
+                              const int* __restrict__ kk, int* __restrict__ src, unsigned long long* __restrict__ keys,
+                              int* __restrict__ vals, int* __restrict__ unsorted, int* status) {
   const int i = ii[e], j = jj[e], k = kk[e];
   vals[e] = e;
   keys[e] = (unsigned)k;
@@ -234,21 +240,19 @@ __device__ bool rs_grid_barrier(int* bar, int* status, long long timeout) {
   return ok != 0;
 }
 
-// The whole stable LSD radix sort (8-bit digits, the low `bits` bits) in one
-// cooperative launch: per pass the tiles' histograms, the exclusive scan of
-// the histogram (tile sums, the sums' scan in CTA 0, down-sweep) and the
-// stable scatter, separated by grid barriers; CTAs stride over tiles.  Exits
-// at once when run_if is given and *run_if is 0 (an input already in order),
-// so that a sorted input costs one launch.  scratch: hist [256 nb], offs
-// [256 nb + 1], sums [ns + 1].
-__global__ void __launch_bounds__(RS_THREADS) k_radix_sort(unsigned long long* k0, int* v0, unsigned long long* k1,
-                                                           int* v1, int M, int bits, int* scratch, int* bar,
-                                                           const int* run_if, int* status, long long timeout) {
-  __shared__ int cnt[256];
-  __shared__ int wcnt[RS_THREADS / 32][256];
-  __shared__ int sh[32];
-  if (run_if && !*run_if) return;
-  if (dpv_status(status)) return;
+// The passes of the stable LSD radix sort (8-bit digits, the low `bits` bits)
+// inside a cooperative launch: per pass the tiles' histograms, the exclusive
+// scan of the histogram (tile sums, the sums' scan in CTA 0, down-sweep) and
+// the stable scatter, separated by grid barriers; CTAs stride over tiles.
+// scratch: hist [256 nb], offs [256 nb + 1], sums [ns + 1].  Returns false
+// when a barrier gave up (status set).
+struct RsShared {
+  int cnt[256];
+  int wcnt[RS_THREADS / 32][256];
+};
+
+__device__ bool rs_passes(unsigned long long* k0, int* v0, unsigned long long* k1, int* v1, int M, int bits,
+                          int* scratch, int* bar, int* status, long long timeout, RsShared& rs, int* sh) {
   const int nb = (M + RS_TILE - 1) / RS_TILE;
   const int nh = 256 * nb;
   const int ns = (nh + RS_SCAN_TILE - 1) / RS_SCAN_TILE;
@@ -258,8 +262,8 @@ __global__ void __launch_bounds__(RS_THREADS) k_radix_sort(unsigned long long* k
   unsigned long long *kin = k0, *kout = k1;
   int *vin = v0, *vout = v1;
   for (int shift = 0; shift < bits; shift += 8) {
-    for (int t = blockIdx.x; t < nb; t += gridDim.x) rs_hist_tile(kin, M, shift, hist, nb, t, cnt);
-    if (!rs_grid_barrier(bar, status, timeout)) return;
+    for (int t = blockIdx.x; t < nb; t += gridDim.x) rs_hist_tile(kin, M, shift, hist, nb, t, rs.cnt);
+    if (!rs_grid_barrier(bar, status, timeout)) return false;
     // tile sums of the histogram
     for (int t = blockIdx.x; t < ns; t += gridDim.x) {
       int v = 0;
@@ -272,7 +276,7 @@ __global__ void __launch_bounds__(RS_THREADS) k_radix_sort(unsigned long long* k
       block_exclusive_scan(v, sh, total);
       if (threadIdx.x == 0) sums[t] = total;
     }
-    if (!rs_grid_barrier(bar, status, timeout)) return;
+    if (!rs_grid_barrier(bar, status, timeout)) return false;
     if (blockIdx.x == 0) {
       const int per = (ns + RS_THREADS - 1) / RS_THREADS;
       const int lo = threadIdx.x * per, hi = min(ns, lo + per);
@@ -286,7 +290,7 @@ __global__ void __launch_bounds__(RS_THREADS) k_radix_sort(unsigned long long* k
         run += x;
       }
     }
-    if (!rs_grid_barrier(bar, status, timeout)) return;
+    if (!rs_grid_barrier(bar, status, timeout)) return false;
     // down-sweep: offs = exclusive scan of hist
     for (int t = blockIdx.x; t < ns; t += gridDim.x) {
       const int base = t * RS_SCAN_TILE + threadIdx.x * RS_SCAN_ITEMS;
@@ -304,10 +308,10 @@ __global__ void __launch_bounds__(RS_THREADS) k_radix_sort(unsigned long long* k
         run += v[r];
       }
     }
-    if (!rs_grid_barrier(bar, status, timeout)) return;
+    if (!rs_grid_barrier(bar, status, timeout)) return false;
     for (int t = blockIdx.x; t < nb; t += gridDim.x)
-      rs_scatter_tile(kin, vin, kout, vout, M, shift, offs, nb, t, cnt, wcnt);
-    if (!rs_grid_barrier(bar, status, timeout)) return;
+      rs_scatter_tile(kin, vin, kout, vout, M, shift, offs, nb, t, rs.cnt, rs.wcnt);
+    if (!rs_grid_barrier(bar, status, timeout)) return false;
     unsigned long long* tk = kin;
     kin = kout;
     kout = tk;
@@ -315,6 +319,20 @@ __global__ void __launch_bounds__(RS_THREADS) k_radix_sort(unsigned long long* k
     vin = vout;
     vout = tv;
   }
+  return true;
+}
+
+// The whole sort in one cooperative launch.  Exits at once when run_if is
+// given and *run_if is 0 (an input already in order), so that a sorted input
+// costs one launch.
+__global__ void __launch_bounds__(RS_THREADS) k_radix_sort(unsigned long long* k0, int* v0, unsigned long long* k1,
+                                                           int* v1, int M, int bits, int* scratch, int* bar,
+                                                           const int* run_if, int* status, long long timeout) {
+  __shared__ RsShared rs;
+  __shared__ int sh[32];
+  if (run_if && !*run_if) return;
+  if (dpv_status(status)) return;
+  rs_passes(k0, v0, k1, v1, M, bits, scratch, bar, status, timeout, rs, sh);
 }
 
 // ---------------------------------------------------------------------------
@@ -322,15 +340,12 @@ __global__ void __launch_bounds__(RS_THREADS) k_radix_sort(unsigned long long* k
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ int pm_edge(int s, const int* perm0, int unsorted) { return unsorted ? perm0[s] : s; }
 
-__global__ void k_bounds(int E, int P, int G, int ngroups, const int* __restrict__ kk, const int* __restrict__ perm0,
-                         const int* __restrict__ unsorted_p, int* __restrict__ gptr, int* __restrict__ pptr,
-                         const int* status) {
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= E || dpv_status(status)) return;
-  const int uns = *unsorted_p;
+// Position s of the patch-major order: the patches (kp, k] and the groups
+// that start there begin at s (kp = the previous position's patch).
+__device__ void bounds_edge(int s, int E, int P, int G, int ngroups, const int* __restrict__ kk,
+                            const int* __restrict__ perm0, int uns, int* __restrict__ gptr, int* __restrict__ pptr) {
   const int k = kk[pm_edge(s, perm0, uns)];
   const int kp = s ? kk[pm_edge(s - 1, perm0, uns)] : -1;
-  // patches (kp, k] start at s; groups likewise
   for (int q = kp + 1; q <= k; ++q) pptr[q] = s;
   for (int q = (kp < 0 ? 0 : kp / G + 1); q <= k / G; ++q)
     if (kp < 0 || q * G > kp) gptr[q] = s;
@@ -345,24 +360,28 @@ __global__ void k_bounds(int E, int P, int G, int ngroups, const int* __restrict
 // ---------------------------------------------------------------------------
 constexpr int NBUCKET = DPV_WMAX * DPV_WMAX;
 
-__global__ void __launch_bounds__(256) k_group_build(
-    int N, int G, const int* __restrict__ gptr, const int* __restrict__ perm0, const int* __restrict__ unsorted_p,
-    const int* __restrict__ ii, const int* __restrict__ jj, const int* __restrict__ kk, int* __restrict__ win,
-    int* __restrict__ wlen, int* __restrict__ perm, unsigned* __restrict__ eslot, int* __restrict__ pmpos,
-    int* __restrict__ grun, int* __restrict__ gnr, int* status) {
-  extern __shared__ unsigned smw[];
-  __shared__ int sh[32];
-  __shared__ int boff[NBUCKET];
-  __shared__ int bcnt[NBUCKET];
+struct GbShared {
+  int boff[NBUCKET];
+  int bcnt[NBUCKET];
+};
+
+// Group g by one CTA of 256 threads: the window (frames touched, as a bitmap
+// over N frames and its prefix counts in smw), the (source slot, target slot)
+// bucket counts, the run table and the stable placement of the group's edges
+// into bucket order.  Returns false (status set) when the window or the run
+// count is too large; the result is uniform over the CTA.
+__device__ bool group_build_one(int g, int N, int G, const int* __restrict__ gptr, const int* __restrict__ perm0,
+                                int uns, const int* __restrict__ ii, const int* __restrict__ jj,
+                                const int* __restrict__ kk, int* __restrict__ win, int* __restrict__ wlen,
+                                int* __restrict__ perm, unsigned* __restrict__ eslot, int* __restrict__ pmpos,
+                                int* __restrict__ grun, int* __restrict__ gnr, int* status, unsigned* smw,
+                                GbShared& gb, int* sh) {
   const int nwords = (N + 31) >> 5;
   unsigned* bm = smw;
   int* wpre = (int*)(smw + nwords);
-  const int g = blockIdx.x;
-  if (dpv_status(status)) return;
-  const int uns = *unsorted_p;
   const int s0 = gptr[g], s1 = gptr[g + 1];
   for (int q = threadIdx.x; q < nwords; q += blockDim.x) bm[q] = 0u;
-  for (int q = threadIdx.x; q < NBUCKET; q += blockDim.x) bcnt[q] = 0;
+  for (int q = threadIdx.x; q < NBUCKET; q += blockDim.x) gb.bcnt[q] = 0;
   __syncthreads();
   for (int s = s0 + threadIdx.x; s < s1; s += blockDim.x) {
     const int e = pm_edge(s, perm0, uns);
@@ -387,7 +406,7 @@ __global__ void __launch_bounds__(256) k_group_build(
       wlen[g] = total;
       dpv_set_status(status, DST_WIDE);
     }
-    return;
+    return false;
   }
   for (int q = threadIdx.x; q < nwords; q += blockDim.x) {
     unsigned word = bm[q];
@@ -406,7 +425,7 @@ __global__ void __launch_bounds__(256) k_group_build(
     const int i = ii[e], j = jj[e];
     const int si = wpre[i >> 5] + __popc(bm[i >> 5] & ((1u << (i & 31)) - 1u));
     const int sj = wpre[j >> 5] + __popc(bm[j >> 5] & ((1u << (j & 31)) - 1u));
-    atomicAdd(&bcnt[si * DPV_WMAX + sj], 1);
+    atomicAdd(&gb.bcnt[si * DPV_WMAX + sj], 1);
   }
   __syncthreads();
   // offsets of the buckets and the run table (non-empty buckets, in order)
@@ -415,7 +434,7 @@ __global__ void __launch_bounds__(256) k_group_build(
     int v[PER], cnt = 0, nz = 0;
 #pragma unroll
     for (int r = 0; r < PER; ++r) {
-      v[r] = bcnt[PER * threadIdx.x + r];
+      v[r] = gb.bcnt[PER * threadIdx.x + r];
       cnt += v[r];
       nz += v[r] > 0;
     }
@@ -425,12 +444,12 @@ __global__ void __launch_bounds__(256) k_group_build(
     int rid = block_exclusive_scan(nz, sh, rtot);
     if (rtot > DPV_RMAX) {
       if (threadIdx.x == 0) dpv_set_status(status, DST_WIDE);
-      return;
+      return false;
     }
     int* gr = grun + (size_t)g * (DPV_RMAX + 1);
 #pragma unroll
     for (int r = 0; r < PER; ++r) {
-      boff[PER * threadIdx.x + r] = off;
+      gb.boff[PER * threadIdx.x + r] = off;
       if (v[r] > 0) gr[rid++] = off;
       off += v[r];
     }
@@ -457,7 +476,7 @@ __global__ void __launch_bounds__(256) k_group_build(
       }
       const unsigned peers = __match_any_sync(0xffffffffu, bucket);
       const int rank = __popc(peers & lt);
-      const int base = valid ? boff[bucket] : 0;
+      const int base = valid ? gb.boff[bucket] : 0;
       if (valid) {
         const int pos = s0 + base + rank;
         perm[pos] = e;
@@ -465,10 +484,122 @@ __global__ void __launch_bounds__(256) k_group_build(
         pmpos[pos] = s;
       }
       __syncwarp();
-      if (valid && rank == 0) boff[bucket] = base + __popc(peers);
+      if (valid && rank == 0) gb.boff[bucket] = base + __popc(peers);
       __syncwarp();
     }
   }
+  __syncthreads();  // the next group of this CTA reuses the shared arrays
+  return true;
+}
+
+// The binding as separate launches (graphs too large for one co-resident
+// wave of the fused kernel): validation, the sort (k_radix_sort), the CSR
+// bounds, then one CTA per group.
+__global__ void k_validate(int E, int N, int P, const int* __restrict__ ii, const int* __restrict__ jj,
+                           const int* __restrict__ kk, int* __restrict__ src, unsigned long long* __restrict__ keys,
+                           int* __restrict__ vals, int* __restrict__ unsorted, int* status) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < E) validate_edge(e, E, N, P, ii, jj, kk, src, keys, vals, unsorted, status);
+}
+
+__global__ void k_bounds(int E, int P, int G, int ngroups, const int* __restrict__ kk, const int* __restrict__ perm0,
+                         const int* __restrict__ unsorted_p, int* __restrict__ gptr, int* __restrict__ pptr,
+                         const int* status) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= E || dpv_status(status)) return;
+  bounds_edge(s, E, P, G, ngroups, kk, perm0, *unsorted_p, gptr, pptr);
+}
+
+__global__ void __launch_bounds__(256) k_group_build(
+    int N, int G, const int* __restrict__ gptr, const int* __restrict__ perm0, const int* __restrict__ unsorted_p,
+    const int* __restrict__ ii, const int* __restrict__ jj, const int* __restrict__ kk, int* __restrict__ win,
+    int* __restrict__ wlen, int* __restrict__ perm, unsigned* __restrict__ eslot, int* __restrict__ pmpos,
+    int* __restrict__ grun, int* __restrict__ gnr, int* status) {
+  extern __shared__ unsigned smw[];
+  __shared__ GbShared gb;
+  __shared__ int sh[32];
+  __shared__ int flag;
+  if (threadIdx.x == 0) flag = dpv_status(status);
+  __syncthreads();
+  if (flag) return;
+  group_build_one(blockIdx.x, N, G, gptr, perm0, *unsorted_p, ii, jj, kk, win, wlen, perm, eslot, pmpos, grun, gnr,
+                  status, smw, gb, sh);
+}
+
+// The device status as one value for the whole CTA.
+__device__ int cta_status(const int* status, int* flag) {
+  __syncthreads();
+  if (threadIdx.x == 0) *flag = dpv_status(status);
+  __syncthreads();
+  return *flag;
+}
+
+// What the binding's fused kernel accumulates into, cleared: the patch
+// source table (-1), the "kk unsorted" flag and the grid barrier's words; for
+// one bound problem also the frame and group problem tables (every frame and
+// group in problem 0, the frame offsets {0, N} after the per-frame entries)
+// and the device status, and the four intrinsics when intr_src (device
+// memory) is given.
+__global__ void k_bind_init(int P, int* __restrict__ src, int* __restrict__ unsorted, int* __restrict__ bar,
+                            int single, int N, int* __restrict__ fprob, int Gn, int* __restrict__ gprob, int* status,
+                            const float* __restrict__ intr_src, float* __restrict__ intr) {
+  const int stride = gridDim.x * blockDim.x;
+  const int q0 = blockIdx.x * blockDim.x + threadIdx.x;
+  if (intr_src && q0 < 4) intr[q0] = intr_src[q0];
+  for (int q = q0; q < P; q += stride) src[q] = -1;
+  if (q0 == 0) {
+    *unsorted = 0;
+    bar[0] = 0;
+    bar[1] = 0;
+  }
+  if (!single) return;
+  for (int q = q0; q <= N + 1; q += stride) fprob[q] = q <= N ? 0 : N;
+  for (int q = q0; q < Gn; q += stride) gprob[q] = 0;
+  if (q0 == 0) *status = 0;
+}
+
+// The whole binding of E > 0 edges in one cooperative launch of 256-thread
+// CTAs, its phases separated by bounded grid barriers: validation and sort
+// keys; the stable sort by kk (only when the input is not kk-sorted; its
+// result is in (k1, v1) after an odd number of 8-bit passes); the group and
+// patch CSR (gptr, pptr); then every group's window, runs and edge order (CTAs
+// stride over the groups).  k_bind_init runs first.  A failed phase leaves
+// its code in the status and the later phases undone.  The sort's barriers
+// take the handle's budget; the two between the phases stand where kernel
+// boundaries stood, so they keep a floor of ~0.05 s (BIND_WAIT_MIN cycles):
+// a short budget meant for the solvers' waits does not fail a binding.
+constexpr long long BIND_WAIT_MIN = 100000000LL;
+
+__global__ void __launch_bounds__(256) k_bind(int E, int N, int P, int G, int ngroups, const int* __restrict__ ii,
+                                              const int* __restrict__ jj, const int* __restrict__ kk, int* src,
+                                              unsigned long long* k0, int* v0, unsigned long long* k1, int* v1,
+                                              int bits, int* scratch, int* bar, int* unsorted, int* gptr, int* pptr,
+                                              int* win, int* wlen, int* perm, unsigned* eslot, int* pmpos, int* grun,
+                                              int* gnr, int* status, long long timeout) {
+  extern __shared__ unsigned smw[];
+  __shared__ union {
+    RsShared rs;
+    GbShared gb;
+  } u;
+  __shared__ int sh[32];
+  __shared__ int flag;
+  const int stride = gridDim.x * blockDim.x;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < E; e += stride)
+    validate_edge(e, E, N, P, ii, jj, kk, src, k0, v0, unsorted, status);
+  const long long phase_timeout = timeout > BIND_WAIT_MIN ? timeout : BIND_WAIT_MIN;
+  if (!rs_grid_barrier(bar, status, phase_timeout) || cta_status(status, &flag)) return;
+  const int uns = *(volatile int*)unsorted;  // final after the barrier
+  if (uns && E > 1) {
+    if (!rs_passes(k0, v0, k1, v1, E, bits, scratch, bar, status, timeout, u.rs, sh)) return;
+  }
+  const int* perm0 = ((bits + 7) / 8) & 1 ? v1 : v0;
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < E; s += stride)
+    bounds_edge(s, E, P, G, ngroups, kk, perm0, uns, gptr, pptr);
+  if (!rs_grid_barrier(bar, status, phase_timeout) || cta_status(status, &flag)) return;
+  for (int g = blockIdx.x; g < ngroups; g += gridDim.x)
+    if (!group_build_one(g, N, G, gptr, perm0, uns, ii, jj, kk, win, wlen, perm, eslot, pmpos, grun, gnr, status,
+                         smw, u.gb, sh))
+      return;
 }
 
 // block keys (inspection): three candidate keys per sorted edge, invalid ->
@@ -547,6 +678,30 @@ ba_status_t radix_sort(ba_handle_t h, unsigned long long* k0, int* v0, unsigned 
   return BA_OK;
 }
 
+// Co-resident k_bind CTAs per SM for `smem` bytes of dynamic shared memory,
+// cached per size (the kernel's limit only ever rises): queried by the eager
+// first run of a binding, so a later capture of the same binding finds it.
+int bind_ctas_per_sm(size_t smem) {
+  static std::map<size_t, int> cache;
+  static size_t raised = 0;
+  auto it = cache.find(smem);
+  if (it != cache.end()) return it->second;
+  if (smem > raised) {
+    if (cudaFuncSetAttribute(k_bind, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+      cudaGetLastError();
+      return 0;
+    }
+    raised = smem;
+  }
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bind, 256, smem) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  cache[smem] = per_sm;
+  return per_sm;
+}
+
 }  // namespace
 
 long long dpv_scan_scratch(long long n) { return (n + SCAN_TILE - 1) / SCAN_TILE + 2; }
@@ -574,20 +729,39 @@ ba_status_t dpv_exclusive_scan(ba_handle_t h, const int* in, int* out, int n, co
   return BA_OK;
 }
 
-ba_status_t dpv_preprocess(ba_handle_t h, const int* ii, const int* jj, const int* kk) {
+ba_status_t dpv_preprocess(ba_handle_t h, const int* ii, const int* jj, const int* kk, int single,
+                           const float* intr_src) {
   Workspace* ws = h->ws;
   const int E = h->E, N = h->N, P = h->P, G = h->G;
   cudaStream_t st = h->stream;
-  DPV_CUDA(h, cudaMemsetAsync(ws->src.p, 0xff, sizeof(int) * P, st));
-  DPV_CUDA(h, cudaMemsetAsync(ws->unsorted, 0, sizeof(int), st));
+  const long long En = std::max(E, 1);
+  int* bar = ws->hist.p + dpv_hist_entries(En) - 2;
+  const int Gn = h->ngroups + 1;
+  const int M = std::max(std::max(P, N + 2), Gn);
+  k_bind_init<<<std::min((M + 255) / 256, 4 * h->num_sms), 256, 0, st>>>(P, ws->src.p, ws->unsorted, bar, single, N,
+                                                                         ws->fprob.p, Gn, ws->gprob.p, ws->status,
+                                                                         intr_src, ws->intr);
+  ++h->launches;
   if (E == 0) {
     DPV_CUDA(h, cudaMemsetAsync(ws->gptr.p, 0, sizeof(int) * (h->ngroups + 1), st));
     DPV_CUDA(h, cudaMemsetAsync(ws->pptr.p, 0, sizeof(int) * (P + 1), st));
-  } else {
+    DPV_CUDA(h, cudaMemsetAsync(ws->gnr.p, 0, sizeof(int) * h->ngroups, st));
+    DPV_CUDA(h, cudaMemsetAsync(ws->wlen.p, 0, sizeof(int) * h->ngroups, st));
+    DPV_CUDA(h, cudaGetLastError());
+    return BA_OK;
+  }
+  const int nwords = (N + 31) / 32;
+  const size_t smem = sizeof(unsigned) * nwords + sizeof(int) * nwords;
+  if (smem > 160 * 1024) return dpv_fail(h, BA_ERR_UNSUPPORTED, "too many frames for the window kernel");
+  const int per_sm = bind_ctas_per_sm(smem);
+  if (per_sm < 1) return dpv_fail(h, BA_ERR_CUDA, "binding kernel occupancy");
+  const int want = std::max(std::max((E + 255) / 256, h->ngroups), (E + RS_TILE - 1) / RS_TILE);
+  if (want > per_sm * h->num_sms) {
+    // more groups or edge blocks than one co-resident wave: separate launches
+    // at full occupancy (the fused kernel would loop at a quarter of it)
     k_validate<<<(E + 255) / 256, 256, 0, st>>>(E, N, P, ii, jj, kk, ws->src.p, ws->keys0.p, ws->vals0.p,
                                                  ws->unsorted, ws->status);
     ++h->launches;
-    // stable sort by kk, only when the input is not kk-sorted
     int which = 0;
     ba_status_t s = radix_sort(h, ws->keys0.p, ws->vals0.p, ws->keys1.p, ws->vals1.p, E, h->kk_bits, ws->hist.p,
                                which, ws->unsorted);
@@ -596,9 +770,6 @@ ba_status_t dpv_preprocess(ba_handle_t h, const int* ii, const int* jj, const in
     k_bounds<<<(E + 255) / 256, 256, 0, st>>>(E, P, G, h->ngroups, kk, perm0, ws->unsorted, ws->gptr.p, ws->pptr.p,
                                                ws->status);
     ++h->launches;
-    const int nwords = (N + 31) / 32;
-    const size_t smem = sizeof(unsigned) * nwords + sizeof(int) * nwords;
-    if (smem > 160 * 1024) return dpv_fail(h, BA_ERR_UNSUPPORTED, "too many frames for the window kernel");
     static size_t smem_set = 0;  // raised once (not inside a graph capture of a later binding)
     if (smem > smem_set) {
       DPV_CUDA(h, cudaFuncSetAttribute(k_group_build, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -608,11 +779,32 @@ ba_status_t dpv_preprocess(ba_handle_t h, const int* ii, const int* jj, const in
                                                  ws->wlen.p, ws->perm.p, ws->eslot.p, ws->pmpos.p, ws->grun.p,
                                                  ws->gnr.p, ws->status);
     ++h->launches;
+    DPV_CUDA(h, cudaGetLastError());
+    return BA_OK;
   }
-  if (E == 0) {
-    DPV_CUDA(h, cudaMemsetAsync(ws->gnr.p, 0, sizeof(int) * h->ngroups, st));
-    DPV_CUDA(h, cudaMemsetAsync(ws->wlen.p, 0, sizeof(int) * h->ngroups, st));
-  }
+  const int grid = want;  // one wave: every group and edge block has its own CTA
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(256);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int bits = h->kk_bits, ngroups = h->ngroups;
+  long long timeout = h->opt.timeout_cycles;
+  int* scratch = ws->hist.p;
+  void* args[] = {(void*)&E,          (void*)&N,          (void*)&P,          (void*)&G,
+                  (void*)&ngroups,    (void*)&ii,         (void*)&jj,         (void*)&kk,
+                  (void*)&ws->src.p,  (void*)&ws->keys0.p, (void*)&ws->vals0.p, (void*)&ws->keys1.p,
+                  (void*)&ws->vals1.p, (void*)&bits,      (void*)&scratch,    (void*)&bar,
+                  (void*)&ws->unsorted, (void*)&ws->gptr.p, (void*)&ws->pptr.p, (void*)&ws->win.p,
+                  (void*)&ws->wlen.p, (void*)&ws->perm.p, (void*)&ws->eslot.p, (void*)&ws->pmpos.p,
+                  (void*)&ws->grun.p, (void*)&ws->gnr.p,  (void*)&ws->status, (void*)&timeout};
+  DPV_CUDA(h, cudaLaunchKernelExC(&cfg, (const void*)k_bind, args));
+  ++h->launches;
   DPV_CUDA(h, cudaGetLastError());
   return BA_OK;
 }

@@ -161,6 +161,30 @@ def test_capture_profiling_reads_every_replay():
     assert prof["solve"][0] > 0 and prof["assemble"][0] > 0 and prof["preprocess"][0] > 0
 
 
+def test_profile_classes_records_only_the_chosen_class():
+    s = scenes.odometry(seed=0)
+    T = scene_tensors(s)
+    pristine = {k: v.clone() for k, v in T.items()}
+    g = DPVBA(capture=True)
+    g.profile(True, classes=["solve"])
+    run_calls(g, T, pristine, 5, s.iters, s.fixed)
+    prof = g.profile_read()
+    assert prof["solve"][1] == 5 * s.iters and prof["solve"][0] > 0, prof
+    assert all(v == (0.0, 0) for k, v in prof.items() if k != "solve"), prof
+    # switching to every class re-captures the step: the replays record all classes again
+    g.profile(True)
+    run_calls(g, T, pristine, 4, s.iters, s.fixed)
+    prof = g.profile_read()
+    assert prof["backsub"][1] == 4 * s.iters and prof["preprocess"][1] == 4, prof
+    # the poses after the masked replays match an unprofiled handle's
+    T2 = {k: v.clone() for k, v in pristine.items()}
+    ref = DPVBA(capture=True)
+    run_calls(ref, T2, pristine, 1, s.iters, s.fixed)
+    close(T, T2)
+    # a bit beyond the last class is refused
+    assert g._lib.ba_profile_classes(g._h, 1 << len(capi.KERNEL_CLASSES)) == capi.BA_ERR_INVALID_ARG
+
+
 def test_autotune_keeps_state_and_fills_table():
     s = scenes.odometry(seed=0)
     T = scene_tensors(s)

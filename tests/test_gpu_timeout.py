@@ -37,7 +37,8 @@ def sized(frames):
 
 def test_factorisation_wait_runs_out_and_state_is_kept():
     s = sized(60)  # 348 unknowns: the persistent tiled factorisation
-    assert np.all(np.diff(s.kk) >= 0)  # kk-sorted: the binding's sort (the only other wait) is skipped
+    # kk-sorted: the binding's sort is skipped; its two other grid barriers keep a ~0.05 s floor
+    assert np.all(np.diff(s.kk) >= 0)
     T = scene_tensors(s)
     p0, t0 = T["poses"].clone(), T["patches"].clone()
     ba = DPVBA(precision="mixed", timeout_cycles=2000)
