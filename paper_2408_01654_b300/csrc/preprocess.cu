@@ -359,10 +359,12 @@ __device__ void bounds_edge(int s, int E, int P, int G, int ngroups, const int* 
 // per group: window, slots, counting sort into (source, target) runs
 // ---------------------------------------------------------------------------
 constexpr int NBUCKET = DPV_WMAX * DPV_WMAX;
+constexpr int GB_EDGES = 2048;  // a group of at most this many edges keeps their slots in shared memory
 
 struct GbShared {
   int boff[NBUCKET];
   int bcnt[NBUCKET];
+  unsigned slot[GB_EDGES];  // packed (source slot, target slot, patch in group) per edge, group order
 };
 
 // Group g by one CTA of 256 threads: the window (frames touched, as a bitmap
@@ -419,13 +421,16 @@ __device__ bool group_build_one(int g, int N, int G, const int* __restrict__ gpt
   }
   for (int q = total + threadIdx.x; q < DPV_WMAX; q += blockDim.x) win[g * DPV_WMAX + q] = -1;
   if (threadIdx.x == 0) wlen[g] = total;
-  // bucket counts by (source slot, target slot)
+  // bucket counts by (source slot, target slot); the packed slots kept for the
+  // placement below when the group is small enough
+  const bool keep = s1 - s0 <= GB_EDGES;
   for (int s = s0 + threadIdx.x; s < s1; s += blockDim.x) {
     const int e = pm_edge(s, perm0, uns);
     const int i = ii[e], j = jj[e];
     const int si = wpre[i >> 5] + __popc(bm[i >> 5] & ((1u << (i & 31)) - 1u));
     const int sj = wpre[j >> 5] + __popc(bm[j >> 5] & ((1u << (j & 31)) - 1u));
     atomicAdd(&gb.bcnt[si * DPV_WMAX + sj], 1);
+    if (keep) gb.slot[s - s0] = dpv_pack_slot(si, sj, kk[e] % G);
   }
   __syncthreads();
   // offsets of the buckets and the run table (non-empty buckets, in order)
@@ -459,20 +464,28 @@ __device__ bool group_build_one(int g, int N, int G, const int* __restrict__ gpt
     }
   }
   __syncthreads();
-  // stable placement (one warp walks the group in patch-major order)
+  // stable placement (one warp walks the group in patch-major order; from
+  // the kept slots when there are, so the serial walk reads no global memory
+  // for a kk-sorted input)
   if (threadIdx.x < 32) {
     const int lane = threadIdx.x;
     const unsigned lt = (1u << lane) - 1u;
     for (int b = s0; b < s1; b += 32) {
       const int s = b + lane;
       const bool valid = s < s1;
-      int bucket = NBUCKET, e = 0, si = 0, sj = 0;
+      int bucket = NBUCKET, e = 0;
+      unsigned slot = 0u;
       if (valid) {
         e = pm_edge(s, perm0, uns);
-        const int i = ii[e], j = jj[e];
-        si = wpre[i >> 5] + __popc(bm[i >> 5] & ((1u << (i & 31)) - 1u));
-        sj = wpre[j >> 5] + __popc(bm[j >> 5] & ((1u << (j & 31)) - 1u));
-        bucket = si * DPV_WMAX + sj;
+        if (keep) {
+          slot = gb.slot[s - s0];
+        } else {
+          const int i = ii[e], j = jj[e];
+          const int si = wpre[i >> 5] + __popc(bm[i >> 5] & ((1u << (i & 31)) - 1u));
+          const int sj = wpre[j >> 5] + __popc(bm[j >> 5] & ((1u << (j & 31)) - 1u));
+          slot = dpv_pack_slot(si, sj, kk[e] % G);
+        }
+        bucket = dpv_slot_i(slot) * DPV_WMAX + dpv_slot_j(slot);
       }
       const unsigned peers = __match_any_sync(0xffffffffu, bucket);
       const int rank = __popc(peers & lt);
@@ -480,7 +493,7 @@ __device__ bool group_build_one(int g, int N, int G, const int* __restrict__ gpt
       if (valid) {
         const int pos = s0 + base + rank;
         perm[pos] = e;
-        eslot[pos] = dpv_pack_slot(si, sj, kk[e] % G);
+        eslot[pos] = slot;
         pmpos[pos] = s;
       }
       __syncwarp();
