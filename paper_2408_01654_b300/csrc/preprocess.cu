@@ -355,23 +355,48 @@ __device__ void bounds_edge(int s, int E, int P, int G, int ngroups, const int* 
   }
 }
 
+// bounds_edge on the input order, before it is known whether the input needs
+// the kk sort: for a kk-sorted input it writes exactly what bounds_edge
+// writes.  It skips positions with an invalid patch index (validation reports
+// it) or a descending one (an unsorted input: bounds_edge runs again after
+// the sort), and flags with bit 2 of *flag the positions that would write
+// more than BOUNDS_SPAN entries (long runs of patches without edges), for
+// the exact pass.
+constexpr int BOUNDS_SPAN = 256;
+__device__ void spec_bounds_edge(int s, int E, int P, int G, int ngroups, const int* __restrict__ kk,
+                                 int* __restrict__ gptr, int* __restrict__ pptr, int* flag) {
+  const int k = kk[s];
+  const int kp = s ? kk[s - 1] : -1;
+  if (k < 0 || k >= P || kp < -1 || kp >= P || kp > k) return;
+  const int tail = s == E - 1 ? P - k : 0;
+  if (k - kp > BOUNDS_SPAN || tail > BOUNDS_SPAN) {
+    atomicOr(flag, 2);
+    return;
+  }
+  bounds_edge(s, E, P, G, ngroups, kk, nullptr, 0, gptr, pptr);
+}
+
 // ---------------------------------------------------------------------------
 // per group: window, slots, counting sort into (source, target) runs
 // ---------------------------------------------------------------------------
 constexpr int NBUCKET = DPV_WMAX * DPV_WMAX;
-constexpr int GB_EDGES = 2048;  // a group of at most this many edges keeps their slots in shared memory
+constexpr int GB_EDGES = 2048;  // a group of at most this many edges keeps them in shared memory
+constexpr int GB_CNT_BITS = 18;  // the packed bucket scan: edge counts below, non-empty buckets above
 
 struct GbShared {
-  int boff[NBUCKET];
-  int bcnt[NBUCKET];
-  unsigned slot[GB_EDGES];  // packed (source slot, target slot, patch in group) per edge, group order
+  int bk[NBUCKET];          // bucket counts, then (scanned in place) each bucket's next position
+  unsigned slot[GB_EDGES];  // per edge (group order): its frames (16 bits each), then its packed slot
+  unsigned char kl[GB_EDGES];  // per edge: its patch within the group
 };
 
 // Group g by one CTA of 256 threads: the window (frames touched, as a bitmap
 // over N frames and its prefix counts in smw), the (source slot, target slot)
-// bucket counts, the run table and the stable placement of the group's edges
-// into bucket order.  Returns false (status set) when the window or the run
-// count is too large; the result is uniform over the CTA.
+// bucket counts over the window's W x W buckets, the run table and the stable
+// placement of the group's edges into bucket order.  A group of at most
+// GB_EDGES edges over at most 65,536 frames keeps its edges' frames and
+// slots in shared memory, so that the edges are read from global memory once
+// and the serial placement reads none.  Returns false (status set) when the
+// window or the run count is too large; the result is uniform over the CTA.
 __device__ bool group_build_one(int g, int N, int G, const int* __restrict__ gptr, const int* __restrict__ perm0,
                                 int uns, const int* __restrict__ ii, const int* __restrict__ jj,
                                 const int* __restrict__ kk, int* __restrict__ win, int* __restrict__ wlen,
@@ -382,27 +407,47 @@ __device__ bool group_build_one(int g, int N, int G, const int* __restrict__ gpt
   unsigned* bm = smw;
   int* wpre = (int*)(smw + nwords);
   const int s0 = gptr[g], s1 = gptr[g + 1];
+  const bool keep = s1 - s0 <= GB_EDGES && N <= 65536;
   for (int q = threadIdx.x; q < nwords; q += blockDim.x) bm[q] = 0u;
-  for (int q = threadIdx.x; q < NBUCKET; q += blockDim.x) gb.bcnt[q] = 0;
   __syncthreads();
   for (int s = s0 + threadIdx.x; s < s1; s += blockDim.x) {
     const int e = pm_edge(s, perm0, uns);
     const int i = ii[e], j = jj[e];
     atomicOr(&bm[i >> 5], 1u << (i & 31));
     atomicOr(&bm[j >> 5], 1u << (j & 31));
+    if (keep) {
+      gb.slot[s - s0] = ((unsigned)i << 16) | (unsigned)j;
+      gb.kl[s - s0] = (unsigned char)(kk[e] % G);
+    }
   }
   __syncthreads();
-  const int per = (nwords + blockDim.x - 1) / blockDim.x;
-  const int lo = threadIdx.x * per, hi = min(nwords, lo + per);
-  int c = 0;
-  for (int q = lo; q < hi; ++q) c += __popc(bm[q]);
+  // the window: prefix counts of the bitmap words (one warp when they fit)
   int total;
-  int run = block_exclusive_scan(c, sh, total);
-  for (int q = lo; q < hi; ++q) {
-    wpre[q] = run;
-    run += __popc(bm[q]);
+  if (nwords <= 32) {
+    if (threadIdx.x < 32) {
+      const int c = threadIdx.x < nwords ? __popc(bm[threadIdx.x]) : 0;
+      int x = c;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if ((int)threadIdx.x >= o) x += y;
+      }
+      if ((int)threadIdx.x < nwords) wpre[threadIdx.x] = x - c;
+      if (threadIdx.x == 31) sh[0] = x;
+    }
+    __syncthreads();
+    total = sh[0];
+  } else {
+    const int per = (nwords + blockDim.x - 1) / blockDim.x;
+    const int lo = threadIdx.x * per, hi = min(nwords, lo + per);
+    int c = 0;
+    for (int q = lo; q < hi; ++q) c += __popc(bm[q]);
+    int run = block_exclusive_scan(c, sh, total);
+    for (int q = lo; q < hi; ++q) {
+      wpre[q] = run;
+      run += __popc(bm[q]);
+    }
   }
-  __syncthreads();
   if (total > DPV_WMAX) {
     if (threadIdx.x == 0) {
       wlen[g] = total;
@@ -410,6 +455,9 @@ __device__ bool group_build_one(int g, int N, int G, const int* __restrict__ gpt
     }
     return false;
   }
+  const int W = total, W2 = W * W;
+  for (int q = threadIdx.x; q < W2; q += blockDim.x) gb.bk[q] = 0;
+  __syncthreads();  // wpre complete, the buckets cleared, sh free again
   for (int q = threadIdx.x; q < nwords; q += blockDim.x) {
     unsigned word = bm[q];
     int slot = wpre[q];
@@ -419,34 +467,52 @@ __device__ bool group_build_one(int g, int N, int G, const int* __restrict__ gpt
       word &= word - 1;
     }
   }
-  for (int q = total + threadIdx.x; q < DPV_WMAX; q += blockDim.x) win[g * DPV_WMAX + q] = -1;
-  if (threadIdx.x == 0) wlen[g] = total;
-  // bucket counts by (source slot, target slot); the packed slots kept for the
-  // placement below when the group is small enough
-  const bool keep = s1 - s0 <= GB_EDGES;
+  for (int q = W + threadIdx.x; q < DPV_WMAX; q += blockDim.x) win[g * DPV_WMAX + q] = -1;
+  if (threadIdx.x == 0) wlen[g] = W;
+  // bucket counts by (source slot, target slot); the packed slots kept
   for (int s = s0 + threadIdx.x; s < s1; s += blockDim.x) {
-    const int e = pm_edge(s, perm0, uns);
-    const int i = ii[e], j = jj[e];
+    int i, j, k;
+    if (keep) {
+      const unsigned f = gb.slot[s - s0];
+      i = (int)(f >> 16);
+      j = (int)(f & 0xffffu);
+      k = gb.kl[s - s0];
+    } else {
+      const int e = pm_edge(s, perm0, uns);
+      i = ii[e];
+      j = jj[e];
+      k = kk[e] % G;
+    }
     const int si = wpre[i >> 5] + __popc(bm[i >> 5] & ((1u << (i & 31)) - 1u));
     const int sj = wpre[j >> 5] + __popc(bm[j >> 5] & ((1u << (j & 31)) - 1u));
-    atomicAdd(&gb.bcnt[si * DPV_WMAX + sj], 1);
-    if (keep) gb.slot[s - s0] = dpv_pack_slot(si, sj, kk[e] % G);
+    atomicAdd(&gb.bk[si * W + sj], 1);
+    if (keep) gb.slot[s - s0] = dpv_pack_slot(si, sj, k);
   }
   __syncthreads();
-  // offsets of the buckets and the run table (non-empty buckets, in order)
+  // positions of the buckets (in place) and the run table (non-empty
+  // buckets, in order): thread t owns buckets 16t .. 16t + 15 of the W^2
   {
     constexpr int PER = NBUCKET / 256;
     int v[PER], cnt = 0, nz = 0;
 #pragma unroll
     for (int r = 0; r < PER; ++r) {
-      v[r] = gb.bcnt[PER * threadIdx.x + r];
+      const int q = PER * threadIdx.x + r;
+      v[r] = q < W2 ? gb.bk[q] : 0;
       cnt += v[r];
       nz += v[r] > 0;
     }
-    int tot;
-    int off = block_exclusive_scan(cnt, sh, tot);
-    int rtot;
-    int rid = block_exclusive_scan(nz, sh, rtot);
+    int off, rid, tot, rtot;
+    if (s1 - s0 < (1 << GB_CNT_BITS)) {  // one scan of (runs, edges) packed
+      int t2;
+      const int x = block_exclusive_scan((nz << GB_CNT_BITS) | cnt, sh, t2);
+      off = x & ((1 << GB_CNT_BITS) - 1);
+      rid = x >> GB_CNT_BITS;
+      tot = t2 & ((1 << GB_CNT_BITS) - 1);
+      rtot = t2 >> GB_CNT_BITS;
+    } else {
+      off = block_exclusive_scan(cnt, sh, tot);
+      rid = block_exclusive_scan(nz, sh, rtot);
+    }
     if (rtot > DPV_RMAX) {
       if (threadIdx.x == 0) dpv_set_status(status, DST_WIDE);
       return false;
@@ -454,7 +520,8 @@ __device__ bool group_build_one(int g, int N, int G, const int* __restrict__ gpt
     int* gr = grun + (size_t)g * (DPV_RMAX + 1);
 #pragma unroll
     for (int r = 0; r < PER; ++r) {
-      gb.boff[PER * threadIdx.x + r] = off;
+      const int q = PER * threadIdx.x + r;
+      if (q < W2) gb.bk[q] = off;
       if (v[r] > 0) gr[rid++] = off;
       off += v[r];
     }
@@ -485,11 +552,11 @@ __device__ bool group_build_one(int g, int N, int G, const int* __restrict__ gpt
           const int sj = wpre[j >> 5] + __popc(bm[j >> 5] & ((1u << (j & 31)) - 1u));
           slot = dpv_pack_slot(si, sj, kk[e] % G);
         }
-        bucket = dpv_slot_i(slot) * DPV_WMAX + dpv_slot_j(slot);
+        bucket = dpv_slot_i(slot) * W + dpv_slot_j(slot);
       }
       const unsigned peers = __match_any_sync(0xffffffffu, bucket);
       const int rank = __popc(peers & lt);
-      const int base = valid ? gb.boff[bucket] : 0;
+      const int base = valid ? gb.bk[bucket] : 0;
       if (valid) {
         const int pos = s0 + base + rank;
         perm[pos] = e;
@@ -497,7 +564,7 @@ __device__ bool group_build_one(int g, int N, int G, const int* __restrict__ gpt
         pmpos[pos] = s;
       }
       __syncwarp();
-      if (valid && rank == 0) gb.boff[bucket] = base + __popc(peers);
+      if (valid && rank == 0) gb.bk[bucket] = base + __popc(peers);
       __syncwarp();
     }
   }
@@ -573,10 +640,11 @@ __global__ void k_bind_init(int P, int* __restrict__ src, int* __restrict__ unso
 
 // The whole binding of E > 0 edges in one cooperative launch of 256-thread
 // CTAs, its phases separated by bounded grid barriers: validation and sort
-// keys; the stable sort by kk (only when the input is not kk-sorted; its
-// result is in (k1, v1) after an odd number of 8-bit passes); the group and
-// patch CSR (gptr, pptr); then every group's window, runs and edge order (CTAs
-// stride over the groups).  k_bind_init runs first.  A failed phase leaves
+// keys, with the group and patch CSR (gptr, pptr) written speculatively in
+// input order; the stable sort by kk (only when the input is not kk-sorted;
+// its result is in (k1, v1) after an odd number of 8-bit passes) and the
+// exact CSR (only for an unsorted input or a flagged long gap); then every
+// group's window, runs and edge order (CTAs stride over the groups).  k_bind_init runs first.  A failed phase leaves
 // its code in the status and the later phases undone.  The sort's barriers
 // take the handle's budget; the two between the phases stand where kernel
 // boundaries stood, so they keep a floor of ~0.05 s (BIND_WAIT_MIN cycles):
@@ -597,18 +665,23 @@ __global__ void __launch_bounds__(256) k_bind(int E, int N, int P, int G, int ng
   __shared__ int sh[32];
   __shared__ int flag;
   const int stride = gridDim.x * blockDim.x;
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < E; e += stride)
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < E; e += stride) {
     validate_edge(e, E, N, P, ii, jj, kk, src, k0, v0, unsorted, status);
+    spec_bounds_edge(e, E, P, G, ngroups, kk, gptr, pptr, unsorted);
+  }
   const long long phase_timeout = timeout > BIND_WAIT_MIN ? timeout : BIND_WAIT_MIN;
   if (!rs_grid_barrier(bar, status, phase_timeout) || cta_status(status, &flag)) return;
-  const int uns = *(volatile int*)unsorted;  // final after the barrier
+  const int fl = *(volatile int*)unsorted;  // final after the barrier
+  const int uns = fl & 1;
   if (uns && E > 1) {
     if (!rs_passes(k0, v0, k1, v1, E, bits, scratch, bar, status, timeout, u.rs, sh)) return;
   }
   const int* perm0 = ((bits + 7) / 8) & 1 ? v1 : v0;
-  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < E; s += stride)
-    bounds_edge(s, E, P, G, ngroups, kk, perm0, uns, gptr, pptr);
-  if (!rs_grid_barrier(bar, status, phase_timeout) || cta_status(status, &flag)) return;
+  if (fl) {  // unsorted, or a long run of patches without edges: the exact bounds
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < E; s += stride)
+      bounds_edge(s, E, P, G, ngroups, kk, perm0, uns, gptr, pptr);
+    if (!rs_grid_barrier(bar, status, phase_timeout) || cta_status(status, &flag)) return;
+  }
   for (int g = blockIdx.x; g < ngroups; g += gridDim.x)
     if (!group_build_one(g, N, G, gptr, perm0, uns, ii, jj, kk, win, wlen, perm, eslot, pmpos, grun, gnr, status,
                          smw, u.gb, sh))

@@ -6,6 +6,8 @@ max(1, |t|)); graph indexing is compared bit-exactly against its definition.
 All inputs come from the seeded scene generator; nothing here reads values
 produced by the CUDA path into the oracle.
 """
+import copy
+
 import numpy as np
 import pytest
 from scipy.spatial.transform import Rotation
@@ -293,6 +295,28 @@ def test_ragged_groups_self_edges_and_patches_without_edges():
         assert rot < TOL and tr < TOL and dep < TOL, (G, rot, tr, dep)
         dd = ba.export(capi.EXPORT_DD).cpu().numpy()
         assert np.all(dd[np.setdiff1d(np.arange(P), s.kk)] == 0)
+
+
+def test_long_runs_of_patches_without_edges():
+    # runs of 300 patches without edges at the start, in the middle and at the
+    # end: longer than the span the fused binding writes speculatively, so it
+    # takes its exact CSR pass (sorted input) or the sort's (shuffled)
+    s = scenes.tiny(seed=3)
+    gap, half = 300, s.P // 2
+    old = s.kk.copy()
+    s.kk = (old + gap + np.where(old >= half, gap, 0)).astype(np.int32)
+    filler = np.repeat(s.patches[:1], gap, axis=0)
+    s.patches = np.concatenate([filler, s.patches[:half], filler, s.patches[half:], filler]).copy()
+    s.P += 3 * gap
+    ba, T = bind(s)
+    ba.step(1, s.fixed)
+    ba.sync()
+    want = oracle.gn_steps(s, iters=1)[0]
+    rot, tr = pose_error(T["poses"].cpu().numpy(), want[0])
+    dep = depth_error(T["patches"][:, 2, 1, 1].cpu().numpy().astype(np.float64), want[1])
+    assert rot < TOL and tr < TOL and dep < TOL, (rot, tr, dep)
+    for shuffle in (False, True):
+        check_indexing(copy.deepcopy(s), 8, shuffle, keys=False)
 
 
 def test_graph_without_edges_leaves_state_unchanged():
