@@ -21,6 +21,7 @@
 
 #include <algorithm>
 #include <map>
+#include <mutex>
 
 namespace {
 
@@ -768,8 +769,10 @@ ba_status_t radix_sort(ba_handle_t h, unsigned long long* k0, int* v0, unsigned 
 // cached per size (the kernel's limit only ever rises): queried by the eager
 // first run of a binding, so a later capture of the same binding finds it.
 int bind_ctas_per_sm(size_t smem) {
+  static std::mutex mu;  // handles may be bound from several host threads
   static std::map<size_t, int> cache;
   static size_t raised = 0;
+  std::lock_guard<std::mutex> lock(mu);
   auto it = cache.find(smem);
   if (it != cache.end()) return it->second;
   if (smem > raised) {
