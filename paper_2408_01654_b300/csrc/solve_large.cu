@@ -1189,6 +1189,53 @@ __device__ void chain_matrix(const float* X, const float* Y, float* out, bool tr
   __syncthreads();
 }
 
+// The same product for k_lg_chainmat with 128-bit shared loads: X staged
+// transposed (xt[k][r]) and Y as is, both with row stride LDS; thread (ty, tx)
+// of a 16 x 16 grid owns the 4 x 4 block at rows 4ty, columns 4tx, so one
+// k-step is two float4 loads and 16 FMAs, and the block leaves as four float4
+// stores (rows, or for the transpose columns, of the output).
+__device__ void chain_matrix4(const float* X, const float* Y, float* out, bool trans, float* xt, float* ys) {
+  constexpr int PER = TILE / 4 / LG_THREADS;
+  float4 vx[PER], vy[PER];
+#pragma unroll
+  for (int u = 0; u < PER; ++u) {
+    vx[u] = __ldcg(reinterpret_cast<const float4*>(X) + threadIdx.x + u * LG_THREADS);
+    vy[u] = __ldcg(reinterpret_cast<const float4*>(Y) + threadIdx.x + u * LG_THREADS);
+  }
+#pragma unroll
+  for (int u = 0; u < PER; ++u) {
+    const int q = threadIdx.x + u * LG_THREADS;
+    const int r = (4 * q) / NB, c = (4 * q) % NB;
+    xt[(c + 0) * LDS + r] = vx[u].x;
+    xt[(c + 1) * LDS + r] = vx[u].y;
+    xt[(c + 2) * LDS + r] = vx[u].z;
+    xt[(c + 3) * LDS + r] = vx[u].w;
+    *reinterpret_cast<float4*>(ys + r * LDS + c) = vy[u];
+  }
+  __syncthreads();
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  float acc[4][4] = {};
+#pragma unroll 4
+  for (int k = 0; k < NB; ++k) {
+    const float4 xa = *reinterpret_cast<const float4*>(xt + k * LDS + 4 * ty);
+    const float4 yb = *reinterpret_cast<const float4*>(ys + k * LDS + 4 * tx);
+    const float xv[4] = {xa.x, xa.y, xa.z, xa.w}, yv[4] = {yb.x, yb.y, yb.z, yb.w};
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(xv[a], yv[b], acc[a][b]);
+  }
+  const int r0 = 4 * ty, c0 = 4 * tx;
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    if (trans)  // column c0 + e of the product is row c0 + e of the output
+      *reinterpret_cast<float4*>(out + (c0 + e) * NB + r0) = make_float4(acc[0][e], acc[1][e], acc[2][e], acc[3][e]);
+    else
+      *reinterpret_cast<float4*>(out + (r0 + e) * NB + c0) = make_float4(acc[e][0], acc[e][1], acc[e][2], acc[e][3]);
+  }
+  __syncthreads();
+}
+
 // --- double-float (FP32 pair) arithmetic of the refinement's products -------
 struct DFp {
   float h, l;
@@ -1680,8 +1727,8 @@ __global__ void __launch_bounds__(LG_THREADS, 2) k_lg_solve(const LgProb* __rest
 //   u_i = L_ii^-1 b_i - sum_j (L_ii^-1 L_ij) u_j,
 //   w_i = L_ii^-T c_i - sum_j (L_ji L_ii^-1)^T w_j.
 __global__ void __launch_bounds__(LG_THREADS) k_lg_chainmat(const LgProb* __restrict__ probs, const int* status) {
-  __shared__ __align__(16) float gx[NB * LDC];
-  __shared__ __align__(16) float gy[NB * LDC];
+  __shared__ __align__(16) float gx[NB * LDS];
+  __shared__ __align__(16) float gy[NB * LDS];
   if (dpv_status(status)) return;
   const LgProb& P = probs[blockIdx.y];
   const int E = __ldg(P.eoff + P.T);
@@ -1698,9 +1745,9 @@ __global__ void __launch_bounds__(LG_THREADS) k_lg_chainmat(const LgProb* __rest
       out[q] = bwd ? __ldcg(li + c * NB + r) : __ldcg(li + q);
     }
   } else if (!bwd) {
-    chain_matrix(P.Linv + (size_t)a * TILE, P.A + (size_t)(tri2(a) + b) * TILE, out, false, gx, gy);
+    chain_matrix4(P.Linv + (size_t)a * TILE, P.A + (size_t)(tri2(a) + b) * TILE, out, false, gx, gy);
   } else {
-    chain_matrix(P.A + (size_t)(tri2(a) + b) * TILE, P.Linv + (size_t)b * TILE, out, true, gx, gy);
+    chain_matrix4(P.A + (size_t)(tri2(a) + b) * TILE, P.Linv + (size_t)b * TILE, out, true, gx, gy);
   }
 }
 
