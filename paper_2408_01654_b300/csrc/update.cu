@@ -91,7 +91,8 @@ __global__ void k_dx_pairs(int n, const double* __restrict__ dx, float2* __restr
 // The same in double-float (the BA_MIXED path): the depth terms are pairs
 // (128 bytes per edge, assemble_df.cu), the pose step comes as pairs
 // (k_dx_pairs), Ct and w are pairs, and the new depth d + dd is rounded to
-// float once.
+// float once.  Two patches per warp, 16 lanes each (a patch has about a dozen
+// edges), each lane's six depth-term loads issued beside its slot load.
 __global__ void __launch_bounds__(BS_THREADS) k_backsub_dd(
     int P, int G, const int* __restrict__ fdx, float d_min, const int* __restrict__ pptr,
     const float4* __restrict__ pterm, const int* __restrict__ win, const float2* __restrict__ dxv,
@@ -109,32 +110,39 @@ __global__ void __launch_bounds__(BS_THREADS) k_backsub_dd(
       if (posef) dpv_pose_table_row(poses + 7 * (size_t)f, posef + DPV_POSE_ROW * (size_t)f);
     }
   }
-  const int k = blockIdx.x * BS_WARPS + (threadIdx.x >> 5);
-  if (k >= P) return;
-  const int* wf = win + (k / G) * DPV_WMAX;
+  const int hl = lane & 15;
+  const int k = 2 * (blockIdx.x * BS_WARPS + (threadIdx.x >> 5)) + (lane >> 4);
+  if (2 * (blockIdx.x * BS_WARPS + (threadIdx.x >> 5)) >= P) return;  // (uniform over the warp)
+  const bool mine = k < P;
   DF acc = {0.f, 0.f};
-  for (int p = pptr[k] + lane; p < pptr[k + 1]; p += 32) {
-    const float4* t4 = pterm + 8 * (size_t)p;
-    const int sl = __float_as_int(t4[7].x);
-    const int fi = fdx[wf[sl & 0xff]], fj = fdx[wf[sl >> 8]];
+  if (mine) {
+    const int* wf = win + (k / G) * DPV_WMAX;
+    const int p1 = pptr[k + 1];
+    for (int p = pptr[k] + hl; p < p1; p += 16) {
+      const float4* t4 = pterm + 8 * (size_t)p;
+      float4 e[6];
 #pragma unroll
-    for (int side = 0; side < 2; ++side) {
-      const int fo = side == 0 ? fi : fj;
-      if (fo < 0) continue;
-      const float4* e4 = t4 + 3 * side;
-      const float4* x = reinterpret_cast<const float4*>(dxv + fo);  // fo is even: 16-byte aligned
+      for (int q = 0; q < 6; ++q) e[q] = t4[q];
+      const int sl = __float_as_int(t4[7].x);
+      const int fi = fdx[wf[sl & 0xff]], fj = fdx[wf[sl >> 8]];
 #pragma unroll
-      for (int h2 = 0; h2 < 3; ++h2) {
-        const float4 v = e4[h2], xv = x[h2];
-        dd_acc(acc, DF{-v.x, -v.y}, DF{xv.x, xv.y});
-        dd_acc(acc, DF{-v.z, -v.w}, DF{xv.z, xv.w});
+      for (int side = 0; side < 2; ++side) {
+        const int fo = side == 0 ? fi : fj;
+        if (fo < 0) continue;
+        const float4* x = reinterpret_cast<const float4*>(dxv + fo);  // fo is even: 16-byte aligned
+#pragma unroll
+        for (int h2 = 0; h2 < 3; ++h2) {
+          const float4 v = e[3 * side + h2], xv = x[h2];
+          dd_acc(acc, DF{-v.x, -v.y}, DF{xv.x, xv.y});
+          dd_acc(acc, DF{-v.z, -v.w}, DF{xv.z, xv.w});
+        }
       }
     }
   }
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) dd_acc_add(acc, DF{__shfl_xor_sync(0xffffffffu, acc.hi, o),
-                                                     __shfl_xor_sync(0xffffffffu, acc.lo, o)});
-  if (lane == 0) {
+  for (int o = 8; o > 0; o >>= 1) dd_acc_add(acc, DF{__shfl_xor_sync(0xffffffffu, acc.hi, o),
+                                                    __shfl_xor_sync(0xffffffffu, acc.lo, o)});
+  if (hl == 0 && mine) {
     const DF wv = w_ext ? DF{w_ext[k], 0.f} : dd_ld(wk2[k]);
     const DF ddk = dd_div(dd_add(dd_norm(acc), wv), dd_ld(Ct2[k]));
     dd_out[k] = ddk.hi + ddk.lo;
@@ -148,8 +156,8 @@ __global__ void __launch_bounds__(BS_THREADS) k_backsub_dd(
   }
 }
 
-unsigned backsub_grid(ba_handle_t h, int retract) {
-  const long long wb = ((long long)h->P + BS_WARPS - 1) / BS_WARPS;
+unsigned backsub_grid(ba_handle_t h, int retract, int per_warp = 1) {
+  const long long wb = ((long long)h->P + per_warp * BS_WARPS - 1) / (per_warp * BS_WARPS);
   const long long rb = retract ? (long long)h->N : 0;
   return (unsigned)(wb > rb ? wb : rb);
 }
@@ -165,7 +173,7 @@ ba_status_t dpv_backsub(ba_handle_t h, int retract) {
     DPV_CUDA(h, dpv_launch_pdl(k_dx_pairs, dim3((h->n_pad + 255) / 256), dim3(256), 0, h->stream, h->n_pad,
                                (const double*)ws->dx.p, ws->dx2.p, (const int*)ws->status));
     ++h->launches;
-    DPV_CUDA(h, dpv_launch_pdl(k_backsub_dd, dim3(backsub_grid(h, retract)), dim3(BS_THREADS), 0, h->stream, h->P,
+    DPV_CUDA(h, dpv_launch_pdl(k_backsub_dd, dim3(backsub_grid(h, retract, 2)), dim3(BS_THREADS), 0, h->stream, h->P,
                                h->G, ws->fdx.p, h->opt.d_min, ws->pptr.p, ws->pterm.p, ws->win.p,
                                (const float2*)ws->dx2.p, (const float2*)ws->Ct2.p, (const float2*)ws->wk2.p,
                                (const float*)nullptr, h->patches, ws->dd.p, h->N, retract, (const double*)ws->dx.p,
@@ -190,7 +198,7 @@ ba_status_t dpv_backsub_ext(ba_handle_t h, const float* w_ext, float* out) {
   if (h->opt.precision == BA_MIXED) {
     k_dx_pairs<<<(h->n_pad + 255) / 256, 256, 0, h->stream>>>(h->n_pad, ws->dx.p, ws->dx2.p, ws->status);
     ++h->launches;
-    k_backsub_dd<<<backsub_grid(h, 0), BS_THREADS, 0, h->stream>>>(
+    k_backsub_dd<<<backsub_grid(h, 0, 2), BS_THREADS, 0, h->stream>>>(
         h->P, h->G, ws->fdx.p, h->opt.d_min, ws->pptr.p, ws->pterm.p, ws->win.p, ws->dx2.p, ws->Ct2.p, ws->wk2.p,
         w_ext, h->patches, out, h->N, 0, ws->dx.p, h->poses, nullptr, 0, ws->status);
     ++h->launches;
