@@ -102,9 +102,11 @@ __device__ __forceinline__ void rel_pose_warp(const float* __restrict__ Pi, cons
   __syncwarp();
 }
 
-// PIX residual pixels per edge: 1 (the patch centre) or 9 (the whole patch)
+// PIX residual pixels per edge: 1 (the patch centre) or 9 (the whole patch).
+// Five CTAs per SM for PIX = 1 (96 registers, no spills; the kernel issues
+// on about half of its cycles, so more resident warps help), four for 9.
 template <int PIX>
-__global__ void __launch_bounds__(RW * 32) k_runs_dd(
+__global__ void __launch_bounds__(RW * 32, PIX == 1 ? 5 : 4) k_runs_dd(
     int G, int P, const int* __restrict__ fdx, const int* __restrict__ gprob, const SysDesc* __restrict__ sysd,
     float z_min, const int* __restrict__ gptr, const int* __restrict__ grun, const int* __restrict__ gnr,
     const unsigned* __restrict__ eslot, const int* __restrict__ perm, const int* __restrict__ pmpos,
